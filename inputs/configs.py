@@ -1,0 +1,36 @@
+"""The synthetic workloads: sizes, step counts and run parameters.
+
+Values, not arithmetic.  Each entry names what it is; the mesh itself comes
+from inputs.channel.  Model constants (C1, C2, ...) are not here: the library
+and the oracle each carry the paper's table themselves.
+"""
+import math
+
+CHANNEL_COMMON = dict(
+    jitter=0.2,
+    seed=1,
+    dt=1e-3,
+    nu=1e-3,           # Re ~ 1000 on centreline velocity and half width
+    Pi=2e-3,           # imposed -d<P>/dx = 2*nu: laminar balance of U = 1 - y^2
+    u_profile="parabola",  # initial mean U(y) = 1 - y^2
+    u_sigma=0.1,       # N(0, 0.1^2) fluctuations on every component
+    omega_init="gamma4",   # Gamma(k=4, theta=0.25): mean 1, variance 1/4
+    psi_slab_x=0.5,    # psi = 1 in elements touching x = 0.5
+    closure="glm",
+)
+
+CONFIGS = {
+    # small case: the oracle finishes it in seconds
+    "channel_20x40_ppe50": dict(CHANNEL_COMMON, nx=20, ny=40, ppe=50, steps=100),
+    # the measured workload: ~16M particles on ~160k triangles
+    "channel_200x400_ppe100": dict(CHANNEL_COMMON, nx=200, ny=400, ppe=100, steps=1000),
+}
+
+
+def workload(name):
+    cfg = dict(CONFIGS[name])
+    cfg["name"] = name
+    cfg["n_tri"] = 2 * (cfg["nx"] - 1) * (cfg["ny"] - 1)
+    cfg["n_particles"] = cfg["n_tri"] * cfg["ppe"]
+    cfg["period"] = 2.0 * math.pi
+    return cfg
