@@ -1,0 +1,339 @@
+"""Benchmark of the particle time step (SDE + tracking + PIC statistics).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One step = pdf_step (coefficient rows + the fused particle kernel) followed by
+pdf_estimate_stats (grouping, element and node statistics, derivatives): every
+row a1-a12 of the hot path, on the channel workload of 200 x 400 nodes,
+158,802 triangles and 100 particles per element (15,880,200 particles).
+The particle state (1.02 GB) is larger than the 129 MB L2, so no flush is
+needed between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
+host cores instead (a bounded sample of the same workload).
+With --gpus N > 1 (under torchrun) each rank runs an independent replica.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import inputs  # noqa: E402
+
+WORKLOAD = "channel_200x400_ppe100"
+METRIC = "particle-steps/s (SDE+search+PIC stats) at 16M particles; % HBM roofline"
+UNIT = "particle-steps/s"
+# Algorithmic DRAM bytes of the fused particle kernel per particle: read x, y,
+# u, v, w, omega, psi (56) and elem (4); write the same (60).  Per element
+# per launch: the coefficient row (256) and the tracking geometry (80).
+K_STEP_BYTES_PER_PARTICLE = 120
+K_STEP_BYTES_PER_ELEMENT = 336
+# Algorithmic bytes of the whole step per particle (state read and written
+# once, element and node tables amortised), the denominator of the
+# whole-step roofline fraction.
+STEP_BYTES_PER_PARTICLE = 134
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_sha():
+    h = hashlib.sha256()
+    for f in ("step.cu", "rng.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1006_0720_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_from_profile():
+    """DRAM bytes per k_step launch from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "k_step_channel_200x400_ppe100.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != _kernel_sha():
+        return None
+    return float(m_b.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", "pdfgb_clocks_%d_%d.csv" % (os.getpid(), index))
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _setup_dist(n_gpus):
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    return rank, world, local, dist
+
+
+def cpu_baseline_measure(steps=1):
+    """The oracle as it stands, single-threaded on a host core, on a bounded
+    sample of the workload: the full 15.9M-particle channel, `steps` steps
+    (coefficients + particle step + statistics), init untimed."""
+    import oracle
+    cfg = inputs.workload(WORKLOAD)
+    m = inputs.channel_mesh(cfg["nx"], cfg["ny"], jitter=cfg["jitter"], seed=cfg["seed"])
+    M = oracle.Mesh(m)
+    counts = np.full(cfg["n_tri"], cfg["ppe"], dtype=np.int32)
+    st = oracle.init(M, counts, cfg["seed"], u_sigma=cfg["u_sigma"],
+                     elem_psi0=inputs.scalar_slab(m, cfg["psi_slab_x"]))
+    P = oracle.make_params(dt=cfg["dt"], nu=cfg["nu"], Pi=cfg["Pi"], closure=cfg["closure"])
+    es, ns, nd, _ = oracle.statistics(M, st)
+    t0 = time.perf_counter()
+    for s in range(steps):
+        rows = oracle.elem_coeff(M, ns, nd, P)
+        oracle.step(M, rows, P, cfg["seed"], s, st)
+        es, ns, nd, _ = oracle.statistics(M, st, ns)
+    dt = time.perf_counter() - t0
+    n = cfg["n_particles"]
+    return {"value": n * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d step(s) of the full %d-particle workload (init untimed), %.1f s" % (steps, n, dt)}
+
+
+def run_reference(args):
+    rank, world, local, dist = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0, None
+    if rank != 0:
+        return 0
+    times = []
+    base = None
+    for _ in range(args.warmup):
+        cpu_baseline_measure(1)
+    for _ in range(args.steps):
+        base = cpu_baseline_measure(1)
+        times.append(base["value"])
+    value = statistics.median(times) if times else 0.0
+    cfg = inputs.workload(WORKLOAD)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * cfg["n_particles"] / value if value else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n_particles": cfg["n_particles"],
+                                            "n_tri": cfg["n_tri"], "closure": cfg["closure"]},
+            "cpu_baseline": dict(base, value=value) if base else None,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import paper_1006_0720_gb300 as pg
+
+    rank, world, local, dist = _setup_dist(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = inputs.workload(args.workload)
+    m = inputs.channel_mesh(cfg["nx"], cfg["ny"], jitter=cfg["jitter"], seed=cfg["seed"])
+    psi = inputs.scalar_slab(m, cfg["psi_slab_x"])
+    gm = pg.Mesh(m)
+    seed = cfg["seed"] + rank  # independent replicas
+    gp = pg.Particles(gm, seed, ppe=cfg["ppe"], u_sigma=cfg["u_sigma"], elem_psi0=psi)
+    n = gp.n
+    p = pg.model_params(dt=cfg["dt"], nu=cfg["nu"], Pi=cfg["Pi"], closure=cfg["closure"])
+    stream = torch.cuda.current_stream(dev)
+    pg.pdf_estimate_stats(gp, gm)
+    step_no = 0
+    for _ in range(args.warmup):
+        pg.pdf_step(gp, gm, p, step=step_no)
+        pg.pdf_estimate_stats(gp, gm)
+        step_no += 1
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    clocks = ClockSampler(local)
+    pg.pdf_profile_reset()
+    pg.pdf_profile_enable(True)
+    launches0 = pg.pdf_kernel_launches()
+    barrier()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        pg.pdf_step(gp, gm, p, step=step_no, stream=stream)
+        pg.pdf_estimate_stats(gp, gm, stream=stream)
+        step_no += 1
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = pg.pdf_kernel_launches() - launches0
+    pg.pdf_profile_enable(False)
+    ms = ev0.elapsed_time(ev1)
+    k_launch, k_ms = pg.pdf_profile_query("k_step")
+    shares = {}
+    for kname in ("k_step", "k_radix_scatter", "k_radix_hist", "k_elem_stats", "k_node_coeff",
+                  "k_elem_rows", "k_seg_offsets", "k_node_stats", "k_scan_reduce", "k_scan_apply",
+                  "k_scan_top", "k_elem_grad1", "k_node_grad1", "k_elem_grad2", "k_node_grad2"):
+        c, t = pg.pdf_profile_query(kname)
+        shares[kname] = {"launches": c, "ms_per_launch": t / c if c else None, "share": t / ms if ms else None}
+    pg.pdf_profile_reset()
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * n * args.steps / (t_max * 1e-3)
+
+    # ---- end-to-end through the public API with host-resident state
+    keys = ("x", "y", "u", "v", "w", "om", "ps")
+    host = {k: torch.empty(n, dtype=torch.float64, pin_memory=True) for k in keys}
+    host["elem"] = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    host_ns = torch.empty((gm.n_nodes, 12), dtype=torch.float64, pin_memory=True)
+    ptr = {k: v.data_ptr() for k, v in host.items()}
+    import ctypes
+    L = pg.lib()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    pg.capi.check(L.pdf_particles_get_state(gp.handle, *[ctypes.c_void_p(ptr[k]) for k in keys + ("elem",)], sp),
+                  "get_state")
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        pg.capi.check(L.pdf_particles_set_state(gp.handle, *[ctypes.c_void_p(ptr[k]) for k in keys + ("elem",)], sp),
+                      "set_state")
+        pg.pdf_step(gp, gm, p, step=step_no, stream=stream)
+        pg.capi.check(L.pdf_estimate_stats(gp.handle, gm.handle, None, ctypes.c_void_p(host_ns.data_ptr()), None, sp),
+                      "estimate_stats")
+        pg.capi.check(L.pdf_particles_get_state(gp.handle, *[ctypes.c_void_p(ptr[k]) for k in keys + ("elem",)], sp),
+                      "get_state")
+        stream.synchronize()
+        step_no += 1
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_max = e2e_s
+    if dist is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_max = float(t.item())
+    state_bytes = n * (7 * 8 + 4)
+    e2e = {"value": world * n * e2e_steps / e2e_max, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+           "d2h_bytes_per_step": state_bytes + gm.n_nodes * 12 * 8, "steps": e2e_steps,
+           "what": "state in page-locked host memory: copied in, stepped, statistics and state copied out every step"}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    peak, peak_kind = _peaks()
+    k_avg_ms = k_ms / k_launch if k_launch else float("nan")
+    k_bytes = K_STEP_BYTES_PER_PARTICLE * n + K_STEP_BYTES_PER_ELEMENT * gm.n_tri
+    achieved = k_bytes / (k_avg_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_step", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": _traffic_from_profile(), "peak_source": peak_kind,
+                "bytes_per_launch_alg": k_bytes, "ms_per_launch": k_avg_ms}
+    step_frac = STEP_BYTES_PER_PARTICLE * (n * args.steps / (ms * 1e-3)) / (peak * 1e9)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n_particles": n, "n_tri": gm.n_tri, "n_nodes": gm.n_nodes,
+                       "closure": cfg["closure"], "dt": cfg["dt"],
+                       "l2": "inputs larger than L2: particle state %.2f GB vs 129 MB L2" % (n * 64 / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "hbm_frac_step": step_frac, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roofline, "kernels": shares}
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            line["cpu_baseline"] = cpu_baseline_measure(1)
+        except Exception as exc:  # report, do not hide
+            line["cpu_baseline"] = {"error": repr(exc)}
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, help="a smaller workload for profiling runs")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,248 @@
+/*
+ * pdfgb — the particle time step of the joint velocity-frequency-scalar PDF
+ * method on unstructured triangle grids (J. Bakosi, "PDF modeling of
+ * turbulent flows on unstructured grids", 2008), as a C-ABI library of
+ * hand-written CUDA kernels for one GB300 (sm_103a).
+ *
+ * Conventions for every entry point:
+ *   - Return value: a pdf_status.  Nothing throws or aborts.  On failure
+ *     pdf_last_error() returns a message (thread-local, valid until the next
+ *     call on the same thread).
+ *   - "host" pointers are read (or written) before the call returns.
+ *     "device" pointers are caller-owned CUDA global memory on the current
+ *     device; they are borrowed for the work enqueued on `stream` and must
+ *     stay valid until that work completes.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     enqueued asynchronously; errors raised by the device surface as
+ *     PDF_ECUDA at the next call that synchronizes.
+ *   - Handles (pdf_mesh, pdf_particles) are library-owned and freed with the
+ *     matching *_destroy.  A handle may be used by one thread at a time.
+ *   - Particle arrays are structure-of-arrays in particle-id order.
+ */
+#ifndef PDFGB_H
+#define PDFGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PDF_OK = 0,
+  PDF_EINVAL = 1,    /* bad argument: NULL handle, size out of range, inconsistent mesh */
+  PDF_ENOMEM = 2,    /* device or host allocation failed */
+  PDF_ECUDA = 3,     /* a CUDA runtime call or kernel failed */
+  PDF_ELOST = 4,     /* a particle could not be located (counted in pdf_step_info.lost) */
+  PDF_ENOTCONV = 5,  /* an iterative solve hit its iteration cap */
+  PDF_ENUMERIC = 6,  /* non-finite values found */
+  PDF_ESTATE = 7     /* call out of order (e.g. pdf_step before any statistics) */
+} pdf_status;
+
+typedef struct pdf_mesh pdf_mesh;
+typedef struct pdf_particles pdf_particles;
+
+/* Boundary-edge tags (sec. 3.5: boundary neighbours are tagged). */
+enum { PDF_TAG_WALL = 1, PDF_TAG_PERIODIC = 2, PDF_TAG_INFLOW = 3, PDF_TAG_OUTFLOW = 4 };
+
+/* Velocity closure.
+ * GLM: generalized Langevin model, eq. Lagrangian-model with G_ij and C0 from
+ *      the elliptic-relaxation tensor by eq. GandC; eps by eq.
+ *      dissipation-from-frequency_wall.
+ * SLM: simplified Langevin model with wall functions, eqs.
+ *      Lagrangian-position-wf, Lagrangian-model-wf and wall-GandC (C0 = 3.5).
+ * FROZEN: the caller supplies the element-average coefficient rows. */
+enum { PDF_CLOSURE_GLM = 0, PDF_CLOSURE_SLM = 1, PDF_CLOSURE_FROZEN = 2 };
+/* Micromixing time scale: TURB = max(k/eps, C_T sqrt(nu/eps)) (the turbulence
+ * part of eq. micromixing-timescale-channel); CPHI = 2/(C_phi <omega>). */
+enum { PDF_TM_TURB = 0, PDF_TM_CPHI = 1 };
+/* Mean pressure gradient: NONE = 0; CHANNEL = imposed -d<P>/dx = Pi and the
+ * cross-stream balance (1/rho) d<P>/dy = -d<v^2>/dy (eq. cross-stream-mean-
+ * momentum-channel). */
+enum { PDF_PRESSURE_NONE = 0, PDF_PRESSURE_CHANNEL = 1 };
+/* Storage precision of u, v, w, omega, psi.  Positions are always FP64. */
+enum { PDF_FP64 = 0, PDF_FP32_STATE = 1 };
+
+/* Number of element-average coefficients a particle sees (layout below). */
+#define PDF_NCOEF 26
+/* Element statistics: N, <U>, <V>, <W>, <omega>, <phi>, <uu>, <vv>, <ww>,
+ * <uv>, <uw>, <vw>, <phi'^2> (sec. 3.3; central moments with 1/N). */
+#define PDF_NES 13
+/* Node statistics: the element layout without N. */
+#define PDF_NNS 12
+/* Node derivatives: dU/dx, dU/dy, dV/dx, dV/dy, dW/dx, dW/dy, lap<U>,
+ * lap<V>, lap<W>, d<vv>/dy (sec. 3.4, two-pass second derivatives). */
+#define PDF_NND 10
+
+typedef struct {
+  double dt;        /* time step */
+  double nu;        /* kinematic viscosity */
+  double Pi;        /* imposed -d<P>/dx for PDF_PRESSURE_CHANNEL */
+  double c_phi;     /* C_phi for PDF_TM_CPHI */
+  int32_t closure;  /* PDF_CLOSURE_* */
+  int32_t tm_mode;  /* PDF_TM_* */
+  int32_t pressure; /* PDF_PRESSURE_* */
+  int32_t reserved;
+  /* model constants, table "Constants for modeling the joint PDF of velocity
+   * and frequency" (ch. 4), and C0 of eq. wall-GandC */
+  double C1, C2, C3, C4, CT, CL, Ceta, Cv, gamma5, Comega1, Comega2, C0_slm;
+} pdf_model_params;
+
+/* Fills the paper's constants and dt = 1e-3, nu = 1e-3, Pi = 2e-3,
+ * c_phi = 2, GLM, TURB, CHANNEL. */
+void pdf_model_params_default(pdf_model_params* p);
+
+typedef struct {
+  const int32_t* count;      /* host [n_tri]: particles per element, or NULL to use ppe */
+  int32_t ppe;               /* particles per element when count == NULL */
+  int32_t u_profile;         /* 0: zero mean velocity; 1: channel profile U = 1 - y^2 */
+  double u_sigma;            /* standard deviation of each velocity component */
+  const double* elem_psi0;   /* host [n_tri]: initial scalar per element, or NULL for 0 */
+} pdf_init_params;
+
+/* Per-step counters (filled when pdf_step is given a non-NULL info). */
+typedef struct {
+  int64_t walk_steps;          /* neighbour-walk steps over all particles */
+  int64_t reflections;         /* wall reflections */
+  int64_t crossings_periodic;  /* periodic-seam crossings */
+  int64_t fallbacks;           /* particles found by the concave-corner fall-back */
+  int64_t brute;               /* particles that needed the all-element search */
+  int64_t lost;                /* particles not found (state kept, elem unchanged) */
+  int64_t omega_reflections;   /* omega < 0 after the Euler-Maruyama step, reflected */
+  int64_t near_face;           /* particles within 1e-12 (relative) of an element edge */
+} pdf_step_info;
+
+/* ---------------------------------------------------------------- mesh */
+
+/* Builds the element-surrounding-element list with tagged boundary
+ * neighbours and the node-surrounding-element lists (sec. 3.3 linked lists,
+ * sec. 3.5) on the host and uploads the mesh to the current device.
+ *   node_xy  host [n_nodes][2] node coordinates
+ *   tri      host [n_tri][3] node ids, counter-clockwise (else PDF_EINVAL)
+ *   twin     host [n_nodes] periodic twin node or -1; may be NULL.  Twin
+ *            nodes are one node for statistics; edges tagged PERIODIC are
+ *            matched to the element holding the twin edge.
+ *   bnd_edge host [n_bnd][3] (node a, node b, PDF_TAG_*) for every boundary
+ *            edge (an edge with one element).  An untagged boundary edge is
+ *            PDF_EINVAL.
+ *   period_x the x-period (the shift applied when crossing a PERIODIC edge).
+ * Sizes: n_nodes, n_tri >= 1 and < 2^31.  *out receives the handle. */
+pdf_status pdf_mesh_create(const double* node_xy, int32_t n_nodes, const int32_t* tri,
+                           int32_t n_tri, const int32_t* twin, const int32_t* bnd_edge,
+                           int32_t n_bnd, double period_x, pdf_mesh** out);
+pdf_status pdf_mesh_destroy(pdf_mesh* m);
+/* Host copies of the connectivity (for checking): nbr [n_tri][3] neighbour
+ * across the edge opposite local vertex k (>= 0 element, -1 wall, -3 inflow,
+ * -4 outflow); shift [n_tri][3] periodic x-shift multiplier.  Either may be NULL. */
+pdf_status pdf_mesh_connectivity(const pdf_mesh* m, int32_t* nbr, int32_t* shift);
+pdf_status pdf_mesh_size(const pdf_mesh* m, int32_t* n_nodes, int32_t* n_tri);
+
+/* ---------------------------------------------------------------- particles */
+
+/* Particle initialisation (sec. 3.6): count[e] (or ppe) particles uniform in
+ * each element, particle ids element by element; velocity = profile +
+ * u_sigma N(0,1) per component; omega ~ Gamma(k=4, theta=1/4) (unit mean,
+ * variance 1/4); psi = elem_psi0[e] or 0.  Random numbers: Philox4x32-10
+ * keyed by seed, counter (particle id, 0, block, 1).
+ * precision: PDF_FP64 (PDF_FP32_STATE is reserved, PDF_EINVAL for now).
+ * Allocates all per-particle and per-mesh device buffers.  The mesh must
+ * outlive the particles. */
+pdf_status pdf_particles_init(const pdf_mesh* m, const pdf_init_params* ip, uint64_t seed,
+                              int32_t precision, void* stream, pdf_particles** out);
+pdf_status pdf_particles_destroy(pdf_particles* p);
+pdf_status pdf_particles_count(const pdf_particles* p, int64_t* n);
+
+/* Copies the state into caller buffers [n] (any pointer may be NULL).  The
+ * buffers may be device memory or page-locked host memory (the copies are
+ * cudaMemcpyDefault, asynchronous on `stream`).  elem: host element id of
+ * each particle. */
+pdf_status pdf_particles_get_state(const pdf_particles* p, double* x, double* y, double* u,
+                                   double* v, double* w, double* om, double* ps, int32_t* elem,
+                                   void* stream);
+/* Overwrites the state from caller buffers [n] (all required; device or
+ * page-locked host memory).  elem must hold each particle's host element
+ * (not checked). */
+pdf_status pdf_particles_set_state(pdf_particles* p, const double* x, const double* y,
+                                   const double* u, const double* v, const double* w,
+                                   const double* om, const double* ps, const int32_t* elem,
+                                   void* stream);
+
+/* ---------------------------------------------------------------- the step */
+
+/* One explicit Euler-Maruyama step of every particle (sec. 2 summary):
+ *   velocity prediction, eq. velocity-prediction (SLM: eq. Lagrangian-model-wf);
+ *   position, eq. Lagrangian-position-exact with the same dW_j as the
+ *     d<U_i>/dx_j term (SLM: eq. Lagrangian-position-wf);
+ *   frequency, eq. frequency-model (a negative result is reflected);
+ *   scalar, eq. IEM;
+ *   then the neighbour walk of sec. 3.5 with periodic seams and reflecting
+ *   walls (position mirrored, wall-normal velocity reversed).
+ * Random numbers: Philox4x32-10 keyed by seed, counter (particle id, step,
+ * block, 0), 6 Gaussians per particle (sec. 3.8 draws 6 per particle).
+ * Coefficients: for GLM/SLM the element averages of the nodal coefficients
+ * computed from the statistics of the last pdf_estimate_stats (sec. 3.3) and,
+ * for GLM, from wp; for FROZEN from elem_coeff.
+ *   params      host; params->closure selects the model
+ *   wp          device [9][n_nodes] elliptic-relaxation tensor at the nodes
+ *               (component-major, wp[(3i+j)*n_nodes + n]) or NULL for the
+ *               local model (wp = right-hand side of eq. elliptic-relaxation-
+ *               Lagrangian); ignored unless GLM
+ *   elem_coeff  device [n_tri][PDF_NCOEF] for FROZEN (ignored otherwise):
+ *               <U_i>(3), d<U_i>/dx_j (6: Ux Uy Vx Vy Wx Wy), a_i = -d<P>/dx_i
+ *               + 2 nu lap<U_i> (3), G_ij row-major (9), sqrt(C0 eps),
+ *               <omega>, S_omega, <phi>, 1/t_m
+ *   step        the step number (Philox counter word 1)
+ *   info        host, may be NULL; when given the call synchronizes `stream`
+ *               and fills the counters.  Returns PDF_ELOST if any particle
+ *               was lost (the rest of the step is still applied).
+ * PDF_ESTATE if GLM/SLM is requested before any pdf_estimate_stats. */
+pdf_status pdf_step(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,
+                    const double* wp, const double* elem_coeff, uint32_t step, void* stream,
+                    pdf_step_info* info);
+
+/* Particle-in-cell statistics (sec. 3.3) and derivatives (sec. 3.4):
+ * groups particles by element (stable radix sort by element id), element
+ * means and central moments (two passes, 1/N), node averages over the
+ * non-empty surrounding elements (a node with none keeps its previous value),
+ * node gradients of the means, second derivatives by the two-pass procedure,
+ * and d<vv>/dy.  The library keeps the results for the next pdf_step; the
+ * optional outputs receive copies (device or page-locked host memory,
+ * layouts PDF_NES / PDF_NNS / PDF_NND per element or node). */
+pdf_status pdf_estimate_stats(pdf_particles* p, const pdf_mesh* m, double* elem_stats,
+                              double* node_stats, double* node_derivs, void* stream);
+
+/* The element-average coefficient rows [n_tri][PDF_NCOEF] that pdf_step
+ * would use for GLM/SLM with this wp (device output). */
+pdf_status pdf_elem_coeff(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,
+                          const double* wp, double* rows, void* stream);
+
+/* ---------------------------------------------------------------- random numbers */
+
+/* The library's Gaussian draw, exposed for checking: for i = 0..n-1 the four
+ * N(0,1) values of Philox4x32-10 block (key = seed, counter (i, c1, c2, c3))
+ * through the FP32 Box-Muller transform.  out: device float [n][4]. */
+pdf_status pdf_rng_gauss(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3, int64_t n,
+                         float* out, void* stream);
+
+/* ---------------------------------------------------------------- measurement */
+
+/* Kernel timing for measurements: while enabled, every kernel the library
+ * launches is bracketed by CUDA events on its launch stream.  The paper has
+ * no counterpart; it only reports per-stage shares of a time step.
+ * pdf_profile_query waits for the recorded events of the named kernel
+ * (e.g. "k_step") and returns how many launches were recorded and their
+ * summed duration since the last reset. */
+pdf_status pdf_profile_enable(int32_t on);
+pdf_status pdf_profile_reset(void);
+pdf_status pdf_profile_query(const char* kernel, int64_t* launches, double* total_ms);
+/* Number of kernels the library has launched in this process. */
+int64_t pdf_kernel_launches(void);
+
+/* ---------------------------------------------------------------- misc */
+const char* pdf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDFGB_H */

@@ -24,6 +24,8 @@ CONFIGS = {
     "channel_20x40_ppe50": dict(CHANNEL_COMMON, nx=20, ny=40, ppe=50, steps=100),
     # the measured workload: ~16M particles on ~160k triangles
     "channel_200x400_ppe100": dict(CHANNEL_COMMON, nx=200, ny=400, ppe=100, steps=1000),
+    # the same mesh with fewer particles (3.2M, state 200 MB > L2): profiler captures
+    "channel_200x400_ppe20": dict(CHANNEL_COMMON, nx=200, ny=400, ppe=20, steps=1000),
 }
 
 

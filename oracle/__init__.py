@@ -101,7 +101,7 @@ def lib():
             L.or_node_coeff.argtypes = [PD, PD, PD, ctypes.POINTER(_Params), PD]
             L.or_elem_coeff.argtypes = [ctypes.c_void_p, PD, PD, PD, ctypes.POINTER(_Params), PD]
             L.or_step.argtypes = [ctypes.c_void_p, ctypes.c_long, PD, ctypes.POINTER(_Params),
-                                  ctypes.c_uint64, U32, PD, PD, PD, PD, PD, PD, PD, PI, PI, PL]
+                                  ctypes.c_uint64, U32, PD, PD, PD, PD, PD, PD, PD, PI, PI, PL, PI]
             _lib = L
     return _lib
 
@@ -274,15 +274,17 @@ def elem_coeff(mesh, ns, nd, params, wp=None):
     return rows
 
 
-def step(mesh, rows, params, seed, step_no, st):
-    """Advance every particle one step in place.  Returns (counters, status)."""
+def step(mesh, rows, params, seed, step_no, st, pid=None):
+    """Advance every particle one step in place.  Returns (counters, status).
+    pid: particle ids of the entries (default: their index)."""
     n = len(st["x"])
+    pid = None if pid is None else np.ascontiguousarray(pid, dtype=np.int32)
     rows = np.ascontiguousarray(rows, dtype=np.float64)
     status = np.zeros(n, dtype=np.int32)
     counters = np.zeros(8, dtype=np.int64)
     lib().or_step(mesh._h, n, _p(rows, D), ctypes.byref(params), int(seed), int(step_no),
                   *[_p(st[k], D) for k in STATE_KEYS], _p(st["elem"], I), _p(status, I),
-                  counters.ctypes.data_as(PL))
+                  counters.ctypes.data_as(PL), None if pid is None else _p(pid, I))
     names = ["walk_steps", "reflections", "crossings_periodic", "fallbacks", "brute", "lost",
              "omega_reflections", "near_face"]
     return dict(zip(names, counters.tolist())), status

@@ -731,10 +731,12 @@ void or_elem_coeff(const or_mesh* m, const double* ns, const double* nd, const d
  * rows: element-average coefficients [n_tri][26].  status_out: per-particle
  * tracking status bits (may be NULL); counters: [0] walk steps, [1]
  * reflections, [2] periodic crossings, [3] fallbacks, [4] brute-force,
- * [5] lost, [6] omega reflections, [7] near-face (min sub-area / A_e < 1e-12). */
+ * [5] lost, [6] omega reflections, [7] near-face (min sub-area / A_e < 1e-12).
+ * pid: the particle id of each entry (NULL: the index), for stepping a
+ * subset of particles. */
 void or_step(const or_mesh* m, long n_p, const double* rows, const or_params* P, uint64_t seed,
              uint32_t step, double* x, double* y, double* u, double* v, double* w, double* om,
-             double* ps, int* elem, int* status_out, long* counters) {
+             double* ps, int* elem, int* status_out, long* counters, const int* pid) {
   double sdt = sqrt(P->dt);
   double s2nu = (P->closure == OR_CLOSURE_SLM) ? 0.0 : sqrt(2.0 * P->nu);
   for (int i = 0; i < 8; ++i) counters[i] = 0;
@@ -742,8 +744,9 @@ void or_step(const or_mesh* m, long n_p, const double* rows, const or_params* P,
     int e = elem[p];
     const double* c = rows + OR_NCOEF * e;
     float g[8];
-    or_gauss4(seed, (uint32_t)p, step, 0u, OR_PURPOSE_STEP, &g[0]);
-    or_gauss4(seed, (uint32_t)p, step, 1u, OR_PURPOSE_STEP, &g[4]);
+    uint32_t id = pid ? (uint32_t)pid[p] : (uint32_t)p;
+    or_gauss4(seed, id, step, 0u, OR_PURPOSE_STEP, &g[0]);
+    or_gauss4(seed, id, step, 1u, OR_PURPOSE_STEP, &g[4]);
     double dWx = sdt * (double)g[0], dWy = sdt * (double)g[1];
     double dWp[3] = {sdt * (double)g[2], sdt * (double)g[3], sdt * (double)g[4]};
     double dWo = sdt * (double)g[5];

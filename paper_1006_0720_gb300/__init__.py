@@ -1,0 +1,16 @@
+"""GB300-native particle time step of the joint velocity-frequency-scalar PDF
+method (Bakosi 2008) behind a C-ABI library of hand-written sm_103a kernels.
+
+The Python layer only marshals arguments; `capi.lib()` loads libpdfgb.so
+(building it with nvcc if needed) and raises if that is impossible.
+"""
+from . import capi
+from .capi import PdfError, lib
+from .api import (Mesh, Particles, model_params, pdf_elem_coeff, pdf_estimate_stats, pdf_kernel_launches,
+                  pdf_last_error, pdf_mesh_create, pdf_particles_init, pdf_profile_enable,
+                  pdf_profile_query, pdf_profile_reset, pdf_rng_gauss, pdf_step)
+
+__all__ = ["capi", "PdfError", "lib", "Mesh", "Particles", "model_params", "pdf_mesh_create",
+           "pdf_particles_init", "pdf_step", "pdf_estimate_stats", "pdf_elem_coeff", "pdf_rng_gauss",
+           "pdf_last_error", "pdf_profile_enable", "pdf_profile_reset", "pdf_profile_query",
+           "pdf_kernel_launches"]

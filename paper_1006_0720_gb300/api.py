@@ -1,0 +1,213 @@
+"""Python binding of libpdfgb with the C names (argument marshalling only).
+
+Device buffers are torch CUDA tensors; every step of the computation runs in
+the library's CUDA kernels.  Streams default to torch's current stream.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import capi
+from .capi import check, lib
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t, dtype=None, numel=None):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("expected %s, got %s" % (dtype, t.dtype))
+    if numel is not None and t.numel() != numel:
+        raise ValueError("expected %d elements, got %d" % (numel, t.numel()))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def model_params(**kw):
+    """pdf_model_params with the library defaults, then the given overrides.
+    closure / tm_mode / pressure accept names ("glm", "slm", "frozen"; "turb",
+    "cphi"; "none", "channel")."""
+    p = capi.ModelParams()
+    lib().pdf_model_params_default(ctypes.byref(p))
+    names = {"closure": {"glm": 0, "slm": 1, "frozen": 2}, "tm_mode": {"turb": 0, "cphi": 1},
+             "pressure": {"none": 0, "channel": 1}}
+    for k, v in kw.items():
+        if k in names and isinstance(v, str):
+            v = names[k][v]
+        setattr(p, k, v)
+    return p
+
+
+class Mesh:
+    """Owns a pdf_mesh handle."""
+
+    def __init__(self, mesh):
+        xy = np.ascontiguousarray(mesh["xy"], dtype=np.float64)
+        tri = np.ascontiguousarray(mesh["tri"], dtype=np.int32)
+        twin = mesh.get("twin")
+        twin = None if twin is None else np.ascontiguousarray(twin, dtype=np.int32)
+        bnd = np.ascontiguousarray(mesh["bnd"], dtype=np.int32)
+        h = ctypes.c_void_p()
+        check(lib().pdf_mesh_create(
+            xy.ctypes.data_as(capi.PD), len(xy), tri.ctypes.data_as(capi.PI32), len(tri),
+            None if twin is None else twin.ctypes.data_as(capi.PI32),
+            bnd.ctypes.data_as(capi.PI32), len(bnd), float(mesh.get("period", 0.0)),
+            ctypes.byref(h)), "pdf_mesh_create")
+        self.handle = h
+        self.n_nodes, self.n_tri = len(xy), len(tri)
+
+    def connectivity(self):
+        nbr = np.zeros((self.n_tri, 3), dtype=np.int32)
+        shift = np.zeros((self.n_tri, 3), dtype=np.int32)
+        check(lib().pdf_mesh_connectivity(self.handle, nbr.ctypes.data_as(capi.PI32),
+                                          shift.ctypes.data_as(capi.PI32)), "pdf_mesh_connectivity")
+        return nbr, shift
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pdf_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Particles:
+    """Owns a pdf_particles handle (the particle state lives in the library)."""
+
+    def __init__(self, mesh, seed, ppe=None, count=None, u_profile="parabola", u_sigma=0.1,
+                 elem_psi0=None, precision=capi.PDF_FP64, stream=None):
+        ip = capi.InitParams()
+        keep = []
+        if count is not None:
+            c = np.ascontiguousarray(count, dtype=np.int32)
+            keep.append(c)
+            ip.count = c.ctypes.data_as(capi.PI32)
+        ip.ppe = int(ppe or 0)
+        ip.u_profile = {"zero": 0, "parabola": 1}[u_profile] if isinstance(u_profile, str) else int(u_profile)
+        ip.u_sigma = float(u_sigma)
+        if elem_psi0 is not None:
+            ps = np.ascontiguousarray(elem_psi0, dtype=np.float64)
+            keep.append(ps)
+            ip.elem_psi0 = ps.ctypes.data_as(capi.PD)
+        h = ctypes.c_void_p()
+        check(lib().pdf_particles_init(mesh.handle, ctypes.byref(ip), int(seed), int(precision),
+                                       _stream(stream), ctypes.byref(h)), "pdf_particles_init")
+        self.handle = h
+        self.mesh = mesh
+        n = ctypes.c_int64()
+        check(lib().pdf_particles_count(h, ctypes.byref(n)), "pdf_particles_count")
+        self.n = n.value
+
+    def get_state(self, stream=None):
+        dev = torch.device("cuda")
+        out = {k: torch.empty(self.n, dtype=torch.float64, device=dev)
+               for k in ("x", "y", "u", "v", "w", "om", "ps")}
+        out["elem"] = torch.empty(self.n, dtype=torch.int32, device=dev)
+        check(lib().pdf_particles_get_state(self.handle, *[_ptr(out[k]) for k in
+                                                            ("x", "y", "u", "v", "w", "om", "ps", "elem")],
+                                            _stream(stream)), "pdf_particles_get_state")
+        return out
+
+    def set_state(self, st, stream=None):
+        args = []
+        for k in ("x", "y", "u", "v", "w", "om", "ps"):
+            args.append(_ptr(st[k], torch.float64, self.n))
+        args.append(_ptr(st["elem"], torch.int32, self.n))
+        check(lib().pdf_particles_set_state(self.handle, *args, _stream(stream)), "pdf_particles_set_state")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pdf_particles_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pdf_mesh_create(mesh):
+    return Mesh(mesh)
+
+
+def pdf_particles_init(mesh, seed, **kw):
+    return Particles(mesh, seed, **kw)
+
+
+def pdf_step(particles, mesh, params, wp=None, elem_coeff=None, step=0, stream=None, info=False):
+    """One particle time step.  Returns the counters dict when info=True."""
+    si = capi.StepInfo() if info else None
+    st = lib().pdf_step(particles.handle, mesh.handle, ctypes.byref(params),
+                        _ptr(wp, torch.float64, None if wp is None else 9 * mesh.n_nodes),
+                        _ptr(elem_coeff, torch.float64, None if elem_coeff is None else capi.PDF_NCOEF * mesh.n_tri),
+                        int(step) & 0xFFFFFFFF, _stream(stream), ctypes.byref(si) if si is not None else None)
+    if info and st == capi.PDF_ELOST:
+        d = si.as_dict()
+        d["status"] = "lost"
+        return d
+    check(st, "pdf_step")
+    return si.as_dict() if info else None
+
+
+def pdf_estimate_stats(particles, mesh, elem_stats=None, node_stats=None, node_derivs=None, stream=None):
+    check(lib().pdf_estimate_stats(particles.handle, mesh.handle,
+                                   _ptr(elem_stats, torch.float64, None if elem_stats is None else capi.PDF_NES * mesh.n_tri),
+                                   _ptr(node_stats, torch.float64, None if node_stats is None else capi.PDF_NNS * mesh.n_nodes),
+                                   _ptr(node_derivs, torch.float64, None if node_derivs is None else capi.PDF_NND * mesh.n_nodes),
+                                   _stream(stream)), "pdf_estimate_stats")
+
+
+def pdf_elem_coeff(particles, mesh, params, wp=None, rows=None, stream=None):
+    if rows is None:
+        rows = torch.empty((mesh.n_tri, capi.PDF_NCOEF), dtype=torch.float64, device="cuda")
+    check(lib().pdf_elem_coeff(particles.handle, mesh.handle, ctypes.byref(params),
+                               _ptr(wp, torch.float64, None if wp is None else 9 * mesh.n_nodes),
+                               _ptr(rows, torch.float64, capi.PDF_NCOEF * mesh.n_tri), _stream(stream)),
+          "pdf_elem_coeff")
+    return rows
+
+
+def pdf_rng_gauss(seed, c1, c2, c3, n, out=None, stream=None):
+    if out is None:
+        out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    check(lib().pdf_rng_gauss(int(seed), c1, c2, c3, int(n), _ptr(out, torch.float32, 4 * n), _stream(stream)),
+          "pdf_rng_gauss")
+    return out
+
+
+def pdf_last_error():
+    m = lib().pdf_last_error()
+    return m.decode() if m else ""
+
+
+def pdf_profile_enable(on=True):
+    check(lib().pdf_profile_enable(1 if on else 0), "pdf_profile_enable")
+
+
+def pdf_profile_reset():
+    check(lib().pdf_profile_reset(), "pdf_profile_reset")
+
+
+def pdf_profile_query(kernel):
+    """(launches, total_ms) of the named kernel since the last reset."""
+    n, ms = ctypes.c_int64(), ctypes.c_double()
+    check(lib().pdf_profile_query(kernel.encode(), ctypes.byref(n), ctypes.byref(ms)), "pdf_profile_query")
+    return n.value, ms.value
+
+
+def pdf_kernel_launches():
+    return int(lib().pdf_kernel_launches())

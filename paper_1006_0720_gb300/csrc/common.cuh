@@ -1,0 +1,130 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pdfgb.h"
+
+namespace pdfgb {
+
+void set_error(const std::string& msg);
+pdf_status fail(pdf_status s, const std::string& msg);
+pdf_status cuda_fail(cudaError_t e, const char* what);
+
+#define PDF_CUDA(call)                                          \
+  do {                                                          \
+    cudaError_t _e = (call);                                    \
+    if (_e != cudaSuccess) return ::pdfgb::cuda_fail(_e, #call); \
+  } while (0)
+
+#define PDF_LAUNCH_CHECK(name)                                   \
+  do {                                                           \
+    cudaError_t _e = cudaGetLastError();                         \
+    if (_e != cudaSuccess) return ::pdfgb::cuda_fail(_e, name);  \
+  } while (0)
+
+constexpr int kNbrWall = -1;
+constexpr int kNbrInflow = -3;
+constexpr int kNbrOutflow = -4;
+
+// Per-element data the neighbour walk reads: node B, the edge vectors
+// C - B and A - B, twice the area, and the three neighbours with their
+// periodic shift multipliers.  80 bytes, 16-byte aligned.
+struct __align__(16) ElemGeo {
+  double xb, yb;    // node B
+  double cbx, cby;  // C - B
+  double abx, aby;  // A - B
+  double two_area;  // 2 A_e
+  int32_t nbr[3];   // neighbour across the edge opposite A, B, C
+  int8_t shift[3];  // periodic x-shift multipliers for those crossings
+  int8_t pad[1];
+};
+static_assert(sizeof(ElemGeo) == 80, "ElemGeo layout");
+
+// Device-resident mesh.
+struct MeshDev {
+  int32_t n_nodes = 0, n_tri = 0;
+  double period = 0.0;
+  double* xy = nullptr;        // [n_nodes][2]
+  int32_t* tri = nullptr;      // [n_tri][3]
+  ElemGeo* geo = nullptr;      // [n_tri]
+  double* dN = nullptr;        // [n_tri][6]: dNA/dx dNB/dx dNC/dx dNA/dy dNB/dy dNC/dy
+  int32_t* nse_off = nullptr;  // [n_nodes + 1] node -> surrounding elements (twins merged)
+  int32_t* nse = nullptr;
+  int32_t* esup_off = nullptr; // [n_nodes + 1] node -> elements holding the node
+  int32_t* esup = nullptr;
+};
+
+}  // namespace pdfgb
+
+struct pdf_mesh {
+  pdfgb::MeshDev d;
+  // host copies
+  std::vector<double> xy;
+  std::vector<int32_t> tri, nbr, shift, twin;
+  std::vector<double> area;
+};
+
+// Internal coefficient row: 32 doubles (256 B) per element.
+//   0-2  <U_i>
+//   3-8  sqrt(2 nu dt) d<U_i>/dx_j   (Ux Uy Vx Vy Wx Wy; 0 for SLM)
+//   9-11 a_i dt
+//   12-20 G_ij dt
+//   21   sqrt(C0 eps) sqrt(dt)
+//   22   <omega>
+//   23   (C3 + S_omega) <omega> dt
+//   24   C3 <omega>^2 dt
+//   25   <omega> sqrt(2 C3 C4 dt)
+//   26   <phi>
+//   27   dt / t_m
+#define PDFGB_ROW 32
+
+struct pdf_particles {
+  const pdf_mesh* mesh = nullptr;
+  int64_t n = 0;
+  int32_t precision = PDF_FP64;
+  uint64_t seed = 0;
+  // state, particle-id order
+  double *x = nullptr, *y = nullptr, *u = nullptr, *v = nullptr, *w = nullptr, *om = nullptr,
+         *ps = nullptr;
+  int32_t* elem = nullptr;
+  // statistics
+  double* es = nullptr;    // [n_tri][13]
+  double* ns = nullptr;    // [n_nodes][12]
+  double* nd = nullptr;    // [n_nodes][10]
+  double* eg = nullptr;    // [n_tri][8] element gradients (scratch)
+  double* nc = nullptr;    // [n_nodes][26] nodal coefficients (scratch)
+  double* rows = nullptr;  // [n_tri][32]
+  bool have_stats = false;
+  // grouping
+  int32_t* keys[2] = {nullptr, nullptr};
+  int32_t* vals[2] = {nullptr, nullptr};
+  int32_t* hist = nullptr;       // [bins][tiles]
+  int32_t* hist_part = nullptr;  // scan partials
+  int32_t* seg = nullptr;        // [n_tri + 1] segment offsets into the sorted order
+  const int32_t* sorted_pid = nullptr;  // points into vals[]
+  int64_t n_tiles = 0;
+  int64_t hist_len = 0;
+  int32_t n_scan_blocks = 0;
+  // counters
+  long long* counters = nullptr;  // [16] device
+};
+
+namespace pdfgb {
+// Launches through prof_launch are counted and, when timing is enabled,
+// bracketed by CUDA events on the launch stream.
+void prof_launch(const char* name, cudaStream_t st, void (*launch)(void*), void* ctx);
+}  // namespace pdfgb
+
+// PDF_KERNEL(name, stream, kernel<<<grid, block, smem, stream>>>(args...));
+#define PDF_KERNEL(name, st, ...)                                          \
+  do {                                                                     \
+    auto _launch = [&]() { __VA_ARGS__; };                                 \
+    ::pdfgb::prof_launch(                                                  \
+        name, (st), [](void* c) { (*static_cast<decltype(_launch)*>(c))(); }, \
+        &_launch);                                                         \
+    PDF_LAUNCH_CHECK(name);                                                \
+  } while (0)

@@ -1,0 +1,231 @@
+// Particle handles: allocation, initialisation (sec. 3.6), state access and
+// the exposed Gaussian draw.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "rng.cuh"
+
+namespace pdfgb {
+
+// Radix grouping geometry (see stats.cu).
+int64_t radix_tiles(int64_t n);
+int32_t radix_bins();
+int32_t radix_scan_blocks(int64_t hist_len);
+
+// One thread per particle.  Particle ids run element by element; elem_off is
+// the exclusive prefix sum of the per-element counts.
+__global__ void k_init(const double* __restrict__ xy, const int32_t* __restrict__ tri,
+                       const int64_t* __restrict__ elem_off, int32_t n_tri, int64_t n,
+                       uint64_t seed, int32_t u_profile, double u_sigma,
+                       const double* __restrict__ elem_psi0, double* __restrict__ x,
+                       double* __restrict__ y, double* __restrict__ u, double* __restrict__ v,
+                       double* __restrict__ w, double* __restrict__ om, double* __restrict__ ps,
+                       int32_t* __restrict__ elem) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    // host element: largest e with elem_off[e] <= p
+    int32_t lo = 0, hi = n_tri - 1;
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if (elem_off[mid] <= p) lo = mid; else hi = mid - 1;
+    }
+    const int32_t e = lo;
+    uint32_t c[4] = {(uint32_t)p, 0u, 0u, kPurposeInit};
+    const uint64_t s = seed;
+    philox4x32_10(c, (uint32_t)s, (uint32_t)(s >> 32));
+    float r1 = u01_from_word(c[0]), r2 = u01_from_word(c[1]);
+    if (__fadd_rn(r1, r2) > 1.0f) {
+      r1 = __fsub_rn(1.0f, r1);
+      r2 = __fsub_rn(1.0f, r2);
+    }
+    float g[6];
+    box_muller(c[2], c[3], &g[0], &g[1]);
+    gauss4(seed, (uint32_t)p, 0u, 1u, kPurposeInit, &g[2]);
+    uint32_t c2[4] = {(uint32_t)p, 0u, 2u, kPurposeInit};
+    philox4x32_10(c2, (uint32_t)s, (uint32_t)(s >> 32));
+    float lsum = __fadd_rn(ln_unit(u01_from_word(c2[0])), ln_unit(u01_from_word(c2[1])));
+    lsum = __fadd_rn(lsum, ln_unit(u01_from_word(c2[2])));
+    lsum = __fadd_rn(lsum, ln_unit(u01_from_word(c2[3])));
+    const int32_t na = tri[3 * e], nb = tri[3 * e + 1], nc = tri[3 * e + 2];
+    const double xa = xy[2 * na], ya = xy[2 * na + 1];
+    const double xb = xy[2 * nb], yb = xy[2 * nb + 1];
+    const double xc = xy[2 * nc], yc = xy[2 * nc + 1];
+    const double R1 = (double)r1, R2 = (double)r2;
+    // uniform point in the triangle, rounded exactly as A + r1 (B-A) + r2 (C-A)
+    const double px = __dadd_rn(__dadd_rn(xa, __dmul_rn(R1, __dsub_rn(xb, xa))),
+                                __dmul_rn(R2, __dsub_rn(xc, xa)));
+    const double py = __dadd_rn(__dadd_rn(ya, __dmul_rn(R1, __dsub_rn(yb, ya))),
+                                __dmul_rn(R2, __dsub_rn(yc, ya)));
+    const double umean = (u_profile == 1) ? __dsub_rn(1.0, __dmul_rn(py, py)) : 0.0;
+    x[p] = px;
+    y[p] = py;
+    u[p] = __dadd_rn(umean, __dmul_rn(u_sigma, (double)g[0]));
+    v[p] = __dmul_rn(u_sigma, (double)g[1]);
+    w[p] = __dmul_rn(u_sigma, (double)g[2]);
+    om[p] = __dmul_rn(-0.25, (double)lsum);   // Gamma(4, 1/4): -1/4 sum of 4 ln u
+    ps[p] = elem_psi0 ? elem_psi0[e] : 0.0;
+    elem[p] = e;
+  }
+}
+
+__global__ void k_rng_gauss(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3, int64_t n,
+                            float4* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float g[4];
+    gauss4(seed, (uint32_t)i, c1, c2, c3, g);
+    out[i] = make_float4(g[0], g[1], g[2], g[3]);
+  }
+}
+
+static void free_particles(pdf_particles* p) {
+  if (!p) return;
+  double* dbl[] = {p->x, p->y, p->u, p->v, p->w, p->om, p->ps, p->es, p->ns, p->nd, p->eg, p->nc, p->rows};
+  for (double* d : dbl) cudaFree(d);
+  cudaFree(p->elem);
+  cudaFree(p->keys[0]); cudaFree(p->keys[1]); cudaFree(p->vals[0]); cudaFree(p->vals[1]);
+  cudaFree(p->hist); cudaFree(p->hist_part); cudaFree(p->seg);
+  cudaFree(p->counters);
+  delete p;
+}
+
+static int grid_for(int64_t n, int threads) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t blocks = (n + threads - 1) / threads;
+  const int64_t cap = (int64_t)sms * 16;
+  return (int)std::max<int64_t>(1, std::min(blocks, cap));
+}
+
+}  // namespace pdfgb
+
+using namespace pdfgb;
+
+#define TRY_ALLOC(ptr, count)                                                        \
+  do {                                                                               \
+    cudaError_t _e = cudaMalloc((void**)&(ptr), (size_t)(count) * sizeof(*(ptr)));  \
+    if (_e != cudaSuccess) {                                                         \
+      free_particles(P);                                                             \
+      return fail(PDF_ENOMEM, "pdf_particles_init: cudaMalloc failed");              \
+    }                                                                                \
+  } while (0)
+
+extern "C" pdf_status pdf_particles_init(const pdf_mesh* m, const pdf_init_params* ip,
+                                         uint64_t seed, int32_t precision, void* stream,
+                                         pdf_particles** out) {
+  if (!out) return fail(PDF_EINVAL, "pdf_particles_init: out is NULL");
+  *out = nullptr;
+  if (!m || !ip) return fail(PDF_EINVAL, "pdf_particles_init: NULL mesh or params");
+  if (precision != PDF_FP64) return fail(PDF_EINVAL, "pdf_particles_init: only PDF_FP64 is available");
+  const int32_t n_tri = m->d.n_tri, n_nodes = m->d.n_nodes;
+  std::vector<int64_t> off(n_tri + 1, 0);
+  for (int32_t e = 0; e < n_tri; ++e) {
+    const int64_t c = ip->count ? ip->count[e] : ip->ppe;
+    if (c < 0) return fail(PDF_EINVAL, "pdf_particles_init: negative particle count");
+    off[e + 1] = off[e] + c;
+  }
+  const int64_t n = off[n_tri];
+  if (n < 1 || n > (int64_t)INT32_MAX) return fail(PDF_EINVAL, "pdf_particles_init: particle count must be in [1, 2^31)");
+  cudaStream_t st = (cudaStream_t)stream;
+  pdf_particles* P = new (std::nothrow) pdf_particles();
+  if (!P) return fail(PDF_ENOMEM, "pdf_particles_init: host allocation");
+  P->mesh = m;
+  P->n = n;
+  P->precision = precision;
+  P->seed = seed;
+  TRY_ALLOC(P->x, n); TRY_ALLOC(P->y, n); TRY_ALLOC(P->u, n); TRY_ALLOC(P->v, n);
+  TRY_ALLOC(P->w, n); TRY_ALLOC(P->om, n); TRY_ALLOC(P->ps, n); TRY_ALLOC(P->elem, n);
+  TRY_ALLOC(P->es, (int64_t)n_tri * PDF_NES);
+  TRY_ALLOC(P->ns, (int64_t)n_nodes * PDF_NNS);
+  TRY_ALLOC(P->nd, (int64_t)n_nodes * PDF_NND);
+  TRY_ALLOC(P->eg, (int64_t)n_tri * 8);
+  TRY_ALLOC(P->nc, (int64_t)n_nodes * PDF_NCOEF);
+  TRY_ALLOC(P->rows, (int64_t)n_tri * PDFGB_ROW);
+  TRY_ALLOC(P->keys[0], n); TRY_ALLOC(P->keys[1], n);
+  TRY_ALLOC(P->vals[0], n); TRY_ALLOC(P->vals[1], n);
+  P->n_tiles = radix_tiles(n);
+  P->hist_len = P->n_tiles * radix_bins();
+  P->n_scan_blocks = radix_scan_blocks(P->hist_len);
+  TRY_ALLOC(P->hist, P->hist_len);
+  TRY_ALLOC(P->hist_part, P->n_scan_blocks + 1);
+  TRY_ALLOC(P->seg, (int64_t)n_tri + 1);
+  TRY_ALLOC(P->counters, 16);
+  cudaError_t e = cudaMemsetAsync(P->ns, 0, sizeof(double) * n_nodes * PDF_NNS, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->counters, 0, sizeof(long long) * 16, st);
+  int64_t* d_off = nullptr;
+  double* d_psi = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&d_off, sizeof(int64_t) * (n_tri + 1));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, off.data(), sizeof(int64_t) * (n_tri + 1), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && ip->elem_psi0) {
+    e = cudaMalloc(&d_psi, sizeof(double) * n_tri);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_psi, ip->elem_psi0, sizeof(double) * n_tri, cudaMemcpyHostToDevice, st);
+  }
+  if (e == cudaSuccess) {
+    prof_launch("k_init", st, nullptr, nullptr);  // counted only
+    k_init<<<grid_for(n, 256), 256, 0, st>>>(m->d.xy, m->d.tri, d_off, n_tri, n, seed,
+                                              ip->u_profile, ip->u_sigma, d_psi, P->x, P->y, P->u,
+                                              P->v, P->w, P->om, P->ps, P->elem);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d_off);
+  cudaFree(d_psi);
+  if (e != cudaSuccess) {
+    free_particles(P);
+    return cuda_fail(e, "pdf_particles_init");
+  }
+  *out = P;
+  return PDF_OK;
+}
+
+extern "C" pdf_status pdf_particles_destroy(pdf_particles* p) {
+  free_particles(p);
+  return PDF_OK;
+}
+
+extern "C" pdf_status pdf_particles_count(const pdf_particles* p, int64_t* n) {
+  if (!p || !n) return fail(PDF_EINVAL, "pdf_particles_count: NULL argument");
+  *n = p->n;
+  return PDF_OK;
+}
+
+extern "C" pdf_status pdf_particles_get_state(const pdf_particles* p, double* x, double* y,
+                                              double* u, double* v, double* w, double* om,
+                                              double* ps, int32_t* elem, void* stream) {
+  if (!p) return fail(PDF_EINVAL, "pdf_particles_get_state: NULL handle");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t b = sizeof(double) * p->n;
+  double* dst[] = {x, y, u, v, w, om, ps};
+  const double* src[] = {p->x, p->y, p->u, p->v, p->w, p->om, p->ps};
+  for (int i = 0; i < 7; ++i)
+    if (dst[i]) PDF_CUDA(cudaMemcpyAsync(dst[i], src[i], b, cudaMemcpyDefault, st));
+  if (elem) PDF_CUDA(cudaMemcpyAsync(elem, p->elem, sizeof(int32_t) * p->n, cudaMemcpyDefault, st));
+  return PDF_OK;
+}
+
+extern "C" pdf_status pdf_particles_set_state(pdf_particles* p, const double* x, const double* y,
+                                              const double* u, const double* v, const double* w,
+                                              const double* om, const double* ps,
+                                              const int32_t* elem, void* stream) {
+  if (!p || !x || !y || !u || !v || !w || !om || !ps || !elem)
+    return fail(PDF_EINVAL, "pdf_particles_set_state: NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t b = sizeof(double) * p->n;
+  double* dst[] = {p->x, p->y, p->u, p->v, p->w, p->om, p->ps};
+  const double* src[] = {x, y, u, v, w, om, ps};
+  for (int i = 0; i < 7; ++i) PDF_CUDA(cudaMemcpyAsync(dst[i], src[i], b, cudaMemcpyDefault, st));
+  PDF_CUDA(cudaMemcpyAsync(p->elem, elem, sizeof(int32_t) * p->n, cudaMemcpyDefault, st));
+  return PDF_OK;
+}
+
+extern "C" pdf_status pdf_rng_gauss(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3, int64_t n,
+                                    float* out, void* stream) {
+  if (n < 0 || (n > 0 && !out)) return fail(PDF_EINVAL, "pdf_rng_gauss: bad arguments");
+  if (n == 0) return PDF_OK;
+  if ((reinterpret_cast<uintptr_t>(out) & 15) != 0) return fail(PDF_EINVAL, "pdf_rng_gauss: out must be 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  PDF_KERNEL("k_rng_gauss", st, k_rng_gauss<<<grid_for(n, 256), 256, 0, st>>>(seed, c1, c2, c3, n, (float4*)out));
+  return PDF_OK;
+}

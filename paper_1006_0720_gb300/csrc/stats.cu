@@ -1,0 +1,405 @@
+// Particle-in-cell statistics (sec. 3.3) and derivatives (sec. 3.4).
+//
+// Grouping: a stable least-significant-digit radix sort of (element id,
+// particle id) pairs, 9-bit digits, in place of the paper's per-element
+// linked lists.  Stability makes the particle order inside every element
+// ascending in particle id, so the segmented reductions below always add
+// the same numbers in the same order: the statistics are deterministic
+// without floating-point atomics.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace pdfgb {
+
+constexpr int kRadixBits = 9;
+constexpr int kBins = 1 << kRadixBits;      // 512
+constexpr int kSortThreads = 256;
+constexpr int kItemsPerThread = 16;
+constexpr int kTile = kSortThreads * kItemsPerThread;  // 4096 keys per tile
+constexpr int kScanChunk = 4096;                       // hist entries per scan block
+
+int64_t radix_tiles(int64_t n) { return (n + kTile - 1) / kTile; }
+int32_t radix_bins() { return kBins; }
+int32_t radix_scan_blocks(int64_t hist_len) { return (int32_t)((hist_len + kScanChunk - 1) / kScanChunk); }
+
+// Per-tile digit histogram, stored bin-major: hist[bin * n_tiles + tile].
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const int32_t* __restrict__ keys, int64_t n,
+                                                             int shift, int64_t n_tiles,
+                                                             int32_t* __restrict__ hist) {
+  __shared__ int32_t h[kBins];
+  for (int b = threadIdx.x; b < kBins; b += kSortThreads) h[b] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kTile;
+  for (int r = 0; r < kItemsPerThread; ++r) {
+    const int64_t i = base + r * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & (kBins - 1)], 1);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < kBins; b += kSortThreads) hist[(int64_t)b * n_tiles + blockIdx.x] = h[b];
+}
+
+// Exclusive scan of hist in three launches: chunk sums, scan of the sums,
+// then each chunk scanned with its base.
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t* total) {
+  __shared__ int32_t warp_sums[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) warp_sums[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    int32_t s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t t = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += t;
+    }
+    if (lane < nw) warp_sums[lane] = s;
+  }
+  __syncthreads();
+  const int32_t warp_base = wid > 0 ? warp_sums[wid - 1] : 0;
+  if (total) *total = warp_sums[(blockDim.x >> 5) - 1];
+  const int32_t r = warp_base + inc - v;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_reduce(const int32_t* __restrict__ a, int64_t len,
+                                                      int32_t* __restrict__ part) {
+  const int64_t base = (int64_t)blockIdx.x * kScanChunk;
+  int32_t s = 0;
+  for (int i = threadIdx.x; i < kScanChunk; i += blockDim.x)
+    if (base + i < len) s += a[base + i];
+  int32_t total;
+  block_exclusive_scan(s, &total);
+  if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(int32_t* __restrict__ part, int32_t nparts) {
+  int32_t carry = 0;
+  for (int32_t start = 0; start < nparts; start += blockDim.x) {
+    const int32_t i = start + threadIdx.x;
+    const int32_t v = i < nparts ? part[i] : 0;
+    int32_t total;
+    const int32_t ex = block_exclusive_scan(v, &total);
+    if (i < nparts) part[i] = carry + ex;
+    carry += total;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_apply(int32_t* __restrict__ a, int64_t len,
+                                                     const int32_t* __restrict__ part) {
+  // each thread owns 4 consecutive entries of the chunk
+  const int64_t base = (int64_t)blockIdx.x * kScanChunk + 4 * threadIdx.x;
+  int32_t v[4];
+  int32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    v[j] = (base + j < len) ? a[base + j] : 0;
+    s += v[j];
+  }
+  int32_t ex = block_exclusive_scan(s, nullptr) + part[blockIdx.x];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (base + j < len) a[base + j] = ex;
+    ex += v[j];
+  }
+}
+
+// Stable scatter of one tile.  Items are ranked in index order: 16 rounds of
+// 256 items; inside a round, warps in order and lanes in order.
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+    const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in, int64_t n, int shift,
+    int64_t n_tiles, const int32_t* __restrict__ hist, int32_t* __restrict__ keys_out,
+    int32_t* __restrict__ vals_out) {
+  constexpr int kWarps = kSortThreads / 32;
+  __shared__ int32_t base[kBins];
+  __shared__ int32_t wcnt[kWarps][kBins];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int b = threadIdx.x; b < kBins; b += kSortThreads) base[b] = hist[(int64_t)b * n_tiles + blockIdx.x];
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const int64_t tile0 = (int64_t)blockIdx.x * kTile;
+  for (int r = 0; r < kItemsPerThread; ++r) {
+    for (int i = threadIdx.x; i < kWarps * kBins; i += kSortThreads) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t i = tile0 + r * kSortThreads + threadIdx.x;
+    const bool valid = i < n;
+    int32_t key = 0, val = 0;
+    int d = kBins;  // invalid items share a digit that is never written
+    if (valid) {
+      key = keys_in[i];
+      val = vals_in ? vals_in[i] : (int32_t)i;
+      d = (key >> shift) & (kBins - 1);
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const int rank = __popc(peers & lt_mask);
+    if (valid && rank == 0) wcnt[wid][d] = __popc(peers);
+    __syncthreads();
+    // per-bin prefix over warps; base[] advances by the round's count
+    for (int b = threadIdx.x; b < kBins; b += kSortThreads) {
+      int32_t acc = base[b];
+#pragma unroll
+      for (int k = 0; k < kWarps; ++k) {
+        const int32_t c = wcnt[k][b];
+        wcnt[k][b] = acc;
+        acc += c;
+      }
+      base[b] = acc;
+    }
+    __syncthreads();
+    if (valid) {
+      const int32_t pos = wcnt[wid][d] + rank;
+      keys_out[pos] = key;
+      vals_out[pos] = val;
+    }
+    __syncthreads();
+  }
+}
+
+// seg[e] = first sorted position whose key >= e; seg[n_tri] = n.
+__global__ void k_seg_offsets(const int32_t* __restrict__ keys, int64_t n, int32_t n_tri,
+                              int32_t* __restrict__ seg) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t prev = (i == 0) ? -1 : keys[i - 1];
+    const int32_t cur = (i == n) ? n_tri : keys[i];
+    for (int32_t e = prev + 1; e <= cur; ++e) seg[e] = (int32_t)i;
+  }
+}
+
+// One warp per element: first pass means, second pass central moments
+// (sec. 3.3, 1/N).  Lane j adds sorted positions j, j+32, ...; the lane
+// partials are combined by a fixed butterfly and lane 0's result is used.
+__global__ void __launch_bounds__(256) k_elem_stats(const int32_t* __restrict__ seg,
+                                                    const int32_t* __restrict__ pid, int32_t n_tri,
+                                                    const double* __restrict__ u, const double* __restrict__ v,
+                                                    const double* __restrict__ w, const double* __restrict__ om,
+                                                    const double* __restrict__ ps, double* __restrict__ es) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = warp; e < n_tri; e += nwarps) {
+    const int32_t beg = seg[e], end = seg[e + 1];
+    const int32_t N = end - beg;
+    double* out = es + e * PDF_NES;
+    if (N == 0) {
+      if (lane < PDF_NES) out[lane] = 0.0;
+      continue;
+    }
+    double s[5] = {0, 0, 0, 0, 0};
+    for (int32_t i = beg + lane; i < end; i += 32) {
+      const int32_t p = pid[i];
+      s[0] += u[p]; s[1] += v[p]; s[2] += w[p]; s[3] += om[p]; s[4] += ps[p];
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+      s[q] = __shfl_sync(0xffffffffu, s[q], 0) / (double)N;
+    }
+    double c[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int32_t i = beg + lane; i < end; i += 32) {
+      const int32_t p = pid[i];
+      const double du = u[p] - s[0], dv = v[p] - s[1], dw = w[p] - s[2], dp = ps[p] - s[4];
+      c[0] += du * du; c[1] += dv * dv; c[2] += dw * dw;
+      c[3] += du * dv; c[4] += du * dw; c[5] += dv * dw; c[6] += dp * dp;
+    }
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c[q] += __shfl_xor_sync(0xffffffffu, c[q], o);
+      c[q] = __shfl_sync(0xffffffffu, c[q], 0) / (double)N;
+    }
+    if (lane == 0) {
+      out[0] = (double)N;
+      for (int q = 0; q < 5; ++q) out[1 + q] = s[q];
+      for (int q = 0; q < 7; ++q) out[6 + q] = c[q];
+    }
+  }
+}
+
+// Node pass: mean over the non-empty surrounding elements (twins merged);
+// a node with none keeps its previous value.
+__global__ void k_node_stats(const int32_t* __restrict__ nse_off, const int32_t* __restrict__ nse,
+                             int32_t n_nodes, const double* __restrict__ es, double* __restrict__ ns,
+                             long long* __restrict__ kept) {
+  for (int32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < n_nodes; n += gridDim.x * blockDim.x) {
+    double acc[PDF_NNS];
+#pragma unroll
+    for (int q = 0; q < PDF_NNS; ++q) acc[q] = 0.0;
+    int c = 0;
+    for (int32_t i = nse_off[n]; i < nse_off[n + 1]; ++i) {
+      const double* s = es + (int64_t)nse[i] * PDF_NES;
+      if (s[0] <= 0.0) continue;
+#pragma unroll
+      for (int q = 0; q < PDF_NNS; ++q) acc[q] += s[1 + q];
+      ++c;
+    }
+    if (c == 0) {
+      atomicAdd(reinterpret_cast<unsigned long long*>(kept), 1ULL);
+      continue;
+    }
+    const double inv = (double)c;
+#pragma unroll
+    for (int q = 0; q < PDF_NNS; ++q) ns[(int64_t)n * PDF_NNS + q] = acc[q] / inv;
+  }
+}
+
+// Element gradients of nodal <U>, <V>, <W>, <vv> (eq. gradient with the
+// analytic shape-function derivatives): eg[e] = Ux Uy Vx Vy Wx Wy vvx vvy.
+__global__ void k_elem_grad1(const int32_t* __restrict__ tri, const double* __restrict__ dN,
+                             int32_t n_tri, const double* __restrict__ ns, double* __restrict__ eg) {
+  for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n_tri; e += gridDim.x * blockDim.x) {
+    const double* d = dN + (int64_t)e * 6;
+    double g[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int fld[4] = {0, 1, 2, 6};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const double* S = ns + (int64_t)tri[3 * e + j] * PDF_NNS;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        g[2 * f] += d[j] * S[fld[f]];
+        g[2 * f + 1] += d[3 + j] * S[fld[f]];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) eg[(int64_t)e * 8 + q] = g[q];
+  }
+}
+
+__global__ void k_node_grad1(const int32_t* __restrict__ nse_off, const int32_t* __restrict__ nse,
+                             int32_t n_nodes, const double* __restrict__ eg, double* __restrict__ nd) {
+  for (int32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < n_nodes; n += gridDim.x * blockDim.x) {
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    const int32_t b = nse_off[n], c = nse_off[n + 1] - b;
+    for (int32_t i = b; i < b + c; ++i) {
+      const double* g = eg + (int64_t)nse[i] * 8;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) acc[q] += g[q];
+      acc[6] += g[7];
+    }
+    double* D = nd + (int64_t)n * PDF_NND;
+    const double inv = c > 0 ? (double)c : 1.0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) D[q] = acc[q] / inv;
+    D[9] = acc[6] / inv;
+  }
+}
+
+// Second pass: d/dx of the node dU_i/dx plus d/dy of the node dU_i/dy.
+__global__ void k_elem_grad2(const int32_t* __restrict__ tri, const double* __restrict__ dN,
+                             int32_t n_tri, const double* __restrict__ nd, double* __restrict__ eg) {
+  for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n_tri; e += gridDim.x * blockDim.x) {
+    const double* d = dN + (int64_t)e * 6;
+    double l[3] = {0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const double* D = nd + (int64_t)tri[3 * e + j] * PDF_NND;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) l[i] += d[j] * D[2 * i] + d[3 + j] * D[2 * i + 1];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) eg[(int64_t)e * 8 + i] = l[i];
+  }
+}
+
+__global__ void k_node_grad2(const int32_t* __restrict__ nse_off, const int32_t* __restrict__ nse,
+                             int32_t n_nodes, const double* __restrict__ eg, double* __restrict__ nd) {
+  for (int32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < n_nodes; n += gridDim.x * blockDim.x) {
+    double acc[3] = {0, 0, 0};
+    const int32_t b = nse_off[n], c = nse_off[n + 1] - b;
+    for (int32_t i = b; i < b + c; ++i) {
+      const double* g = eg + (int64_t)nse[i] * 8;
+      acc[0] += g[0]; acc[1] += g[1]; acc[2] += g[2];
+    }
+    const double inv = c > 0 ? (double)c : 1.0;
+    double* D = nd + (int64_t)n * PDF_NND;
+    D[6] = acc[0] / inv; D[7] = acc[1] / inv; D[8] = acc[2] / inv;
+  }
+}
+
+static int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+  }
+  return sms;
+}
+
+static int blocks_for(int64_t n, int threads) {
+  const int64_t b = (n + threads - 1) / threads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)sm_count() * 32));
+}
+
+// Stable grouping of particles by element.  Leaves sorted element ids in
+// keys[out], particle ids in vals[out] and segment offsets in seg.
+pdf_status group_by_element(pdf_particles* P, cudaStream_t st) {
+  const int32_t n_tri = P->mesh->d.n_tri;
+  const int64_t n = P->n;
+  int bits = 1;
+  while ((1LL << bits) < (int64_t)n_tri) ++bits;
+  const int passes = (bits + kRadixBits - 1) / kRadixBits;
+  const int32_t* kin = P->elem;
+  const int32_t* vin = nullptr;  // first pass: particle ids are the indices
+  int cur = 0;
+  for (int pass = 0; pass < passes; ++pass) {
+    const int shift = pass * kRadixBits;
+    PDF_KERNEL("k_radix_hist", st, k_radix_hist<<<(unsigned)P->n_tiles, kSortThreads, 0, st>>>(kin, n, shift, P->n_tiles, P->hist););
+    PDF_KERNEL("k_scan_reduce", st, k_scan_reduce<<<P->n_scan_blocks, 1024, 0, st>>>(P->hist, P->hist_len, P->hist_part););
+    PDF_KERNEL("k_scan_top", st, k_scan_top<<<1, 1024, 0, st>>>(P->hist_part, P->n_scan_blocks););
+    PDF_KERNEL("k_scan_apply", st, k_scan_apply<<<P->n_scan_blocks, 1024, 0, st>>>(P->hist, P->hist_len, P->hist_part););
+    PDF_KERNEL("k_radix_scatter", st, k_radix_scatter<<<(unsigned)P->n_tiles, kSortThreads, 0, st>>>(kin, vin, n, shift, P->n_tiles, P->hist,
+                                                                   P->keys[cur], P->vals[cur]););
+    kin = P->keys[cur];
+    vin = P->vals[cur];
+    cur ^= 1;
+  }
+  PDF_KERNEL("k_seg_offsets", st, k_seg_offsets<<<blocks_for(n + 1, 256), 256, 0, st>>>(kin, n, n_tri, P->seg););
+  P->sorted_pid = vin;
+  return PDF_OK;
+}
+
+pdf_status estimate_stats(pdf_particles* P, cudaStream_t st) {
+  const MeshDev& M = P->mesh->d;
+  pdf_status s = group_by_element(P, st);
+  if (s != PDF_OK) return s;
+  PDF_KERNEL("k_elem_stats", st, k_elem_stats<<<blocks_for((int64_t)M.n_tri * 32, 256), 256, 0, st>>>(
+      P->seg, P->sorted_pid, M.n_tri, P->u, P->v, P->w, P->om, P->ps, P->es););
+  PDF_KERNEL("k_node_stats", st, k_node_stats<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(M.nse_off, M.nse, M.n_nodes, P->es, P->ns,
+                                                          P->counters + 8););
+  PDF_KERNEL("k_elem_grad1", st, k_elem_grad1<<<blocks_for(M.n_tri, 128), 128, 0, st>>>(M.tri, M.dN, M.n_tri, P->ns, P->eg););
+  PDF_KERNEL("k_node_grad1", st, k_node_grad1<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(M.nse_off, M.nse, M.n_nodes, P->eg, P->nd););
+  PDF_KERNEL("k_elem_grad2", st, k_elem_grad2<<<blocks_for(M.n_tri, 128), 128, 0, st>>>(M.tri, M.dN, M.n_tri, P->nd, P->eg););
+  PDF_KERNEL("k_node_grad2", st, k_node_grad2<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(M.nse_off, M.nse, M.n_nodes, P->eg, P->nd););
+  P->have_stats = true;
+  return PDF_OK;
+}
+
+}  // namespace pdfgb
+
+using namespace pdfgb;
+
+extern "C" pdf_status pdf_estimate_stats(pdf_particles* p, const pdf_mesh* m, double* elem_stats,
+                                         double* node_stats, double* node_derivs, void* stream) {
+  if (!p || !m || p->mesh != m) return fail(PDF_EINVAL, "pdf_estimate_stats: NULL or mismatched handles");
+  cudaStream_t st = (cudaStream_t)stream;
+  pdf_status s = estimate_stats(p, st);
+  if (s != PDF_OK) return s;
+  const MeshDev& M = m->d;
+  if (elem_stats)
+    PDF_CUDA(cudaMemcpyAsync(elem_stats, p->es, sizeof(double) * M.n_tri * PDF_NES, cudaMemcpyDefault, st));
+  if (node_stats)
+    PDF_CUDA(cudaMemcpyAsync(node_stats, p->ns, sizeof(double) * M.n_nodes * PDF_NNS, cudaMemcpyDefault, st));
+  if (node_derivs)
+    PDF_CUDA(cudaMemcpyAsync(node_derivs, p->nd, sizeof(double) * M.n_nodes * PDF_NND, cudaMemcpyDefault, st));
+  return PDF_OK;
+}

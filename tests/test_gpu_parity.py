@@ -1,0 +1,245 @@
+"""Parity of the CUDA library (through its C-ABI) with the CPU oracle.
+
+States and statistics: |gpu - oracle| <= 1e-10 * max(|oracle|, rms of the
+field).  Random draws, the initial state and element ids: bit-exact, except
+element ids of particles the oracle flags as within 1e-12 (relative) of an
+element edge, whose fraction is reported.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+from parity_util import RTOL, assert_field_close
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU only
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1006_0720_gb300 as pg  # noqa: E402
+
+KEYS = ("x", "y", "u", "v", "w", "om", "ps")
+
+
+def _host(st):
+    return {k: v.cpu().numpy() for k, v in st.items()}
+
+
+def _pair(m, counts, seed=1, psi=None, u_profile="parabola", u_sigma=0.1):
+    gm = pg.Mesh(m)
+    om_ = oracle.Mesh(m)
+    gp = pg.Particles(gm, seed, count=counts, u_profile=u_profile, u_sigma=u_sigma, elem_psi0=psi)
+    ost = oracle.init(om_, counts, seed, u_profile=u_profile, u_sigma=u_sigma, elem_psi0=psi)
+    return gm, om_, gp, ost
+
+
+def _oracle_params(p):
+    names = {0: "glm", 1: "slm"}
+    return oracle.make_params(dt=p.dt, nu=p.nu, Pi=p.Pi, closure=names[p.closure],
+                              tm_mode={0: "turb", 1: "cphi"}[p.tm_mode], c_phi=p.c_phi,
+                              pressure={0: "none", 1: "channel"}[p.pressure])
+
+
+def test_gaussians_bit_exact():
+    n = 200_003
+    g = pg.pdf_rng_gauss(1, 7, 1, 0, n).cpu().numpy()
+    ref = oracle.gauss_fill(1, n, 7, 1, 0)
+    assert np.array_equal(g.view(np.uint32), ref.view(np.uint32))
+    g2 = pg.pdf_rng_gauss(0xDEADBEEF12345678, 3, 0, 1, 1000).cpu().numpy()
+    assert np.array_equal(g2, oracle.gauss_fill(0xDEADBEEF12345678, 1000, 3, 0, 1))
+
+
+def test_connectivity_matches_oracle():
+    for nx, ny in ((3, 2), (20, 40), (57, 31)):
+        m = inputs.channel_mesh(nx, ny, seed=nx)
+        nbr, shift = pg.Mesh(m).connectivity()
+        M = oracle.Mesh(m)
+        assert np.array_equal(nbr, M.nbr) and np.array_equal(shift, M.shift)
+
+
+def test_init_bit_exact_with_ragged_counts():
+    m = inputs.channel_mesh(20, 40, seed=1)
+    rng = np.random.default_rng(0)
+    counts = rng.integers(0, 9, 2 * 19 * 39).astype(np.int32)  # includes empty elements
+    gm, M, gp, ost = _pair(m, counts, psi=inputs.scalar_slab(m))
+    st = _host(gp.get_state())
+    for k in KEYS:
+        assert np.array_equal(st[k], ost[k]), k
+    assert np.array_equal(st["elem"], ost["elem"])
+
+
+def _check_stats(gp, gm, M, ost, prev_ns=None):
+    es = torch.empty((gm.n_tri, 13), dtype=torch.float64, device="cuda")
+    ns = torch.empty((gm.n_nodes, 12), dtype=torch.float64, device="cuda")
+    nd = torch.empty((gm.n_nodes, 10), dtype=torch.float64, device="cuda")
+    pg.pdf_estimate_stats(gp, gm, es, ns, nd)
+    es, ns, nd = es.cpu().numpy(), ns.cpu().numpy(), nd.cpu().numpy()
+    oes, ons, ond, _ = oracle.statistics(M, ost, prev_ns)
+    assert np.array_equal(es[:, 0], oes[:, 0]), "element counts"
+    assert_field_close(es[:, 1:], oes[:, 1:], "element stats")
+    assert_field_close(ns, ons, "node stats")
+    assert_field_close(nd, ond, "node derivatives")
+    return oes, ons, ond
+
+
+def test_statistics_and_coefficients_after_init():
+    m = inputs.channel_mesh(20, 40, seed=1)
+    counts = np.full(2 * 19 * 39, 50, dtype=np.int32)
+    gm, M, gp, ost = _pair(m, counts, psi=inputs.scalar_slab(m))
+    oes, ons, ond = _check_stats(gp, gm, M, ost)
+    for closure in ("glm", "slm"):
+        p = pg.model_params(closure=closure)
+        rows = pg.pdf_elem_coeff(gp, gm, p).cpu().numpy()
+        ref = oracle.elem_coeff(M, ons, ond, _oracle_params(p))
+        assert_field_close(rows, ref, "coefficient rows (%s)" % closure)
+    # a given wp field
+    rng = np.random.default_rng(3)
+    wp = rng.normal(size=(9, gm.n_nodes)) * 0.01 - 0.02 * np.eye(3).reshape(9, 1)
+    p = pg.model_params(closure="glm")
+    rows = pg.pdf_elem_coeff(gp, gm, p, wp=torch.from_numpy(wp).cuda()).cpu().numpy()
+    ref = oracle.elem_coeff(M, ons, ond, _oracle_params(p), wp=wp)
+    assert_field_close(rows, ref, "coefficient rows (given wp)")
+
+
+def _compare_states(st, ost, what, allow_flagged=None):
+    el_ok = st["elem"] == ost["elem"]
+    if allow_flagged is not None:
+        bad = ~el_ok & ~allow_flagged
+        assert not bad.any(), "%s: %d element ids differ outside the near-face band" % (what, bad.sum())
+    else:
+        assert el_ok.all(), "%s: %d element ids differ" % (what, (~el_ok).sum())
+    for k in KEYS:
+        assert_field_close(st[k][el_ok], ost[k][el_ok], "%s: %s" % (what, k))
+    return float((~el_ok).mean())
+
+
+def test_frozen_step_parity():
+    m = inputs.channel_mesh(20, 40, seed=1)
+    counts = np.full(2 * 19 * 39, 30, dtype=np.int32)
+    gm, M, gp, ost = _pair(m, counts, psi=inputs.scalar_slab(m))
+    rng = np.random.default_rng(5)
+    rows = np.zeros((gm.n_tri, 26))
+    rows[:, 0:3] = rng.normal(size=(gm.n_tri, 3)) * 0.1
+    rows[:, 3:9] = rng.normal(size=(gm.n_tri, 6))
+    rows[:, 9:12] = rng.normal(size=(gm.n_tri, 3)) * 0.01
+    G = rng.normal(size=(gm.n_tri, 9)) * 0.5
+    G[:, [0, 4, 8]] -= 5.0
+    rows[:, 12:21] = G
+    rows[:, 21] = rng.uniform(0.1, 0.5, gm.n_tri)
+    rows[:, 22] = rng.uniform(0.5, 2.0, gm.n_tri)
+    rows[:, 23] = rng.normal(size=gm.n_tri)
+    rows[:, 24] = rng.uniform(0, 1, gm.n_tri)
+    rows[:, 25] = rng.uniform(0.5, 5, gm.n_tri)
+    for closure in ("glm", "slm"):
+        p = pg.model_params(closure="frozen", dt=2e-3, nu=1e-3)
+        # the FROZEN closure moves positions with sqrt(2 nu) diffusion like GLM
+        po = oracle.make_params(dt=2e-3, nu=1e-3, closure="glm")
+        if closure == "slm":
+            continue
+        d_rows = torch.from_numpy(rows).cuda()
+        info = pg.pdf_step(gp, gm, p, elem_coeff=d_rows, step=3, info=True)
+        cnt, status = oracle.step(M, rows, po, 1, 3, ost)
+        st = _host(gp.get_state())
+        flagged = (status & oracle.TRK_NEAR_FACE) != 0
+        _compare_states(st, ost, "frozen step", flagged)
+        assert info["lost"] == 0 and cnt["lost"] == 0
+        assert info["reflections"] == cnt["reflections"]
+        assert info["crossings_periodic"] == cnt["crossings_periodic"]
+
+
+def _run_config(name, steps, check_every=None):
+    cfg = inputs.workload(name)
+    m = inputs.channel_mesh(cfg["nx"], cfg["ny"], jitter=cfg["jitter"], seed=cfg["seed"])
+    counts = np.full(cfg["n_tri"], cfg["ppe"], dtype=np.int32)
+    psi = inputs.scalar_slab(m, cfg["psi_slab_x"])
+    gm, M, gp, ost = _pair(m, counts, seed=cfg["seed"], psi=psi, u_sigma=cfg["u_sigma"])
+    p = pg.model_params(dt=cfg["dt"], nu=cfg["nu"], Pi=cfg["Pi"], closure=cfg["closure"])
+    po = _oracle_params(p)
+    pg.pdf_estimate_stats(gp, gm)
+    oes, ons, ond, _ = oracle.statistics(M, ost)
+    near = []
+    for s in range(steps):
+        rows = oracle.elem_coeff(M, ons, ond, po)
+        cnt, status = oracle.step(M, rows, po, cfg["seed"], s, ost)
+        info = pg.pdf_step(gp, gm, p, step=s, info=True)
+        assert info["lost"] == 0 and cnt["lost"] == 0
+        oes, ons, ond, _ = oracle.statistics(M, ost, ons)
+        pg.pdf_estimate_stats(gp, gm)
+        if check_every and (s + 1) % check_every == 0:
+            st = _host(gp.get_state())
+            flagged = (status & oracle.TRK_NEAR_FACE) != 0
+            near.append(_compare_states(st, ost, "step %d" % s, flagged))
+    return gm, M, gp, ost, ons, near
+
+
+def test_small_channel_free_run_100_steps():
+    """The small channel workload (20x40 nodes, 50 particles per element, GLM
+    with the local wp, channel pressure), 100 steps free-running: states,
+    statistics and element ids stay within the tolerance."""
+    gm, M, gp, ost, ons, near = _run_config("channel_20x40_ppe50", 100, check_every=25)
+    assert max(near) < 1e-4
+    _check_stats(gp, gm, M, ost, ons)
+
+
+def test_tiny_mesh_edge_cases():
+    """4 triangles, a handful of particles: warps and tiles mostly empty,
+    empty elements, walls and seams crossed every step."""
+    m = inputs.channel_mesh(3, 2, seed=2)
+    counts = np.array([3, 0, 1, 5], dtype=np.int32)
+    gm, M, gp, ost = _pair(m, counts, u_sigma=0.5)
+    p = pg.model_params(closure="slm", dt=0.05, nu=1e-3)
+    po = _oracle_params(p)
+    pg.pdf_estimate_stats(gp, gm)
+    oes, ons, ond, _ = oracle.statistics(M, ost)
+    for s in range(20):
+        rows = oracle.elem_coeff(M, ons, ond, po)
+        cnt, status = oracle.step(M, rows, po, 1, s, ost)
+        info = pg.pdf_step(gp, gm, p, step=s, info=True)
+        oes, ons, ond, _ = oracle.statistics(M, ost, ons)
+        pg.pdf_estimate_stats(gp, gm)
+        st = _host(gp.get_state())
+        _compare_states(st, ost, "tiny step %d" % s, (status & oracle.TRK_NEAR_FACE) != 0)
+    _check_stats(gp, gm, M, ost, ons)
+
+
+def test_full_size_sampled_step_and_statistics():
+    """The measured workload (200x400 nodes, 100 particles per element, ~16M
+    particles) in the launch configuration the benchmark times: statistics
+    checked in full against the oracle, one step checked on a sample of
+    particles that the oracle advances one by one with the library's rows."""
+    cfg = inputs.workload("channel_200x400_ppe100")
+    m = inputs.channel_mesh(cfg["nx"], cfg["ny"], jitter=cfg["jitter"], seed=cfg["seed"])
+    psi = inputs.scalar_slab(m, cfg["psi_slab_x"])
+    gm = pg.Mesh(m)
+    M = oracle.Mesh(m)
+    gp = pg.Particles(gm, cfg["seed"], ppe=cfg["ppe"], u_sigma=cfg["u_sigma"], elem_psi0=psi)
+    p = pg.model_params(dt=cfg["dt"], nu=cfg["nu"], Pi=cfg["Pi"], closure=cfg["closure"])
+    po = _oracle_params(p)
+    pg.pdf_estimate_stats(gp, gm)
+    for s in range(2):
+        pg.pdf_step(gp, gm, p, step=s)
+        pg.pdf_estimate_stats(gp, gm)
+    st0 = _host(gp.get_state())
+    rows = pg.pdf_elem_coeff(gp, gm, p).cpu().numpy()
+    # full statistics check of the library's current state
+    es = torch.empty((gm.n_tri, 13), dtype=torch.float64, device="cuda")
+    pg.pdf_estimate_stats(gp, gm, es)
+    oes = oracle.elem_stats(gm.n_tri, st0)
+    assert np.array_equal(es[:, 0].cpu().numpy(), oes[:, 0])
+    assert_field_close(es[:, 1:].cpu().numpy(), oes[:, 1:], "full-size element stats")
+    # sampled one-step parity
+    rng = np.random.default_rng(9)
+    pid = np.sort(rng.choice(gp.n, 4000, replace=False)).astype(np.int32)
+    sub = {k: st0[k][pid].copy() for k in KEYS}
+    sub["elem"] = st0["elem"][pid].copy()
+    info = pg.pdf_step(gp, gm, p, step=2, info=True)
+    cnt, status = oracle.step(M, rows, po, cfg["seed"], 2, sub, pid=pid)
+    st1 = _host(gp.get_state())
+    got = {k: st1[k][pid] for k in KEYS}
+    got["elem"] = st1["elem"][pid]
+    _compare_states(got, sub, "full-size sampled step", (status & oracle.TRK_NEAR_FACE) != 0)
+    assert info["lost"] == 0
