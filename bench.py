@@ -66,7 +66,7 @@ def _kernel_sha():
 def _traffic_from_profile():
     """DRAM bytes per k_step launch from the committed ncu summary, if it was
     taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "k_step_channel_200x400_ppe100.md")
+    path = os.path.join(ROOT, "profiles", "k_step_channel_200x400.md")
     try:
         text = open(path).read()
     except OSError:
