@@ -212,6 +212,34 @@ pdf_status pdf_step(pdf_particles* p, const pdf_mesh* m, const pdf_model_params*
 pdf_status pdf_estimate_stats(pdf_particles* p, const pdf_mesh* m, double* elem_stats,
                               double* node_stats, double* node_derivs, void* stream);
 
+/* pdf_estimate_stats for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart; this is a service of the library.  Some
+ * callers must not call cudaMalloc or cudaFree: a host loop that cannot take
+ * the device-wide synchronization those calls may cause, code running where
+ * another allocator (an application's memory pool) already owns the device
+ * memory budget, or a plugin or callback that is forbidden to allocate.
+ * pdf_estimate_stats keeps its grouping scratch in buffers allocated by
+ * pdf_particles_init; this variant allocates nothing and instead uses one
+ * scratch array of fixed size compiled into the library (about 9.2 MiB, held
+ * by every GPU that loads the library until the process exits).
+ *
+ * Same arguments, results and outputs as pdf_estimate_stats (the statistics
+ * are bit-identical to it), with these limits and rules:
+ *   - at most PDF_NOALLOC_MAX_PARTICLES particles and PDF_NOALLOC_MAX_ELEMENTS
+ *     elements, else PDF_EINVAL with a message naming the limit;
+ *   - the first call on each device looks up that device's copy of the
+ *     scratch array (with the device current), so make the first call on a
+ *     device before any stream capture;
+ *   - every call shares the one scratch array: calls whose work overlaps on
+ *     the GPU (different streams or threads without ordering) race and give
+ *     wrong statistics.  The scratch keeps the last call's contents; nothing
+ *     in it needs to start at zero. */
+#define PDF_NOALLOC_MAX_PARTICLES 524288
+#define PDF_NOALLOC_MAX_ELEMENTS 262144
+pdf_status pdf_estimate_stats_noalloc(pdf_particles* p, const pdf_mesh* m, double* elem_stats,
+                                      double* node_stats, double* node_derivs, void* stream);
+
 /* The element-average coefficient rows [n_tri][PDF_NCOEF] that pdf_step
  * would use for GLM/SLM with this wp (device output). */
 pdf_status pdf_elem_coeff(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,

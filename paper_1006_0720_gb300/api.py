@@ -171,6 +171,18 @@ def pdf_estimate_stats(particles, mesh, elem_stats=None, node_stats=None, node_d
                                    _stream(stream)), "pdf_estimate_stats")
 
 
+def pdf_estimate_stats_noalloc(particles, mesh, elem_stats=None, node_stats=None, node_derivs=None,
+                               stream=None):
+    """pdf_estimate_stats without any device allocation (fixed library scratch;
+    see include/pdfgb.h for its limits and the rule on overlapping calls)."""
+    check(lib().pdf_estimate_stats_noalloc(
+        particles.handle, mesh.handle,
+        _ptr(elem_stats, torch.float64, None if elem_stats is None else capi.PDF_NES * mesh.n_tri),
+        _ptr(node_stats, torch.float64, None if node_stats is None else capi.PDF_NNS * mesh.n_nodes),
+        _ptr(node_derivs, torch.float64, None if node_derivs is None else capi.PDF_NND * mesh.n_nodes),
+        _stream(stream)), "pdf_estimate_stats_noalloc")
+
+
 def pdf_elem_coeff(particles, mesh, params, wp=None, rows=None, stream=None):
     if rows is None:
         rows = torch.empty((mesh.n_tri, capi.PDF_NCOEF), dtype=torch.float64, device="cuda")

@@ -14,6 +14,7 @@ PDF_TM_TURB, PDF_TM_CPHI = 0, 1
 PDF_PRESSURE_NONE, PDF_PRESSURE_CHANNEL = 0, 1
 PDF_FP64, PDF_FP32_STATE = 0, 1
 PDF_NCOEF, PDF_NES, PDF_NNS, PDF_NND = 26, 13, 12, 10
+PDF_NOALLOC_MAX_PARTICLES, PDF_NOALLOC_MAX_ELEMENTS = 524288, 262144
 
 
 class PdfError(RuntimeError):
@@ -73,6 +74,7 @@ PROTOTYPES = {
     "pdf_particles_set_state": (I32, [V, V, V, V, V, V, V, V, V, V]),
     "pdf_step": (I32, [V, V, ctypes.POINTER(ModelParams), V, V, U32, V, ctypes.POINTER(StepInfo)]),
     "pdf_estimate_stats": (I32, [V, V, V, V, V, V]),
+    "pdf_estimate_stats_noalloc": (I32, [V, V, V, V, V, V]),
     "pdf_elem_coeff": (I32, [V, V, ctypes.POINTER(ModelParams), V, V, V]),
     "pdf_rng_gauss": (I32, [U64, U32, U32, U32, I64, V, V]),
     "pdf_profile_enable": (I32, [I32]),

@@ -403,3 +403,51 @@ extern "C" pdf_status pdf_estimate_stats(pdf_particles* p, const pdf_mesh* m, do
     PDF_CUDA(cudaMemcpyAsync(node_derivs, p->nd, sizeof(double) * M.n_nodes * PDF_NND, cudaMemcpyDefault, st));
   return PDF_OK;
 }
+
+namespace pdfgb {
+
+// Statistics with caller-chosen grouping buffers (used by the
+// allocation-free entry point in noalloc.cu).  keys_a/vals_a receive the
+// first radix pass, keys_b/vals_b the second; at most two passes, so
+// n_tri <= 2^18.
+pdf_status estimate_stats_with_buffers(pdf_particles* P, int32_t* keys_a, int32_t* vals_a,
+                                       int32_t* keys_b, int32_t* vals_b, int32_t* hist,
+                                       int32_t* hist_part, int32_t* seg, cudaStream_t st) {
+  const MeshDev& M = P->mesh->d;
+  const int64_t n = P->n;
+  int bits = 1;
+  while ((1LL << bits) < (int64_t)M.n_tri) ++bits;
+  const int passes = (bits + kRadixBits - 1) / kRadixBits;
+  if (passes > 2) return fail(PDF_EINVAL, "estimate_stats_with_buffers: more than 2^18 elements");
+  const int64_t n_tiles = radix_tiles(n);
+  const int64_t hist_len = n_tiles * kBins;
+  const int32_t n_scan = radix_scan_blocks(hist_len);
+  const int32_t* kin = P->elem;
+  const int32_t* vin = nullptr;
+  int32_t* kout[2] = {passes == 2 ? keys_a : keys_b, keys_b};
+  int32_t* vout[2] = {passes == 2 ? vals_a : vals_b, vals_b};
+  for (int pass = 0; pass < passes; ++pass) {
+    const int shift = pass * kRadixBits;
+    PDF_KERNEL("k_radix_hist", st, k_radix_hist<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(kin, n, shift, n_tiles, hist));
+    PDF_KERNEL("k_scan_reduce", st, k_scan_reduce<<<n_scan, 1024, 0, st>>>(hist, hist_len, hist_part));
+    PDF_KERNEL("k_scan_top", st, k_scan_top<<<1, 1024, 0, st>>>(hist_part, n_scan));
+    PDF_KERNEL("k_scan_apply", st, k_scan_apply<<<n_scan, 1024, 0, st>>>(hist, hist_len, hist_part));
+    PDF_KERNEL("k_radix_scatter", st, k_radix_scatter<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(
+                                          kin, vin, n, shift, n_tiles, hist, kout[pass], vout[pass]));
+    kin = kout[pass];
+    vin = vout[pass];
+  }
+  PDF_KERNEL("k_seg_offsets", st, k_seg_offsets<<<blocks_for(n + 1, 256), 256, 0, st>>>(kin, n, M.n_tri, seg));
+  PDF_KERNEL("k_elem_stats", st, k_elem_stats<<<blocks_for((int64_t)M.n_tri * 32, 256), 256, 0, st>>>(
+                                     seg, vin, M.n_tri, P->u, P->v, P->w, P->om, P->ps, P->es));
+  PDF_KERNEL("k_node_stats", st, k_node_stats<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(
+                                     M.nse_off, M.nse, M.n_nodes, P->es, P->ns, P->counters + 8));
+  PDF_KERNEL("k_elem_grad1", st, k_elem_grad1<<<blocks_for(M.n_tri, 128), 128, 0, st>>>(M.tri, M.dN, M.n_tri, P->ns, P->eg));
+  PDF_KERNEL("k_node_grad1", st, k_node_grad1<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(M.nse_off, M.nse, M.n_nodes, P->eg, P->nd));
+  PDF_KERNEL("k_elem_grad2", st, k_elem_grad2<<<blocks_for(M.n_tri, 128), 128, 0, st>>>(M.tri, M.dN, M.n_tri, P->nd, P->eg));
+  PDF_KERNEL("k_node_grad2", st, k_node_grad2<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(M.nse_off, M.nse, M.n_nodes, P->eg, P->nd));
+  P->have_stats = true;
+  return PDF_OK;
+}
+
+}  // namespace pdfgb
