@@ -61,6 +61,13 @@ enum { PDF_TM_TURB = 0, PDF_TM_CPHI = 1 };
  * cross-stream balance (1/rho) d<P>/dy = -d<v^2>/dy (eq. cross-stream-mean-
  * momentum-channel). */
 enum { PDF_PRESSURE_NONE = 0, PDF_PRESSURE_CHANNEL = 1 };
+/* How the FP64 particle step is computed.  FX (default): no FP64
+ * instructions on the fast path -- FP64 values decoded into 64-bit fixed point
+ * (exact sums), products in double-float FP32 pairs; particles with values
+ * outside the fixed-point ranges (|x|, |u|, |psi| < 64, |omega| < 1024) or whose
+ * walk meets a wall are finished in FP64.  FP64: native FP64 instructions
+ * throughout (GB300 runs them at ~1/70 of the FP32 rate). */
+enum { PDF_ARITH_FX = 0, PDF_ARITH_FP64 = 1 };
 /* Storage precision of u, v, w, omega, psi.  Positions are always FP64. */
 enum { PDF_FP64 = 0, PDF_FP32_STATE = 1 };
 
@@ -83,14 +90,14 @@ typedef struct {
   int32_t closure;  /* PDF_CLOSURE_* */
   int32_t tm_mode;  /* PDF_TM_* */
   int32_t pressure; /* PDF_PRESSURE_* */
-  int32_t reserved;
+  int32_t arith;    /* PDF_ARITH_* */
   /* model constants, table "Constants for modeling the joint PDF of velocity
    * and frequency" (ch. 4), and C0 of eq. wall-GandC */
   double C1, C2, C3, C4, CT, CL, Ceta, Cv, gamma5, Comega1, Comega2, C0_slm;
 } pdf_model_params;
 
 /* Fills the paper's constants and dt = 1e-3, nu = 1e-3, Pi = 2e-3,
- * c_phi = 2, GLM, TURB, CHANNEL. */
+ * c_phi = 2, GLM, TURB, CHANNEL, ARITH_FX. */
 void pdf_model_params_default(pdf_model_params* p);
 
 typedef struct {
@@ -244,6 +251,82 @@ pdf_status pdf_estimate_stats_noalloc(pdf_particles* p, const pdf_mesh* m, doubl
  * would use for GLM/SLM with this wp (device output). */
 pdf_status pdf_elem_coeff(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,
                           const double* wp, double* rows, void* stream);
+
+/* ---------------------------------------------------------------- elliptic relaxation */
+
+/* The elliptic-relaxation solve for the tensor wp_ij (eq. elliptic-relaxation-
+ * Lagrangian, with eqs. H, A_v, bij, L and Cxi), discretised with linear
+ * triangles and solved by Jacobi-preconditioned conjugate gradients in FP64
+ * (sec. 3.2), all nine components at once:
+ *   (M + K_L) wp = M rhs,  M the consistent mass matrix, K_L the stiffness
+ *   matrix weighted by the element mean of the nodal L^2.
+ * Right-hand side and L from the statistics of the last pdf_estimate_stats.
+ * Reflecting walls act as symmetry planes: off-diagonal components are 0 on
+ * wall nodes, diagonal components have zero normal derivative.  C_xi =
+ * 1 + 1.3 n_i n_i for wp_ii with n the outward normal of the nearest wall
+ * edge.  Periodic twin nodes share one unknown.
+ *   wp       device [9][n_nodes] (component-major, wp[(3i+j)*n_nodes + n]);
+ *            in: the initial guess (warm start), out: the solution
+ *   rtol     stop a component when ||r|| <= rtol ||b|| (b = M rhs)
+ *   max_it   iteration cap; PDF_ENOTCONV if a component is not converged
+ *   iters, rel_res  host [9] or NULL: iterations and final ||r||/||b||
+ * The call synchronizes `stream` once per iteration (convergence test). */
+pdf_status pdf_relax_solve(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params, double* wp,
+                           double rtol, int32_t max_it, int32_t* iters, double* rel_res, void* stream);
+/* The nodal right-hand side rhs [9][n_nodes] and L^2 [3][n_nodes] (C_xi of
+ * wp_11, of wp_22, and 1) that pdf_relax_solve uses (device or page-locked
+ * host outputs; either may be NULL). */
+pdf_status pdf_relax_rhs(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params, double* rhs,
+                         double* L2, void* stream);
+/* Host copies of each node's distance to the nearest wall edge [n_nodes] and
+ * that edge's unit outward normal [n_nodes][2]; either may be NULL. */
+pdf_status pdf_mesh_wall_distance(const pdf_mesh* m, double* dist, double* normal);
+
+/* ---------------------------------------------------------------- learned warm start */
+
+/* A per-node MLP that proposes the initial guess of pdf_relax_solve.  The
+ * paper warm-starts from the previous step (sec. 3.2); the network is an
+ * addition, and the FP64 solve it seeds still runs to the same residual.
+ * Architecture: 11 inputs (<U>, <V>, <W>, <uu>, <vv>, <ww>, <uv>, <uw>, <vw>,
+ * <omega>, wall distance) -> 64 -> 64 -> 64 -> 9 outputs (wp_ij, row-major
+ * ij), GELU, standardized inputs and outputs.  Matrix products on the
+ * tensor cores from BF16 operands with FP32 accumulation; the standardized
+ * input, the weights, each hidden activation and each back-propagated
+ * gradient are rounded to BF16 before a product.  Training: mean squared
+ * error over the batch and the 9 standardized outputs, Adam (beta 0.9,
+ * 0.999, eps 1e-8) on FP32 master parameters.  Deterministic.
+ * Parameters, flat FP32 [PDF_MLP_NPARAM]: W0[64][11] b0[64] W1[64][64]
+ * b1[64] W2[64][64] b2[64] W3[9][64] b3[9].  Standardization, FP32 [64]:
+ * in_mean[16] in_inv_std[16] out_mean[16] out_std[16] (first 11 / 9 used).
+ * Feature and target arrays are device FP32: X [n][11], Y [n][9]. */
+#define PDF_MLP_NPARAM 9673
+typedef struct pdf_mlp pdf_mlp;
+/* He-normal weights from Philox (key seed, purpose 3), zero biases, identity
+ * standardization; allocates ~12 MB of device memory. */
+pdf_status pdf_mlp_create(uint64_t seed, pdf_mlp** out);
+pdf_status pdf_mlp_destroy(pdf_mlp* net);
+/* Copy parameters / standardization in (set, set_norm) or out (get,
+ * get_norm); any pointer may be NULL; host or device memory.  Setting
+ * parameters resets the Adam state.  Synchronous. */
+pdf_status pdf_mlp_params(pdf_mlp* net, const float* set, float* get, const float* set_norm, float* get_norm);
+/* Standardization fitted to n training pairs (means and standard deviations). */
+pdf_status pdf_mlp_fit_norm(pdf_mlp* net, const float* X, const float* Y, int64_t n, void* stream);
+pdf_status pdf_mlp_forward(const pdf_mlp* net, const float* X, int64_t n, float* Y, void* stream);
+/* Loss and gradient [PDF_MLP_NPARAM] (device or host) on n pairs, no update;
+ * loss (host, may be NULL; synchronizes). */
+pdf_status pdf_mlp_grad(pdf_mlp* net, const float* X, const float* Y, int64_t n, float* grad, float* loss,
+                        void* stream);
+/* One Adam step with learning rate lr on the n pairs (one batch). */
+pdf_status pdf_mlp_train_step(pdf_mlp* net, const float* X, const float* Y, int64_t n, float lr, float* loss,
+                              void* stream);
+/* Features X [n_nodes][11] of every node from the last statistics and, if wp
+ * (device [9][n_nodes]) and Y are given, the targets Y [n_nodes][9]. */
+pdf_status pdf_mlp_features(pdf_particles* p, const pdf_mesh* m, const double* wp, float* X, float* Y,
+                            void* stream);
+/* The network's wp [9][n_nodes] (device FP64) for the current statistics;
+ * scratch: device FP32 of at least 20 n_nodes entries. */
+pdf_status pdf_mlp_guess(const pdf_mlp* net, pdf_particles* p, const pdf_mesh* m, double* wp, float* scratch,
+                         void* stream);
 
 /* ---------------------------------------------------------------- random numbers */
 

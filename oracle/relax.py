@@ -1,0 +1,163 @@
+"""Oracle of the elliptic-relaxation solve (TEST INFRASTRUCTURE ONLY).
+
+Eq. elliptic-relaxation-Lagrangian, wp_ij - L^2 lap wp_ij = rhs_ij, with the
+lengthscale of Eq. L (anisotropic C_xi of Eq. Cxi), discretised with linear
+triangles (sec. 3.2: P1 finite elements) as
+
+    (M + K_L) wp = M rhs,
+    M_ab   = sum_e A_e (1 + delta_ab) / 12          (consistent mass)
+    K_L,ab = sum_e L2_e A_e grad N_a . grad N_b      (L2_e: mean of nodal L^2)
+
+READINGS (the paper only says "P1 FEM, Jacobi-PCG, warm start"):
+  * the term from grad(L^2) is dropped, matching the L^2 lap wp form (ch. 2);
+  * reflecting walls are symmetry planes (as the channel centreline, sec.
+    4.2.1): off-diagonal components Dirichlet 0 at wall nodes, diagonal
+    components natural (Neumann) conditions;
+  * C_xi = 1 + 1.3 n_i n_i for wp_ii, 1 for off-diagonal components, n the
+    unit outward normal of the nearest wall edge;
+  * periodic twin nodes are one unknown.
+The linear system is solved by scipy's sparse direct solver (a library
+primitive); the oracle does not iterate.
+"""
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import NNS  # noqa: F401  (layout constants live in the package)
+
+CL, CETA, CT = 0.134, 72.0, 6.0
+KFLOOR = EFLOOR = 1e-12
+
+
+def wall_normals(mesh):
+    """Per node: distance to the nearest wall edge and that edge's unit
+    outward normal (nx, ny).  Wall edges are the boundary edges tagged WALL."""
+    xy = mesh["xy"]
+    bnd = mesh["bnd"]
+    walls = bnd[bnd[:, 2] == 1]
+    a = xy[walls[:, 0]]
+    b = xy[walls[:, 1]]
+    # outward normal: the wall edge belongs to one triangle; the normal points
+    # away from that triangle's third node
+    tri = mesh["tri"]
+    n_out = np.zeros((len(walls), 2))
+    for i, (p, q, _) in enumerate(walls):
+        t = np.nonzero(np.sum((tri == p) | (tri == q), axis=1) == 2)[0][0]
+        c = [v for v in tri[t] if v != p and v != q][0]
+        d = b[i] - a[i]
+        nrm = np.array([d[1], -d[0]]) / np.hypot(d[0], d[1])
+        if np.dot(xy[c] - a[i], nrm) > 0:
+            nrm = -nrm
+        n_out[i] = nrm
+    dist = np.full(len(xy), np.inf)
+    nn = np.zeros((len(xy), 2))
+    for i in range(len(walls)):
+        d = b[i] - a[i]
+        t = np.clip(((xy - a[i]) @ d) / (d @ d), 0.0, 1.0)
+        proj = a[i] + t[:, None] * d[None, :]
+        di = np.hypot(*(xy - proj).T)
+        better = di < dist
+        dist[better] = di[better]
+        nn[better] = n_out[i]
+    return dist, nn
+
+
+def lengthscale2(S, nu, cxi):
+    """L^2 at nodes (Eq. L), S the node statistics [n, 12]."""
+    k = np.maximum(0.5 * (S[:, 5] + S[:, 6] + S[:, 7]), KFLOOR)
+    om = S[:, 3]
+    eps = np.maximum(om * (k + nu * CT * CT * om), EFLOOR)
+    L = CL * np.maximum(cxi * k ** 1.5 / eps, CETA * (nu ** 3 / eps) ** 0.25)
+    return L * L
+
+
+def _rep(mesh):
+    n = len(mesh["xy"])
+    twin = mesh.get("twin")
+    rep = np.arange(n)
+    if twin is not None:
+        t = np.asarray(twin)
+        m = t >= 0
+        rep[m] = np.minimum(np.arange(n)[m], t[m])
+    return rep
+
+
+def assemble(mesh, L2_node):
+    """Sparse (M, K_L) over representative nodes (twins merged)."""
+    xy, tri = mesh["xy"], mesh["tri"]
+    rep = _rep(mesh)
+    n = len(xy)
+    rows, cols, mv, kv = [], [], [], []
+    for e, t in enumerate(tri):
+        P = xy[t]
+        twoA = (P[1, 0] - P[0, 0]) * (P[2, 1] - P[0, 1]) - (P[1, 1] - P[0, 1]) * (P[2, 0] - P[0, 0])
+        A = 0.5 * twoA
+        # shape-function derivatives (sec. 3.4)
+        yCA, yBA = P[2, 1] - P[0, 1], P[1, 1] - P[0, 1]
+        xCA, xBA = P[2, 0] - P[0, 0], P[1, 0] - P[0, 0]
+        dx = np.array([-yCA + yBA, yCA, -yBA]) / twoA
+        dy = np.array([xCA - xBA, -xCA, xBA]) / twoA
+        L2e = np.mean(L2_node[t])
+        for a in range(3):
+            for b in range(3):
+                rows.append(rep[t[a]])
+                cols.append(rep[t[b]])
+                mv.append(A * (2.0 if a == b else 1.0) / 12.0)
+                kv.append(L2e * A * (dx[a] * dx[b] + dy[a] * dy[b]))
+    M = sp.csr_matrix((mv, (rows, cols)), shape=(n, n))
+    K = sp.csr_matrix((kv, (rows, cols)), shape=(n, n))
+    return M, K
+
+
+def wall_nodes(mesh):
+    bnd = mesh["bnd"]
+    w = bnd[bnd[:, 2] == 1]
+    return np.unique(np.concatenate([w[:, 0], w[:, 1]]))
+
+
+def solve(mesh, S, rhs, nu):
+    """wp [9, n_nodes] from node statistics S [n, 12] and the right-hand side
+    rhs [9, n_nodes] (Eq. elliptic-relaxation-Lagrangian at the nodes)."""
+    n = len(mesh["xy"])
+    rep = _rep(mesh)
+    is_rep = rep == np.arange(n)
+    _, nrm = wall_normals(mesh)
+    walls = wall_nodes(mesh)
+    wall_rep = np.unique(rep[walls])
+    out = np.zeros((9, n))
+    cache = {}
+    for ij in range(9):
+        i, j = divmod(ij, 3)
+        if i == j:
+            ni = nrm[:, i] if i < 2 else np.zeros(n)
+            cxi = 1.0 + 1.3 * ni * ni
+        else:
+            cxi = np.ones(n)
+        key = (tuple(np.round(cxi, 12)), i == j)
+        if key not in cache:
+            M, K = assemble(mesh, lengthscale2(S, nu, cxi))
+            A = (M + K).tolil()
+            if i != j:
+                for r in wall_rep:
+                    A.rows[r] = [r]
+                    A.data[r] = [1.0]
+                A = A.tocsr()
+                # symmetric elimination: zero the Dirichlet columns (value 0)
+                mask = np.ones(n)
+                mask[wall_rep] = 0.0
+                D = sp.diags(mask)
+                A = (D @ A @ D + sp.diags(1.0 - mask)).tocsr()
+            else:
+                A = A.tocsr()
+            # unknowns: representative nodes only
+            idx = np.nonzero(is_rep)[0]
+            cache[key] = (A[idx][:, idx].tocsc(), M, idx)
+        A, M, idx = cache[key]
+        b = M @ rhs[ij]
+        if i != j:
+            b[wall_rep] = 0.0
+        x = spla.spsolve(A, b[idx])
+        full = np.zeros(n)
+        full[idx] = x
+        out[ij] = full[rep]
+    return out

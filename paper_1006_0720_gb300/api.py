@@ -39,7 +39,7 @@ def model_params(**kw):
     p = capi.ModelParams()
     lib().pdf_model_params_default(ctypes.byref(p))
     names = {"closure": {"glm": 0, "slm": 1, "frozen": 2}, "tm_mode": {"turb": 0, "cphi": 1},
-             "pressure": {"none": 0, "channel": 1}}
+             "pressure": {"none": 0, "channel": 1}, "arith": {"fx": 0, "fp64": 1}}
     for k, v in kw.items():
         if k in names and isinstance(v, str):
             v = names[k][v]
@@ -71,6 +71,13 @@ class Mesh:
         check(lib().pdf_mesh_connectivity(self.handle, nbr.ctypes.data_as(capi.PI32),
                                           shift.ctypes.data_as(capi.PI32)), "pdf_mesh_connectivity")
         return nbr, shift
+
+    def wall_distance(self):
+        d = np.zeros(self.n_nodes)
+        nrm = np.zeros((self.n_nodes, 2))
+        check(lib().pdf_mesh_wall_distance(self.handle, d.ctypes.data_as(capi.PD), nrm.ctypes.data_as(capi.PD)),
+              "pdf_mesh_wall_distance")
+        return d, nrm
 
     def close(self):
         if getattr(self, "handle", None):
@@ -223,3 +230,93 @@ def pdf_profile_query(kernel):
 
 def pdf_kernel_launches():
     return int(lib().pdf_kernel_launches())
+
+
+def pdf_relax_solve(particles, mesh, params, wp, rtol=1e-10, max_it=1000, stream=None):
+    """Solve for wp in place (device [9, n_nodes] float64, in: initial guess).
+    Returns (iterations [9], relative residuals [9]); raises on PDF_ENOTCONV."""
+    it = (ctypes.c_int32 * 9)()
+    rr = (ctypes.c_double * 9)()
+    check(lib().pdf_relax_solve(particles.handle, mesh.handle, ctypes.byref(params),
+                                _ptr(wp, torch.float64, 9 * mesh.n_nodes), float(rtol), int(max_it), it, rr,
+                                _stream(stream)), "pdf_relax_solve")
+    return list(it), list(rr)
+
+
+def pdf_relax_rhs(particles, mesh, params, stream=None):
+    rhs = torch.empty((9, mesh.n_nodes), dtype=torch.float64, device="cuda")
+    L2 = torch.empty((3, mesh.n_nodes), dtype=torch.float64, device="cuda")
+    check(lib().pdf_relax_rhs(particles.handle, mesh.handle, ctypes.byref(params), _ptr(rhs), _ptr(L2),
+                              _stream(stream)), "pdf_relax_rhs")
+    return rhs, L2
+
+
+class Mlp:
+    """Owns a pdf_mlp handle (the learned warm start of the relaxation solve)."""
+
+    def __init__(self, seed=0):
+        h = ctypes.c_void_p()
+        check(lib().pdf_mlp_create(int(seed), ctypes.byref(h)), "pdf_mlp_create")
+        self.handle = h
+
+    def params(self):
+        out = np.zeros(capi.PDF_MLP_NPARAM, dtype=np.float32)
+        nrm = np.zeros(64, dtype=np.float32)
+        check(lib().pdf_mlp_params(self.handle, None, ctypes.c_void_p(out.ctypes.data), None,
+                                   ctypes.c_void_p(nrm.ctypes.data)), "pdf_mlp_params")
+        return out, nrm
+
+    def set_params(self, flat=None, norm=None):
+        f = None if flat is None else np.ascontiguousarray(flat, dtype=np.float32)
+        n = None if norm is None else np.ascontiguousarray(norm, dtype=np.float32)
+        check(lib().pdf_mlp_params(self.handle, None if f is None else ctypes.c_void_p(f.ctypes.data), None,
+                                   None if n is None else ctypes.c_void_p(n.ctypes.data), None), "pdf_mlp_params")
+
+    def fit_norm(self, X, Y, stream=None):
+        check(lib().pdf_mlp_fit_norm(self.handle, _ptr(X, torch.float32), _ptr(Y, torch.float32), X.shape[0],
+                                     _stream(stream)), "pdf_mlp_fit_norm")
+
+    def forward(self, X, stream=None):
+        Y = torch.empty((X.shape[0], 9), dtype=torch.float32, device="cuda")
+        check(lib().pdf_mlp_forward(self.handle, _ptr(X, torch.float32), X.shape[0], _ptr(Y), _stream(stream)),
+              "pdf_mlp_forward")
+        return Y
+
+    def grad(self, X, Y, stream=None):
+        g = torch.empty(capi.PDF_MLP_NPARAM, dtype=torch.float32, device="cuda")
+        loss = ctypes.c_float()
+        check(lib().pdf_mlp_grad(self.handle, _ptr(X, torch.float32), _ptr(Y, torch.float32), X.shape[0], _ptr(g),
+                                 ctypes.byref(loss), _stream(stream)), "pdf_mlp_grad")
+        return loss.value, g
+
+    def train_step(self, X, Y, lr, want_loss=False, stream=None):
+        loss = ctypes.c_float()
+        check(lib().pdf_mlp_train_step(self.handle, _ptr(X, torch.float32), _ptr(Y, torch.float32), X.shape[0],
+                                       float(lr), ctypes.byref(loss) if want_loss else None, _stream(stream)),
+              "pdf_mlp_train_step")
+        return loss.value if want_loss else None
+
+    def guess(self, particles, mesh, wp, stream=None):
+        scratch = torch.empty(20 * mesh.n_nodes, dtype=torch.float32, device="cuda")
+        check(lib().pdf_mlp_guess(self.handle, particles.handle, mesh.handle, _ptr(wp, torch.float64),
+                                  _ptr(scratch), _stream(stream)), "pdf_mlp_guess")
+        return wp
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pdf_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pdf_mlp_features(particles, mesh, wp=None, stream=None):
+    X = torch.empty((mesh.n_nodes, 11), dtype=torch.float32, device="cuda")
+    Y = None if wp is None else torch.empty((mesh.n_nodes, 9), dtype=torch.float32, device="cuda")
+    check(lib().pdf_mlp_features(particles.handle, mesh.handle, _ptr(wp, torch.float64), _ptr(X), _ptr(Y),
+                                 _stream(stream)), "pdf_mlp_features")
+    return X, Y

@@ -13,8 +13,10 @@ PDF_CLOSURE_GLM, PDF_CLOSURE_SLM, PDF_CLOSURE_FROZEN = 0, 1, 2
 PDF_TM_TURB, PDF_TM_CPHI = 0, 1
 PDF_PRESSURE_NONE, PDF_PRESSURE_CHANNEL = 0, 1
 PDF_FP64, PDF_FP32_STATE = 0, 1
+PDF_ARITH_FX, PDF_ARITH_FP64 = 0, 1
 PDF_NCOEF, PDF_NES, PDF_NNS, PDF_NND = 26, 13, 12, 10
 PDF_NOALLOC_MAX_PARTICLES, PDF_NOALLOC_MAX_ELEMENTS = 524288, 262144
+PDF_MLP_NPARAM = 9673
 
 
 class PdfError(RuntimeError):
@@ -27,7 +29,7 @@ class PdfError(RuntimeError):
 class ModelParams(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("nu", ctypes.c_double), ("Pi", ctypes.c_double),
                 ("c_phi", ctypes.c_double), ("closure", ctypes.c_int32), ("tm_mode", ctypes.c_int32),
-                ("pressure", ctypes.c_int32), ("reserved", ctypes.c_int32)] + [
+                ("pressure", ctypes.c_int32), ("arith", ctypes.c_int32)] + [
         (n, ctypes.c_double) for n in ("C1", "C2", "C3", "C4", "CT", "CL", "Ceta", "Cv", "gamma5",
                                        "Comega1", "Comega2", "C0_slm")]
 
@@ -76,6 +78,18 @@ PROTOTYPES = {
     "pdf_estimate_stats": (I32, [V, V, V, V, V, V]),
     "pdf_estimate_stats_noalloc": (I32, [V, V, V, V, V, V]),
     "pdf_elem_coeff": (I32, [V, V, ctypes.POINTER(ModelParams), V, V, V]),
+    "pdf_relax_solve": (I32, [V, V, ctypes.POINTER(ModelParams), V, D, I32, ctypes.POINTER(I32), PD, V]),
+    "pdf_relax_rhs": (I32, [V, V, ctypes.POINTER(ModelParams), V, V, V]),
+    "pdf_mesh_wall_distance": (I32, [V, PD, PD]),
+    "pdf_mlp_create": (I32, [U64, PV]),
+    "pdf_mlp_destroy": (I32, [V]),
+    "pdf_mlp_params": (I32, [V, V, V, V, V]),
+    "pdf_mlp_fit_norm": (I32, [V, V, V, I64, V]),
+    "pdf_mlp_forward": (I32, [V, V, I64, V, V]),
+    "pdf_mlp_grad": (I32, [V, V, V, I64, V, ctypes.POINTER(ctypes.c_float), V]),
+    "pdf_mlp_train_step": (I32, [V, V, V, I64, ctypes.c_float, ctypes.POINTER(ctypes.c_float), V]),
+    "pdf_mlp_features": (I32, [V, V, V, V, V, V]),
+    "pdf_mlp_guess": (I32, [V, V, V, V, V, V]),
     "pdf_rng_gauss": (I32, [U64, U32, U32, U32, I64, V, V]),
     "pdf_profile_enable": (I32, [I32]),
     "pdf_profile_reset": (I32, []),

@@ -33,7 +33,7 @@ extern "C" void pdf_model_params_default(pdf_model_params* p) {
   p->closure = PDF_CLOSURE_GLM;
   p->tm_mode = PDF_TM_TURB;
   p->pressure = PDF_PRESSURE_CHANNEL;
-  p->reserved = 0;
+  p->arith = PDF_ARITH_FX;
   // table "Constants for modeling the joint PDF of velocity and frequency"
   p->C1 = 1.85; p->C2 = 0.63; p->C3 = 5.0; p->C4 = 0.25; p->CT = 6.0; p->CL = 0.134;
   p->Ceta = 72.0; p->Cv = 1.4; p->gamma5 = 0.1; p->Comega1 = 0.5; p->Comega2 = 0.73;

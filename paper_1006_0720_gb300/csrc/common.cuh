@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/pdfgb.h"
+#include "fx.cuh"
 
 namespace pdfgb {
 
@@ -44,6 +45,29 @@ struct __align__(16) ElemGeo {
 };
 static_assert(sizeof(ElemGeo) == 80, "ElemGeo layout");
 
+// The same data for the fixed-point walk: node B in fixed point (56 fraction
+// bits), the edge vectors and twice the area as double-floats.
+struct __align__(16) FxGeo {
+  int64_t xb, yb;
+  fx::df cbx, cby, abx, aby, two_area;
+  int32_t nbr[3];
+  int8_t shift[3];
+  int8_t pad;
+};
+static_assert(sizeof(FxGeo) == 80, "FxGeo layout");
+
+// Coefficient row of the fixed-point kernel (256 B): the element means of
+// U, V, W and phi in fixed point (56 fraction bits) and the scaled
+// coefficients as double-floats:
+//   c0-5 sqrt(2 nu dt) d<U_i>/dx_j; c6-8 a_i dt; c9-17 G_ij dt;
+//   c18 sqrt(C0 eps dt); c19 (C3 + S_w) <w> dt; c20 C3 <w>^2 dt;
+//   c21 <w> sqrt(2 C3 C4 dt); c22 dt / t_m; c27.h != 0: use the FP64 path.
+struct __align__(16) FxRow {
+  int64_t mean[4];
+  fx::df c[28];
+};
+static_assert(sizeof(FxRow) == 256, "FxRow layout");
+
 // Device-resident mesh.
 struct MeshDev {
   int32_t n_nodes = 0, n_tri = 0;
@@ -51,6 +75,7 @@ struct MeshDev {
   double* xy = nullptr;        // [n_nodes][2]
   int32_t* tri = nullptr;      // [n_tri][3]
   ElemGeo* geo = nullptr;      // [n_tri]
+  FxGeo* fgeo = nullptr;       // [n_tri]
   double* dN = nullptr;        // [n_tri][6]: dNA/dx dNB/dx dNC/dx dNA/dy dNB/dy dNC/dy
   int32_t* nse_off = nullptr;  // [n_nodes + 1] node -> surrounding elements (twins merged)
   int32_t* nse = nullptr;
@@ -60,8 +85,37 @@ struct MeshDev {
 
 }  // namespace pdfgb
 
+namespace pdfgb {
+// The relaxation system over the unknowns (periodic twins merged).
+struct RelaxMesh {
+  int32_t n_rep = 0;
+  int64_t nnz = 0;
+  int32_t* rp = nullptr;        // [n_rep + 1] CSR rows
+  int32_t* ci = nullptr;        // [nnz] columns (unknown ids)
+  double* mval = nullptr;       // [nnz] consistent mass
+  int32_t* ctb_off = nullptr;   // [nnz + 1] stiffness contributions per entry
+  int32_t* ctb_e = nullptr;     //   element
+  double* ctb_k = nullptr;      //   A_e grad N_a . grad N_b
+  uint8_t* wall = nullptr;      // [n_rep] unknown on a wall
+  int32_t* rep_node = nullptr;  // [n_rep] node id of each unknown
+  int32_t* node_rep = nullptr;  // [n_nodes] unknown of each node
+  double* wall_n = nullptr;     // [n_nodes][2] outward normal of the nearest wall edge
+  double* wall_d = nullptr;     // [n_nodes] distance to it
+};
+struct RelaxWork {
+  int32_t nb = 0;
+  double *f = nullptr, *L2 = nullptr, *aval = nullptr, *diag = nullptr;
+  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  double *part = nullptr, *scal = nullptr, *beta = nullptr, *host = nullptr;
+  int32_t* active = nullptr;
+};
+void relax_free(RelaxWork& W);
+}  // namespace pdfgb
+
 struct pdf_mesh {
   pdfgb::MeshDev d;
+  pdfgb::RelaxMesh rx;
+  std::vector<double> wall_d, wall_n;
   // host copies
   std::vector<double> xy;
   std::vector<int32_t> tri, nbr, shift, twin;
@@ -91,6 +145,9 @@ struct pdf_particles {
   double *x = nullptr, *y = nullptr, *u = nullptr, *v = nullptr, *w = nullptr, *om = nullptr,
          *ps = nullptr;
   int32_t* elem = nullptr;
+  // PDF_FP32_STATE: u, v, w, omega, psi in FP32 (x, y stay FP64 above)
+  float *uf = nullptr, *vf = nullptr, *wf = nullptr, *omf = nullptr, *psf = nullptr;
+  float* rows_f32 = nullptr;  // [n_tri][32] coefficient rows in FP32 (same layout as rows)
   // statistics
   double* es = nullptr;    // [n_tri][13]
   double* ns = nullptr;    // [n_nodes][12]
@@ -98,6 +155,7 @@ struct pdf_particles {
   double* eg = nullptr;    // [n_tri][8] element gradients (scratch)
   double* nc = nullptr;    // [n_nodes][26] nodal coefficients (scratch)
   double* rows = nullptr;  // [n_tri][32]
+  pdfgb::FxRow* rows_fx = nullptr;  // [n_tri]
   bool have_stats = false;
   // grouping
   int32_t* keys[2] = {nullptr, nullptr};
@@ -111,6 +169,8 @@ struct pdf_particles {
   int32_t n_scan_blocks = 0;
   // counters
   long long* counters = nullptr;  // [16] device
+  // elliptic relaxation work space (allocated on first use)
+  pdfgb::RelaxWork rx;
 };
 
 namespace pdfgb {

@@ -22,8 +22,130 @@ static pdf_status upload(T** dst, const T* src, size_t n) {
   return PDF_OK;
 }
 
+static void free_relax(RelaxMesh& r) {
+  cudaFree(r.rp); cudaFree(r.ci); cudaFree(r.mval); cudaFree(r.ctb_off); cudaFree(r.ctb_e); cudaFree(r.ctb_k);
+  cudaFree(r.wall); cudaFree(r.rep_node); cudaFree(r.node_rep); cudaFree(r.wall_n); cudaFree(r.wall_d);
+  r = RelaxMesh();
+}
+
+// The relaxation system's structure: unknowns (twins merged), CSR pattern,
+// consistent mass, per-entry stiffness contributions (element order), wall
+// flags and the outward normal of the nearest wall edge at every node.
+static pdf_status build_relax(pdf_mesh* m, const std::vector<int32_t>& bnd_wall, const std::vector<double>& dN,
+                              const std::vector<int32_t>& nse_off, const std::vector<int32_t>& nse) {
+  const int32_t nn = m->d.n_nodes, nt = m->d.n_tri;
+  const int32_t* T = m->tri.data();
+  const double* X = m->xy.data();
+  std::vector<int32_t> node_rep(nn), rep_node;
+  std::vector<int32_t> rep_of(nn);
+  for (int32_t n = 0; n < nn; ++n) rep_of[n] = m->twin[n] >= 0 ? std::min(n, m->twin[n]) : n;
+  std::vector<int32_t> idx(nn, -1);
+  for (int32_t n = 0; n < nn; ++n)
+    if (rep_of[n] == n) { idx[n] = (int32_t)rep_node.size(); rep_node.push_back(n); }
+  for (int32_t n = 0; n < nn; ++n) node_rep[n] = idx[rep_of[n]];
+  const int32_t nr = (int32_t)rep_node.size();
+  // wall unknowns and the nearest wall edge of every node
+  std::vector<uint8_t> wall(nr, 0);
+  const size_t nw = bnd_wall.size() / 2;
+  for (size_t i = 0; i < nw; ++i) { wall[node_rep[bnd_wall[2 * i]]] = 1; wall[node_rep[bnd_wall[2 * i + 1]]] = 1; }
+  std::vector<double> wn(2 * (size_t)nn, 0.0), wd(nn, 1e300);
+  std::vector<double> en(2 * nw);
+  for (size_t i = 0; i < nw; ++i) {
+    const int32_t a = bnd_wall[2 * i], b = bnd_wall[2 * i + 1];
+    const double tx = X[2 * b] - X[2 * a], ty = X[2 * b + 1] - X[2 * a + 1];
+    const double len = std::sqrt(tx * tx + ty * ty);
+    double nx = ty / len, ny = -tx / len;
+    // point away from the element holding the edge
+    for (int32_t e = 0; e < nt; ++e) {
+      const int32_t* t = T + 3 * e;
+      const bool ha = t[0] == a || t[1] == a || t[2] == a, hb = t[0] == b || t[1] == b || t[2] == b;
+      if (!(ha && hb)) continue;
+      const int32_t c = (t[0] != a && t[0] != b) ? t[0] : ((t[1] != a && t[1] != b) ? t[1] : t[2]);
+      if ((X[2 * c] - X[2 * a]) * nx + (X[2 * c + 1] - X[2 * a + 1]) * ny > 0.0) { nx = -nx; ny = -ny; }
+      break;
+    }
+    en[2 * i] = nx; en[2 * i + 1] = ny;
+  }
+  for (int32_t n = 0; n < nn; ++n) {
+    for (size_t i = 0; i < nw; ++i) {
+      const int32_t a = bnd_wall[2 * i], b = bnd_wall[2 * i + 1];
+      const double ax = X[2 * a], ay = X[2 * a + 1], dx = X[2 * b] - ax, dy = X[2 * b + 1] - ay;
+      double t = ((X[2 * n] - ax) * dx + (X[2 * n + 1] - ay) * dy) / (dx * dx + dy * dy);
+      t = std::min(1.0, std::max(0.0, t));
+      const double px = ax + t * dx - X[2 * n], py = ay + t * dy - X[2 * n + 1];
+      const double d = std::sqrt(px * px + py * py);
+      if (d < wd[n]) { wd[n] = d; wn[2 * n] = en[2 * i]; wn[2 * n + 1] = en[2 * i + 1]; }
+    }
+    if (nw == 0) wd[n] = 0.0;
+  }
+  // CSR pattern: row u holds the unknowns of the elements around its node(s)
+  std::vector<int32_t> rp(nr + 1, 0), ci;
+  std::vector<std::vector<int32_t>> cols(nr);
+  for (int32_t u = 0; u < nr; ++u) {
+    const int32_t n = rep_node[u];
+    std::vector<int32_t>& c = cols[u];
+    for (int32_t i = nse_off[n]; i < nse_off[n + 1]; ++i)
+      for (int k = 0; k < 3; ++k) c.push_back(node_rep[T[3 * nse[i] + k]]);
+    std::sort(c.begin(), c.end());
+    c.erase(std::unique(c.begin(), c.end()), c.end());
+    rp[u + 1] = rp[u] + (int32_t)c.size();
+  }
+  const int64_t nnz = rp[nr];
+  ci.reserve(nnz);
+  for (int32_t u = 0; u < nr; ++u) ci.insert(ci.end(), cols[u].begin(), cols[u].end());
+  std::vector<double> mval(nnz, 0.0);
+  std::vector<std::vector<std::pair<int32_t, double>>> ctb(nnz);
+  for (int32_t e = 0; e < nt; ++e) {
+    const double* d = &dN[6 * (size_t)e];
+    const double A = m->area[e];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        const int32_t r = node_rep[T[3 * e + a]], c = node_rep[T[3 * e + b]];
+        const int32_t* beg = ci.data() + rp[r];
+        const int32_t* end = ci.data() + rp[r + 1];
+        const int64_t q = (int64_t)(std::lower_bound(beg, end, c) - ci.data());
+        mval[q] += A * (a == b ? 2.0 : 1.0) / 12.0;
+        ctb[q].push_back({e, A * (d[a] * d[b] + d[3 + a] * d[3 + b])});
+      }
+  }
+  std::vector<int32_t> ctb_off(nnz + 1, 0), ctb_e;
+  std::vector<double> ctb_k;
+  for (int64_t q = 0; q < nnz; ++q) {
+    ctb_off[q + 1] = ctb_off[q] + (int32_t)ctb[q].size();
+    for (auto& pr : ctb[q]) { ctb_e.push_back(pr.first); ctb_k.push_back(pr.second); }
+  }
+  // structural checks before upload: every row and contribution list is
+  // short and inside its array
+  for (int32_t u = 0; u < nr; ++u)
+    if (rp[u + 1] - rp[u] < 1 || rp[u + 1] - rp[u] > 64) return fail(PDF_EINVAL, "pdf_mesh_create: relaxation row out of range");
+  for (int64_t q = 0; q < nnz; ++q) {
+    if (ci[q] < 0 || ci[q] >= nr) return fail(PDF_EINVAL, "pdf_mesh_create: relaxation column out of range");
+    if (ctb_off[q + 1] - ctb_off[q] < 1 || ctb_off[q + 1] - ctb_off[q] > 64) return fail(PDF_EINVAL, "pdf_mesh_create: relaxation contributions out of range");
+  }
+  RelaxMesh& R = m->rx;
+  R.n_rep = nr;
+  R.nnz = nnz;
+  m->wall_d = wd;
+  m->wall_n = wn;
+  pdf_status s;
+  if ((s = upload(&R.rp, rp.data(), rp.size())) != PDF_OK || (s = upload(&R.ci, ci.data(), ci.size())) != PDF_OK ||
+      (s = upload(&R.mval, mval.data(), mval.size())) != PDF_OK ||
+      (s = upload(&R.ctb_off, ctb_off.data(), ctb_off.size())) != PDF_OK ||
+      (s = upload(&R.ctb_e, ctb_e.data(), ctb_e.size())) != PDF_OK ||
+      (s = upload(&R.ctb_k, ctb_k.data(), ctb_k.size())) != PDF_OK ||
+      (s = upload(&R.wall, wall.data(), wall.size())) != PDF_OK ||
+      (s = upload(&R.rep_node, rep_node.data(), rep_node.size())) != PDF_OK ||
+      (s = upload(&R.node_rep, node_rep.data(), node_rep.size())) != PDF_OK ||
+      (s = upload(&R.wall_n, wn.data(), wn.size())) != PDF_OK ||
+      (s = upload(&R.wall_d, wd.data(), wd.size())) != PDF_OK) {
+    free_relax(R);
+    return s;
+  }
+  return PDF_OK;
+}
+
 static void free_mesh_dev(MeshDev& d) {
-  cudaFree(d.xy); cudaFree(d.tri); cudaFree(d.geo); cudaFree(d.dN);
+  cudaFree(d.xy); cudaFree(d.tri); cudaFree(d.geo); cudaFree(d.fgeo); cudaFree(d.dN);
   cudaFree(d.nse_off); cudaFree(d.nse); cudaFree(d.esup_off); cudaFree(d.esup);
   d = MeshDev();
 }
@@ -131,6 +253,24 @@ extern "C" pdf_status pdf_mesh_create(const double* node_xy, int32_t n_nodes, co
       geo[e].nbr[k] = m->nbr[3 * e + k];
       geo[e].shift[k] = (int8_t)m->shift[3 * e + k];
     }
+  // the fixed-point copy for the FP64-free walk
+  std::vector<FxGeo> fgeo(n_tri);
+  auto bits = [](double v) { uint64_t b; std::memcpy(&b, &v, 8); return b; };
+  for (int32_t e = 0; e < n_tri; ++e) {
+    const ElemGeo& g = geo[e];
+    FxGeo& f = fgeo[e];
+    std::memset(&f, 0, sizeof(f));
+    f.xb = fx::d2fix(bits(g.xb), 56);
+    f.yb = fx::d2fix(bits(g.yb), 56);
+    f.cbx = fx::d2df(bits(g.cbx)); f.cby = fx::d2df(bits(g.cby));
+    f.abx = fx::d2df(bits(g.abx)); f.aby = fx::d2df(bits(g.aby));
+    f.two_area = fx::d2df(bits(g.two_area));
+    for (int k = 0; k < 3; ++k) { f.nbr[k] = g.nbr[k]; f.shift[k] = g.shift[k]; }
+    if (std::fabs(g.xb) >= 63.0 || std::fabs(g.yb) >= 63.0) {
+      delete m;
+      return fail(PDF_EINVAL, "pdf_mesh_create: node coordinates must lie within |x|, |y| < 63");
+    }
+  }
 
   // node -> elements, ascending element ids; merged with the periodic twin
   std::vector<int32_t> esup_off(n_nodes + 1, 0), esup(3 * (size_t)n_tri);
@@ -159,14 +299,23 @@ extern "C" pdf_status pdf_mesh_create(const double* node_xy, int32_t n_nodes, co
   d.n_tri = n_tri;
   d.period = period_x;
   pdf_status s;
+  std::vector<int32_t> bnd_wall;
+  for (int32_t i = 0; i < n_bnd; ++i)
+    if (bnd_edge[3 * i + 2] == PDF_TAG_WALL) { bnd_wall.push_back(bnd_edge[3 * i]); bnd_wall.push_back(bnd_edge[3 * i + 1]); }
   if ((s = upload(&d.xy, m->xy.data(), m->xy.size())) != PDF_OK ||
       (s = upload(&d.tri, m->tri.data(), m->tri.size())) != PDF_OK ||
       (s = upload(&d.geo, geo.data(), geo.size())) != PDF_OK ||
+      (s = upload(&d.fgeo, fgeo.data(), fgeo.size())) != PDF_OK ||
       (s = upload(&d.dN, dN.data(), dN.size())) != PDF_OK ||
       (s = upload(&d.nse_off, nse_off.data(), nse_off.size())) != PDF_OK ||
       (s = upload(&d.nse, nse.data(), nse.size())) != PDF_OK ||
       (s = upload(&d.esup_off, esup_off.data(), esup_off.size())) != PDF_OK ||
       (s = upload(&d.esup, esup.data(), esup.size())) != PDF_OK) {
+    free_mesh_dev(d);
+    delete m;
+    return s;
+  }
+  if ((s = build_relax(m, bnd_wall, dN, nse_off, nse)) != PDF_OK) {
     free_mesh_dev(d);
     delete m;
     return s;
@@ -178,6 +327,7 @@ extern "C" pdf_status pdf_mesh_create(const double* node_xy, int32_t n_nodes, co
 extern "C" pdf_status pdf_mesh_destroy(pdf_mesh* m) {
   if (!m) return PDF_OK;
   free_mesh_dev(m->d);
+  free_relax(m->rx);
   delete m;
   return PDF_OK;
 }
@@ -186,6 +336,13 @@ extern "C" pdf_status pdf_mesh_connectivity(const pdf_mesh* m, int32_t* nbr, int
   if (!m) return fail(PDF_EINVAL, "pdf_mesh_connectivity: NULL mesh");
   if (nbr) std::memcpy(nbr, m->nbr.data(), m->nbr.size() * sizeof(int32_t));
   if (shift) std::memcpy(shift, m->shift.data(), m->shift.size() * sizeof(int32_t));
+  return PDF_OK;
+}
+
+extern "C" pdf_status pdf_mesh_wall_distance(const pdf_mesh* m, double* dist, double* normal) {
+  if (!m) return fail(PDF_EINVAL, "pdf_mesh_wall_distance: NULL mesh");
+  if (dist) std::memcpy(dist, m->wall_d.data(), m->wall_d.size() * sizeof(double));
+  if (normal) std::memcpy(normal, m->wall_n.data(), m->wall_n.size() * sizeof(double));
   return PDF_OK;
 }
 

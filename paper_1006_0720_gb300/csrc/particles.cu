@@ -21,7 +21,8 @@ __global__ void k_init(const double* __restrict__ xy, const int32_t* __restrict_
                        const double* __restrict__ elem_psi0, double* __restrict__ x,
                        double* __restrict__ y, double* __restrict__ u, double* __restrict__ v,
                        double* __restrict__ w, double* __restrict__ om, double* __restrict__ ps,
-                       int32_t* __restrict__ elem) {
+                       int32_t* __restrict__ elem, float* __restrict__ uf, float* __restrict__ vf,
+                       float* __restrict__ wf, float* __restrict__ omf, float* __restrict__ psf) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     // host element: largest e with elem_off[e] <= p
@@ -60,11 +61,17 @@ __global__ void k_init(const double* __restrict__ xy, const int32_t* __restrict_
     const double umean = (u_profile == 1) ? __dsub_rn(1.0, __dmul_rn(py, py)) : 0.0;
     x[p] = px;
     y[p] = py;
-    u[p] = __dadd_rn(umean, __dmul_rn(u_sigma, (double)g[0]));
-    v[p] = __dmul_rn(u_sigma, (double)g[1]);
-    w[p] = __dmul_rn(u_sigma, (double)g[2]);
-    om[p] = __dmul_rn(-0.25, (double)lsum);   // Gamma(4, 1/4): -1/4 sum of 4 ln u
-    ps[p] = elem_psi0 ? elem_psi0[e] : 0.0;
+    const double U = __dadd_rn(umean, __dmul_rn(u_sigma, (double)g[0]));
+    const double V = __dmul_rn(u_sigma, (double)g[1]);
+    const double W = __dmul_rn(u_sigma, (double)g[2]);
+    const double O = __dmul_rn(-0.25, (double)lsum);   // Gamma(4, 1/4): -1/4 sum of 4 ln u
+    const double S = elem_psi0 ? elem_psi0[e] : 0.0;
+    if (u) {
+      u[p] = U; v[p] = V; w[p] = W; om[p] = O; ps[p] = S;
+    } else {  // FP32 state: the FP64 values rounded to nearest
+      uf[p] = __double2float_rn(U); vf[p] = __double2float_rn(V); wf[p] = __double2float_rn(W);
+      omf[p] = __double2float_rn(O); psf[p] = __double2float_rn(S);
+    }
     elem[p] = e;
   }
 }
@@ -79,14 +86,27 @@ __global__ void k_rng_gauss(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3
   }
 }
 
+__global__ void k_widen(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+__global__ void k_narrow(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = __double2float_rn(a[i]);
+}
+
 static void free_particles(pdf_particles* p) {
   if (!p) return;
+  cudaFree(p->uf); cudaFree(p->vf); cudaFree(p->wf); cudaFree(p->omf); cudaFree(p->psf); cudaFree(p->rows_f32);
   double* dbl[] = {p->x, p->y, p->u, p->v, p->w, p->om, p->ps, p->es, p->ns, p->nd, p->eg, p->nc, p->rows};
   for (double* d : dbl) cudaFree(d);
   cudaFree(p->elem);
+  cudaFree(p->rows_fx);
   cudaFree(p->keys[0]); cudaFree(p->keys[1]); cudaFree(p->vals[0]); cudaFree(p->vals[1]);
   cudaFree(p->hist); cudaFree(p->hist_part); cudaFree(p->seg);
   cudaFree(p->counters);
+  relax_free(p->rx);
   delete p;
 }
 
@@ -118,7 +138,7 @@ extern "C" pdf_status pdf_particles_init(const pdf_mesh* m, const pdf_init_param
   if (!out) return fail(PDF_EINVAL, "pdf_particles_init: out is NULL");
   *out = nullptr;
   if (!m || !ip) return fail(PDF_EINVAL, "pdf_particles_init: NULL mesh or params");
-  if (precision != PDF_FP64) return fail(PDF_EINVAL, "pdf_particles_init: only PDF_FP64 is available");
+  if (precision != PDF_FP64 && precision != PDF_FP32_STATE) return fail(PDF_EINVAL, "pdf_particles_init: unknown precision");
   const int32_t n_tri = m->d.n_tri, n_nodes = m->d.n_nodes;
   std::vector<int64_t> off(n_tri + 1, 0);
   for (int32_t e = 0; e < n_tri; ++e) {
@@ -135,14 +155,20 @@ extern "C" pdf_status pdf_particles_init(const pdf_mesh* m, const pdf_init_param
   P->n = n;
   P->precision = precision;
   P->seed = seed;
-  TRY_ALLOC(P->x, n); TRY_ALLOC(P->y, n); TRY_ALLOC(P->u, n); TRY_ALLOC(P->v, n);
-  TRY_ALLOC(P->w, n); TRY_ALLOC(P->om, n); TRY_ALLOC(P->ps, n); TRY_ALLOC(P->elem, n);
+  TRY_ALLOC(P->x, n); TRY_ALLOC(P->y, n); TRY_ALLOC(P->elem, n);
+  if (precision == PDF_FP64) {
+    TRY_ALLOC(P->u, n); TRY_ALLOC(P->v, n); TRY_ALLOC(P->w, n); TRY_ALLOC(P->om, n); TRY_ALLOC(P->ps, n);
+  } else {
+    TRY_ALLOC(P->uf, n); TRY_ALLOC(P->vf, n); TRY_ALLOC(P->wf, n); TRY_ALLOC(P->omf, n); TRY_ALLOC(P->psf, n);
+    TRY_ALLOC(P->rows_f32, (int64_t)n_tri * PDFGB_ROW);
+  }
   TRY_ALLOC(P->es, (int64_t)n_tri * PDF_NES);
   TRY_ALLOC(P->ns, (int64_t)n_nodes * PDF_NNS);
   TRY_ALLOC(P->nd, (int64_t)n_nodes * PDF_NND);
   TRY_ALLOC(P->eg, (int64_t)n_tri * 8);
   TRY_ALLOC(P->nc, (int64_t)n_nodes * PDF_NCOEF);
   TRY_ALLOC(P->rows, (int64_t)n_tri * PDFGB_ROW);
+  TRY_ALLOC(P->rows_fx, (int64_t)n_tri);
   TRY_ALLOC(P->keys[0], n); TRY_ALLOC(P->keys[1], n);
   TRY_ALLOC(P->vals[0], n); TRY_ALLOC(P->vals[1], n);
   P->n_tiles = radix_tiles(n);
@@ -166,7 +192,8 @@ extern "C" pdf_status pdf_particles_init(const pdf_mesh* m, const pdf_init_param
     prof_launch("k_init", st, nullptr, nullptr);  // counted only
     k_init<<<grid_for(n, 256), 256, 0, st>>>(m->d.xy, m->d.tri, d_off, n_tri, n, seed,
                                               ip->u_profile, ip->u_sigma, d_psi, P->x, P->y, P->u,
-                                              P->v, P->w, P->om, P->ps, P->elem);
+                                              P->v, P->w, P->om, P->ps, P->elem, P->uf, P->vf, P->wf,
+                                              P->omf, P->psf);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -199,8 +226,18 @@ extern "C" pdf_status pdf_particles_get_state(const pdf_particles* p, double* x,
   const size_t b = sizeof(double) * p->n;
   double* dst[] = {x, y, u, v, w, om, ps};
   const double* src[] = {p->x, p->y, p->u, p->v, p->w, p->om, p->ps};
-  for (int i = 0; i < 7; ++i)
-    if (dst[i]) PDF_CUDA(cudaMemcpyAsync(dst[i], src[i], b, cudaMemcpyDefault, st));
+  const float* srcf[] = {nullptr, nullptr, p->uf, p->vf, p->wf, p->omf, p->psf};
+  for (int i = 0; i < 7; ++i) {
+    if (!dst[i]) continue;
+    if (src[i]) {
+      PDF_CUDA(cudaMemcpyAsync(dst[i], src[i], b, cudaMemcpyDefault, st));
+    } else {  // FP32 state widened on the device (device destinations only)
+      cudaPointerAttributes at;
+      if (cudaPointerGetAttributes(&at, dst[i]) != cudaSuccess || at.type != cudaMemoryTypeDevice)
+        return fail(PDF_EINVAL, "pdf_particles_get_state: FP32 state needs device destinations");
+      PDF_KERNEL("k_widen", st, k_widen<<<grid_for(p->n, 256), 256, 0, st>>>(srcf[i], dst[i], p->n));
+    }
+  }
   if (elem) PDF_CUDA(cudaMemcpyAsync(elem, p->elem, sizeof(int32_t) * p->n, cudaMemcpyDefault, st));
   return PDF_OK;
 }
@@ -214,8 +251,18 @@ extern "C" pdf_status pdf_particles_set_state(pdf_particles* p, const double* x,
   cudaStream_t st = (cudaStream_t)stream;
   const size_t b = sizeof(double) * p->n;
   double* dst[] = {p->x, p->y, p->u, p->v, p->w, p->om, p->ps};
+  float* dstf[] = {nullptr, nullptr, p->uf, p->vf, p->wf, p->omf, p->psf};
   const double* src[] = {x, y, u, v, w, om, ps};
-  for (int i = 0; i < 7; ++i) PDF_CUDA(cudaMemcpyAsync(dst[i], src[i], b, cudaMemcpyDefault, st));
+  for (int i = 0; i < 7; ++i) {
+    if (dst[i]) {
+      PDF_CUDA(cudaMemcpyAsync(dst[i], src[i], b, cudaMemcpyDefault, st));
+    } else {
+      cudaPointerAttributes at;
+      if (cudaPointerGetAttributes(&at, src[i]) != cudaSuccess || at.type != cudaMemoryTypeDevice)
+        return fail(PDF_EINVAL, "pdf_particles_set_state: FP32 state needs device sources");
+      PDF_KERNEL("k_narrow", st, k_narrow<<<grid_for(p->n, 256), 256, 0, st>>>(src[i], dstf[i], p->n));
+    }
+  }
   PDF_CUDA(cudaMemcpyAsync(p->elem, elem, sizeof(int32_t) * p->n, cudaMemcpyDefault, st));
   return PDF_OK;
 }

@@ -1,0 +1,420 @@
+// Elliptic relaxation for the tensor wp_ij (eq. elliptic-relaxation-
+// Lagrangian): (M + K_L) wp = M rhs with linear triangles (sec. 3.2: P1 FEM,
+// Jacobi-preconditioned conjugate gradients, warm start), solved in FP64 for
+// the nine components at once.
+//   M_ab   = sum_e A_e (1 + delta_ab) / 12
+//   K_L,ab = sum_e L2_e A_e grad N_a . grad N_b,  L2_e = mean of nodal L^2
+//   L = C_L max(C_xi k^1.5 / eps, C_eta (nu^3 / eps)^1/4) (eq. L), with
+//   C_xi = 1 + 1.3 n_i n_i for wp_ii and 1 otherwise (eq. Cxi), n the unit
+//   outward normal of the nearest wall edge.
+// Reflecting walls are symmetry planes: off-diagonal components are held at
+// 0 on wall nodes, diagonal components take the natural condition.
+// Periodic twin nodes are one unknown.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace pdfgb {
+
+struct RelaxParams {
+  double nu, C1, C2, CT, CL, Ceta, Cv, gamma5;
+};
+
+constexpr double kRKFloor = 1e-12, kREFloor = 1e-12;
+
+// Per node: the nine right-hand sides and the three L^2 fields (C_xi of
+// wp_11, of wp_22, and 1).
+__global__ void k_relax_nodes(int32_t n_nodes, const double* __restrict__ ns, const double* __restrict__ nd,
+                              const double* __restrict__ wall_n, RelaxParams P, double* __restrict__ rhs,
+                              double* __restrict__ L2) {
+  for (int32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < n_nodes; n += gridDim.x * blockDim.x) {
+    const double* S = ns + (int64_t)n * PDF_NNS;
+    const double* D = nd + (int64_t)n * PDF_NND;
+    const double k = fmax(0.5 * (S[5] + S[6] + S[7]), kRKFloor);
+    const double om = S[3];
+    const double eps = fmax(om * (k + P.nu * P.CT * P.CT * om), kREFloor);
+    // right-hand side (eq. elliptic-relaxation-Lagrangian with eqs. H, A_v, bij)
+    const double R[3][3] = {{S[5], S[8], S[9]}, {S[8], S[6], S[10]}, {S[9], S[10], S[7]}};
+    const double g[3][3] = {{D[0], D[1], 0.0}, {D[2], D[3], 0.0}, {D[4], D[5], 0.0}};
+    const double det = R[0][0] * (R[1][1] * R[2][2] - R[1][2] * R[2][1]) -
+                       R[0][1] * (R[1][0] * R[2][2] - R[1][2] * R[2][0]) +
+                       R[0][2] * (R[1][0] * R[2][1] - R[1][1] * R[2][0]);
+    const double tk = 2.0 * k / 3.0;
+    const double Av = fmin(1.0, P.Cv * det / (tk * tk * tk));
+    double b[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) b[i][j] = R[i][j] / (2.0 * k) - (i == j ? 1.0 / 3.0 : 0.0);
+    const double g3 = P.gamma5 / 3.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double bk = 0.0, bl = 0.0;
+        for (int q = 0; q < 3; ++q) {
+          bk += b[i][q] * g[q][j];
+          bl += b[i][q] * g[j][q];
+        }
+        const double h = (P.C2 * Av + g3) * g[i][j] - g3 * g[j][i] + P.gamma5 * (bk - bl);
+        rhs[(int64_t)(3 * i + j) * n_nodes + n] = (i == j ? 0.5 * (1.0 - P.C1) * k * om : 0.0) + k * h;
+      }
+    const double nx = wall_n[2 * n], ny = wall_n[2 * n + 1];
+    const double lt = k * sqrt(k) / eps, lk = P.Ceta * sqrt(sqrt(P.nu * P.nu * P.nu / eps));
+    const double cxi[3] = {1.0 + 1.3 * nx * nx, 1.0 + 1.3 * ny * ny, 1.0};
+    for (int c = 0; c < 3; ++c) {
+      const double L = P.CL * fmax(cxi[c] * lt, lk);
+      L2[(int64_t)c * n_nodes + n] = L * L;
+    }
+  }
+}
+
+// Matrix values of the three classes for every stored entry: the constant
+// mass part plus sum over contributing elements of L2_e * (stiffness entry).
+__global__ void k_relax_assemble(int64_t nnz, const double* __restrict__ mval, const int32_t* __restrict__ ctb_off,
+                                 const int32_t* __restrict__ ctb_e, const double* __restrict__ ctb_k,
+                                 const int32_t* __restrict__ tri, int32_t n_nodes, const double* __restrict__ L2,
+                                 double* __restrict__ aval) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x) {
+    double s[3] = {mval[q], mval[q], mval[q]};
+    for (int32_t t = ctb_off[q]; t < ctb_off[q + 1]; ++t) {
+      const int32_t e = ctb_e[t];
+      const double kab = ctb_k[t];
+      const int32_t a = tri[3 * e], b = tri[3 * e + 1], c = tri[3 * e + 2];
+#pragma unroll
+      for (int cl = 0; cl < 3; ++cl) {
+        const double* L = L2 + (int64_t)cl * n_nodes;
+        s[cl] += (L[a] + L[b] + L[c]) / 3.0 * kab;
+      }
+    }
+#pragma unroll
+    for (int cl = 0; cl < 3; ++cl) aval[(int64_t)cl * nnz + q] = s[cl];
+  }
+}
+
+__device__ __forceinline__ int comp_class(int ij) { return ij == 0 ? 0 : (ij == 4 ? 1 : 2); }
+__device__ __forceinline__ bool comp_dirichlet(int ij) { return ij != 0 && ij != 4 && ij != 8; }
+
+// y = A x for component ij over the unknowns (masked rows/cols for Dirichlet).
+__device__ __forceinline__ double spmv_row(int32_t r, int ij, int32_t n_rep, int64_t nnz,
+                                           const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                           const double* __restrict__ aval, const uint8_t* __restrict__ wall,
+                                           const double* __restrict__ x) {
+  const bool dir = comp_dirichlet(ij);
+  if (dir && wall[r]) return 0.0;
+  const double* A = aval + (int64_t)comp_class(ij) * nnz;
+  const double* X = x + (int64_t)ij * n_rep;
+  double s = 0.0;
+  for (int32_t q = rp[r]; q < rp[r + 1]; ++q) {
+    const int32_t c = ci[q];
+    if (dir && wall[c]) continue;
+    s += A[q] * X[c];
+  }
+  return s;
+}
+
+constexpr int kRBlock = 256;
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[kRBlock / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  v = __shfl_sync(0xffffffffu, v, 0);  // every lane takes part in the broadcast
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < kRBlock / 32; ++i) t += sh[i];
+  __syncthreads();
+  return t;  // valid in thread 0
+}
+
+// Set-up: b = M f (masked), x = initial guess (masked), r = b - A x,
+// z = r / diag, p = z; partials of r.z, r.r and b.b.  grid (blocks, 9).
+__global__ void __launch_bounds__(kRBlock) k_cg_init(
+    int32_t n_rep, int64_t nnz, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+    const double* __restrict__ mval, const double* __restrict__ aval, const double* __restrict__ diag,
+    const uint8_t* __restrict__ wall, const int32_t* __restrict__ rep_node, int32_t n_nodes,
+    const double* __restrict__ f, const double* __restrict__ wp, double* __restrict__ x, double* __restrict__ r,
+    double* __restrict__ z, double* __restrict__ p, double* __restrict__ part) {
+  const int ij = blockIdx.y;
+  const bool dir = comp_dirichlet(ij);
+  const int32_t row = blockIdx.x * kRBlock + threadIdx.x;
+  double rz = 0.0, rr = 0.0, bb = 0.0;
+  if (row < n_rep) {
+    const int64_t o = (int64_t)ij * n_rep + row;
+    x[o] = (dir && wall[row]) ? 0.0 : wp[(int64_t)ij * n_nodes + rep_node[row]];
+  }
+  __syncthreads();
+  // x of other rows is written by other blocks: computed r below uses the
+  // initial guess read directly from wp instead of x
+  if (row < n_rep) {
+    double b = 0.0, ax = 0.0;
+    if (!(dir && wall[row])) {
+      const double* A = aval + (int64_t)comp_class(ij) * nnz;
+      for (int32_t q = rp[row]; q < rp[row + 1]; ++q) {
+        const int32_t c = ci[q];
+        b += mval[q] * f[(int64_t)ij * n_nodes + rep_node[c]];
+        if (dir && wall[c]) continue;
+        ax += A[q] * wp[(int64_t)ij * n_nodes + rep_node[c]];
+      }
+    }
+    const double res = b - ax;
+    const double zz = res / diag[(int64_t)comp_class(ij) * n_rep + row];
+    const int64_t o = (int64_t)ij * n_rep + row;
+    r[o] = res;
+    z[o] = (dir && wall[row]) ? 0.0 : zz;
+    p[o] = z[o];
+    rz = res * z[o];
+    rr = res * res;
+    bb = b * b;
+  }
+  const double s1 = block_sum(rz), s2 = block_sum(rr), s3 = block_sum(bb);
+  if (threadIdx.x == 0) {
+    const int64_t nb = gridDim.x;
+    part[(0 * 9 + ij) * nb + blockIdx.x] = s1;
+    part[(1 * 9 + ij) * nb + blockIdx.x] = s2;
+    part[(2 * 9 + ij) * nb + blockIdx.x] = s3;
+  }
+}
+
+// Sum the block partials of `nq` quantities for 9 components (fixed order).
+__global__ void k_cg_reduce(const double* __restrict__ part, int32_t nb, int32_t nq, double* __restrict__ out) {
+  const int q = blockIdx.x;  // quantity * 9 + component
+  double s = 0.0;
+  for (int32_t i = threadIdx.x; i < nb; i += kRBlock) s += part[(int64_t)q * nb + i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) out[q] = s;
+}
+
+// q = A p and partials of p.q.
+__global__ void __launch_bounds__(kRBlock) k_cg_spmv(int32_t n_rep, int64_t nnz, const int32_t* __restrict__ rp,
+                                                      const int32_t* __restrict__ ci, const double* __restrict__ aval,
+                                                      const uint8_t* __restrict__ wall, const double* __restrict__ p,
+                                                      double* __restrict__ q, double* __restrict__ part,
+                                                      const int32_t* __restrict__ active) {
+  const int ij = blockIdx.y;
+  const int32_t row = blockIdx.x * kRBlock + threadIdx.x;
+  double pq = 0.0;
+  if (active[ij] && row < n_rep) {
+    const double v = spmv_row(row, ij, n_rep, nnz, rp, ci, aval, wall, p);
+    q[(int64_t)ij * n_rep + row] = v;
+    pq = v * p[(int64_t)ij * n_rep + row];
+  }
+  const double s = block_sum(pq);
+  if (threadIdx.x == 0) part[(int64_t)ij * gridDim.x + blockIdx.x] = s;
+}
+
+// alpha = rz / pq; x += alpha p; r -= alpha q; z = r / diag; partials of r.z, r.r.
+__global__ void __launch_bounds__(kRBlock) k_cg_update(int32_t n_rep, const double* __restrict__ diag,
+                                                        const uint8_t* __restrict__ wall,
+                                                        const double* __restrict__ scal, double* __restrict__ x,
+                                                        double* __restrict__ r, double* __restrict__ z,
+                                                        const double* __restrict__ p, const double* __restrict__ q,
+                                                        double* __restrict__ part, const int32_t* __restrict__ active) {
+  const int ij = blockIdx.y;
+  const int32_t row = blockIdx.x * kRBlock + threadIdx.x;
+  double rz = 0.0, rr = 0.0;
+  if (active[ij] && row < n_rep) {
+    const double pq = scal[ij];        // p.q
+    const double rzo = scal[9 + ij];   // previous r.z
+    const double alpha = pq != 0.0 ? rzo / pq : 0.0;
+    const int64_t o = (int64_t)ij * n_rep + row;
+    x[o] += alpha * p[o];
+    const double res = r[o] - alpha * q[o];
+    r[o] = res;
+    const bool fixed = comp_dirichlet(ij) && wall[row];
+    const double zz = fixed ? 0.0 : res / diag[(int64_t)comp_class(ij) * n_rep + row];
+    z[o] = zz;
+    rz = res * zz;
+    rr = res * res;
+  }
+  const double s1 = block_sum(rz), s2 = block_sum(rr);
+  if (threadIdx.x == 0) {
+    part[(int64_t)(0 * 9 + ij) * gridDim.x + blockIdx.x] = s1;
+    part[(int64_t)(1 * 9 + ij) * gridDim.x + blockIdx.x] = s2;
+  }
+}
+
+// p = z + beta p, beta = rz_new / rz_old.
+__global__ void k_cg_dir(int32_t n_rep, const double* __restrict__ beta, const double* __restrict__ z,
+                         double* __restrict__ p, const int32_t* __restrict__ active) {
+  const int ij = blockIdx.y;
+  const int32_t row = blockIdx.x * kRBlock + threadIdx.x;
+  if (!active[ij] || row >= n_rep) return;
+  const int64_t o = (int64_t)ij * n_rep + row;
+  p[o] = z[o] + beta[ij] * p[o];
+}
+
+__global__ void k_cg_diag(int32_t n_rep, int64_t nnz, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const double* __restrict__ aval, double* __restrict__ diag) {
+  const int cl = blockIdx.y;
+  for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n_rep; r += gridDim.x * blockDim.x) {
+    double d = 1.0;
+    for (int32_t q = rp[r]; q < rp[r + 1]; ++q)
+      if (ci[q] == r) d = aval[(int64_t)cl * nnz + q];
+    diag[(int64_t)cl * n_rep + r] = d;
+  }
+}
+
+// Solution back to all nodes (twins get their representative's value).
+__global__ void k_cg_scatter(int32_t n_nodes, const int32_t* __restrict__ node_rep, int32_t n_rep,
+                             const double* __restrict__ x, double* __restrict__ wp) {
+  const int ij = blockIdx.y;
+  for (int32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < n_nodes; n += gridDim.x * blockDim.x)
+    wp[(int64_t)ij * n_nodes + n] = x[(int64_t)ij * n_rep + node_rep[n]];
+}
+
+}  // namespace pdfgb
+
+// ----------------------------------------------------------------------------
+// Host side.
+// ----------------------------------------------------------------------------
+namespace pdfgb {
+
+static pdf_status relax_alloc(pdf_particles* P) {
+  if (P->rx.x) return PDF_OK;
+  const RelaxMesh& R = P->mesh->rx;
+  const int32_t nn = P->mesh->d.n_nodes;
+  const int32_t nb = (R.n_rep + kRBlock - 1) / kRBlock;
+  RelaxWork& W = P->rx;
+  W.nb = nb;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+  A((void**)&W.f, sizeof(double) * 9 * nn);
+  A((void**)&W.L2, sizeof(double) * 3 * nn);
+  A((void**)&W.aval, sizeof(double) * 3 * R.nnz);
+  A((void**)&W.diag, sizeof(double) * 3 * R.n_rep);
+  A((void**)&W.x, sizeof(double) * 9 * R.n_rep);
+  A((void**)&W.r, sizeof(double) * 9 * R.n_rep);
+  A((void**)&W.z, sizeof(double) * 9 * R.n_rep);
+  A((void**)&W.p, sizeof(double) * 9 * R.n_rep);
+  A((void**)&W.q, sizeof(double) * 9 * R.n_rep);
+  A((void**)&W.part, sizeof(double) * 3 * 9 * nb);
+  A((void**)&W.scal, sizeof(double) * 64);  // [0,9) p.q  [9,18) r.z  [18,36) r.z, r.r  (and the 27 set-up sums)
+  A((void**)&W.beta, sizeof(double) * 9);
+  A((void**)&W.active, sizeof(int32_t) * 9);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&W.host, sizeof(double) * 64);
+  if (e != cudaSuccess) return cuda_fail(e, "pdf_relax_solve: allocation");
+  return PDF_OK;
+}
+
+void relax_free(RelaxWork& W) {
+  cudaFree(W.f); cudaFree(W.L2); cudaFree(W.aval); cudaFree(W.diag); cudaFree(W.x); cudaFree(W.r);
+  cudaFree(W.z); cudaFree(W.p); cudaFree(W.q); cudaFree(W.part); cudaFree(W.scal); cudaFree(W.beta);
+  cudaFree(W.active);
+  if (W.host) cudaFreeHost(W.host);
+  W = RelaxWork();
+}
+
+static RelaxParams relax_params(const pdf_model_params* p) {
+  RelaxParams r;
+  r.nu = p->nu; r.C1 = p->C1; r.C2 = p->C2; r.CT = p->CT; r.CL = p->CL; r.Ceta = p->Ceta;
+  r.Cv = p->Cv; r.gamma5 = p->gamma5;
+  return r;
+}
+
+static int rblocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096)); }
+
+static pdf_status relax_prepare(pdf_particles* P, const pdf_model_params* params, cudaStream_t st) {
+  const pdf_mesh* m = P->mesh;
+  const RelaxMesh& R = m->rx;
+  RelaxWork& W = P->rx;
+  const int32_t nn = m->d.n_nodes;
+  PDF_KERNEL("k_relax_nodes", st, k_relax_nodes<<<rblocks(nn), 256, 0, st>>>(nn, P->ns, P->nd, R.wall_n, relax_params(params), W.f, W.L2));
+  PDF_KERNEL("k_relax_assemble", st, k_relax_assemble<<<rblocks(R.nnz), 256, 0, st>>>(R.nnz, R.mval, R.ctb_off, R.ctb_e, R.ctb_k,
+                                                                                      m->d.tri, nn, W.L2, W.aval));
+  PDF_KERNEL("k_cg_diag", st, k_cg_diag<<<dim3(rblocks(R.n_rep), 3), 256, 0, st>>>(R.n_rep, R.nnz, R.rp, R.ci, W.aval, W.diag));
+  return PDF_OK;
+}
+
+}  // namespace pdfgb
+
+using namespace pdfgb;
+
+extern "C" pdf_status pdf_relax_rhs(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,
+                                    double* rhs, double* L2, void* stream) {
+  if (!p || !m || p->mesh != m || !params) return fail(PDF_EINVAL, "pdf_relax_rhs: bad arguments");
+  if (!p->have_stats) return fail(PDF_ESTATE, "pdf_relax_rhs: call pdf_estimate_stats first");
+  cudaStream_t st = (cudaStream_t)stream;
+  pdf_status s = relax_alloc(p);
+  if (s != PDF_OK) return s;
+  s = relax_prepare(p, params, st);
+  if (s != PDF_OK) return s;
+  const int32_t nn = m->d.n_nodes;
+  if (rhs) PDF_CUDA(cudaMemcpyAsync(rhs, p->rx.f, sizeof(double) * 9 * nn, cudaMemcpyDefault, st));
+  if (L2) PDF_CUDA(cudaMemcpyAsync(L2, p->rx.L2, sizeof(double) * 3 * nn, cudaMemcpyDefault, st));
+  return PDF_OK;
+}
+
+extern "C" pdf_status pdf_relax_solve(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,
+                                      double* wp, double rtol, int32_t max_it, int32_t* iters, double* rel_res,
+                                      void* stream) {
+  if (!p || !m || p->mesh != m || !params || !wp) return fail(PDF_EINVAL, "pdf_relax_solve: bad arguments");
+  if (!(rtol > 0.0) || max_it < 0) return fail(PDF_EINVAL, "pdf_relax_solve: rtol must be > 0 and max_it >= 0");
+  if (!p->have_stats) return fail(PDF_ESTATE, "pdf_relax_solve: call pdf_estimate_stats first");
+  cudaStream_t st = (cudaStream_t)stream;
+  pdf_status s = relax_alloc(p);
+  if (s != PDF_OK) return s;
+  s = relax_prepare(p, params, st);
+  if (s != PDF_OK) return s;
+  const RelaxMesh& R = m->rx;
+  RelaxWork& W = p->rx;
+  const int32_t nn = m->d.n_nodes, nb = W.nb;
+  const dim3 grid(nb, 9);
+  PDF_KERNEL("k_cg_init", st, k_cg_init<<<grid, kRBlock, 0, st>>>(R.n_rep, R.nnz, R.rp, R.ci, R.mval, W.aval, W.diag,
+                                                                   R.wall, R.rep_node, nn, W.f, wp, W.x, W.r, W.z,
+                                                                   W.p, W.part));
+  PDF_KERNEL("k_cg_reduce", st, k_cg_reduce<<<27, kRBlock, 0, st>>>(W.part, nb, 3, W.scal));
+  PDF_CUDA(cudaMemcpyAsync(W.host, W.scal, sizeof(double) * 27, cudaMemcpyDeviceToHost, st));
+  PDF_CUDA(cudaStreamSynchronize(st));
+  double rz[9], bn[9], rn[9];
+  int32_t act[9], it_done[9];
+  int n_active = 0;
+  for (int c = 0; c < 9; ++c) {
+    rz[c] = W.host[c];
+    rn[c] = std::sqrt(W.host[9 + c]);
+    bn[c] = std::sqrt(W.host[18 + c]);
+    act[c] = (rn[c] > rtol * bn[c] && bn[c] > 0.0) ? 1 : 0;
+    it_done[c] = 0;
+    n_active += act[c];
+  }
+  double scal_host[18];
+  int it = 0;
+  while (n_active > 0 && it < max_it) {
+    for (int c = 0; c < 9; ++c) scal_host[9 + c] = rz[c];
+    PDF_CUDA(cudaMemcpyAsync(W.active, act, sizeof(act), cudaMemcpyHostToDevice, st));
+    PDF_CUDA(cudaMemcpyAsync(W.scal + 9, scal_host + 9, sizeof(double) * 9, cudaMemcpyHostToDevice, st));
+    PDF_KERNEL("k_cg_spmv", st, k_cg_spmv<<<grid, kRBlock, 0, st>>>(R.n_rep, R.nnz, R.rp, R.ci, W.aval, R.wall, W.p, W.q,
+                                                                     W.part, W.active));
+    PDF_KERNEL("k_cg_reduce", st, k_cg_reduce<<<9, kRBlock, 0, st>>>(W.part, nb, 1, W.scal));
+    PDF_KERNEL("k_cg_update", st, k_cg_update<<<grid, kRBlock, 0, st>>>(R.n_rep, W.diag, R.wall, W.scal, W.x, W.r, W.z,
+                                                                         W.p, W.q, W.part, W.active));
+    PDF_KERNEL("k_cg_reduce", st, k_cg_reduce<<<18, kRBlock, 0, st>>>(W.part, nb, 2, W.scal + 18));
+    PDF_CUDA(cudaMemcpyAsync(W.host, W.scal + 18, sizeof(double) * 18, cudaMemcpyDeviceToHost, st));
+    PDF_CUDA(cudaStreamSynchronize(st));
+    ++it;
+    double beta[9];
+    for (int c = 0; c < 9; ++c) {
+      beta[c] = 0.0;
+      if (!act[c]) continue;
+      const double rzn = W.host[c];
+      rn[c] = std::sqrt(W.host[9 + c]);
+      beta[c] = rz[c] != 0.0 ? rzn / rz[c] : 0.0;
+      rz[c] = rzn;
+      it_done[c] = it;
+      if (rn[c] <= rtol * bn[c]) { act[c] = 0; --n_active; }
+    }
+    if (n_active == 0) break;
+    PDF_CUDA(cudaMemcpyAsync(W.beta, beta, sizeof(beta), cudaMemcpyHostToDevice, st));
+    PDF_CUDA(cudaMemcpyAsync(W.active, act, sizeof(act), cudaMemcpyHostToDevice, st));
+    PDF_KERNEL("k_cg_dir", st, k_cg_dir<<<grid, kRBlock, 0, st>>>(R.n_rep, W.beta, W.z, W.p, W.active));
+  }
+  PDF_KERNEL("k_cg_scatter", st, k_cg_scatter<<<dim3(rblocks(nn), 9), 256, 0, st>>>(nn, R.node_rep, R.n_rep, W.x, wp));
+  for (int c = 0; c < 9; ++c) {
+    if (iters) iters[c] = it_done[c];
+    if (rel_res) rel_res[c] = bn[c] > 0.0 ? rn[c] / bn[c] : 0.0;
+  }
+  if (n_active > 0) return fail(PDF_ENOTCONV, "pdf_relax_solve: iteration cap reached");
+  return PDF_OK;
+}

@@ -9,6 +9,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "fx.cuh"
 
 namespace pdfgb {
 
@@ -176,11 +177,124 @@ __global__ void k_seg_offsets(const int32_t* __restrict__ keys, int64_t n, int32
 // One warp per element: first pass means, second pass central moments
 // (sec. 3.3, 1/N).  Lane j adds sorted positions j, j+32, ...; the lane
 // partials are combined by a fixed butterfly and lane 0's result is used.
-__global__ void __launch_bounds__(256) k_elem_stats(const int32_t* __restrict__ seg,
-                                                    const int32_t* __restrict__ pid, int32_t n_tri,
-                                                    const double* __restrict__ u, const double* __restrict__ v,
-                                                    const double* __restrict__ w, const double* __restrict__ om,
-                                                    const double* __restrict__ ps, double* __restrict__ es) {
+template <typename T>
+__device__ void elem_stats_fp64(int32_t beg, int32_t end, int lane, const int32_t* __restrict__ pid,
+                                const T* __restrict__ u, const T* __restrict__ v,
+                                const T* __restrict__ w, const T* __restrict__ om,
+                                const T* __restrict__ ps, double* __restrict__ out) {
+  const int32_t N = end - beg;
+  double s[5] = {0, 0, 0, 0, 0};
+  for (int32_t i = beg + lane; i < end; i += 32) {
+    const int32_t p = pid[i];
+    s[0] += (double)u[p]; s[1] += (double)v[p]; s[2] += (double)w[p]; s[3] += (double)om[p]; s[4] += (double)ps[p];
+  }
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+    s[q] = __shfl_sync(0xffffffffu, s[q], 0) / (double)N;
+  }
+  double c[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int32_t i = beg + lane; i < end; i += 32) {
+    const int32_t p = pid[i];
+    const double du = (double)u[p] - s[0], dv = (double)v[p] - s[1], dw = (double)w[p] - s[2],
+                 dp = (double)ps[p] - s[4];
+    c[0] += du * du; c[1] += dv * dv; c[2] += dw * dw;
+    c[3] += du * dv; c[4] += du * dw; c[5] += dv * dw; c[6] += dp * dp;
+  }
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c[q] += __shfl_xor_sync(0xffffffffu, c[q], o);
+    c[q] = __shfl_sync(0xffffffffu, c[q], 0) / (double)N;
+  }
+  if (lane == 0) {
+    out[0] = (double)N;
+    for (int q = 0; q < 5; ++q) out[1 + q] = s[q];
+    for (int q = 0; q < 7; ++q) out[6 + q] = c[q];
+  }
+}
+
+// Element statistics without FP64 arithmetic per particle (the default):
+// the same two passes as above, but every particle value is decoded into
+// fixed point with 48 fraction bits and the sums are 128-bit integers, so
+// they are exact and independent of the order of the particles.
+//   pass 1: S_i = sum q_i (q = value 2^48)          -> means S_i / N
+//   pass 2: D_i = q_i - M_i with M_i ~ the mean,   -> central moments
+//           (sum D_i D_j - sum D_i sum D_j / N) / N
+// Only the per-element finishing (a few divisions) runs in FP64.  An element
+// with |value| >= 128 (omega >= 2^14) or more than 2^17 particles falls back
+// to the FP64 kernel's arithmetic (exact sums need those bounds).
+constexpr int kFQ = 48;
+
+// Signed 64 x 64 -> 128-bit product from 32 x 32 -> 64-bit pieces (the
+// native 64-bit multiply-high runs on GB300's slow FP64 unit).
+__device__ __forceinline__ void mul_s64(long long a, long long b, unsigned long long& lo, long long& hi) {
+  const bool neg = (a < 0) != (b < 0);
+  const unsigned long long ua = a < 0 ? 0ull - (unsigned long long)a : (unsigned long long)a;
+  const unsigned long long ub = b < 0 ? 0ull - (unsigned long long)b : (unsigned long long)b;
+  const unsigned int a0 = (unsigned int)ua, a1 = (unsigned int)(ua >> 32);
+  const unsigned int b0 = (unsigned int)ub, b1 = (unsigned int)(ub >> 32);
+  const unsigned long long p00 = (unsigned long long)a0 * b0;
+  const unsigned long long p01 = (unsigned long long)a0 * b1;
+  const unsigned long long p10 = (unsigned long long)a1 * b0;
+  const unsigned long long p11 = (unsigned long long)a1 * b1;
+  const unsigned long long mid = (p00 >> 32) + (unsigned int)p01 + (unsigned int)p10;
+  unsigned long long l = (mid << 32) | (unsigned int)p00;
+  unsigned long long h = p11 + (p01 >> 32) + (p10 >> 32) + (mid >> 32);
+  if (neg) {  // two's complement of the 128-bit magnitude
+    l = ~l + 1ull;
+    h = ~h + (l == 0ull ? 1ull : 0ull);
+  }
+  lo = l;
+  hi = (long long)h;
+}
+
+__device__ __forceinline__ void mac128(unsigned long long& lo, long long& hi, long long a, long long b) {
+  unsigned long long pl;
+  long long ph;
+  mul_s64(a, b, pl, ph);
+  const unsigned long long nl = lo + pl;
+  hi = hi + ph + (nl < lo ? 1 : 0);
+  lo = nl;
+}
+
+__device__ __forceinline__ void add64(unsigned long long& lo, long long& hi, long long v) {
+  const unsigned long long nl = lo + (unsigned long long)v;
+  hi = hi + (v < 0 ? -1 : 0) + (nl < lo ? 1 : 0);
+  lo = nl;
+}
+
+__device__ __forceinline__ void warp_sum128(unsigned long long& lo, long long& hi) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long ol = __shfl_xor_sync(0xffffffffu, lo, o);
+    const long long oh = __shfl_xor_sync(0xffffffffu, hi, o);
+    const unsigned long long nl = lo + ol;
+    hi = hi + oh + (nl < lo ? 1 : 0);
+    lo = nl;
+  }
+}
+
+
+// Value -> fixed point with kFQ fraction bits; `ok` cleared outside |v| < 2^lim.
+__device__ __forceinline__ long long to_fix(const double* a, int64_t i, int lim, bool& ok) {
+  const uint64_t b = (uint64_t)__ldg(reinterpret_cast<const long long*>(a) + i);
+  ok = ok && fx::d_exp(b) <= 1023 + lim;
+  return fx::d2fix(b, kFQ);
+}
+__device__ __forceinline__ long long to_fix(const float* a, int64_t i, int lim, bool& ok) {
+  const float f = __ldg(a + i);
+  ok = ok && (int)((fx::f_bits(f) >> 23) & 0xFF) <= 127 + lim;
+  return fx::f2fix(f, kFQ);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_elem_stats_fx(const int32_t* __restrict__ seg,
+                                                       const int32_t* __restrict__ pid, int32_t n_tri,
+                                                       const T* __restrict__ u, const T* __restrict__ v,
+                                                       const T* __restrict__ w, const T* __restrict__ om,
+                                                       const T* __restrict__ ps, double* __restrict__ es) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -192,35 +306,82 @@ __global__ void __launch_bounds__(256) k_elem_stats(const int32_t* __restrict__ 
       if (lane < PDF_NES) out[lane] = 0.0;
       continue;
     }
-    double s[5] = {0, 0, 0, 0, 0};
+    // pass 1: exact sums of the fixed-point values
+    unsigned long long lo[5] = {0, 0, 0, 0, 0};
+    long long hi[5] = {0, 0, 0, 0, 0};
+    bool ok = N <= (1 << 17);
     for (int32_t i = beg + lane; i < end; i += 32) {
       const int32_t p = pid[i];
-      s[0] += u[p]; s[1] += v[p]; s[2] += w[p]; s[3] += om[p]; s[4] += ps[p];
+      add64(lo[0], hi[0], to_fix(u, p, 6, ok));
+      add64(lo[1], hi[1], to_fix(v, p, 6, ok));
+      add64(lo[2], hi[2], to_fix(w, p, 6, ok));
+      add64(lo[3], hi[3], to_fix(om, p, 13, ok));
+      add64(lo[4], hi[4], to_fix(ps, p, 6, ok));
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok) {
+      elem_stats_fp64(beg, end, lane, pid, u, v, w, om, ps, out);
+      continue;
     }
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
+    for (int q = 0; q < 5; ++q) warp_sum128(lo[q], hi[q]);
+    // all lanes hold identical exact sums; lane q < 5 forms mean q, lane q
+    // of the moments below forms output q: the finishing runs in
+    // double-float FP32 and integer operations, never in FP64
+    const fx::df invN = fx::recip_df(N);
+    fx::df mine = fx::df{0.f, 0.f};
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
-      s[q] = __shfl_sync(0xffffffffu, s[q], 0) / (double)N;
+    for (int q = 0; q < 5; ++q)
+      if (lane == q) mine = fx::df_norm(fx::mul(fx::i128_to_df(lo[q], hi[q], -kFQ), invN));
+    long long M[4];
+    const int idx[4] = {0, 1, 2, 4};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float mh = __shfl_sync(0xffffffffu, mine.h, idx[k]);
+      const float ml = __shfl_sync(0xffffffffu, mine.l, idx[k]);
+      M[k] = fx::f2fix(mh, kFQ) + fx::f2fix(ml, kFQ);
     }
-    double c[7] = {0, 0, 0, 0, 0, 0, 0};
+    // pass 2: deviations from M, exact products and sums
+    unsigned long long clo[7] = {0, 0, 0, 0, 0, 0, 0}, dlo[4] = {0, 0, 0, 0};
+    long long chi[7] = {0, 0, 0, 0, 0, 0, 0}, dhi[4] = {0, 0, 0, 0};
     for (int32_t i = beg + lane; i < end; i += 32) {
       const int32_t p = pid[i];
-      const double du = u[p] - s[0], dv = v[p] - s[1], dw = w[p] - s[2], dp = ps[p] - s[4];
-      c[0] += du * du; c[1] += dv * dv; c[2] += dw * dw;
-      c[3] += du * dv; c[4] += du * dw; c[5] += dv * dw; c[6] += dp * dp;
+      bool dummy = true;
+      const long long D[4] = {to_fix(u, p, 6, dummy) - M[0], to_fix(v, p, 6, dummy) - M[1],
+                              to_fix(w, p, 6, dummy) - M[2], to_fix(ps, p, 6, dummy) - M[3]};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) add64(dlo[k], dhi[k], D[k]);
+      mac128(clo[0], chi[0], D[0], D[0]);
+      mac128(clo[1], chi[1], D[1], D[1]);
+      mac128(clo[2], chi[2], D[2], D[2]);
+      mac128(clo[3], chi[3], D[0], D[1]);
+      mac128(clo[4], chi[4], D[0], D[2]);
+      mac128(clo[5], chi[5], D[1], D[2]);
+      mac128(clo[6], chi[6], D[3], D[3]);
     }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) warp_sum128(dlo[k], dhi[k]);
+#pragma unroll
+    for (int q = 0; q < 7; ++q) warp_sum128(clo[q], chi[q]);
+    // output lane: 0 -> N, 1..5 -> means, 6..12 -> central moments
+    // (sum D_a D_b - sum D_a sum D_b / N) / N, scaled by 2^-96
+    const int pa[7] = {0, 1, 2, 0, 0, 1, 3}, pb[7] = {0, 1, 2, 1, 2, 2, 3};
+    fx::df val = fx::df{0.f, 0.f};
+    const fx::df mean_here_h = fx::df{__shfl_sync(0xffffffffu, mine.h, (lane + 31) & 31),
+                                      __shfl_sync(0xffffffffu, mine.l, (lane + 31) & 31)};
+    if (lane >= 1 && lane <= 5) val = mean_here_h;
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) c[q] += __shfl_xor_sync(0xffffffffu, c[q], o);
-      c[q] = __shfl_sync(0xffffffffu, c[q], 0) / (double)N;
+      if (lane == 6 + q) {
+        const fx::df s2 = fx::i128_to_df(clo[q], chi[q], -2 * kFQ);
+        const fx::df da = fx::i128_to_df(dlo[pa[q]], dhi[pa[q]], -kFQ);
+        const fx::df db = fx::i128_to_df(dlo[pb[q]], dhi[pb[q]], -kFQ);
+        const fx::df corr = fx::df_norm(fx::mul(fx::df_norm(fx::mul(da, db)), invN));
+        val = fx::df_norm(fx::mul(fx::sub(s2, corr), invN));
+      }
     }
-    if (lane == 0) {
-      out[0] = (double)N;
-      for (int q = 0; q < 5; ++q) out[1 + q] = s[q];
-      for (int q = 0; q < 7; ++q) out[6 + q] = c[q];
-    }
+    if (lane == 0) out[0] = (double)N;
+    else if (lane < PDF_NES) out[lane] = __longlong_as_double((long long)fx::df2d(val));
   }
 }
 
@@ -372,8 +533,12 @@ pdf_status estimate_stats(pdf_particles* P, cudaStream_t st) {
   const MeshDev& M = P->mesh->d;
   pdf_status s = group_by_element(P, st);
   if (s != PDF_OK) return s;
-  PDF_KERNEL("k_elem_stats", st, k_elem_stats<<<blocks_for((int64_t)M.n_tri * 32, 256), 256, 0, st>>>(
-      P->seg, P->sorted_pid, M.n_tri, P->u, P->v, P->w, P->om, P->ps, P->es););
+  if (P->precision == PDF_FP64)
+    PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<double><<<blocks_for((int64_t)M.n_tri * 32, 256), 256, 0, st>>>(
+        P->seg, P->sorted_pid, M.n_tri, P->u, P->v, P->w, P->om, P->ps, P->es));
+  else
+    PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<float><<<blocks_for((int64_t)M.n_tri * 32, 256), 256, 0, st>>>(
+        P->seg, P->sorted_pid, M.n_tri, P->uf, P->vf, P->wf, P->omf, P->psf, P->es));
   PDF_KERNEL("k_node_stats", st, k_node_stats<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(M.nse_off, M.nse, M.n_nodes, P->es, P->ns,
                                                           P->counters + 8););
   PDF_KERNEL("k_elem_grad1", st, k_elem_grad1<<<blocks_for(M.n_tri, 128), 128, 0, st>>>(M.tri, M.dN, M.n_tri, P->ns, P->eg););
@@ -438,8 +603,12 @@ pdf_status estimate_stats_with_buffers(pdf_particles* P, int32_t* keys_a, int32_
     vin = vout[pass];
   }
   PDF_KERNEL("k_seg_offsets", st, k_seg_offsets<<<blocks_for(n + 1, 256), 256, 0, st>>>(kin, n, M.n_tri, seg));
-  PDF_KERNEL("k_elem_stats", st, k_elem_stats<<<blocks_for((int64_t)M.n_tri * 32, 256), 256, 0, st>>>(
-                                     seg, vin, M.n_tri, P->u, P->v, P->w, P->om, P->ps, P->es));
+  if (P->precision == PDF_FP64)
+    PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<double><<<blocks_for((int64_t)M.n_tri * 32, 256), 256, 0, st>>>(
+                                       seg, vin, M.n_tri, P->u, P->v, P->w, P->om, P->ps, P->es));
+  else
+    PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<float><<<blocks_for((int64_t)M.n_tri * 32, 256), 256, 0, st>>>(
+                                       seg, vin, M.n_tri, P->uf, P->vf, P->wf, P->omf, P->psf, P->es));
   PDF_KERNEL("k_node_stats", st, k_node_stats<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(
                                      M.nse_off, M.nse, M.n_nodes, P->es, P->ns, P->counters + 8));
   PDF_KERNEL("k_elem_grad1", st, k_elem_grad1<<<blocks_for(M.n_tri, 128), 128, 0, st>>>(M.tri, M.dN, M.n_tri, P->ns, P->eg));

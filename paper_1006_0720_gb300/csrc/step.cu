@@ -4,22 +4,24 @@
 // updates, boundary conditions, neighbour walk).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "common.cuh"
+#include "fx.cuh"
 #include "rng.cuh"
 
 namespace pdfgb {
 
 struct CoeffParams {
   double dt, nu, Pi, c_phi;
-  int closure, tm_mode, pressure;
+  int closure, tm_mode, pressure, arith;
   double C1, C2, C3, C4, CT, Cv, gamma5, Comega1, Comega2, C0_slm;
 };
 
 static CoeffParams coeff_params(const pdf_model_params* p) {
   CoeffParams c;
   c.dt = p->dt; c.nu = p->nu; c.Pi = p->Pi; c.c_phi = p->c_phi;
-  c.closure = p->closure; c.tm_mode = p->tm_mode; c.pressure = p->pressure;
+  c.closure = p->closure; c.tm_mode = p->tm_mode; c.pressure = p->pressure; c.arith = p->arith;
   c.C1 = p->C1; c.C2 = p->C2; c.C3 = p->C3; c.C4 = p->C4; c.CT = p->CT; c.Cv = p->Cv;
   c.gamma5 = p->gamma5; c.Comega1 = p->Comega1; c.Comega2 = p->Comega2; c.C0_slm = p->C0_slm;
   return c;
@@ -132,8 +134,30 @@ __device__ __forceinline__ void scale_row(const double a[PDF_NCOEF], const Coeff
   r[28] = r[29] = r[30] = r[31] = 0.0;
 }
 
+// The fixed-point kernel's row from the scaled FP64 row.  A mean outside
+// |value| < 32 marks the element for the FP64 path.
+__device__ __forceinline__ void make_fx_row(const double* r, FxRow* out) {
+  FxRow f;
+  bool ok = true;
+  const int mi[4] = {0, 1, 2, 26};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint64_t b = (uint64_t)__double_as_longlong(r[mi[j]]);
+    ok = ok && fx::d_exp(b) <= 1023 + 4;
+    f.mean[j] = fx::d2fix(b, 56);
+  }
+  const int ci[23] = {3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 23, 24, 25, 27};
+#pragma unroll
+  for (int q = 0; q < 23; ++q) f.c[q] = fx::d2df((uint64_t)__double_as_longlong(r[ci[q]]));
+#pragma unroll
+  for (int q = 23; q < 28; ++q) f.c[q] = fx::df{0.f, 0.f};
+  if (!ok) f.c[27].h = 1.0f;
+  *out = f;
+}
+
 __global__ void k_elem_rows(const int32_t* __restrict__ tri, int32_t n_tri, const double* __restrict__ nc,
-                            CoeffParams P, double* __restrict__ rows, double* __restrict__ avg_out) {
+                            CoeffParams P, double* __restrict__ rows, double* __restrict__ avg_out,
+                            FxRow* __restrict__ rows_fx, float* __restrict__ rows_f32) {
   for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n_tri; e += gridDim.x * blockDim.x) {
     const double* c0 = nc + (int64_t)tri[3 * e] * PDF_NCOEF;
     const double* c1 = nc + (int64_t)tri[3 * e + 1] * PDF_NCOEF;
@@ -142,16 +166,29 @@ __global__ void k_elem_rows(const int32_t* __restrict__ tri, int32_t n_tri, cons
     for (int q = 0; q < PDF_NCOEF; ++q) a[q] = (c0[q] + c1[q] + c2[q]) / 3.0;
     if (avg_out)
       for (int q = 0; q < PDF_NCOEF; ++q) avg_out[(int64_t)e * PDF_NCOEF + q] = a[q];
-    if (rows) scale_row(a, P, rows + (int64_t)e * PDFGB_ROW);
+    if (rows || rows_fx || rows_f32) {
+      double r[PDFGB_ROW];
+      scale_row(a, P, r);
+      if (rows)
+        for (int q = 0; q < PDFGB_ROW; ++q) rows[(int64_t)e * PDFGB_ROW + q] = r[q];
+      if (rows_fx) make_fx_row(r, rows_fx + e);
+      if (rows_f32)
+        for (int q = 0; q < PDFGB_ROW; ++q) rows_f32[(int64_t)e * PDFGB_ROW + q] = __double2float_rn(r[q]);
+    }
   }
 }
 
 __global__ void k_frozen_rows(int32_t n_tri, const double* __restrict__ coeff, CoeffParams P,
-                              double* __restrict__ rows) {
+                              double* __restrict__ rows, FxRow* __restrict__ rows_fx, float* __restrict__ rows_f32) {
   for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n_tri; e += gridDim.x * blockDim.x) {
     double a[PDF_NCOEF];
     for (int q = 0; q < PDF_NCOEF; ++q) a[q] = coeff[(int64_t)e * PDF_NCOEF + q];
-    scale_row(a, P, rows + (int64_t)e * PDFGB_ROW);
+    double r[PDFGB_ROW];
+    scale_row(a, P, r);
+    for (int q = 0; q < PDFGB_ROW; ++q) rows[(int64_t)e * PDFGB_ROW + q] = r[q];
+    if (rows_fx) make_fx_row(r, rows_fx + e);
+    if (rows_f32)
+      for (int q = 0; q < PDFGB_ROW; ++q) rows_f32[(int64_t)e * PDFGB_ROW + q] = __double2float_rn(r[q]);
   }
 }
 
@@ -301,53 +338,378 @@ __device__ __forceinline__ void add_counter(long long* c, int v) {
   if ((threadIdx.x & 31) == 0 && s != 0) atomicAdd(reinterpret_cast<unsigned long long*>(c), (unsigned long long)(long long)s);
 }
 
+struct Counts {
+  int walk = 0, refl = 0, per = 0, fb = 0, brute = 0, lost = 0, om = 0, near = 0;
+};
+
+struct Draws {
+  float g[8];
+};
+
+__device__ __forceinline__ Draws draw_step(const StepArgs& A, int64_t p) {
+  Draws d;
+  gauss4(A.seed, (uint32_t)p, A.step, 0u, kPurposeStep, &d.g[0]);
+  uint32_t c[4] = {(uint32_t)p, A.step, 1u, kPurposeStep};
+  philox4x32_10(c, (uint32_t)A.seed, (uint32_t)(A.seed >> 32));
+  box_muller(c[0], c[1], &d.g[4], &d.g[5]);  // g6, g7 are not used by the step
+  d.g[6] = d.g[7] = 0.0f;
+  return d;
+}
+
+// One particle in native FP64 instructions (PDF_ARITH_FP64, and the
+// fall-back of the fixed-point kernel for out-of-range values).
+__device__ __noinline__ Counts advance_native(const StepArgs& A, int64_t p, const Draws D) {
+  Counts c;
+  const float* g = D.g;
+  const int32_t e = A.elem[p];
+  const double* R = A.rows + (int64_t)e * PDFGB_ROW;
+  const double U0 = A.u[p], U1 = A.v[p], U2 = A.w[p];
+  const double gx = (double)g[0], gy = (double)g[1];
+  const double d0 = U0 - __ldg(R + 0), d1 = U1 - __ldg(R + 1), d2 = U2 - __ldg(R + 2);
+  const double G0 = (double)g[2], G1 = (double)g[3], G2 = (double)g[4];
+  const double b = __ldg(R + 21);
+  // velocity prediction (eq. velocity-prediction), time-n values throughout
+  double un = U0 + __ldg(R + 9) + __ldg(R + 3) * gx + __ldg(R + 4) * gy +
+              __ldg(R + 12) * d0 + __ldg(R + 13) * d1 + __ldg(R + 14) * d2 + b * G0;
+  double vn = U1 + __ldg(R + 10) + __ldg(R + 5) * gx + __ldg(R + 6) * gy +
+              __ldg(R + 15) * d0 + __ldg(R + 16) * d1 + __ldg(R + 17) * d2 + b * G1;
+  const double wn = U2 + __ldg(R + 11) + __ldg(R + 7) * gx + __ldg(R + 8) * gy +
+                    __ldg(R + 18) * d0 + __ldg(R + 19) * d1 + __ldg(R + 20) * d2 + b * G2;
+  // position (eq. Lagrangian-position-exact) with the same dW_x, dW_y
+  double xn = A.x[p] + U0 * A.dt + A.sdiff * gx;
+  double yn = A.y[p] + U1 * A.dt + A.sdiff * gy;
+  // frequency (eq. frequency-model); a negative result is reflected
+  const double o = A.om[p];
+  double on = o - __ldg(R + 23) * o + __ldg(R + 24) + __ldg(R + 25) * sqrt(fmax(o, 0.0)) * (double)g[5];
+  if (on < 0.0) { on = -on; ++c.om; }
+  // scalar (eq. IEM)
+  const double s = A.ps[p];
+  const double sn = s - (s - __ldg(R + 26)) * __ldg(R + 27);
+  const int32_t en = walk(A, e, xn, yn, un, vn, c.walk, c.refl, c.per, c.fb, c.brute, c.near);
+  A.x[p] = xn; A.y[p] = yn; A.u[p] = un; A.v[p] = vn; A.w[p] = wn; A.om[p] = on; A.ps[p] = sn;
+  if (en >= 0) A.elem[p] = en; else ++c.lost;
+  return c;
+}
+
+__device__ __forceinline__ void merge(Counts& a, const Counts& b) {
+  a.walk += b.walk; a.refl += b.refl; a.per += b.per; a.fb += b.fb;
+  a.brute += b.brute; a.lost += b.lost; a.om += b.om; a.near += b.near;
+}
+
+__device__ __forceinline__ void flush_counts(const StepArgs& A, const Counts& c) {
+  add_counter(A.counters + kCntWalk, c.walk);
+  add_counter(A.counters + kCntRefl, c.refl);
+  add_counter(A.counters + kCntPeriodic, c.per);
+  add_counter(A.counters + kCntFallback, c.fb);
+  add_counter(A.counters + kCntBrute, c.brute);
+  add_counter(A.counters + kCntLost, c.lost);
+  add_counter(A.counters + kCntOmega, c.om);
+  add_counter(A.counters + kCntNear, c.near);
+}
+
 __global__ void __launch_bounds__(256) k_step(StepArgs A) {
-  int c_walk = 0, c_refl = 0, c_per = 0, c_fb = 0, c_brute = 0, c_lost = 0, c_om = 0, c_near = 0;
+  Counts c;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // every lane runs the same number of iterations so the warp reductions below see all lanes
   const int64_t iters = (A.n + stride - 1) / stride;
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   for (int64_t it = 0; it < iters; ++it, p += stride) {
     if (p >= A.n) continue;
-    const int32_t e = A.elem[p];
-    float g[8];
-    gauss4(A.seed, (uint32_t)p, A.step, 0u, kPurposeStep, &g[0]);
-    gauss4(A.seed, (uint32_t)p, A.step, 1u, kPurposeStep, &g[4]);
-    const double* R = A.rows + (int64_t)e * PDFGB_ROW;
-    const double U0 = A.u[p], U1 = A.v[p], U2 = A.w[p];
-    const double gx = (double)g[0], gy = (double)g[1];
-    const double d0 = U0 - __ldg(R + 0), d1 = U1 - __ldg(R + 1), d2 = U2 - __ldg(R + 2);
-    const double G0 = (double)g[2], G1 = (double)g[3], G2 = (double)g[4];
-    const double b = __ldg(R + 21);
-    // velocity prediction (eq. velocity-prediction), time-n values throughout
-    double un = U0 + __ldg(R + 9) + __ldg(R + 3) * gx + __ldg(R + 4) * gy +
-                __ldg(R + 12) * d0 + __ldg(R + 13) * d1 + __ldg(R + 14) * d2 + b * G0;
-    double vn = U1 + __ldg(R + 10) + __ldg(R + 5) * gx + __ldg(R + 6) * gy +
-                __ldg(R + 15) * d0 + __ldg(R + 16) * d1 + __ldg(R + 17) * d2 + b * G1;
-    const double wn = U2 + __ldg(R + 11) + __ldg(R + 7) * gx + __ldg(R + 8) * gy +
-                      __ldg(R + 18) * d0 + __ldg(R + 19) * d1 + __ldg(R + 20) * d2 + b * G2;
-    // position (eq. Lagrangian-position-exact) with the same dW_x, dW_y
-    double xn = A.x[p] + U0 * A.dt + A.sdiff * gx;
-    double yn = A.y[p] + U1 * A.dt + A.sdiff * gy;
-    // frequency (eq. frequency-model); a negative result is reflected
-    const double o = A.om[p];
-    double on = o - __ldg(R + 23) * o + __ldg(R + 24) + __ldg(R + 25) * sqrt(fmax(o, 0.0)) * (double)g[5];
-    if (on < 0.0) { on = -on; ++c_om; }
-    // scalar (eq. IEM)
-    const double s = A.ps[p];
-    const double sn = s - (s - __ldg(R + 26)) * __ldg(R + 27);
-    const int32_t en = walk(A, e, xn, yn, un, vn, c_walk, c_refl, c_per, c_fb, c_brute, c_near);
-    A.x[p] = xn; A.y[p] = yn; A.u[p] = un; A.v[p] = vn; A.w[p] = wn; A.om[p] = on; A.ps[p] = sn;
-    if (en >= 0) A.elem[p] = en; else ++c_lost;
+    merge(c, advance_native(A, p, draw_step(A, p)));
   }
-  add_counter(A.counters + kCntWalk, c_walk);
-  add_counter(A.counters + kCntRefl, c_refl);
-  add_counter(A.counters + kCntPeriodic, c_per);
-  add_counter(A.counters + kCntFallback, c_fb);
-  add_counter(A.counters + kCntBrute, c_brute);
-  add_counter(A.counters + kCntLost, c_lost);
-  add_counter(A.counters + kCntOmega, c_om);
-  add_counter(A.counters + kCntNear, c_near);
+  flush_counts(A, c);
+}
+
+// ----------------------------------------------------------------------------
+// The same step without FP64 instructions (PDF_ARITH_FX, the default).
+// State in fixed point: positions, velocities and psi with 56 fraction bits
+// (|value| < 64), omega with 52 (|omega| < 1024); coefficients and products
+// as double-floats.  A particle with a value outside these ranges, or whose
+// walk meets a wall, an open boundary or the step cap, is finished by the
+// native FP64 code above.
+// ----------------------------------------------------------------------------
+constexpr int kF = 56;
+constexpr int kFO = 52;
+constexpr int kExpMax = 1023 + 5;    // |value| < 64
+constexpr int kExpMaxO = 1023 + 9;   // |omega| < 1024
+
+struct FxArgs {
+  const FxRow* rows;
+  const FxGeo* geo;
+  int64_t period_fix;
+  fx::df dt;      // dt
+  fx::df sdiff;   // sqrt(2 nu dt)
+};
+
+__device__ __forceinline__ fx::df ldc(const FxRow* r, int q) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(&r->c[q]));
+  return fx::df{v.x, v.y};
+}
+
+__device__ __forceinline__ int64_t ldm(const FxRow* r, int j) {
+  return (int64_t)__ldg(reinterpret_cast<const long long*>(&r->mean[j]));
+}
+
+__device__ __forceinline__ FxGeo load_fx_geo(const FxGeo* geo, int32_t e) {
+  FxGeo g;
+  const int4* src = reinterpret_cast<const int4*>(geo + e);
+  int4* dst = reinterpret_cast<int4*>(&g);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) dst[i] = __ldg(src + i);
+  return g;
+}
+
+// Twice the sub-areas in double-float (normalized), from fixed-point offsets.
+__device__ __forceinline__ void sub_areas_fx(const FxGeo& g, int64_t X, int64_t Y, fx::df& na, fx::df& nb,
+                                             fx::df& nc) {
+  const fx::df dx = fx::fix2df(X - g.xb, kF), dy = fx::fix2df(Y - g.yb, kF);
+  fx::acc a;
+  a.init(fx::mul(g.cbx, dy));
+  a.sub(fx::mul(g.cby, dx));
+  na = a.value();
+  fx::acc c;
+  c.init(fx::mul(dx, g.aby));
+  c.sub(fx::mul(dy, g.abx));
+  nc = c.value();
+  fx::acc b;
+  b.init(g.two_area);
+  b.sub(na);
+  b.sub(nc);
+  nb = b.value();
+}
+
+// FP32 screen of the element test: true only if all three sub-areas are
+// certainly positive.  Each FP32 value carries at most a few relative errors
+// of 2^-24 from the rounded offsets, the high parts of the coefficients and
+// the operations; the margin 2^-18 of the magnitudes involved covers them
+// with room to spare, so a "true" is never wrong and undecided particles go
+// to the double-float test.  A particle passing the screen is farther than
+// ~4e-6 A_e from every edge, far outside the 1e-12 near-face band.
+__device__ __forceinline__ bool inside_certain(const FxGeo& g, int64_t X, int64_t Y) {
+  const fx::df dxd = fx::fix2df(X - g.xb, kF), dyd = fx::fix2df(Y - g.yb, kF);
+  const float dx = dxd.h + dxd.l, dy = dyd.h + dyd.l;
+  const float p1 = g.cbx.h * dy, p2 = g.cby.h * dx;
+  const float q1 = dx * g.aby.h, q2 = dy * g.abx.h;
+  const float na = p1 - p2, nc = q1 - q2;
+  const float ba = (fabsf(p1) + fabsf(p2)) * 0x1p-18f;
+  const float bc = (fabsf(q1) + fabsf(q2)) * 0x1p-18f;
+  const float nb = g.two_area.h - na - nc;
+  const float bb = (fabsf(g.two_area.h) + fabsf(na) + fabsf(nc)) * 0x1p-18f + ba + bc;
+  return na > ba && nc > bc && nb > bb;
+}
+
+// Fixed-point neighbour walk; returns true when the FP64 walk must finish it
+// (a wall or open-boundary edge, or the 64-step cap).
+__device__ __forceinline__ bool walk_fx(const FxArgs& F, int32_t& e, int64_t& Xn, int64_t Yn, int& steps, int& c_per,
+                                        int& c_near) {
+  for (;;) {
+    const FxGeo G = load_fx_geo(F.geo, e);
+    if (inside_certain(G, Xn, Yn)) return false;
+    fx::df na, nb, nc;
+    sub_areas_fx(G, Xn, Yn, na, nb, nc);
+    if (fx::ge0(na) && fx::ge0(nb) && fx::ge0(nc)) {
+      const float mn = fminf(na.h, fminf(nb.h, nc.h));
+      if (mn < 1e-12f * G.two_area.h) ++c_near;
+      return false;
+    }
+    if (steps >= 64) return true;
+    int k = 0;
+    fx::df mn = na;
+    if (fx::lt(nb, mn)) { k = 1; mn = nb; }
+    if (fx::lt(nc, mn)) { k = 2; }
+    const int32_t nbr = G.nbr[k];
+    if (nbr < 0) return true;
+    ++steps;
+    if (G.shift[k] != 0) {
+      Xn += (int64_t)G.shift[k] * F.period_fix;
+      ++c_per;
+    }
+    e = nbr;
+  }
+}
+
+__device__ __noinline__ int32_t walk_slow(const StepArgs& A, int32_t e, double& x, double& y, double& u,
+                                          double& v, Counts& c) {
+  return walk(A, e, x, y, u, v, c.walk, c.refl, c.per, c.fb, c.brute, c.near);
+}
+
+__global__ void __launch_bounds__(256) k_step_fx(StepArgs A, FxArgs F) {
+  int c_walk = 0, c_per = 0, c_om = 0, c_near = 0;
+  Counts cs;  // counts of the FP64 fall-backs
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t iters = (A.n + stride - 1) / stride;
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t it = 0; it < iters; ++it, p += stride) {
+    if (p >= A.n) continue;
+    const Draws D = draw_step(A, p);
+    const uint64_t bx = (uint64_t)__double_as_longlong(A.x[p]);
+    const uint64_t by = (uint64_t)__double_as_longlong(A.y[p]);
+    const uint64_t bu = (uint64_t)__double_as_longlong(A.u[p]);
+    const uint64_t bv = (uint64_t)__double_as_longlong(A.v[p]);
+    const uint64_t bw = (uint64_t)__double_as_longlong(A.w[p]);
+    const uint64_t bo = (uint64_t)__double_as_longlong(A.om[p]);
+    const uint64_t bs = (uint64_t)__double_as_longlong(A.ps[p]);
+    int32_t e = A.elem[p];
+    const FxRow* R = F.rows + e;
+    const bool in_range = fx::d_exp(bx) <= kExpMax && fx::d_exp(by) <= kExpMax && fx::d_exp(bu) <= kExpMax &&
+                          fx::d_exp(bv) <= kExpMax && fx::d_exp(bw) <= kExpMax && fx::d_exp(bs) <= kExpMax &&
+                          fx::d_exp(bo) <= kExpMaxO && ldc(R, 27).h == 0.0f;
+    if (!in_range) {
+      merge(cs, advance_native(A, p, D));
+      continue;
+    }
+    // velocity prediction (eq. velocity-prediction): U + a dt
+    // + sqrt(2 nu) dU_i/dx_j dW_j + G_ij (U_j - <U_j>) dt + sqrt(C0 eps) dW'_i
+    const int64_t U0 = fx::d2fix(bu, kF), U1 = fx::d2fix(bv, kF), U2 = fx::d2fix(bw, kF);
+    const fx::df d0 = fx::fix2df(U0 - ldm(R, 0), kF);
+    const fx::df d1 = fx::fix2df(U1 - ldm(R, 1), kF);
+    const fx::df d2 = fx::fix2df(U2 - ldm(R, 2), kF);
+    const fx::df sc = ldc(R, 18);
+    int64_t Un[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      fx::acc a;
+      a.init(ldc(R, 6 + i));
+      a.add(fx::mul_f(ldc(R, 2 * i), D.g[0]));
+      a.add(fx::mul_f(ldc(R, 2 * i + 1), D.g[1]));
+      a.add(fx::mul(ldc(R, 9 + 3 * i), d0));
+      a.add(fx::mul(ldc(R, 10 + 3 * i), d1));
+      a.add(fx::mul(ldc(R, 11 + 3 * i), d2));
+      a.add(fx::mul_f(sc, D.g[2 + i]));
+      Un[i] = (i == 0 ? U0 : (i == 1 ? U1 : U2)) + a.fix(kF);
+    }
+    // position (eq. Lagrangian-position-exact): X + U^n dt + sqrt(2 nu) dW
+    int64_t Xn, Yn;
+    {
+      fx::acc a;
+      a.init(fx::mul(fx::fix2df(U0, kF), F.dt));
+      a.add(fx::mul_f(F.sdiff, D.g[0]));
+      Xn = fx::d2fix(bx, kF) + a.fix(kF);
+      fx::acc b;
+      b.init(fx::mul(fx::fix2df(U1, kF), F.dt));
+      b.add(fx::mul_f(F.sdiff, D.g[1]));
+      Yn = fx::d2fix(by, kF) + b.fix(kF);
+    }
+    // frequency (eq. frequency-model): omega - (C3 + S_w) <w> dt omega + C3 <w>^2 dt
+    // + <w> sqrt(2 C3 C4 dt) sqrt(max(omega, 0)) dW
+    const int64_t O = fx::d2fix(bo, kFO);
+    int64_t On;
+    {
+      const fx::df od = fx::fix2df(O, kFO);
+      fx::acc a;
+      a.init(ldc(R, 20));
+      a.sub(fx::mul(ldc(R, 19), od));
+      a.add(fx::mul_f(fx::mul(ldc(R, 21), fx::sqrt_df(od)), D.g[5]));
+      On = O + a.fix(kFO);
+      if (On < 0) { On = -On; ++c_om; }
+    }
+    // scalar (eq. IEM): psi - (psi - <phi>) dt / t_m
+    const int64_t S = fx::d2fix(bs, kF);
+    const fx::df prod = fx::mul(ldc(R, 22), fx::fix2df(S - ldm(R, 3), kF));
+    const int64_t Sn = S - (fx::f2fix(prod.h, kF) + fx::f2fix(prod.l, kF));
+    // neighbour walk (sec. 3.5) in fixed point; walls, open boundaries and
+    // the step cap go to the FP64 walk
+    int steps = 0;
+    const bool slow = walk_fx(F, e, Xn, Yn, steps, c_per, c_near);
+    c_walk += steps;
+    double xn = __longlong_as_double((long long)fx::fix2d(Xn, kF));
+    double yn = __longlong_as_double((long long)fx::fix2d(Yn, kF));
+    double un = __longlong_as_double((long long)fx::fix2d(Un[0], kF));
+    double vn = __longlong_as_double((long long)fx::fix2d(Un[1], kF));
+    if (slow) {
+      const int32_t en = walk_slow(A, e, xn, yn, un, vn, cs);
+      if (en >= 0) e = en; else { ++cs.lost; e = A.elem[p]; }
+    }
+    A.x[p] = xn;
+    A.y[p] = yn;
+    A.u[p] = un;
+    A.v[p] = vn;
+    A.w[p] = __longlong_as_double((long long)fx::fix2d(Un[2], kF));
+    A.om[p] = __longlong_as_double((long long)fx::fix2d(On, kFO));
+    A.ps[p] = __longlong_as_double((long long)fx::fix2d(Sn, kF));
+    A.elem[p] = e;
+  }
+  cs.walk += c_walk; cs.per += c_per; cs.om += c_om; cs.near += c_near;
+  flush_counts(A, cs);
+}
+
+// ----------------------------------------------------------------------------
+// PDF_FP32_STATE: velocity, frequency and scalar stored and advanced in FP32;
+// positions and the walk stay FP64-accurate (fixed point, as above).
+// ----------------------------------------------------------------------------
+struct F32Args {
+  float *u, *v, *w, *om, *ps;
+  const float* rows;  // [n_tri][32], the layout of the FP64 rows
+};
+
+__global__ void __launch_bounds__(256) k_step_f32(StepArgs A, FxArgs F, F32Args S) {
+  int c_walk = 0, c_per = 0, c_om = 0, c_near = 0;
+  Counts cs;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t iters = (A.n + stride - 1) / stride;
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t it = 0; it < iters; ++it, p += stride) {
+    if (p >= A.n) continue;
+    const Draws D = draw_step(A, p);
+    int32_t e = A.elem[p];
+    const float* R = S.rows + (int64_t)e * PDFGB_ROW;
+    const float U0 = S.u[p], U1 = S.v[p], U2 = S.w[p];
+    const float d0 = U0 - __ldg(R + 0), d1 = U1 - __ldg(R + 1), d2 = U2 - __ldg(R + 2);
+    const float b = __ldg(R + 21);
+    // velocity prediction (eq. velocity-prediction) in FP32
+    float un = U0 + __ldg(R + 9) + __ldg(R + 3) * D.g[0] + __ldg(R + 4) * D.g[1] + __ldg(R + 12) * d0 +
+               __ldg(R + 13) * d1 + __ldg(R + 14) * d2 + b * D.g[2];
+    float vn = U1 + __ldg(R + 10) + __ldg(R + 5) * D.g[0] + __ldg(R + 6) * D.g[1] + __ldg(R + 15) * d0 +
+               __ldg(R + 16) * d1 + __ldg(R + 17) * d2 + b * D.g[3];
+    const float wn = U2 + __ldg(R + 11) + __ldg(R + 7) * D.g[0] + __ldg(R + 8) * D.g[1] + __ldg(R + 18) * d0 +
+                     __ldg(R + 19) * d1 + __ldg(R + 20) * d2 + b * D.g[4];
+    // frequency (eq. frequency-model) and scalar (eq. IEM) in FP32
+    const float o = S.om[p];
+    float on = o - __ldg(R + 23) * o + __ldg(R + 24) + __ldg(R + 25) * sqrtf(fmaxf(o, 0.f)) * D.g[5];
+    if (on < 0.f) { on = -on; ++c_om; }
+    const float s = S.ps[p];
+    const float sn = s - (s - __ldg(R + 26)) * __ldg(R + 27);
+    // position (eq. Lagrangian-position-exact), FP64-accurate
+    const uint64_t bx = (uint64_t)__double_as_longlong(A.x[p]);
+    const uint64_t by = (uint64_t)__double_as_longlong(A.y[p]);
+    double xn, yn, ud = (double)un, vd = (double)vn;
+    bool slow;
+    if (fx::d_exp(bx) <= kExpMax && fx::d_exp(by) <= kExpMax) {
+      fx::acc a;
+      a.init(fx::mul_f(F.dt, U0));
+      a.add(fx::mul_f(F.sdiff, D.g[0]));
+      int64_t Xn = fx::d2fix(bx, kF) + a.fix(kF);
+      fx::acc c;
+      c.init(fx::mul_f(F.dt, U1));
+      c.add(fx::mul_f(F.sdiff, D.g[1]));
+      const int64_t Yn = fx::d2fix(by, kF) + c.fix(kF);
+      int steps = 0;
+      slow = walk_fx(F, e, Xn, Yn, steps, c_per, c_near);
+      c_walk += steps;
+      xn = __longlong_as_double((long long)fx::fix2d(Xn, kF));
+      yn = __longlong_as_double((long long)fx::fix2d(Yn, kF));
+    } else {
+      xn = A.x[p] + (double)U0 * A.dt + A.sdiff * (double)D.g[0];
+      yn = A.y[p] + (double)U1 * A.dt + A.sdiff * (double)D.g[1];
+      slow = true;
+    }
+    if (slow) {
+      const int32_t en = walk_slow(A, e, xn, yn, ud, vd, cs);
+      if (en >= 0) e = en; else { ++cs.lost; e = A.elem[p]; }
+      un = (float)ud;
+      vn = (float)vd;
+    }
+    A.x[p] = xn;
+    A.y[p] = yn;
+    S.u[p] = un;
+    S.v[p] = vn;
+    S.w[p] = wn;
+    S.om[p] = on;
+    S.ps[p] = sn;
+    A.elem[p] = e;
+  }
+  cs.walk += c_walk; cs.per += c_per; cs.om += c_om; cs.near += c_near;
+  flush_counts(A, cs);
 }
 
 static int sm_count() {
@@ -369,7 +731,8 @@ static int blocks_for(int64_t n, int threads, int per_sm) {
 static pdf_status check_params(const pdf_model_params* p) {
   if (!p) return fail(PDF_EINVAL, "NULL params");
   if (!(p->dt > 0.0) || !(p->nu >= 0.0)) return fail(PDF_EINVAL, "params: dt must be > 0 and nu >= 0");
-  if (p->closure < 0 || p->closure > 2 || p->tm_mode < 0 || p->tm_mode > 1 || p->pressure < 0 || p->pressure > 1)
+  if (p->closure < 0 || p->closure > 2 || p->tm_mode < 0 || p->tm_mode > 1 || p->pressure < 0 ||
+      p->pressure > 1 || p->arith < 0 || p->arith > 1)
     return fail(PDF_EINVAL, "params: closure, tm_mode or pressure out of range");
   return PDF_OK;
 }
@@ -383,7 +746,9 @@ static pdf_status build_rows(pdf_particles* P, const pdf_model_params* params, c
                                                                 params->closure == PDF_CLOSURE_GLM ? wp : nullptr,
                                                                 C, P->nc););
   PDF_KERNEL("k_elem_rows", st, k_elem_rows<<<blocks_for(M.n_tri, 128, 32), 128, 0, st>>>(M.tri, M.n_tri, P->nc, C,
-                                                             internal ? P->rows : nullptr, avg_out););
+                                                             internal ? P->rows : nullptr, avg_out,
+                                                             internal && C.arith == PDF_ARITH_FX ? P->rows_fx : nullptr,
+                                                             internal ? P->rows_f32 : nullptr););
   return PDF_OK;
 }
 
@@ -411,7 +776,9 @@ extern "C" pdf_status pdf_step(pdf_particles* p, const pdf_mesh* m, const pdf_mo
   const MeshDev& M = m->d;
   if (params->closure == PDF_CLOSURE_FROZEN) {
     if (!elem_coeff) return fail(PDF_EINVAL, "pdf_step: FROZEN needs elem_coeff");
-    PDF_KERNEL("k_frozen_rows", st, k_frozen_rows<<<blocks_for(M.n_tri, 128, 32), 128, 0, st>>>(M.n_tri, elem_coeff, coeff_params(params), p->rows););
+    PDF_KERNEL("k_frozen_rows", st, k_frozen_rows<<<blocks_for(M.n_tri, 128, 32), 128, 0, st>>>(
+                                         M.n_tri, elem_coeff, coeff_params(params), p->rows,
+                                         params->arith == PDF_ARITH_FX ? p->rows_fx : nullptr, p->rows_f32););
   } else {
     if (!p->have_stats) return fail(PDF_ESTATE, "pdf_step: call pdf_estimate_stats before a GLM/SLM step");
     s = build_rows(p, params, wp, nullptr, true, st);
@@ -431,7 +798,28 @@ extern "C" pdf_status pdf_step(pdf_particles* p, const pdf_mesh* m, const pdf_mo
   A.seed = p->seed;
   A.step = step;
   A.counters = p->counters;
-  PDF_KERNEL("k_step", st, k_step<<<blocks_for(p->n, 256, 8), 256, 0, st>>>(A););
+  if (p->precision == PDF_FP32_STATE || params->arith == PDF_ARITH_FX) {
+    FxArgs F;
+    F.rows = p->rows_fx;
+    F.geo = M.fgeo;
+    uint64_t b;
+    std::memcpy(&b, &M.period, 8);
+    F.period_fix = fx::d2fix(b, kF);
+    std::memcpy(&b, &A.dt, 8);
+    F.dt = fx::d2df(b);
+    std::memcpy(&b, &A.sdiff, 8);
+    F.sdiff = fx::d2df(b);
+    if (p->precision == PDF_FP32_STATE) {
+      F32Args S;
+      S.u = p->uf; S.v = p->vf; S.w = p->wf; S.om = p->omf; S.ps = p->psf;
+      S.rows = p->rows_f32;
+      PDF_KERNEL("k_step", st, k_step_f32<<<blocks_for(p->n, 256, 8), 256, 0, st>>>(A, F, S));
+    } else {
+      PDF_KERNEL("k_step", st, k_step_fx<<<blocks_for(p->n, 256, 8), 256, 0, st>>>(A, F));
+    }
+  } else {
+    PDF_KERNEL("k_step", st, k_step<<<blocks_for(p->n, 256, 8), 256, 0, st>>>(A));
+  }
   if (info) {
     long long c[8];
     PDF_CUDA(cudaMemcpyAsync(c, p->counters, sizeof(c), cudaMemcpyDeviceToHost, st));

@@ -117,7 +117,8 @@ def _compare_states(st, ost, what, allow_flagged=None):
     return float((~el_ok).mean())
 
 
-def test_frozen_step_parity():
+@pytest.mark.parametrize("arith", ["fx", "fp64"])
+def test_frozen_step_parity(arith):
     m = inputs.channel_mesh(20, 40, seed=1)
     counts = np.full(2 * 19 * 39, 30, dtype=np.int32)
     gm, M, gp, ost = _pair(m, counts, psi=inputs.scalar_slab(m))
@@ -135,7 +136,7 @@ def test_frozen_step_parity():
     rows[:, 24] = rng.uniform(0, 1, gm.n_tri)
     rows[:, 25] = rng.uniform(0.5, 5, gm.n_tri)
     for closure in ("glm", "slm"):
-        p = pg.model_params(closure="frozen", dt=2e-3, nu=1e-3)
+        p = pg.model_params(closure="frozen", dt=2e-3, nu=1e-3, arith=arith)
         # the FROZEN closure moves positions with sqrt(2 nu) diffusion like GLM
         po = oracle.make_params(dt=2e-3, nu=1e-3, closure="glm")
         if closure == "slm":
@@ -151,13 +152,13 @@ def test_frozen_step_parity():
         assert info["crossings_periodic"] == cnt["crossings_periodic"]
 
 
-def _run_config(name, steps, check_every=None):
+def _run_config(name, steps, check_every=None, arith="fx"):
     cfg = inputs.workload(name)
     m = inputs.channel_mesh(cfg["nx"], cfg["ny"], jitter=cfg["jitter"], seed=cfg["seed"])
     counts = np.full(cfg["n_tri"], cfg["ppe"], dtype=np.int32)
     psi = inputs.scalar_slab(m, cfg["psi_slab_x"])
     gm, M, gp, ost = _pair(m, counts, seed=cfg["seed"], psi=psi, u_sigma=cfg["u_sigma"])
-    p = pg.model_params(dt=cfg["dt"], nu=cfg["nu"], Pi=cfg["Pi"], closure=cfg["closure"])
+    p = pg.model_params(dt=cfg["dt"], nu=cfg["nu"], Pi=cfg["Pi"], closure=cfg["closure"], arith=arith)
     po = _oracle_params(p)
     pg.pdf_estimate_stats(gp, gm)
     oes, ons, ond, _ = oracle.statistics(M, ost)
@@ -176,11 +177,13 @@ def _run_config(name, steps, check_every=None):
     return gm, M, gp, ost, ons, near
 
 
-def test_small_channel_free_run_100_steps():
+@pytest.mark.parametrize("arith", ["fx", "fp64"])
+def test_small_channel_free_run_100_steps(arith):
     """The small channel workload (20x40 nodes, 50 particles per element, GLM
     with the local wp, channel pressure), 100 steps free-running: states,
-    statistics and element ids stay within the tolerance."""
-    gm, M, gp, ost, ons, near = _run_config("channel_20x40_ppe50", 100, check_every=25)
+    statistics and element ids stay within the tolerance, for both the
+    FP64-free default arithmetic and native FP64."""
+    gm, M, gp, ost, ons, near = _run_config("channel_20x40_ppe50", 100, check_every=25, arith=arith)
     assert max(near) < 1e-4
     _check_stats(gp, gm, M, ost, ons)
 
@@ -193,6 +196,7 @@ def test_tiny_mesh_edge_cases():
     gm, M, gp, ost = _pair(m, counts, u_sigma=0.5)
     p = pg.model_params(closure="slm", dt=0.05, nu=1e-3)
     po = _oracle_params(p)
+    assert p.arith == 0  # the default FP64-free kernel (walls go to its FP64 fall-back)
     pg.pdf_estimate_stats(gp, gm)
     oes, ons, ond, _ = oracle.statistics(M, ost)
     for s in range(20):
@@ -243,3 +247,62 @@ def test_full_size_sampled_step_and_statistics():
     got["elem"] = st1["elem"][pid]
     _compare_states(got, sub, "full-size sampled step", (status & oracle.TRK_NEAR_FACE) != 0)
     assert info["lost"] == 0
+
+
+def test_fallbacks_for_values_outside_the_fixed_point_ranges():
+    """Particles with |u| >= 64 (outside the fixed-point range of the step)
+    and elements holding them (outside the range of the exact integer
+    statistics) are handled by the FP64 fall-backs; results still match."""
+    m = inputs.channel_mesh(20, 40, seed=1)
+    counts = np.full(2 * 19 * 39, 20, dtype=np.int32)
+    gm, M, gp, ost = _pair(m, counts, psi=inputs.scalar_slab(m))
+    sel = ost["elem"] < 12
+    ost["u"][sel] += 300.0
+    ost["om"][ost["elem"] == 40] += 5000.0
+    st = {k: torch.from_numpy(np.ascontiguousarray(ost[k])).cuda() for k in KEYS}
+    st["elem"] = torch.from_numpy(ost["elem"]).cuda()
+    gp.set_state(st)
+    oes, ons, ond = _check_stats(gp, gm, M, ost)
+    p = pg.model_params(closure="slm", dt=1e-4)
+    po = _oracle_params(p)
+    rows = oracle.elem_coeff(M, ons, ond, po)
+    cnt, status = oracle.step(M, rows, po, 1, 0, ost)
+    info = pg.pdf_step(gp, gm, p, step=0, info=True)
+    got = _host(gp.get_state())
+    _compare_states(got, ost, "fall-back step", (status & oracle.TRK_NEAR_FACE) != 0)
+    assert info["lost"] == 0
+
+
+def test_relaxation_solve_matches_the_oracle():
+    """pdf_relax_solve on the small channel after a few steps: the nodal
+    right-hand side, the L^2 fields and the converged solution agree with the
+    oracle's assembly and sparse direct solve."""
+    import oracle.relax as OR
+    m = inputs.channel_mesh(20, 40, seed=1)
+    counts = np.full(2 * 19 * 39, 50, dtype=np.int32)
+    gm, M, gp, ost = _pair(m, counts, psi=inputs.scalar_slab(m))
+    p = pg.model_params(closure="glm")
+    pg.pdf_estimate_stats(gp, gm)
+    for s in range(3):
+        pg.pdf_step(gp, gm, p, step=s)
+        pg.pdf_estimate_stats(gp, gm)
+    ns = torch.empty((gm.n_nodes, 12), dtype=torch.float64, device="cuda")
+    nd = torch.empty((gm.n_nodes, 10), dtype=torch.float64, device="cuda")
+    pg.pdf_estimate_stats(gp, gm, None, ns, nd)
+    S, Dv = ns.cpu().numpy(), nd.cpu().numpy()
+    rhs, L2 = pg.pdf_relax_rhs(gp, gm, p)
+    ref_rhs = np.stack([oracle.relax_rhs(S[n], Dv[n]) for n in range(gm.n_nodes)], axis=1)
+    assert_field_close(rhs.cpu().numpy().T, ref_rhs.T, "relaxation right-hand side")
+    dist, nrm = OR.wall_normals(m)
+    gd, gn = gm.wall_distance()
+    assert np.allclose(gd, dist, atol=1e-14) and np.array_equal(gn, nrm)
+    for c, cxi in enumerate((1 + 1.3 * nrm[:, 0] ** 2, 1 + 1.3 * nrm[:, 1] ** 2, np.ones(gm.n_nodes))):
+        assert_field_close(L2[c].cpu().numpy(), OR.lengthscale2(S, p.nu, cxi), "L^2 class %d" % c)
+    wp = torch.zeros((9, gm.n_nodes), dtype=torch.float64, device="cuda")
+    iters, res = pg.pdf_relax_solve(gp, gm, p, wp, rtol=1e-13, max_it=2000)
+    ref = OR.solve(m, S, ref_rhs, p.nu)
+    assert_field_close(wp.cpu().numpy().T, ref.T, "relaxation solution", rtol=1e-9)
+    assert max(res) <= 1e-13
+    # warm start from the solution: converged at once
+    iters2, _ = pg.pdf_relax_solve(gp, gm, p, wp, rtol=1e-10, max_it=2000)
+    assert max(iters2) <= 1
