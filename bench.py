@@ -310,6 +310,46 @@ def run_gpu(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "hbm_frac_step": step_frac, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
             "roofline": roofline, "kernels": shares}
+    # the precision form (FP32 velocity/frequency/scalar state) on the same workload
+    if not args.skip_extras:
+        del gp
+        torch.cuda.empty_cache()
+        gq = pg.Particles(gm, seed, ppe=cfg["ppe"], u_sigma=cfg["u_sigma"], elem_psi0=psi,
+                          precision=pg.capi.PDF_FP32_STATE)
+        pg.pdf_estimate_stats(gq, gm)
+        for s in range(3):
+            pg.pdf_step(gq, gm, p, step=s)
+            pg.pdf_estimate_stats(gq, gm)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ksteps = max(5, min(args.steps, 20))
+        for s in range(ksteps):
+            pg.pdf_step(gq, gm, p, step=3 + s, stream=stream)
+            pg.pdf_estimate_stats(gq, gm, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = e0.elapsed_time(e1) / ksteps
+        line["precision_fp32_state"] = {"value": n / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32,
+                                        "steps": ksteps,
+                                        "what": "u, v, w, omega, psi stored and advanced in FP32; x, y FP64"}
+        # the elliptic-relaxation solve on this mesh: cold, and warm from the previous step
+        wp = torch.zeros((9, gm.n_nodes), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it_cold, _ = pg.pdf_relax_solve(gq, gm, p, wp, rtol=1e-10, max_it=20000)
+        t_cold = time.perf_counter() - t0
+        pg.pdf_step(gq, gm, p, wp=wp, step=100)
+        pg.pdf_estimate_stats(gq, gm)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it_warm, _ = pg.pdf_relax_solve(gq, gm, p, wp, rtol=1e-10, max_it=20000)
+        t_warm = time.perf_counter() - t0
+        line["relax_solve"] = {"rtol": 1e-10, "n_nodes": gm.n_nodes,
+                               "cold": {"iterations_max": max(it_cold), "seconds": t_cold},
+                               "warm_previous_step": {"iterations_max": max(it_warm), "seconds": t_warm}}
+        del gq
     if not args.no_cpu_baseline and world == 1:
         try:
             line["cpu_baseline"] = cpu_baseline_measure(1)
@@ -321,17 +361,51 @@ def run_gpu(args):
     return 0
 
 
+def run_warmstart(args):
+    """Train the per-node MLP on elliptic-relaxation solves of the small
+    channel (the library's kernels only), then on the 158,802-triangle mesh
+    solve to rtol 1e-10 from zero, from the previous step's solution and from
+    the network's guess."""
+    import torch
+    from paper_1006_0720_gb300 import experiments as E
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    X, Y = E.collect_solves(args.solves)
+    t_collect = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    net, losses = E.train(X, Y, steps=args.train_steps, batch=8192, lr=2e-3, log_every=max(1, args.train_steps // 10))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del X, Y
+    cfg, gm, gp, p, wp = E.setup(WORKLOAD, seed=3)
+    its = E.advance(gm, gp, p, wp, args.steps)
+    res = E.compare(gm, gp, p, wp, net)
+    line = {"mode": "warmstart", "train_solves": args.solves, "train_samples": args.solves * 800,
+            "train_steps": args.train_steps, "collect_seconds": t_collect, "train_seconds": t_train,
+            "loss_log": losses, "eval_workload": WORKLOAD, "eval_after_steps": args.steps,
+            "warm_iterations_during_run": its, "compare": res}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--solves", type=int, default=10000, help="warmstart: training solves of the small channel")
+    ap.add_argument("--train-steps", type=int, default=4000, help="warmstart: Adam steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, help="a smaller workload for profiling runs")
+    ap.add_argument("--skip-extras", action="store_true", help="only the main line (no FP32-state and solve figures)")
+    ap.add_argument("--mode", default="step", choices=["step", "warmstart"],
+                    help="warmstart: the learned warm start experiment instead of the step benchmark")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "warmstart":
+        return run_warmstart(args)
     return run_gpu(args)
 
 

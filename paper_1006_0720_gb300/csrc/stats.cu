@@ -289,12 +289,22 @@ __device__ __forceinline__ long long to_fix(const float* a, int64_t i, int lim, 
   return fx::f2fix(f, kFQ);
 }
 
+// Per-warp shared scratch of the statistics kernel: lane partials, stored
+// column-wise so that one lane can add up one quantity over the 32 lanes.
+struct StatScratch {
+  unsigned long long lo[5][32];
+  long long hi[5][32];
+  float h[11][32], l[11][32];
+};
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_elem_stats_fx(const int32_t* __restrict__ seg,
                                                        const int32_t* __restrict__ pid, int32_t n_tri,
                                                        const T* __restrict__ u, const T* __restrict__ v,
                                                        const T* __restrict__ w, const T* __restrict__ om,
                                                        const T* __restrict__ ps, double* __restrict__ es) {
+  __shared__ StatScratch scratch[8];
+  StatScratch& SS = scratch[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -324,61 +334,90 @@ __global__ void __launch_bounds__(256) k_elem_stats_fx(const int32_t* __restrict
       continue;
     }
 #pragma unroll
-    for (int q = 0; q < 5; ++q) warp_sum128(lo[q], hi[q]);
-    // all lanes hold identical exact sums; lane q < 5 forms mean q, lane q
-    // of the moments below forms output q: the finishing runs in
-    // double-float FP32 and integer operations, never in FP64
+    for (int q = 0; q < 5; ++q) {
+      SS.lo[q][lane] = lo[q];
+      SS.hi[q][lane] = hi[q];
+    }
+    __syncwarp();
+    // lane q < 5 adds quantity q over the lanes (exact) and forms its mean
     const fx::df invN = fx::recip_df(N);
-    fx::df mine = fx::df{0.f, 0.f};
-#pragma unroll
-    for (int q = 0; q < 5; ++q)
-      if (lane == q) mine = fx::df_norm(fx::mul(fx::i128_to_df(lo[q], hi[q], -kFQ), invN));
+    fx::df mean = fx::df{0.f, 0.f};
+    if (lane < 5) {
+      unsigned long long sl = 0;
+      long long sh = 0;
+      for (int j = 0; j < 32; ++j) {
+        const unsigned long long nl = sl + SS.lo[lane][j];
+        sh = sh + SS.hi[lane][j] + (nl < sl ? 1 : 0);
+        sl = nl;
+      }
+      mean = fx::df_norm(fx::mul(fx::i128_to_df(sl, sh, -kFQ), invN));
+    }
     long long M[4];
     const int idx[4] = {0, 1, 2, 4};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const float mh = __shfl_sync(0xffffffffu, mine.h, idx[k]);
-      const float ml = __shfl_sync(0xffffffffu, mine.l, idx[k]);
+      const float mh = __shfl_sync(0xffffffffu, mean.h, idx[k]);
+      const float ml = __shfl_sync(0xffffffffu, mean.l, idx[k]);
       M[k] = fx::f2fix(mh, kFQ) + fx::f2fix(ml, kFQ);
     }
-    // pass 2: deviations from M, exact products and sums
-    unsigned long long clo[7] = {0, 0, 0, 0, 0, 0, 0}, dlo[4] = {0, 0, 0, 0};
-    long long chi[7] = {0, 0, 0, 0, 0, 0, 0}, dhi[4] = {0, 0, 0, 0};
+    // pass 2: deviations from M (exact), their products and sums in
+    // double-float, each lane's particles in order
+    fx::acc c[7], d[4];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) c[q].init(fx::df{0.f, 0.f});
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d[k].init(fx::df{0.f, 0.f});
     for (int32_t i = beg + lane; i < end; i += 32) {
       const int32_t p = pid[i];
       bool dummy = true;
-      const long long D[4] = {to_fix(u, p, 6, dummy) - M[0], to_fix(v, p, 6, dummy) - M[1],
-                              to_fix(w, p, 6, dummy) - M[2], to_fix(ps, p, 6, dummy) - M[3]};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) add64(dlo[k], dhi[k], D[k]);
-      mac128(clo[0], chi[0], D[0], D[0]);
-      mac128(clo[1], chi[1], D[1], D[1]);
-      mac128(clo[2], chi[2], D[2], D[2]);
-      mac128(clo[3], chi[3], D[0], D[1]);
-      mac128(clo[4], chi[4], D[0], D[2]);
-      mac128(clo[5], chi[5], D[1], D[2]);
-      mac128(clo[6], chi[6], D[3], D[3]);
+      const fx::df D0 = fx::fix2df(to_fix(u, p, 6, dummy) - M[0], kFQ);
+      const fx::df D1 = fx::fix2df(to_fix(v, p, 6, dummy) - M[1], kFQ);
+      const fx::df D2 = fx::fix2df(to_fix(w, p, 6, dummy) - M[2], kFQ);
+      const fx::df D3 = fx::fix2df(to_fix(ps, p, 6, dummy) - M[3], kFQ);
+      d[0].add(D0); d[1].add(D1); d[2].add(D2); d[3].add(D3);
+      c[0].add(fx::mul(D0, D0));
+      c[1].add(fx::mul(D1, D1));
+      c[2].add(fx::mul(D2, D2));
+      c[3].add(fx::mul(D0, D1));
+      c[4].add(fx::mul(D0, D2));
+      c[5].add(fx::mul(D1, D2));
+      c[6].add(fx::mul(D3, D3));
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) warp_sum128(dlo[k], dhi[k]);
-#pragma unroll
-    for (int q = 0; q < 7; ++q) warp_sum128(clo[q], chi[q]);
-    // output lane: 0 -> N, 1..5 -> means, 6..12 -> central moments
-    // (sum D_a D_b - sum D_a sum D_b / N) / N, scaled by 2^-96
-    const int pa[7] = {0, 1, 2, 0, 0, 1, 3}, pb[7] = {0, 1, 2, 1, 2, 2, 3};
-    fx::df val = fx::df{0.f, 0.f};
-    const fx::df mean_here_h = fx::df{__shfl_sync(0xffffffffu, mine.h, (lane + 31) & 31),
-                                      __shfl_sync(0xffffffffu, mine.l, (lane + 31) & 31)};
-    if (lane >= 1 && lane <= 5) val = mean_here_h;
+    __syncwarp();
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
-      if (lane == 6 + q) {
-        const fx::df s2 = fx::i128_to_df(clo[q], chi[q], -2 * kFQ);
-        const fx::df da = fx::i128_to_df(dlo[pa[q]], dhi[pa[q]], -kFQ);
-        const fx::df db = fx::i128_to_df(dlo[pb[q]], dhi[pb[q]], -kFQ);
-        const fx::df corr = fx::df_norm(fx::mul(fx::df_norm(fx::mul(da, db)), invN));
-        val = fx::df_norm(fx::mul(fx::sub(s2, corr), invN));
-      }
+      SS.h[q][lane] = c[q].h;
+      SS.l[q][lane] = c[q].l;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      SS.h[7 + k][lane] = d[k].h;
+      SS.l[7 + k][lane] = d[k].l;
+    }
+    __syncwarp();
+    // lane q < 11 adds quantity q over the lanes, in lane order
+    fx::df tot = fx::df{0.f, 0.f};
+    if (lane < 11) {
+      fx::acc a;
+      a.init(fx::df{SS.h[lane][0], SS.l[lane][0]});
+      for (int j = 1; j < 32; ++j) a.add(fx::df{SS.h[lane][j], SS.l[lane][j]});
+      tot = a.value();
+    }
+    // output lane: 0 -> N, 1..5 -> means, 6..12 -> central moments
+    // (sum D_a D_b - sum D_a sum D_b / N) / N
+    const int q = lane - 6;
+    const int pa = q == 1 ? 1 : (q == 2 ? 2 : (q == 5 ? 1 : (q == 6 ? 3 : 0)));
+    const int pb = q == 0 ? 0 : (q == 1 ? 1 : (q == 2 ? 2 : (q == 3 ? 1 : (q == 6 ? 3 : 2))));
+    const float s2h = __shfl_sync(0xffffffffu, tot.h, q < 0 ? 0 : q);
+    const float s2l = __shfl_sync(0xffffffffu, tot.l, q < 0 ? 0 : q);
+    const float dah = __shfl_sync(0xffffffffu, tot.h, 7 + pa), dal = __shfl_sync(0xffffffffu, tot.l, 7 + pa);
+    const float dbh = __shfl_sync(0xffffffffu, tot.h, 7 + pb), dbl = __shfl_sync(0xffffffffu, tot.l, 7 + pb);
+    const float mh = __shfl_sync(0xffffffffu, mean.h, (lane + 31) & 31);
+    const float ml = __shfl_sync(0xffffffffu, mean.l, (lane + 31) & 31);
+    fx::df val = fx::df{mh, ml};
+    if (lane >= 6) {
+      const fx::df corr = fx::df_norm(fx::mul(fx::df_norm(fx::mul(fx::df{dah, dal}, fx::df{dbh, dbl})), invN));
+      val = fx::df_norm(fx::mul(fx::sub(fx::df{s2h, s2l}, corr), invN));
     }
     if (lane == 0) out[0] = (double)N;
     else if (lane < PDF_NES) out[lane] = __longlong_as_double((long long)fx::df2d(val));
