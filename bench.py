@@ -310,10 +310,15 @@ def run_gpu(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "hbm_frac_step": step_frac, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
             "roofline": roofline, "kernels": shares}
-    # the precision form (FP32 velocity/frequency/scalar state) on the same workload
+    # the complex-geometry workload (obstacles, FP32 state, 68.6M particles)
     if not args.skip_extras:
         del gp
         torch.cuda.empty_cache()
+        line["complex_geometry"] = run_obstacles(pg, torch, stream, steps=max(5, min(args.steps, 10)))
+        torch.cuda.empty_cache()
+        gp = None
+    # the precision form (FP32 velocity/frequency/scalar state) on the same workload
+    if not args.skip_extras:
         gq = pg.Particles(gm, seed, ppe=cfg["ppe"], u_sigma=cfg["u_sigma"], elem_psi0=psi,
                           precision=pg.capi.PDF_FP32_STATE)
         pg.pdf_estimate_stats(gq, gm)
@@ -359,6 +364,43 @@ def run_gpu(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def run_obstacles(pg, torch, stream, steps=10, name="obstacles_20x5_mean128"):
+    """Throughput of the complex-geometry workload: graded mesh around three
+    obstacles, particles per element proportional to area (mean 128), point
+    source, periodic inflow/outflow with re-injection, FP32 state."""
+    cfg = inputs.OBSTACLES[name]
+    t0 = time.perf_counter()
+    m = inputs.obstacle_mesh(h_min=cfg["h_min"], ratio=cfg["ratio"], growth=cfg["growth"])
+    counts = inputs.counts_by_area(m, cfg["mean_ppe"])
+    gm = pg.Mesh(m)
+    gp = pg.Particles(gm, cfg["seed"], count=counts, u_profile=cfg["u_profile"], u_sigma=cfg["u_sigma"],
+                      precision=pg.capi.PDF_FP32_STATE)
+    p = pg.model_params(dt=cfg["dt"], nu=cfg["nu"], Pi=cfg["Pi"], closure=cfg["closure"], tm_mode=cfg["tm_mode"],
+                        src_x=cfg["src"][0], src_y=cfg["src"][1], src_r=cfg["src"][2])
+    setup_s = time.perf_counter() - t0
+    pg.pdf_estimate_stats(gp, gm)
+    for s in range(3):
+        pg.pdf_step(gp, gm, p, step=s)
+        pg.pdf_estimate_stats(gp, gm)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(steps):
+        pg.pdf_step(gp, gm, p, step=3 + s, stream=stream)
+        pg.pdf_estimate_stats(gp, gm, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    info = pg.pdf_step(gp, gm, p, step=3 + steps, info=True)
+    n = gp.n
+    out = {"workload": name, "n_particles": n, "n_tri": gm.n_tri, "value": n / (ms * 1e-3), "unit": UNIT,
+           "ms_per_step": ms, "steps": steps, "setup_seconds": setup_s, "precision": "fp32_state",
+           "last_step_counters": info}
+    del gp, gm
+    return out
 
 
 def run_warmstart(args):

@@ -43,7 +43,12 @@ typedef enum {
 typedef struct pdf_mesh pdf_mesh;
 typedef struct pdf_particles pdf_particles;
 
-/* Boundary-edge tags (sec. 3.5: boundary neighbours are tagged). */
+/* Boundary-edge tags (sec. 3.5: boundary neighbours are tagged).  INFLOW and
+ * OUTFLOW edges whose nodes have periodic twins form a periodic pair for the
+ * particles' positions (the canyon case of ch. 5 imposes only periodicity on
+ * the streamwise positions); a particle leaving through an OUTFLOW edge
+ * re-enters as fresh fluid (its scalar is set to 0).  Without twins they are
+ * open boundaries and a particle crossing them is reported lost. */
 enum { PDF_TAG_WALL = 1, PDF_TAG_PERIODIC = 2, PDF_TAG_INFLOW = 3, PDF_TAG_OUTFLOW = 4 };
 
 /* Velocity closure.
@@ -55,8 +60,10 @@ enum { PDF_TAG_WALL = 1, PDF_TAG_PERIODIC = 2, PDF_TAG_INFLOW = 3, PDF_TAG_OUTFL
  * FROZEN: the caller supplies the element-average coefficient rows. */
 enum { PDF_CLOSURE_GLM = 0, PDF_CLOSURE_SLM = 1, PDF_CLOSURE_FROZEN = 2 };
 /* Micromixing time scale: TURB = max(k/eps, C_T sqrt(nu/eps)) (the turbulence
- * part of eq. micromixing-timescale-channel); CPHI = 2/(C_phi <omega>). */
-enum { PDF_TM_TURB = 0, PDF_TM_CPHI = 1 };
+ * part of eq. micromixing-timescale-channel); CPHI = 2/(C_phi <omega>);
+ * SOURCE = eq. micromixing-timescale-canyon, min(C_s (r0^2/eps)^(1/3) +
+ * C_t d/|<U>|, TURB) with d the node's distance to the source (src_*). */
+enum { PDF_TM_TURB = 0, PDF_TM_CPHI = 1, PDF_TM_SOURCE = 2 };
 /* Mean pressure gradient: NONE = 0; CHANNEL = imposed -d<P>/dx = Pi and the
  * cross-stream balance (1/rho) d<P>/dy = -d<v^2>/dy (eq. cross-stream-mean-
  * momentum-channel). */
@@ -94,16 +101,21 @@ typedef struct {
   /* model constants, table "Constants for modeling the joint PDF of velocity
    * and frequency" (ch. 4), and C0 of eq. wall-GandC */
   double C1, C2, C3, C4, CT, CL, Ceta, Cv, gamma5, Comega1, Comega2, C0_slm;
+  /* concentrated scalar source (ch. 4: particles passing through it get
+   * psi = 1): centre and radius; src_r = 0 disables it */
+  double src_x, src_y, src_r;
+  /* micromixing constants C_s, C_t of eq. micromixing-timescale-canyon */
+  double Cs, Ct;
 } pdf_model_params;
 
 /* Fills the paper's constants and dt = 1e-3, nu = 1e-3, Pi = 2e-3,
- * c_phi = 2, GLM, TURB, CHANNEL, ARITH_FX. */
+ * c_phi = 2, GLM, TURB, CHANNEL, ARITH_FX, no source, C_s = 0.02, C_t = 0.7. */
 void pdf_model_params_default(pdf_model_params* p);
 
 typedef struct {
   const int32_t* count;      /* host [n_tri]: particles per element, or NULL to use ppe */
   int32_t ppe;               /* particles per element when count == NULL */
-  int32_t u_profile;         /* 0: zero mean velocity; 1: channel profile U = 1 - y^2 */
+  int32_t u_profile;         /* 0: zero mean velocity; 1: channel profile U = 1 - y^2; 2: U = 1 */
   double u_sigma;            /* standard deviation of each velocity component */
   const double* elem_psi0;   /* host [n_tri]: initial scalar per element, or NULL for 0 */
 } pdf_init_params;
@@ -184,7 +196,9 @@ pdf_status pdf_particles_set_state(pdf_particles* p, const double* x, const doub
  *   frequency, eq. frequency-model (a negative result is reflected);
  *   scalar, eq. IEM;
  *   then the neighbour walk of sec. 3.5 with periodic seams and reflecting
- *   walls (position mirrored, wall-normal velocity reversed).
+ *   walls (position mirrored, wall-normal velocity reversed); a particle
+ *   that left through an outflow edge gets psi = 0, one inside the source
+ *   circle psi = 1.
  * Random numbers: Philox4x32-10 keyed by seed, counter (particle id, step,
  * block, 0), 6 Gaussians per particle (sec. 3.8 draws 6 per particle).
  * Coefficients: for GLM/SLM the element averages of the nodal coefficients

@@ -6,7 +6,8 @@ none of the method's arithmetic, so both the CUDA library and the CPU oracle
 consume exactly the same inputs without sharing any computation.
 """
 from .channel import channel_mesh, scalar_slab, TAG_WALL, TAG_PERIODIC, TAG_INFLOW, TAG_OUTFLOW
-from .configs import CONFIGS, workload
+from .configs import CONFIGS, OBSTACLES, workload
+from .obstacles import counts_by_area, obstacle_mesh
 
-__all__ = ["channel_mesh", "scalar_slab", "CONFIGS", "workload",
+__all__ = ["channel_mesh", "scalar_slab", "CONFIGS", "OBSTACLES", "workload", "obstacle_mesh", "counts_by_area",
            "TAG_WALL", "TAG_PERIODIC", "TAG_INFLOW", "TAG_OUTFLOW"]

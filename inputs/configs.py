@@ -28,6 +28,27 @@ CONFIGS = {
     "channel_200x400_ppe20": dict(CHANNEL_COMMON, nx=200, ny=400, ppe=20, steps=1000),
 }
 
+# Complex geometry: 20 x 5 domain, obstacles 1x1, 1x2, 0.5x1.5 on the bottom
+# wall, graded triangulation (535,720 triangles, 50:1 spacing), particles per
+# element proportional to its area with mean 128 (68.6M), a point source of
+# scalar at (2, 0.5) of radius 0.05 with the source-dependent micromixing
+# time, periodic inflow/outflow re-injecting clean fluid, FP32 velocity /
+# frequency / scalar state with FP64 positions.  Closure: the simplified
+# Langevin model (eq. wall-GandC): with counts proportional to area the
+# smallest wall elements hold a few particles, k -> 0 there and the GLM's
+# G = (wp - eps/2)/k is unbounded without particle redistribution.
+OBSTACLES = {
+    "obstacles_20x5_mean128": dict(mesh="obstacles", h_min=0.0025, ratio=37.0, growth=1.04, mean_ppe=128,
+                                   steps=2000, seed=1, dt=1e-3, nu=1e-3, Pi=2e-2, u_profile="uniform",
+                                   u_sigma=0.1, closure="slm", tm_mode="source", src=(2.0, 0.5, 0.05),
+                                   precision="fp32_state"),
+    # a small version for parity tests
+    "obstacles_small_mean20": dict(mesh="obstacles", h_min=0.05, ratio=6.0, growth=1.3, mean_ppe=20,
+                                   steps=30, seed=1, dt=2e-3, nu=1e-3, Pi=2e-2, u_profile="uniform",
+                                   u_sigma=0.1, closure="slm", tm_mode="source", src=(2.0, 0.5, 0.05),
+                                   precision="fp64"),
+}
+
 
 def workload(name):
     cfg = dict(CONFIGS[name])

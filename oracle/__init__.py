@@ -29,10 +29,10 @@ NND = 10   # node derivatives: dU/dx dU/dy dV/dx dV/dy dW/dx dW/dy lapU lapV lap
 NCOEF = 26
 
 CLOSURE = {"glm": 0, "slm": 1}
-TM_MODE = {"turb": 0, "cphi": 1}
+TM_MODE = {"turb": 0, "cphi": 1, "source": 2}
 PRESSURE = {"none": 0, "channel": 1}
 
-TRK_FALLBACK, TRK_BRUTE, TRK_LOST, TRK_EXIT_OUT, TRK_EXIT_IN, TRK_NEAR_FACE = 1, 2, 4, 8, 16, 256
+TRK_FALLBACK, TRK_BRUTE, TRK_LOST, TRK_EXIT_OUT, TRK_EXIT_IN, TRK_REINJECT, TRK_NEAR_FACE = 1, 2, 4, 8, 16, 32, 256
 
 
 def build(force=False):
@@ -51,7 +51,8 @@ def build(force=False):
 class _Params(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("nu", ctypes.c_double), ("Pi", ctypes.c_double),
                 ("c_phi", ctypes.c_double), ("closure", ctypes.c_int), ("tm_mode", ctypes.c_int),
-                ("pressure", ctypes.c_int)]
+                ("pressure", ctypes.c_int), ("src_x", ctypes.c_double), ("src_y", ctypes.c_double),
+                ("src_r", ctypes.c_double)]
 
 
 def _p(a, ct):
@@ -98,7 +99,7 @@ def lib():
             L.or_shape_derivs.argtypes = [ctypes.c_void_p, I, PD, PD]
             L.or_node_derivs.argtypes = [ctypes.c_void_p, PD, PD]
             L.or_relax_rhs.argtypes = [PD, PD, PD]
-            L.or_node_coeff.argtypes = [PD, PD, PD, ctypes.POINTER(_Params), PD]
+            L.or_node_coeff.argtypes = [PD, PD, PD, ctypes.POINTER(_Params), PD, PD]
             L.or_elem_coeff.argtypes = [ctypes.c_void_p, PD, PD, PD, ctypes.POINTER(_Params), PD]
             L.or_step.argtypes = [ctypes.c_void_p, ctypes.c_long, PD, ctypes.POINTER(_Params),
                                   ctypes.c_uint64, U32, PD, PD, PD, PD, PD, PD, PD, PI, PI, PL, PI]
@@ -208,13 +209,16 @@ class Mesh:
 STATE_KEYS = ("x", "y", "u", "v", "w", "om", "ps")
 
 
+U_PROFILE = {"zero": 0, "parabola": 1, "uniform": 2}
+
+
 def init(mesh, counts, seed, u_profile="parabola", u_sigma=0.1, elem_psi0=None):
     counts = np.ascontiguousarray(counts, dtype=np.int32)
     n = int(counts.sum())
     st = {k: np.zeros(n) for k in STATE_KEYS}
     st["elem"] = np.zeros(n, dtype=np.int32)
     psi0 = None if elem_psi0 is None else np.ascontiguousarray(elem_psi0, dtype=np.float64)
-    lib().or_init(mesh._h, _p(counts, I), int(seed), 1 if u_profile == "parabola" else 0,
+    lib().or_init(mesh._h, _p(counts, I), int(seed), U_PROFILE[u_profile],
                   float(u_sigma), None if psi0 is None else _p(psi0, D),
                   *[_p(st[k], D) for k in STATE_KEYS], _p(st["elem"], I))
     return st
@@ -242,8 +246,10 @@ def node_derivs(mesh, ns):
     return nd
 
 
-def make_params(dt, nu, Pi=0.0, closure="glm", tm_mode="turb", c_phi=2.0, pressure="channel"):
-    return _Params(dt, nu, Pi, c_phi, CLOSURE[closure], TM_MODE[tm_mode], PRESSURE[pressure])
+def make_params(dt, nu, Pi=0.0, closure="glm", tm_mode="turb", c_phi=2.0, pressure="channel",
+                src=(0.0, 0.0, 0.0)):
+    return _Params(dt, nu, Pi, c_phi, CLOSURE[closure], TM_MODE[tm_mode], PRESSURE[pressure],
+                   float(src[0]), float(src[1]), float(src[2]))
 
 
 def relax_rhs(S, Dv):
@@ -254,13 +260,14 @@ def relax_rhs(S, Dv):
     return out
 
 
-def node_coeff(S, Dv, wp, params):
+def node_coeff(S, Dv, wp, params, xy=(0.0, 0.0)):
     out = np.zeros(NCOEF)
     S = np.ascontiguousarray(S, dtype=np.float64)
     Dv = np.ascontiguousarray(Dv, dtype=np.float64)
     w = None if wp is None else np.ascontiguousarray(wp, dtype=np.float64)
+    P = np.ascontiguousarray(xy, dtype=np.float64)
     lib().or_node_coeff(_p(S, D), _p(Dv, D), None if w is None else _p(w, D),
-                        ctypes.byref(params), _p(out, D))
+                        ctypes.byref(params), _p(P, D), _p(out, D))
     return out
 
 

@@ -164,6 +164,7 @@ typedef struct {
   double* area;    /* A_e */
   int* nbr;        /* [n_tri][3] neighbour across the edge opposite vertex k */
   int* shift;      /* [n_tri][3] periodic shift (multiples of period) of x when crossing */
+  int* reinj;      /* [n_tri][3] 1 if crossing this edge leaves through the outflow */
   int* esup_off;   /* node -> elements containing the node (ascending ids) */
   int* esup;
   int* nse_off;    /* node -> elements around the node or its twin (ascending ids) */
@@ -190,7 +191,7 @@ static int edge_tag(int n_bnd, const int* bnd, int a, int b) {
 
 void or_mesh_free(or_mesh* m) {
   if (!m) return;
-  free(m->xy); free(m->tri); free(m->twin); free(m->area); free(m->nbr); free(m->shift);
+  free(m->xy); free(m->tri); free(m->twin); free(m->area); free(m->nbr); free(m->shift); free(m->reinj);
   free(m->esup_off); free(m->esup); free(m->nse_off); free(m->nse);
   free(m);
 }
@@ -249,6 +250,7 @@ or_mesh* or_mesh_create(int n_nodes, const double* xy, int n_tri, const int* tri
   /* element-surrounding-element list; edge k is opposite local vertex k */
   m->nbr = (int*)malloc(sizeof(int) * 3 * n_tri);
   m->shift = (int*)calloc(3 * n_tri, sizeof(int));
+  m->reinj = (int*)calloc(3 * n_tri, sizeof(int));
   for (int e = 0; e < n_tri; ++e) {
     for (int k = 0; k < 3; ++k) {
       int a = m->tri[3 * e + (k + 1) % 3], b = m->tri[3 * e + (k + 2) % 3];
@@ -259,10 +261,16 @@ or_mesh* or_mesh_create(int n_nodes, const double* xy, int n_tri, const int* tri
       }
       if (found >= 0) { m->nbr[3 * e + k] = found; continue; }
       int tag = edge_tag(n_bnd, bnd, a, b);
+      /* READING (the paper's canyon, ch. 5): inflow and outflow edges whose
+       * nodes have periodic twins form a periodic pair for the particles'
+       * positions; leaving through the outflow marks the particle as
+       * re-entering fluid.  Without twins they are open boundaries. */
+      int open_pair = (tag == OR_TAG_INFLOW || tag == OR_TAG_OUTFLOW) && m->twin[a] >= 0 && m->twin[b] >= 0;
       if (tag == OR_TAG_WALL) m->nbr[3 * e + k] = OR_NBR_WALL;
-      else if (tag == OR_TAG_INFLOW) m->nbr[3 * e + k] = OR_NBR_INFLOW;
-      else if (tag == OR_TAG_OUTFLOW) m->nbr[3 * e + k] = OR_NBR_OUTFLOW;
-      else if (tag == OR_TAG_PERIODIC) {
+      else if (tag == OR_TAG_INFLOW && !open_pair) m->nbr[3 * e + k] = OR_NBR_INFLOW;
+      else if (tag == OR_TAG_OUTFLOW && !open_pair) m->nbr[3 * e + k] = OR_NBR_OUTFLOW;
+      else if (tag == OR_TAG_PERIODIC || open_pair) {
+        if (tag == OR_TAG_OUTFLOW) m->reinj[3 * e + k] = 1;
         int ta = m->twin[a], tb = m->twin[b];
         if (ta < 0 || tb < 0) { or_mesh_free(m); return NULL; }
         for (int i = m->esup_off[ta]; i < m->esup_off[ta + 1]; ++i) {
@@ -307,7 +315,8 @@ void or_subareas(const or_mesh* m, int e, double px, double py, double N[3]) {
 static int or_inside(const double N[3]) { return N[0] >= 0.0 && N[1] >= 0.0 && N[2] >= 0.0; }
 
 /* Tracking status bits (returned per particle). */
-enum { OR_TRK_FALLBACK = 1, OR_TRK_BRUTE = 2, OR_TRK_LOST = 4, OR_TRK_EXIT_OUT = 8, OR_TRK_EXIT_IN = 16 };
+enum { OR_TRK_FALLBACK = 1, OR_TRK_BRUTE = 2, OR_TRK_LOST = 4, OR_TRK_EXIT_OUT = 8, OR_TRK_EXIT_IN = 16,
+       OR_TRK_REINJECT = 32 };
 
 typedef struct { int walk_steps, reflections, crossings_periodic, status; double min_rel; } or_track_info;
 
@@ -358,6 +367,7 @@ int or_track(const or_mesh* m, int e0, double* px, double* py, double* u, double
         x += m->shift[3 * e + k] * m->period;
         info->crossings_periodic++;
       }
+      if (m->reinj[3 * e + k]) info->status |= OR_TRK_REINJECT;
       e = nb;
       continue;
     }
@@ -420,7 +430,7 @@ int or_locate_brute(const or_mesh* m, double x, double y) {
 /*   block 1: Gaussians g2..g5 (g2 used)                                      */
 /*   block 2: four uniforms; omega = -theta * sum ln u_i: Gamma(k=4, theta)   */
 /*            (sum of 4 exponentials), theta = 1/4: mean 1, variance 1/4.     */
-/* u_profile 1: mean U = 1 - y^2 (channel); 0: zero mean.                     */
+/* u_profile 1: mean U = 1 - y^2 (channel); 2: uniform U = 1; 0: zero mean.   */
 /* ------------------------------------------------------------------------ */
 void or_init(const or_mesh* m, const int* count, uint64_t seed, int u_profile, double u_sigma,
              const double* elem_psi0, double* x, double* y, double* u, double* v, double* w,
@@ -449,7 +459,7 @@ void or_init(const or_mesh* m, const int* count, uint64_t seed, int u_profile, d
       double R1 = (double)r1, R2 = (double)r2;
       x[p] = xa + R1 * (xb - xa) + R2 * (xc - xa);
       y[p] = ya + R1 * (yb - ya) + R2 * (yc - ya);
-      double umean = (u_profile == 1) ? 1.0 - y[p] * y[p] : 0.0;
+      double umean = (u_profile == 1) ? 1.0 - y[p] * y[p] : (u_profile == 2 ? 1.0 : 0.0);
       u[p] = umean + u_sigma * (double)g[0];
       v[p] = u_sigma * (double)g[1];
       w[p] = u_sigma * (double)g[2];
@@ -592,10 +602,14 @@ enum { OR_CLOSURE_GLM = 0, OR_CLOSURE_SLM = 1 };
 enum { OR_TM_TURB = 0, OR_TM_CPHI = 1 };
 enum { OR_PRESSURE_NONE = 0, OR_PRESSURE_CHANNEL = 1 };
 
+enum { OR_TM_SOURCE = 2 };
 typedef struct {
   double dt, nu, Pi, c_phi;
   int closure, tm_mode, pressure;
+  double src_x, src_y, src_r;  /* point source (src_r > 0: particles inside get psi = 1) */
 } or_params;
+/* micromixing constants of the concentrated-source form (table of constants, ch. 5) */
+static const double OR_CS = 0.02, OR_CTT = 0.7;
 
 /* Right-hand side of the elliptic relaxation equation (eq. elliptic-
  * relaxation-Lagrangian): (1-C1)/2 k<omega> delta_ij + k H_ijkl d<U_k>/dx_l
@@ -651,7 +665,7 @@ void or_relax_rhs(const double* S /*12 node stats*/, const double* D /*node deri
  * wp: the 9 node values of the elliptic-relaxation tensor, or NULL for the
  * local model (wp = right-hand side, elliptic term dropped). */
 void or_node_coeff(const double* S, const double* D, const double* wp_in, const or_params* P,
-                   double* c) {
+                   const double* xy, double* c) {
   double k = 0.5 * (S[5] + S[6] + S[7]);
   double kg = k > OR_KFLOOR ? k : OR_KFLOOR;
   double om = S[3];
@@ -690,7 +704,18 @@ void or_node_coeff(const double* S, const double* D, const double* wp_in, const 
     c[25] = 0.5 * P->c_phi * om;
   } else {
     double t1 = kg / eg, t2 = OR_CT * sqrt(P->nu / eg);
-    c[25] = 1.0 / (t1 > t2 ? t1 : t2);
+    double tm = t1 > t2 ? t1 : t2;
+    if (P->tm_mode == OR_TM_SOURCE) {
+      /* eq. micromixing-timescale-canyon: min(C_s (r0^2/eps)^(1/3) + C_t d/U_c, tm);
+       * U_c = |<U>| at the node (READING: floored at 1e-12), d its distance to the source */
+      double dx = xy[0] - P->src_x, dy = xy[1] - P->src_y;
+      double d = sqrt(dx * dx + dy * dy);
+      double uc = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+      if (uc < 1e-12) uc = 1e-12;
+      double ts = OR_CS * cbrt(P->src_r * P->src_r / eg) + OR_CTT * d / uc;
+      if (ts < tm) tm = ts;
+    }
+    c[25] = 1.0 / tm;
   }
 }
 
@@ -704,7 +729,7 @@ void or_elem_coeff(const or_mesh* m, const double* ns, const double* nd, const d
   for (int n = 0; n < m->n_nodes; ++n) {
     double w9[9];
     if (wp) for (int i = 0; i < 9; ++i) w9[i] = wp[(long)i * m->n_nodes + n];
-    or_node_coeff(ns + OR_NNS * n, nd + OR_NND * n, wp ? w9 : NULL, P, nc + OR_NCOEF * n);
+    or_node_coeff(ns + OR_NNS * n, nd + OR_NND * n, wp ? w9 : NULL, P, m->xy + 2 * n, nc + OR_NCOEF * n);
   }
   for (int e = 0; e < m->n_tri; ++e)
     for (int q = 0; q < OR_NCOEF; ++q) {
@@ -777,6 +802,11 @@ void or_step(const or_mesh* m, long n_p, const double* rows, const or_params* P,
     if (ti.status & OR_TRK_LOST) counters[5]++;
     if (!(ti.status & OR_TRK_LOST) && ti.min_rel < 1e-12) counters[7]++;
     if (status_out) status_out[p] = ti.status | ((ti.min_rel < 1e-12) ? 256 : 0);
+    /* READING: fluid re-entering through the inflow carries no scalar */
+    if (ti.status & OR_TRK_REINJECT) pn = 0.0;
+    /* the concentrated source (ch. 4): particles inside it get psi = 1 */
+    if (P->src_r > 0.0 && (xn - P->src_x) * (xn - P->src_x) + (yn - P->src_y) * (yn - P->src_y) <= P->src_r * P->src_r)
+      pn = 1.0;
     x[p] = xn; y[p] = yn; u[p] = Un[0]; v[p] = Un[1]; w[p] = Un[2];
     om[p] = on; ps[p] = pn;
     if (!(ti.status & OR_TRK_LOST)) elem[p] = en;

@@ -38,7 +38,7 @@ def model_params(**kw):
     "cphi"; "none", "channel")."""
     p = capi.ModelParams()
     lib().pdf_model_params_default(ctypes.byref(p))
-    names = {"closure": {"glm": 0, "slm": 1, "frozen": 2}, "tm_mode": {"turb": 0, "cphi": 1},
+    names = {"closure": {"glm": 0, "slm": 1, "frozen": 2}, "tm_mode": {"turb": 0, "cphi": 1, "source": 2},
              "pressure": {"none": 0, "channel": 1}, "arith": {"fx": 0, "fp64": 1}}
     for k, v in kw.items():
         if k in names and isinstance(v, str):
@@ -103,7 +103,8 @@ class Particles:
             keep.append(c)
             ip.count = c.ctypes.data_as(capi.PI32)
         ip.ppe = int(ppe or 0)
-        ip.u_profile = {"zero": 0, "parabola": 1}[u_profile] if isinstance(u_profile, str) else int(u_profile)
+        ip.u_profile = ({"zero": 0, "parabola": 1, "uniform": 2}[u_profile] if isinstance(u_profile, str)
+                        else int(u_profile))
         ip.u_sigma = float(u_sigma)
         if elem_psi0 is not None:
             ps = np.ascontiguousarray(elem_psi0, dtype=np.float64)

@@ -10,7 +10,7 @@ STATUS_NAMES = ["PDF_OK", "PDF_EINVAL", "PDF_ENOMEM", "PDF_ECUDA", "PDF_ELOST", 
                 "PDF_ENUMERIC", "PDF_ESTATE"]
 PDF_TAG_WALL, PDF_TAG_PERIODIC, PDF_TAG_INFLOW, PDF_TAG_OUTFLOW = 1, 2, 3, 4
 PDF_CLOSURE_GLM, PDF_CLOSURE_SLM, PDF_CLOSURE_FROZEN = 0, 1, 2
-PDF_TM_TURB, PDF_TM_CPHI = 0, 1
+PDF_TM_TURB, PDF_TM_CPHI, PDF_TM_SOURCE = 0, 1, 2
 PDF_PRESSURE_NONE, PDF_PRESSURE_CHANNEL = 0, 1
 PDF_FP64, PDF_FP32_STATE = 0, 1
 PDF_ARITH_FX, PDF_ARITH_FP64 = 0, 1
@@ -31,7 +31,7 @@ class ModelParams(ctypes.Structure):
                 ("c_phi", ctypes.c_double), ("closure", ctypes.c_int32), ("tm_mode", ctypes.c_int32),
                 ("pressure", ctypes.c_int32), ("arith", ctypes.c_int32)] + [
         (n, ctypes.c_double) for n in ("C1", "C2", "C3", "C4", "CT", "CL", "Ceta", "Cv", "gamma5",
-                                       "Comega1", "Comega2", "C0_slm")]
+                                       "Comega1", "Comega2", "C0_slm", "src_x", "src_y", "src_r", "Cs", "Ct")]
 
 
 class InitParams(ctypes.Structure):

@@ -39,4 +39,7 @@ extern "C" void pdf_model_params_default(pdf_model_params* p) {
   p->Ceta = 72.0; p->Cv = 1.4; p->gamma5 = 0.1; p->Comega1 = 0.5; p->Comega2 = 0.73;
   // eq. wall-GandC
   p->C0_slm = 3.5;
+  // concentrated source: none; micromixing constants of the table of constants (ch. 5)
+  p->src_x = 0.0; p->src_y = 0.0; p->src_r = 0.0;
+  p->Cs = 0.02; p->Ct = 0.7;
 }

@@ -41,7 +41,7 @@ struct __align__(16) ElemGeo {
   double two_area;  // 2 A_e
   int32_t nbr[3];   // neighbour across the edge opposite A, B, C
   int8_t shift[3];  // periodic x-shift multipliers for those crossings
-  int8_t pad[1];
+  uint8_t reinj;    // bit k: crossing edge k leaves through the outflow
 };
 static_assert(sizeof(ElemGeo) == 80, "ElemGeo layout");
 
@@ -52,7 +52,7 @@ struct __align__(16) FxGeo {
   fx::df cbx, cby, abx, aby, two_area;
   int32_t nbr[3];
   int8_t shift[3];
-  int8_t pad;
+  uint8_t reinj;
 };
 static_assert(sizeof(FxGeo) == 80, "FxGeo layout");
 
@@ -118,7 +118,7 @@ struct pdf_mesh {
   std::vector<double> wall_d, wall_n;
   // host copies
   std::vector<double> xy;
-  std::vector<int32_t> tri, nbr, shift, twin;
+  std::vector<int32_t> tri, nbr, shift, twin, reinj;
   std::vector<double> area;
 };
 

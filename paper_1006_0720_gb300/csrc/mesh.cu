@@ -32,7 +32,8 @@ static void free_relax(RelaxMesh& r) {
 // consistent mass, per-entry stiffness contributions (element order), wall
 // flags and the outward normal of the nearest wall edge at every node.
 static pdf_status build_relax(pdf_mesh* m, const std::vector<int32_t>& bnd_wall, const std::vector<double>& dN,
-                              const std::vector<int32_t>& nse_off, const std::vector<int32_t>& nse) {
+                              const std::vector<int32_t>& nse_off, const std::vector<int32_t>& nse,
+                              const std::vector<int32_t>& esup_off, const std::vector<int32_t>& esup) {
   const int32_t nn = m->d.n_nodes, nt = m->d.n_tri;
   const int32_t* T = m->tri.data();
   const double* X = m->xy.data();
@@ -56,7 +57,8 @@ static pdf_status build_relax(pdf_mesh* m, const std::vector<int32_t>& bnd_wall,
     const double len = std::sqrt(tx * tx + ty * ty);
     double nx = ty / len, ny = -tx / len;
     // point away from the element holding the edge
-    for (int32_t e = 0; e < nt; ++e) {
+    for (int32_t i = esup_off[a]; i < esup_off[a + 1]; ++i) {
+      const int32_t e = esup[i];
       const int32_t* t = T + 3 * e;
       const bool ha = t[0] == a || t[1] == a || t[2] == a, hb = t[0] == b || t[1] == b || t[2] == b;
       if (!(ha && hb)) continue;
@@ -207,6 +209,7 @@ extern "C" pdf_status pdf_mesh_create(const double* node_xy, int32_t n_nodes, co
   first.reserve((size_t)n_tri * 2);
   m->nbr.assign(3 * (size_t)n_tri, INT32_MIN);
   m->shift.assign(3 * (size_t)n_tri, 0);
+  m->reinj.assign(3 * (size_t)n_tri, 0);
   for (int32_t e = 0; e < n_tri; ++e) {
     for (int k = 0; k < 3; ++k) {
       const int32_t a = T[3 * e + (k + 1) % 3], b = T[3 * e + (k + 2) % 3];
@@ -230,7 +233,15 @@ extern "C" pdf_status pdf_mesh_create(const double* node_xy, int32_t n_nodes, co
       const int32_t a = T[3 * e + (k + 1) % 3], b = T[3 * e + (k + 2) % 3];
       auto t = tags.find(edge_key(a, b));
       if (t == tags.end()) { delete m; return fail(PDF_EINVAL, "pdf_mesh_create: untagged boundary edge"); }
-      switch (t->second) {
+      // inflow/outflow edges whose nodes have periodic twins form a periodic
+      // pair for the positions; leaving through the outflow re-injects
+      int tag = t->second;
+      const bool pair = (tag == PDF_TAG_INFLOW || tag == PDF_TAG_OUTFLOW) && m->twin[a] >= 0 && m->twin[b] >= 0;
+      if (pair) {
+        if (tag == PDF_TAG_OUTFLOW) m->reinj[3 * e + k] = 1;
+        tag = PDF_TAG_PERIODIC;
+      }
+      switch (tag) {
         case PDF_TAG_WALL: m->nbr[3 * e + k] = kNbrWall; break;
         case PDF_TAG_INFLOW: m->nbr[3 * e + k] = kNbrInflow; break;
         case PDF_TAG_OUTFLOW: m->nbr[3 * e + k] = kNbrOutflow; break;
@@ -252,6 +263,7 @@ extern "C" pdf_status pdf_mesh_create(const double* node_xy, int32_t n_nodes, co
     for (int k = 0; k < 3; ++k) {
       geo[e].nbr[k] = m->nbr[3 * e + k];
       geo[e].shift[k] = (int8_t)m->shift[3 * e + k];
+      if (m->reinj[3 * e + k]) geo[e].reinj |= (uint8_t)(1u << k);
     }
   // the fixed-point copy for the FP64-free walk
   std::vector<FxGeo> fgeo(n_tri);
@@ -266,6 +278,7 @@ extern "C" pdf_status pdf_mesh_create(const double* node_xy, int32_t n_nodes, co
     f.abx = fx::d2df(bits(g.abx)); f.aby = fx::d2df(bits(g.aby));
     f.two_area = fx::d2df(bits(g.two_area));
     for (int k = 0; k < 3; ++k) { f.nbr[k] = g.nbr[k]; f.shift[k] = g.shift[k]; }
+    f.reinj = g.reinj;
     if (std::fabs(g.xb) >= 63.0 || std::fabs(g.yb) >= 63.0) {
       delete m;
       return fail(PDF_EINVAL, "pdf_mesh_create: node coordinates must lie within |x|, |y| < 63");
@@ -315,7 +328,7 @@ extern "C" pdf_status pdf_mesh_create(const double* node_xy, int32_t n_nodes, co
     delete m;
     return s;
   }
-  if ((s = build_relax(m, bnd_wall, dN, nse_off, nse)) != PDF_OK) {
+  if ((s = build_relax(m, bnd_wall, dN, nse_off, nse, esup_off, esup)) != PDF_OK) {
     free_mesh_dev(d);
     delete m;
     return s;

@@ -58,7 +58,7 @@ __global__ void k_init(const double* __restrict__ xy, const int32_t* __restrict_
                                 __dmul_rn(R2, __dsub_rn(xc, xa)));
     const double py = __dadd_rn(__dadd_rn(ya, __dmul_rn(R1, __dsub_rn(yb, ya))),
                                 __dmul_rn(R2, __dsub_rn(yc, ya)));
-    const double umean = (u_profile == 1) ? __dsub_rn(1.0, __dmul_rn(py, py)) : 0.0;
+    const double umean = (u_profile == 1) ? __dsub_rn(1.0, __dmul_rn(py, py)) : (u_profile == 2 ? 1.0 : 0.0);
     x[p] = px;
     y[p] = py;
     const double U = __dadd_rn(umean, __dmul_rn(u_sigma, (double)g[0]));

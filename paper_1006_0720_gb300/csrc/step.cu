@@ -15,6 +15,7 @@ namespace pdfgb {
 struct CoeffParams {
   double dt, nu, Pi, c_phi;
   int closure, tm_mode, pressure, arith;
+  double src_x, src_y, src_r, Cs, Ct;
   double C1, C2, C3, C4, CT, Cv, gamma5, Comega1, Comega2, C0_slm;
 };
 
@@ -24,6 +25,7 @@ static CoeffParams coeff_params(const pdf_model_params* p) {
   c.closure = p->closure; c.tm_mode = p->tm_mode; c.pressure = p->pressure; c.arith = p->arith;
   c.C1 = p->C1; c.C2 = p->C2; c.C3 = p->C3; c.C4 = p->C4; c.CT = p->CT; c.Cv = p->Cv;
   c.gamma5 = p->gamma5; c.Comega1 = p->Comega1; c.Comega2 = p->Comega2; c.C0_slm = p->C0_slm;
+  c.src_x = p->src_x; c.src_y = p->src_y; c.src_r = p->src_r; c.Cs = p->Cs; c.Ct = p->Ct;
   return c;
 }
 
@@ -65,7 +67,8 @@ __device__ void relax_rhs(const double* S, const double* D, const CoeffParams& P
 // (SLM); G_ij (eq. GandC or eq. wall-GandC); sqrt(C0 eps); <omega>; S_omega
 // (eq. frequency-source); <phi>; 1/t_m.
 __global__ void k_node_coeff(int32_t n_nodes, const double* __restrict__ ns, const double* __restrict__ nd,
-                             const double* __restrict__ wp, CoeffParams P, double* __restrict__ nc) {
+                             const double* __restrict__ wp, const double* __restrict__ xy, CoeffParams P,
+                             double* __restrict__ nc) {
   for (int32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < n_nodes; n += gridDim.x * blockDim.x) {
     double S[PDF_NNS], D[PDF_NND];
     for (int q = 0; q < PDF_NNS; ++q) S[q] = ns[(int64_t)n * PDF_NNS + q];
@@ -109,7 +112,15 @@ __global__ void k_node_coeff(int32_t n_nodes, const double* __restrict__ ns, con
     if (P.tm_mode == PDF_TM_CPHI) {
       c[25] = 0.5 * P.c_phi * om;
     } else {
-      c[25] = 1.0 / fmax(kg / eg, P.CT * sqrt(P.nu / eg));
+      double tm = fmax(kg / eg, P.CT * sqrt(P.nu / eg));
+      if (P.tm_mode == PDF_TM_SOURCE) {
+        // eq. micromixing-timescale-canyon: the source term, U_c = |<U>| at the node
+        const double dx = xy[2 * n] - P.src_x, dy = xy[2 * n + 1] - P.src_y;
+        const double d = sqrt(dx * dx + dy * dy);
+        const double uc = fmax(sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]), 1e-12);
+        tm = fmin(tm, P.Cs * cbrt(P.src_r * P.src_r / eg) + P.Ct * d / uc);
+      }
+      c[25] = 1.0 / tm;
     }
   }
 }
@@ -212,6 +223,7 @@ struct StepArgs {
   uint64_t seed;
   uint32_t step;
   long long* counters;
+  double src_x, src_y, src_r;  // concentrated source (src_r > 0)
 };
 
 enum { kCntWalk = 0, kCntRefl, kCntPeriodic, kCntFallback, kCntBrute, kCntLost, kCntOmega, kCntNear };
@@ -242,6 +254,7 @@ __device__ __forceinline__ ElemGeo load_geo(const ElemGeo* geo, int32_t e) {
   g.shift[0] = (int8_t)(sh & 0xff);
   g.shift[1] = (int8_t)((sh >> 8) & 0xff);
   g.shift[2] = (int8_t)((sh >> 16) & 0xff);
+  g.reinj = (uint8_t)((sh >> 24) & 0xff);
   return g;
 }
 
@@ -249,7 +262,8 @@ __device__ __forceinline__ ElemGeo load_geo(const ElemGeo* geo, int32_t e) {
 // (or -1 if lost); updates x, y (periodic shifts, wall mirror) and u, v
 // (wall-normal component reversed on reflection).
 __device__ int32_t walk(const StepArgs& A, int32_t e, double& x, double& y, double& u, double& v,
-                        int& c_walk, int& c_refl, int& c_per, int& c_fb, int& c_brute, int& c_near) {
+                        int& c_walk, int& c_refl, int& c_per, int& c_fb, int& c_brute, int& c_near,
+                        bool& reinj) {
   int steps = 0, refl = 0;
   for (;;) {
     ElemGeo g = load_geo(A.geo, e);
@@ -285,6 +299,7 @@ __device__ int32_t walk(const StepArgs& A, int32_t e, double& x, double& y, doub
         x += (double)g.shift[k] * A.period;
         ++c_per;
       }
+      if (g.reinj & (1u << k)) reinj = true;
       e = nbr;
       continue;
     }
@@ -328,6 +343,15 @@ __device__ int32_t walk(const StepArgs& A, int32_t e, double& x, double& y, doub
   }
   c_walk += steps;
   return e;
+}
+
+// The scalar after the move: fluid re-entering through the inflow carries
+// none, particles inside the concentrated source get 1 (the test is the
+// oracle's FP64 expression, rounded the same way).
+__device__ __forceinline__ bool in_source(const StepArgs& A, double x, double y) {
+  if (!(A.src_r > 0.0)) return false;
+  const double dx = __dsub_rn(x, A.src_x), dy = __dsub_rn(y, A.src_y);
+  return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= __dmul_rn(A.src_r, A.src_r);
 }
 
 __device__ __forceinline__ void add_counter(long long* c, int v) {
@@ -385,8 +409,11 @@ __device__ __noinline__ Counts advance_native(const StepArgs& A, int64_t p, cons
   // scalar (eq. IEM)
   const double s = A.ps[p];
   const double sn = s - (s - __ldg(R + 26)) * __ldg(R + 27);
-  const int32_t en = walk(A, e, xn, yn, un, vn, c.walk, c.refl, c.per, c.fb, c.brute, c.near);
-  A.x[p] = xn; A.y[p] = yn; A.u[p] = un; A.v[p] = vn; A.w[p] = wn; A.om[p] = on; A.ps[p] = sn;
+  bool reinj = false;
+  const int32_t en = walk(A, e, xn, yn, un, vn, c.walk, c.refl, c.per, c.fb, c.brute, c.near, reinj);
+  double sf = reinj ? 0.0 : sn;
+  if (in_source(A, xn, yn)) sf = 1.0;
+  A.x[p] = xn; A.y[p] = yn; A.u[p] = un; A.v[p] = vn; A.w[p] = wn; A.om[p] = on; A.ps[p] = sf;
   if (en >= 0) A.elem[p] = en; else ++c.lost;
   return c;
 }
@@ -501,7 +528,7 @@ __device__ __forceinline__ bool inside_certain(const FxGeo& g, int64_t X, int64_
 // Fixed-point neighbour walk; returns true when the FP64 walk must finish it
 // (a wall or open-boundary edge, or the 64-step cap).
 __device__ __forceinline__ bool walk_fx(const FxArgs& F, int32_t& e, int64_t& Xn, int64_t Yn, int& steps, int& c_per,
-                                        int& c_near) {
+                                        int& c_near, bool& reinj) {
   for (;;) {
     const FxGeo G = load_fx_geo(F.geo, e);
     if (inside_certain(G, Xn, Yn)) return false;
@@ -524,13 +551,14 @@ __device__ __forceinline__ bool walk_fx(const FxArgs& F, int32_t& e, int64_t& Xn
       Xn += (int64_t)G.shift[k] * F.period_fix;
       ++c_per;
     }
+    if (G.reinj & (1u << k)) reinj = true;
     e = nbr;
   }
 }
 
 __device__ __noinline__ int32_t walk_slow(const StepArgs& A, int32_t e, double& x, double& y, double& u,
-                                          double& v, Counts& c) {
-  return walk(A, e, x, y, u, v, c.walk, c.refl, c.per, c.fb, c.brute, c.near);
+                                          double& v, Counts& c, bool& reinj) {
+  return walk(A, e, x, y, u, v, c.walk, c.refl, c.per, c.fb, c.brute, c.near, reinj);
 }
 
 __global__ void __launch_bounds__(256) k_step_fx(StepArgs A, FxArgs F) {
@@ -610,23 +638,26 @@ __global__ void __launch_bounds__(256) k_step_fx(StepArgs A, FxArgs F) {
     // neighbour walk (sec. 3.5) in fixed point; walls, open boundaries and
     // the step cap go to the FP64 walk
     int steps = 0;
-    const bool slow = walk_fx(F, e, Xn, Yn, steps, c_per, c_near);
+    bool reinj = false;
+    const bool slow = walk_fx(F, e, Xn, Yn, steps, c_per, c_near, reinj);
     c_walk += steps;
     double xn = __longlong_as_double((long long)fx::fix2d(Xn, kF));
     double yn = __longlong_as_double((long long)fx::fix2d(Yn, kF));
     double un = __longlong_as_double((long long)fx::fix2d(Un[0], kF));
     double vn = __longlong_as_double((long long)fx::fix2d(Un[1], kF));
     if (slow) {
-      const int32_t en = walk_slow(A, e, xn, yn, un, vn, cs);
+      const int32_t en = walk_slow(A, e, xn, yn, un, vn, cs, reinj);
       if (en >= 0) e = en; else { ++cs.lost; e = A.elem[p]; }
     }
+    double sf = reinj ? 0.0 : __longlong_as_double((long long)fx::fix2d(Sn, kF));
+    if (in_source(A, xn, yn)) sf = 1.0;
     A.x[p] = xn;
     A.y[p] = yn;
     A.u[p] = un;
     A.v[p] = vn;
     A.w[p] = __longlong_as_double((long long)fx::fix2d(Un[2], kF));
     A.om[p] = __longlong_as_double((long long)fx::fix2d(On, kFO));
-    A.ps[p] = __longlong_as_double((long long)fx::fix2d(Sn, kF));
+    A.ps[p] = sf;
     A.elem[p] = e;
   }
   cs.walk += c_walk; cs.per += c_per; cs.om += c_om; cs.near += c_near;
@@ -673,7 +704,7 @@ __global__ void __launch_bounds__(256) k_step_f32(StepArgs A, FxArgs F, F32Args 
     const uint64_t bx = (uint64_t)__double_as_longlong(A.x[p]);
     const uint64_t by = (uint64_t)__double_as_longlong(A.y[p]);
     double xn, yn, ud = (double)un, vd = (double)vn;
-    bool slow;
+    bool slow, reinj = false;
     if (fx::d_exp(bx) <= kExpMax && fx::d_exp(by) <= kExpMax) {
       fx::acc a;
       a.init(fx::mul_f(F.dt, U0));
@@ -684,7 +715,7 @@ __global__ void __launch_bounds__(256) k_step_f32(StepArgs A, FxArgs F, F32Args 
       c.add(fx::mul_f(F.sdiff, D.g[1]));
       const int64_t Yn = fx::d2fix(by, kF) + c.fix(kF);
       int steps = 0;
-      slow = walk_fx(F, e, Xn, Yn, steps, c_per, c_near);
+      slow = walk_fx(F, e, Xn, Yn, steps, c_per, c_near, reinj);
       c_walk += steps;
       xn = __longlong_as_double((long long)fx::fix2d(Xn, kF));
       yn = __longlong_as_double((long long)fx::fix2d(Yn, kF));
@@ -694,18 +725,20 @@ __global__ void __launch_bounds__(256) k_step_f32(StepArgs A, FxArgs F, F32Args 
       slow = true;
     }
     if (slow) {
-      const int32_t en = walk_slow(A, e, xn, yn, ud, vd, cs);
+      const int32_t en = walk_slow(A, e, xn, yn, ud, vd, cs, reinj);
       if (en >= 0) e = en; else { ++cs.lost; e = A.elem[p]; }
       un = (float)ud;
       vn = (float)vd;
     }
+    float sf = reinj ? 0.0f : sn;
+    if (in_source(A, xn, yn)) sf = 1.0f;
     A.x[p] = xn;
     A.y[p] = yn;
     S.u[p] = un;
     S.v[p] = vn;
     S.w[p] = wn;
     S.om[p] = on;
-    S.ps[p] = sn;
+    S.ps[p] = sf;
     A.elem[p] = e;
   }
   cs.walk += c_walk; cs.per += c_per; cs.om += c_om; cs.near += c_near;
@@ -731,7 +764,7 @@ static int blocks_for(int64_t n, int threads, int per_sm) {
 static pdf_status check_params(const pdf_model_params* p) {
   if (!p) return fail(PDF_EINVAL, "NULL params");
   if (!(p->dt > 0.0) || !(p->nu >= 0.0)) return fail(PDF_EINVAL, "params: dt must be > 0 and nu >= 0");
-  if (p->closure < 0 || p->closure > 2 || p->tm_mode < 0 || p->tm_mode > 1 || p->pressure < 0 ||
+  if (p->closure < 0 || p->closure > 2 || p->tm_mode < 0 || p->tm_mode > 2 || p->pressure < 0 ||
       p->pressure > 1 || p->arith < 0 || p->arith > 1)
     return fail(PDF_EINVAL, "params: closure, tm_mode or pressure out of range");
   return PDF_OK;
@@ -744,7 +777,7 @@ static pdf_status build_rows(pdf_particles* P, const pdf_model_params* params, c
   const CoeffParams C = coeff_params(params);
   PDF_KERNEL("k_node_coeff", st, k_node_coeff<<<blocks_for(M.n_nodes, 128, 32), 128, 0, st>>>(M.n_nodes, P->ns, P->nd,
                                                                 params->closure == PDF_CLOSURE_GLM ? wp : nullptr,
-                                                                C, P->nc););
+                                                                M.xy, C, P->nc););
   PDF_KERNEL("k_elem_rows", st, k_elem_rows<<<blocks_for(M.n_tri, 128, 32), 128, 0, st>>>(M.tri, M.n_tri, P->nc, C,
                                                              internal ? P->rows : nullptr, avg_out,
                                                              internal && C.arith == PDF_ARITH_FX ? P->rows_fx : nullptr,
@@ -798,6 +831,9 @@ extern "C" pdf_status pdf_step(pdf_particles* p, const pdf_mesh* m, const pdf_mo
   A.seed = p->seed;
   A.step = step;
   A.counters = p->counters;
+  A.src_x = params->src_x;
+  A.src_y = params->src_y;
+  A.src_r = params->src_r;
   if (p->precision == PDF_FP32_STATE || params->arith == PDF_ARITH_FX) {
     FxArgs F;
     F.rows = p->rows_fx;

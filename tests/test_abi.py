@@ -58,6 +58,8 @@ def test_default_parameters_are_the_papers_constants():
             golden[k] = float(v)
     for k, v in golden.items():
         assert getattr(p, k) == v, k
+    # micromixing constants of the concentrated-source form (table of constants, ch. 5)
+    assert p.Cs == 0.02 and p.Ct == 0.7
 
 
 def test_errors_are_reported_not_raised_in_c():
