@@ -57,7 +57,7 @@ def _peaks():
 
 def _kernel_sha():
     h = hashlib.sha256()
-    for f in ("step.cu", "rng.cuh", "common.cuh"):
+    for f in ("step.cu", "rng.cuh", "common.cuh", "fx.cuh"):
         with open(os.path.join(ROOT, "paper_1006_0720_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -66,7 +66,7 @@ def _kernel_sha():
 def _traffic_from_profile():
     """DRAM bytes per k_step launch from the committed ncu summary, if it was
     taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "k_step_channel_200x400.md")
+    path = os.path.join(ROOT, "profiles", "k_step_fx_channel_200x400.md")
     try:
         text = open(path).read()
     except OSError:
