@@ -68,14 +68,20 @@ enum { PDF_TM_TURB = 0, PDF_TM_CPHI = 1, PDF_TM_SOURCE = 2 };
  * cross-stream balance (1/rho) d<P>/dy = -d<v^2>/dy (eq. cross-stream-mean-
  * momentum-channel). */
 enum { PDF_PRESSURE_NONE = 0, PDF_PRESSURE_CHANNEL = 1 };
-/* How the FP64 particle step is computed.  FX (default): no FP64
- * instructions on the fast path -- FP64 values decoded into 64-bit fixed point
- * (exact sums), products in double-float FP32 pairs; particles with values
- * outside the fixed-point ranges (|x|, |u|, |psi| < 64, |omega| < 1024) or whose
- * walk meets a wall are finished in FP64.  FP64: native FP64 instructions
- * throughout (GB300 runs them at ~1/70 of the FP32 rate). */
+/* How the FP64-accurate particle step is computed.  FX (default): no FP64
+ * instructions on the fast path -- positions in 64-bit fixed point (exact
+ * increments and element tests), velocity, frequency and scalar in
+ * double-float FP32 pairs (FMA-exact products, TwoSum additions); particles
+ * that move one length unit or more in a step, or whose walk meets a wall,
+ * are finished in FP64.  FP64: native FP64 instructions throughout (GB300
+ * runs them at ~1/70 of the FP32 rate), on the same stored forms. */
 enum { PDF_ARITH_FX = 0, PDF_ARITH_FP64 = 1 };
-/* Storage precision of u, v, w, omega, psi.  Positions are always FP64. */
+/* Storage of the particle state on the device.  Positions: 64-bit fixed
+ * point with 56 fraction bits (resolution 2^-56, |x|, |y| < 64) in both
+ * modes.  PDF_FP64: u, v, w, omega, psi as double-float pairs (48
+ * significant bits, relative resolution 2^-48 ~ 3.6e-15, FP32 exponent
+ * range).  PDF_FP32_STATE: u, v, w, omega, psi in FP32.  The interface
+ * reads and writes FP64 in both modes. */
 enum { PDF_FP64 = 0, PDF_FP32_STATE = 1 };
 
 /* Number of element-average coefficients a particle sees (layout below). */
@@ -164,24 +170,29 @@ pdf_status pdf_mesh_size(const pdf_mesh* m, int32_t* n_nodes, int32_t* n_tri);
  * u_sigma N(0,1) per component; omega ~ Gamma(k=4, theta=1/4) (unit mean,
  * variance 1/4); psi = elem_psi0[e] or 0.  Random numbers: Philox4x32-10
  * keyed by seed, counter (particle id, 0, block, 1).
- * precision: PDF_FP64 (PDF_FP32_STATE is reserved, PDF_EINVAL for now).
- * Allocates all per-particle and per-mesh device buffers.  The mesh must
- * outlive the particles. */
+ * precision: PDF_FP64 or PDF_FP32_STATE (the storage above); anything else
+ * is PDF_EINVAL.  Allocates all per-particle and per-mesh device buffers
+ * (PDF_ENOMEM if one fails, nothing kept).  The mesh must outlive the
+ * particles. */
 pdf_status pdf_particles_init(const pdf_mesh* m, const pdf_init_params* ip, uint64_t seed,
                               int32_t precision, void* stream, pdf_particles** out);
 pdf_status pdf_particles_destroy(pdf_particles* p);
 pdf_status pdf_particles_count(const pdf_particles* p, int64_t* n);
 
-/* Copies the state into caller buffers [n] (any pointer may be NULL).  The
- * buffers may be device memory or page-locked host memory (the copies are
- * cudaMemcpyDefault, asynchronous on `stream`).  elem: host element id of
- * each particle. */
+/* Copies the state, converted to FP64, into caller buffers [n] (any pointer
+ * may be NULL).  The buffers may be device or host memory: device buffers
+ * are written by conversion kernels on `stream`; host buffers through an
+ * FP64 staging buffer of n doubles that the handle allocates on first use
+ * and keeps (asynchronous on `stream` for page-locked memory).  elem: host
+ * element id of each particle. */
 pdf_status pdf_particles_get_state(const pdf_particles* p, double* x, double* y, double* u,
                                    double* v, double* w, double* om, double* ps, int32_t* elem,
                                    void* stream);
-/* Overwrites the state from caller buffers [n] (all required; device or
- * page-locked host memory).  elem must hold each particle's host element
- * (not checked). */
+/* Overwrites the state from FP64 caller buffers [n] (all required; device
+ * or host memory, host sources through the staging buffer above), rounding
+ * to the stored forms.  Synchronizes `stream`.  A position outside
+ * |x|, |y| < 64 is PDF_EINVAL (the state is then undefined).  elem must
+ * hold each particle's host element (not checked). */
 pdf_status pdf_particles_set_state(pdf_particles* p, const double* x, const double* y,
                                    const double* u, const double* v, const double* w,
                                    const double* om, const double* ps, const int32_t* elem,

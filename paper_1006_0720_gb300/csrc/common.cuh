@@ -56,14 +56,16 @@ struct __align__(16) FxGeo {
 };
 static_assert(sizeof(FxGeo) == 80, "FxGeo layout");
 
+// Fraction bits of the fixed-point particle positions (|x|, |y| < 64).
+constexpr int kPosF = 56;
+
 // Coefficient row of the fixed-point kernel (256 B): the element means of
-// U, V, W and phi in fixed point (56 fraction bits) and the scaled
-// coefficients as double-floats:
+// U, V, W and phi and the scaled coefficients, all as double-floats:
 //   c0-5 sqrt(2 nu dt) d<U_i>/dx_j; c6-8 a_i dt; c9-17 G_ij dt;
 //   c18 sqrt(C0 eps dt); c19 (C3 + S_w) <w> dt; c20 C3 <w>^2 dt;
-//   c21 <w> sqrt(2 C3 C4 dt); c22 dt / t_m; c27.h != 0: use the FP64 path.
+//   c21 <w> sqrt(2 C3 C4 dt); c22 dt / t_m; c23-27 unused (zero).
 struct __align__(16) FxRow {
-  int64_t mean[4];
+  fx::df mean[4];
   fx::df c[28];
 };
 static_assert(sizeof(FxRow) == 256, "FxRow layout");
@@ -136,17 +138,26 @@ struct pdf_mesh {
 //   27   dt / t_m
 #define PDFGB_ROW 32
 
+// Particle state in HBM, particle-id order, structure of arrays (8 B per
+// value):
+//   x, y              64-bit fixed point with kPosF fraction bits: exact
+//                     additions and periodic shifts, uniform absolute
+//                     resolution 2^-56 over the domain;
+//   u, v, w, om, ps   PDF_FP64: double-float pairs (h, l), |l| <= ulp(h)/2,
+//                     48 significant bits, the full FP32 exponent range;
+//                     PDF_FP32_STATE: FP32 (uf ... psf).
+// The public interface reads and writes FP64; the conversions run in
+// pdf_particles_get_state / pdf_particles_set_state.
 struct pdf_particles {
   const pdf_mesh* mesh = nullptr;
   int64_t n = 0;
   int32_t precision = PDF_FP64;
   uint64_t seed = 0;
-  // state, particle-id order
-  double *x = nullptr, *y = nullptr, *u = nullptr, *v = nullptr, *w = nullptr, *om = nullptr,
-         *ps = nullptr;
+  int64_t *x = nullptr, *y = nullptr;
+  fx::df *u = nullptr, *v = nullptr, *w = nullptr, *om = nullptr, *ps = nullptr;
   int32_t* elem = nullptr;
-  // PDF_FP32_STATE: u, v, w, omega, psi in FP32 (x, y stay FP64 above)
   float *uf = nullptr, *vf = nullptr, *wf = nullptr, *omf = nullptr, *psf = nullptr;
+  double* stage = nullptr;  // [n] FP64 staging for host transfers (allocated on first use)
   float* rows_f32 = nullptr;  // [n_tri][32] coefficient rows in FP32 (same layout as rows)
   // statistics
   double* es = nullptr;    // [n_tri][13]

@@ -98,9 +98,18 @@ FX_HD int64_t f2fix(float f, int F) {
   return (b >> 31) ? -(int64_t)r : (int64_t)r;
 }
 
-struct df {
+struct alignas(8) df {
   float h, l;
 };
+
+// FP64 <-> double-float with FP64 instructions (initialisation, state
+// transfers and the FP64 fall-back only): h = x rounded to FP32, l = the
+// exact remainder rounded to FP32; back as the FP64 sum, rounded once.
+FX_HD df from_double(double x) {
+  const float h = (float)x;
+  return df{h, (float)(x - (double)h)};
+}
+FX_HD double to_double(df a) { return (double)a.h + (double)a.l; }
 
 // Knuth's TwoSum: s + e == a + b exactly.
 FX_HD df two_sum(float a, float b) {

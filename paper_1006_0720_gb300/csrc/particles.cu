@@ -18,9 +18,9 @@ int32_t radix_scan_blocks(int64_t hist_len);
 __global__ void k_init(const double* __restrict__ xy, const int32_t* __restrict__ tri,
                        const int64_t* __restrict__ elem_off, int32_t n_tri, int64_t n,
                        uint64_t seed, int32_t u_profile, double u_sigma,
-                       const double* __restrict__ elem_psi0, double* __restrict__ x,
-                       double* __restrict__ y, double* __restrict__ u, double* __restrict__ v,
-                       double* __restrict__ w, double* __restrict__ om, double* __restrict__ ps,
+                       const double* __restrict__ elem_psi0, int64_t* __restrict__ x,
+                       int64_t* __restrict__ y, fx::df* __restrict__ u, fx::df* __restrict__ v,
+                       fx::df* __restrict__ w, fx::df* __restrict__ om, fx::df* __restrict__ ps,
                        int32_t* __restrict__ elem, float* __restrict__ uf, float* __restrict__ vf,
                        float* __restrict__ wf, float* __restrict__ omf, float* __restrict__ psf) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
@@ -59,15 +59,16 @@ __global__ void k_init(const double* __restrict__ xy, const int32_t* __restrict_
     const double py = __dadd_rn(__dadd_rn(ya, __dmul_rn(R1, __dsub_rn(yb, ya))),
                                 __dmul_rn(R2, __dsub_rn(yc, ya)));
     const double umean = (u_profile == 1) ? __dsub_rn(1.0, __dmul_rn(py, py)) : (u_profile == 2 ? 1.0 : 0.0);
-    x[p] = px;
-    y[p] = py;
+    x[p] = fx::d2fix((uint64_t)__double_as_longlong(px), kPosF);
+    y[p] = fx::d2fix((uint64_t)__double_as_longlong(py), kPosF);
     const double U = __dadd_rn(umean, __dmul_rn(u_sigma, (double)g[0]));
     const double V = __dmul_rn(u_sigma, (double)g[1]);
     const double W = __dmul_rn(u_sigma, (double)g[2]);
     const double O = __dmul_rn(-0.25, (double)lsum);   // Gamma(4, 1/4): -1/4 sum of 4 ln u
     const double S = elem_psi0 ? elem_psi0[e] : 0.0;
     if (u) {
-      u[p] = U; v[p] = V; w[p] = W; om[p] = O; ps[p] = S;
+      u[p] = fx::from_double(U); v[p] = fx::from_double(V); w[p] = fx::from_double(W);
+      om[p] = fx::from_double(O); ps[p] = fx::from_double(S);
     } else {  // FP32 state: the FP64 values rounded to nearest
       uf[p] = __double2float_rn(U); vf[p] = __double2float_rn(V); wf[p] = __double2float_rn(W);
       omf[p] = __double2float_rn(O); psf[p] = __double2float_rn(S);
@@ -86,12 +87,42 @@ __global__ void k_rng_gauss(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3
   }
 }
 
-__global__ void k_widen(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+// Stored representation -> FP64 (get_state) and back (set_state).
+__global__ void k_fix_to_f64(const int64_t* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = __longlong_as_double((long long)fx::fix2d(a[i], kPosF));
+}
+
+__global__ void k_df_to_f64(const fx::df* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = fx::to_double(a[i]);
+}
+
+__global__ void k_f32_to_f64(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = (double)a[i];
 }
 
-__global__ void k_narrow(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+// Positions outside |x| < 64 are counted in *bad and stored as 0.
+__global__ void k_f64_to_fix(const double* __restrict__ a, int64_t* __restrict__ b, int64_t n,
+                             unsigned long long* __restrict__ bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t bits = (uint64_t)__double_as_longlong(a[i]);
+    if (fx::d_exp(bits) <= 1023 + 5) {
+      b[i] = fx::d2fix(bits, kPosF);
+    } else {
+      b[i] = 0;
+      atomicAdd(bad, 1ull);
+    }
+  }
+}
+
+__global__ void k_f64_to_df(const double* __restrict__ a, fx::df* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = fx::from_double(a[i]);
+}
+
+__global__ void k_f64_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = __double2float_rn(a[i]);
 }
@@ -99,7 +130,10 @@ __global__ void k_narrow(const double* __restrict__ a, float* __restrict__ b, in
 static void free_particles(pdf_particles* p) {
   if (!p) return;
   cudaFree(p->uf); cudaFree(p->vf); cudaFree(p->wf); cudaFree(p->omf); cudaFree(p->psf); cudaFree(p->rows_f32);
-  double* dbl[] = {p->x, p->y, p->u, p->v, p->w, p->om, p->ps, p->es, p->ns, p->nd, p->eg, p->nc, p->rows};
+  cudaFree(p->x); cudaFree(p->y);
+  cudaFree(p->u); cudaFree(p->v); cudaFree(p->w); cudaFree(p->om); cudaFree(p->ps);
+  cudaFree(p->stage);
+  double* dbl[] = {p->es, p->ns, p->nd, p->eg, p->nc, p->rows};
   for (double* d : dbl) cudaFree(d);
   cudaFree(p->elem);
   cudaFree(p->rows_fx);
@@ -218,6 +252,21 @@ extern "C" pdf_status pdf_particles_count(const pdf_particles* p, int64_t* n) {
   return PDF_OK;
 }
 
+static bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static pdf_status ensure_stage(const pdf_particles* p) {
+  pdf_particles* q = const_cast<pdf_particles*>(p);
+  if (!q->stage) PDF_CUDA(cudaMalloc((void**)&q->stage, sizeof(double) * (size_t)p->n));
+  return PDF_OK;
+}
+
 extern "C" pdf_status pdf_particles_get_state(const pdf_particles* p, double* x, double* y,
                                               double* u, double* v, double* w, double* om,
                                               double* ps, int32_t* elem, void* stream) {
@@ -225,18 +274,28 @@ extern "C" pdf_status pdf_particles_get_state(const pdf_particles* p, double* x,
   cudaStream_t st = (cudaStream_t)stream;
   const size_t b = sizeof(double) * p->n;
   double* dst[] = {x, y, u, v, w, om, ps};
-  const double* src[] = {p->x, p->y, p->u, p->v, p->w, p->om, p->ps};
+  const fx::df* srcd[] = {nullptr, nullptr, p->u, p->v, p->w, p->om, p->ps};
   const float* srcf[] = {nullptr, nullptr, p->uf, p->vf, p->wf, p->omf, p->psf};
+  const int g = grid_for(p->n, 256);
   for (int i = 0; i < 7; ++i) {
     if (!dst[i]) continue;
-    if (src[i]) {
-      PDF_CUDA(cudaMemcpyAsync(dst[i], src[i], b, cudaMemcpyDefault, st));
-    } else {  // FP32 state widened on the device (device destinations only)
-      cudaPointerAttributes at;
-      if (cudaPointerGetAttributes(&at, dst[i]) != cudaSuccess || at.type != cudaMemoryTypeDevice)
-        return fail(PDF_EINVAL, "pdf_particles_get_state: FP32 state needs device destinations");
-      PDF_KERNEL("k_widen", st, k_widen<<<grid_for(p->n, 256), 256, 0, st>>>(srcf[i], dst[i], p->n));
+    // convert on the device, straight into a device destination or through
+    // the staging buffer for host memory
+    const bool dev = is_device_ptr(dst[i]);
+    if (!dev) {
+      pdf_status s = ensure_stage(p);
+      if (s != PDF_OK) return s;
     }
+    double* to = dev ? dst[i] : p->stage;
+    if (i < 2) {
+      const int64_t* a = i == 0 ? p->x : p->y;
+      PDF_KERNEL("k_fix_to_f64", st, k_fix_to_f64<<<g, 256, 0, st>>>(a, to, p->n));
+    } else if (srcd[i]) {
+      PDF_KERNEL("k_df_to_f64", st, k_df_to_f64<<<g, 256, 0, st>>>(srcd[i], to, p->n));
+    } else {
+      PDF_KERNEL("k_f32_to_f64", st, k_f32_to_f64<<<g, 256, 0, st>>>(srcf[i], to, p->n));
+    }
+    if (!dev) PDF_CUDA(cudaMemcpyAsync(dst[i], p->stage, b, cudaMemcpyDeviceToHost, st));
   }
   if (elem) PDF_CUDA(cudaMemcpyAsync(elem, p->elem, sizeof(int32_t) * p->n, cudaMemcpyDefault, st));
   return PDF_OK;
@@ -250,20 +309,34 @@ extern "C" pdf_status pdf_particles_set_state(pdf_particles* p, const double* x,
     return fail(PDF_EINVAL, "pdf_particles_set_state: NULL argument");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t b = sizeof(double) * p->n;
-  double* dst[] = {p->x, p->y, p->u, p->v, p->w, p->om, p->ps};
+  fx::df* dstd[] = {nullptr, nullptr, p->u, p->v, p->w, p->om, p->ps};
   float* dstf[] = {nullptr, nullptr, p->uf, p->vf, p->wf, p->omf, p->psf};
   const double* src[] = {x, y, u, v, w, om, ps};
+  const int g = grid_for(p->n, 256);
+  unsigned long long* bad = reinterpret_cast<unsigned long long*>(p->counters + 15);
+  PDF_CUDA(cudaMemsetAsync(bad, 0, sizeof(long long), st));
   for (int i = 0; i < 7; ++i) {
-    if (dst[i]) {
-      PDF_CUDA(cudaMemcpyAsync(dst[i], src[i], b, cudaMemcpyDefault, st));
+    const bool dev = is_device_ptr(src[i]);
+    if (!dev) {
+      pdf_status s = ensure_stage(p);
+      if (s != PDF_OK) return s;
+      PDF_CUDA(cudaMemcpyAsync(p->stage, src[i], b, cudaMemcpyHostToDevice, st));
+    }
+    const double* from = dev ? src[i] : p->stage;
+    if (i < 2) {
+      int64_t* a = i == 0 ? p->x : p->y;
+      PDF_KERNEL("k_f64_to_fix", st, k_f64_to_fix<<<g, 256, 0, st>>>(from, a, p->n, bad));
+    } else if (dstd[i]) {
+      PDF_KERNEL("k_f64_to_df", st, k_f64_to_df<<<g, 256, 0, st>>>(from, dstd[i], p->n));
     } else {
-      cudaPointerAttributes at;
-      if (cudaPointerGetAttributes(&at, src[i]) != cudaSuccess || at.type != cudaMemoryTypeDevice)
-        return fail(PDF_EINVAL, "pdf_particles_set_state: FP32 state needs device sources");
-      PDF_KERNEL("k_narrow", st, k_narrow<<<grid_for(p->n, 256), 256, 0, st>>>(src[i], dstf[i], p->n));
+      PDF_KERNEL("k_f64_to_f32", st, k_f64_to_f32<<<g, 256, 0, st>>>(from, dstf[i], p->n));
     }
   }
   PDF_CUDA(cudaMemcpyAsync(p->elem, elem, sizeof(int32_t) * p->n, cudaMemcpyDefault, st));
+  long long nbad = 0;
+  PDF_CUDA(cudaMemcpyAsync(&nbad, bad, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  PDF_CUDA(cudaStreamSynchronize(st));
+  if (nbad) return fail(PDF_EINVAL, "pdf_particles_set_state: positions must lie within |x|, |y| < 64");
   return PDF_OK;
 }
 

@@ -174,6 +174,14 @@ __global__ void k_seg_offsets(const int32_t* __restrict__ keys, int64_t n, int32
   }
 }
 
+// A state value as FP64, whatever its stored representation.
+__device__ __forceinline__ double ld64(const double* a, int64_t i) { return __ldg(a + i); }
+__device__ __forceinline__ double ld64(const float* a, int64_t i) { return (double)__ldg(a + i); }
+__device__ __forceinline__ double ld64(const fx::df* a, int64_t i) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(a) + i);
+  return fx::to_double(fx::df{v.x, v.y});
+}
+
 // One warp per element: first pass means, second pass central moments
 // (sec. 3.3, 1/N).  Lane j adds sorted positions j, j+32, ...; the lane
 // partials are combined by a fixed butterfly and lane 0's result is used.
@@ -186,7 +194,7 @@ __device__ void elem_stats_fp64(int32_t beg, int32_t end, int lane, const int32_
   double s[5] = {0, 0, 0, 0, 0};
   for (int32_t i = beg + lane; i < end; i += 32) {
     const int32_t p = pid[i];
-    s[0] += (double)u[p]; s[1] += (double)v[p]; s[2] += (double)w[p]; s[3] += (double)om[p]; s[4] += (double)ps[p];
+    s[0] += ld64(u, p); s[1] += ld64(v, p); s[2] += ld64(w, p); s[3] += ld64(om, p); s[4] += ld64(ps, p);
   }
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
@@ -197,8 +205,8 @@ __device__ void elem_stats_fp64(int32_t beg, int32_t end, int lane, const int32_
   double c[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int32_t i = beg + lane; i < end; i += 32) {
     const int32_t p = pid[i];
-    const double du = (double)u[p] - s[0], dv = (double)v[p] - s[1], dw = (double)w[p] - s[2],
-                 dp = (double)ps[p] - s[4];
+    const double du = ld64(u, p) - s[0], dv = ld64(v, p) - s[1], dw = ld64(w, p) - s[2],
+                 dp = ld64(ps, p) - s[4];
     c[0] += du * du; c[1] += dv * dv; c[2] += dw * dw;
     c[3] += du * dv; c[4] += du * dw; c[5] += dv * dw; c[6] += dp * dp;
   }
@@ -283,6 +291,11 @@ __device__ __forceinline__ long long to_fix(const double* a, int64_t i, int lim,
   ok = ok && fx::d_exp(b) <= 1023 + lim;
   return fx::d2fix(b, kFQ);
 }
+__device__ __forceinline__ long long to_fix(const fx::df* a, int64_t i, int lim, bool& ok) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(a) + i);
+  ok = ok && (int)((fx::f_bits(v.x) >> 23) & 0xFF) <= 127 + lim;
+  return fx::f2fix(v.x, kFQ) + fx::f2fix(v.y, kFQ);
+}
 __device__ __forceinline__ long long to_fix(const float* a, int64_t i, int lim, bool& ok) {
   const float f = __ldg(a + i);
   ok = ok && (int)((fx::f_bits(f) >> 23) & 0xFF) <= 127 + lim;
@@ -291,14 +304,23 @@ __device__ __forceinline__ long long to_fix(const float* a, int64_t i, int lim, 
 
 // Per-warp shared scratch of the statistics kernel: lane partials, stored
 // column-wise so that one lane can add up one quantity over the 32 lanes.
+// Rows are padded to 33 entries so that the lanes reading different
+// quantities at the same column hit different banks; the integer partials
+// of pass 1 and the double-float partials of pass 2 share the storage.
 struct StatScratch {
-  unsigned long long lo[5][32];
-  long long hi[5][32];
-  float h[11][32], l[11][32];
+  union {
+    struct {
+      unsigned long long lo[5][33];
+      long long hi[5][33];
+    } i;
+    struct {
+      float h[11][33], l[11][33];
+    } f;
+  };
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_elem_stats_fx(const int32_t* __restrict__ seg,
+__global__ void __launch_bounds__(256, 4) k_elem_stats_fx(const int32_t* __restrict__ seg,
                                                        const int32_t* __restrict__ pid, int32_t n_tri,
                                                        const T* __restrict__ u, const T* __restrict__ v,
                                                        const T* __restrict__ w, const T* __restrict__ om,
@@ -316,6 +338,7 @@ __global__ void __launch_bounds__(256) k_elem_stats_fx(const int32_t* __restrict
       if (lane < PDF_NES) out[lane] = 0.0;
       continue;
     }
+    __syncwarp();  // the previous element's readers of the scratch are done
     // pass 1: exact sums of the fixed-point values
     unsigned long long lo[5] = {0, 0, 0, 0, 0};
     long long hi[5] = {0, 0, 0, 0, 0};
@@ -335,8 +358,8 @@ __global__ void __launch_bounds__(256) k_elem_stats_fx(const int32_t* __restrict
     }
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-      SS.lo[q][lane] = lo[q];
-      SS.hi[q][lane] = hi[q];
+      SS.i.lo[q][lane] = lo[q];
+      SS.i.hi[q][lane] = hi[q];
     }
     __syncwarp();
     // lane q < 5 adds quantity q over the lanes (exact) and forms its mean
@@ -346,8 +369,8 @@ __global__ void __launch_bounds__(256) k_elem_stats_fx(const int32_t* __restrict
       unsigned long long sl = 0;
       long long sh = 0;
       for (int j = 0; j < 32; ++j) {
-        const unsigned long long nl = sl + SS.lo[lane][j];
-        sh = sh + SS.hi[lane][j] + (nl < sl ? 1 : 0);
+        const unsigned long long nl = sl + SS.i.lo[lane][j];
+        sh = sh + SS.i.hi[lane][j] + (nl < sl ? 1 : 0);
         sl = nl;
       }
       mean = fx::df_norm(fx::mul(fx::i128_to_df(sl, sh, -kFQ), invN));
@@ -386,21 +409,21 @@ __global__ void __launch_bounds__(256) k_elem_stats_fx(const int32_t* __restrict
     __syncwarp();
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
-      SS.h[q][lane] = c[q].h;
-      SS.l[q][lane] = c[q].l;
+      SS.f.h[q][lane] = c[q].h;
+      SS.f.l[q][lane] = c[q].l;
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      SS.h[7 + k][lane] = d[k].h;
-      SS.l[7 + k][lane] = d[k].l;
+      SS.f.h[7 + k][lane] = d[k].h;
+      SS.f.l[7 + k][lane] = d[k].l;
     }
     __syncwarp();
     // lane q < 11 adds quantity q over the lanes, in lane order
     fx::df tot = fx::df{0.f, 0.f};
     if (lane < 11) {
       fx::acc a;
-      a.init(fx::df{SS.h[lane][0], SS.l[lane][0]});
-      for (int j = 1; j < 32; ++j) a.add(fx::df{SS.h[lane][j], SS.l[lane][j]});
+      a.init(fx::df{SS.f.h[lane][0], SS.f.l[lane][0]});
+      for (int j = 1; j < 32; ++j) a.add(fx::df{SS.f.h[lane][j], SS.f.l[lane][j]});
       tot = a.value();
     }
     // output lane: 0 -> N, 1..5 -> means, 6..12 -> central moments
@@ -573,7 +596,7 @@ pdf_status estimate_stats(pdf_particles* P, cudaStream_t st) {
   pdf_status s = group_by_element(P, st);
   if (s != PDF_OK) return s;
   if (P->precision == PDF_FP64)
-    PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<double><<<blocks_for((int64_t)M.n_tri * 32, 256), 256, 0, st>>>(
+    PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<fx::df><<<blocks_for((int64_t)M.n_tri * 32, 256), 256, 0, st>>>(
         P->seg, P->sorted_pid, M.n_tri, P->u, P->v, P->w, P->om, P->ps, P->es));
   else
     PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<float><<<blocks_for((int64_t)M.n_tri * 32, 256), 256, 0, st>>>(
@@ -643,7 +666,7 @@ pdf_status estimate_stats_with_buffers(pdf_particles* P, int32_t* keys_a, int32_
   }
   PDF_KERNEL("k_seg_offsets", st, k_seg_offsets<<<blocks_for(n + 1, 256), 256, 0, st>>>(kin, n, M.n_tri, seg));
   if (P->precision == PDF_FP64)
-    PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<double><<<blocks_for((int64_t)M.n_tri * 32, 256), 256, 0, st>>>(
+    PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<fx::df><<<blocks_for((int64_t)M.n_tri * 32, 256), 256, 0, st>>>(
                                        seg, vin, M.n_tri, P->u, P->v, P->w, P->om, P->ps, P->es));
   else
     PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<float><<<blocks_for((int64_t)M.n_tri * 32, 256), 256, 0, st>>>(

@@ -145,24 +145,17 @@ __device__ __forceinline__ void scale_row(const double a[PDF_NCOEF], const Coeff
   r[28] = r[29] = r[30] = r[31] = 0.0;
 }
 
-// The fixed-point kernel's row from the scaled FP64 row.  A mean outside
-// |value| < 32 marks the element for the FP64 path.
+// The fixed-point kernel's row from the scaled FP64 row.
 __device__ __forceinline__ void make_fx_row(const double* r, FxRow* out) {
   FxRow f;
-  bool ok = true;
   const int mi[4] = {0, 1, 2, 26};
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const uint64_t b = (uint64_t)__double_as_longlong(r[mi[j]]);
-    ok = ok && fx::d_exp(b) <= 1023 + 4;
-    f.mean[j] = fx::d2fix(b, 56);
-  }
+  for (int j = 0; j < 4; ++j) f.mean[j] = fx::d2df((uint64_t)__double_as_longlong(r[mi[j]]));
   const int ci[23] = {3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 23, 24, 25, 27};
 #pragma unroll
   for (int q = 0; q < 23; ++q) f.c[q] = fx::d2df((uint64_t)__double_as_longlong(r[ci[q]]));
 #pragma unroll
   for (int q = 23; q < 28; ++q) f.c[q] = fx::df{0.f, 0.f};
-  if (!ok) f.c[27].h = 1.0f;
   *out = f;
 }
 
@@ -208,7 +201,8 @@ __global__ void k_frozen_rows(int32_t n_tri, const double* __restrict__ coeff, C
 // ----------------------------------------------------------------------------
 struct StepArgs {
   int64_t n;
-  double *x, *y, *u, *v, *w, *om, *ps;
+  int64_t *x, *y;                  // fixed point, kPosF fraction bits
+  fx::df *u, *v, *w, *om, *ps;     // double-float (PDF_FP64 storage)
   int32_t* elem;
   const double* rows;
   const ElemGeo* geo;
@@ -381,13 +375,15 @@ __device__ __forceinline__ Draws draw_step(const StepArgs& A, int64_t p) {
 }
 
 // One particle in native FP64 instructions (PDF_ARITH_FP64, and the
-// fall-back of the fixed-point kernel for out-of-range values).
+// fall-back of the fixed-point kernel for large moves).  The stored forms are
+// widened to FP64 on load and rounded back on store; a particle that is lost,
+// or whose new position leaves |x|, |y| < 64, keeps its position and element.
 __device__ __noinline__ Counts advance_native(const StepArgs& A, int64_t p, const Draws D) {
   Counts c;
   const float* g = D.g;
   const int32_t e = A.elem[p];
   const double* R = A.rows + (int64_t)e * PDFGB_ROW;
-  const double U0 = A.u[p], U1 = A.v[p], U2 = A.w[p];
+  const double U0 = fx::to_double(A.u[p]), U1 = fx::to_double(A.v[p]), U2 = fx::to_double(A.w[p]);
   const double gx = (double)g[0], gy = (double)g[1];
   const double d0 = U0 - __ldg(R + 0), d1 = U1 - __ldg(R + 1), d2 = U2 - __ldg(R + 2);
   const double G0 = (double)g[2], G1 = (double)g[3], G2 = (double)g[4];
@@ -400,21 +396,30 @@ __device__ __noinline__ Counts advance_native(const StepArgs& A, int64_t p, cons
   const double wn = U2 + __ldg(R + 11) + __ldg(R + 7) * gx + __ldg(R + 8) * gy +
                     __ldg(R + 18) * d0 + __ldg(R + 19) * d1 + __ldg(R + 20) * d2 + b * G2;
   // position (eq. Lagrangian-position-exact) with the same dW_x, dW_y
-  double xn = A.x[p] + U0 * A.dt + A.sdiff * gx;
-  double yn = A.y[p] + U1 * A.dt + A.sdiff * gy;
+  double xn = __longlong_as_double((long long)fx::fix2d(A.x[p], kPosF)) + U0 * A.dt + A.sdiff * gx;
+  double yn = __longlong_as_double((long long)fx::fix2d(A.y[p], kPosF)) + U1 * A.dt + A.sdiff * gy;
   // frequency (eq. frequency-model); a negative result is reflected
-  const double o = A.om[p];
+  const double o = fx::to_double(A.om[p]);
   double on = o - __ldg(R + 23) * o + __ldg(R + 24) + __ldg(R + 25) * sqrt(fmax(o, 0.0)) * (double)g[5];
   if (on < 0.0) { on = -on; ++c.om; }
   // scalar (eq. IEM)
-  const double s = A.ps[p];
+  const double s = fx::to_double(A.ps[p]);
   const double sn = s - (s - __ldg(R + 26)) * __ldg(R + 27);
   bool reinj = false;
   const int32_t en = walk(A, e, xn, yn, un, vn, c.walk, c.refl, c.per, c.fb, c.brute, c.near, reinj);
+  if (en >= 0 && fabs(xn) < 64.0 && fabs(yn) < 64.0) {
+    A.x[p] = fx::d2fix((uint64_t)__double_as_longlong(xn), kPosF);
+    A.y[p] = fx::d2fix((uint64_t)__double_as_longlong(yn), kPosF);
+    A.elem[p] = en;
+  } else {
+    ++c.lost;
+    xn = __longlong_as_double((long long)fx::fix2d(A.x[p], kPosF));
+    yn = __longlong_as_double((long long)fx::fix2d(A.y[p], kPosF));
+  }
   double sf = reinj ? 0.0 : sn;
   if (in_source(A, xn, yn)) sf = 1.0;
-  A.x[p] = xn; A.y[p] = yn; A.u[p] = un; A.v[p] = vn; A.w[p] = wn; A.om[p] = on; A.ps[p] = sf;
-  if (en >= 0) A.elem[p] = en; else ++c.lost;
+  A.u[p] = fx::from_double(un); A.v[p] = fx::from_double(vn); A.w[p] = fx::from_double(wn);
+  A.om[p] = fx::from_double(on); A.ps[p] = fx::from_double(sf);
   return c;
 }
 
@@ -449,16 +454,14 @@ __global__ void __launch_bounds__(256) k_step(StepArgs A) {
 
 // ----------------------------------------------------------------------------
 // The same step without FP64 instructions (PDF_ARITH_FX, the default).
-// State in fixed point: positions, velocities and psi with 56 fraction bits
-// (|value| < 64), omega with 52 (|omega| < 1024); coefficients and products
-// as double-floats.  A particle with a value outside these ranges, or whose
-// walk meets a wall, an open boundary or the step cap, is finished by the
-// native FP64 code above.
+// Positions in their stored fixed point (56 fraction bits): exact
+// increments, periodic shifts and element tests; velocity, frequency and
+// scalar in their stored double-float form, products by the FMA-exact
+// product and sums by TwoSum.  A particle whose position increment
+// reaches one length unit, or whose walk meets a wall, an open boundary or
+// the step cap, is finished by the native FP64 code above.
 // ----------------------------------------------------------------------------
-constexpr int kF = 56;
-constexpr int kFO = 52;
-constexpr int kExpMax = 1023 + 5;    // |value| < 64
-constexpr int kExpMaxO = 1023 + 9;   // |omega| < 1024
+constexpr int kF = kPosF;
 
 struct FxArgs {
   const FxRow* rows;
@@ -466,6 +469,11 @@ struct FxArgs {
   int64_t period_fix;
   fx::df dt;      // dt
   fx::df sdiff;   // sqrt(2 nu dt)
+  // concentrated source: 0 none, 1 double-float test with the FP64 test in
+  // the rounding band, 2 FP64 test only (centre outside the fixed range)
+  int src_mode;
+  int64_t src_x, src_y;  // centre in fixed point
+  fx::df src_r2;         // r^2
 };
 
 __device__ __forceinline__ fx::df ldc(const FxRow* r, int q) {
@@ -473,8 +481,27 @@ __device__ __forceinline__ fx::df ldc(const FxRow* r, int q) {
   return fx::df{v.x, v.y};
 }
 
-__device__ __forceinline__ int64_t ldm(const FxRow* r, int j) {
-  return (int64_t)__ldg(reinterpret_cast<const long long*>(&r->mean[j]));
+__device__ __forceinline__ fx::df ldmean(const FxRow* r, int j) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(&r->mean[j]));
+  return fx::df{v.x, v.y};
+}
+
+__device__ __forceinline__ fx::df ld_state(const fx::df* a, int64_t p) {
+  const float2 v = reinterpret_cast<const float2*>(a)[p];
+  return fx::df{v.x, v.y};
+}
+
+__device__ __forceinline__ void st_state(fx::df* a, int64_t p, fx::df v) {
+  reinterpret_cast<float2*>(a)[p] = make_float2(v.h, v.l);
+}
+
+// a - b with the rounding error of the high parts kept (not renormalized;
+// used as a multiplicand).
+__device__ __forceinline__ fx::df dsub(fx::df a, fx::df b) {
+  fx::acc t;
+  t.init(a);
+  t.sub(b);
+  return fx::df{t.h, t.l};
 }
 
 __device__ __forceinline__ FxGeo load_fx_geo(const FxGeo* geo, int32_t e) {
@@ -561,7 +588,34 @@ __device__ __noinline__ int32_t walk_slow(const StepArgs& A, int32_t e, double& 
   return walk(A, e, x, y, u, v, c.walk, c.refl, c.per, c.fb, c.brute, c.near, reinj);
 }
 
-__global__ void __launch_bounds__(256) k_step_fx(StepArgs A, FxArgs F) {
+// Source test on the fixed-point position: d^2 - r^2 in double-float
+// (error below 2^-44 of d^2 + r^2); inside a band of 2^-40 of that around
+// zero the FP64 expression decides, as in the FP64 kernel.
+__device__ __forceinline__ bool in_source_fx(const StepArgs& A, const FxArgs& F, int64_t X, int64_t Y) {
+  if (F.src_mode == 0) return false;
+  if (F.src_mode == 1) {
+    const fx::df dx = fx::fix2df(X - F.src_x, kF), dy = fx::fix2df(Y - F.src_y, kF);
+    const fx::df dx2 = fx::mul(dx, dx), dy2 = fx::mul(dy, dy);
+    fx::acc a;
+    a.init(dx2);
+    a.add(dy2);
+    a.sub(F.src_r2);
+    const float v = a.h + a.l;
+    const float band = (dx2.h + dy2.h + F.src_r2.h) * 0x1p-40f;
+    if (fabsf(v) > band) return v < 0.0f;
+  }
+  return in_source(A, __longlong_as_double((long long)fx::fix2d(X, kF)),
+                   __longlong_as_double((long long)fx::fix2d(Y, kF)));
+}
+
+// Position increment bound of the fixed-point path: |U dt + sqrt(2 nu dt) dW| < 1,
+// which keeps every fixed-point offset of the walk below 2^7.
+__device__ __forceinline__ bool small_move(const fx::acc& a) { return fabsf(a.h) < 1.0f; }
+
+// FP64 back to the stored forms after the FP64 walk (the wall fall-back).
+__device__ __forceinline__ bool pos_fits(double x) { return fabs(x) < 64.0; }
+
+__global__ void __launch_bounds__(256, 4) k_step_fx(StepArgs A, FxArgs F) {
   int c_walk = 0, c_per = 0, c_om = 0, c_near = 0;
   Counts cs;  // counts of the FP64 fall-backs
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -570,94 +624,97 @@ __global__ void __launch_bounds__(256) k_step_fx(StepArgs A, FxArgs F) {
   for (int64_t it = 0; it < iters; ++it, p += stride) {
     if (p >= A.n) continue;
     const Draws D = draw_step(A, p);
-    const uint64_t bx = (uint64_t)__double_as_longlong(A.x[p]);
-    const uint64_t by = (uint64_t)__double_as_longlong(A.y[p]);
-    const uint64_t bu = (uint64_t)__double_as_longlong(A.u[p]);
-    const uint64_t bv = (uint64_t)__double_as_longlong(A.v[p]);
-    const uint64_t bw = (uint64_t)__double_as_longlong(A.w[p]);
-    const uint64_t bo = (uint64_t)__double_as_longlong(A.om[p]);
-    const uint64_t bs = (uint64_t)__double_as_longlong(A.ps[p]);
     int32_t e = A.elem[p];
     const FxRow* R = F.rows + e;
-    const bool in_range = fx::d_exp(bx) <= kExpMax && fx::d_exp(by) <= kExpMax && fx::d_exp(bu) <= kExpMax &&
-                          fx::d_exp(bv) <= kExpMax && fx::d_exp(bw) <= kExpMax && fx::d_exp(bs) <= kExpMax &&
-                          fx::d_exp(bo) <= kExpMaxO && ldc(R, 27).h == 0.0f;
-    if (!in_range) {
+    const fx::df U[3] = {ld_state(A.u, p), ld_state(A.v, p), ld_state(A.w, p)};
+    // position (eq. Lagrangian-position-exact): X + U^n dt + sqrt(2 nu) dW
+    fx::acc ax, ay;
+    ax.init(fx::mul(U[0], F.dt));
+    ax.add(fx::mul_f(F.sdiff, D.g[0]));
+    ay.init(fx::mul(U[1], F.dt));
+    ay.add(fx::mul_f(F.sdiff, D.g[1]));
+    if (!(small_move(ax) && small_move(ay))) {
       merge(cs, advance_native(A, p, D));
       continue;
     }
+    int64_t Xn = A.x[p] + ax.fix(kF);
+    const int64_t Yn = A.y[p] + ay.fix(kF);
     // velocity prediction (eq. velocity-prediction): U + a dt
     // + sqrt(2 nu) dU_i/dx_j dW_j + G_ij (U_j - <U_j>) dt + sqrt(C0 eps) dW'_i
-    const int64_t U0 = fx::d2fix(bu, kF), U1 = fx::d2fix(bv, kF), U2 = fx::d2fix(bw, kF);
-    const fx::df d0 = fx::fix2df(U0 - ldm(R, 0), kF);
-    const fx::df d1 = fx::fix2df(U1 - ldm(R, 1), kF);
-    const fx::df d2 = fx::fix2df(U2 - ldm(R, 2), kF);
+    const fx::df d0 = dsub(U[0], ldmean(R, 0));
+    const fx::df d1 = dsub(U[1], ldmean(R, 1));
+    const fx::df d2 = dsub(U[2], ldmean(R, 2));
     const fx::df sc = ldc(R, 18);
-    int64_t Un[3];
+    fx::df Un[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       fx::acc a;
-      a.init(ldc(R, 6 + i));
+      a.init(U[i]);
+      a.add(ldc(R, 6 + i));
       a.add(fx::mul_f(ldc(R, 2 * i), D.g[0]));
       a.add(fx::mul_f(ldc(R, 2 * i + 1), D.g[1]));
       a.add(fx::mul(ldc(R, 9 + 3 * i), d0));
       a.add(fx::mul(ldc(R, 10 + 3 * i), d1));
       a.add(fx::mul(ldc(R, 11 + 3 * i), d2));
       a.add(fx::mul_f(sc, D.g[2 + i]));
-      Un[i] = (i == 0 ? U0 : (i == 1 ? U1 : U2)) + a.fix(kF);
-    }
-    // position (eq. Lagrangian-position-exact): X + U^n dt + sqrt(2 nu) dW
-    int64_t Xn, Yn;
-    {
-      fx::acc a;
-      a.init(fx::mul(fx::fix2df(U0, kF), F.dt));
-      a.add(fx::mul_f(F.sdiff, D.g[0]));
-      Xn = fx::d2fix(bx, kF) + a.fix(kF);
-      fx::acc b;
-      b.init(fx::mul(fx::fix2df(U1, kF), F.dt));
-      b.add(fx::mul_f(F.sdiff, D.g[1]));
-      Yn = fx::d2fix(by, kF) + b.fix(kF);
+      Un[i] = a.value();
     }
     // frequency (eq. frequency-model): omega - (C3 + S_w) <w> dt omega + C3 <w>^2 dt
     // + <w> sqrt(2 C3 C4 dt) sqrt(max(omega, 0)) dW
-    const int64_t O = fx::d2fix(bo, kFO);
-    int64_t On;
+    const fx::df O = ld_state(A.om, p);
+    fx::df On;
     {
-      const fx::df od = fx::fix2df(O, kFO);
       fx::acc a;
-      a.init(ldc(R, 20));
-      a.sub(fx::mul(ldc(R, 19), od));
-      a.add(fx::mul_f(fx::mul(ldc(R, 21), fx::sqrt_df(od)), D.g[5]));
-      On = O + a.fix(kFO);
-      if (On < 0) { On = -On; ++c_om; }
+      a.init(O);
+      a.sub(fx::mul(ldc(R, 19), O));
+      a.add(ldc(R, 20));
+      a.add(fx::mul_f(fx::mul(ldc(R, 21), fx::sqrt_df(O)), D.g[5]));
+      On = a.value();
+      if (On.h < 0.0f) { On = fx::df{-On.h, -On.l}; ++c_om; }
     }
     // scalar (eq. IEM): psi - (psi - <phi>) dt / t_m
-    const int64_t S = fx::d2fix(bs, kF);
-    const fx::df prod = fx::mul(ldc(R, 22), fx::fix2df(S - ldm(R, 3), kF));
-    const int64_t Sn = S - (fx::f2fix(prod.h, kF) + fx::f2fix(prod.l, kF));
+    const fx::df S = ld_state(A.ps, p);
+    fx::df Sn;
+    {
+      fx::acc a;
+      a.init(S);
+      a.sub(fx::mul(ldc(R, 22), dsub(S, ldmean(R, 3))));
+      Sn = a.value();
+    }
     // neighbour walk (sec. 3.5) in fixed point; walls, open boundaries and
     // the step cap go to the FP64 walk
     int steps = 0;
     bool reinj = false;
     const bool slow = walk_fx(F, e, Xn, Yn, steps, c_per, c_near, reinj);
     c_walk += steps;
-    double xn = __longlong_as_double((long long)fx::fix2d(Xn, kF));
-    double yn = __longlong_as_double((long long)fx::fix2d(Yn, kF));
-    double un = __longlong_as_double((long long)fx::fix2d(Un[0], kF));
-    double vn = __longlong_as_double((long long)fx::fix2d(Un[1], kF));
+    int64_t Xs = Xn, Ys = Yn;
     if (slow) {
+      double xn = __longlong_as_double((long long)fx::fix2d(Xn, kF));
+      double yn = __longlong_as_double((long long)fx::fix2d(Yn, kF));
+      double un = fx::to_double(Un[0]), vn = fx::to_double(Un[1]);
       const int32_t en = walk_slow(A, e, xn, yn, un, vn, cs, reinj);
-      if (en >= 0) e = en; else { ++cs.lost; e = A.elem[p]; }
+      if (en >= 0 && pos_fits(xn) && pos_fits(yn)) {
+        e = en;
+        Xs = fx::d2fix((uint64_t)__double_as_longlong(xn), kF);
+        Ys = fx::d2fix((uint64_t)__double_as_longlong(yn), kF);
+        Un[0] = fx::from_double(un);
+        Un[1] = fx::from_double(vn);
+      } else {  // lost: keeps its element and position
+        ++cs.lost;
+        e = A.elem[p];
+        Xs = A.x[p];
+        Ys = A.y[p];
+      }
     }
-    double sf = reinj ? 0.0 : __longlong_as_double((long long)fx::fix2d(Sn, kF));
-    if (in_source(A, xn, yn)) sf = 1.0;
-    A.x[p] = xn;
-    A.y[p] = yn;
-    A.u[p] = un;
-    A.v[p] = vn;
-    A.w[p] = __longlong_as_double((long long)fx::fix2d(Un[2], kF));
-    A.om[p] = __longlong_as_double((long long)fx::fix2d(On, kFO));
-    A.ps[p] = sf;
+    if (reinj) Sn = fx::df{0.f, 0.f};
+    if (in_source_fx(A, F, Xs, Ys)) Sn = fx::df{1.f, 0.f};
+    A.x[p] = Xs;
+    A.y[p] = Ys;
+    st_state(A.u, p, Un[0]);
+    st_state(A.v, p, Un[1]);
+    st_state(A.w, p, Un[2]);
+    st_state(A.om, p, On);
+    st_state(A.ps, p, Sn);
     A.elem[p] = e;
   }
   cs.walk += c_walk; cs.per += c_per; cs.om += c_om; cs.near += c_near;
@@ -700,40 +757,50 @@ __global__ void __launch_bounds__(256) k_step_f32(StepArgs A, FxArgs F, F32Args 
     if (on < 0.f) { on = -on; ++c_om; }
     const float s = S.ps[p];
     const float sn = s - (s - __ldg(R + 26)) * __ldg(R + 27);
-    // position (eq. Lagrangian-position-exact), FP64-accurate
-    const uint64_t bx = (uint64_t)__double_as_longlong(A.x[p]);
-    const uint64_t by = (uint64_t)__double_as_longlong(A.y[p]);
-    double xn, yn, ud = (double)un, vd = (double)vn;
+    // position (eq. Lagrangian-position-exact), fixed point
+    const int64_t X0 = A.x[p], Y0 = A.y[p];
+    fx::acc a;
+    a.init(fx::mul_f(F.dt, U0));
+    a.add(fx::mul_f(F.sdiff, D.g[0]));
+    fx::acc c;
+    c.init(fx::mul_f(F.dt, U1));
+    c.add(fx::mul_f(F.sdiff, D.g[1]));
+    int64_t Xn = X0, Yn = Y0;
     bool slow, reinj = false;
-    if (fx::d_exp(bx) <= kExpMax && fx::d_exp(by) <= kExpMax) {
-      fx::acc a;
-      a.init(fx::mul_f(F.dt, U0));
-      a.add(fx::mul_f(F.sdiff, D.g[0]));
-      int64_t Xn = fx::d2fix(bx, kF) + a.fix(kF);
-      fx::acc c;
-      c.init(fx::mul_f(F.dt, U1));
-      c.add(fx::mul_f(F.sdiff, D.g[1]));
-      const int64_t Yn = fx::d2fix(by, kF) + c.fix(kF);
+    double xn, yn;
+    if (small_move(a) && small_move(c)) {
+      Xn = X0 + a.fix(kF);
+      Yn = Y0 + c.fix(kF);
       int steps = 0;
       slow = walk_fx(F, e, Xn, Yn, steps, c_per, c_near, reinj);
       c_walk += steps;
       xn = __longlong_as_double((long long)fx::fix2d(Xn, kF));
       yn = __longlong_as_double((long long)fx::fix2d(Yn, kF));
     } else {
-      xn = A.x[p] + (double)U0 * A.dt + A.sdiff * (double)D.g[0];
-      yn = A.y[p] + (double)U1 * A.dt + A.sdiff * (double)D.g[1];
+      xn = __longlong_as_double((long long)fx::fix2d(X0, kF)) + (double)U0 * A.dt + A.sdiff * (double)D.g[0];
+      yn = __longlong_as_double((long long)fx::fix2d(Y0, kF)) + (double)U1 * A.dt + A.sdiff * (double)D.g[1];
       slow = true;
     }
     if (slow) {
+      double ud = (double)un, vd = (double)vn;
       const int32_t en = walk_slow(A, e, xn, yn, ud, vd, cs, reinj);
-      if (en >= 0) e = en; else { ++cs.lost; e = A.elem[p]; }
-      un = (float)ud;
-      vn = (float)vd;
+      if (en >= 0 && pos_fits(xn) && pos_fits(yn)) {
+        e = en;
+        Xn = fx::d2fix((uint64_t)__double_as_longlong(xn), kF);
+        Yn = fx::d2fix((uint64_t)__double_as_longlong(yn), kF);
+        un = (float)ud;
+        vn = (float)vd;
+      } else {  // lost: keeps its element and position
+        ++cs.lost;
+        e = A.elem[p];
+        Xn = X0;
+        Yn = Y0;
+      }
     }
     float sf = reinj ? 0.0f : sn;
-    if (in_source(A, xn, yn)) sf = 1.0f;
-    A.x[p] = xn;
-    A.y[p] = yn;
+    if (in_source_fx(A, F, Xn, Yn)) sf = 1.0f;
+    A.x[p] = Xn;
+    A.y[p] = Yn;
     S.u[p] = un;
     S.v[p] = vn;
     S.w[p] = wn;
@@ -845,6 +912,20 @@ extern "C" pdf_status pdf_step(pdf_particles* p, const pdf_mesh* m, const pdf_mo
     F.dt = fx::d2df(b);
     std::memcpy(&b, &A.sdiff, 8);
     F.sdiff = fx::d2df(b);
+    F.src_mode = 0;
+    F.src_x = F.src_y = 0;
+    F.src_r2 = fx::df{0.f, 0.f};
+    if (params->src_r > 0.0) {
+      const double r2 = params->src_r * params->src_r;
+      F.src_mode = (std::fabs(params->src_x) < 64.0 && std::fabs(params->src_y) < 64.0 && r2 < 1e30) ? 1 : 2;
+      if (F.src_mode == 1) {
+        std::memcpy(&b, &params->src_x, 8);
+        F.src_x = fx::d2fix(b, kF);
+        std::memcpy(&b, &params->src_y, 8);
+        F.src_y = fx::d2fix(b, kF);
+        F.src_r2 = fx::from_double(r2);
+      }
+    }
     if (p->precision == PDF_FP32_STATE) {
       F32Args S;
       S.u = p->uf; S.v = p->vf; S.w = p->wf; S.om = p->omf; S.ps = p->psf;

@@ -28,3 +28,23 @@ def field_close(a, b, rtol=RTOL, axis=0):
 def assert_field_close(a, b, what, rtol=RTOL):
     ok, worst = field_close(a, b, rtol)
     assert ok, "%s: worst scaled error %.3e > %.1e" % (what, worst, rtol)
+
+
+def stored_position(x):
+    """x rounded to the library's stored position format: 64-bit fixed
+    point with 56 fraction bits, rounded to nearest with ties away from
+    zero (returned as the FP64 value it reads back as; exact for |x| < 64)."""
+    x = np.asarray(x, dtype=np.float64)
+    s = np.ldexp(np.abs(x), 56)
+    fl = np.floor(s)
+    r = np.where(s - fl >= 0.5, fl + 1.0, fl)
+    return np.copysign(np.ldexp(r, -56), x)
+
+
+def stored_df(x):
+    """x rounded to the library's stored double-float pair (h = x rounded to
+    FP32, l = the remainder rounded to FP32), read back as the FP64 sum."""
+    x = np.asarray(x, dtype=np.float64)
+    h = x.astype(np.float32).astype(np.float64)
+    lo = (x - h).astype(np.float32).astype(np.float64)
+    return h + lo
