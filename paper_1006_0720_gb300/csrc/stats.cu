@@ -302,30 +302,33 @@ __device__ __forceinline__ long long to_fix(const float* a, int64_t i, int lim, 
   return fx::f2fix(f, kFQ);
 }
 
-// Per-warp shared scratch of the statistics kernel: lane partials, stored
-// column-wise so that one lane can add up one quantity over the 32 lanes.
-// Rows are padded to 33 entries so that the lanes reading different
-// quantities at the same column hit different banks; the integer partials
-// of pass 1 and the double-float partials of pass 2 share the storage.
+// Per-warp shared scratch of the statistics kernel.  Lane partials are
+// stored column-wise so that one lane can add up one quantity over the 32
+// lanes; rows are padded to 33 entries so that the lanes reading different
+// quantities at the same column hit different banks.  Pass 1 also keeps the
+// fixed-point u, v, w, psi of the element's first kStatCache particles for
+// pass 2 (which re-reads only the rest); the double-float partials of pass
+// 2 reuse that storage once it has been read.
+constexpr int kStatCache = 128;
 struct StatScratch {
+  unsigned long long lo[5][33];
+  long long hi[5][33];
   union {
-    struct {
-      unsigned long long lo[5][33];
-      long long hi[5][33];
-    } i;
+    long long q[4][kStatCache];
     struct {
       float h[11][33], l[11][33];
     } f;
   };
 };
+constexpr int kStatWarps = 4;  // warps per block (27 KB of shared memory)
 
 template <typename T>
-__global__ void __launch_bounds__(256, 4) k_elem_stats_fx(const int32_t* __restrict__ seg,
+__global__ void __launch_bounds__(kStatWarps * 32, 8) k_elem_stats_fx(const int32_t* __restrict__ seg,
                                                        const int32_t* __restrict__ pid, int32_t n_tri,
                                                        const T* __restrict__ u, const T* __restrict__ v,
                                                        const T* __restrict__ w, const T* __restrict__ om,
                                                        const T* __restrict__ ps, double* __restrict__ es) {
-  __shared__ StatScratch scratch[8];
+  __shared__ StatScratch scratch[kStatWarps];
   StatScratch& SS = scratch[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -345,11 +348,20 @@ __global__ void __launch_bounds__(256, 4) k_elem_stats_fx(const int32_t* __restr
     bool ok = N <= (1 << 17);
     for (int32_t i = beg + lane; i < end; i += 32) {
       const int32_t p = pid[i];
-      add64(lo[0], hi[0], to_fix(u, p, 6, ok));
-      add64(lo[1], hi[1], to_fix(v, p, 6, ok));
-      add64(lo[2], hi[2], to_fix(w, p, 6, ok));
+      const long long qu = to_fix(u, p, 6, ok), qv = to_fix(v, p, 6, ok), qw = to_fix(w, p, 6, ok);
+      const long long qs = to_fix(ps, p, 6, ok);
+      add64(lo[0], hi[0], qu);
+      add64(lo[1], hi[1], qv);
+      add64(lo[2], hi[2], qw);
       add64(lo[3], hi[3], to_fix(om, p, 13, ok));
-      add64(lo[4], hi[4], to_fix(ps, p, 6, ok));
+      add64(lo[4], hi[4], qs);
+      const int32_t slot = i - beg;
+      if (slot < kStatCache) {
+        SS.q[0][slot] = qu;
+        SS.q[1][slot] = qv;
+        SS.q[2][slot] = qw;
+        SS.q[3][slot] = qs;
+      }
     }
     ok = __all_sync(0xffffffffu, ok);
     if (!ok) {
@@ -358,8 +370,8 @@ __global__ void __launch_bounds__(256, 4) k_elem_stats_fx(const int32_t* __restr
     }
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-      SS.i.lo[q][lane] = lo[q];
-      SS.i.hi[q][lane] = hi[q];
+      SS.lo[q][lane] = lo[q];
+      SS.hi[q][lane] = hi[q];
     }
     __syncwarp();
     // lane q < 5 adds quantity q over the lanes (exact) and forms its mean
@@ -369,8 +381,8 @@ __global__ void __launch_bounds__(256, 4) k_elem_stats_fx(const int32_t* __restr
       unsigned long long sl = 0;
       long long sh = 0;
       for (int j = 0; j < 32; ++j) {
-        const unsigned long long nl = sl + SS.i.lo[lane][j];
-        sh = sh + SS.i.hi[lane][j] + (nl < sl ? 1 : 0);
+        const unsigned long long nl = sl + SS.lo[lane][j];
+        sh = sh + SS.hi[lane][j] + (nl < sl ? 1 : 0);
         sl = nl;
       }
       mean = fx::df_norm(fx::mul(fx::i128_to_df(sl, sh, -kFQ), invN));
@@ -391,12 +403,25 @@ __global__ void __launch_bounds__(256, 4) k_elem_stats_fx(const int32_t* __restr
 #pragma unroll
     for (int k = 0; k < 4; ++k) d[k].init(fx::df{0.f, 0.f});
     for (int32_t i = beg + lane; i < end; i += 32) {
-      const int32_t p = pid[i];
-      bool dummy = true;
-      const fx::df D0 = fx::fix2df(to_fix(u, p, 6, dummy) - M[0], kFQ);
-      const fx::df D1 = fx::fix2df(to_fix(v, p, 6, dummy) - M[1], kFQ);
-      const fx::df D2 = fx::fix2df(to_fix(w, p, 6, dummy) - M[2], kFQ);
-      const fx::df D3 = fx::fix2df(to_fix(ps, p, 6, dummy) - M[3], kFQ);
+      const int32_t slot = i - beg;
+      long long qu, qv, qw, qs;
+      if (slot < kStatCache) {
+        qu = SS.q[0][slot];
+        qv = SS.q[1][slot];
+        qw = SS.q[2][slot];
+        qs = SS.q[3][slot];
+      } else {
+        const int32_t p = pid[i];
+        bool dummy = true;
+        qu = to_fix(u, p, 6, dummy);
+        qv = to_fix(v, p, 6, dummy);
+        qw = to_fix(w, p, 6, dummy);
+        qs = to_fix(ps, p, 6, dummy);
+      }
+      const fx::df D0 = fx::fix2df(qu - M[0], kFQ);
+      const fx::df D1 = fx::fix2df(qv - M[1], kFQ);
+      const fx::df D2 = fx::fix2df(qw - M[2], kFQ);
+      const fx::df D3 = fx::fix2df(qs - M[3], kFQ);
       d[0].add(D0); d[1].add(D1); d[2].add(D2); d[3].add(D3);
       c[0].add(fx::mul(D0, D0));
       c[1].add(fx::mul(D1, D1));
@@ -596,10 +621,10 @@ pdf_status estimate_stats(pdf_particles* P, cudaStream_t st) {
   pdf_status s = group_by_element(P, st);
   if (s != PDF_OK) return s;
   if (P->precision == PDF_FP64)
-    PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<fx::df><<<blocks_for((int64_t)M.n_tri * 32, 256), 256, 0, st>>>(
+    PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<fx::df><<<blocks_for((int64_t)M.n_tri * 32, kStatWarps * 32), kStatWarps * 32, 0, st>>>(
         P->seg, P->sorted_pid, M.n_tri, P->u, P->v, P->w, P->om, P->ps, P->es));
   else
-    PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<float><<<blocks_for((int64_t)M.n_tri * 32, 256), 256, 0, st>>>(
+    PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<float><<<blocks_for((int64_t)M.n_tri * 32, kStatWarps * 32), kStatWarps * 32, 0, st>>>(
         P->seg, P->sorted_pid, M.n_tri, P->uf, P->vf, P->wf, P->omf, P->psf, P->es));
   PDF_KERNEL("k_node_stats", st, k_node_stats<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(M.nse_off, M.nse, M.n_nodes, P->es, P->ns,
                                                           P->counters + 8););
@@ -666,10 +691,10 @@ pdf_status estimate_stats_with_buffers(pdf_particles* P, int32_t* keys_a, int32_
   }
   PDF_KERNEL("k_seg_offsets", st, k_seg_offsets<<<blocks_for(n + 1, 256), 256, 0, st>>>(kin, n, M.n_tri, seg));
   if (P->precision == PDF_FP64)
-    PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<fx::df><<<blocks_for((int64_t)M.n_tri * 32, 256), 256, 0, st>>>(
+    PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<fx::df><<<blocks_for((int64_t)M.n_tri * 32, kStatWarps * 32), kStatWarps * 32, 0, st>>>(
                                        seg, vin, M.n_tri, P->u, P->v, P->w, P->om, P->ps, P->es));
   else
-    PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<float><<<blocks_for((int64_t)M.n_tri * 32, 256), 256, 0, st>>>(
+    PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<float><<<blocks_for((int64_t)M.n_tri * 32, kStatWarps * 32), kStatWarps * 32, 0, st>>>(
                                        seg, vin, M.n_tri, P->uf, P->vf, P->wf, P->omf, P->psf, P->es));
   PDF_KERNEL("k_node_stats", st, k_node_stats<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(
                                      M.nse_off, M.nse, M.n_nodes, P->es, P->ns, P->counters + 8));
