@@ -217,9 +217,11 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- device-resident timed region
+    # ---- device-resident timed region (CUDA events around k_step only, for
+    # its average launch duration)
     clocks = ClockSampler(local)
     pg.pdf_profile_reset()
+    pg.pdf_profile_only("k_step")
     pg.pdf_profile_enable(True)
     launches0 = pg.pdf_kernel_launches()
     barrier()
@@ -238,12 +240,28 @@ def run_gpu(args):
     pg.pdf_profile_enable(False)
     ms = ev0.elapsed_time(ev1)
     k_launch, k_ms = pg.pdf_profile_query("k_step")
+    pg.pdf_profile_reset()
+    # ---- a second pass of the same steps with every kernel timed, for the
+    # per-kernel shares (events around every launch add a few us each)
+    pg.pdf_profile_only(None)
+    pg.pdf_profile_enable(True)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        pg.pdf_step(gp, gm, p, step=step_no, stream=stream)
+        pg.pdf_estimate_stats(gp, gm, stream=stream)
+        step_no += 1
+    ev1.record(stream)
+    barrier()
+    pg.pdf_profile_enable(False)
+    ms_prof = ev0.elapsed_time(ev1)
     shares = {}
     for kname in ("k_step", "k_radix_scatter", "k_radix_hist", "k_elem_stats", "k_node_coeff",
                   "k_elem_rows", "k_seg_offsets", "k_node_stats", "k_scan_reduce", "k_scan_apply",
-                  "k_scan_top", "k_elem_grad1", "k_node_grad1", "k_elem_grad2", "k_node_grad2"):
+                  "k_scan_top", "k_elem_grad1", "k_node_grad1", "k_elem_grad2", "k_node_grad2", "k_reorder"):
         c, t = pg.pdf_profile_query(kname)
-        shares[kname] = {"launches": c, "ms_per_launch": t / c if c else None, "share": t / ms if ms else None}
+        shares[kname] = {"launches": c, "ms_per_launch": t / c if c else None,
+                         "share": t / ms_prof if ms_prof else None}
     pg.pdf_profile_reset()
     t_max = ms
     if dist is not None:
@@ -309,7 +327,7 @@ def run_gpu(args):
                        "l2": "inputs larger than L2: particle state %.2f GB vs 129 MB L2" % (n * 64 / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "hbm_frac_step": step_frac, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
-            "roofline": roofline, "kernels": shares}
+            "roofline": roofline, "kernels": shares, "kernels_pass_ms_per_step": ms_prof / args.steps}
     # the complex-geometry workload (obstacles, FP32 state, 68.6M particles)
     if not args.skip_extras:
         del gp

@@ -178,6 +178,18 @@ pdf_status pdf_particles_init(const pdf_mesh* m, const pdf_init_params* ip, uint
                               int32_t precision, void* stream, pdf_particles** out);
 pdf_status pdf_particles_destroy(pdf_particles* p);
 pdf_status pdf_particles_count(const pdf_particles* p, int64_t* n);
+/* Storage order.  Every `every`-th pdf_estimate_stats call (default 8; 0
+ * never) copies the state into the element order its grouping computed, so
+ * that the particles of one element sit in consecutive slots and the
+ * step's coefficient-row and geometry loads, and the statistics' reads,
+ * stay local as particles disperse.  The copy needs a second set of state
+ * arrays (allocated by pdf_particles_init).  The order is invisible at the
+ * interface: particle ids (the random-number counters and the order of
+ * pdf_particles_get_state/set_state) move with the particles.  Results
+ * depend on it only through the order of the rounded double-float sums of
+ * the central moments.  The paper has no counterpart (its particles live
+ * in per-element linked lists).  PDF_EINVAL for every < 0. */
+pdf_status pdf_particles_set_reorder(pdf_particles* p, int32_t every);
 
 /* Copies the state, converted to FP64, into caller buffers [n] (any pointer
  * may be NULL).  The buffers may be device or host memory: device buffers
@@ -370,6 +382,10 @@ pdf_status pdf_rng_gauss(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3, i
  * (e.g. "k_step") and returns how many launches were recorded and their
  * summed duration since the last reset. */
 pdf_status pdf_profile_enable(int32_t on);
+/* Restricts the timing to the kernels named `kernel` (NULL: all kernels),
+ * so that a measurement of one kernel does not pay for the events around
+ * the others. */
+pdf_status pdf_profile_only(const char* kernel);
 pdf_status pdf_profile_reset(void);
 pdf_status pdf_profile_query(const char* kernel, int64_t* launches, double* total_ms);
 /* Number of kernels the library has launched in this process. */

@@ -129,6 +129,10 @@ class Particles:
                                             _stream(stream)), "pdf_particles_get_state")
         return out
 
+    def set_reorder(self, every):
+        """Copy the state into element order every `every` statistics calls (0: never)."""
+        check(lib().pdf_particles_set_reorder(self.handle, int(every)), "pdf_particles_set_reorder")
+
     def set_state(self, st, stream=None):
         args = []
         for k in ("x", "y", "u", "v", "w", "om", "ps"):
@@ -216,6 +220,10 @@ def pdf_last_error():
 
 def pdf_profile_enable(on=True):
     check(lib().pdf_profile_enable(1 if on else 0), "pdf_profile_enable")
+
+
+def pdf_profile_only(kernel=None):
+    check(lib().pdf_profile_only(kernel.encode() if kernel else None), "pdf_profile_only")
 
 
 def pdf_profile_reset():

@@ -72,6 +72,7 @@ PROTOTYPES = {
     "pdf_particles_init": (I32, [V, ctypes.POINTER(InitParams), U64, I32, V, PV]),
     "pdf_particles_destroy": (I32, [V]),
     "pdf_particles_count": (I32, [V, ctypes.POINTER(I64)]),
+    "pdf_particles_set_reorder": (I32, [V, I32]),
     "pdf_particles_get_state": (I32, [V, V, V, V, V, V, V, V, V, V]),
     "pdf_particles_set_state": (I32, [V, V, V, V, V, V, V, V, V, V]),
     "pdf_step": (I32, [V, V, ctypes.POINTER(ModelParams), V, V, U32, V, ctypes.POINTER(StepInfo)]),
@@ -92,6 +93,7 @@ PROTOTYPES = {
     "pdf_mlp_guess": (I32, [V, V, V, V, V, V]),
     "pdf_rng_gauss": (I32, [U64, U32, U32, U32, I64, V, V]),
     "pdf_profile_enable": (I32, [I32]),
+    "pdf_profile_only": (I32, [ctypes.c_char_p]),
     "pdf_profile_reset": (I32, []),
     "pdf_profile_query": (I32, [ctypes.c_char_p, ctypes.POINTER(I64), ctypes.POINTER(D)]),
     "pdf_kernel_launches": (I64, []),

@@ -146,8 +146,13 @@ struct pdf_mesh {
 //   u, v, w, om, ps   PDF_FP64: double-float pairs (h, l), |l| <= ulp(h)/2,
 //                     48 significant bits, the full FP32 exponent range;
 //                     PDF_FP32_STATE: FP32 (uf ... psf).
-// The public interface reads and writes FP64; the conversions run in
-// pdf_particles_get_state / pdf_particles_set_state.
+// The public interface reads and writes FP64 in particle-id order; the
+// conversions run in pdf_particles_get_state / pdf_particles_set_state.
+// Storage order: every `reorder_every` statistics calls the state is
+// permuted into the element order of the grouping (so that the particles
+// of one element sit together and a warp's row, geometry and state loads
+// stay local); pid[i] is the particle id held in slot i (the Philox counter
+// and the interface order).
 struct pdf_particles {
   const pdf_mesh* mesh = nullptr;
   int64_t n = 0;
@@ -156,7 +161,14 @@ struct pdf_particles {
   int64_t *x = nullptr, *y = nullptr;
   fx::df *u = nullptr, *v = nullptr, *w = nullptr, *om = nullptr, *ps = nullptr;
   int32_t* elem = nullptr;
+  int32_t* pid = nullptr;
   float *uf = nullptr, *vf = nullptr, *wf = nullptr, *omf = nullptr, *psf = nullptr;
+  // the other half of each state array for the reordering copy
+  int64_t *x2 = nullptr, *y2 = nullptr;
+  fx::df *u2 = nullptr, *v2 = nullptr, *w2 = nullptr, *om2 = nullptr, *ps2 = nullptr;
+  float *uf2 = nullptr, *vf2 = nullptr, *wf2 = nullptr, *omf2 = nullptr, *psf2 = nullptr;
+  int32_t* pid2 = nullptr;
+  int32_t reorder_every = 8, since_reorder = 0;
   double* stage = nullptr;  // [n] FP64 staging for host transfers (allocated on first use)
   float* rows_f32 = nullptr;  // [n_tri][32] coefficient rows in FP32 (same layout as rows)
   // statistics
@@ -174,7 +186,8 @@ struct pdf_particles {
   int32_t* hist = nullptr;       // [bins][tiles]
   int32_t* hist_part = nullptr;  // scan partials
   int32_t* seg = nullptr;        // [n_tri + 1] segment offsets into the sorted order
-  const int32_t* sorted_pid = nullptr;  // points into vals[]
+  const int32_t* sorted_pid = nullptr;  // storage slot of each sorted position (vals[]), NULL: identity
+  int sorted_key_slot = 0;              // keys[] buffer holding the sorted element ids
   int64_t n_tiles = 0;
   int64_t hist_len = 0;
   int32_t n_scan_blocks = 0;

@@ -21,8 +21,9 @@ __global__ void k_init(const double* __restrict__ xy, const int32_t* __restrict_
                        const double* __restrict__ elem_psi0, int64_t* __restrict__ x,
                        int64_t* __restrict__ y, fx::df* __restrict__ u, fx::df* __restrict__ v,
                        fx::df* __restrict__ w, fx::df* __restrict__ om, fx::df* __restrict__ ps,
-                       int32_t* __restrict__ elem, float* __restrict__ uf, float* __restrict__ vf,
-                       float* __restrict__ wf, float* __restrict__ omf, float* __restrict__ psf) {
+                       int32_t* __restrict__ elem, int32_t* __restrict__ pid, float* __restrict__ uf,
+                       float* __restrict__ vf, float* __restrict__ wf, float* __restrict__ omf,
+                       float* __restrict__ psf) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     // host element: largest e with elem_off[e] <= p
@@ -74,6 +75,7 @@ __global__ void k_init(const double* __restrict__ xy, const int32_t* __restrict_
       omf[p] = __double2float_rn(O); psf[p] = __double2float_rn(S);
     }
     elem[p] = e;
+    pid[p] = (int32_t)p;
   }
 }
 
@@ -87,20 +89,35 @@ __global__ void k_rng_gauss(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3
   }
 }
 
-// Stored representation -> FP64 (get_state) and back (set_state).
-__global__ void k_fix_to_f64(const int64_t* __restrict__ a, double* __restrict__ b, int64_t n) {
+// Stored representation in storage order -> FP64 in particle-id order
+// (get_state) and back (set_state, which leaves the storage in id order).
+__global__ void k_fix_to_f64(const int64_t* __restrict__ a, const int32_t* __restrict__ pid,
+                             double* __restrict__ b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = __longlong_as_double((long long)fx::fix2d(a[i], kPosF));
+    b[pid[i]] = __longlong_as_double((long long)fx::fix2d(a[i], kPosF));
 }
 
-__global__ void k_df_to_f64(const fx::df* __restrict__ a, double* __restrict__ b, int64_t n) {
+__global__ void k_df_to_f64(const fx::df* __restrict__ a, const int32_t* __restrict__ pid,
+                            double* __restrict__ b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = fx::to_double(a[i]);
+    b[pid[i]] = fx::to_double(a[i]);
 }
 
-__global__ void k_f32_to_f64(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+__global__ void k_f32_to_f64(const float* __restrict__ a, const int32_t* __restrict__ pid,
+                             double* __restrict__ b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = (double)a[i];
+    b[pid[i]] = (double)a[i];
+}
+
+__global__ void k_elem_by_id(const int32_t* __restrict__ a, const int32_t* __restrict__ pid,
+                             int32_t* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[pid[i]] = a[i];
+}
+
+__global__ void k_iota(int32_t* __restrict__ a, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = (int32_t)i;
 }
 
 // Positions outside |x| < 64 are counted in *bad and stored as 0.
@@ -132,6 +149,10 @@ static void free_particles(pdf_particles* p) {
   cudaFree(p->uf); cudaFree(p->vf); cudaFree(p->wf); cudaFree(p->omf); cudaFree(p->psf); cudaFree(p->rows_f32);
   cudaFree(p->x); cudaFree(p->y);
   cudaFree(p->u); cudaFree(p->v); cudaFree(p->w); cudaFree(p->om); cudaFree(p->ps);
+  cudaFree(p->x2); cudaFree(p->y2);
+  cudaFree(p->u2); cudaFree(p->v2); cudaFree(p->w2); cudaFree(p->om2); cudaFree(p->ps2);
+  cudaFree(p->uf2); cudaFree(p->vf2); cudaFree(p->wf2); cudaFree(p->omf2); cudaFree(p->psf2);
+  cudaFree(p->pid); cudaFree(p->pid2);
   cudaFree(p->stage);
   double* dbl[] = {p->es, p->ns, p->nd, p->eg, p->nc, p->rows};
   for (double* d : dbl) cudaFree(d);
@@ -189,11 +210,14 @@ extern "C" pdf_status pdf_particles_init(const pdf_mesh* m, const pdf_init_param
   P->n = n;
   P->precision = precision;
   P->seed = seed;
-  TRY_ALLOC(P->x, n); TRY_ALLOC(P->y, n); TRY_ALLOC(P->elem, n);
+  TRY_ALLOC(P->x, n); TRY_ALLOC(P->y, n); TRY_ALLOC(P->elem, n); TRY_ALLOC(P->pid, n);
+  TRY_ALLOC(P->x2, n); TRY_ALLOC(P->y2, n); TRY_ALLOC(P->pid2, n);
   if (precision == PDF_FP64) {
     TRY_ALLOC(P->u, n); TRY_ALLOC(P->v, n); TRY_ALLOC(P->w, n); TRY_ALLOC(P->om, n); TRY_ALLOC(P->ps, n);
+    TRY_ALLOC(P->u2, n); TRY_ALLOC(P->v2, n); TRY_ALLOC(P->w2, n); TRY_ALLOC(P->om2, n); TRY_ALLOC(P->ps2, n);
   } else {
     TRY_ALLOC(P->uf, n); TRY_ALLOC(P->vf, n); TRY_ALLOC(P->wf, n); TRY_ALLOC(P->omf, n); TRY_ALLOC(P->psf, n);
+    TRY_ALLOC(P->uf2, n); TRY_ALLOC(P->vf2, n); TRY_ALLOC(P->wf2, n); TRY_ALLOC(P->omf2, n); TRY_ALLOC(P->psf2, n);
     TRY_ALLOC(P->rows_f32, (int64_t)n_tri * PDFGB_ROW);
   }
   TRY_ALLOC(P->es, (int64_t)n_tri * PDF_NES);
@@ -226,8 +250,8 @@ extern "C" pdf_status pdf_particles_init(const pdf_mesh* m, const pdf_init_param
     prof_launch("k_init", st, nullptr, nullptr);  // counted only
     k_init<<<grid_for(n, 256), 256, 0, st>>>(m->d.xy, m->d.tri, d_off, n_tri, n, seed,
                                               ip->u_profile, ip->u_sigma, d_psi, P->x, P->y, P->u,
-                                              P->v, P->w, P->om, P->ps, P->elem, P->uf, P->vf, P->wf,
-                                              P->omf, P->psf);
+                                              P->v, P->w, P->om, P->ps, P->elem, P->pid, P->uf, P->vf,
+                                              P->wf, P->omf, P->psf);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -289,15 +313,24 @@ extern "C" pdf_status pdf_particles_get_state(const pdf_particles* p, double* x,
     double* to = dev ? dst[i] : p->stage;
     if (i < 2) {
       const int64_t* a = i == 0 ? p->x : p->y;
-      PDF_KERNEL("k_fix_to_f64", st, k_fix_to_f64<<<g, 256, 0, st>>>(a, to, p->n));
+      PDF_KERNEL("k_fix_to_f64", st, k_fix_to_f64<<<g, 256, 0, st>>>(a, p->pid, to, p->n));
     } else if (srcd[i]) {
-      PDF_KERNEL("k_df_to_f64", st, k_df_to_f64<<<g, 256, 0, st>>>(srcd[i], to, p->n));
+      PDF_KERNEL("k_df_to_f64", st, k_df_to_f64<<<g, 256, 0, st>>>(srcd[i], p->pid, to, p->n));
     } else {
-      PDF_KERNEL("k_f32_to_f64", st, k_f32_to_f64<<<g, 256, 0, st>>>(srcf[i], to, p->n));
+      PDF_KERNEL("k_f32_to_f64", st, k_f32_to_f64<<<g, 256, 0, st>>>(srcf[i], p->pid, to, p->n));
     }
     if (!dev) PDF_CUDA(cudaMemcpyAsync(dst[i], p->stage, b, cudaMemcpyDeviceToHost, st));
   }
-  if (elem) PDF_CUDA(cudaMemcpyAsync(elem, p->elem, sizeof(int32_t) * p->n, cudaMemcpyDefault, st));
+  if (elem) {
+    const bool dev = is_device_ptr(elem);
+    if (!dev) {
+      pdf_status s = ensure_stage(p);
+      if (s != PDF_OK) return s;
+    }
+    int32_t* to = dev ? elem : reinterpret_cast<int32_t*>(p->stage);
+    PDF_KERNEL("k_elem_by_id", st, k_elem_by_id<<<g, 256, 0, st>>>(p->elem, p->pid, to, p->n));
+    if (!dev) PDF_CUDA(cudaMemcpyAsync(elem, p->stage, sizeof(int32_t) * p->n, cudaMemcpyDeviceToHost, st));
+  }
   return PDF_OK;
 }
 
@@ -333,10 +366,19 @@ extern "C" pdf_status pdf_particles_set_state(pdf_particles* p, const double* x,
     }
   }
   PDF_CUDA(cudaMemcpyAsync(p->elem, elem, sizeof(int32_t) * p->n, cudaMemcpyDefault, st));
+  PDF_KERNEL("k_iota", st, k_iota<<<g, 256, 0, st>>>(p->pid, p->n));
+  p->since_reorder = 0;
   long long nbad = 0;
   PDF_CUDA(cudaMemcpyAsync(&nbad, bad, sizeof(long long), cudaMemcpyDeviceToHost, st));
   PDF_CUDA(cudaStreamSynchronize(st));
   if (nbad) return fail(PDF_EINVAL, "pdf_particles_set_state: positions must lie within |x|, |y| < 64");
+  return PDF_OK;
+}
+
+extern "C" pdf_status pdf_particles_set_reorder(pdf_particles* p, int32_t every) {
+  if (!p || every < 0) return fail(PDF_EINVAL, "pdf_particles_set_reorder: NULL handle or negative interval");
+  p->reorder_every = every;
+  p->since_reorder = 0;
   return PDF_OK;
 }
 

@@ -16,6 +16,7 @@ struct Rec {
 };
 std::mutex g_mu;
 bool g_on = false;
+std::string g_only;  // empty: every kernel
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
 std::atomic<long long> g_launches{0};
@@ -40,6 +41,10 @@ void prof_launch(const char* name, cudaStream_t st, void (*launch)(void*), void*
     return;
   }
   std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_only.empty() && g_only != name) {
+    launch(ctx);
+    return;
+  }
   Rec r{name, take_event(), take_event()};
   cudaEventRecord(r.a, st);
   launch(ctx);
@@ -54,6 +59,12 @@ using namespace pdfgb;
 extern "C" pdf_status pdf_profile_enable(int32_t on) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_on = on != 0;
+  return PDF_OK;
+}
+
+extern "C" pdf_status pdf_profile_only(const char* kernel) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_only = kernel ? kernel : "";
   return PDF_OK;
 }
 

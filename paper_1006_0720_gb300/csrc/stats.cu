@@ -193,7 +193,7 @@ __device__ void elem_stats_fp64(int32_t beg, int32_t end, int lane, const int32_
   const int32_t N = end - beg;
   double s[5] = {0, 0, 0, 0, 0};
   for (int32_t i = beg + lane; i < end; i += 32) {
-    const int32_t p = pid[i];
+    const int32_t p = pid ? pid[i] : i;
     s[0] += ld64(u, p); s[1] += ld64(v, p); s[2] += ld64(w, p); s[3] += ld64(om, p); s[4] += ld64(ps, p);
   }
 #pragma unroll
@@ -204,7 +204,7 @@ __device__ void elem_stats_fp64(int32_t beg, int32_t end, int lane, const int32_
   }
   double c[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int32_t i = beg + lane; i < end; i += 32) {
-    const int32_t p = pid[i];
+    const int32_t p = pid ? pid[i] : i;
     const double du = ld64(u, p) - s[0], dv = ld64(v, p) - s[1], dw = ld64(w, p) - s[2],
                  dp = ld64(ps, p) - s[4];
     c[0] += du * du; c[1] += dv * dv; c[2] += dw * dw;
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(kStatWarps * 32, 8) k_elem_stats_fx(const int3
     long long hi[5] = {0, 0, 0, 0, 0};
     bool ok = N <= (1 << 17);
     for (int32_t i = beg + lane; i < end; i += 32) {
-      const int32_t p = pid[i];
+      const int32_t p = pid ? pid[i] : i;
       const long long qu = to_fix(u, p, 6, ok), qv = to_fix(v, p, 6, ok), qw = to_fix(w, p, 6, ok);
       const long long qs = to_fix(ps, p, 6, ok);
       add64(lo[0], hi[0], qu);
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(kStatWarps * 32, 8) k_elem_stats_fx(const int3
         qw = SS.q[2][slot];
         qs = SS.q[3][slot];
       } else {
-        const int32_t p = pid[i];
+        const int32_t p = pid ? pid[i] : i;
         bool dummy = true;
         qu = to_fix(u, p, 6, dummy);
         qv = to_fix(v, p, 6, dummy);
@@ -613,6 +613,67 @@ pdf_status group_by_element(pdf_particles* P, cudaStream_t st) {
   }
   PDF_KERNEL("k_seg_offsets", st, k_seg_offsets<<<blocks_for(n + 1, 256), 256, 0, st>>>(kin, n, n_tri, P->seg););
   P->sorted_pid = vin;
+  P->sorted_key_slot = cur ^ 1;
+  return PDF_OK;
+}
+
+// Copy of every state array into the grouping's order (slot i <- slot idx[i]).
+struct ReorderArgs {
+  const int32_t* idx;
+  int64_t n;
+  const long long* src8[7];
+  long long* dst8[7];
+  const int32_t* src4[6];
+  int32_t* dst4[6];
+  int n8, n4;
+};
+
+__global__ void k_reorder(ReorderArgs R) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < R.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t j = R.idx[i];
+#pragma unroll
+    for (int k = 0; k < 7; ++k)
+      if (k < R.n8) R.dst8[k][i] = __ldg(R.src8[k] + j);
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (k < R.n4) R.dst4[k][i] = __ldg(R.src4[k] + j);
+  }
+}
+
+// Permutes the state into element order after a grouping: afterwards the
+// sorted order is the storage order (sorted_pid = NULL) and the element ids
+// are the sorted keys.
+static pdf_status reorder_state(pdf_particles* P, cudaStream_t st) {
+  ReorderArgs R;
+  R.idx = P->sorted_pid;
+  R.n = P->n;
+  R.n8 = R.n4 = 0;
+  auto add8 = [&](void* src, void* dst) {
+    R.src8[R.n8] = static_cast<const long long*>(src);
+    R.dst8[R.n8++] = static_cast<long long*>(dst);
+  };
+  auto add4 = [&](void* src, void* dst) {
+    R.src4[R.n4] = static_cast<const int32_t*>(src);
+    R.dst4[R.n4++] = static_cast<int32_t*>(dst);
+  };
+  add8(P->x, P->x2);
+  add8(P->y, P->y2);
+  if (P->precision == PDF_FP64) {
+    add8(P->u, P->u2); add8(P->v, P->v2); add8(P->w, P->w2); add8(P->om, P->om2); add8(P->ps, P->ps2);
+  } else {
+    add4(P->uf, P->uf2); add4(P->vf, P->vf2); add4(P->wf, P->wf2); add4(P->omf, P->omf2); add4(P->psf, P->psf2);
+  }
+  add4(P->pid, P->pid2);
+  PDF_KERNEL("k_reorder", st, k_reorder<<<blocks_for(P->n, 256), 256, 0, st>>>(R););
+  std::swap(P->x, P->x2);
+  std::swap(P->y, P->y2);
+  std::swap(P->u, P->u2); std::swap(P->v, P->v2); std::swap(P->w, P->w2);
+  std::swap(P->om, P->om2); std::swap(P->ps, P->ps2);
+  std::swap(P->uf, P->uf2); std::swap(P->vf, P->vf2); std::swap(P->wf, P->wf2);
+  std::swap(P->omf, P->omf2); std::swap(P->psf, P->psf2);
+  std::swap(P->pid, P->pid2);
+  std::swap(P->elem, P->keys[P->sorted_key_slot]);
+  P->sorted_pid = nullptr;
   return PDF_OK;
 }
 
@@ -620,6 +681,11 @@ pdf_status estimate_stats(pdf_particles* P, cudaStream_t st) {
   const MeshDev& M = P->mesh->d;
   pdf_status s = group_by_element(P, st);
   if (s != PDF_OK) return s;
+  if (P->reorder_every > 0 && ++P->since_reorder >= P->reorder_every) {
+    s = reorder_state(P, st);
+    if (s != PDF_OK) return s;
+    P->since_reorder = 0;
+  }
   if (P->precision == PDF_FP64)
     PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<fx::df><<<blocks_for((int64_t)M.n_tri * 32, kStatWarps * 32), kStatWarps * 32, 0, st>>>(
         P->seg, P->sorted_pid, M.n_tri, P->u, P->v, P->w, P->om, P->ps, P->es));

@@ -204,6 +204,7 @@ struct StepArgs {
   int64_t *x, *y;                  // fixed point, kPosF fraction bits
   fx::df *u, *v, *w, *om, *ps;     // double-float (PDF_FP64 storage)
   int32_t* elem;
+  const int32_t* pid;              // particle id of each slot (the Philox counter)
   const double* rows;
   const ElemGeo* geo;
   const int32_t* tri;
@@ -364,10 +365,11 @@ struct Draws {
   float g[8];
 };
 
-__device__ __forceinline__ Draws draw_step(const StepArgs& A, int64_t p) {
+__device__ __forceinline__ Draws draw_step(const StepArgs& A, int64_t slot) {
   Draws d;
-  gauss4(A.seed, (uint32_t)p, A.step, 0u, kPurposeStep, &d.g[0]);
-  uint32_t c[4] = {(uint32_t)p, A.step, 1u, kPurposeStep};
+  const uint32_t id = (uint32_t)__ldg(A.pid + slot);
+  gauss4(A.seed, id, A.step, 0u, kPurposeStep, &d.g[0]);
+  uint32_t c[4] = {id, A.step, 1u, kPurposeStep};
   philox4x32_10(c, (uint32_t)A.seed, (uint32_t)(A.seed >> 32));
   box_muller(c[0], c[1], &d.g[4], &d.g[5]);  // g6, g7 are not used by the step
   d.g[6] = d.g[7] = 0.0f;
@@ -889,6 +891,7 @@ extern "C" pdf_status pdf_step(pdf_particles* p, const pdf_mesh* m, const pdf_mo
   A.n = p->n;
   A.x = p->x; A.y = p->y; A.u = p->u; A.v = p->v; A.w = p->w; A.om = p->om; A.ps = p->ps;
   A.elem = p->elem;
+  A.pid = p->pid;
   A.rows = p->rows;
   A.geo = M.geo; A.tri = M.tri; A.xy = M.xy; A.esup_off = M.esup_off; A.esup = M.esup;
   A.n_tri = M.n_tri;

@@ -155,12 +155,14 @@ def test_frozen_step_parity(arith):
         assert info["crossings_periodic"] == cnt["crossings_periodic"]
 
 
-def _run_config(name, steps, check_every=None, arith="fx"):
+def _run_config(name, steps, check_every=None, arith="fx", reorder=None):
     cfg = inputs.workload(name)
     m = inputs.channel_mesh(cfg["nx"], cfg["ny"], jitter=cfg["jitter"], seed=cfg["seed"])
     counts = np.full(cfg["n_tri"], cfg["ppe"], dtype=np.int32)
     psi = inputs.scalar_slab(m, cfg["psi_slab_x"])
     gm, M, gp, ost = _pair(m, counts, seed=cfg["seed"], psi=psi, u_sigma=cfg["u_sigma"])
+    if reorder is not None:
+        gp.set_reorder(reorder)
     p = pg.model_params(dt=cfg["dt"], nu=cfg["nu"], Pi=cfg["Pi"], closure=cfg["closure"], arith=arith)
     po = _oracle_params(p)
     pg.pdf_estimate_stats(gp, gm)
@@ -187,6 +189,49 @@ def test_small_channel_free_run_100_steps(arith):
     statistics and element ids stay within the tolerance, for both the
     FP64-free default arithmetic and native FP64."""
     gm, M, gp, ost, ons, near = _run_config("channel_20x40_ppe50", 100, check_every=25, arith=arith)
+    assert max(near) < 1e-4
+    _check_stats(gp, gm, M, ost, ons)
+
+
+def test_reordering_is_invisible_at_the_interface():
+    """The state copied into element order at every statistics call (the
+    densest reordering) against no reordering.  With frozen coefficients the
+    steps do not depend on the statistics, so both runs hold bit-identical
+    states (ids and random-number counters move with the particles), counts
+    and means; the moments agree to rounding.  A 30-step free run with
+    every-call reordering still matches the oracle particle by particle."""
+    m = inputs.channel_mesh(20, 40, seed=1)
+    counts = np.random.default_rng(2).integers(0, 60, 2 * 19 * 39).astype(np.int32)
+    rng = np.random.default_rng(7)
+    n_tri = 2 * 19 * 39
+    rows = np.zeros((n_tri, 26))
+    rows[:, 0] = 1.0
+    rows[:, 3:9] = rng.normal(size=(n_tri, 6)) * 0.1
+    rows[:, 12:21] = np.tile(np.array([-5.0, 0, 0, 0, -5.0, 0, 0, 0, -5.0]), (n_tri, 1))
+    rows[:, 21] = 0.3
+    rows[:, 22] = 1.0
+    rows[:, 24] = 0.5
+    rows[:, 25] = 2.0
+    d_rows = torch.from_numpy(rows).cuda()
+    p = pg.model_params(closure="frozen", dt=5e-3, nu=1e-3)
+    out = []
+    for every in (0, 1):
+        gm, M, gp, ost = _pair(m, counts, psi=inputs.scalar_slab(m))
+        gp.set_reorder(every)
+        pg.pdf_estimate_stats(gp, gm)
+        for s in range(6):
+            pg.pdf_step(gp, gm, p, elem_coeff=d_rows, step=s)
+            pg.pdf_estimate_stats(gp, gm)
+        es = torch.empty((gm.n_tri, 13), dtype=torch.float64, device="cuda")
+        pg.pdf_estimate_stats(gp, gm, es)
+        out.append((es.cpu().numpy(), _host(gp.get_state())))
+    (es0, st0), (es1, st1) = out
+    for k in KEYS + ("elem",):
+        assert np.array_equal(st0[k], st1[k]), k
+    assert (st0["elem"] != np.repeat(np.arange(n_tri), counts)).any()  # particles changed elements
+    assert np.array_equal(es0[:, :6], es1[:, :6])
+    assert_field_close(es1[:, 6:], es0[:, 6:], "moments, reordered")
+    gm, M, gp, ost, ons, near = _run_config("channel_20x40_ppe50", 30, check_every=10, reorder=1)
     assert max(near) < 1e-4
     _check_stats(gp, gm, M, ost, ons)
 
