@@ -94,7 +94,7 @@ class ClockSampler:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -139,50 +139,55 @@ def _setup_dist(n_gpus):
     return rank, world, local, dist
 
 
-def cpu_baseline_measure(steps=1):
+def cpu_baseline_measure(steps=1, warmup=0, ppe=None):
     """The oracle as it stands, single-threaded on a host core, on a bounded
-    sample of the workload: the full 15.9M-particle channel, `steps` steps
-    (coefficients + particle step + statistics), init untimed."""
+    sample of the workload: the benchmark mesh with `ppe` particles per
+    element (default: the workload's 100), initialised once (untimed), then
+    `warmup` untimed and `steps` timed steps (coefficients + particle step +
+    statistics); value = the median per-step throughput."""
     import oracle
     cfg = inputs.workload(WORKLOAD)
+    ppe = ppe or cfg["ppe"]
     m = inputs.channel_mesh(cfg["nx"], cfg["ny"], jitter=cfg["jitter"], seed=cfg["seed"])
     M = oracle.Mesh(m)
-    counts = np.full(cfg["n_tri"], cfg["ppe"], dtype=np.int32)
+    counts = np.full(cfg["n_tri"], ppe, dtype=np.int32)
     st = oracle.init(M, counts, cfg["seed"], u_sigma=cfg["u_sigma"],
                      elem_psi0=inputs.scalar_slab(m, cfg["psi_slab_x"]))
     P = oracle.make_params(dt=cfg["dt"], nu=cfg["nu"], Pi=cfg["Pi"], closure=cfg["closure"])
     es, ns, nd, _ = oracle.statistics(M, st)
-    t0 = time.perf_counter()
-    for s in range(steps):
+    n = int(counts.sum())
+    rates, total = [], 0.0
+    for s in range(warmup + steps):
+        t0 = time.perf_counter()
         rows = oracle.elem_coeff(M, ns, nd, P)
         oracle.step(M, rows, P, cfg["seed"], s, st)
         es, ns, nd, _ = oracle.statistics(M, st, ns)
-    dt = time.perf_counter() - t0
-    n = cfg["n_particles"]
-    return {"value": n * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d step(s) of the full %d-particle workload (init untimed), %.1f s" % (steps, n, dt)}
+        dt = time.perf_counter() - t0
+        if s >= warmup:
+            rates.append(n / dt)
+            total += dt
+    return {"value": statistics.median(rates), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d timed step(s) of the %d-triangle channel with %d particles per element (%d particles; "
+                      "the workload has %d), %.1f s of stepping" % (steps, cfg["n_tri"], ppe, n, cfg["ppe"], total)}
 
 
 def run_reference(args):
     rank, world, local, dist = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0, None
     if rank != 0:
         return 0
-    times = []
-    base = None
-    for _ in range(args.warmup):
-        cpu_baseline_measure(1)
-    for _ in range(args.steps):
-        base = cpu_baseline_measure(1)
-        times.append(base["value"])
-    value = statistics.median(times) if times else 0.0
     cfg = inputs.workload(WORKLOAD)
+    # bound the whole run to ~2 minutes of oracle work at ~5.6e6 particle-steps/s
+    per_step = 6.5e8 / max(1, args.steps + args.warmup)
+    ppe = int(max(5, min(cfg["ppe"], per_step // cfg["n_tri"])))
+    base = cpu_baseline_measure(args.steps, args.warmup, ppe=ppe)
+    value = base["value"]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * cfg["n_particles"] / value if value else None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "n_particles": cfg["n_particles"],
                                             "n_tri": cfg["n_tri"], "closure": cfg["closure"]},
-            "cpu_baseline": dict(base, value=value) if base else None,
+            "cpu_baseline": base,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -321,9 +326,11 @@ def run_gpu(args):
     step_frac = STEP_BYTES_PER_PARTICLE * (n * args.steps / (ms * 1e-3)) / (peak * 1e9)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "i64+f32x2", "data": "synthetic",
             "config": {"workload": args.workload, "n_particles": n, "n_tri": gm.n_tri, "n_nodes": gm.n_nodes,
                        "closure": cfg["closure"], "dt": cfg["dt"],
+                       "arith": "FP64-accurate without FP64 instructions: positions 64-bit fixed point, "
+                                "u, v, w, omega, psi double-float (FP32 pairs)",
                        "l2": "inputs larger than L2: particle state %.2f GB vs 129 MB L2" % (n * 64 / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "hbm_frac_step": step_frac, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
@@ -375,7 +382,7 @@ def run_gpu(args):
         del gq
     if not args.no_cpu_baseline and world == 1:
         try:
-            line["cpu_baseline"] = cpu_baseline_measure(1)
+            line["cpu_baseline"] = cpu_baseline_measure(3)
         except Exception as exc:  # report, do not hide
             line["cpu_baseline"] = {"error": repr(exc)}
     print(json.dumps(line))
@@ -451,8 +458,8 @@ def run_warmstart(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--solves", type=int, default=10000, help="warmstart: training solves of the small channel")
     ap.add_argument("--train-steps", type=int, default=4000, help="warmstart: Adam steps")
