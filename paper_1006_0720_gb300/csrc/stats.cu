@@ -313,6 +313,8 @@ constexpr int kStatCache = 128;
 struct StatScratch {
   unsigned long long lo[5][33];
   long long hi[5][33];
+  unsigned long long lo2[5][6];  // second level of the pass-1 sums
+  long long hi2[5][6];
   union {
     long long q[4][kStatCache];
     struct {
@@ -374,15 +376,30 @@ __global__ void __launch_bounds__(kStatWarps * 32, 8) k_elem_stats_fx(const int3
       SS.hi[q][lane] = hi[q];
     }
     __syncwarp();
-    // lane q < 5 adds quantity q over the lanes (exact) and forms its mean
+    // exact sums over the lanes in two levels: lane 6q + r (r < 6) adds
+    // columns r, r + 6, ... of quantity q, then lane q adds its six results
     const fx::df invN = fx::recip_df(N);
     fx::df mean = fx::df{0.f, 0.f};
+    if (lane < 30) {
+      const int q = lane / 6, r = lane - 6 * (lane / 6);
+      unsigned long long sl = 0;
+      long long sh = 0;
+      for (int j = r; j < 32; j += 6) {
+        const unsigned long long nl = sl + SS.lo[q][j];
+        sh = sh + SS.hi[q][j] + (nl < sl ? 1 : 0);
+        sl = nl;
+      }
+      SS.lo2[q][r] = sl;
+      SS.hi2[q][r] = sh;
+    }
+    __syncwarp();
     if (lane < 5) {
       unsigned long long sl = 0;
       long long sh = 0;
-      for (int j = 0; j < 32; ++j) {
-        const unsigned long long nl = sl + SS.lo[lane][j];
-        sh = sh + SS.hi[lane][j] + (nl < sl ? 1 : 0);
+#pragma unroll
+      for (int r = 0; r < 6; ++r) {
+        const unsigned long long nl = sl + SS.lo2[lane][r];
+        sh = sh + SS.hi2[lane][r] + (nl < sl ? 1 : 0);
         sl = nl;
       }
       mean = fx::df_norm(fx::mul(fx::i128_to_df(sl, sh, -kFQ), invN));
@@ -443,14 +460,25 @@ __global__ void __launch_bounds__(kStatWarps * 32, 8) k_elem_stats_fx(const int3
       SS.f.l[7 + k][lane] = d[k].l;
     }
     __syncwarp();
-    // lane q < 11 adds quantity q over the lanes, in lane order
-    fx::df tot = fx::df{0.f, 0.f};
-    if (lane < 11) {
+    // lanes 2q and 2q + 1 add the first and second 16 lanes' partials of
+    // quantity q in lane order; lane 2q adds the two halves; lane q gets it
+    fx::df half = fx::df{0.f, 0.f};
+    if (lane < 22) {
+      const int q = lane >> 1, j0 = (lane & 1) * 16;
       fx::acc a;
-      a.init(fx::df{SS.f.h[lane][0], SS.f.l[lane][0]});
-      for (int j = 1; j < 32; ++j) a.add(fx::df{SS.f.h[lane][j], SS.f.l[lane][j]});
-      tot = a.value();
+      a.init(fx::df{SS.f.h[q][j0], SS.f.l[q][j0]});
+#pragma unroll 5
+      for (int j = j0 + 1; j < j0 + 16; ++j) a.add(fx::df{SS.f.h[q][j], SS.f.l[q][j]});
+      half = fx::df{a.h, a.l};
     }
+    const float oh = __shfl_down_sync(0xffffffffu, half.h, 1), ol = __shfl_down_sync(0xffffffffu, half.l, 1);
+    fx::acc a2;
+    a2.init(half);
+    a2.add(fx::df{oh, ol});
+    const fx::df pair = a2.value();
+    const float th = __shfl_sync(0xffffffffu, pair.h, (2 * lane) & 31);
+    const float tl = __shfl_sync(0xffffffffu, pair.l, (2 * lane) & 31);
+    const fx::df tot = lane < 11 ? fx::df{th, tl} : fx::df{0.f, 0.f};
     // output lane: 0 -> N, 1..5 -> means, 6..12 -> central moments
     // (sum D_a D_b - sum D_a sum D_b / N) / N
     const int q = lane - 6;
@@ -493,9 +521,9 @@ __global__ void k_node_stats(const int32_t* __restrict__ nse_off, const int32_t*
       atomicAdd(reinterpret_cast<unsigned long long*>(kept), 1ULL);
       continue;
     }
-    const double inv = (double)c;
+    const double inv = 1.0 / (double)c;
 #pragma unroll
-    for (int q = 0; q < PDF_NNS; ++q) ns[(int64_t)n * PDF_NNS + q] = acc[q] / inv;
+    for (int q = 0; q < PDF_NNS; ++q) ns[(int64_t)n * PDF_NNS + q] = acc[q] * inv;
   }
 }
 
@@ -533,10 +561,10 @@ __global__ void k_node_grad1(const int32_t* __restrict__ nse_off, const int32_t*
       acc[6] += g[7];
     }
     double* D = nd + (int64_t)n * PDF_NND;
-    const double inv = c > 0 ? (double)c : 1.0;
+    const double inv = 1.0 / (c > 0 ? (double)c : 1.0);
 #pragma unroll
-    for (int q = 0; q < 6; ++q) D[q] = acc[q] / inv;
-    D[9] = acc[6] / inv;
+    for (int q = 0; q < 6; ++q) D[q] = acc[q] * inv;
+    D[9] = acc[6] * inv;
   }
 }
 
@@ -566,9 +594,9 @@ __global__ void k_node_grad2(const int32_t* __restrict__ nse_off, const int32_t*
       const double* g = eg + (int64_t)nse[i] * 8;
       acc[0] += g[0]; acc[1] += g[1]; acc[2] += g[2];
     }
-    const double inv = c > 0 ? (double)c : 1.0;
+    const double inv = 1.0 / (c > 0 ? (double)c : 1.0);
     double* D = nd + (int64_t)n * PDF_NND;
-    D[6] = acc[0] / inv; D[7] = acc[1] / inv; D[8] = acc[2] / inv;
+    D[6] = acc[0] * inv; D[7] = acc[1] * inv; D[8] = acc[2] * inv;
   }
 }
 

@@ -17,6 +17,7 @@ struct CoeffParams {
   int closure, tm_mode, pressure, arith;
   double src_x, src_y, src_r, Cs, Ct;
   double C1, C2, C3, C4, CT, Cv, gamma5, Comega1, Comega2, C0_slm;
+  double sdt, s2nu, s2c3c4dt;  // sqrt(dt), sqrt(2 nu), sqrt(2 C3 C4 dt): once per call, not per element
 };
 
 static CoeffParams coeff_params(const pdf_model_params* p) {
@@ -26,6 +27,9 @@ static CoeffParams coeff_params(const pdf_model_params* p) {
   c.C1 = p->C1; c.C2 = p->C2; c.C3 = p->C3; c.C4 = p->C4; c.CT = p->CT; c.Cv = p->Cv;
   c.gamma5 = p->gamma5; c.Comega1 = p->Comega1; c.Comega2 = p->Comega2; c.C0_slm = p->C0_slm;
   c.src_x = p->src_x; c.src_y = p->src_y; c.src_r = p->src_r; c.Cs = p->Cs; c.Ct = p->Ct;
+  c.sdt = std::sqrt(p->dt);
+  c.s2nu = std::sqrt(2.0 * p->nu);
+  c.s2c3c4dt = std::sqrt(2.0 * p->C3 * p->C4 * p->dt);
   return c;
 }
 
@@ -47,8 +51,9 @@ __device__ void relax_rhs(const double* S, const double* D, const CoeffParams& P
   const double tk = 2.0 * k / 3.0;
   const double Av = fmin(1.0, P.Cv * det / (tk * tk * tk));
   double b[3][3];
+  const double inv_2k = 0.5 / k;
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) b[i][j] = R[i][j] / (2.0 * k) - (i == j ? 1.0 / 3.0 : 0.0);
+    for (int j = 0; j < 3; ++j) b[i][j] = R[i][j] * inv_2k - (i == j ? 1.0 / 3.0 : 0.0);
   const double g3 = P.gamma5 / 3.0;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
@@ -101,7 +106,8 @@ __global__ void k_node_coeff(int32_t n_nodes, const double* __restrict__ ns, con
       const double R9[9] = {S[5], S[8], S[9], S[8], S[6], S[10], S[9], S[10], S[7]};
       double wr = 0.0;
       for (int q = 0; q < 9; ++q) wr += w9[q] * R9[q];
-      for (int q = 0; q < 9; ++q) c[12 + q] = (w9[q] - ((q % 4 == 0) ? 0.5 * eg : 0.0)) / kg;
+      const double inv_kg = 1.0 / kg;
+      for (int q = 0; q < 9; ++q) c[12 + q] = (w9[q] - ((q % 4 == 0) ? 0.5 * eg : 0.0)) * inv_kg;
       const double C0 = fmax(-2.0 * wr / (3.0 * kg * eg), 0.0);
       c[21] = sqrt(C0 * eg);
     }
@@ -128,8 +134,8 @@ __global__ void k_node_coeff(int32_t n_nodes, const double* __restrict__ ns, con
 // Internal row (32 doubles) from the 26 element-average coefficients: the
 // time-step factors of the Euler-Maruyama updates folded in once per element.
 __device__ __forceinline__ void scale_row(const double a[PDF_NCOEF], const CoeffParams& P, double* r) {
-  const double dt = P.dt, sdt = sqrt(P.dt);
-  const double sgrad = (P.closure == PDF_CLOSURE_SLM) ? 0.0 : sqrt(2.0 * P.nu) * sdt;
+  const double dt = P.dt, sdt = P.sdt;
+  const double sgrad = (P.closure == PDF_CLOSURE_SLM) ? 0.0 : P.s2nu * sdt;
   for (int i = 0; i < 3; ++i) r[i] = a[i];
   for (int q = 0; q < 6; ++q) r[3 + q] = sgrad * a[3 + q];
   for (int i = 0; i < 3; ++i) r[9 + i] = a[9 + i] * dt;
@@ -139,7 +145,7 @@ __device__ __forceinline__ void scale_row(const double a[PDF_NCOEF], const Coeff
   r[22] = mo;
   r[23] = (P.C3 + a[23]) * mo * dt;
   r[24] = P.C3 * mo * mo * dt;
-  r[25] = mo * sqrt(2.0 * P.C3 * P.C4 * dt);
+  r[25] = mo * P.s2c3c4dt;
   r[26] = a[24];
   r[27] = dt * a[25];
   r[28] = r[29] = r[30] = r[31] = 0.0;
@@ -167,7 +173,7 @@ __global__ void k_elem_rows(const int32_t* __restrict__ tri, int32_t n_tri, cons
     const double* c1 = nc + (int64_t)tri[3 * e + 1] * PDF_NCOEF;
     const double* c2 = nc + (int64_t)tri[3 * e + 2] * PDF_NCOEF;
     double a[PDF_NCOEF];
-    for (int q = 0; q < PDF_NCOEF; ++q) a[q] = (c0[q] + c1[q] + c2[q]) / 3.0;
+    for (int q = 0; q < PDF_NCOEF; ++q) a[q] = (c0[q] + c1[q] + c2[q]) * (1.0 / 3.0);
     if (avg_out)
       for (int q = 0; q < PDF_NCOEF; ++q) avg_out[(int64_t)e * PDF_NCOEF + q] = a[q];
     if (rows || rows_fx || rows_f32) {
@@ -506,15 +512,6 @@ __device__ __forceinline__ fx::df dsub(fx::df a, fx::df b) {
   return fx::df{t.h, t.l};
 }
 
-__device__ __forceinline__ FxGeo load_fx_geo(const FxGeo* geo, int32_t e) {
-  FxGeo g;
-  const int4* src = reinterpret_cast<const int4*>(geo + e);
-  int4* dst = reinterpret_cast<int4*>(&g);
-#pragma unroll
-  for (int i = 0; i < 5; ++i) dst[i] = __ldg(src + i);
-  return g;
-}
-
 // Twice the sub-areas in double-float (normalized), from fixed-point offsets.
 __device__ __forceinline__ void sub_areas_fx(const FxGeo& g, int64_t X, int64_t Y, fx::df& na, fx::df& nb,
                                              fx::df& nc) {
@@ -534,54 +531,132 @@ __device__ __forceinline__ void sub_areas_fx(const FxGeo& g, int64_t X, int64_t 
   nb = b.value();
 }
 
-// FP32 screen of the element test: true only if all three sub-areas are
-// certainly positive.  Each FP32 value carries at most a few relative errors
-// of 2^-24 from the rounded offsets, the high parts of the coefficients and
-// the operations; the margin 2^-18 of the magnitudes involved covers them
-// with room to spare, so a "true" is never wrong and undecided particles go
-// to the double-float test.  A particle passing the screen is farther than
-// ~4e-6 A_e from every edge, far outside the 1e-12 near-face band.
-__device__ __forceinline__ bool inside_certain(const FxGeo& g, int64_t X, int64_t Y) {
-  const fx::df dxd = fx::fix2df(X - g.xb, kF), dyd = fx::fix2df(Y - g.yb, kF);
+// The three sub-areas in FP32 with error bounds: |n - n_exact| < b for each,
+// with a margin of 8 over the accumulated rounding (relative errors of
+// 2^-24 from the rounded offsets, 2^-23 from the truncated high parts of the
+// coefficients, 2^-24 per operation).  "Certain" decisions below are never
+// wrong; the undecided go to the double-float test.
+struct Screen {
+  float na, nb, nc, ba, bb, bc;
+};
+
+__device__ __forceinline__ Screen screen_xy(int64_t xb, int64_t yb, float cbx, float cby, float abx, float aby,
+                                            float two_area, int64_t X, int64_t Y) {
+  const fx::df dxd = fx::fix2df(X - xb, kF), dyd = fx::fix2df(Y - yb, kF);
   const float dx = dxd.h + dxd.l, dy = dyd.h + dyd.l;
-  const float p1 = g.cbx.h * dy, p2 = g.cby.h * dx;
-  const float q1 = dx * g.aby.h, q2 = dy * g.abx.h;
-  const float na = p1 - p2, nc = q1 - q2;
-  const float ba = (fabsf(p1) + fabsf(p2)) * 0x1p-18f;
-  const float bc = (fabsf(q1) + fabsf(q2)) * 0x1p-18f;
-  const float nb = g.two_area.h - na - nc;
-  const float bb = (fabsf(g.two_area.h) + fabsf(na) + fabsf(nc)) * 0x1p-18f + ba + bc;
-  return na > ba && nc > bc && nb > bb;
+  const float p1 = cbx * dy, p2 = cby * dx;
+  const float q1 = dx * aby, q2 = dy * abx;
+  Screen S;
+  S.na = p1 - p2;
+  S.nc = q1 - q2;
+  S.ba = (fabsf(p1) + fabsf(p2)) * 0x1p-18f;
+  S.bc = (fabsf(q1) + fabsf(q2)) * 0x1p-18f;
+  S.nb = two_area - S.na - S.nc;
+  S.bb = (fabsf(two_area) + fabsf(S.na) + fabsf(S.nc)) * 0x1p-18f + S.ba + S.bc;
+  return S;
 }
 
-// Fixed-point neighbour walk; returns true when the FP64 walk must finish it
-// (a wall or open-boundary edge, or the 64-step cap).
+// All three sub-areas certainly positive: the particle is inside, farther
+// than ~4e-6 A_e from every edge (far outside the 1e-12 near-face band).
+__device__ __forceinline__ bool certain_inside(const Screen& S) {
+  return S.na > S.ba && S.nc > S.bc && S.nb > S.bb;
+}
+
+// The edge the walk leaves through when FP32 decides it: the smallest
+// sub-area is certainly negative and certainly below the other two, so the
+// exact choice (smallest, ties to the lowest local vertex) is the same.
+// -1 when undecided.
+__device__ __forceinline__ int certain_exit(const Screen& S) {
+  int k = 0;
+  float mn = S.na, mb = S.ba;
+  if (S.nb < mn) { k = 1; mn = S.nb; mb = S.bb; }
+  if (S.nc < mn) { k = 2; mn = S.nc; mb = S.bc; }
+  const float hi = mn + mb;
+  if (!(hi < 0.0f)) return -1;
+  if (k != 0 && !(S.na - S.ba > hi)) return -1;
+  if (k != 1 && !(S.nb - S.bb > hi)) return -1;
+  if (k != 2 && !(S.nc - S.bc > hi)) return -1;
+  return k;
+}
+
+// One element of the fixed-point neighbour walk:
+// kWalkInside (e holds the point), kWalkSlow (a wall or open-boundary edge,
+// or the 64-step cap: the FP64 walk finishes it) or kWalkMoved (e, Xn now
+// the neighbour across the edge opposite the smallest sub-area).
+enum { kWalkInside = 0, kWalkMoved = 1, kWalkSlow = 2 };
+
+// Crossing edge k of the element whose last 32 bytes are d (2A_e, nbr0,
+// nbr1) and f (nbr2, shifts and outflow bits); selects rather than an
+// indexed array, so that nothing goes to local memory.
+__device__ __forceinline__ int cross_edge(const FxArgs& F, int k, int4 d, int2 f, int32_t& e, int64_t& Xn,
+                                          int& steps, int& c_per, bool& reinj) {
+  const int32_t nbr = k == 0 ? d.z : (k == 1 ? d.w : f.x);
+  if (nbr < 0) return kWalkSlow;
+  const int sh = (int)(int8_t)((f.y >> (8 * k)) & 0xff);
+  ++steps;
+  if (sh != 0) {
+    Xn += (int64_t)sh * F.period_fix;
+    ++c_per;
+  }
+  if ((f.y >> (24 + k)) & 1) reinj = true;
+  e = nbr;
+  return kWalkMoved;
+}
+
+// The undecided case: double-float sub-areas (rare; kept out of line so that
+// the common path holds few registers).
+__device__ __noinline__ int walk_one_df(const FxArgs& F, int32_t& e, int64_t& Xn, int64_t Yn, int& steps,
+                                        int& c_per, int& c_near, bool& reinj) {
+  const int4* src = reinterpret_cast<const int4*>(F.geo + e);
+  const int4 a = __ldg(src), b = __ldg(src + 1), c = __ldg(src + 2), d = __ldg(src + 3);
+  const int2 f = __ldg(reinterpret_cast<const int2*>(src + 4));
+  FxGeo G;
+  G.xb = ((int64_t)(uint32_t)a.y << 32) | (uint32_t)a.x;
+  G.yb = ((int64_t)(uint32_t)a.w << 32) | (uint32_t)a.z;
+  G.cbx = fx::df{__int_as_float(b.x), __int_as_float(b.y)};
+  G.cby = fx::df{__int_as_float(b.z), __int_as_float(b.w)};
+  G.abx = fx::df{__int_as_float(c.x), __int_as_float(c.y)};
+  G.aby = fx::df{__int_as_float(c.z), __int_as_float(c.w)};
+  G.two_area = fx::df{__int_as_float(d.x), __int_as_float(d.y)};
+  fx::df na, nb, nc;
+  sub_areas_fx(G, Xn, Yn, na, nb, nc);
+  if (fx::ge0(na) && fx::ge0(nb) && fx::ge0(nc)) {
+    const float mn = fminf(na.h, fminf(nb.h, nc.h));
+    if (mn < 1e-12f * G.two_area.h) ++c_near;
+    return kWalkInside;
+  }
+  if (steps >= 64) return kWalkSlow;
+  int k = 0;
+  fx::df mn = na;
+  if (fx::lt(nb, mn)) { k = 1; mn = nb; }
+  if (fx::lt(nc, mn)) { k = 2; }
+  return cross_edge(F, k, d, f, e, Xn, steps, c_per, reinj);
+}
+
+__device__ __forceinline__ int walk_one(const FxArgs& F, int32_t& e, int64_t& Xn, int64_t Yn, int& steps,
+                                        int& c_per, int& c_near, bool& reinj) {
+  const int4* src = reinterpret_cast<const int4*>(F.geo + e);
+  const int4 a = __ldg(src), b = __ldg(src + 1), c = __ldg(src + 2);
+  const float two_area = __int_as_float(__ldg(reinterpret_cast<const int*>(src + 3)));
+  const Screen S = screen_xy(((int64_t)(uint32_t)a.y << 32) | (uint32_t)a.x,
+                             ((int64_t)(uint32_t)a.w << 32) | (uint32_t)a.z, __int_as_float(b.x),
+                             __int_as_float(b.z), __int_as_float(c.x), __int_as_float(c.z), two_area, Xn, Yn);
+  if (certain_inside(S)) return kWalkInside;
+  const int k = certain_exit(S);
+  if (k < 0) return walk_one_df(F, e, Xn, Yn, steps, c_per, c_near, reinj);
+  if (steps >= 64) return kWalkSlow;
+  const int4 d = __ldg(src + 3);
+  const int2 f = __ldg(reinterpret_cast<const int2*>(src + 4));
+  return cross_edge(F, k, d, f, e, Xn, steps, c_per, reinj);
+}
+
+// Fixed-point neighbour walk from element e; returns true when the FP64 walk
+// must finish it.
 __device__ __forceinline__ bool walk_fx(const FxArgs& F, int32_t& e, int64_t& Xn, int64_t Yn, int& steps, int& c_per,
                                         int& c_near, bool& reinj) {
   for (;;) {
-    const FxGeo G = load_fx_geo(F.geo, e);
-    if (inside_certain(G, Xn, Yn)) return false;
-    fx::df na, nb, nc;
-    sub_areas_fx(G, Xn, Yn, na, nb, nc);
-    if (fx::ge0(na) && fx::ge0(nb) && fx::ge0(nc)) {
-      const float mn = fminf(na.h, fminf(nb.h, nc.h));
-      if (mn < 1e-12f * G.two_area.h) ++c_near;
-      return false;
-    }
-    if (steps >= 64) return true;
-    int k = 0;
-    fx::df mn = na;
-    if (fx::lt(nb, mn)) { k = 1; mn = nb; }
-    if (fx::lt(nc, mn)) { k = 2; }
-    const int32_t nbr = G.nbr[k];
-    if (nbr < 0) return true;
-    ++steps;
-    if (G.shift[k] != 0) {
-      Xn += (int64_t)G.shift[k] * F.period_fix;
-      ++c_per;
-    }
-    if (G.reinj & (1u << k)) reinj = true;
-    e = nbr;
+    const int r = walk_one(F, e, Xn, Yn, steps, c_per, c_near, reinj);
+    if (r != kWalkMoved) return r == kWalkSlow;
   }
 }
 
@@ -732,7 +807,7 @@ struct F32Args {
   const float* rows;  // [n_tri][32], the layout of the FP64 rows
 };
 
-__global__ void __launch_bounds__(256) k_step_f32(StepArgs A, FxArgs F, F32Args S) {
+__global__ void __launch_bounds__(256, 4) k_step_f32(StepArgs A, FxArgs F, F32Args S) {
   int c_walk = 0, c_per = 0, c_om = 0, c_near = 0;
   Counts cs;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
