@@ -113,53 +113,65 @@ __global__ void __launch_bounds__(1024) k_scan_apply(int32_t* __restrict__ a, in
   }
 }
 
-// Stable scatter of one tile.  Items are ranked in index order: 16 rounds of
-// 256 items; inside a round, warps in order and lanes in order.
+// Stable scatter of one tile.  Warp w owns the tile's items
+// [512 w, 512 (w + 1)) and ranks them in 16 rounds of 32 in index order,
+// counting digits in its own row of shared counters (no block barrier
+// between rounds); one block-wide prefix over the warps then gives every
+// (warp, digit) its output offset, so items with equal digits keep their
+// index order.
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in, int64_t n, int shift,
     int64_t n_tiles, const int32_t* __restrict__ hist, int32_t* __restrict__ keys_out,
     int32_t* __restrict__ vals_out) {
   constexpr int kWarps = kSortThreads / 32;
-  __shared__ int32_t base[kBins];
-  __shared__ int32_t wcnt[kWarps][kBins];
+  constexpr int kPerWarp = kTile / kWarps;  // 512 items, 16 rounds
+  __shared__ int32_t wcnt[kWarps][kBins + 1];  // the extra bin takes the tile's padding
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int b = threadIdx.x; b < kBins; b += kSortThreads) base[b] = hist[(int64_t)b * n_tiles + blockIdx.x];
+  for (int i = threadIdx.x; i < kWarps * (kBins + 1); i += kSortThreads) (&wcnt[0][0])[i] = 0;
+  __syncthreads();
   const uint32_t lt_mask = (1u << lane) - 1u;
-  const int64_t tile0 = (int64_t)blockIdx.x * kTile;
+  const int64_t w0 = (int64_t)blockIdx.x * kTile + (int64_t)wid * kPerWarp;
+  int32_t key[kItemsPerThread], val[kItemsPerThread], off[kItemsPerThread];
+#pragma unroll
   for (int r = 0; r < kItemsPerThread; ++r) {
-    for (int i = threadIdx.x; i < kWarps * kBins; i += kSortThreads) (&wcnt[0][0])[i] = 0;
-    __syncthreads();
-    const int64_t i = tile0 + r * kSortThreads + threadIdx.x;
+    const int64_t i = w0 + r * 32 + lane;
     const bool valid = i < n;
-    int32_t key = 0, val = 0;
-    int d = kBins;  // invalid items share a digit that is never written
-    if (valid) {
-      key = keys_in[i];
-      val = vals_in ? vals_in[i] : (int32_t)i;
-      d = (key >> shift) & (kBins - 1);
-    }
+    key[r] = valid ? keys_in[i] : 0;
+    val[r] = valid ? (vals_in ? vals_in[i] : (int32_t)i) : 0;
+  }
+#pragma unroll
+  for (int r = 0; r < kItemsPerThread; ++r) {
+    const int64_t i = w0 + r * 32 + lane;
+    const int d = (i < n) ? ((key[r] >> shift) & (kBins - 1)) : kBins;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const int rank = __popc(peers & lt_mask);
-    if (valid && rank == 0) wcnt[wid][d] = __popc(peers);
-    __syncthreads();
-    // per-bin prefix over warps; base[] advances by the round's count
-    for (int b = threadIdx.x; b < kBins; b += kSortThreads) {
-      int32_t acc = base[b];
+    const int32_t before = wcnt[wid][d];
+    __syncwarp();
+    if (rank == 0) wcnt[wid][d] = before + __popc(peers);
+    __syncwarp();
+    off[r] = before + rank;
+  }
+  __syncthreads();
+  // (warp, digit) offsets: the tile's base of the digit plus the earlier warps' counts
+  for (int b = threadIdx.x; b < kBins; b += kSortThreads) {
+    int32_t acc = hist[(int64_t)b * n_tiles + blockIdx.x];
 #pragma unroll
-      for (int k = 0; k < kWarps; ++k) {
-        const int32_t c = wcnt[k][b];
-        wcnt[k][b] = acc;
-        acc += c;
-      }
-      base[b] = acc;
+    for (int k = 0; k < kWarps; ++k) {
+      const int32_t c = wcnt[k][b];
+      wcnt[k][b] = acc;
+      acc += c;
     }
-    __syncthreads();
-    if (valid) {
-      const int32_t pos = wcnt[wid][d] + rank;
-      keys_out[pos] = key;
-      vals_out[pos] = val;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kItemsPerThread; ++r) {
+    const int64_t i = w0 + r * 32 + lane;
+    if (i < n) {
+      const int d = (key[r] >> shift) & (kBins - 1);
+      const int32_t pos = wcnt[wid][d] + off[r];
+      keys_out[pos] = key[r];
+      vals_out[pos] = val[r];
     }
-    __syncthreads();
   }
 }
 
