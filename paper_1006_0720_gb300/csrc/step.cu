@@ -386,7 +386,7 @@ __device__ __forceinline__ Draws draw_step(const StepArgs& A, int64_t slot) {
 // fall-back of the fixed-point kernel for large moves).  The stored forms are
 // widened to FP64 on load and rounded back on store; a particle that is lost,
 // or whose new position leaves |x|, |y| < 64, keeps its position and element.
-__device__ __noinline__ Counts advance_native(const StepArgs& A, int64_t p, const Draws D) {
+__device__ __forceinline__ Counts advance_native(const StepArgs& A, int64_t p, const Draws D) {
   Counts c;
   const float* g = D.g;
   const int32_t e = A.elem[p];
@@ -429,6 +429,13 @@ __device__ __noinline__ Counts advance_native(const StepArgs& A, int64_t p, cons
   A.u[p] = fx::from_double(un); A.v[p] = fx::from_double(vn); A.w[p] = fx::from_double(wn);
   A.om[p] = fx::from_double(on); A.ps[p] = fx::from_double(sf);
   return c;
+}
+
+// The same, out of line for the fixed-point kernels' rare fall-back.  All
+// arguments by value, so that no variable of the caller has its address
+// taken (which would keep it in local memory for its whole life).
+__device__ __noinline__ Counts advance_native_ool(const StepArgs A, int64_t p, const Draws D) {
+  return advance_native(A, p, D);
 }
 
 __device__ __forceinline__ void merge(Counts& a, const Counts& b) {
@@ -604,10 +611,17 @@ __device__ __forceinline__ int cross_edge(const FxArgs& F, int k, int4 d, int2 f
 }
 
 // The undecided case: double-float sub-areas (rare; kept out of line so that
-// the common path holds few registers).
-__device__ __noinline__ int walk_one_df(const FxArgs& F, int32_t& e, int64_t& Xn, int64_t Yn, int& steps,
-                                        int& c_per, int& c_near, bool& reinj) {
-  const int4* src = reinterpret_cast<const int4*>(F.geo + e);
+// the common path holds few registers; by value in and out).
+struct WalkStep {
+  int r;              // kWalkInside / kWalkMoved / kWalkSlow
+  int32_t e;          // the element after the step
+  int64_t Xn;         // x after a periodic shift
+  int near, per, reinj, crossed;
+};
+
+__device__ __noinline__ WalkStep walk_one_df(const FxGeo* geo, int64_t period_fix, int32_t e, int64_t Xn,
+                                             int64_t Yn, int steps) {
+  const int4* src = reinterpret_cast<const int4*>(geo + e);
   const int4 a = __ldg(src), b = __ldg(src + 1), c = __ldg(src + 2), d = __ldg(src + 3);
   const int2 f = __ldg(reinterpret_cast<const int2*>(src + 4));
   FxGeo G;
@@ -618,19 +632,32 @@ __device__ __noinline__ int walk_one_df(const FxArgs& F, int32_t& e, int64_t& Xn
   G.abx = fx::df{__int_as_float(c.x), __int_as_float(c.y)};
   G.aby = fx::df{__int_as_float(c.z), __int_as_float(c.w)};
   G.two_area = fx::df{__int_as_float(d.x), __int_as_float(d.y)};
+  WalkStep w{kWalkInside, e, Xn, 0, 0, 0, 0};
   fx::df na, nb, nc;
   sub_areas_fx(G, Xn, Yn, na, nb, nc);
   if (fx::ge0(na) && fx::ge0(nb) && fx::ge0(nc)) {
     const float mn = fminf(na.h, fminf(nb.h, nc.h));
-    if (mn < 1e-12f * G.two_area.h) ++c_near;
-    return kWalkInside;
+    if (mn < 1e-12f * G.two_area.h) w.near = 1;
+    return w;
   }
-  if (steps >= 64) return kWalkSlow;
+  w.r = kWalkSlow;
+  if (steps >= 64) return w;
   int k = 0;
   fx::df mn = na;
   if (fx::lt(nb, mn)) { k = 1; mn = nb; }
   if (fx::lt(nc, mn)) { k = 2; }
-  return cross_edge(F, k, d, f, e, Xn, steps, c_per, reinj);
+  const int32_t nbr = k == 0 ? d.z : (k == 1 ? d.w : f.x);
+  if (nbr < 0) return w;
+  const int sh = (int)(int8_t)((f.y >> (8 * k)) & 0xff);
+  w.r = kWalkMoved;
+  w.crossed = 1;
+  if (sh != 0) {
+    w.Xn = Xn + (int64_t)sh * period_fix;
+    w.per = 1;
+  }
+  w.reinj = (f.y >> (24 + k)) & 1;
+  w.e = nbr;
+  return w;
 }
 
 __device__ __forceinline__ int walk_one(const FxArgs& F, int32_t& e, int64_t& Xn, int64_t Yn, int& steps,
@@ -643,7 +670,16 @@ __device__ __forceinline__ int walk_one(const FxArgs& F, int32_t& e, int64_t& Xn
                              __int_as_float(b.z), __int_as_float(c.x), __int_as_float(c.z), two_area, Xn, Yn);
   if (certain_inside(S)) return kWalkInside;
   const int k = certain_exit(S);
-  if (k < 0) return walk_one_df(F, e, Xn, Yn, steps, c_per, c_near, reinj);
+  if (k < 0) {
+    const WalkStep w = walk_one_df(F.geo, F.period_fix, e, Xn, Yn, steps);
+    e = w.e;
+    Xn = w.Xn;
+    steps += w.crossed;
+    c_per += w.per;
+    c_near += w.near;
+    if (w.reinj) reinj = true;
+    return w.r;
+  }
   if (steps >= 64) return kWalkSlow;
   const int4 d = __ldg(src + 3);
   const int2 f = __ldg(reinterpret_cast<const int2*>(src + 4));
@@ -660,9 +696,24 @@ __device__ __forceinline__ bool walk_fx(const FxArgs& F, int32_t& e, int64_t& Xn
   }
 }
 
-__device__ __noinline__ int32_t walk_slow(const StepArgs& A, int32_t e, double& x, double& y, double& u,
-                                          double& v, Counts& c, bool& reinj) {
-  return walk(A, e, x, y, u, v, c.walk, c.refl, c.per, c.fb, c.brute, c.near, reinj);
+// The FP64 walk (walls, open boundaries, the step cap), out of line and by
+// value for the fixed-point kernels.
+struct SlowWalk {
+  int32_t e;  // host element, -1 if lost
+  double x, y, u, v;
+  Counts c;
+  bool reinj;
+};
+
+__device__ __noinline__ SlowWalk walk_slow(const StepArgs A, int32_t e, double x, double y, double u, double v) {
+  SlowWalk r;
+  r.reinj = false;
+  r.e = walk(A, e, x, y, u, v, r.c.walk, r.c.refl, r.c.per, r.c.fb, r.c.brute, r.c.near, r.reinj);
+  r.x = x;
+  r.y = y;
+  r.u = u;
+  r.v = v;
+  return r;
 }
 
 // Source test on the fixed-point position: d^2 - r^2 in double-float
@@ -711,7 +762,7 @@ __global__ void __launch_bounds__(256, 4) k_step_fx(StepArgs A, FxArgs F) {
     ay.init(fx::mul(U[1], F.dt));
     ay.add(fx::mul_f(F.sdiff, D.g[1]));
     if (!(small_move(ax) && small_move(ay))) {
-      merge(cs, advance_native(A, p, D));
+      merge(cs, advance_native_ool(A, p, D));
       continue;
     }
     int64_t Xn = A.x[p] + ax.fix(kF);
@@ -769,13 +820,15 @@ __global__ void __launch_bounds__(256, 4) k_step_fx(StepArgs A, FxArgs F) {
       double xn = __longlong_as_double((long long)fx::fix2d(Xn, kF));
       double yn = __longlong_as_double((long long)fx::fix2d(Yn, kF));
       double un = fx::to_double(Un[0]), vn = fx::to_double(Un[1]);
-      const int32_t en = walk_slow(A, e, xn, yn, un, vn, cs, reinj);
-      if (en >= 0 && pos_fits(xn) && pos_fits(yn)) {
-        e = en;
-        Xs = fx::d2fix((uint64_t)__double_as_longlong(xn), kF);
-        Ys = fx::d2fix((uint64_t)__double_as_longlong(yn), kF);
-        Un[0] = fx::from_double(un);
-        Un[1] = fx::from_double(vn);
+      const SlowWalk sw = walk_slow(A, e, xn, yn, un, vn);
+      merge(cs, sw.c);
+      if (sw.reinj) reinj = true;
+      if (sw.e >= 0 && pos_fits(sw.x) && pos_fits(sw.y)) {
+        e = sw.e;
+        Xs = fx::d2fix((uint64_t)__double_as_longlong(sw.x), kF);
+        Ys = fx::d2fix((uint64_t)__double_as_longlong(sw.y), kF);
+        Un[0] = fx::from_double(sw.u);
+        Un[1] = fx::from_double(sw.v);
       } else {  // lost: keeps its element and position
         ++cs.lost;
         e = A.elem[p];
@@ -860,13 +913,17 @@ __global__ void __launch_bounds__(256, 4) k_step_f32(StepArgs A, FxArgs F, F32Ar
     }
     if (slow) {
       double ud = (double)un, vd = (double)vn;
-      const int32_t en = walk_slow(A, e, xn, yn, ud, vd, cs, reinj);
-      if (en >= 0 && pos_fits(xn) && pos_fits(yn)) {
-        e = en;
+      const SlowWalk sw = walk_slow(A, e, xn, yn, ud, vd);
+      merge(cs, sw.c);
+      if (sw.reinj) reinj = true;
+      if (sw.e >= 0 && pos_fits(sw.x) && pos_fits(sw.y)) {
+        e = sw.e;
+        xn = sw.x;
+        yn = sw.y;
         Xn = fx::d2fix((uint64_t)__double_as_longlong(xn), kF);
         Yn = fx::d2fix((uint64_t)__double_as_longlong(yn), kF);
-        un = (float)ud;
-        vn = (float)vd;
+        un = (float)sw.u;
+        vn = (float)sw.v;
       } else {  // lost: keeps its element and position
         ++cs.lost;
         e = A.elem[p];
