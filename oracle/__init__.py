@@ -102,7 +102,8 @@ def lib():
             L.or_node_coeff.argtypes = [PD, PD, PD, ctypes.POINTER(_Params), PD, PD]
             L.or_elem_coeff.argtypes = [ctypes.c_void_p, PD, PD, PD, ctypes.POINTER(_Params), PD]
             L.or_step.argtypes = [ctypes.c_void_p, ctypes.c_long, PD, ctypes.POINTER(_Params),
-                                  ctypes.c_uint64, U32, PD, PD, PD, PD, PD, PD, PD, PI, PI, PL, PI]
+                                  ctypes.c_uint64, U32, PD, PD, PD, PD, PD, PD, PD, PI, PI, PL, PI, PD]
+            L.or_iecm_cond.argtypes = [I, ctypes.c_long, PI, PD, PD, PD, PD, PI, I, I, I, I, PD]
             _lib = L
     return _lib
 
@@ -281,17 +282,33 @@ def elem_coeff(mesh, ns, nd, params, wp=None):
     return rows
 
 
-def step(mesh, rows, params, seed, step_no, st, pid=None):
+def iecm_cond(n_tri, st, bins=(5, 5, 5), m_min=2, pid=None):
+    """Velocity-conditioned scalar mean of every particle (eq. IECM) by the
+    sort-and-divide binning over the particles of each element."""
+    el = np.ascontiguousarray(st["elem"], dtype=np.int32)
+    arrs = [np.ascontiguousarray(st[k], dtype=np.float64) for k in ("u", "v", "w", "ps")]
+    pid = None if pid is None else np.ascontiguousarray(pid, dtype=np.int32)
+    out = np.zeros(len(el))
+    lib().or_iecm_cond(n_tri, len(el), _p(el, I), *[_p(a, D) for a in arrs],
+                       None if pid is None else _p(pid, I), int(bins[0]), int(bins[1]), int(bins[2]),
+                       int(m_min), _p(out, D))
+    return out
+
+
+def step(mesh, rows, params, seed, step_no, st, pid=None, cond=None):
     """Advance every particle one step in place.  Returns (counters, status).
-    pid: particle ids of the entries (default: their index)."""
+    pid: particle ids of the entries (default: their index); cond: the
+    velocity-conditioned scalar means for eq. IECM (default: eq. IEM)."""
     n = len(st["x"])
     pid = None if pid is None else np.ascontiguousarray(pid, dtype=np.int32)
+    cond = None if cond is None else np.ascontiguousarray(cond, dtype=np.float64)
     rows = np.ascontiguousarray(rows, dtype=np.float64)
     status = np.zeros(n, dtype=np.int32)
     counters = np.zeros(8, dtype=np.int64)
     lib().or_step(mesh._h, n, _p(rows, D), ctypes.byref(params), int(seed), int(step_no),
                   *[_p(st[k], D) for k in STATE_KEYS], _p(st["elem"], I), _p(status, I),
-                  counters.ctypes.data_as(PL), None if pid is None else _p(pid, I))
+                  counters.ctypes.data_as(PL), None if pid is None else _p(pid, I),
+                  None if cond is None else _p(cond, D))
     names = ["walk_steps", "reflections", "crossings_periodic", "fallbacks", "brute", "lost",
              "omega_reflections", "near_face"]
     return dict(zip(names, counters.tolist())), status

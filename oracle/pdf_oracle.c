@@ -504,6 +504,76 @@ void or_elem_stats(int n_tri, long n_p, const int* elem, const double* u, const 
   }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Velocity-conditioned scalar mean for the IECM model (eq. IECM), by the    */
+/* sort-and-divide binning of the section on conditional statistics and its  */
+/* appendix: the particles of an element are sorted by U and divided into    */
+/* groups of equal count (up to one), each group sorted by V and divided,    */
+/* each subgroup sorted by W and divided; the conditional mean of a particle  */
+/* is the scalar mean of its final subgroup.                                  */
+/* READINGS: a group of n particles is divided into k = min(n_c, n / m_min)   */
+/* parts (at least 1), part j holding sorted positions with floor(k i / n) =  */
+/* j (the appendix's bin index, equal counts up to one); m_min = 2 unless     */
+/* given ("at least 2 particles should remain in every subgroup"); equal     */
+/* velocity components are ordered by particle id; sorts use the stored      */
+/* values.                                                                   */
+/* ------------------------------------------------------------------------ */
+static const double* or_sort_key;  /* component array the comparator reads */
+static const int* or_sort_pid;
+static int or_cmp_comp(const void* a, const void* b) {
+  const long i = *(const long*)a, j = *(const long*)b;
+  const double ki = or_sort_key[i], kj = or_sort_key[j];
+  if (ki < kj) return -1;
+  if (ki > kj) return 1;
+  const int pi = or_sort_pid ? or_sort_pid[i] : (int)i, pj = or_sort_pid ? or_sort_pid[j] : (int)j;
+  return (pi > pj) - (pi < pj);
+}
+
+/* Sorts idx[0..n) by component `level` (0 U, 1 V, 2 W) and divides it;
+ * recursion into the parts for the next component; at the last level the
+ * parts are the conditioning bins: cond[p] = the bin's scalar mean. */
+static void or_iecm_divide(long* idx, long n, int level, const int nc[3], int m_min, const double* comp[3],
+                           const int* pid, const double* ps, double* cond) {
+  if (level == 3) {
+    double s = 0.0;
+    for (long i = 0; i < n; ++i) s += ps[idx[i]];
+    const double mean = s / (double)n;
+    for (long i = 0; i < n; ++i) cond[idx[i]] = mean;
+    return;
+  }
+  or_sort_key = comp[level];
+  or_sort_pid = pid;
+  qsort(idx, (size_t)n, sizeof(long), or_cmp_comp);
+  long k = n / m_min;
+  if (k > nc[level]) k = nc[level];
+  if (k < 1) k = 1;
+  long start = 0;
+  for (long j = 0; j < k; ++j) {
+    /* part j: positions i with floor(k i / n) == j, i.e. [ceil(j n / k), ceil((j + 1) n / k)) */
+    const long end = ((j + 1) * n + k - 1) / k;
+    or_iecm_divide(idx + start, end - start, level + 1, nc, m_min, comp, pid, ps, cond);
+    start = end;
+  }
+}
+
+void or_iecm_cond(int n_tri, long n_p, const int* elem, const double* u, const double* v, const double* w,
+                  const double* ps, const int* pid, int nu, int nv, int nw, int m_min, double* cond) {
+  const int nc[3] = {nu, nv, nw};
+  const double* comp[3] = {u, v, w};
+  long* cnt = (long*)calloc((size_t)n_tri + 1, sizeof(long));
+  long* idx = (long*)malloc(sizeof(long) * (size_t)(n_p > 0 ? n_p : 1));
+  for (long p = 0; p < n_p; ++p) cnt[elem[p] + 1]++;
+  for (int e = 0; e < n_tri; ++e) cnt[e + 1] += cnt[e];
+  long* fill = (long*)malloc(sizeof(long) * ((size_t)n_tri + 1));
+  memcpy(fill, cnt, sizeof(long) * ((size_t)n_tri + 1));
+  for (long p = 0; p < n_p; ++p) idx[fill[elem[p]]++] = p;  /* particles of each element in index order */
+  for (int e = 0; e < n_tri; ++e)
+    if (cnt[e + 1] > cnt[e]) or_iecm_divide(idx + cnt[e], cnt[e + 1] - cnt[e], 0, nc, m_min, comp, pid, ps, cond);
+  free(fill);
+  free(idx);
+  free(cnt);
+}
+
 /* Second pass (sec. 3.3): node value = average over the non-empty elements
  * surrounding the node (READING: unweighted; a periodic twin pair is one
  * node; a node whose surrounding elements are all empty keeps its previous
@@ -758,10 +828,11 @@ void or_elem_coeff(const or_mesh* m, const double* ns, const double* nd, const d
  * reflections, [2] periodic crossings, [3] fallbacks, [4] brute-force,
  * [5] lost, [6] omega reflections, [7] near-face (min sub-area / A_e < 1e-12).
  * pid: the particle id of each entry (NULL: the index), for stepping a
- * subset of particles. */
+ * subset of particles.  cond: the velocity-conditioned scalar mean of each
+ * entry for eq. IECM (NULL: eq. IEM with the element mean). */
 void or_step(const or_mesh* m, long n_p, const double* rows, const or_params* P, uint64_t seed,
              uint32_t step, double* x, double* y, double* u, double* v, double* w, double* om,
-             double* ps, int* elem, int* status_out, long* counters, const int* pid) {
+             double* ps, int* elem, int* status_out, long* counters, const int* pid, const double* cond) {
   double sdt = sqrt(P->dt);
   double s2nu = (P->closure == OR_CLOSURE_SLM) ? 0.0 : sqrt(2.0 * P->nu);
   for (int i = 0; i < 8; ++i) counters[i] = 0;
@@ -791,7 +862,9 @@ void or_step(const or_mesh* m, long n_p, const double* rows, const or_params* P,
     double on = o - OR_C3 * mo * (o - mo) * P->dt - c[23] * mo * o * P->dt
               + sqrt(2.0 * OR_C3 * OR_C4 * mo * mo * (o > 0.0 ? o : 0.0)) * dWo;
     if (on < 0.0) { on = -on; counters[6]++; }
-    double pn = ps[p] - (ps[p] - c[24]) * P->dt * c[25];
+    /* eq. IEM with the element mean, or eq. IECM with the velocity-conditioned
+     * mean of the particle's bin when cond is given */
+    double pn = ps[p] - (ps[p] - (cond ? cond[p] : c[24])) * P->dt * c[25];
     or_track_info ti;
     int en = or_track(m, e, &xn, &yn, &Un[0], &Un[1], &ti);
     counters[0] += ti.walk_steps;
