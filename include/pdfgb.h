@@ -68,6 +68,7 @@ enum { PDF_TM_TURB = 0, PDF_TM_CPHI = 1, PDF_TM_SOURCE = 2 };
  * cross-stream balance (1/rho) d<P>/dy = -d<v^2>/dy (eq. cross-stream-mean-
  * momentum-channel). */
 enum { PDF_PRESSURE_NONE = 0, PDF_PRESSURE_CHANNEL = 1 };
+enum { PDF_MIX_IEM = 0, PDF_MIX_IECM = 1 };
 /* How the FP64-accurate particle step is computed.  FX (default): no FP64
  * instructions on the fast path -- positions in 64-bit fixed point (exact
  * increments and element tests), velocity, frequency and scalar in
@@ -112,6 +113,11 @@ typedef struct {
   double src_x, src_y, src_r;
   /* micromixing constants C_s, C_t of eq. micromixing-timescale-canyon */
   double Cs, Ct;
+  /* micromixing model: PDF_MIX_IEM (eq. IEM, the element mean of <phi>) or
+   * PDF_MIX_IECM (eq. IECM, the velocity-conditioned mean of the particle's
+   * bin from the last pdf_estimate_stats; needs pdf_particles_set_iecm) */
+  int32_t mix;
+  int32_t reserved;
 } pdf_model_params;
 
 /* Fills the paper's constants and dt = 1e-3, nu = 1e-3, Pi = 2e-3,
@@ -190,6 +196,22 @@ pdf_status pdf_particles_count(const pdf_particles* p, int64_t* n);
  * the central moments.  The paper has no counterpart (its particles live
  * in per-element linked lists).  PDF_EINVAL for every < 0. */
 pdf_status pdf_particles_set_reorder(pdf_particles* p, int32_t every);
+/* IECM conditioning (eq. IECM; the section on conditional statistics and
+ * its appendix): while enabled, every pdf_estimate_stats also computes each
+ * particle's velocity-conditioned scalar mean by sort-and-divide binning:
+ * the particles of an element are sorted by U and divided into nu parts of
+ * equal count (up to one), each part sorted by V and divided into nv, each
+ * of those sorted by W and divided into nw; a group of n particles is
+ * divided into min(n_c, n / m_min) parts (at least one), so every bin keeps
+ * m_min particles; equal components are ordered by particle id.  The mean
+ * of a particle is its final bin's scalar mean.  nu = nv = nw = 0 disables
+ * it.  The first call allocates 8 + 56 bytes per particle (the means and the
+ * working arrays of elements with more than 512 particles).  PDF_EINVAL for
+ * values < 1 (other than all zero). */
+pdf_status pdf_particles_set_iecm(pdf_particles* p, int32_t nu, int32_t nv, int32_t nw, int32_t m_min);
+/* The conditional means of the last pdf_estimate_stats, FP64 [n] in
+ * particle-id order (device memory); PDF_ESTATE if there are none. */
+pdf_status pdf_iecm_cond(const pdf_particles* p, double* cond, void* stream);
 
 /* Copies the state, converted to FP64, into caller buffers [n] (any pointer
  * may be NULL).  The buffers may be device or host memory: device buffers

@@ -39,7 +39,7 @@ def model_params(**kw):
     p = capi.ModelParams()
     lib().pdf_model_params_default(ctypes.byref(p))
     names = {"closure": {"glm": 0, "slm": 1, "frozen": 2}, "tm_mode": {"turb": 0, "cphi": 1, "source": 2},
-             "pressure": {"none": 0, "channel": 1}, "arith": {"fx": 0, "fp64": 1}}
+             "pressure": {"none": 0, "channel": 1}, "arith": {"fx": 0, "fp64": 1}, "mix": {"iem": 0, "iecm": 1}}
     for k, v in kw.items():
         if k in names and isinstance(v, str):
             v = names[k][v]
@@ -127,6 +127,17 @@ class Particles:
         check(lib().pdf_particles_get_state(self.handle, *[_ptr(out[k]) for k in
                                                             ("x", "y", "u", "v", "w", "om", "ps", "elem")],
                                             _stream(stream)), "pdf_particles_get_state")
+        return out
+
+    def set_iecm(self, bins=(5, 5, 5), m_min=2):
+        """Compute velocity-conditioned scalar means (IECM) at every statistics
+        call with the given sort-and-divide binning; bins=None disables it."""
+        b = (0, 0, 0) if bins is None else tuple(int(x) for x in bins)
+        check(lib().pdf_particles_set_iecm(self.handle, b[0], b[1], b[2], int(m_min)), "pdf_particles_set_iecm")
+
+    def iecm_cond(self, stream=None):
+        out = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        check(lib().pdf_iecm_cond(self.handle, _ptr(out), _stream(stream)), "pdf_iecm_cond")
         return out
 
     def set_reorder(self, every):

@@ -31,7 +31,8 @@ class ModelParams(ctypes.Structure):
                 ("c_phi", ctypes.c_double), ("closure", ctypes.c_int32), ("tm_mode", ctypes.c_int32),
                 ("pressure", ctypes.c_int32), ("arith", ctypes.c_int32)] + [
         (n, ctypes.c_double) for n in ("C1", "C2", "C3", "C4", "CT", "CL", "Ceta", "Cv", "gamma5",
-                                       "Comega1", "Comega2", "C0_slm", "src_x", "src_y", "src_r", "Cs", "Ct")]
+                                       "Comega1", "Comega2", "C0_slm", "src_x", "src_y", "src_r", "Cs", "Ct")] + [
+        ("mix", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class InitParams(ctypes.Structure):
@@ -73,6 +74,8 @@ PROTOTYPES = {
     "pdf_particles_destroy": (I32, [V]),
     "pdf_particles_count": (I32, [V, ctypes.POINTER(I64)]),
     "pdf_particles_set_reorder": (I32, [V, I32]),
+    "pdf_particles_set_iecm": (I32, [V, I32, I32, I32, I32]),
+    "pdf_iecm_cond": (I32, [V, V, V]),
     "pdf_particles_get_state": (I32, [V, V, V, V, V, V, V, V, V, V]),
     "pdf_particles_set_state": (I32, [V, V, V, V, V, V, V, V, V, V]),
     "pdf_step": (I32, [V, V, ctypes.POINTER(ModelParams), V, V, U32, V, ctypes.POINTER(StepInfo)]),

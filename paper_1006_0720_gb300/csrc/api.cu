@@ -42,4 +42,6 @@ extern "C" void pdf_model_params_default(pdf_model_params* p) {
   // concentrated source: none; micromixing constants of the table of constants (ch. 5)
   p->src_x = 0.0; p->src_y = 0.0; p->src_r = 0.0;
   p->Cs = 0.02; p->Ct = 0.7;
+  p->mix = PDF_MIX_IEM;
+  p->reserved = 0;
 }

@@ -169,6 +169,13 @@ struct pdf_particles {
   float *uf2 = nullptr, *vf2 = nullptr, *wf2 = nullptr, *omf2 = nullptr, *psf2 = nullptr;
   int32_t* pid2 = nullptr;
   int32_t reorder_every = 8, since_reorder = 0;
+  // IECM (eq. IECM): velocity-conditioned scalar mean per slot, computed by
+  // every pdf_estimate_stats while iecm_bins[0] > 0
+  fx::df* cond = nullptr;
+  float* iecm_scratch_f = nullptr;     // [8 n] working arrays of elements above the shared-memory cap
+  int32_t* iecm_scratch_i = nullptr;   // [6 n]
+  int32_t iecm_bins[3] = {0, 0, 0}, iecm_min = 2;
+  bool have_cond = false;
   double* stage = nullptr;  // [n] FP64 staging for host transfers (allocated on first use)
   float* rows_f32 = nullptr;  // [n_tri][32] coefficient rows in FP32 (same layout as rows)
   // statistics

@@ -153,6 +153,7 @@ static void free_particles(pdf_particles* p) {
   cudaFree(p->u2); cudaFree(p->v2); cudaFree(p->w2); cudaFree(p->om2); cudaFree(p->ps2);
   cudaFree(p->uf2); cudaFree(p->vf2); cudaFree(p->wf2); cudaFree(p->omf2); cudaFree(p->psf2);
   cudaFree(p->pid); cudaFree(p->pid2);
+  cudaFree(p->cond); cudaFree(p->iecm_scratch_f); cudaFree(p->iecm_scratch_i);
   cudaFree(p->stage);
   double* dbl[] = {p->es, p->ns, p->nd, p->eg, p->nc, p->rows};
   for (double* d : dbl) cudaFree(d);
@@ -368,6 +369,7 @@ extern "C" pdf_status pdf_particles_set_state(pdf_particles* p, const double* x,
   PDF_CUDA(cudaMemcpyAsync(p->elem, elem, sizeof(int32_t) * p->n, cudaMemcpyDefault, st));
   PDF_KERNEL("k_iota", st, k_iota<<<g, 256, 0, st>>>(p->pid, p->n));
   p->since_reorder = 0;
+  p->have_cond = false;
   long long nbad = 0;
   PDF_CUDA(cudaMemcpyAsync(&nbad, bad, sizeof(long long), cudaMemcpyDeviceToHost, st));
   PDF_CUDA(cudaStreamSynchronize(st));

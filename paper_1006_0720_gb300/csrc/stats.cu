@@ -717,6 +717,8 @@ static pdf_status reorder_state(pdf_particles* P, cudaStream_t st) {
   return PDF_OK;
 }
 
+pdf_status iecm_cond(pdf_particles* P, const int32_t* seg, const int32_t* order, cudaStream_t st);
+
 pdf_status estimate_stats(pdf_particles* P, cudaStream_t st) {
   const MeshDev& M = P->mesh->d;
   pdf_status s = group_by_element(P, st);
@@ -739,7 +741,7 @@ pdf_status estimate_stats(pdf_particles* P, cudaStream_t st) {
   PDF_KERNEL("k_elem_grad2", st, k_elem_grad2<<<blocks_for(M.n_tri, 128), 128, 0, st>>>(M.tri, M.dN, M.n_tri, P->nd, P->eg););
   PDF_KERNEL("k_node_grad2", st, k_node_grad2<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(M.nse_off, M.nse, M.n_nodes, P->eg, P->nd););
   P->have_stats = true;
-  return PDF_OK;
+  return iecm_cond(P, P->seg, P->sorted_pid, st);
 }
 
 }  // namespace pdfgb
@@ -809,7 +811,7 @@ pdf_status estimate_stats_with_buffers(pdf_particles* P, int32_t* keys_a, int32_
   PDF_KERNEL("k_elem_grad2", st, k_elem_grad2<<<blocks_for(M.n_tri, 128), 128, 0, st>>>(M.tri, M.dN, M.n_tri, P->nd, P->eg));
   PDF_KERNEL("k_node_grad2", st, k_node_grad2<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(M.nse_off, M.nse, M.n_nodes, P->eg, P->nd));
   P->have_stats = true;
-  return PDF_OK;
+  return iecm_cond(P, seg, vin, st);
 }
 
 }  // namespace pdfgb

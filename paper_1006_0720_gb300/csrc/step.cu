@@ -211,6 +211,7 @@ struct StepArgs {
   fx::df *u, *v, *w, *om, *ps;     // double-float (PDF_FP64 storage)
   int32_t* elem;
   const int32_t* pid;              // particle id of each slot (the Philox counter)
+  const fx::df* cond;              // IECM: the velocity-conditioned scalar mean of each slot, else NULL
   const double* rows;
   const ElemGeo* geo;
   const int32_t* tri;
@@ -412,7 +413,9 @@ __device__ __forceinline__ Counts advance_native(const StepArgs& A, int64_t p, c
   if (on < 0.0) { on = -on; ++c.om; }
   // scalar (eq. IEM)
   const double s = fx::to_double(A.ps[p]);
-  const double sn = s - (s - __ldg(R + 26)) * __ldg(R + 27);
+  // eq. IEM (element mean) or eq. IECM (the particle's conditional mean)
+  const double tgt = A.cond ? fx::to_double(A.cond[p]) : __ldg(R + 26);
+  const double sn = s - (s - tgt) * __ldg(R + 27);
   bool reinj = false;
   const int32_t en = walk(A, e, xn, yn, un, vn, c.walk, c.refl, c.per, c.fb, c.brute, c.near, reinj);
   if (en >= 0 && fabs(xn) < 64.0 && fabs(yn) < 64.0) {
@@ -800,13 +803,14 @@ __global__ void __launch_bounds__(256, 4) k_step_fx(StepArgs A, FxArgs F) {
       On = a.value();
       if (On.h < 0.0f) { On = fx::df{-On.h, -On.l}; ++c_om; }
     }
-    // scalar (eq. IEM): psi - (psi - <phi>) dt / t_m
+    // scalar: psi - (psi - <phi>) dt / t_m (eq. IEM) or with the particle's
+    // velocity-conditioned mean <phi|V> (eq. IECM)
     const fx::df S = ld_state(A.ps, p);
     fx::df Sn;
     {
       fx::acc a;
       a.init(S);
-      a.sub(fx::mul(ldc(R, 22), dsub(S, ldmean(R, 3))));
+      a.sub(fx::mul(ldc(R, 22), dsub(S, A.cond ? ld_state(A.cond, p) : ldmean(R, 3))));
       Sn = a.value();
     }
     // neighbour walk (sec. 3.5) in fixed point; walls, open boundaries and
@@ -886,7 +890,7 @@ __global__ void __launch_bounds__(256, 4) k_step_f32(StepArgs A, FxArgs F, F32Ar
     float on = o - __ldg(R + 23) * o + __ldg(R + 24) + __ldg(R + 25) * sqrtf(fmaxf(o, 0.f)) * D.g[5];
     if (on < 0.f) { on = -on; ++c_om; }
     const float s = S.ps[p];
-    const float sn = s - (s - __ldg(R + 26)) * __ldg(R + 27);
+    const float sn = s - (s - (A.cond ? A.cond[p].h : __ldg(R + 26))) * __ldg(R + 27);
     // position (eq. Lagrangian-position-exact), fixed point
     const int64_t X0 = A.x[p], Y0 = A.y[p];
     fx::acc a;
@@ -966,8 +970,8 @@ static pdf_status check_params(const pdf_model_params* p) {
   if (!p) return fail(PDF_EINVAL, "NULL params");
   if (!(p->dt > 0.0) || !(p->nu >= 0.0)) return fail(PDF_EINVAL, "params: dt must be > 0 and nu >= 0");
   if (p->closure < 0 || p->closure > 2 || p->tm_mode < 0 || p->tm_mode > 2 || p->pressure < 0 ||
-      p->pressure > 1 || p->arith < 0 || p->arith > 1)
-    return fail(PDF_EINVAL, "params: closure, tm_mode or pressure out of range");
+      p->pressure > 1 || p->arith < 0 || p->arith > 1 || p->mix < 0 || p->mix > 1)
+    return fail(PDF_EINVAL, "params: closure, tm_mode, pressure, arith or mix out of range");
   return PDF_OK;
 }
 
@@ -1018,12 +1022,15 @@ extern "C" pdf_status pdf_step(pdf_particles* p, const pdf_mesh* m, const pdf_mo
     s = build_rows(p, params, wp, nullptr, true, st);
     if (s != PDF_OK) return s;
   }
+  if (params->mix == PDF_MIX_IECM && !p->have_cond)
+    return fail(PDF_ESTATE, "pdf_step: IECM needs pdf_particles_set_iecm and a pdf_estimate_stats after it");
   if (info) PDF_CUDA(cudaMemsetAsync(p->counters, 0, sizeof(long long) * 8, st));
   StepArgs A;
   A.n = p->n;
   A.x = p->x; A.y = p->y; A.u = p->u; A.v = p->v; A.w = p->w; A.om = p->om; A.ps = p->ps;
   A.elem = p->elem;
   A.pid = p->pid;
+  A.cond = params->mix == PDF_MIX_IECM ? p->cond : nullptr;
   A.rows = p->rows;
   A.geo = M.geo; A.tri = M.tri; A.xy = M.xy; A.esup_off = M.esup_off; A.esup = M.esup;
   A.n_tri = M.n_tri;
