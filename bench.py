@@ -363,7 +363,7 @@ def run_gpu(args):
         ms32 = e0.elapsed_time(e1) / ksteps
         line["precision_fp32_state"] = {"value": n / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32,
                                         "steps": ksteps,
-                                        "what": "u, v, w, omega, psi stored and advanced in FP32; x, y FP64"}
+                                        "what": "u, v, w, omega, psi stored and advanced in FP32; x, y 64-bit fixed point"}
         # the elliptic-relaxation solve on this mesh: cold, and warm from the previous step
         wp = torch.zeros((9, gm.n_nodes), dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
@@ -380,6 +380,7 @@ def run_gpu(args):
                                "cold": {"iterations_max": max(it_cold), "seconds": t_cold},
                                "warm_previous_step": {"iterations_max": max(it_warm), "seconds": t_warm}}
         del gq
+        line["iecm"] = run_iecm(pg, torch, stream, gm, cfg, seed, psi, p, max(5, min(args.steps, 20)))
     if not args.no_cpu_baseline and world == 1:
         try:
             line["cpu_baseline"] = cpu_baseline_measure(3)
@@ -389,6 +390,45 @@ def run_gpu(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def run_iecm(pg, torch, stream, gm, cfg, seed, psi, p, steps, bins=(5, 5, 5)):
+    """Steps of the benchmark workload with the IECM micromixing model: the
+    velocity-conditioned scalar means (sort-and-divide binning) are computed
+    at every statistics call; the time per step and of the conditioning
+    kernel alone."""
+    gi = pg.Particles(gm, seed, ppe=cfg["ppe"], u_sigma=cfg["u_sigma"], elem_psi0=psi)
+    gi.set_iecm(bins, 2)
+    pi = pg.model_params(dt=p.dt, nu=p.nu, Pi=p.Pi, closure=cfg["closure"], mix="iecm")
+    pg.pdf_estimate_stats(gi, gm)
+    for s in range(3):
+        pg.pdf_step(gi, gm, pi, step=s)
+        pg.pdf_estimate_stats(gi, gm)
+    torch.cuda.synchronize()
+    pg.pdf_profile_reset()
+    pg.pdf_profile_only("k_iecm_cond")
+    pg.pdf_profile_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(steps):
+        pg.pdf_step(gi, gm, pi, step=3 + s, stream=stream)
+        pg.pdf_estimate_stats(gi, gm, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pg.pdf_profile_enable(False)
+    c, t = pg.pdf_profile_query("k_iecm_cond")
+    pg.pdf_profile_reset()
+    pg.pdf_profile_only(None)
+    ms = e0.elapsed_time(e1) / steps
+    del gi
+    return {"value": gm_particles(cfg) / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "bins": list(bins), "m_min": 2, "k_iecm_cond_ms": t / c if c else None,
+            "what": "IECM micromixing (eq. IECM) with sort-and-divide conditioning at every statistics call"}
+
+
+def gm_particles(cfg):
+    return cfg["n_tri"] * cfg["ppe"]
 
 
 def run_obstacles(pg, torch, stream, steps=10, name="obstacles_20x5_mean128"):

@@ -205,9 +205,9 @@ pdf_status pdf_particles_set_reorder(pdf_particles* p, int32_t every);
  * divided into min(n_c, n / m_min) parts (at least one), so every bin keeps
  * m_min particles; equal components are ordered by particle id.  The mean
  * of a particle is its final bin's scalar mean.  nu = nv = nw = 0 disables
- * it.  The first call allocates 8 + 56 bytes per particle (the means and the
- * working arrays of elements with more than 512 particles).  PDF_EINVAL for
- * values < 1 (other than all zero). */
+ * it.  The first call allocates 8 + 88 bytes per particle (the means and the
+ * working arrays of elements with more than 256 particles).  PDF_EINVAL for
+ * bins outside [1, 127] (other than all zero) or m_min < 1. */
 pdf_status pdf_particles_set_iecm(pdf_particles* p, int32_t nu, int32_t nv, int32_t nw, int32_t m_min);
 /* The conditional means of the last pdf_estimate_stats, FP64 [n] in
  * particle-id order (device memory); PDF_ESTATE if there are none. */

@@ -172,7 +172,7 @@ struct pdf_particles {
   // IECM (eq. IECM): velocity-conditioned scalar mean per slot, computed by
   // every pdf_estimate_stats while iecm_bins[0] > 0
   fx::df* cond = nullptr;
-  float* iecm_scratch_f = nullptr;     // [8 n] working arrays of elements above the shared-memory cap
+  float* iecm_scratch_f = nullptr;     // [16 n] working arrays of elements above the shared-memory cap
   int32_t* iecm_scratch_i = nullptr;   // [6 n]
   int32_t iecm_bins[3] = {0, 0, 0}, iecm_min = 2;
   bool have_cond = false;

@@ -9,7 +9,7 @@
 // are ordered by particle id.
 //
 // One block per element.  The element's particles are copied into shared
-// memory (or, above kIecmCap particles, into a global scratch slice) and
+// memory (or, above kIecmCap particles, into global scratch slices) and
 // sorted by rank counting inside each group: O(n^2) comparisons per level,
 // fine for the tens to hundreds of particles per element the method uses.
 #include "common.cuh"
@@ -18,12 +18,22 @@
 namespace pdfgb {
 
 constexpr int kIecmThreads = 128;
-constexpr int kIecmCap = 512;
+constexpr int kIecmCap = 256;
 
-struct IecmView {  // per-particle working arrays (shared or global)
-  float *uh, *ul, *vh, *vl, *wh, *wl;
-  float *sh, *sl;  // the scalar
-  int32_t *id, *slot, *perm, *perm2, *gs, *ge;
+// One copy of the per-particle data (shared or global): the three velocity
+// components and the scalar as (high, low) pairs, the particle id and the
+// storage slot.  Two copies alternate: every level sorts by moving the data
+// into the other copy at the sorted positions, so that the comparisons read
+// consecutive entries (no indirection).
+struct IecmBuf {
+  float* f[8];  // uh ul vh vl wh wl sh sl
+  int32_t* id;
+  int32_t* slot;
+};
+
+struct IecmView {  // the two copies and the group bounds of each position
+  IecmBuf a, b;
+  int32_t *gs, *ge;
 };
 
 __device__ __forceinline__ void load_comp(const fx::df* a, int64_t s, float& h, float& l) {
@@ -36,10 +46,22 @@ __device__ __forceinline__ void load_comp(const float* a, int64_t s, float& h, f
   l = 0.0f;
 }
 
-// (key_i, id_i) < (key_j, id_j) for double-float keys (normalized pairs
-// order like their values)
-__device__ __forceinline__ bool key_less(float hi, float li, int32_t ii, float hj, float lj, int32_t ij) {
-  return hi < hj || (hi == hj && (li < lj || (li == lj && ii < ij)));
+// (key_j, id_j) < (key_i, id_i) for double-float keys (normalized pairs
+// order like their values); evaluated without branches
+__device__ __forceinline__ int key_less(float hj, float lj, int32_t ij, float hi, float li, int32_t ii) {
+  return (int)((hj < hi) | ((hj == hi) & ((lj < li) | ((lj == li) & (ij < ii)))));
+}
+
+// floor(k i / n) and ceil(j n / k) for 0 <= i < n, 0 <= j <= k <= 127: 32-bit
+// unsigned arithmetic while the products stay below 2^31 (n < 2^24), 64-bit
+// beyond
+__device__ __forceinline__ int32_t part_of(int32_t k, int32_t i, int32_t n) {
+  if (n < (1 << 24)) return (int32_t)((uint32_t)(k * i) / (uint32_t)n);
+  return (int32_t)(((int64_t)k * i) / n);
+}
+__device__ __forceinline__ int32_t part_start(int32_t j, int32_t n, int32_t k) {
+  if (n < (1 << 24)) return (int32_t)(((uint32_t)(j * n) + (uint32_t)(k - 1)) / (uint32_t)k);
+  return (int32_t)(((int64_t)j * n + k - 1) / k);
 }
 
 template <typename T>
@@ -50,7 +72,7 @@ __global__ void __launch_bounds__(kIecmThreads) k_iecm_cond(const int32_t* __res
                                                             const int32_t* __restrict__ pid, int nc0, int nc1,
                                                             int nc2, int m_min, IecmView big,
                                                             fx::df* __restrict__ cond) {
-  __shared__ float s_f[8][kIecmCap];
+  __shared__ float s_f[2][8][kIecmCap];
   __shared__ int32_t s_i[6][kIecmCap];
   const int tid = threadIdx.x;
   for (int32_t e = blockIdx.x; e < n_tri; e += gridDim.x) {
@@ -58,74 +80,89 @@ __global__ void __launch_bounds__(kIecmThreads) k_iecm_cond(const int32_t* __res
     if (N == 0) continue;
     IecmView V;
     if (N <= kIecmCap) {
-      V = IecmView{s_f[0], s_f[1], s_f[2], s_f[3], s_f[4], s_f[5], s_f[6], s_f[7],
-                   s_i[0], s_i[1], s_i[2], s_i[3], s_i[4], s_i[5]};
-    } else {  // the element's slice of the global scratch
-      V = IecmView{big.uh + beg, big.ul + beg, big.vh + beg, big.vl + beg, big.wh + beg, big.wl + beg,
-                   big.sh + beg, big.sl + beg, big.id + beg, big.slot + beg, big.perm + beg,
-                   big.perm2 + beg, big.gs + beg, big.ge + beg};
+      for (int c = 0; c < 2; ++c) {
+        IecmBuf& B = c == 0 ? V.a : V.b;
+        for (int q = 0; q < 8; ++q) B.f[q] = s_f[c][q];
+        B.id = s_i[2 * c];
+        B.slot = s_i[2 * c + 1];
+      }
+      V.gs = s_i[4];
+      V.ge = s_i[5];
+    } else {  // the element's slices of the global scratch
+      V = big;
+      for (int c = 0; c < 2; ++c) {
+        IecmBuf& B = c == 0 ? V.a : V.b;
+        for (int q = 0; q < 8; ++q) B.f[q] += beg;
+        B.id += beg;
+        B.slot += beg;
+      }
+      V.gs += beg;
+      V.ge += beg;
     }
     __syncthreads();  // the previous element is done with the arrays
     for (int i = tid; i < N; i += kIecmThreads) {
       const int64_t s = order ? (int64_t)order[beg + i] : (int64_t)(beg + i);
-      V.slot[i] = (int32_t)s;
-      V.id[i] = pid[s];
-      load_comp(u, s, V.uh[i], V.ul[i]);
-      load_comp(v, s, V.vh[i], V.vl[i]);
-      load_comp(w, s, V.wh[i], V.wl[i]);
-      load_comp(ps, s, V.sh[i], V.sl[i]);
-      V.perm[i] = i;
+      V.a.slot[i] = (int32_t)s;
+      V.a.id[i] = pid[s];
+      load_comp(u, s, V.a.f[0][i], V.a.f[1][i]);
+      load_comp(v, s, V.a.f[2][i], V.a.f[3][i]);
+      load_comp(w, s, V.a.f[4][i], V.a.f[5][i]);
+      load_comp(ps, s, V.a.f[6][i], V.a.f[7][i]);
       V.gs[i] = 0;
       V.ge[i] = N;
     }
     __syncthreads();
     const int ncs[3] = {nc0, nc1, nc2};
     for (int level = 0; level < 3; ++level) {
-      const float* kh = level == 0 ? V.uh : (level == 1 ? V.vh : V.wh);
-      const float* kl = level == 0 ? V.ul : (level == 1 ? V.vl : V.wl);
-      // sort each group [gs, ge) by rank counting
+      const float* kh = V.a.f[2 * level];
+      const float* kl = V.a.f[2 * level + 1];
+      // sort each group [gs, ge) by rank counting; every entry moves to its
+      // sorted position in the other copy
       for (int pos = tid; pos < N; pos += kIecmThreads) {
-        const int32_t i = V.perm[pos];
         const int32_t a = V.gs[pos], b = V.ge[pos];
-        const float hi = kh[i], li = kl[i];
-        const int32_t ii = V.id[i];
+        const float hi = kh[pos], li = kl[pos];
+        const int32_t ii = V.a.id[pos];
         int32_t r = 0;
-        for (int32_t q = a; q < b; ++q) {
-          const int32_t j = V.perm[q];
-          r += key_less(kh[j], kl[j], V.id[j], hi, li, ii) ? 1 : 0;
-        }
-        V.perm2[a + r] = i;
+#pragma unroll 4
+        for (int32_t q = a; q < b; ++q) r += key_less(kh[q], kl[q], V.a.id[q], hi, li, ii);
+        const int32_t to = a + r;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) V.b.f[c][to] = V.a.f[c][pos];
+        V.b.id[to] = ii;
+        V.b.slot[to] = V.a.slot[pos];
       }
       __syncthreads();
       // divide each group into k parts of equal count
       for (int pos = tid; pos < N; pos += kIecmThreads) {
         const int32_t a = V.gs[pos], n = V.ge[pos] - a;
-        int32_t k = n / m_min;
+        int32_t k = (int32_t)((uint32_t)n / (uint32_t)m_min);
         if (k > ncs[level]) k = ncs[level];
         if (k < 1) k = 1;
-        const int32_t j = (int32_t)(((int64_t)k * (pos - a)) / n);
-        V.gs[pos] = a + (int32_t)(((int64_t)j * n + k - 1) / k);
-        V.ge[pos] = a + (int32_t)(((int64_t)(j + 1) * n + k - 1) / k);
-        V.perm[pos] = V.perm2[pos];
+        const int32_t j = part_of(k, pos - a, n);
+        V.gs[pos] = a + part_start(j, n, k);
+        V.ge[pos] = a + part_start(j + 1, n, k);
       }
+      const IecmBuf t = V.a;
+      V.a = V.b;
+      V.b = t;
       __syncthreads();
     }
     // bin means: the first position of each bin adds its bin in sorted order
-    // (double-float) and stores the mean at that position
+    // (double-float) and leaves the mean at that position of the spare copy
     for (int pos = tid; pos < N; pos += kIecmThreads) {
       const int32_t a = V.gs[pos], b = V.ge[pos];
       if (pos != a) continue;
       fx::acc s;
-      s.init(fx::df{V.sh[V.perm[a]], V.sl[V.perm[a]]});
-      for (int32_t q = a + 1; q < b; ++q) s.add(fx::df{V.sh[V.perm[q]], V.sl[V.perm[q]]});
+      s.init(fx::df{V.a.f[6][a], V.a.f[7][a]});
+      for (int32_t q = a + 1; q < b; ++q) s.add(fx::df{V.a.f[6][q], V.a.f[7][q]});
       const fx::df mean = fx::df_norm(fx::mul(s.value(), fx::recip_df(b - a)));
-      V.uh[a] = mean.h;  // the sort keys are no longer needed
-      V.ul[a] = mean.l;
+      V.b.f[0][a] = mean.h;
+      V.b.f[1][a] = mean.l;
     }
     __syncthreads();
     for (int pos = tid; pos < N; pos += kIecmThreads) {
       const int32_t a = V.gs[pos];
-      reinterpret_cast<float2*>(cond)[V.slot[V.perm[pos]]] = make_float2(V.uh[a], V.ul[a]);
+      reinterpret_cast<float2*>(cond)[V.a.slot[pos]] = make_float2(V.b.f[0][a], V.b.f[1][a]);
     }
   }
 }
@@ -146,8 +183,14 @@ pdf_status iecm_cond(pdf_particles* P, const int32_t* seg, const int32_t* order,
   float* f = P->iecm_scratch_f;
   int32_t* g = P->iecm_scratch_i;
   const int64_t n = P->n;
-  big = IecmView{f, f + n, f + 2 * n, f + 3 * n, f + 4 * n, f + 5 * n, f + 6 * n, f + 7 * n,
-                 g, g + n, g + 2 * n, g + 3 * n, g + 4 * n, g + 5 * n};
+  for (int c = 0; c < 2; ++c) {
+    IecmBuf& B = c == 0 ? big.a : big.b;
+    for (int q = 0; q < 8; ++q) B.f[q] = f + (8 * c + q) * n;
+    B.id = g + (2 * c) * n;
+    B.slot = g + (2 * c + 1) * n;
+  }
+  big.gs = g + 4 * n;
+  big.ge = g + 5 * n;
   const int nb = iecm_blocks(M.n_tri);
   if (P->precision == PDF_FP64) {
     PDF_KERNEL("k_iecm_cond", st, k_iecm_cond<fx::df><<<nb, kIecmThreads, 0, st>>>(
@@ -180,12 +223,12 @@ extern "C" pdf_status pdf_particles_set_iecm(pdf_particles* p, int32_t nu, int32
     p->have_cond = false;
     return PDF_OK;
   }
-  if (nu < 1 || nv < 1 || nw < 1 || m_min < 1)
-    return fail(PDF_EINVAL, "pdf_particles_set_iecm: bins and m_min must be >= 1 (or all bins 0 to disable)");
+  if (nu < 1 || nv < 1 || nw < 1 || m_min < 1 || nu > 127 || nv > 127 || nw > 127)
+    return fail(PDF_EINVAL, "pdf_particles_set_iecm: bins must be in [1, 127] and m_min >= 1 (or all bins 0 to disable)");
   if (!p->cond) {
     const size_t n = (size_t)p->n;
     PDF_CUDA(cudaMalloc((void**)&p->cond, sizeof(fx::df) * n));
-    PDF_CUDA(cudaMalloc((void**)&p->iecm_scratch_f, sizeof(float) * 8 * n));
+    PDF_CUDA(cudaMalloc((void**)&p->iecm_scratch_f, sizeof(float) * 16 * n));
     PDF_CUDA(cudaMalloc((void**)&p->iecm_scratch_i, sizeof(int32_t) * 6 * n));
   }
   p->iecm_bins[0] = nu;

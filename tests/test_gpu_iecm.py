@@ -31,7 +31,7 @@ def _setup(precision=capi.PDF_FP64, big=True):
     n_tri = 2 * 19 * 39
     counts = np.random.default_rng(5).integers(0, 120, n_tri).astype(np.int32)
     if big:
-        counts[[7, 300, 301]] = [600, 777, 1500]   # above the shared-memory capacity of 512
+        counts[[7, 300, 301]] = [600, 777, 1500]   # above the shared-memory capacity of 256
     counts[[11, 12]] = [1, 2]
     psi = inputs.scalar_slab(m)
     gm = pg.Mesh(m)
