@@ -22,9 +22,10 @@ TAG_WALL = 1
 TAG_PERIODIC = 2
 TAG_INFLOW = 3
 TAG_OUTFLOW = 4
+TAG_NOSLIP = 5
 
 
-def channel_mesh(nx, ny, jitter=0.2, seed=1, period=2.0 * np.pi, y0=-1.0, y1=1.0):
+def channel_mesh(nx, ny, jitter=0.2, seed=1, period=2.0 * np.pi, y0=-1.0, y1=1.0, wall_tag=None):
     if nx < 3 or ny < 2:
         raise ValueError("channel_mesh needs nx >= 3 and ny >= 2")
     dx = period / (nx - 1)
@@ -73,11 +74,12 @@ def channel_mesh(nx, ny, jitter=0.2, seed=1, period=2.0 * np.pi, y0=-1.0, y1=1.0
     for j in range(ny):
         twin[j * nx] = j * nx + nx - 1
         twin[j * nx + nx - 1] = j * nx
+    wtag = TAG_WALL if wall_tag is None else wall_tag
     bnd = []
     for i in range(nx - 1):
-        bnd.append((i, i + 1, TAG_WALL))
+        bnd.append((i, i + 1, wtag))
         top = (ny - 1) * nx
-        bnd.append((top + i, top + i + 1, TAG_WALL))
+        bnd.append((top + i, top + i + 1, wtag))
     for j in range(ny - 1):
         bnd.append((j * nx, (j + 1) * nx, TAG_PERIODIC))
         bnd.append((j * nx + nx - 1, (j + 1) * nx + nx - 1, TAG_PERIODIC))

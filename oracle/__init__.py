@@ -33,6 +33,7 @@ TM_MODE = {"turb": 0, "cphi": 1, "source": 2}
 PRESSURE = {"none": 0, "channel": 1}
 
 TRK_FALLBACK, TRK_BRUTE, TRK_LOST, TRK_EXIT_OUT, TRK_EXIT_IN, TRK_REINJECT, TRK_NEAR_FACE = 1, 2, 4, 8, 16, 32, 256
+TRK_NOSLIP = 64     # the no-slip wall condition was applied
 
 
 def build(force=False):
@@ -102,7 +103,9 @@ def lib():
             L.or_node_coeff.argtypes = [PD, PD, PD, ctypes.POINTER(_Params), PD, PD]
             L.or_elem_coeff.argtypes = [ctypes.c_void_p, PD, PD, PD, ctypes.POINTER(_Params), PD]
             L.or_step.argtypes = [ctypes.c_void_p, ctypes.c_long, PD, ctypes.POINTER(_Params),
-                                  ctypes.c_uint64, U32, PD, PD, PD, PD, PD, PD, PD, PI, PI, PL, PI, PD]
+                                  ctypes.c_uint64, U32, PD, PD, PD, PD, PD, PD, PD, PI, PI, PL, PI, PD, PD]
+            L.or_noslip_omega.argtypes = [ctypes.c_void_p, PD, PD]
+            L.or_mesh_noslip.argtypes = [ctypes.c_void_p, PI, PD]
             L.or_iecm_cond.argtypes = [I, ctypes.c_long, PI, PD, PD, PD, PD, PI, I, I, I, I, PD]
             _lib = L
     return _lib
@@ -171,6 +174,9 @@ class Mesh:
         self.nbr = np.zeros((self.n_tri, 3), dtype=np.int32)
         self.shift = np.zeros((self.n_tri, 3), dtype=np.int32)
         lib().or_mesh_get(h, _p(self.area, D), _p(self.nbr, I), _p(self.shift, I))
+        self.noslip_flag = np.zeros(self.n_tri, dtype=np.int32)
+        self.noslip_line = np.zeros((self.n_tri, 4))
+        lib().or_mesh_noslip(h, _p(self.noslip_flag, I), _p(self.noslip_line, D))
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -295,20 +301,31 @@ def iecm_cond(n_tri, st, bins=(5, 5, 5), m_min=2, pid=None):
     return out
 
 
-def step(mesh, rows, params, seed, step_no, st, pid=None, cond=None):
+def noslip_omega(mesh, ns):
+    """Per element: the mean frequency given to particles striking a no-slip
+    wall (eq. frequency-wallstats); 0 away from no-slip walls."""
+    out = np.zeros(mesh.n_tri)
+    ns = np.ascontiguousarray(ns, dtype=np.float64)
+    lib().or_noslip_omega(mesh._h, _p(ns, D), _p(out, D))
+    return out
+
+
+def step(mesh, rows, params, seed, step_no, st, pid=None, cond=None, omega_wall=None):
     """Advance every particle one step in place.  Returns (counters, status).
     pid: particle ids of the entries (default: their index); cond: the
-    velocity-conditioned scalar means for eq. IECM (default: eq. IEM)."""
+    velocity-conditioned scalar means for eq. IECM (default: eq. IEM);
+    omega_wall: noslip_omega() for meshes with no-slip walls."""
     n = len(st["x"])
     pid = None if pid is None else np.ascontiguousarray(pid, dtype=np.int32)
     cond = None if cond is None else np.ascontiguousarray(cond, dtype=np.float64)
+    omega_wall = None if omega_wall is None else np.ascontiguousarray(omega_wall, dtype=np.float64)
     rows = np.ascontiguousarray(rows, dtype=np.float64)
     status = np.zeros(n, dtype=np.int32)
     counters = np.zeros(8, dtype=np.int64)
     lib().or_step(mesh._h, n, _p(rows, D), ctypes.byref(params), int(seed), int(step_no),
                   *[_p(st[k], D) for k in STATE_KEYS], _p(st["elem"], I), _p(status, I),
                   counters.ctypes.data_as(PL), None if pid is None else _p(pid, I),
-                  None if cond is None else _p(cond, D))
+                  None if cond is None else _p(cond, D), None if omega_wall is None else _p(omega_wall, D))
     names = ["walk_steps", "reflections", "crossings_periodic", "fallbacks", "brute", "lost",
              "omega_reflections", "near_face"]
     return dict(zip(names, counters.tolist())), status

@@ -152,8 +152,8 @@ enum { OR_PURPOSE_STEP = 0, OR_PURPOSE_INIT = 1 };
 /* Mesh connectivity (sec. 3.3 linked lists; sec. 3.5 element-surrounding-  */
 /* element list with tagged boundary neighbours).                            */
 /* ------------------------------------------------------------------------ */
-enum { OR_TAG_WALL = 1, OR_TAG_PERIODIC = 2, OR_TAG_INFLOW = 3, OR_TAG_OUTFLOW = 4 };
-enum { OR_NBR_WALL = -1, OR_NBR_INFLOW = -3, OR_NBR_OUTFLOW = -4 };
+enum { OR_TAG_WALL = 1, OR_TAG_PERIODIC = 2, OR_TAG_INFLOW = 3, OR_TAG_OUTFLOW = 4, OR_TAG_NOSLIP = 5 };
+enum { OR_NBR_WALL = -1, OR_NBR_INFLOW = -3, OR_NBR_OUTFLOW = -4, OR_NBR_NOSLIP = -5 };
 
 typedef struct {
   int n_nodes, n_tri;
@@ -169,6 +169,11 @@ typedef struct {
   int* esup;
   int* nse_off;    /* node -> elements around the node or its twin (ascending ids) */
   int* nse;
+  /* no-slip walls (sec. no-slip wall-boundary conditions): for an element
+   * with a node on a no-slip edge, the line of the nearest such edge (a point
+   * and the unit normal into the fluid); nsw_flag[e] = 0 elsewhere */
+  int* nsw_flag;
+  double* nsw;     /* [n_tri][4] x_a, y_a, n_x, n_y */
 } or_mesh;
 
 static int cmp_int(const void* a, const void* b) {
@@ -193,6 +198,7 @@ void or_mesh_free(or_mesh* m) {
   if (!m) return;
   free(m->xy); free(m->tri); free(m->twin); free(m->area); free(m->nbr); free(m->shift); free(m->reinj);
   free(m->esup_off); free(m->esup); free(m->nse_off); free(m->nse);
+  free(m->nsw_flag); free(m->nsw);
   free(m);
 }
 
@@ -267,6 +273,7 @@ or_mesh* or_mesh_create(int n_nodes, const double* xy, int n_tri, const int* tri
        * re-entering fluid.  Without twins they are open boundaries. */
       int open_pair = (tag == OR_TAG_INFLOW || tag == OR_TAG_OUTFLOW) && m->twin[a] >= 0 && m->twin[b] >= 0;
       if (tag == OR_TAG_WALL) m->nbr[3 * e + k] = OR_NBR_WALL;
+      else if (tag == OR_TAG_NOSLIP) m->nbr[3 * e + k] = OR_NBR_NOSLIP;
       else if (tag == OR_TAG_INFLOW && !open_pair) m->nbr[3 * e + k] = OR_NBR_INFLOW;
       else if (tag == OR_TAG_OUTFLOW && !open_pair) m->nbr[3 * e + k] = OR_NBR_OUTFLOW;
       else if (tag == OR_TAG_PERIODIC || open_pair) {
@@ -283,7 +290,47 @@ or_mesh* or_mesh_create(int n_nodes, const double* xy, int n_tri, const int* tri
       } else { or_mesh_free(m); return NULL; }
     }
   }
+  /* READING: the wall a near-wall particle is measured from is the no-slip
+   * edge nearest to its element's centroid among the edges sharing a node
+   * with the element (ties: the first found, elements and edges ascending) */
+  m->nsw_flag = (int*)calloc(n_tri, sizeof(int));
+  m->nsw = (double*)calloc(4 * (size_t)n_tri, sizeof(double));
+  double* best = (double*)malloc(sizeof(double) * n_tri);
+  for (int e = 0; e < n_tri; ++e) best[e] = INFINITY;
+  for (int f = 0; f < n_tri; ++f)
+    for (int k = 0; k < 3; ++k) {
+      if (m->nbr[3 * f + k] != OR_NBR_NOSLIP) continue;
+      int a = m->tri[3 * f + (k + 1) % 3], b = m->tri[3 * f + (k + 2) % 3];
+      double xa = xy[2 * a], ya = xy[2 * a + 1], tx = xy[2 * b] - xa, ty = xy[2 * b + 1] - ya;
+      double len = sqrt(tx * tx + ty * ty);
+      double nx = -ty / len, ny = tx / len;  /* into the fluid: the edge runs a -> b counter-clockwise */
+      int ends[2] = {a, b};
+      for (int q = 0; q < 2; ++q)
+        for (int i = m->esup_off[ends[q]]; i < m->esup_off[ends[q] + 1]; ++i) {
+          int e = m->esup[i];
+          const int* t = m->tri + 3 * e;
+          double cx = (xy[2 * t[0]] + xy[2 * t[1]] + xy[2 * t[2]]) / 3.0;
+          double cy = (xy[2 * t[0] + 1] + xy[2 * t[1] + 1] + xy[2 * t[2] + 1]) / 3.0;
+          /* distance from the centroid to the segment a-b */
+          double s = ((cx - xa) * tx + (cy - ya) * ty) / (len * len);
+          if (s < 0.0) s = 0.0;
+          if (s > 1.0) s = 1.0;
+          double dx = cx - (xa + s * tx), dy = cy - (ya + s * ty);
+          double dist = sqrt(dx * dx + dy * dy);
+          if (dist < best[e]) {
+            best[e] = dist;
+            m->nsw_flag[e] = 1;
+            m->nsw[4 * e] = xa; m->nsw[4 * e + 1] = ya; m->nsw[4 * e + 2] = nx; m->nsw[4 * e + 3] = ny;
+          }
+        }
+    }
+  free(best);
   return m;
+}
+
+void or_mesh_noslip(const or_mesh* m, int* flag, double* line) {
+  if (flag) memcpy(flag, m->nsw_flag, sizeof(int) * m->n_tri);
+  if (line) memcpy(line, m->nsw, sizeof(double) * 4 * m->n_tri);
 }
 
 void or_mesh_get(const or_mesh* m, double* area, int* nbr, int* shift) {
@@ -316,7 +363,7 @@ static int or_inside(const double N[3]) { return N[0] >= 0.0 && N[1] >= 0.0 && N
 
 /* Tracking status bits (returned per particle). */
 enum { OR_TRK_FALLBACK = 1, OR_TRK_BRUTE = 2, OR_TRK_LOST = 4, OR_TRK_EXIT_OUT = 8, OR_TRK_EXIT_IN = 16,
-       OR_TRK_REINJECT = 32 };
+       OR_TRK_REINJECT = 32, OR_TRK_NOSLIP = 64 };
 
 typedef struct { int walk_steps, reflections, crossings_periodic, status; double min_rel; } or_track_info;
 
@@ -397,7 +444,11 @@ int or_track(const or_mesh* m, int e0, double* px, double* py, double* u, double
     double d = (x - xa) * nx + (y - ya) * ny;
     x = x - 2.0 * d * nx;
     y = y - 2.0 * d * ny;
-    if (u && v) {
+    if (nb == OR_NBR_NOSLIP) {
+      /* no-slip wall: the position is reflected, the velocity is reset by the
+       * wall condition in or_step */
+      info->status |= OR_TRK_NOSLIP;
+    } else if (u && v) {
       double un = (*u) * nx + (*v) * ny;
       *u = *u - 2.0 * un * nx;
       *v = *v - 2.0 * un * ny;
@@ -608,6 +659,31 @@ void or_shape_derivs(const or_mesh* m, int e, double dNdx[3], double dNdy[3]) {
   double twoA = 2.0 * m->area[e];
   dNdx[0] = (-yCA + yBA) / twoA; dNdx[1] = yCA / twoA; dNdx[2] = -yBA / twoA;
   dNdy[0] = (xCA - xBA) / twoA;  dNdy[1] = -xCA / twoA; dNdy[2] = xBA / twoA;
+}
+
+/* Mean of the frequency given to a particle striking a no-slip wall (eq.
+ * frequency-wallstats): <omega> = (1/C_T) d sqrt(2k)/dn along the normal into
+ * the fluid, from the element gradient (eq. gradient) of the nodal sqrt(2k) =
+ * sqrt(<uu> + <vv> + <ww>).  READING: where that is not positive (no growth
+ * of k away from the wall yet) the element average of the nodal <omega> is
+ * used.  out[e] = 0 for elements away from no-slip walls. */
+void or_noslip_omega(const or_mesh* m, const double* ns, double* out) {
+  for (int e = 0; e < m->n_tri; ++e) {
+    out[e] = 0.0;
+    if (!m->nsw_flag[e]) continue;
+    double dNdx[3], dNdy[3];
+    or_shape_derivs(m, e, dNdx, dNdy);
+    const double nx = m->nsw[4 * e + 2], ny = m->nsw[4 * e + 3];
+    double g = 0.0, om = 0.0;
+    for (int j = 0; j < 3; ++j) {
+      const double* S = ns + OR_NNS * m->tri[3 * e + j];
+      double kk = S[5] + S[6] + S[7];
+      g += sqrt(kk > 0.0 ? kk : 0.0) * (dNdx[j] * nx + dNdy[j] * ny);
+      om += S[3];
+    }
+    double w = g / OR_CT;
+    out[e] = (w > 0.0) ? w : om / 3.0;
+  }
 }
 
 /* Gradient of nodal fields q[n*stride + off] over each element (eq.
@@ -832,7 +908,8 @@ void or_elem_coeff(const or_mesh* m, const double* ns, const double* nd, const d
  * entry for eq. IECM (NULL: eq. IEM with the element mean). */
 void or_step(const or_mesh* m, long n_p, const double* rows, const or_params* P, uint64_t seed,
              uint32_t step, double* x, double* y, double* u, double* v, double* w, double* om,
-             double* ps, int* elem, int* status_out, long* counters, const int* pid, const double* cond) {
+             double* ps, int* elem, int* status_out, long* counters, const int* pid, const double* cond,
+             const double* omega_wall) {
   double sdt = sqrt(P->dt);
   double s2nu = (P->closure == OR_CLOSURE_SLM) ? 0.0 : sqrt(2.0 * P->nu);
   for (int i = 0; i < 8; ++i) counters[i] = 0;
@@ -865,8 +942,48 @@ void or_step(const or_mesh* m, long n_p, const double* rows, const or_params* P,
     /* eq. IEM with the element mean, or eq. IECM with the velocity-conditioned
      * mean of the particle's bin when cond is given */
     double pn = ps[p] - (ps[p] - (cond ? cond[p] : c[24])) * P->dt * c[25];
+    /* distances from the no-slip wall before and after the move (sec.
+     * no-slip wall-boundary conditions), for particles in elements with a
+     * node on such a wall */
+    const int near = m->nsw_flag[e];
+    double dn = 0.0, d1 = 0.0;
+    if (near) {
+      const double* L = m->nsw + 4 * e;
+      dn = (x[p] - L[0]) * L[2] + (y[p] - L[1]) * L[3];
+      d1 = (xn - L[0]) * L[2] + (yn - L[1]) * L[3];
+    }
     or_track_info ti;
     int en = or_track(m, e, &xn, &yn, &Un[0], &Un[1], &ti);
+    /* wall condition: trajectory (a), behind the wall after the move (the
+     * walk reflected the position at a no-slip edge, or d^{n+1} < 0), or
+     * trajectory (b), eta < f_w = exp(-d^n d^{n+1} / (nu dt)) (eq. fw,
+     * eq. exp-wall-condition); eta is the third word of the step's second
+     * random block.  Then U = 0 and omega from a Gamma distribution with
+     * the mean of eq. frequency-wallstats and variance C4 <omega>^2 (shape
+     * 1/C4 = 4): -<omega>/4 times the sum of the logarithms of the four
+     * uniforms of the step's third block. */
+    int wall = (ti.status & OR_TRK_NOSLIP) != 0;
+    if (near && !wall) {
+      if (d1 < 0.0) {
+        wall = 1;
+      } else {
+        uint32_t ctr[4] = {id, step, 1u, OR_PURPOSE_STEP}, key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)}, out[4];
+        or_philox(ctr, key, out);
+        const double eta = (double)or_u01(out[2]);
+        if (eta < exp(-dn * d1 / (P->nu * P->dt))) wall = 1;
+      }
+    }
+    if (wall) {
+      Un[0] = Un[1] = Un[2] = 0.0;
+      uint32_t ctr[4] = {id, step, 2u, OR_PURPOSE_STEP}, key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)}, out[4];
+      or_philox(ctr, key, out);
+      float lsum = or_logf(or_u01(out[0])) + or_logf(or_u01(out[1]));
+      lsum = lsum + or_logf(or_u01(out[2]));
+      lsum = lsum + or_logf(or_u01(out[3]));
+      const double mw = omega_wall ? omega_wall[e] : mo;
+      on = -0.25 * (mw > 0.0 ? mw : mo) * (double)lsum;
+      ti.status |= OR_TRK_NOSLIP;
+    }
     counters[0] += ti.walk_steps;
     counters[1] += ti.reflections;
     counters[2] += ti.crossings_periodic;
