@@ -48,8 +48,19 @@ typedef struct pdf_particles pdf_particles;
  * particles' positions (the canyon case of ch. 5 imposes only periodicity on
  * the streamwise positions); a particle leaving through an OUTFLOW edge
  * re-enters as fresh fluid (its scalar is set to 0).  Without twins they are
- * open boundaries and a particle crossing them is reported lost. */
-enum { PDF_TAG_WALL = 1, PDF_TAG_PERIODIC = 2, PDF_TAG_INFLOW = 3, PDF_TAG_OUTFLOW = 4 };
+ * open boundaries and a particle crossing them is reported lost.  WALL is a
+ * free-slip reflecting wall.  NOSLIP is a no-slip wall (the section on no-slip
+ * wall-boundary conditions): a particle in an element with a node on such a
+ * wall gets the wall condition when its move ends behind the wall line
+ * (trajectory (a): the position is reflected) or, staying in front of it,
+ * with probability f_w = exp(-d^n d^{n+1} / (nu dt)) (eq. fw, trajectory
+ * (b); eta = the third word of the step's second Philox block): U = 0 and
+ * omega drawn from a Gamma distribution of shape 1/C4 = 4 with the mean of
+ * eq. frequency-wallstats (from the third Philox block).  d is measured from
+ * the no-slip edge nearest to the element's centroid among those sharing a
+ * node with the element.  In the elliptic relaxation NOSLIP nodes take the
+ * Dirichlet condition wp_ij = -4.5 eps n_i n_j. */
+enum { PDF_TAG_WALL = 1, PDF_TAG_PERIODIC = 2, PDF_TAG_INFLOW = 3, PDF_TAG_OUTFLOW = 4, PDF_TAG_NOSLIP = 5 };
 
 /* Velocity closure.
  * GLM: generalized Langevin model, eq. Lagrangian-model with G_ij and C0 from
@@ -165,7 +176,8 @@ pdf_status pdf_mesh_create(const double* node_xy, int32_t n_nodes, const int32_t
 pdf_status pdf_mesh_destroy(pdf_mesh* m);
 /* Host copies of the connectivity (for checking): nbr [n_tri][3] neighbour
  * across the edge opposite local vertex k (>= 0 element, -1 wall, -3 inflow,
- * -4 outflow); shift [n_tri][3] periodic x-shift multiplier.  Either may be NULL. */
+ * -4 outflow, -5 no-slip wall); shift [n_tri][3] periodic x-shift
+ * multiplier.  Either may be NULL. */
 pdf_status pdf_mesh_connectivity(const pdf_mesh* m, int32_t* nbr, int32_t* shift);
 pdf_status pdf_mesh_size(const pdf_mesh* m, int32_t* n_nodes, int32_t* n_tri);
 

@@ -30,6 +30,7 @@ pdf_status cuda_fail(cudaError_t e, const char* what);
 constexpr int kNbrWall = -1;
 constexpr int kNbrInflow = -3;
 constexpr int kNbrOutflow = -4;
+constexpr int kNbrNoslip = -5;
 
 // Per-element data the neighbour walk reads: node B, the edge vectors
 // C - B and A - B, twice the area, and the three neighbours with their
@@ -42,6 +43,7 @@ struct __align__(16) ElemGeo {
   int32_t nbr[3];   // neighbour across the edge opposite A, B, C
   int8_t shift[3];  // periodic x-shift multipliers for those crossings
   uint8_t reinj;    // bit k: crossing edge k leaves through the outflow
+  int32_t nsw;      // 1: a node lies on a no-slip wall (nsw_line holds the wall)
 };
 static_assert(sizeof(ElemGeo) == 80, "ElemGeo layout");
 
@@ -53,6 +55,7 @@ struct __align__(16) FxGeo {
   int32_t nbr[3];
   int8_t shift[3];
   uint8_t reinj;
+  int32_t nsw;
 };
 static_assert(sizeof(FxGeo) == 80, "FxGeo layout");
 
@@ -83,6 +86,7 @@ struct MeshDev {
   int32_t* nse = nullptr;
   int32_t* esup_off = nullptr; // [n_nodes + 1] node -> elements holding the node
   int32_t* esup = nullptr;
+  double* nsw_line = nullptr;  // [n_tri][4] nearest no-slip wall edge: x_a, y_a, normal into the fluid
 };
 
 }  // namespace pdfgb

@@ -57,8 +57,8 @@ static pdf_status build_relax(pdf_mesh* m, const std::vector<int32_t>& bnd_wall,
     const double len = std::sqrt(tx * tx + ty * ty);
     double nx = ty / len, ny = -tx / len;
     // point away from the element holding the edge
-    for (int32_t i = esup_off[a]; i < esup_off[a + 1]; ++i) {
-      const int32_t e = esup[i];
+    for (int32_t q = esup_off[a]; q < esup_off[a + 1]; ++q) {
+      const int32_t e = esup[q];
       const int32_t* t = T + 3 * e;
       const bool ha = t[0] == a || t[1] == a || t[2] == a, hb = t[0] == b || t[1] == b || t[2] == b;
       if (!(ha && hb)) continue;
@@ -148,7 +148,7 @@ static pdf_status build_relax(pdf_mesh* m, const std::vector<int32_t>& bnd_wall,
 
 static void free_mesh_dev(MeshDev& d) {
   cudaFree(d.xy); cudaFree(d.tri); cudaFree(d.geo); cudaFree(d.fgeo); cudaFree(d.dN);
-  cudaFree(d.nse_off); cudaFree(d.nse); cudaFree(d.esup_off); cudaFree(d.esup);
+  cudaFree(d.nse_off); cudaFree(d.nse); cudaFree(d.esup_off); cudaFree(d.esup); cudaFree(d.nsw_line);
   d = MeshDev();
 }
 
@@ -243,6 +243,7 @@ extern "C" pdf_status pdf_mesh_create(const double* node_xy, int32_t n_nodes, co
       }
       switch (tag) {
         case PDF_TAG_WALL: m->nbr[3 * e + k] = kNbrWall; break;
+        case PDF_TAG_NOSLIP: m->nbr[3 * e + k] = kNbrNoslip; break;
         case PDF_TAG_INFLOW: m->nbr[3 * e + k] = kNbrInflow; break;
         case PDF_TAG_OUTFLOW: m->nbr[3 * e + k] = kNbrOutflow; break;
         case PDF_TAG_PERIODIC: {
@@ -265,6 +266,45 @@ extern "C" pdf_status pdf_mesh_create(const double* node_xy, int32_t n_nodes, co
       geo[e].shift[k] = (int8_t)m->shift[3 * e + k];
       if (m->reinj[3 * e + k]) geo[e].reinj |= (uint8_t)(1u << k);
     }
+  // no-slip walls: for an element with a node on a no-slip edge, the line of
+  // the nearest such edge (from the element's centroid; ties: the first in
+  // the order elements, edges, edge ends, elements around the end) with its
+  // normal into the fluid
+  std::vector<double> nsw_line(4 * (size_t)n_tri, 0.0);
+  {
+    std::vector<int32_t> esu_off(n_nodes + 1, 0), esu(3 * (size_t)n_tri);
+    for (int32_t i = 0; i < 3 * n_tri; ++i) esu_off[T[i] + 1]++;
+    for (int32_t n = 0; n < n_nodes; ++n) esu_off[n + 1] += esu_off[n];
+    std::vector<int32_t> fill(esu_off.begin(), esu_off.end() - 1);
+    for (int32_t e = 0; e < n_tri; ++e)
+      for (int k = 0; k < 3; ++k) esu[fill[T[3 * e + k]]++] = e;
+    std::vector<double> best(n_tri, INFINITY);
+    for (int32_t f = 0; f < n_tri; ++f)
+      for (int k = 0; k < 3; ++k) {
+        if (m->nbr[3 * f + k] != kNbrNoslip) continue;
+        const int32_t a = T[3 * f + (k + 1) % 3], b = T[3 * f + (k + 2) % 3];
+        const double xa = X[2 * a], ya = X[2 * a + 1], tx = X[2 * b] - xa, ty = X[2 * b + 1] - ya;
+        const double len = std::sqrt(tx * tx + ty * ty);
+        const double nx = -ty / len, ny = tx / len;
+        const int32_t ends[2] = {a, b};
+        for (int q = 0; q < 2; ++q)
+          for (int32_t i = esu_off[ends[q]]; i < esu_off[ends[q] + 1]; ++i) {
+            const int32_t e = esu[i];
+            const int32_t* t = T + 3 * e;
+            const double cx = (X[2 * t[0]] + X[2 * t[1]] + X[2 * t[2]]) / 3.0;
+            const double cy = (X[2 * t[0] + 1] + X[2 * t[1] + 1] + X[2 * t[2] + 1]) / 3.0;
+            double sp = ((cx - xa) * tx + (cy - ya) * ty) / (len * len);
+            sp = std::min(1.0, std::max(0.0, sp));
+            const double dx = cx - (xa + sp * tx), dy = cy - (ya + sp * ty);
+            const double dist = std::sqrt(dx * dx + dy * dy);
+            if (dist < best[e]) {
+              best[e] = dist;
+              geo[e].nsw = 1;
+              nsw_line[4 * e] = xa; nsw_line[4 * e + 1] = ya; nsw_line[4 * e + 2] = nx; nsw_line[4 * e + 3] = ny;
+            }
+          }
+      }
+  }
   // the fixed-point copy for the FP64-free walk
   std::vector<FxGeo> fgeo(n_tri);
   auto bits = [](double v) { uint64_t b; std::memcpy(&b, &v, 8); return b; };
@@ -279,6 +319,7 @@ extern "C" pdf_status pdf_mesh_create(const double* node_xy, int32_t n_nodes, co
     f.two_area = fx::d2df(bits(g.two_area));
     for (int k = 0; k < 3; ++k) { f.nbr[k] = g.nbr[k]; f.shift[k] = g.shift[k]; }
     f.reinj = g.reinj;
+    f.nsw = g.nsw;
     if (std::fabs(g.xb) >= 63.0 || std::fabs(g.yb) >= 63.0) {
       delete m;
       return fail(PDF_EINVAL, "pdf_mesh_create: node coordinates must lie within |x|, |y| < 63");
@@ -314,7 +355,10 @@ extern "C" pdf_status pdf_mesh_create(const double* node_xy, int32_t n_nodes, co
   pdf_status s;
   std::vector<int32_t> bnd_wall;
   for (int32_t i = 0; i < n_bnd; ++i)
-    if (bnd_edge[3 * i + 2] == PDF_TAG_WALL) { bnd_wall.push_back(bnd_edge[3 * i]); bnd_wall.push_back(bnd_edge[3 * i + 1]); }
+    if (bnd_edge[3 * i + 2] == PDF_TAG_WALL || bnd_edge[3 * i + 2] == PDF_TAG_NOSLIP) {
+      bnd_wall.push_back(bnd_edge[3 * i]);
+      bnd_wall.push_back(bnd_edge[3 * i + 1]);
+    }
   if ((s = upload(&d.xy, m->xy.data(), m->xy.size())) != PDF_OK ||
       (s = upload(&d.tri, m->tri.data(), m->tri.size())) != PDF_OK ||
       (s = upload(&d.geo, geo.data(), geo.size())) != PDF_OK ||
@@ -323,7 +367,8 @@ extern "C" pdf_status pdf_mesh_create(const double* node_xy, int32_t n_nodes, co
       (s = upload(&d.nse_off, nse_off.data(), nse_off.size())) != PDF_OK ||
       (s = upload(&d.nse, nse.data(), nse.size())) != PDF_OK ||
       (s = upload(&d.esup_off, esup_off.data(), esup_off.size())) != PDF_OK ||
-      (s = upload(&d.esup, esup.data(), esup.size())) != PDF_OK) {
+      (s = upload(&d.esup, esup.data(), esup.size())) != PDF_OK ||
+      (s = upload(&d.nsw_line, nsw_line.data(), nsw_line.size())) != PDF_OK) {
     free_mesh_dev(d);
     delete m;
     return s;

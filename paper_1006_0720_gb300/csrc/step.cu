@@ -165,9 +165,29 @@ __device__ __forceinline__ void make_fx_row(const double* r, FxRow* out) {
   *out = f;
 }
 
+// Mean of the frequency given to a particle striking a no-slip wall (eq.
+// frequency-wallstats): (1/C_T) d sqrt(2k)/dn into the fluid from the
+// element gradient of the nodal sqrt(2k) = sqrt(<uu> + <vv> + <ww>); where that
+// is not positive, the element average of the nodal <omega>.
+__device__ __forceinline__ double noslip_omega(int32_t e, const int32_t* tri, const double* ns, const double* dN,
+                                               const double* L, double CT) {
+  const double* d = dN + (int64_t)e * 6;
+  double g = 0.0, om = 0.0;
+  for (int j = 0; j < 3; ++j) {
+    const double* S = ns + (int64_t)tri[3 * e + j] * PDF_NNS;
+    const double kk = S[5] + S[6] + S[7];
+    g += sqrt(kk > 0.0 ? kk : 0.0) * (d[j] * L[2] + d[3 + j] * L[3]);
+    om += S[3];
+  }
+  const double w = g / CT;
+  return w > 0.0 ? w : om / 3.0;
+}
+
 __global__ void k_elem_rows(const int32_t* __restrict__ tri, int32_t n_tri, const double* __restrict__ nc,
                             CoeffParams P, double* __restrict__ rows, double* __restrict__ avg_out,
-                            FxRow* __restrict__ rows_fx, float* __restrict__ rows_f32) {
+                            FxRow* __restrict__ rows_fx, float* __restrict__ rows_f32,
+                            const ElemGeo* __restrict__ geo, const double* __restrict__ nsw_line,
+                            const double* __restrict__ ns, const double* __restrict__ dN) {
   for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n_tri; e += gridDim.x * blockDim.x) {
     const double* c0 = nc + (int64_t)tri[3 * e] * PDF_NCOEF;
     const double* c1 = nc + (int64_t)tri[3 * e + 1] * PDF_NCOEF;
@@ -179,6 +199,8 @@ __global__ void k_elem_rows(const int32_t* __restrict__ tri, int32_t n_tri, cons
     if (rows || rows_fx || rows_f32) {
       double r[PDFGB_ROW];
       scale_row(a, P, r);
+      // r[28]: the no-slip wall frequency of elements next to a no-slip wall
+      if (geo[e].nsw) r[28] = noslip_omega(e, tri, ns, dN, nsw_line + 4 * (int64_t)e, P.CT);
       if (rows)
         for (int q = 0; q < PDFGB_ROW; ++q) rows[(int64_t)e * PDFGB_ROW + q] = r[q];
       if (rows_fx) make_fx_row(r, rows_fx + e);
@@ -226,6 +248,8 @@ struct StepArgs {
   uint32_t step;
   long long* counters;
   double src_x, src_y, src_r;  // concentrated source (src_r > 0)
+  const double* nsw_line;      // [n_tri][4] nearest no-slip wall of flagged elements
+  double nu;                   // kinematic viscosity (no-slip crossing probability)
 };
 
 enum { kCntWalk = 0, kCntRefl, kCntPeriodic, kCntFallback, kCntBrute, kCntLost, kCntOmega, kCntNear };
@@ -257,6 +281,7 @@ __device__ __forceinline__ ElemGeo load_geo(const ElemGeo* geo, int32_t e) {
   g.shift[1] = (int8_t)((sh >> 8) & 0xff);
   g.shift[2] = (int8_t)((sh >> 16) & 0xff);
   g.reinj = (uint8_t)((sh >> 24) & 0xff);
+  g.nsw = d.z;
   return g;
 }
 
@@ -265,7 +290,7 @@ __device__ __forceinline__ ElemGeo load_geo(const ElemGeo* geo, int32_t e) {
 // (wall-normal component reversed on reflection).
 __device__ int32_t walk(const StepArgs& A, int32_t e, double& x, double& y, double& u, double& v,
                         int& c_walk, int& c_refl, int& c_per, int& c_fb, int& c_brute, int& c_near,
-                        bool& reinj) {
+                        bool& reinj, bool& noslip) {
   int steps = 0, refl = 0;
   for (;;) {
     ElemGeo g = load_geo(A.geo, e);
@@ -337,9 +362,13 @@ __device__ int32_t walk(const StepArgs& A, int32_t e, double& x, double& y, doub
     const double d = (x - xa) * nx + (y - ya) * ny;
     x = x - 2.0 * d * nx;
     y = y - 2.0 * d * ny;
-    const double un = u * nx + v * ny;
-    u = u - 2.0 * un * nx;
-    v = v - 2.0 * un * ny;
+    if (nbr == kNbrNoslip) {
+      noslip = true;  // the wall condition resets the velocity
+    } else {
+      const double un = u * nx + v * ny;
+      u = u - 2.0 * un * nx;
+      v = v - 2.0 * un * ny;
+    }
     ++refl;
     ++c_refl;
   }
@@ -383,16 +412,61 @@ __device__ __forceinline__ Draws draw_step(const StepArgs& A, int64_t slot) {
   return d;
 }
 
-// One particle in native FP64 instructions (PDF_ARITH_FP64, and the
-// fall-back of the fixed-point kernel for large moves).  The stored forms are
-// widened to FP64 on load and rounded back on store; a particle that is lost,
-// or whose new position leaves |x|, |y| < 64, keeps its position and element.
-__device__ __forceinline__ Counts advance_native(const StepArgs& A, int64_t p, const Draws D) {
+// Frequency of a particle striking a no-slip wall (eq. frequency-wallstats):
+// Gamma of shape 1/C4 = 4 and mean mw, -mw/4 times the sum of the logarithms
+// of the four uniforms of the step's third Philox block (the same FP32
+// logarithm as the initial Gamma(4) draw).
+__device__ __noinline__ double wall_frequency(uint64_t seed, uint32_t id, uint32_t step, double mw) {
+  uint32_t c[4] = {id, step, 2u, kPurposeStep};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  float lsum = __fadd_rn(ln_unit(u01_from_word(c[0])), ln_unit(u01_from_word(c[1])));
+  lsum = __fadd_rn(lsum, ln_unit(u01_from_word(c[2])));
+  lsum = __fadd_rn(lsum, ln_unit(u01_from_word(c[3])));
+  return __dmul_rn(__dmul_rn(-0.25, mw), (double)lsum);
+}
+
+// eta of trajectory (b): the third word of the step's second Philox block.
+__device__ __forceinline__ double wall_eta(uint64_t seed, uint32_t id, uint32_t step) {
+  uint32_t c[4] = {id, step, 1u, kPurposeStep};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  return (double)u01_from_word(c[2]);
+}
+
+// The stored forms of u, v, w, omega, psi, read as and written from FP64.
+struct DfIO {
+  fx::df *u, *v, *w, *om, *ps;
+  __device__ void load(int64_t p, double& U0, double& U1, double& U2, double& o, double& s) const {
+    U0 = fx::to_double(u[p]); U1 = fx::to_double(v[p]); U2 = fx::to_double(w[p]);
+    o = fx::to_double(om[p]); s = fx::to_double(ps[p]);
+  }
+  __device__ void store(int64_t p, double U0, double U1, double U2, double o, double s) const {
+    u[p] = fx::from_double(U0); v[p] = fx::from_double(U1); w[p] = fx::from_double(U2);
+    om[p] = fx::from_double(o); ps[p] = fx::from_double(s);
+  }
+};
+struct F32IO {
+  float *u, *v, *w, *om, *ps;
+  __device__ void load(int64_t p, double& U0, double& U1, double& U2, double& o, double& s) const {
+    U0 = u[p]; U1 = v[p]; U2 = w[p]; o = om[p]; s = ps[p];
+  }
+  __device__ void store(int64_t p, double U0, double U1, double U2, double o, double s) const {
+    u[p] = (float)U0; v[p] = (float)U1; w[p] = (float)U2; om[p] = (float)o; ps[p] = (float)s;
+  }
+};
+
+// One particle in native FP64 instructions (PDF_ARITH_FP64, the fall-back
+// of the fixed-point kernels for large moves, and every particle next to a
+// no-slip wall).  The stored forms are widened to FP64 on load and rounded
+// back on store; a particle that is lost, or whose new position leaves
+// |x|, |y| < 64, keeps its position and element.
+template <typename IO>
+__device__ __forceinline__ Counts advance_native(const StepArgs& A, const IO& io, int64_t p, const Draws D) {
   Counts c;
   const float* g = D.g;
   const int32_t e = A.elem[p];
   const double* R = A.rows + (int64_t)e * PDFGB_ROW;
-  const double U0 = fx::to_double(A.u[p]), U1 = fx::to_double(A.v[p]), U2 = fx::to_double(A.w[p]);
+  double U0, U1, U2, o, s;
+  io.load(p, U0, U1, U2, o, s);
   const double gx = (double)g[0], gy = (double)g[1];
   const double d0 = U0 - __ldg(R + 0), d1 = U1 - __ldg(R + 1), d2 = U2 - __ldg(R + 2);
   const double G0 = (double)g[2], G1 = (double)g[3], G2 = (double)g[4];
@@ -402,43 +476,61 @@ __device__ __forceinline__ Counts advance_native(const StepArgs& A, int64_t p, c
               __ldg(R + 12) * d0 + __ldg(R + 13) * d1 + __ldg(R + 14) * d2 + b * G0;
   double vn = U1 + __ldg(R + 10) + __ldg(R + 5) * gx + __ldg(R + 6) * gy +
               __ldg(R + 15) * d0 + __ldg(R + 16) * d1 + __ldg(R + 17) * d2 + b * G1;
-  const double wn = U2 + __ldg(R + 11) + __ldg(R + 7) * gx + __ldg(R + 8) * gy +
-                    __ldg(R + 18) * d0 + __ldg(R + 19) * d1 + __ldg(R + 20) * d2 + b * G2;
+  double wn = U2 + __ldg(R + 11) + __ldg(R + 7) * gx + __ldg(R + 8) * gy +
+              __ldg(R + 18) * d0 + __ldg(R + 19) * d1 + __ldg(R + 20) * d2 + b * G2;
   // position (eq. Lagrangian-position-exact) with the same dW_x, dW_y
-  double xn = __longlong_as_double((long long)fx::fix2d(A.x[p], kPosF)) + U0 * A.dt + A.sdiff * gx;
-  double yn = __longlong_as_double((long long)fx::fix2d(A.y[p], kPosF)) + U1 * A.dt + A.sdiff * gy;
+  const double x0 = __longlong_as_double((long long)fx::fix2d(A.x[p], kPosF));
+  const double y0 = __longlong_as_double((long long)fx::fix2d(A.y[p], kPosF));
+  double xn = x0 + U0 * A.dt + A.sdiff * gx;
+  double yn = y0 + U1 * A.dt + A.sdiff * gy;
   // frequency (eq. frequency-model); a negative result is reflected
-  const double o = fx::to_double(A.om[p]);
   double on = o - __ldg(R + 23) * o + __ldg(R + 24) + __ldg(R + 25) * sqrt(fmax(o, 0.0)) * (double)g[5];
   if (on < 0.0) { on = -on; ++c.om; }
-  // scalar (eq. IEM)
-  const double s = fx::to_double(A.ps[p]);
-  // eq. IEM (element mean) or eq. IECM (the particle's conditional mean)
+  // scalar: eq. IEM (element mean) or eq. IECM (the particle's conditional mean)
   const double tgt = A.cond ? fx::to_double(A.cond[p]) : __ldg(R + 26);
   const double sn = s - (s - tgt) * __ldg(R + 27);
-  bool reinj = false;
-  const int32_t en = walk(A, e, xn, yn, un, vn, c.walk, c.refl, c.per, c.fb, c.brute, c.near, reinj);
+  // distances from the no-slip wall before and after the move
+  const bool near = load_geo(A.geo, e).nsw != 0;
+  double dn = 0.0, d1w = 0.0;
+  if (near) {
+    const double* L = A.nsw_line + 4 * (int64_t)e;
+    dn = (x0 - L[0]) * L[2] + (y0 - L[1]) * L[3];
+    d1w = (xn - L[0]) * L[2] + (yn - L[1]) * L[3];
+  }
+  bool reinj = false, wall = false;
+  const int32_t en = walk(A, e, xn, yn, un, vn, c.walk, c.refl, c.per, c.fb, c.brute, c.near, reinj, wall);
+  // no-slip wall condition: trajectory (a) (reflected at a no-slip edge, or
+  // behind the wall line) or (b) (eta < f_w, eq. fw): U = 0, omega ~ Gamma
+  if (near && !wall) wall = d1w < 0.0 || wall_eta(A.seed, (uint32_t)__ldg(A.pid + p), A.step) <
+                                          exp(-dn * d1w / (A.nu * A.dt));
+  if (wall) {
+    un = vn = wn = 0.0;
+    const double mw = __ldg(R + 28) > 0.0 ? __ldg(R + 28) : __ldg(R + 22);
+    on = wall_frequency(A.seed, (uint32_t)__ldg(A.pid + p), A.step, mw);
+  }
   if (en >= 0 && fabs(xn) < 64.0 && fabs(yn) < 64.0) {
     A.x[p] = fx::d2fix((uint64_t)__double_as_longlong(xn), kPosF);
     A.y[p] = fx::d2fix((uint64_t)__double_as_longlong(yn), kPosF);
     A.elem[p] = en;
   } else {
     ++c.lost;
-    xn = __longlong_as_double((long long)fx::fix2d(A.x[p], kPosF));
-    yn = __longlong_as_double((long long)fx::fix2d(A.y[p], kPosF));
+    xn = x0;
+    yn = y0;
   }
   double sf = reinj ? 0.0 : sn;
   if (in_source(A, xn, yn)) sf = 1.0;
-  A.u[p] = fx::from_double(un); A.v[p] = fx::from_double(vn); A.w[p] = fx::from_double(wn);
-  A.om[p] = fx::from_double(on); A.ps[p] = fx::from_double(sf);
+  io.store(p, un, vn, wn, on, sf);
   return c;
 }
 
-// The same, out of line for the fixed-point kernels' rare fall-back.  All
+// The same, out of line for the fixed-point kernels' rare fall-backs.  All
 // arguments by value, so that no variable of the caller has its address
 // taken (which would keep it in local memory for its whole life).
 __device__ __noinline__ Counts advance_native_ool(const StepArgs A, int64_t p, const Draws D) {
-  return advance_native(A, p, D);
+  return advance_native(A, DfIO{A.u, A.v, A.w, A.om, A.ps}, p, D);
+}
+__device__ __noinline__ Counts advance_native_f32_ool(const StepArgs A, const F32IO io, int64_t p, const Draws D) {
+  return advance_native(A, io, p, D);
 }
 
 __device__ __forceinline__ void merge(Counts& a, const Counts& b) {
@@ -465,7 +557,7 @@ __global__ void __launch_bounds__(256) k_step(StepArgs A) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   for (int64_t it = 0; it < iters; ++it, p += stride) {
     if (p >= A.n) continue;
-    merge(c, advance_native(A, p, draw_step(A, p)));
+    merge(c, advance_native(A, DfIO{A.u, A.v, A.w, A.om, A.ps}, p, draw_step(A, p)));
   }
   flush_counts(A, c);
 }
@@ -706,12 +798,14 @@ struct SlowWalk {
   double x, y, u, v;
   Counts c;
   bool reinj;
+  bool noslip;  // reflected at a no-slip wall
 };
 
 __device__ __noinline__ SlowWalk walk_slow(const StepArgs A, int32_t e, double x, double y, double u, double v) {
   SlowWalk r;
   r.reinj = false;
-  r.e = walk(A, e, x, y, u, v, r.c.walk, r.c.refl, r.c.per, r.c.fb, r.c.brute, r.c.near, r.reinj);
+  r.noslip = false;
+  r.e = walk(A, e, x, y, u, v, r.c.walk, r.c.refl, r.c.per, r.c.fb, r.c.brute, r.c.near, r.reinj, r.noslip);
   r.x = x;
   r.y = y;
   r.u = u;
@@ -764,7 +858,8 @@ __global__ void __launch_bounds__(256, 4) k_step_fx(StepArgs A, FxArgs F) {
     ax.add(fx::mul_f(F.sdiff, D.g[0]));
     ay.init(fx::mul(U[1], F.dt));
     ay.add(fx::mul_f(F.sdiff, D.g[1]));
-    if (!(small_move(ax) && small_move(ay))) {
+    // large moves and particles next to a no-slip wall go to the FP64 path
+    if (!(small_move(ax) && small_move(ay)) || __ldg(reinterpret_cast<const int*>(F.geo + e) + 18) != 0) {
       merge(cs, advance_native_ool(A, p, D));
       continue;
     }
@@ -820,6 +915,7 @@ __global__ void __launch_bounds__(256, 4) k_step_fx(StepArgs A, FxArgs F) {
     const bool slow = walk_fx(F, e, Xn, Yn, steps, c_per, c_near, reinj);
     c_walk += steps;
     int64_t Xs = Xn, Ys = Yn;
+    bool slow_noslip = false;
     if (slow) {
       double xn = __longlong_as_double((long long)fx::fix2d(Xn, kF));
       double yn = __longlong_as_double((long long)fx::fix2d(Yn, kF));
@@ -827,6 +923,12 @@ __global__ void __launch_bounds__(256, 4) k_step_fx(StepArgs A, FxArgs F) {
       const SlowWalk sw = walk_slow(A, e, xn, yn, un, vn);
       merge(cs, sw.c);
       if (sw.reinj) reinj = true;
+      if (sw.noslip) {  // no-slip wall reached through other elements: the wall condition
+        const double* Rd = A.rows + (int64_t)A.elem[p] * PDFGB_ROW;
+        const double mw = __ldg(Rd + 28) > 0.0 ? __ldg(Rd + 28) : __ldg(Rd + 22);
+        On = fx::from_double(wall_frequency(A.seed, (uint32_t)__ldg(A.pid + p), A.step, mw));
+        slow_noslip = true;
+      }
       if (sw.e >= 0 && pos_fits(sw.x) && pos_fits(sw.y)) {
         e = sw.e;
         Xs = fx::d2fix((uint64_t)__double_as_longlong(sw.x), kF);
@@ -842,6 +944,7 @@ __global__ void __launch_bounds__(256, 4) k_step_fx(StepArgs A, FxArgs F) {
     }
     if (reinj) Sn = fx::df{0.f, 0.f};
     if (in_source_fx(A, F, Xs, Ys)) Sn = fx::df{1.f, 0.f};
+    if (slow_noslip) Un[0] = Un[1] = Un[2] = fx::df{0.f, 0.f};
     A.x[p] = Xs;
     A.y[p] = Ys;
     st_state(A.u, p, Un[0]);
@@ -883,7 +986,7 @@ __global__ void __launch_bounds__(256, 4) k_step_f32(StepArgs A, FxArgs F, F32Ar
                __ldg(R + 13) * d1 + __ldg(R + 14) * d2 + b * D.g[2];
     float vn = U1 + __ldg(R + 10) + __ldg(R + 5) * D.g[0] + __ldg(R + 6) * D.g[1] + __ldg(R + 15) * d0 +
                __ldg(R + 16) * d1 + __ldg(R + 17) * d2 + b * D.g[3];
-    const float wn = U2 + __ldg(R + 11) + __ldg(R + 7) * D.g[0] + __ldg(R + 8) * D.g[1] + __ldg(R + 18) * d0 +
+    float wn = U2 + __ldg(R + 11) + __ldg(R + 7) * D.g[0] + __ldg(R + 8) * D.g[1] + __ldg(R + 18) * d0 +
                      __ldg(R + 19) * d1 + __ldg(R + 20) * d2 + b * D.g[4];
     // frequency (eq. frequency-model) and scalar (eq. IEM) in FP32
     const float o = S.om[p];
@@ -891,6 +994,11 @@ __global__ void __launch_bounds__(256, 4) k_step_f32(StepArgs A, FxArgs F, F32Ar
     if (on < 0.f) { on = -on; ++c_om; }
     const float s = S.ps[p];
     const float sn = s - (s - (A.cond ? A.cond[p].h : __ldg(R + 26))) * __ldg(R + 27);
+    // particles next to a no-slip wall go to the FP64 path
+    if (__ldg(reinterpret_cast<const int*>(F.geo + e) + 18) != 0) {
+      merge(cs, advance_native_f32_ool(A, F32IO{S.u, S.v, S.w, S.om, S.ps}, p, D));
+      continue;
+    }
     // position (eq. Lagrangian-position-exact), fixed point
     const int64_t X0 = A.x[p], Y0 = A.y[p];
     fx::acc a;
@@ -915,11 +1023,19 @@ __global__ void __launch_bounds__(256, 4) k_step_f32(StepArgs A, FxArgs F, F32Ar
       yn = __longlong_as_double((long long)fx::fix2d(Y0, kF)) + (double)U1 * A.dt + A.sdiff * (double)D.g[1];
       slow = true;
     }
+    bool slow_noslip = false;
     if (slow) {
       double ud = (double)un, vd = (double)vn;
       const SlowWalk sw = walk_slow(A, e, xn, yn, ud, vd);
       merge(cs, sw.c);
       if (sw.reinj) reinj = true;
+      if (sw.noslip) {  // no-slip wall reached through other elements: the wall condition
+        const double* Rd = A.rows + (int64_t)A.elem[p] * PDFGB_ROW;
+        const double mw = __ldg(Rd + 28) > 0.0 ? __ldg(Rd + 28) : __ldg(Rd + 22);
+        on = (float)wall_frequency(A.seed, (uint32_t)__ldg(A.pid + p), A.step, mw);
+        wn = 0.0f;
+        slow_noslip = true;
+      }
       if (sw.e >= 0 && pos_fits(sw.x) && pos_fits(sw.y)) {
         e = sw.e;
         xn = sw.x;
@@ -935,6 +1051,7 @@ __global__ void __launch_bounds__(256, 4) k_step_f32(StepArgs A, FxArgs F, F32Ar
         Yn = Y0;
       }
     }
+    if (slow_noslip) un = vn = wn = 0.0f;
     float sf = reinj ? 0.0f : sn;
     if (in_source_fx(A, F, Xn, Yn)) sf = 1.0f;
     A.x[p] = Xn;
@@ -986,7 +1103,8 @@ static pdf_status build_rows(pdf_particles* P, const pdf_model_params* params, c
   PDF_KERNEL("k_elem_rows", st, k_elem_rows<<<blocks_for(M.n_tri, 128, 32), 128, 0, st>>>(M.tri, M.n_tri, P->nc, C,
                                                              internal ? P->rows : nullptr, avg_out,
                                                              internal && C.arith == PDF_ARITH_FX ? P->rows_fx : nullptr,
-                                                             internal ? P->rows_f32 : nullptr););
+                                                             internal ? P->rows_f32 : nullptr, M.geo, M.nsw_line,
+                                                             P->ns, M.dN););
   return PDF_OK;
 }
 
@@ -1040,6 +1158,8 @@ extern "C" pdf_status pdf_step(pdf_particles* p, const pdf_mesh* m, const pdf_mo
   A.seed = p->seed;
   A.step = step;
   A.counters = p->counters;
+  A.nsw_line = M.nsw_line;
+  A.nu = params->nu;
   A.src_x = params->src_x;
   A.src_y = params->src_y;
   A.src_r = params->src_r;
