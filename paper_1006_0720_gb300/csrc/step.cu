@@ -858,8 +858,11 @@ __global__ void __launch_bounds__(256, 4) k_step_fx(StepArgs A, FxArgs F) {
     ax.add(fx::mul_f(F.sdiff, D.g[0]));
     ay.init(fx::mul(U[1], F.dt));
     ay.add(fx::mul_f(F.sdiff, D.g[1]));
-    // large moves and particles next to a no-slip wall go to the FP64 path
-    if (!(small_move(ax) && small_move(ay)) || __ldg(reinterpret_cast<const int*>(F.geo + e) + 18) != 0) {
+    // large moves go to the FP64 path; so do particles next to a no-slip
+    // wall (the flag is loaded here and tested after the SDE updates, so
+    // that its latency is hidden)
+    const int near_noslip = __ldg(reinterpret_cast<const int*>(F.geo + e) + 18);
+    if (!(small_move(ax) && small_move(ay))) {
       merge(cs, advance_native_ool(A, p, D));
       continue;
     }
@@ -907,6 +910,10 @@ __global__ void __launch_bounds__(256, 4) k_step_fx(StepArgs A, FxArgs F) {
       a.init(S);
       a.sub(fx::mul(ldc(R, 22), dsub(S, A.cond ? ld_state(A.cond, p) : ldmean(R, 3))));
       Sn = a.value();
+    }
+    if (near_noslip) {
+      merge(cs, advance_native_ool(A, p, D));
+      continue;
     }
     // neighbour walk (sec. 3.5) in fixed point; walls, open boundaries and
     // the step cap go to the FP64 walk
