@@ -13,6 +13,10 @@ READINGS (the paper only says "P1 FEM, Jacobi-PCG, warm start"):
   * reflecting walls are symmetry planes (as the channel centreline, sec.
     4.2.1): off-diagonal components Dirichlet 0 at wall nodes, diagonal
     components natural (Neumann) conditions;
+  * no-slip walls take the Dirichlet condition wp_ij = -4.5 eps n_i n_j for
+    every component (the section on no-slip wall-boundary conditions), eps of
+    eq. dissipation-from-frequency_wall at the node; a node on both kinds of
+    wall is a no-slip node;
   * C_xi = 1 + 1.3 n_i n_i for wp_ii, 1 for off-diagonal components, n the
     unit outward normal of the nearest wall edge;
   * periodic twin nodes are one unknown.
@@ -31,10 +35,11 @@ KFLOOR = EFLOOR = 1e-12
 
 def wall_normals(mesh):
     """Per node: distance to the nearest wall edge and that edge's unit
-    outward normal (nx, ny).  Wall edges are the boundary edges tagged WALL."""
+    outward normal (nx, ny).  Wall edges are the boundary edges tagged WALL
+    or NOSLIP."""
     xy = mesh["xy"]
     bnd = mesh["bnd"]
-    walls = bnd[bnd[:, 2] == 1]
+    walls = bnd[(bnd[:, 2] == 1) | (bnd[:, 2] == 5)]
     a = xy[walls[:, 0]]
     b = xy[walls[:, 1]]
     # outward normal: the wall edge belongs to one triangle; the normal points
@@ -109,10 +114,21 @@ def assemble(mesh, L2_node):
     return M, K
 
 
-def wall_nodes(mesh):
+def wall_nodes(mesh, tag=1):
     bnd = mesh["bnd"]
-    w = bnd[bnd[:, 2] == 1]
+    w = bnd[bnd[:, 2] == tag]
+    if len(w) == 0:
+        return np.zeros(0, dtype=np.int64)
     return np.unique(np.concatenate([w[:, 0], w[:, 1]]))
+
+
+def noslip_values(S, nu, nrm):
+    """Dirichlet values -4.5 eps n_i n_j [9, n] at every node."""
+    k = np.maximum(0.5 * (S[:, 5] + S[:, 6] + S[:, 7]), KFLOOR)
+    om = S[:, 3]
+    eps = np.maximum(om * (k + nu * CT * CT * om), EFLOOR)
+    n3 = np.stack([nrm[:, 0], nrm[:, 1], np.zeros(len(nrm))], axis=1)
+    return np.stack([-4.5 * eps * n3[:, i] * n3[:, j] for i in range(3) for j in range(3)])
 
 
 def solve(mesh, S, rhs, nu):
@@ -122,10 +138,11 @@ def solve(mesh, S, rhs, nu):
     rep = _rep(mesh)
     is_rep = rep == np.arange(n)
     _, nrm = wall_normals(mesh)
-    walls = wall_nodes(mesh)
-    wall_rep = np.unique(rep[walls])
+    noslip_rep = np.unique(rep[wall_nodes(mesh, 5)])
+    free_rep = np.setdiff1d(np.unique(rep[wall_nodes(mesh, 1)]), noslip_rep)
+    gval = noslip_values(S, nu, nrm)
     out = np.zeros((9, n))
-    cache = {}
+    idx = np.nonzero(is_rep)[0]
     for ij in range(9):
         i, j = divmod(ij, 3)
         if i == j:
@@ -133,30 +150,18 @@ def solve(mesh, S, rhs, nu):
             cxi = 1.0 + 1.3 * ni * ni
         else:
             cxi = np.ones(n)
-        key = (tuple(np.round(cxi, 12)), i == j)
-        if key not in cache:
-            M, K = assemble(mesh, lengthscale2(S, nu, cxi))
-            A = (M + K).tolil()
-            if i != j:
-                for r in wall_rep:
-                    A.rows[r] = [r]
-                    A.data[r] = [1.0]
-                A = A.tocsr()
-                # symmetric elimination: zero the Dirichlet columns (value 0)
-                mask = np.ones(n)
-                mask[wall_rep] = 0.0
-                D = sp.diags(mask)
-                A = (D @ A @ D + sp.diags(1.0 - mask)).tocsr()
-            else:
-                A = A.tocsr()
-            # unknowns: representative nodes only
-            idx = np.nonzero(is_rep)[0]
-            cache[key] = (A[idx][:, idx].tocsc(), M, idx)
-        A, M, idx = cache[key]
-        b = M @ rhs[ij]
-        if i != j:
-            b[wall_rep] = 0.0
-        x = spla.spsolve(A, b[idx])
+        M, K = assemble(mesh, lengthscale2(S, nu, cxi))
+        A = (M + K).tocsr()
+        fixed = noslip_rep if i == j else np.union1d(free_rep, noslip_rep)
+        g = np.zeros(n)
+        g[noslip_rep] = gval[ij][noslip_rep]
+        b = M @ rhs[ij] - A @ g          # lift the Dirichlet values
+        b[fixed] = g[fixed]
+        mask = np.ones(n)
+        mask[fixed] = 0.0
+        D = sp.diags(mask)
+        A = (D @ A @ D + sp.diags(1.0 - mask)).tocsr()
+        x = spla.spsolve(A[idx][:, idx].tocsc(), b[idx])
         full = np.zeros(n)
         full[idx] = x
         out[ij] = full[rep]

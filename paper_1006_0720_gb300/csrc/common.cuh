@@ -102,7 +102,7 @@ struct RelaxMesh {
   int32_t* ctb_off = nullptr;   // [nnz + 1] stiffness contributions per entry
   int32_t* ctb_e = nullptr;     //   element
   double* ctb_k = nullptr;      //   A_e grad N_a . grad N_b
-  uint8_t* wall = nullptr;      // [n_rep] unknown on a wall
+  uint8_t* wall = nullptr;      // [n_rep] 1: free-slip wall node, 2: no-slip wall node
   int32_t* rep_node = nullptr;  // [n_rep] node id of each unknown
   int32_t* node_rep = nullptr;  // [n_nodes] unknown of each node
   double* wall_n = nullptr;     // [n_nodes][2] outward normal of the nearest wall edge
@@ -110,7 +110,7 @@ struct RelaxMesh {
 };
 struct RelaxWork {
   int32_t nb = 0;
-  double *f = nullptr, *L2 = nullptr, *aval = nullptr, *diag = nullptr;
+  double *f = nullptr, *L2 = nullptr, *aval = nullptr, *diag = nullptr, *g = nullptr;
   double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
   double *part = nullptr, *scal = nullptr, *beta = nullptr, *host = nullptr;
   int32_t* active = nullptr;

@@ -31,7 +31,8 @@ static void free_relax(RelaxMesh& r) {
 // The relaxation system's structure: unknowns (twins merged), CSR pattern,
 // consistent mass, per-entry stiffness contributions (element order), wall
 // flags and the outward normal of the nearest wall edge at every node.
-static pdf_status build_relax(pdf_mesh* m, const std::vector<int32_t>& bnd_wall, const std::vector<double>& dN,
+static pdf_status build_relax(pdf_mesh* m, const std::vector<int32_t>& bnd_wall, const std::vector<int32_t>& wall_tag,
+                              const std::vector<double>& dN,
                               const std::vector<int32_t>& nse_off, const std::vector<int32_t>& nse,
                               const std::vector<int32_t>& esup_off, const std::vector<int32_t>& esup) {
   const int32_t nn = m->d.n_nodes, nt = m->d.n_tri;
@@ -48,7 +49,15 @@ static pdf_status build_relax(pdf_mesh* m, const std::vector<int32_t>& bnd_wall,
   // wall unknowns and the nearest wall edge of every node
   std::vector<uint8_t> wall(nr, 0);
   const size_t nw = bnd_wall.size() / 2;
-  for (size_t i = 0; i < nw; ++i) { wall[node_rep[bnd_wall[2 * i]]] = 1; wall[node_rep[bnd_wall[2 * i + 1]]] = 1; }
+  // 1: free-slip wall node (off-diagonal components 0); 2: no-slip wall node
+  // (every component -4.5 eps n_i n_j), which wins where both meet
+  for (size_t i = 0; i < nw; ++i) {
+    const uint8_t t = wall_tag[i] == PDF_TAG_NOSLIP ? 2 : 1;
+    for (int q = 0; q < 2; ++q) {
+      uint8_t& w = wall[node_rep[bnd_wall[2 * i + q]]];
+      w = std::max(w, t);
+    }
+  }
   std::vector<double> wn(2 * (size_t)nn, 0.0), wd(nn, 1e300);
   std::vector<double> en(2 * nw);
   for (size_t i = 0; i < nw; ++i) {
@@ -353,11 +362,12 @@ extern "C" pdf_status pdf_mesh_create(const double* node_xy, int32_t n_nodes, co
   d.n_tri = n_tri;
   d.period = period_x;
   pdf_status s;
-  std::vector<int32_t> bnd_wall;
+  std::vector<int32_t> bnd_wall, wall_tag;
   for (int32_t i = 0; i < n_bnd; ++i)
     if (bnd_edge[3 * i + 2] == PDF_TAG_WALL || bnd_edge[3 * i + 2] == PDF_TAG_NOSLIP) {
       bnd_wall.push_back(bnd_edge[3 * i]);
       bnd_wall.push_back(bnd_edge[3 * i + 1]);
+      wall_tag.push_back(bnd_edge[3 * i + 2]);
     }
   if ((s = upload(&d.xy, m->xy.data(), m->xy.size())) != PDF_OK ||
       (s = upload(&d.tri, m->tri.data(), m->tri.size())) != PDF_OK ||
@@ -373,7 +383,7 @@ extern "C" pdf_status pdf_mesh_create(const double* node_xy, int32_t n_nodes, co
     delete m;
     return s;
   }
-  if ((s = build_relax(m, bnd_wall, dN, nse_off, nse, esup_off, esup)) != PDF_OK) {
+  if ((s = build_relax(m, bnd_wall, wall_tag, dN, nse_off, nse, esup_off, esup)) != PDF_OK) {
     free_mesh_dev(d);
     delete m;
     return s;

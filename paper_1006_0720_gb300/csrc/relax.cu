@@ -7,9 +7,11 @@
 //   L = C_L max(C_xi k^1.5 / eps, C_eta (nu^3 / eps)^1/4) (eq. L), with
 //   C_xi = 1 + 1.3 n_i n_i for wp_ii and 1 otherwise (eq. Cxi), n the unit
 //   outward normal of the nearest wall edge.
-// Reflecting walls are symmetry planes: off-diagonal components are held at
-// 0 on wall nodes, diagonal components take the natural condition.
-// Periodic twin nodes are one unknown.
+// Reflecting (free-slip) walls are symmetry planes: off-diagonal components
+// are held at 0 on wall nodes, diagonal components take the natural
+// condition.  No-slip walls hold every component at wp_ij = -4.5 eps n_i n_j
+// (the section on no-slip wall-boundary conditions).  Periodic twin nodes
+// are one unknown.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -29,7 +31,7 @@ constexpr double kRKFloor = 1e-12, kREFloor = 1e-12;
 // wp_11, of wp_22, and 1).
 __global__ void k_relax_nodes(int32_t n_nodes, const double* __restrict__ ns, const double* __restrict__ nd,
                               const double* __restrict__ wall_n, RelaxParams P, double* __restrict__ rhs,
-                              double* __restrict__ L2) {
+                              double* __restrict__ L2, double* __restrict__ gdir) {
   for (int32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < n_nodes; n += gridDim.x * blockDim.x) {
     const double* S = ns + (int64_t)n * PDF_NNS;
     const double* D = nd + (int64_t)n * PDF_NND;
@@ -59,6 +61,10 @@ __global__ void k_relax_nodes(int32_t n_nodes, const double* __restrict__ ns, co
         rhs[(int64_t)(3 * i + j) * n_nodes + n] = (i == j ? 0.5 * (1.0 - P.C1) * k * om : 0.0) + k * h;
       }
     const double nx = wall_n[2 * n], ny = wall_n[2 * n + 1];
+    // the no-slip Dirichlet values -4.5 eps n_i n_j (n_z = 0)
+    const double n3[3] = {nx, ny, 0.0};
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) gdir[(int64_t)(3 * i + j) * n_nodes + n] = -4.5 * eps * n3[i] * n3[j];
     const double lt = k * sqrt(k) / eps, lk = P.Ceta * sqrt(sqrt(P.nu * P.nu * P.nu / eps));
     const double cxi[3] = {1.0 + 1.3 * nx * nx, 1.0 + 1.3 * ny * ny, 1.0};
     for (int c = 0; c < 3; ++c) {
@@ -93,20 +99,22 @@ __global__ void k_relax_assemble(int64_t nnz, const double* __restrict__ mval, c
 
 __device__ __forceinline__ int comp_class(int ij) { return ij == 0 ? 0 : (ij == 4 ? 1 : 2); }
 __device__ __forceinline__ bool comp_dirichlet(int ij) { return ij != 0 && ij != 4 && ij != 8; }
+// component ij of unknown r is held fixed: off-diagonal on any wall, every
+// component on a no-slip wall
+__device__ __forceinline__ bool fixed_at(int ij, uint8_t w) { return w == 2 || (w == 1 && comp_dirichlet(ij)); }
 
 // y = A x for component ij over the unknowns (masked rows/cols for Dirichlet).
 __device__ __forceinline__ double spmv_row(int32_t r, int ij, int32_t n_rep, int64_t nnz,
                                            const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                            const double* __restrict__ aval, const uint8_t* __restrict__ wall,
                                            const double* __restrict__ x) {
-  const bool dir = comp_dirichlet(ij);
-  if (dir && wall[r]) return 0.0;
+  if (fixed_at(ij, wall[r])) return 0.0;
   const double* A = aval + (int64_t)comp_class(ij) * nnz;
   const double* X = x + (int64_t)ij * n_rep;
   double s = 0.0;
   for (int32_t q = rp[r]; q < rp[r + 1]; ++q) {
     const int32_t c = ci[q];
-    if (dir && wall[c]) continue;
+    if (fixed_at(ij, wall[c])) continue;
     s += A[q] * X[c];
   }
   return s;
@@ -135,35 +143,39 @@ __global__ void __launch_bounds__(kRBlock) k_cg_init(
     int32_t n_rep, int64_t nnz, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
     const double* __restrict__ mval, const double* __restrict__ aval, const double* __restrict__ diag,
     const uint8_t* __restrict__ wall, const int32_t* __restrict__ rep_node, int32_t n_nodes,
-    const double* __restrict__ f, const double* __restrict__ wp, double* __restrict__ x, double* __restrict__ r,
-    double* __restrict__ z, double* __restrict__ p, double* __restrict__ part) {
+    const double* __restrict__ f, const double* __restrict__ gdir, const double* __restrict__ wp,
+    double* __restrict__ x, double* __restrict__ r, double* __restrict__ z, double* __restrict__ p,
+    double* __restrict__ part) {
   const int ij = blockIdx.y;
-  const bool dir = comp_dirichlet(ij);
   const int32_t row = blockIdx.x * kRBlock + threadIdx.x;
   double rz = 0.0, rr = 0.0, bb = 0.0;
-  if (row < n_rep) {
-    const int64_t o = (int64_t)ij * n_rep + row;
-    x[o] = (dir && wall[row]) ? 0.0 : wp[(int64_t)ij * n_nodes + rep_node[row]];
-  }
-  __syncthreads();
-  // x of other rows is written by other blocks: computed r below uses the
-  // initial guess read directly from wp instead of x
+  // the starting value of an unknown: its fixed value (0, or the no-slip
+  // Dirichlet value), else the initial guess
+  auto start = [&](int32_t u) {
+    const uint8_t w = wall[u];
+    const int64_t o = (int64_t)ij * n_nodes + rep_node[u];
+    return fixed_at(ij, w) ? (w == 2 ? gdir[o] : 0.0) : wp[o];
+  };
+  if (row < n_rep) x[(int64_t)ij * n_rep + row] = start(row);
+  // x of other rows is written by other blocks: the residual below takes the
+  // starting values directly; the fixed columns carry their values into the
+  // free rows' right-hand side
+  const bool fixed_row = row < n_rep && fixed_at(ij, wall[row]);
   if (row < n_rep) {
     double b = 0.0, ax = 0.0;
-    if (!(dir && wall[row])) {
+    if (!fixed_row) {
       const double* A = aval + (int64_t)comp_class(ij) * nnz;
       for (int32_t q = rp[row]; q < rp[row + 1]; ++q) {
         const int32_t c = ci[q];
         b += mval[q] * f[(int64_t)ij * n_nodes + rep_node[c]];
-        if (dir && wall[c]) continue;
-        ax += A[q] * wp[(int64_t)ij * n_nodes + rep_node[c]];
+        ax += A[q] * start(c);
       }
     }
     const double res = b - ax;
     const double zz = res / diag[(int64_t)comp_class(ij) * n_rep + row];
     const int64_t o = (int64_t)ij * n_rep + row;
     r[o] = res;
-    z[o] = (dir && wall[row]) ? 0.0 : zz;
+    z[o] = fixed_row ? 0.0 : zz;
     p[o] = z[o];
     rz = res * z[o];
     rr = res * res;
@@ -223,7 +235,7 @@ __global__ void __launch_bounds__(kRBlock) k_cg_update(int32_t n_rep, const doub
     x[o] += alpha * p[o];
     const double res = r[o] - alpha * q[o];
     r[o] = res;
-    const bool fixed = comp_dirichlet(ij) && wall[row];
+    const bool fixed = fixed_at(ij, wall[row]);
     const double zz = fixed ? 0.0 : res / diag[(int64_t)comp_class(ij) * n_rep + row];
     z[o] = zz;
     rz = res * zz;
@@ -282,6 +294,7 @@ static pdf_status relax_alloc(pdf_particles* P) {
   cudaError_t e = cudaSuccess;
   auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
   A((void**)&W.f, sizeof(double) * 9 * nn);
+  A((void**)&W.g, sizeof(double) * 9 * nn);
   A((void**)&W.L2, sizeof(double) * 3 * nn);
   A((void**)&W.aval, sizeof(double) * 3 * R.nnz);
   A((void**)&W.diag, sizeof(double) * 3 * R.n_rep);
@@ -300,7 +313,7 @@ static pdf_status relax_alloc(pdf_particles* P) {
 }
 
 void relax_free(RelaxWork& W) {
-  cudaFree(W.f); cudaFree(W.L2); cudaFree(W.aval); cudaFree(W.diag); cudaFree(W.x); cudaFree(W.r);
+  cudaFree(W.f); cudaFree(W.g); cudaFree(W.L2); cudaFree(W.aval); cudaFree(W.diag); cudaFree(W.x); cudaFree(W.r);
   cudaFree(W.z); cudaFree(W.p); cudaFree(W.q); cudaFree(W.part); cudaFree(W.scal); cudaFree(W.beta);
   cudaFree(W.active);
   if (W.host) cudaFreeHost(W.host);
@@ -321,7 +334,7 @@ static pdf_status relax_prepare(pdf_particles* P, const pdf_model_params* params
   const RelaxMesh& R = m->rx;
   RelaxWork& W = P->rx;
   const int32_t nn = m->d.n_nodes;
-  PDF_KERNEL("k_relax_nodes", st, k_relax_nodes<<<rblocks(nn), 256, 0, st>>>(nn, P->ns, P->nd, R.wall_n, relax_params(params), W.f, W.L2));
+  PDF_KERNEL("k_relax_nodes", st, k_relax_nodes<<<rblocks(nn), 256, 0, st>>>(nn, P->ns, P->nd, R.wall_n, relax_params(params), W.f, W.L2, W.g));
   PDF_KERNEL("k_relax_assemble", st, k_relax_assemble<<<rblocks(R.nnz), 256, 0, st>>>(R.nnz, R.mval, R.ctb_off, R.ctb_e, R.ctb_k,
                                                                                       m->d.tri, nn, W.L2, W.aval));
   PDF_KERNEL("k_cg_diag", st, k_cg_diag<<<dim3(rblocks(R.n_rep), 3), 256, 0, st>>>(R.n_rep, R.nnz, R.rp, R.ci, W.aval, W.diag));
@@ -363,7 +376,7 @@ extern "C" pdf_status pdf_relax_solve(pdf_particles* p, const pdf_mesh* m, const
   const int32_t nn = m->d.n_nodes, nb = W.nb;
   const dim3 grid(nb, 9);
   PDF_KERNEL("k_cg_init", st, k_cg_init<<<grid, kRBlock, 0, st>>>(R.n_rep, R.nnz, R.rp, R.ci, R.mval, W.aval, W.diag,
-                                                                   R.wall, R.rep_node, nn, W.f, wp, W.x, W.r, W.z,
+                                                                   R.wall, R.rep_node, nn, W.f, W.g, wp, W.x, W.r, W.z,
                                                                    W.p, W.part));
   PDF_KERNEL("k_cg_reduce", st, k_cg_reduce<<<27, kRBlock, 0, st>>>(W.part, nb, 3, W.scal));
   PDF_CUDA(cudaMemcpyAsync(W.host, W.scal, sizeof(double) * 27, cudaMemcpyDeviceToHost, st));

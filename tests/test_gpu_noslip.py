@@ -95,3 +95,39 @@ def test_noslip_fp32_state_invariants():
     es = torch.empty((gm.n_tri, 13), dtype=torch.float64, device="cuda")
     pg.pdf_estimate_stats(gp, gm, es)
     assert int(es[:, 0].sum().item()) == int(counts.sum())
+
+
+def test_noslip_relaxation_solve_matches_the_oracle():
+    """pdf_relax_solve on the no-slip channel after a few steps: every
+    component holds -4.5 eps n_i n_j on the no-slip nodes and the solution
+    agrees with the oracle's sparse direct solve (each side with its own
+    statistics)."""
+    import oracle.relax as OR
+    m = _channel()
+    n_tri = 2 * 19 * 39
+    counts = np.full(n_tri, 40, dtype=np.int32)
+    psi = inputs.scalar_slab(m)
+    gm = pg.Mesh(m)
+    gp = pg.Particles(gm, 9, count=counts, u_sigma=0.2, elem_psi0=psi)
+    M = oracle.Mesh(m)
+    ost = oracle.init(M, counts, 9, u_sigma=0.2, elem_psi0=psi)
+    p = pg.model_params(closure="slm", dt=2e-3, nu=5e-3)
+    po = oracle.make_params(dt=p.dt, nu=p.nu, Pi=p.Pi, closure="slm", pressure="channel")
+    pg.pdf_estimate_stats(gp, gm)
+    es, ns, nd, _ = oracle.statistics(M, ost)
+    for s in range(3):
+        oracle.step(M, oracle.elem_coeff(M, ns, nd, po), po, 9, s, ost, omega_wall=oracle.noslip_omega(M, ns))
+        es, ns, nd, _ = oracle.statistics(M, ost, ns)
+        pg.pdf_step(gp, gm, p, step=s)
+        pg.pdf_estimate_stats(gp, gm)
+    wp = torch.zeros((9, gm.n_nodes), dtype=torch.float64, device="cuda")
+    iters, res = pg.pdf_relax_solve(gp, gm, p, wp, rtol=1e-13, max_it=4000)
+    got = wp.cpu().numpy()
+    rhs = np.stack([oracle.relax_rhs(ns[n], nd[n]) for n in range(gm.n_nodes)], axis=1)
+    ref = OR.solve(m, ns, rhs, p.nu)
+    assert_field_close(got.T, ref.T, "no-slip relaxation solution", rtol=1e-9)
+    walls = OR.wall_nodes(m, 5)
+    _, nrm = OR.wall_normals(m)
+    g = OR.noslip_values(ns, p.nu, nrm)
+    assert np.allclose(got[:, walls], g[:, walls], rtol=1e-9, atol=1e-12)
+    assert max(res) <= 1e-13

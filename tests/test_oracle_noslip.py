@@ -129,3 +129,33 @@ def test_wall_frequency_mean_from_the_kinetic_energy_gradient():
     assert np.allclose(w[lo], a / 6.0, rtol=1e-12)
     assert np.allclose(w[hi], 7.0)     # sqrt(2k) decreases towards y = +1
     assert np.all(w[~M.noslip_flag.astype(bool)] == 0.0)
+
+
+def test_relaxation_holds_the_noslip_dirichlet_values():
+    # eq. elliptic-relaxation-Lagrangian with no-slip walls: wp_ij = -4.5 eps
+    # n_i n_j on the wall nodes for every component; interior values follow
+    # the right-hand side when the lengthscale is small
+    import oracle.relax as OR
+    m = _mesh(10, 8)
+    n = len(m["xy"])
+    rng = np.random.default_rng(7)
+    S = np.zeros((n, 12))
+    S[:, 5:8] = rng.uniform(0.5, 1.0, (n, 3))
+    S[:, 3] = rng.uniform(1.0, 2.0, n)
+    rhs = rng.normal(size=(9, n))
+    twin = np.asarray(m["twin"])   # periodic twins are one node: equal statistics
+    t = np.flatnonzero(twin >= 0)
+    S[t] = S[np.minimum(t, twin[t])]
+    rhs[:, t] = rhs[:, np.minimum(t, twin[t])]
+    nu = 1e-3
+    wp = OR.solve(m, S, rhs, nu)
+    _, nrm = OR.wall_normals(m)
+    g = OR.noslip_values(S, nu, nrm)
+    walls = OR.wall_nodes(m, 5)
+    assert len(walls) == 2 * 10
+    for ij in range(9):
+        assert np.allclose(wp[ij][walls], g[ij][walls], rtol=1e-12, atol=1e-14)
+    # wall-normal is +-y: only the (y, y) component is non-zero there
+    assert np.allclose(g[4][walls], -4.5 * np.maximum(S[walls, 3] * (0.5 * S[walls, 5:8].sum(1)
+                                                                    + nu * 36.0 * S[walls, 3]), 1e-12))
+    assert np.allclose(g[0][walls], 0.0) and np.allclose(g[1][walls], 0.0)
