@@ -30,7 +30,7 @@ NCOEF = 26
 
 CLOSURE = {"glm": 0, "slm": 1}
 TM_MODE = {"turb": 0, "cphi": 1, "source": 2}
-PRESSURE = {"none": 0, "channel": 1}
+PRESSURE = {"none": 0, "channel": 1, "projection": 2}
 
 TRK_FALLBACK, TRK_BRUTE, TRK_LOST, TRK_EXIT_OUT, TRK_EXIT_IN, TRK_REINJECT, TRK_NEAR_FACE = 1, 2, 4, 8, 16, 32, 256
 TRK_NOSLIP = 64     # the no-slip wall condition was applied
@@ -100,8 +100,8 @@ def lib():
             L.or_shape_derivs.argtypes = [ctypes.c_void_p, I, PD, PD]
             L.or_node_derivs.argtypes = [ctypes.c_void_p, PD, PD]
             L.or_relax_rhs.argtypes = [PD, PD, PD]
-            L.or_node_coeff.argtypes = [PD, PD, PD, ctypes.POINTER(_Params), PD, PD]
-            L.or_elem_coeff.argtypes = [ctypes.c_void_p, PD, PD, PD, ctypes.POINTER(_Params), PD]
+            L.or_node_coeff.argtypes = [PD, PD, PD, ctypes.POINTER(_Params), PD, PD, PD]
+            L.or_elem_coeff.argtypes = [ctypes.c_void_p, PD, PD, PD, ctypes.POINTER(_Params), PD, PD]
             L.or_step.argtypes = [ctypes.c_void_p, ctypes.c_long, PD, ctypes.POINTER(_Params),
                                   ctypes.c_uint64, U32, PD, PD, PD, PD, PD, PD, PD, PI, PI, PL, PI, PD, PD]
             L.or_noslip_omega.argtypes = [ctypes.c_void_p, PD, PD]
@@ -267,24 +267,28 @@ def relax_rhs(S, Dv):
     return out
 
 
-def node_coeff(S, Dv, wp, params, xy=(0.0, 0.0)):
+def node_coeff(S, Dv, wp, params, xy=(0.0, 0.0), grad_p=None):
     out = np.zeros(NCOEF)
     S = np.ascontiguousarray(S, dtype=np.float64)
     Dv = np.ascontiguousarray(Dv, dtype=np.float64)
     w = None if wp is None else np.ascontiguousarray(wp, dtype=np.float64)
     P = np.ascontiguousarray(xy, dtype=np.float64)
+    g = None if grad_p is None else np.ascontiguousarray(grad_p, dtype=np.float64)
     lib().or_node_coeff(_p(S, D), _p(Dv, D), None if w is None else _p(w, D),
-                        ctypes.byref(params), _p(P, D), _p(out, D))
+                        ctypes.byref(params), _p(P, D), None if g is None else _p(g, D), _p(out, D))
     return out
 
 
-def elem_coeff(mesh, ns, nd, params, wp=None):
+def elem_coeff(mesh, ns, nd, params, wp=None, grad_p=None):
+    """grad_p: [n_nodes, 2] nodal gradient of the projected pressure (for
+    make_params(pressure="projection"))."""
     rows = np.zeros((mesh.n_tri, NCOEF))
     ns = np.ascontiguousarray(ns, dtype=np.float64)
     nd = np.ascontiguousarray(nd, dtype=np.float64)
     w = None if wp is None else np.ascontiguousarray(wp, dtype=np.float64)
+    g = None if grad_p is None else np.ascontiguousarray(grad_p, dtype=np.float64)
     lib().or_elem_coeff(mesh._h, _p(ns, D), _p(nd, D), None if w is None else _p(w, D),
-                        ctypes.byref(params), _p(rows, D))
+                        ctypes.byref(params), None if g is None else _p(g, D), _p(rows, D))
     return rows
 
 

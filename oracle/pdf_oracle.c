@@ -746,7 +746,7 @@ void or_node_derivs(const or_mesh* m, const double* ns, double* nd) {
 /* ------------------------------------------------------------------------ */
 enum { OR_CLOSURE_GLM = 0, OR_CLOSURE_SLM = 1 };
 enum { OR_TM_TURB = 0, OR_TM_CPHI = 1 };
-enum { OR_PRESSURE_NONE = 0, OR_PRESSURE_CHANNEL = 1 };
+enum { OR_PRESSURE_NONE = 0, OR_PRESSURE_CHANNEL = 1, OR_PRESSURE_PROJECTION = 2 };
 
 enum { OR_TM_SOURCE = 2 };
 typedef struct {
@@ -807,11 +807,13 @@ void or_relax_rhs(const double* S /*12 node stats*/, const double* D /*node deri
  *        eq. micromixing-timescale-channel), or 2/(C_phi <omega>)
  * eps: eq. dissipation-from-frequency_wall (GLM), eq. dissipation-from-
  * frequency (SLM).  Mean pressure (READING for the periodic channel, sec.
- * 4.2.1): -d<P>/dx = Pi imposed, -d<P>/dy = d<v^2>/dy.
+ * 4.2.1): -d<P>/dx = Pi imposed, -d<P>/dy = d<v^2>/dy; with the pressure
+ * projection (sec. 3.2): -d<P>/dx_i = Pi delta_i1 - gp_i, gp the nodal
+ * gradient of the projected field (NULL: zero).
  * wp: the 9 node values of the elliptic-relaxation tensor, or NULL for the
  * local model (wp = right-hand side, elliptic term dropped). */
 void or_node_coeff(const double* S, const double* D, const double* wp_in, const or_params* P,
-                   const double* xy, double* c) {
+                   const double* xy, const double* gp, double* c) {
   double k = 0.5 * (S[5] + S[6] + S[7]);
   double kg = k > OR_KFLOOR ? k : OR_KFLOOR;
   double om = S[3];
@@ -821,6 +823,10 @@ void or_node_coeff(const double* S, const double* D, const double* wp_in, const 
   for (int i = 0; i < 6; ++i) c[3 + i] = D[i];
   double dpx = 0.0, dpy = 0.0;  /* -d<P>/dx, -d<P>/dy */
   if (P->pressure == OR_PRESSURE_CHANNEL) { dpx = P->Pi; dpy = D[9]; }
+  if (P->pressure == OR_PRESSURE_PROJECTION) {
+    dpx = P->Pi - (gp ? gp[0] : 0.0);
+    dpy = -(gp ? gp[1] : 0.0);
+  }
   if (P->closure == OR_CLOSURE_SLM) {
     c[9] = dpx; c[10] = dpy; c[11] = 0.0;
     double g = -(0.5 + 0.75 * OR_C0_SLM) * om;
@@ -867,15 +873,17 @@ void or_node_coeff(const double* S, const double* D, const double* wp_in, const 
 
 /* Element-average coefficient rows: the mean of the three nodal values
  * (sec. 3.3: the average of the nodal values is used for all particles in
- * the element; loop (ii) of the table of loop designs).  wp: [9][n_nodes] or NULL. */
+ * the element; loop (ii) of the table of loop designs).  wp: [9][n_nodes] or
+ * NULL; gp: [n_nodes][2] nodal gradient of the projected pressure or NULL. */
 enum { OR_NCOEF = 26 };
 void or_elem_coeff(const or_mesh* m, const double* ns, const double* nd, const double* wp,
-                   const or_params* P, double* rows) {
+                   const or_params* P, const double* gp, double* rows) {
   double* nc = (double*)malloc(sizeof(double) * OR_NCOEF * m->n_nodes);
   for (int n = 0; n < m->n_nodes; ++n) {
     double w9[9];
     if (wp) for (int i = 0; i < 9; ++i) w9[i] = wp[(long)i * m->n_nodes + n];
-    or_node_coeff(ns + OR_NNS * n, nd + OR_NND * n, wp ? w9 : NULL, P, m->xy + 2 * n, nc + OR_NCOEF * n);
+    or_node_coeff(ns + OR_NNS * n, nd + OR_NND * n, wp ? w9 : NULL, P, m->xy + 2 * n, gp ? gp + 2 * n : NULL,
+                  nc + OR_NCOEF * n);
   }
   for (int e = 0; e < m->n_tri; ++e)
     for (int q = 0; q < OR_NCOEF; ++q) {
