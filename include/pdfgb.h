@@ -75,10 +75,11 @@ enum { PDF_CLOSURE_GLM = 0, PDF_CLOSURE_SLM = 1, PDF_CLOSURE_FROZEN = 2 };
  * SOURCE = eq. micromixing-timescale-canyon, min(C_s (r0^2/eps)^(1/3) +
  * C_t d/|<U>|, TURB) with d the node's distance to the source (src_*). */
 enum { PDF_TM_TURB = 0, PDF_TM_CPHI = 1, PDF_TM_SOURCE = 2 };
-/* Mean pressure gradient: NONE = 0; CHANNEL = imposed -d<P>/dx = Pi and the
- * cross-stream balance (1/rho) d<P>/dy = -d<v^2>/dy (eq. cross-stream-mean-
- * momentum-channel). */
-enum { PDF_PRESSURE_NONE = 0, PDF_PRESSURE_CHANNEL = 1 };
+/* Mean pressure gradient in the velocity prediction: NONE (0); CHANNEL,
+ * -d<P>/dx = Pi and -d<P>/dy = d<vv>/dy (the channel's cross-stream
+ * balance); PROJECTION, -d<P>/dx_i = Pi delta_i1 - d<P'>/dx_i with <P'> the
+ * nodal field of pdf_pressure_project (zero until its first call). */
+enum { PDF_PRESSURE_NONE = 0, PDF_PRESSURE_CHANNEL = 1, PDF_PRESSURE_PROJECTION = 2 };
 enum { PDF_MIX_IEM = 0, PDF_MIX_IECM = 1 };
 /* How the FP64-accurate particle step is computed.  FX (default): no FP64
  * instructions on the fast path -- positions in 64-bit fixed point (exact
@@ -352,6 +353,40 @@ pdf_status pdf_relax_rhs(pdf_particles* p, const pdf_mesh* m, const pdf_model_pa
 /* Host copies of each node's distance to the nearest wall edge [n_nodes] and
  * that edge's unit outward normal [n_nodes][2]; either may be NULL. */
 pdf_status pdf_mesh_wall_distance(const pdf_mesh* m, double* dist, double* normal);
+
+/* ---------------------------------------------------------------- pressure projection */
+
+/* The stabilised pressure projection (sec. 3.2: eqs. velocity-prediction,
+ * pressure-projection-smooth, velocity-correction) after a step whose
+ * statistics have been estimated (the particles hold U*):
+ *   grad^2 dP = (div <U*> - C_p grad^2 <P'>^n) / dt,   dP = <P'>^{n+1} - <P'>^n,
+ * with linear triangles, periodic twins one unknown:
+ *   K dP = -(d + C_p (K <P'>^n - G^n)) / dt + G^{n+1} - G^n,
+ * K the stiffness matrix, d_a = sum_e A_e / 3 div_e <U*>, G the load of the
+ * Neumann condition at WALL and NO-SLIP edges (eq. wall-pressure-condition:
+ * d<P>/dn = nu lap<U_i> n_i - d<u_i u_j>/dx_j n_i, and with the SLM closure,
+ * the wall-functions case, also - <U_j> d<U_i>/dx_j n_i; per edge the
+ * element's gradients and the mean of the edge's nodes, load h |edge| / 2 on
+ * each end), G^{n+1} from the present statistics and G^n the one stored by
+ * the projection that made <P'>^n (0 initially and after pdf_pressure_field
+ * sets the field); zero flux at inflow and outflow edges.  Solved by
+ * Jacobi-PCG in FP64 from zero; the right-hand side has its mean removed
+ * (compatibility of the pure-Neumann problem) and dP is normalised to zero
+ * mean over the unknowns.  Then every
+ * particle's velocity is corrected by -dt grad dP of its element, <P'> +=
+ * dP, the nodal gradient of <P'> (element gradients averaged over the
+ * surrounding elements) is stored for PDF_PRESSURE_PROJECTION steps, and the
+ * statistics are estimated again.
+ *   Cp       the stabilisation constant C_p (the paper suggests 1e-3)
+ *   rtol     stop when ||r|| <= rtol ||b||; PDF_ENOTCONV after max_it
+ *   iters, rel_res  host or NULL
+ * Synchronizes `stream` once per iteration.  PDF_ESTATE without statistics. */
+pdf_status pdf_pressure_project(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params, double Cp,
+                                double rtol, int32_t max_it, int32_t* iters, double* rel_res, void* stream);
+/* Copies the pressure field <P'> [n_nodes] (FP64, device or host) in (set,
+ * recomputing its nodal gradient and zeroing the stored wall load G^n)
+ * and/or out (get); either may be NULL. */
+pdf_status pdf_pressure_field(pdf_particles* p, const double* set, double* get, void* stream);
 
 /* ---------------------------------------------------------------- learned warm start */
 

@@ -39,7 +39,7 @@ def model_params(**kw):
     p = capi.ModelParams()
     lib().pdf_model_params_default(ctypes.byref(p))
     names = {"closure": {"glm": 0, "slm": 1, "frozen": 2}, "tm_mode": {"turb": 0, "cphi": 1, "source": 2},
-             "pressure": {"none": 0, "channel": 1}, "arith": {"fx": 0, "fp64": 1}, "mix": {"iem": 0, "iecm": 1}}
+             "pressure": {"none": 0, "channel": 1, "projection": 2}, "arith": {"fx": 0, "fp64": 1}, "mix": {"iem": 0, "iecm": 1}}
     for k, v in kw.items():
         if k in names and isinstance(v, str):
             v = names[k][v]
@@ -231,6 +231,27 @@ def pdf_last_error():
 
 def pdf_profile_enable(on=True):
     check(lib().pdf_profile_enable(1 if on else 0), "pdf_profile_enable")
+
+
+def pdf_pressure_project(particles, mesh, params, Cp=1e-3, rtol=1e-10, max_it=20000, stream=None):
+    """Stabilised pressure projection after a step's statistics; returns
+    (iterations, relative residual).  The particles' velocities are corrected
+    and the statistics estimated again."""
+    it = ctypes.c_int32()
+    res = ctypes.c_double()
+    check(lib().pdf_pressure_project(particles.handle, mesh.handle, ctypes.byref(params), float(Cp), float(rtol),
+                                     int(max_it), ctypes.byref(it), ctypes.byref(res), _stream(stream)),
+          "pdf_pressure_project")
+    return it.value, res.value
+
+
+def pdf_pressure_field(particles, mesh, set=None, stream=None):
+    """The projection's nodal pressure <P'> (device FP64 tensor); `set`
+    replaces it first."""
+    out = torch.empty(mesh.n_nodes, dtype=torch.float64, device="cuda")
+    check(lib().pdf_pressure_field(particles.handle, _ptr(set, torch.float64, mesh.n_nodes) if set is not None else None,
+                                   _ptr(out), _stream(stream)), "pdf_pressure_field")
+    return out
 
 
 def pdf_profile_only(kernel=None):

@@ -76,6 +76,8 @@ PROTOTYPES = {
     "pdf_particles_set_reorder": (I32, [V, I32]),
     "pdf_particles_set_iecm": (I32, [V, I32, I32, I32, I32]),
     "pdf_iecm_cond": (I32, [V, V, V]),
+    "pdf_pressure_project": (I32, [V, V, ctypes.POINTER(ModelParams), D, D, I32, ctypes.POINTER(I32), ctypes.POINTER(D), V]),
+    "pdf_pressure_field": (I32, [V, V, V, V]),
     "pdf_particles_get_state": (I32, [V, V, V, V, V, V, V, V, V, V]),
     "pdf_particles_set_state": (I32, [V, V, V, V, V, V, V, V, V, V]),
     "pdf_step": (I32, [V, V, ctypes.POINTER(ModelParams), V, V, U32, V, ctypes.POINTER(StepInfo)]),

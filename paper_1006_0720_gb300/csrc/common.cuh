@@ -107,6 +107,11 @@ struct RelaxMesh {
   int32_t* node_rep = nullptr;  // [n_nodes] unknown of each node
   double* wall_n = nullptr;     // [n_nodes][2] outward normal of the nearest wall edge
   double* wall_d = nullptr;     // [n_nodes] distance to it
+  // wall edges (WALL and NO-SLIP) at each unknown, for the pressure's
+  // Neumann load: element, node a, node b; outward normal and length
+  int32_t* pw_off = nullptr;    // [n_rep + 1]
+  int32_t* pw_e = nullptr;      // [pw_off[n_rep]][3]
+  double* pw_n = nullptr;       // [pw_off[n_rep]][3]
 };
 struct RelaxWork {
   int32_t nb = 0;
@@ -116,6 +121,16 @@ struct RelaxWork {
   int32_t* active = nullptr;
 };
 void relax_free(RelaxWork& W);
+// The pressure projection's work space (allocated on first use).
+struct PressWork {
+  int32_t nb = 0;
+  bool have_k = false;
+  double *kval = nullptr, *diag = nullptr, *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr;
+  double *p = nullptr, *q = nullptr, *part = nullptr, *scal = nullptr, *dP = nullptr, *ge = nullptr;
+  double *gw = nullptr, *gw_prev = nullptr;  // wall loads of the new and the current <P'>
+  double* host = nullptr;
+};
+void press_free(PressWork& W);
 }  // namespace pdfgb
 
 struct pdf_mesh {
@@ -206,6 +221,11 @@ struct pdf_particles {
   long long* counters = nullptr;  // [16] device
   // elliptic relaxation work space (allocated on first use)
   pdfgb::RelaxWork rx;
+  // pressure projection: the nodal field <P'> and its nodal gradient
+  // (zero until the first projection), and the solver's work space
+  double* pres = nullptr;   // [n_nodes]
+  double* gradP = nullptr;  // [n_nodes][2]
+  pdfgb::PressWork pw;
 };
 
 namespace pdfgb {

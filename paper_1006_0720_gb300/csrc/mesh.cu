@@ -25,6 +25,7 @@ static pdf_status upload(T** dst, const T* src, size_t n) {
 static void free_relax(RelaxMesh& r) {
   cudaFree(r.rp); cudaFree(r.ci); cudaFree(r.mval); cudaFree(r.ctb_off); cudaFree(r.ctb_e); cudaFree(r.ctb_k);
   cudaFree(r.wall); cudaFree(r.rep_node); cudaFree(r.node_rep); cudaFree(r.wall_n); cudaFree(r.wall_d);
+  cudaFree(r.pw_off); cudaFree(r.pw_e); cudaFree(r.pw_n);
   r = RelaxMesh();
 }
 
@@ -133,6 +134,33 @@ static pdf_status build_relax(pdf_mesh* m, const std::vector<int32_t>& bnd_wall,
     if (ci[q] < 0 || ci[q] >= nr) return fail(PDF_EINVAL, "pdf_mesh_create: relaxation column out of range");
     if (ctb_off[q + 1] - ctb_off[q] < 1 || ctb_off[q + 1] - ctb_off[q] > 64) return fail(PDF_EINVAL, "pdf_mesh_create: relaxation contributions out of range");
   }
+  // wall edges at each unknown (elements in order, local edges in order)
+  std::vector<std::vector<int32_t>> pwl(nr);
+  std::vector<int32_t> pw_e;
+  std::vector<double> pw_n;
+  for (int32_t e = 0; e < nt; ++e)
+    for (int k = 0; k < 3; ++k) {
+      const int32_t c = m->nbr[3 * e + k];
+      if (c != kNbrWall && c != kNbrNoslip) continue;
+      const int32_t a = T[3 * e + (k + 1) % 3], b = T[3 * e + (k + 2) % 3];
+      const int32_t id = (int32_t)(pw_e.size() / 3);
+      pw_e.insert(pw_e.end(), {e, a, b});
+      const double tx = X[2 * b] - X[2 * a], ty = X[2 * b + 1] - X[2 * a + 1];
+      const double len = std::sqrt(tx * tx + ty * ty);
+      // counter-clockwise element: the outside lies to the right of a -> b
+      pw_n.insert(pw_n.end(), {ty / len, -tx / len, len});
+      pwl[node_rep[a]].push_back(id);
+      pwl[node_rep[b]].push_back(id);
+    }
+  std::vector<int32_t> pw_off(nr + 1, 0), pw_ue;
+  std::vector<double> pw_un;
+  for (int32_t u = 0; u < nr; ++u) {
+    pw_off[u + 1] = pw_off[u] + (int32_t)pwl[u].size();
+    for (int32_t id : pwl[u]) {
+      pw_ue.insert(pw_ue.end(), pw_e.begin() + 3 * id, pw_e.begin() + 3 * id + 3);
+      pw_un.insert(pw_un.end(), pw_n.begin() + 3 * id, pw_n.begin() + 3 * id + 3);
+    }
+  }
   RelaxMesh& R = m->rx;
   R.n_rep = nr;
   R.nnz = nnz;
@@ -148,7 +176,10 @@ static pdf_status build_relax(pdf_mesh* m, const std::vector<int32_t>& bnd_wall,
       (s = upload(&R.rep_node, rep_node.data(), rep_node.size())) != PDF_OK ||
       (s = upload(&R.node_rep, node_rep.data(), node_rep.size())) != PDF_OK ||
       (s = upload(&R.wall_n, wn.data(), wn.size())) != PDF_OK ||
-      (s = upload(&R.wall_d, wd.data(), wd.size())) != PDF_OK) {
+      (s = upload(&R.wall_d, wd.data(), wd.size())) != PDF_OK ||
+      (s = upload(&R.pw_off, pw_off.data(), pw_off.size())) != PDF_OK ||
+      (s = upload(&R.pw_e, pw_ue.data(), pw_ue.size())) != PDF_OK ||
+      (s = upload(&R.pw_n, pw_un.data(), pw_un.size())) != PDF_OK) {
     free_relax(R);
     return s;
   }

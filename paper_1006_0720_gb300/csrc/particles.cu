@@ -162,7 +162,9 @@ static void free_particles(pdf_particles* p) {
   cudaFree(p->keys[0]); cudaFree(p->keys[1]); cudaFree(p->vals[0]); cudaFree(p->vals[1]);
   cudaFree(p->hist); cudaFree(p->hist_part); cudaFree(p->seg);
   cudaFree(p->counters);
+  cudaFree(p->pres); cudaFree(p->gradP);
   relax_free(p->rx);
+  press_free(p->pw);
   delete p;
 }
 
@@ -237,8 +239,12 @@ extern "C" pdf_status pdf_particles_init(const pdf_mesh* m, const pdf_init_param
   TRY_ALLOC(P->hist_part, P->n_scan_blocks + 1);
   TRY_ALLOC(P->seg, (int64_t)n_tri + 1);
   TRY_ALLOC(P->counters, 16);
+  TRY_ALLOC(P->pres, n_nodes);
+  TRY_ALLOC(P->gradP, 2 * (int64_t)n_nodes);
   cudaError_t e = cudaMemsetAsync(P->ns, 0, sizeof(double) * n_nodes * PDF_NNS, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(P->counters, 0, sizeof(long long) * 16, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->pres, 0, sizeof(double) * n_nodes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->gradP, 0, sizeof(double) * 2 * n_nodes, st);
   int64_t* d_off = nullptr;
   double* d_psi = nullptr;
   if (e == cudaSuccess) e = cudaMalloc(&d_off, sizeof(int64_t) * (n_tri + 1));

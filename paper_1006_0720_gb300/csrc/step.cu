@@ -73,7 +73,7 @@ __device__ void relax_rhs(const double* S, const double* D, const CoeffParams& P
 // (eq. frequency-source); <phi>; 1/t_m.
 __global__ void k_node_coeff(int32_t n_nodes, const double* __restrict__ ns, const double* __restrict__ nd,
                              const double* __restrict__ wp, const double* __restrict__ xy, CoeffParams P,
-                             double* __restrict__ nc) {
+                             const double* __restrict__ gradP, double* __restrict__ nc) {
   for (int32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < n_nodes; n += gridDim.x * blockDim.x) {
     double S[PDF_NNS], D[PDF_NND];
     for (int q = 0; q < PDF_NNS; ++q) S[q] = ns[(int64_t)n * PDF_NNS + q];
@@ -88,6 +88,7 @@ __global__ void k_node_coeff(int32_t n_nodes, const double* __restrict__ ns, con
     for (int q = 0; q < 6; ++q) c[3 + q] = D[q];
     double dpx = 0.0, dpy = 0.0;
     if (P.pressure == PDF_PRESSURE_CHANNEL) { dpx = P.Pi; dpy = D[9]; }
+    if (P.pressure == PDF_PRESSURE_PROJECTION) { dpx = P.Pi - gradP[2 * n]; dpy = -gradP[2 * n + 1]; }
     if (P.closure == PDF_CLOSURE_SLM) {
       c[9] = dpx; c[10] = dpy; c[11] = 0.0;
       const double g = -(0.5 + 0.75 * P.C0_slm) * om;
@@ -1094,7 +1095,7 @@ static pdf_status check_params(const pdf_model_params* p) {
   if (!p) return fail(PDF_EINVAL, "NULL params");
   if (!(p->dt > 0.0) || !(p->nu >= 0.0)) return fail(PDF_EINVAL, "params: dt must be > 0 and nu >= 0");
   if (p->closure < 0 || p->closure > 2 || p->tm_mode < 0 || p->tm_mode > 2 || p->pressure < 0 ||
-      p->pressure > 1 || p->arith < 0 || p->arith > 1 || p->mix < 0 || p->mix > 1)
+      p->pressure > 2 || p->arith < 0 || p->arith > 1 || p->mix < 0 || p->mix > 1)
     return fail(PDF_EINVAL, "params: closure, tm_mode, pressure, arith or mix out of range");
   return PDF_OK;
 }
@@ -1106,7 +1107,7 @@ static pdf_status build_rows(pdf_particles* P, const pdf_model_params* params, c
   const CoeffParams C = coeff_params(params);
   PDF_KERNEL("k_node_coeff", st, k_node_coeff<<<blocks_for(M.n_nodes, 128, 32), 128, 0, st>>>(M.n_nodes, P->ns, P->nd,
                                                                 params->closure == PDF_CLOSURE_GLM ? wp : nullptr,
-                                                                M.xy, C, P->nc););
+                                                                M.xy, C, P->gradP, P->nc););
   PDF_KERNEL("k_elem_rows", st, k_elem_rows<<<blocks_for(M.n_tri, 128, 32), 128, 0, st>>>(M.tri, M.n_tri, P->nc, C,
                                                              internal ? P->rows : nullptr, avg_out,
                                                              internal && C.arith == PDF_ARITH_FX ? P->rows_fx : nullptr,

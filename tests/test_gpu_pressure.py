@@ -1,0 +1,115 @@
+"""The stabilised mean-pressure projection (sec. 3.2: eqs. pressure-
+projection-smooth and velocity-correction, with the wall condition of eq.
+wall-pressure-condition) on the GPU against the oracle, each side on its own
+from the same seeded state: the pressure field, the corrected particle
+velocities, a second projection that carries the stored wall load, the
+statistics estimated after it, and a step whose drift sees the projected
+pressure gradient (eq. velocity-prediction)."""
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+import oracle.pressure as OP
+from parity_util import assert_field_close
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1006_0720_gb300 as pg  # noqa: E402
+from paper_1006_0720_gb300 import capi  # noqa: E402
+
+KEYS = ("x", "y", "u", "v", "w", "om", "ps")
+
+
+def _host(st):
+    return {k: v.cpu().numpy() for k, v in st.items()}
+
+
+def _setup(closure, wall_tag, seed=11, ppe=30, precision=capi.PDF_FP64):
+    m = inputs.channel_mesh(16, 24, seed=2, wall_tag=wall_tag)
+    n_tri = len(m["tri"])
+    counts = np.full(n_tri, ppe, dtype=np.int32)
+    psi = inputs.scalar_slab(m)
+    gm = pg.Mesh(m)
+    gp = pg.Particles(gm, seed, count=counts, u_sigma=0.3, elem_psi0=psi, precision=precision)
+    M = oracle.Mesh(m)
+    ost = oracle.init(M, counts, seed, u_sigma=0.3, elem_psi0=psi)
+    p = pg.model_params(closure=closure, dt=2e-3, nu=5e-3, pressure="projection")
+    return m, gm, gp, M, ost, p
+
+
+@pytest.mark.parametrize("closure,wall_tag", [("slm", inputs.TAG_NOSLIP), ("glm", None)])
+def test_projection_matches_the_oracle(closure, wall_tag):
+    m, gm, gp, M, ost, p = _setup(closure, wall_tag)
+    slm = closure == "slm"
+    Cp = 1e-3
+    n = gm.n_nodes
+    pg.pdf_estimate_stats(gp, gm)
+    _, ns, nd, _ = oracle.statistics(M, ost)
+    pres, G = np.zeros(n), np.zeros(n)
+    for k in range(2):
+        it, res = pg.pdf_pressure_project(gp, gm, p, Cp=Cp, rtol=1e-13, max_it=20000)
+        assert 0 < it < 20000 and res <= 1e-13
+        dP, pres, G, gradP = OP.project(m, ns, nd, ost, pres, G, p.nu, p.dt, Cp, slm)
+        got = pg.pdf_pressure_field(gp, gm).cpu().numpy()
+        assert np.abs(dP).max() > 1e-3
+        assert_field_close(got, pres, "projected pressure %d" % k, rtol=1e-9)
+        st = _host(gp.get_state())
+        assert np.array_equal(st["elem"], ost["elem"])
+        for key in ("u", "v"):
+            assert_field_close(st[key], ost[key], "corrected %s %d" % (key, k), rtol=1e-10)
+        # the statistics the library estimated again after the correction
+        es_g = torch.empty((gm.n_tri, capi.PDF_NES), dtype=torch.float64, device="cuda")
+        ns_g = torch.empty((n, capi.PDF_NNS), dtype=torch.float64, device="cuda")
+        pg.pdf_estimate_stats(gp, gm, es_g, ns_g)
+        es, ns, nd, _ = oracle.statistics(M, ost, ns)
+        assert_field_close(ns_g.cpu().numpy(), ns, "node stats after projection %d" % k, rtol=1e-9)
+    # a step whose drift sees Pi - grad <P'>
+    po = oracle.make_params(dt=p.dt, nu=p.nu, Pi=p.Pi, closure=closure, pressure="projection")
+    rows = oracle.elem_coeff(M, ns, nd, po, grad_p=gradP)
+    kw = {"omega_wall": oracle.noslip_omega(M, ns)} if wall_tag is not None else {}
+    cnt, status = oracle.step(M, rows, po, 11, 0, ost, **kw)
+    info = pg.pdf_step(gp, gm, p, step=0, info=True)
+    assert info["lost"] == 0 and cnt["lost"] == 0
+    st = _host(gp.get_state())
+    flagged = (status & oracle.TRK_NEAR_FACE) != 0
+    same = st["elem"] == ost["elem"]
+    assert (same | flagged).all()
+    for key in KEYS:
+        assert_field_close(st[key][same], ost[key][same], "projection step %s" % key)
+
+
+def test_pressure_field_set_and_get():
+    """A field set through pdf_pressure_field reaches the drift: with the
+    SLM closure the coefficient rows hold Pi - d<P'>/dx and -d<P'>/dy
+    exactly (eq. velocity-prediction), here 0.5 y gives -0.5."""
+    m, gm, gp, M, ost, p = _setup("slm", None)
+    y = m["xy"][:, 1]
+    f = torch.tensor(0.5 * y, dtype=torch.float64, device="cuda")
+    back = pg.pdf_pressure_field(gp, gm, set=f).cpu().numpy()
+    assert np.array_equal(back, 0.5 * y)
+    ce = torch.empty((gm.n_tri, capi.PDF_NCOEF), dtype=torch.float64, device="cuda")
+    pg.pdf_estimate_stats(gp, gm)
+    pg.pdf_elem_coeff(gp, gm, p, rows=ce)
+    c = ce.cpu().numpy()
+    np.testing.assert_allclose(c[:, 9], p.Pi, atol=1e-12)
+    np.testing.assert_allclose(c[:, 10], -0.5, atol=1e-12)
+
+
+def test_projection_fp32_state():
+    m, gm, gp, M, ost, p = _setup("slm", inputs.TAG_NOSLIP, precision=capi.PDF_FP32_STATE)
+    n = gm.n_nodes
+    pg.pdf_estimate_stats(gp, gm)
+    _, ns, nd, _ = oracle.statistics(M, ost)
+    it, res = pg.pdf_pressure_project(gp, gm, p, Cp=1e-3, rtol=1e-12, max_it=20000)
+    dP, pres, G, gradP = OP.project(m, ns, nd, ost, np.zeros(n), np.zeros(n), p.nu, p.dt, 1e-3, True)
+    got = pg.pdf_pressure_field(gp, gm).cpu().numpy()
+    # the FP32 state rounds the velocities the statistics come from
+    assert_field_close(got, pres, "projected pressure (FP32 state)", rtol=1e-4)
+    st = _host(gp.get_state())
+    for key in ("u", "v"):
+        assert_field_close(st[key], ost[key], "corrected %s (FP32 state)" % key, rtol=1e-5)
