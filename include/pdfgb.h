@@ -369,18 +369,22 @@ pdf_status pdf_mesh_wall_distance(const pdf_mesh* m, double* dist, double* norma
  * element's gradients and the mean of the edge's nodes, load h |edge| / 2 on
  * each end), G^{n+1} from the present statistics and G^n the one stored by
  * the projection that made <P'>^n (0 initially and after pdf_pressure_field
- * sets the field); zero flux at inflow and outflow edges.  Solved by
- * Jacobi-PCG in FP64 from zero; the right-hand side has its mean removed
+ * sets the field); zero flux at inflow and outflow edges.  Solved in FP64
+ * from zero by conjugate gradients preconditioned with one V-cycle of a
+ * smoothed-aggregation multigrid of K (built on the host at the first call,
+ * once per particle set); the right-hand side has its mean removed
  * (compatibility of the pure-Neumann problem) and dP is normalised to zero
- * mean over the unknowns.  Then every
- * particle's velocity is corrected by -dt grad dP of its element, <P'> +=
- * dP, the nodal gradient of <P'> (element gradients averaged over the
- * surrounding elements) is stored for PDF_PRESSURE_PROJECTION steps, and the
- * statistics are estimated again.
+ * mean over the unknowns.  Then every particle's velocity is corrected by
+ * -dt grad dP of its element, <P'> += dP, the nodal gradient of <P'>
+ * (element gradients averaged over the surrounding elements) is stored for
+ * PDF_PRESSURE_PROJECTION steps, and the statistics follow the correction
+ * (element means shifted by the same vector, central moments and conditional
+ * means unchanged; node statistics and derivatives recomputed).
  *   Cp       the stabilisation constant C_p (the paper suggests 1e-3)
  *   rtol     stop when ||r|| <= rtol ||b||; PDF_ENOTCONV after max_it
  *   iters, rel_res  host or NULL
- * Synchronizes `stream` once per iteration.  PDF_ESTATE without statistics. */
+ * Synchronizes `stream` once per 8 iterations.  PDF_ESTATE without
+ * statistics. */
 pdf_status pdf_pressure_project(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params, double Cp,
                                 double rtol, int32_t max_it, int32_t* iters, double* rel_res, void* stream);
 /* Copies the pressure field <P'> [n_nodes] (FP64, device or host) in (set,

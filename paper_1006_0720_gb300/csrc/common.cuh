@@ -122,12 +122,22 @@ struct RelaxWork {
 };
 void relax_free(RelaxWork& W);
 // The pressure projection's work space (allocated on first use).
+struct Amg;
 struct PressWork {
   int32_t nb = 0;
-  bool have_k = false;
-  double *kval = nullptr, *diag = nullptr, *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr;
+  Amg* amg = nullptr;          // multigrid preconditioner of K
+  int32_t* ctl = nullptr;      // device: done, iterations, max_it, tol flag, block counters
+  int32_t* host_ctl = nullptr; // page-locked copy
+  double *kval = nullptr, *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr;
   double *p = nullptr, *q = nullptr, *part = nullptr, *scal = nullptr, *dP = nullptr, *ge = nullptr;
   double *gw = nullptr, *gw_prev = nullptr;  // wall loads of the new and the current <P'>
+  float4* gc = nullptr;                      // per element -dt grad dP as double-float pairs
+  // a chunk of iterations captured as a CUDA graph on the library's own
+  // stream (replayed while kernel timing is off)
+  cudaStream_t cs = nullptr;
+  cudaGraphExec_t gx = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  long long graph_launches = 0;
   double* host = nullptr;
 };
 void press_free(PressWork& W);
@@ -141,6 +151,10 @@ struct pdf_mesh {
   std::vector<double> xy;
   std::vector<int32_t> tri, nbr, shift, twin, reinj;
   std::vector<double> area;
+  // host copy of the pressure stiffness matrix over the unknowns (the
+  // relaxation pattern rp/ci, values sum_e A_e grad N_a . grad N_b)
+  std::vector<int32_t> k_rp, k_ci;
+  std::vector<double> k_v;
 };
 
 // Internal coefficient row: 32 doubles (256 B) per element.
@@ -232,6 +246,11 @@ namespace pdfgb {
 // Launches through prof_launch are counted and, when timing is enabled,
 // bracketed by CUDA events on the launch stream.
 void prof_launch(const char* name, cudaStream_t st, void (*launch)(void*), void* ctx);
+// Whether per-kernel timing is on; adding launches made by a graph replay
+// to the counter; the counter itself.
+bool prof_timing();
+void prof_count(long long n);
+long long prof_launches();
 }  // namespace pdfgb
 
 // PDF_KERNEL(name, stream, kernel<<<grid, block, smem, stream>>>(args...));

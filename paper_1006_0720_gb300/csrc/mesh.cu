@@ -161,6 +161,11 @@ static pdf_status build_relax(pdf_mesh* m, const std::vector<int32_t>& bnd_wall,
       pw_un.insert(pw_un.end(), pw_n.begin() + 3 * id, pw_n.begin() + 3 * id + 3);
     }
   }
+  m->k_rp = rp;
+  m->k_ci = ci;
+  m->k_v.assign(nnz, 0.0);
+  for (int64_t q = 0; q < nnz; ++q)
+    for (int32_t t = ctb_off[q]; t < ctb_off[q + 1]; ++t) m->k_v[q] += ctb_k[t];
   RelaxMesh& R = m->rx;
   R.n_rep = nr;
   R.nnz = nnz;

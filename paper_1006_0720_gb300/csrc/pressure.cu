@@ -8,17 +8,26 @@
 // the statistics at the projection that made <P'>^n (G^0 = 0) and from the
 // present ones; zero flux at inflow and outflow edges.  The pure-Neumann
 // system is made compatible by removing the mean of the right-hand side and
-// solved by Jacobi-preconditioned conjugate gradients in FP64 from zero; dP
-// is normalised to zero mean.  The particles' velocities are corrected by
-// -dt grad dP of their element.
+// solved by preconditioned conjugate gradients in FP64 from zero; dP is
+// normalised to zero mean.  The particles' velocities are corrected by
+// -dt grad dP of their element, and the statistics follow the correction.
+//
+// The conjugate-gradient iteration runs under device control: alpha, beta
+// and the stopping test live in device memory (the last block of each
+// reduction finishes it), every kernel returns at once after the stop, and
+// the host looks at the state once per chunk of iterations.  The
+// preconditioner is one V-cycle of the smoothed-aggregation multigrid of
+// amg.cu (the paper's Jacobi preconditioner needs thousands of iterations on
+// meshes of 10^5 nodes).
 #include <algorithm>
 #include <cmath>
 
+#include "amg.cuh"
 #include "common.cuh"
 
 namespace pdfgb {
 
-pdf_status estimate_stats(pdf_particles* P, cudaStream_t st);
+pdf_status node_stats_from_elements(pdf_particles* P, cudaStream_t st);
 
 constexpr int kPBlock = 256;
 
@@ -34,27 +43,6 @@ __device__ __forceinline__ double pblock_sum(double v) {
     for (int i = 0; i < kPBlock / 32; ++i) t += sh[i];
   __syncthreads();
   return t;  // valid in thread 0
-}
-
-// K values (the relaxation pattern's stiffness contributions without L^2)
-// and the diagonal.
-__global__ void k_press_kval(int64_t nnz, const int32_t* __restrict__ ctb_off, const double* __restrict__ ctb_k,
-                             double* __restrict__ kval) {
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int32_t t = ctb_off[q]; t < ctb_off[q + 1]; ++t) s += ctb_k[t];
-    kval[q] = s;
-  }
-}
-
-__global__ void k_press_diag(int32_t n_rep, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                             const double* __restrict__ kval, double* __restrict__ diag) {
-  for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n_rep; r += gridDim.x * blockDim.x) {
-    double d = 1.0;
-    for (int32_t q = rp[r]; q < rp[r + 1]; ++q)
-      if (ci[q] == r) d = kval[q];
-    diag[r] = d > 0.0 ? d : 1.0;
-  }
 }
 
 // Neumann data at solid walls (eq. wall-pressure-condition; with wall
@@ -146,36 +134,96 @@ __global__ void k_press_sum(const double* __restrict__ part, int32_t nb, double*
   if (threadIdx.x == 0) *out = s;
 }
 
-// b -= mean(b); x = 0; r = b; z = r / diag; p = z; partials of r.z, r.r.
-__global__ void __launch_bounds__(kPBlock) k_press_init(int32_t n_rep, const double* __restrict__ bsum,
-                                                        const double* __restrict__ diag, double* __restrict__ b,
+// Device control words of the iteration.
+enum { kCtlDone = 0, kCtlIters = 1, kCtlMaxIt = 2, kCtlCount0 = 4, kCtlCount1 = 5 };
+// Device scalars.
+enum { kSPq = 0, kSRz = 1, kSRr = 2, kSXsum = 3, kSBsum = 4, kSAlpha = 5, kSRzOld = 6, kSTol2 = 7, kSRr0 = 8 };
+
+// True in the one block that arrives last at this reduction (its partial
+// written before); it resets the counter for the next use.
+__device__ __forceinline__ bool last_block(int32_t* counter) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    last = atomicAdd(counter, 1) == (int32_t)gridDim.x - 1;
+    if (last) *counter = 0;
+  }
+  __syncthreads();
+  return last;
+}
+
+// Sum of the block partials by the whole (last) block, in a fixed order;
+// the result is valid in thread 0.
+__device__ __forceinline__ double sum_parts(const double* part, int32_t nb) {
+  double t = 0.0;
+  for (int32_t i = threadIdx.x; i < nb; i += kPBlock) t += __ldcg(part + i);
+  return pblock_sum(t);
+}
+
+// b -= mean(b); x = 0; r = b; p = 0; r.r (last block: the stopping
+// threshold rtol^2 r.r, done when r = 0).
+__global__ void __launch_bounds__(kPBlock) k_press_init(int32_t n_rep, double rtol2, int32_t max_it,
+                                                        double* __restrict__ scal,
+                                                        int32_t* __restrict__ ctl, double* __restrict__ b,
                                                         double* __restrict__ x, double* __restrict__ r,
-                                                        double* __restrict__ z, double* __restrict__ p,
-                                                        double* __restrict__ part) {
+                                                        double* __restrict__ p, double* __restrict__ part) {
   const int32_t u = blockIdx.x * kPBlock + threadIdx.x;
-  double rz = 0.0, rr = 0.0;
+  double rr = 0.0;
   if (u < n_rep) {
-    const double bv = b[u] - *bsum / (double)n_rep;
+    const double bv = b[u] - scal[kSBsum] / (double)n_rep;
     b[u] = bv;
     x[u] = 0.0;
     r[u] = bv;
-    const double zz = bv / diag[u];
-    z[u] = zz;
-    p[u] = zz;
-    rz = bv * zz;
+    p[u] = 0.0;
     rr = bv * bv;
   }
-  const double s1 = pblock_sum(rz), s2 = pblock_sum(rr);
+  const double s = pblock_sum(rr);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (!last_block(ctl + kCtlCount0)) return;
+  const double t = sum_parts(part, gridDim.x);
   if (threadIdx.x == 0) {
-    part[blockIdx.x] = s1;
-    part[gridDim.x + blockIdx.x] = s2;
+    scal[kSRr] = t;
+    scal[kSRr0] = t;
+    scal[kSTol2] = rtol2 * t;
+    scal[kSRz] = 1.0;
+    scal[kSRzOld] = 1.0;
+    ctl[kCtlIters] = 0;
+    ctl[kCtlMaxIt] = max_it;
+    ctl[kCtlDone] = (t > 0.0 && max_it > 0) ? 0 : 1;
   }
 }
 
+// r . z from the preconditioner's partials: rz_old = rz, rz = sum.
+__global__ void k_press_rz(const double* __restrict__ part, int32_t nb, double* __restrict__ scal,
+                           const int32_t* __restrict__ done) {
+  if (*done) return;
+  double s = 0.0;
+  for (int32_t i = threadIdx.x; i < nb; i += kPBlock) s += part[i];
+  s = pblock_sum(s);
+  if (threadIdx.x == 0) {
+    scal[kSRzOld] = scal[kSRz];
+    scal[kSRz] = s;
+  }
+}
+
+// p = z + beta p, beta = rz / rz_old (p = 0 before the first iteration).
+__global__ void k_press_dir(int32_t n_rep, const double* __restrict__ scal, const double* __restrict__ z,
+                            double* __restrict__ p, const int32_t* __restrict__ done) {
+  if (*done) return;
+  const double ro = scal[kSRzOld];
+  const double beta = ro != 0.0 ? scal[kSRz] / ro : 0.0;
+  for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n_rep; u += gridDim.x * blockDim.x)
+    p[u] = z[u] + beta * p[u];
+}
+
+// q = K p, p . q (last block: alpha = rz / p.q).
 __global__ void __launch_bounds__(kPBlock) k_press_spmv(int32_t n_rep, const int32_t* __restrict__ rp,
                                                         const int32_t* __restrict__ ci, const double* __restrict__ kval,
                                                         const double* __restrict__ p, double* __restrict__ q,
+                                                        double* __restrict__ scal, int32_t* __restrict__ ctl,
                                                         double* __restrict__ part) {
+  if (ctl[kCtlDone]) return;
   const int32_t u = blockIdx.x * kPBlock + threadIdx.x;
   double pq = 0.0;
   if (u < n_rep) {
@@ -186,36 +234,50 @@ __global__ void __launch_bounds__(kPBlock) k_press_spmv(int32_t n_rep, const int
   }
   const double t = pblock_sum(pq);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
+  if (!last_block(ctl + kCtlCount0)) return;
+  const double v = sum_parts(part, gridDim.x);
+  if (threadIdx.x == 0) {
+    scal[kSPq] = v;
+    scal[kSAlpha] = v > 0.0 ? scal[kSRz] / v : 0.0;
+  }
 }
 
-// scal[0] = p.q, scal[1] = r.z (old): x += a p, r -= a q, z = r / diag.
-__global__ void __launch_bounds__(kPBlock) k_press_update(int32_t n_rep, const double* __restrict__ scal,
-                                                          const double* __restrict__ diag, double* __restrict__ x,
-                                                          double* __restrict__ r, double* __restrict__ z,
-                                                          const double* __restrict__ p, const double* __restrict__ q,
-                                                          double* __restrict__ part) {
+// x += alpha p, r -= alpha q, r . r (last block: count the iteration and
+// stop at r.r <= rtol^2 r0.r0, at max_it, or when p.q <= 0).
+__global__ void __launch_bounds__(kPBlock) k_press_update(int32_t n_rep, double* __restrict__ scal,
+                                                          int32_t* __restrict__ ctl, double* __restrict__ x,
+                                                          double* __restrict__ r, const double* __restrict__ p,
+                                                          const double* __restrict__ q, double* __restrict__ part) {
+  if (ctl[kCtlDone]) return;
   const int32_t u = blockIdx.x * kPBlock + threadIdx.x;
-  double rz = 0.0, rr = 0.0;
+  const double a = scal[kSAlpha];
+  double rr = 0.0;
   if (u < n_rep) {
-    const double a = scal[0] != 0.0 ? scal[1] / scal[0] : 0.0;
     x[u] += a * p[u];
     const double rv = r[u] - a * q[u];
     r[u] = rv;
-    const double zz = rv / diag[u];
-    z[u] = zz;
-    rz = rv * zz;
     rr = rv * rv;
   }
-  const double s1 = pblock_sum(rz), s2 = pblock_sum(rr);
+  const double t = pblock_sum(rr);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+  if (!last_block(ctl + kCtlCount1)) return;
+  const double v = sum_parts(part, gridDim.x);
   if (threadIdx.x == 0) {
-    part[blockIdx.x] = s1;
-    part[gridDim.x + blockIdx.x] = s2;
+    scal[kSRr] = v;
+    const int32_t it = ctl[kCtlIters] + 1;
+    ctl[kCtlIters] = it;
+    if (v <= scal[kSTol2] || it >= ctl[kCtlMaxIt] || !(scal[kSPq] > 0.0)) ctl[kCtlDone] = 1;
   }
 }
 
-__global__ void k_press_dir(int32_t n_rep, double beta, const double* __restrict__ z, double* __restrict__ p) {
-  for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n_rep; u += gridDim.x * blockDim.x)
-    p[u] = z[u] + beta * p[u];
+// r . z partials when the hierarchy has no level (z = the coarse solve).
+__global__ void __launch_bounds__(kPBlock) k_press_dot(int32_t n_rep, const double* __restrict__ r,
+                                                       const double* __restrict__ z, double* __restrict__ part,
+                                                       const int32_t* __restrict__ done) {
+  if (*done) return;
+  const int32_t u = blockIdx.x * kPBlock + threadIdx.x;
+  const double s = pblock_sum(u < n_rep ? r[u] * z[u] : 0.0);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
 // partials of sum x (for the zero-mean normalisation)
@@ -269,29 +331,52 @@ __global__ void k_press_ngrad(int32_t n_nodes, const int32_t* __restrict__ nse_o
   }
 }
 
-// Velocity correction of every particle: U -= dt grad dP of its element.
-template <typename T>
-__global__ void k_press_correct(int64_t n, const int32_t* __restrict__ elem, const double* __restrict__ gdp,
-                                double dt, T* __restrict__ u, T* __restrict__ v);
-
-template <>
-__global__ void k_press_correct<fx::df>(int64_t n, const int32_t* __restrict__ elem, const double* __restrict__ gdp,
-                                        double dt, fx::df* __restrict__ u, fx::df* __restrict__ v) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = elem[p];
-    u[p] = fx::from_double(fx::to_double(u[p]) - dt * gdp[2 * e]);
-    v[p] = fx::from_double(fx::to_double(v[p]) - dt * gdp[2 * e + 1]);
+// The correction shifts every particle of an element by the same vector, so
+// the element means <U>, <V> shift by it and the central moments (and the
+// velocity ranks the conditional means bin by) stay as they are.
+__global__ void k_press_shift_stats(int32_t n_tri, const double* __restrict__ gdp, double dt, double* __restrict__ es) {
+  for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n_tri; e += gridDim.x * blockDim.x) {
+    double* s = es + (int64_t)e * PDF_NES;
+    if (s[0] <= 0.0) continue;
+    s[1] -= dt * gdp[2 * (int64_t)e];
+    s[2] -= dt * gdp[2 * (int64_t)e + 1];
   }
 }
 
-template <>
-__global__ void k_press_correct<float>(int64_t n, const int32_t* __restrict__ elem, const double* __restrict__ gdp,
-                                       double dt, float* __restrict__ u, float* __restrict__ v) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = elem[p];
-    u[p] = (float)((double)u[p] - dt * gdp[2 * e]);
-    v[p] = (float)((double)v[p] - dt * gdp[2 * e + 1]);
+// The correction of an element, -dt grad dP, as double-float pairs
+// (x.h, x.l, y.h, y.l), so that the particle pass needs no FP64.
+__global__ void k_press_corr_coef(int32_t n_tri, const double* __restrict__ gdp, double dt, float4* __restrict__ gc) {
+  for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n_tri; e += gridDim.x * blockDim.x) {
+    const fx::df cx = fx::from_double(-dt * gdp[2 * (int64_t)e]);
+    const fx::df cy = fx::from_double(-dt * gdp[2 * (int64_t)e + 1]);
+    gc[e] = make_float4(cx.h, cx.l, cy.h, cy.l);
   }
+}
+
+// Velocity correction of every particle: U += -dt grad dP of its element
+// (double-float addition; FP32 state: the nearest float of the sum).
+template <typename T>
+__global__ void k_press_correct(int64_t n, const int32_t* __restrict__ elem, const float4* __restrict__ gc,
+                                T* __restrict__ u, T* __restrict__ v);
+
+template <>
+__global__ void k_press_correct<fx::df>(int64_t n, const int32_t* __restrict__ elem, const float4* __restrict__ gc,
+                                        fx::df* __restrict__ u, fx::df* __restrict__ v) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const float4 c = __ldg(gc + elem[p]);
+  u[p] = fx::add(u[p], fx::df{c.x, c.y});
+  v[p] = fx::add(v[p], fx::df{c.z, c.w});
+}
+
+template <>
+__global__ void k_press_correct<float>(int64_t n, const int32_t* __restrict__ elem, const float4* __restrict__ gc,
+                                       float* __restrict__ u, float* __restrict__ v) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const float4 c = __ldg(gc + elem[p]);
+  u[p] = fx::add(fx::df{u[p], 0.f}, fx::df{c.x, c.y}).h;
+  v[p] = fx::add(fx::df{v[p], 0.f}, fx::df{c.z, c.w}).h;
 }
 
 static int pblocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096)); }
@@ -299,13 +384,13 @@ static int pblocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_
 static pdf_status press_alloc(pdf_particles* P) {
   PressWork& W = P->pw;
   if (W.x) return PDF_OK;
-  const RelaxMesh& R = P->mesh->rx;
-  const int32_t nn = P->mesh->d.n_nodes, nt = P->mesh->d.n_tri;
+  const pdf_mesh* m = P->mesh;
+  const RelaxMesh& R = m->rx;
+  const int32_t nn = m->d.n_nodes, nt = m->d.n_tri;
   W.nb = (R.n_rep + kPBlock - 1) / kPBlock;
   cudaError_t e = cudaSuccess;
   auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
   A((void**)&W.kval, sizeof(double) * R.nnz);
-  A((void**)&W.diag, sizeof(double) * R.n_rep);
   A((void**)&W.b, sizeof(double) * R.n_rep);
   A((void**)&W.x, sizeof(double) * R.n_rep);
   A((void**)&W.r, sizeof(double) * R.n_rep);
@@ -313,23 +398,96 @@ static pdf_status press_alloc(pdf_particles* P) {
   A((void**)&W.p, sizeof(double) * R.n_rep);
   A((void**)&W.q, sizeof(double) * R.n_rep);
   A((void**)&W.part, sizeof(double) * 2 * W.nb);
-  A((void**)&W.scal, sizeof(double) * 8);
+  A((void**)&W.scal, sizeof(double) * 16);
   A((void**)&W.dP, sizeof(double) * nn);
   A((void**)&W.ge, sizeof(double) * 2 * nt);
+  A((void**)&W.gc, sizeof(float4) * nt);
   A((void**)&W.gw, sizeof(double) * R.n_rep);
   A((void**)&W.gw_prev, sizeof(double) * R.n_rep);
+  A((void**)&W.ctl, sizeof(int32_t) * 8);
   if (e == cudaSuccess) e = cudaMemset(W.gw_prev, 0, sizeof(double) * R.n_rep);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&W.host, sizeof(double) * 8);
-  if (e != cudaSuccess) return cuda_fail(e, "pdf_pressure_project: allocation");
-  return PDF_OK;
+  if (e == cudaSuccess) e = cudaMemset(W.ctl, 0, sizeof(int32_t) * 8);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(W.kval, m->k_v.data(), sizeof(double) * R.nnz, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&W.host, sizeof(double) * 16);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&W.host_ctl, sizeof(int32_t) * 8);
+  if (e != cudaSuccess) {
+    press_free(W);
+    return cuda_fail(e, "pdf_pressure_project: allocation");
+  }
+  W.amg = new Amg();
+  pdf_status s = amg_setup(R.n_rep, m->k_rp, m->k_ci, m->k_v, *W.amg);
+  if (s != PDF_OK) press_free(W);
+  return s;
 }
 
 void press_free(PressWork& W) {
-  cudaFree(W.kval); cudaFree(W.diag); cudaFree(W.b); cudaFree(W.x); cudaFree(W.r); cudaFree(W.z);
+  cudaFree(W.kval); cudaFree(W.b); cudaFree(W.x); cudaFree(W.r); cudaFree(W.z);
   cudaFree(W.p); cudaFree(W.q); cudaFree(W.part); cudaFree(W.scal); cudaFree(W.dP); cudaFree(W.ge);
-  cudaFree(W.gw); cudaFree(W.gw_prev);
+  cudaFree(W.gw); cudaFree(W.gw_prev); cudaFree(W.ctl); cudaFree(W.gc);
   if (W.host) cudaFreeHost(W.host);
+  if (W.host_ctl) cudaFreeHost(W.host_ctl);
+  if (W.amg) {
+    amg_free(*W.amg);
+    delete W.amg;
+  }
+  if (W.gx) cudaGraphExecDestroy(W.gx);
+  if (W.ev0) cudaEventDestroy(W.ev0);
+  if (W.ev1) cudaEventDestroy(W.ev1);
+  if (W.cs) cudaStreamDestroy(W.cs);
   W = PressWork();
+}
+
+// k preconditioned conjugate-gradient iterations (each kernel returns at
+// once after the stop).
+static pdf_status press_iterations(pdf_particles* P, int k, cudaStream_t st) {
+  PressWork& W = P->pw;
+  const RelaxMesh& R = P->mesh->rx;
+  const Amg& G = *W.amg;
+  const int nb = W.nb;
+  const int32_t* done = W.ctl + kCtlDone;
+  for (int i = 0; i < k; ++i) {
+    pdf_status s = amg_apply(G, W.r, W.z, W.part, done, st);
+    if (s != PDF_OK) return s;
+    if (G.lv.empty())
+      PDF_KERNEL("k_press_dot", st, k_press_dot<<<nb, kPBlock, 0, st>>>(R.n_rep, W.r, W.z, W.part, done));
+    PDF_KERNEL("k_press_rz", st, k_press_rz<<<1, kPBlock, 0, st>>>(W.part, nb, W.scal, done));
+    PDF_KERNEL("k_press_dir", st, k_press_dir<<<pblocks(R.n_rep), 256, 0, st>>>(R.n_rep, W.scal, W.z, W.p, done));
+    PDF_KERNEL("k_press_spmv", st, k_press_spmv<<<nb, kPBlock, 0, st>>>(R.n_rep, R.rp, R.ci, W.kval, W.p, W.q, W.scal,
+                                                                         W.ctl, W.part));
+    PDF_KERNEL("k_press_update", st, k_press_update<<<nb, kPBlock, 0, st>>>(R.n_rep, W.scal, W.ctl, W.x, W.r, W.p, W.q,
+                                                                             W.part));
+  }
+  return PDF_OK;
+}
+
+// Captures k iterations into W.gx on the library's stream W.cs.
+static pdf_status press_capture(pdf_particles* P, int k) {
+  PressWork& W = P->pw;
+  if (!W.cs) {
+    PDF_CUDA(cudaStreamCreateWithFlags(&W.cs, cudaStreamNonBlocking));
+    PDF_CUDA(cudaEventCreateWithFlags(&W.ev0, cudaEventDisableTiming));
+    PDF_CUDA(cudaEventCreateWithFlags(&W.ev1, cudaEventDisableTiming));
+  }
+  const long long n0 = prof_launches();
+  PDF_CUDA(cudaStreamBeginCapture(W.cs, cudaStreamCaptureModeThreadLocal));
+  pdf_status s = press_iterations(P, k, W.cs);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(W.cs, &g);
+  if (s != PDF_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "pdf_pressure_project: graph capture");
+  const cudaError_t e2 = cudaGraphInstantiate(&W.gx, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) {
+    W.gx = nullptr;
+    return cuda_fail(e2, "pdf_pressure_project: graph instantiation");
+  }
+  W.graph_launches = prof_launches() - n0;
+  prof_count(-W.graph_launches);  // captured, not launched
+  return PDF_OK;
 }
 
 // Nodal gradient of <P'> for PDF_PRESSURE_PROJECTION steps.
@@ -360,65 +518,72 @@ extern "C" pdf_status pdf_pressure_project(pdf_particles* p, const pdf_mesh* m, 
   const RelaxMesh& R = m->rx;
   PressWork& W = p->pw;
   const int nb = W.nb;
-  if (!W.have_k) {
-    PDF_KERNEL("k_press_kval", st, k_press_kval<<<pblocks(R.nnz), 256, 0, st>>>(R.nnz, R.ctb_off, R.ctb_k, W.kval));
-    PDF_KERNEL("k_press_diag", st, k_press_diag<<<pblocks(R.n_rep), 256, 0, st>>>(R.n_rep, R.rp, R.ci, W.kval, W.diag));
-    W.have_k = true;
-  }
   PDF_KERNEL("k_press_rhs", st, k_press_rhs<<<nb, kPBlock, 0, st>>>(R.n_rep, R.rep_node, R.rp, R.ci, W.kval, M.nse_off,
                                                                      M.nse, M.tri, M.dN, M.geo, p->ns, p->nd, R.pw_off,
                                                                      R.pw_e, R.pw_n, params->nu,
                                                                      params->closure == PDF_CLOSURE_SLM, p->pres,
                                                                      W.gw_prev, Cp, 1.0 / params->dt, W.gw, W.b,
                                                                      W.part));
-  PDF_KERNEL("k_press_sum", st, k_press_sum<<<1, kPBlock, 0, st>>>(W.part, nb, W.scal + 4));
-  PDF_KERNEL("k_press_init", st, k_press_init<<<nb, kPBlock, 0, st>>>(R.n_rep, W.scal + 4, W.diag, W.b, W.x, W.r, W.z,
-                                                                       W.p, W.part));
-  PDF_KERNEL("k_press_sum", st, k_press_sum<<<1, kPBlock, 0, st>>>(W.part, nb, W.scal + 1));
-  PDF_KERNEL("k_press_sum", st, k_press_sum<<<1, kPBlock, 0, st>>>(W.part + nb, nb, W.scal + 2));
-  PDF_CUDA(cudaMemcpyAsync(W.host, W.scal, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
-  PDF_CUDA(cudaStreamSynchronize(st));
-  double rz = W.host[1];
-  const double bn = std::sqrt(W.host[2]);
-  double rn = bn;
-  int it = 0;
-  while (rn > rtol * bn && bn > 0.0 && it < max_it) {
-    PDF_KERNEL("k_press_spmv", st, k_press_spmv<<<nb, kPBlock, 0, st>>>(R.n_rep, R.rp, R.ci, W.kval, W.p, W.q, W.part));
-    PDF_KERNEL("k_press_sum", st, k_press_sum<<<1, kPBlock, 0, st>>>(W.part, nb, W.scal));
-    PDF_KERNEL("k_press_update", st, k_press_update<<<nb, kPBlock, 0, st>>>(R.n_rep, W.scal, W.diag, W.x, W.r, W.z, W.p,
-                                                                             W.q, W.part));
-    PDF_KERNEL("k_press_sum", st, k_press_sum<<<1, kPBlock, 0, st>>>(W.part, nb, W.scal + 1));
-    PDF_KERNEL("k_press_sum", st, k_press_sum<<<1, kPBlock, 0, st>>>(W.part + nb, nb, W.scal + 2));
-    PDF_CUDA(cudaMemcpyAsync(W.host, W.scal, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
-    PDF_CUDA(cudaStreamSynchronize(st));
-    ++it;
-    const double rzn = W.host[1];
-    rn = std::sqrt(W.host[2]);
-    const double beta = rz != 0.0 ? rzn / rz : 0.0;
-    rz = rzn;
-    if (rn > rtol * bn)
-      PDF_KERNEL("k_press_dir", st, k_press_dir<<<pblocks(R.n_rep), 256, 0, st>>>(R.n_rep, beta, W.z, W.p));
+  PDF_KERNEL("k_press_sum", st, k_press_sum<<<1, kPBlock, 0, st>>>(W.part, nb, W.scal + kSBsum));
+  PDF_KERNEL("k_press_init", st, k_press_init<<<nb, kPBlock, 0, st>>>(R.n_rep, rtol * rtol, max_it, W.scal, W.ctl,
+                                                                       W.b, W.x, W.r, W.p, W.part));
+  // iterations in chunks; the host reads the control words once per chunk
+  constexpr int kChunk = 8;
+  if (prof_timing()) {
+    for (int launched = 0; launched < max_it; launched += kChunk) {
+      s = press_iterations(p, kChunk, st);
+      if (s != PDF_OK) return s;
+      PDF_CUDA(cudaMemcpyAsync(W.host_ctl, W.ctl, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, st));
+      PDF_CUDA(cudaStreamSynchronize(st));
+      if (W.host_ctl[kCtlDone]) break;
+    }
+  } else {
+    if (!W.gx) {
+      s = press_capture(p, kChunk);
+      if (s != PDF_OK) return s;
+    }
+    PDF_CUDA(cudaEventRecord(W.ev0, st));
+    PDF_CUDA(cudaStreamWaitEvent(W.cs, W.ev0, 0));
+    for (int launched = 0; launched < max_it; launched += kChunk) {
+      PDF_CUDA(cudaGraphLaunch(W.gx, W.cs));
+      prof_count(W.graph_launches);
+      PDF_CUDA(cudaMemcpyAsync(W.host_ctl, W.ctl, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, W.cs));
+      PDF_CUDA(cudaStreamSynchronize(W.cs));
+      if (W.host_ctl[kCtlDone]) break;
+    }
+    PDF_CUDA(cudaEventRecord(W.ev1, W.cs));
+    PDF_CUDA(cudaStreamWaitEvent(st, W.ev1, 0));
   }
+  PDF_CUDA(cudaMemcpyAsync(W.host, W.scal, sizeof(double) * 16, cudaMemcpyDeviceToHost, st));
+  PDF_CUDA(cudaMemcpyAsync(W.host_ctl, W.ctl, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, st));
+  PDF_CUDA(cudaStreamSynchronize(st));
+  const int it = W.host_ctl[kCtlIters];
+  const double bn = std::sqrt(W.host[kSRr0]);
+  const double rn = std::sqrt(W.host[kSRr]);
+  const bool converged = W.host[kSRr] <= W.host[kSTol2];
   if (iters) *iters = it;
   if (rel_res) *rel_res = bn > 0.0 ? rn / bn : 0.0;
   PDF_KERNEL("k_press_xsum", st, k_press_xsum<<<nb, kPBlock, 0, st>>>(R.n_rep, W.x, W.part));
-  PDF_KERNEL("k_press_sum", st, k_press_sum<<<1, kPBlock, 0, st>>>(W.part, nb, W.scal + 3));
+  PDF_KERNEL("k_press_sum", st, k_press_sum<<<1, kPBlock, 0, st>>>(W.part, nb, W.scal + kSXsum));
   PDF_KERNEL("k_press_scatter", st, k_press_scatter<<<pblocks(M.n_nodes), 256, 0, st>>>(M.n_nodes, R.n_rep, R.node_rep,
-                                                                                          W.x, W.scal + 3, W.dP, p->pres));
+                                                                                          W.x, W.scal + kSXsum, W.dP, p->pres));
   std::swap(W.gw, W.gw_prev);  // <P'>^{n+1} satisfies the new wall load
   // velocity correction with the element gradients of dP
   PDF_KERNEL("k_press_egrad", st, k_press_egrad<<<pblocks(M.n_tri), 256, 0, st>>>(M.n_tri, M.tri, M.dN, W.dP, W.ge));
+  PDF_KERNEL("k_press_corr_coef", st, k_press_corr_coef<<<pblocks(M.n_tri), 256, 0, st>>>(M.n_tri, W.ge, params->dt,
+                                                                                            W.gc));
+  const unsigned pb = (unsigned)std::max<int64_t>(1, (p->n + 255) / 256);
   if (p->precision == PDF_FP64)
-    PDF_KERNEL("k_press_correct", st, k_press_correct<fx::df><<<pblocks(p->n), 256, 0, st>>>(p->n, p->elem, W.ge,
-                                                                                           params->dt, p->u, p->v));
+    PDF_KERNEL("k_press_correct", st, k_press_correct<fx::df><<<pb, 256, 0, st>>>(p->n, p->elem, W.gc, p->u, p->v));
   else
-    PDF_KERNEL("k_press_correct", st, k_press_correct<float><<<pblocks(p->n), 256, 0, st>>>(p->n, p->elem, W.ge,
-                                                                                          params->dt, p->uf, p->vf));
+    PDF_KERNEL("k_press_correct", st, k_press_correct<float><<<pb, 256, 0, st>>>(p->n, p->elem, W.gc, p->uf, p->vf));
   s = press_gradient(p, st);
   if (s != PDF_OK) return s;
-  s = estimate_stats(p, st);
+  PDF_KERNEL("k_press_shift_stats", st, k_press_shift_stats<<<pblocks(M.n_tri), 256, 0, st>>>(M.n_tri, W.ge, params->dt,
+                                                                                                p->es));
+  s = node_stats_from_elements(p, st);
   if (s != PDF_OK) return s;
-  if (rn > rtol * bn && bn > 0.0) return fail(PDF_ENOTCONV, "pdf_pressure_project: not converged");
+  if (!converged) return fail(PDF_ENOTCONV, "pdf_pressure_project: not converged");
   return PDF_OK;
 }
 

@@ -33,6 +33,15 @@ cudaEvent_t take_event() {
 }
 }  // namespace
 
+bool prof_timing() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_on;
+}
+
+void prof_count(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+long long prof_launches() { return g_launches.load(std::memory_order_relaxed); }
+
 void prof_launch(const char* name, cudaStream_t st, void (*launch)(void*), void* ctx) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (!launch) return;

@@ -719,6 +719,19 @@ static pdf_status reorder_state(pdf_particles* P, cudaStream_t st) {
 
 pdf_status iecm_cond(pdf_particles* P, const int32_t* seg, const int32_t* order, cudaStream_t st);
 
+// Node statistics and node derivatives from the element statistics P->es
+// (sec. 3.3 second pass, sec. 3.4).
+pdf_status node_stats_from_elements(pdf_particles* P, cudaStream_t st) {
+  const MeshDev& M = P->mesh->d;
+  PDF_KERNEL("k_node_stats", st, k_node_stats<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(M.nse_off, M.nse, M.n_nodes, P->es, P->ns,
+                                                          P->counters + 8););
+  PDF_KERNEL("k_elem_grad1", st, k_elem_grad1<<<blocks_for(M.n_tri, 128), 128, 0, st>>>(M.tri, M.dN, M.n_tri, P->ns, P->eg););
+  PDF_KERNEL("k_node_grad1", st, k_node_grad1<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(M.nse_off, M.nse, M.n_nodes, P->eg, P->nd););
+  PDF_KERNEL("k_elem_grad2", st, k_elem_grad2<<<blocks_for(M.n_tri, 128), 128, 0, st>>>(M.tri, M.dN, M.n_tri, P->nd, P->eg););
+  PDF_KERNEL("k_node_grad2", st, k_node_grad2<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(M.nse_off, M.nse, M.n_nodes, P->eg, P->nd););
+  return PDF_OK;
+}
+
 pdf_status estimate_stats(pdf_particles* P, cudaStream_t st) {
   const MeshDev& M = P->mesh->d;
   pdf_status s = group_by_element(P, st);
@@ -734,12 +747,8 @@ pdf_status estimate_stats(pdf_particles* P, cudaStream_t st) {
   else
     PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<float><<<blocks_for((int64_t)M.n_tri * 32, kStatWarps * 32), kStatWarps * 32, 0, st>>>(
         P->seg, P->sorted_pid, M.n_tri, P->uf, P->vf, P->wf, P->omf, P->psf, P->es));
-  PDF_KERNEL("k_node_stats", st, k_node_stats<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(M.nse_off, M.nse, M.n_nodes, P->es, P->ns,
-                                                          P->counters + 8););
-  PDF_KERNEL("k_elem_grad1", st, k_elem_grad1<<<blocks_for(M.n_tri, 128), 128, 0, st>>>(M.tri, M.dN, M.n_tri, P->ns, P->eg););
-  PDF_KERNEL("k_node_grad1", st, k_node_grad1<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(M.nse_off, M.nse, M.n_nodes, P->eg, P->nd););
-  PDF_KERNEL("k_elem_grad2", st, k_elem_grad2<<<blocks_for(M.n_tri, 128), 128, 0, st>>>(M.tri, M.dN, M.n_tri, P->nd, P->eg););
-  PDF_KERNEL("k_node_grad2", st, k_node_grad2<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(M.nse_off, M.nse, M.n_nodes, P->eg, P->nd););
+  s = node_stats_from_elements(P, st);
+  if (s != PDF_OK) return s;
   P->have_stats = true;
   return iecm_cond(P, P->seg, P->sorted_pid, st);
 }
@@ -804,12 +813,8 @@ pdf_status estimate_stats_with_buffers(pdf_particles* P, int32_t* keys_a, int32_
   else
     PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<float><<<blocks_for((int64_t)M.n_tri * 32, kStatWarps * 32), kStatWarps * 32, 0, st>>>(
                                        seg, vin, M.n_tri, P->uf, P->vf, P->wf, P->omf, P->psf, P->es));
-  PDF_KERNEL("k_node_stats", st, k_node_stats<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(
-                                     M.nse_off, M.nse, M.n_nodes, P->es, P->ns, P->counters + 8));
-  PDF_KERNEL("k_elem_grad1", st, k_elem_grad1<<<blocks_for(M.n_tri, 128), 128, 0, st>>>(M.tri, M.dN, M.n_tri, P->ns, P->eg));
-  PDF_KERNEL("k_node_grad1", st, k_node_grad1<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(M.nse_off, M.nse, M.n_nodes, P->eg, P->nd));
-  PDF_KERNEL("k_elem_grad2", st, k_elem_grad2<<<blocks_for(M.n_tri, 128), 128, 0, st>>>(M.tri, M.dN, M.n_tri, P->nd, P->eg));
-  PDF_KERNEL("k_node_grad2", st, k_node_grad2<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(M.nse_off, M.nse, M.n_nodes, P->eg, P->nd));
+  pdf_status s = node_stats_from_elements(P, st);
+  if (s != PDF_OK) return s;
   P->have_stats = true;
   return iecm_cond(P, seg, vin, st);
 }
