@@ -381,6 +381,8 @@ def run_gpu(args):
                                "warm_previous_step": {"iterations_max": max(it_warm), "seconds": t_warm}}
         del gq
         line["iecm"] = run_iecm(pg, torch, stream, gm, cfg, seed, psi, p, max(5, min(args.steps, 20)))
+        line["pressure_projection"] = run_projection(pg, torch, stream, gm, cfg, seed, psi, p,
+                                                     max(5, min(args.steps, 20)))
     if not args.no_cpu_baseline and world == 1:
         try:
             line["cpu_baseline"] = cpu_baseline_measure(3)
@@ -425,6 +427,50 @@ def run_iecm(pg, torch, stream, gm, cfg, seed, psi, p, steps, bins=(5, 5, 5)):
     return {"value": gm_particles(cfg) / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "bins": list(bins), "m_min": 2, "k_iecm_cond_ms": t / c if c else None,
             "what": "IECM micromixing (eq. IECM) with sort-and-divide conditioning at every statistics call"}
+
+
+def run_projection(pg, torch, stream, gm, cfg, seed, psi, p, steps, rtol=1e-8, Cp=5e-4):
+    """Steps of the benchmark workload with the stabilised mean-pressure
+    projection after every step (eqs. velocity-prediction, pressure-
+    projection-smooth, velocity-correction): the drift sees Pi - grad <P'>,
+    the Poisson system is solved to rtol, particles are corrected.  C_p =
+    dt / 2 (C_p = dt lets the discrete pressure mode grow)."""
+    gj = pg.Particles(gm, seed, ppe=cfg["ppe"], u_sigma=cfg["u_sigma"], elem_psi0=psi)
+    pj = pg.model_params(dt=p.dt, nu=p.nu, Pi=p.Pi, closure=cfg["closure"], pressure="projection")
+    pg.pdf_estimate_stats(gj, gm)
+    t0 = time.perf_counter()
+    pg.pdf_pressure_project(gj, gm, pj, Cp=Cp, rtol=rtol, max_it=2000)
+    setup_s = time.perf_counter() - t0
+    for s in range(3):
+        pg.pdf_step(gj, gm, pj, step=s)
+        pg.pdf_estimate_stats(gj, gm)
+        pg.pdf_pressure_project(gj, gm, pj, Cp=Cp, rtol=rtol, max_it=2000)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2 = torch.cuda.Event(enable_timing=True)
+    its = []
+    proj_ms = 0.0
+    e0.record(stream)
+    for s in range(steps):
+        pg.pdf_step(gj, gm, pj, step=3 + s, stream=stream)
+        pg.pdf_estimate_stats(gj, gm, stream=stream)
+        e1.record(stream)
+        it, _ = pg.pdf_pressure_project(gj, gm, pj, Cp=Cp, rtol=rtol, max_it=2000, stream=stream)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        proj_ms += e1.elapsed_time(e2)
+        its.append(it)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    pres = pg.pdf_pressure_field(gj, gm)
+    del gj
+    return {"value": gm_particles(cfg) / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "projection_ms": proj_ms / steps, "iterations": [min(its), max(its)], "rtol": rtol, "Cp": Cp,
+            "n_unknowns": gm.n_nodes - int(cfg["ny"]), "setup_seconds_first_call": setup_s,
+            "pressure_range": [float(pres.min()), float(pres.max())],
+            "what": "step + statistics + pressure projection (multigrid-preconditioned CG, FP64) per step"}
 
 
 def gm_particles(cfg):

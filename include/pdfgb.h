@@ -380,7 +380,12 @@ pdf_status pdf_mesh_wall_distance(const pdf_mesh* m, double* dist, double* norma
  * PDF_PRESSURE_PROJECTION steps, and the statistics follow the correction
  * (element means shifted by the same vector, central moments and conditional
  * means unchanged; node statistics and derivatives recomputed).
- *   Cp       the stabilisation constant C_p (the paper suggests 1e-3)
+ *   Cp       the stabilisation constant C_p, a time (the paper suggests 1e-3
+ *            in its units).  The pressure mode of this discretisation is
+ *            multiplied each step by about 1 - C_p/dt - lambda, lambda in
+ *            [0, ~1.2] the ratio of the drift's averaged-gradient Laplacian
+ *            to K: C_p/dt near 0.5 damps it, C_p/dt = 1 lets it grow, and
+ *            C_p/dt -> 0 leaves the statistical noise undamped.
  *   rtol     stop when ||r|| <= rtol ||b||; PDF_ENOTCONV after max_it
  *   iters, rel_res  host or NULL
  * Synchronizes `stream` once per 8 iterations.  PDF_ESTATE without

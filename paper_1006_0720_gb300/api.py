@@ -233,10 +233,12 @@ def pdf_profile_enable(on=True):
     check(lib().pdf_profile_enable(1 if on else 0), "pdf_profile_enable")
 
 
-def pdf_pressure_project(particles, mesh, params, Cp=1e-3, rtol=1e-10, max_it=20000, stream=None):
+def pdf_pressure_project(particles, mesh, params, Cp=None, rtol=1e-10, max_it=20000, stream=None):
     """Stabilised pressure projection after a step's statistics; returns
     (iterations, relative residual).  The particles' velocities are corrected
-    and the statistics estimated again."""
+    and the statistics follow.  Cp defaults to dt / 2."""
+    if Cp is None:
+        Cp = 0.5 * params.dt
     it = ctypes.c_int32()
     res = ctypes.c_double()
     check(lib().pdf_pressure_project(particles.handle, mesh.handle, ctypes.byref(params), float(Cp), float(rtol),

@@ -143,3 +143,42 @@ def test_not_converged_is_reported():
     with pytest.raises(capi.PdfError) as err:
         pg.pdf_pressure_project(gp, gm, p, Cp=1e-3, rtol=1e-14, max_it=2)
     assert err.value.status == capi.PDF_ENOTCONV
+
+
+def test_projection_on_the_obstacle_mesh():
+    """Graded mesh with three obstacles (wall edges on every obstacle side,
+    inflow/outflow twins one unknown): the projection and the next step with
+    its pressure gradient match the oracle."""
+    cfg = inputs.OBSTACLES["obstacles_small_mean20"]
+    m = inputs.obstacle_mesh(h_min=cfg["h_min"], ratio=cfg["ratio"], growth=cfg["growth"])
+    counts = inputs.counts_by_area(m, cfg["mean_ppe"])
+    gm = pg.Mesh(m)
+    gp = pg.Particles(gm, cfg["seed"], count=counts, u_profile=cfg["u_profile"], u_sigma=cfg["u_sigma"])
+    M = oracle.Mesh(m)
+    ost = oracle.init(M, counts, cfg["seed"], u_profile=cfg["u_profile"], u_sigma=cfg["u_sigma"])
+    p = pg.model_params(dt=cfg["dt"], nu=cfg["nu"], Pi=cfg["Pi"], closure=cfg["closure"], tm_mode=cfg["tm_mode"],
+                        src_x=cfg["src"][0], src_y=cfg["src"][1], src_r=cfg["src"][2], pressure="projection")
+    po = oracle.make_params(dt=p.dt, nu=p.nu, Pi=p.Pi, closure=cfg["closure"], tm_mode="source",
+                            pressure="projection", src=cfg["src"])
+    n = gm.n_nodes
+    pg.pdf_estimate_stats(gp, gm)
+    _, ns, nd, _ = oracle.statistics(M, ost)
+    it, res = pg.pdf_pressure_project(gp, gm, p, Cp=1e-3, rtol=1e-13, max_it=5000)
+    assert res <= 1e-13
+    dP, pres, G, gradP = OP.project(m, ns, nd, ost, np.zeros(n), np.zeros(n), p.nu, p.dt, 1e-3,
+                                    cfg["closure"] == "slm")
+    assert np.abs(G).max() > 0
+    assert_field_close(pg.pdf_pressure_field(gp, gm).cpu().numpy(), pres, "obstacle pressure", rtol=1e-9)
+    st = _host(gp.get_state())
+    for key in ("u", "v"):
+        assert_field_close(st[key], ost[key], "obstacle corrected %s" % key, rtol=1e-10)
+    _, ns, nd, _ = oracle.statistics(M, ost, ns)
+    rows = oracle.elem_coeff(M, ns, nd, po, grad_p=gradP)
+    assert_field_close(pg.pdf_elem_coeff(gp, gm, p).cpu().numpy(), rows, "obstacle rows with grad <P'>", rtol=1e-9)
+    cnt, status = oracle.step(M, rows, po, cfg["seed"], 0, ost)
+    pg.pdf_step(gp, gm, p, step=0)
+    st = _host(gp.get_state())
+    same = st["elem"] == ost["elem"]
+    assert np.all(same | ((status & oracle.TRK_NEAR_FACE) != 0))
+    for key in KEYS:
+        assert_field_close(st[key][same], ost[key][same], "obstacle projection step %s" % key)

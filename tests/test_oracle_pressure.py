@@ -202,3 +202,36 @@ def test_projection_drift_in_the_coefficients():
         assert np.isclose(c[9], 1.5) and np.isclose(c[10], 0.25)
         c0 = oracle.node_coeff(S, Dv, None, pj)
         assert np.isclose(c0[9], 2.0) and c0[10] == 0.0
+
+
+def _coupled_run(Cp, steps=25):
+    """Steps of the small channel with the projection after every step
+    (eqs. velocity-prediction, pressure-projection-smooth, velocity-
+    correction), all in the oracle."""
+    m = inputs.channel_mesh(14, 24, seed=1)
+    M = oracle.Mesh(m)
+    n_tri, n = len(m["tri"]), len(m["xy"])
+    st = oracle.init(M, np.full(n_tri, 30, dtype=np.int32), 1, u_sigma=0.1)
+    dt, nu = 1e-3, 1e-3
+    po = oracle.make_params(dt=dt, nu=nu, Pi=2 * nu, closure="glm", pressure="projection")
+    _, ns, nd, _ = oracle.statistics(M, st)
+    pres, G, gradP = np.zeros(n), np.zeros(n), np.zeros((n, 2))
+    v0 = st["v"].std()
+    dPs = []
+    for s in range(steps):
+        oracle.step(M, oracle.elem_coeff(M, ns, nd, po, grad_p=gradP), po, 1, s, st)
+        _, ns, nd, _ = oracle.statistics(M, st, ns)
+        dP, pres, G, gradP = OP.project(m, ns, nd, st, pres, G, nu, dt, Cp, False)
+        _, ns, nd, _ = oracle.statistics(M, st, ns)
+        dPs.append(np.abs(dP).max())
+    return np.array(dPs), st["v"].std() / v0
+
+
+def test_coupled_projection_stability_depends_on_cp_over_dt():
+    """The reading of C_p as a time: with C_p = dt / 2 the coupled scheme
+    stays bounded (the increments shrink, the cross-stream fluctuations keep
+    their size), with C_p = dt the discrete pressure mode grows each step."""
+    d, vr = _coupled_run(5e-4)
+    assert d[-5:].max() < d[0] and 0.9 < vr < 1.05
+    d, vr = _coupled_run(1e-3)
+    assert d[-1] > 100 * d[0]
