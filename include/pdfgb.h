@@ -78,8 +78,13 @@ enum { PDF_TM_TURB = 0, PDF_TM_CPHI = 1, PDF_TM_SOURCE = 2 };
 /* Mean pressure gradient in the velocity prediction: NONE (0); CHANNEL,
  * -d<P>/dx = Pi and -d<P>/dy = d<vv>/dy (the channel's cross-stream
  * balance); PROJECTION, -d<P>/dx_i = Pi delta_i1 - d<P'>/dx_i with <P'> the
- * nodal field of pdf_pressure_project (zero until its first call). */
-enum { PDF_PRESSURE_NONE = 0, PDF_PRESSURE_CHANNEL = 1, PDF_PRESSURE_PROJECTION = 2 };
+ * nodal field of pdf_pressure_project (zero until its first call), periodic
+ * in x; PROJECTION_INOUT, -d<P>/dx_i = -d<P>/dx_i of the projected field,
+ * which carries the imposed drop Pi L_x between the inflow and the outflow
+ * through their Dirichlet condition (the street canyon's inflow/outflow
+ * condition; see pdf_pressure_project). */
+enum { PDF_PRESSURE_NONE = 0, PDF_PRESSURE_CHANNEL = 1, PDF_PRESSURE_PROJECTION = 2,
+       PDF_PRESSURE_PROJECTION_INOUT = 3 };
 enum { PDF_MIX_IEM = 0, PDF_MIX_IECM = 1 };
 /* How the FP64-accurate particle step is computed.  FX (default): no FP64
  * instructions on the fast path -- positions in 64-bit fixed point (exact

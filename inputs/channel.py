@@ -13,8 +13,11 @@ Layout:
     only, with the same draw for both twins (keyed by j); corners are fixed.
   * quad q = j*(nx-1) + i is split along its shorter diagonal (tie: the
     (i,j)-(i+1,j+1) diagonal) into triangles 2q and 2q+1, both counter-clockwise.
-  * boundary edges carry a tag: TAG_WALL on y = -1 and y = +1, TAG_PERIODIC on
-    the two seams.
+  * boundary edges carry a tag: TAG_WALL on y = -1 and y = +1 (wall_tag
+    overrides it), TAG_PERIODIC on the two seams, or with inout=True
+    TAG_INFLOW at x = 0 and TAG_OUTFLOW at x = period (the twins then pair
+    the two ends for the particles, and the mean pressure takes the
+    inflow/outflow condition).
 """
 import numpy as np
 
@@ -25,7 +28,7 @@ TAG_OUTFLOW = 4
 TAG_NOSLIP = 5
 
 
-def channel_mesh(nx, ny, jitter=0.2, seed=1, period=2.0 * np.pi, y0=-1.0, y1=1.0, wall_tag=None):
+def channel_mesh(nx, ny, jitter=0.2, seed=1, period=2.0 * np.pi, y0=-1.0, y1=1.0, wall_tag=None, inout=False):
     if nx < 3 or ny < 2:
         raise ValueError("channel_mesh needs nx >= 3 and ny >= 2")
     dx = period / (nx - 1)
@@ -80,9 +83,10 @@ def channel_mesh(nx, ny, jitter=0.2, seed=1, period=2.0 * np.pi, y0=-1.0, y1=1.0
         bnd.append((i, i + 1, wtag))
         top = (ny - 1) * nx
         bnd.append((top + i, top + i + 1, wtag))
+    left, right = (TAG_INFLOW, TAG_OUTFLOW) if inout else (TAG_PERIODIC, TAG_PERIODIC)
     for j in range(ny - 1):
-        bnd.append((j * nx, (j + 1) * nx, TAG_PERIODIC))
-        bnd.append((j * nx + nx - 1, (j + 1) * nx + nx - 1, TAG_PERIODIC))
+        bnd.append((j * nx, (j + 1) * nx, left))
+        bnd.append((j * nx + nx - 1, (j + 1) * nx + nx - 1, right))
     bnd = np.asarray(bnd, dtype=np.int32)
     return {
         "xy": np.ascontiguousarray(xy),

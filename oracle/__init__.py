@@ -30,7 +30,7 @@ NCOEF = 26
 
 CLOSURE = {"glm": 0, "slm": 1}
 TM_MODE = {"turb": 0, "cphi": 1, "source": 2}
-PRESSURE = {"none": 0, "channel": 1, "projection": 2}
+PRESSURE = {"none": 0, "channel": 1, "projection": 2, "projection_inout": 3}
 
 TRK_FALLBACK, TRK_BRUTE, TRK_LOST, TRK_EXIT_OUT, TRK_EXIT_IN, TRK_REINJECT, TRK_NEAR_FACE = 1, 2, 4, 8, 16, 32, 256
 TRK_NOSLIP = 64     # the no-slip wall condition was applied

@@ -746,7 +746,7 @@ void or_node_derivs(const or_mesh* m, const double* ns, double* nd) {
 /* ------------------------------------------------------------------------ */
 enum { OR_CLOSURE_GLM = 0, OR_CLOSURE_SLM = 1 };
 enum { OR_TM_TURB = 0, OR_TM_CPHI = 1 };
-enum { OR_PRESSURE_NONE = 0, OR_PRESSURE_CHANNEL = 1, OR_PRESSURE_PROJECTION = 2 };
+enum { OR_PRESSURE_NONE = 0, OR_PRESSURE_CHANNEL = 1, OR_PRESSURE_PROJECTION = 2, OR_PRESSURE_PROJECTION_INOUT = 3 };
 
 enum { OR_TM_SOURCE = 2 };
 typedef struct {
@@ -809,7 +809,8 @@ void or_relax_rhs(const double* S /*12 node stats*/, const double* D /*node deri
  * frequency (SLM).  Mean pressure (READING for the periodic channel, sec.
  * 4.2.1): -d<P>/dx = Pi imposed, -d<P>/dy = d<v^2>/dy; with the pressure
  * projection (sec. 3.2): -d<P>/dx_i = Pi delta_i1 - gp_i, gp the nodal
- * gradient of the projected field (NULL: zero).
+ * gradient of the projected field (NULL: zero); with the inflow/outflow
+ * condition of the canyon -d<P>/dx_i = -gp_i.
  * wp: the 9 node values of the elliptic-relaxation tensor, or NULL for the
  * local model (wp = right-hand side, elliptic term dropped). */
 void or_node_coeff(const double* S, const double* D, const double* wp_in, const or_params* P,
@@ -825,6 +826,10 @@ void or_node_coeff(const double* S, const double* D, const double* wp_in, const 
   if (P->pressure == OR_PRESSURE_CHANNEL) { dpx = P->Pi; dpy = D[9]; }
   if (P->pressure == OR_PRESSURE_PROJECTION) {
     dpx = P->Pi - (gp ? gp[0] : 0.0);
+    dpy = -(gp ? gp[1] : 0.0);
+  }
+  if (P->pressure == OR_PRESSURE_PROJECTION_INOUT) {  /* the drop comes through the field */
+    dpx = -(gp ? gp[0] : 0.0);
     dpy = -(gp ? gp[1] : 0.0);
   }
   if (P->closure == OR_CLOSURE_SLM) {

@@ -36,9 +36,16 @@ READINGS (the paper states the equations, not their discretisation):
   * the pressure gradient the velocity prediction sees at a node is the mean
     of the gradients of the elements around it (the element-to-node transfer
     of sec. 3.3), periodic twins merged;
-  * periodic twin nodes are one unknown.
-The linear system is solved by scipy's sparse direct solver with one unknown
-pinned (a library primitive); the oracle does not iterate.
+  * periodic twin nodes are one unknown;
+  * with the street canyon's inflow/outflow condition (the section on the
+    canyon's boundary conditions) the inflow and outflow twins are separate
+    unknowns with the Dirichlet values dP = Pi L_x - <vv> - <P'>^n
+    (inflow) and -<vv> - <P'>^n (outflow), Pi = -Delta P the imposed
+    -d<P>/dx and L_x the x-period; the system is then regular (no mean
+    removal, no normalisation) and the drift takes the whole gradient of
+    the projected field (no separate Pi).
+The linear system is solved by scipy's sparse direct solver (one unknown
+pinned for the singular system); the oracle does not iterate.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -47,13 +54,27 @@ import scipy.sparse.linalg as spla
 WALL_TAGS = (1, 5)  # WALL, NO-SLIP
 
 
-def _rep(mesh):
+def inout_nodes(mesh):
+    """Per node: 1 on an INFLOW edge, 2 on an OUTFLOW edge, else 0."""
+    io = np.zeros(len(mesh["xy"]), dtype=np.int64)
+    for a, b, tag in mesh["bnd"]:
+        if tag in (3, 4):
+            io[a] = io[b] = 1 if tag == 3 else 2
+    return io
+
+
+def _rep(mesh, inout=False):
+    """Representative node of every node: periodic twins merged (with
+    inout=True, except the inflow/outflow pairs)."""
     n = len(mesh["xy"])
     rep = np.arange(n)
     twin = mesh.get("twin")
     if twin is not None:
         t = np.asarray(twin)
         m = t >= 0
+        if inout:
+            io = inout_nodes(mesh)
+            m &= ~((io != 0) & (io[np.maximum(t, 0)] != 0))
         rep[m] = np.minimum(np.arange(n)[m], t[m])
     return rep
 
@@ -79,11 +100,11 @@ def element_gradient(mesh, f):
     return np.einsum("eki,ei->ek", g, fv)
 
 
-def stiffness(mesh):
+def stiffness(mesh, inout=False):
     """K over the unknowns (twins merged) as a sparse matrix indexed by node
     id (rows and columns of non-representative nodes are empty)."""
     A, g = shape_gradients(mesh)
-    rep = _rep(mesh)
+    rep = _rep(mesh, inout)
     tri = mesh["tri"]
     n = len(mesh["xy"])
     rows, cols, vals = [], [], []
@@ -95,13 +116,13 @@ def stiffness(mesh):
     return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
 
 
-def divergence_load(mesh, ns):
+def divergence_load(mesh, ns, inout=False):
     """d_a = int N_a div <U> [n_nodes] (on representative nodes), <U>, <V>
     the nodal means of node statistics ns: div is constant on an element and
     int_e N_a = A_e / 3."""
     A, _ = shape_gradients(mesh)
     div = element_gradient(mesh, ns[:, 0])[:, 0] + element_gradient(mesh, ns[:, 1])[:, 1]
-    rep = _rep(mesh)
+    rep = _rep(mesh, inout)
     d = np.zeros(len(mesh["xy"]))
     for a in range(3):
         np.add.at(d, rep[mesh["tri"][:, a]], A * div / 3.0)
@@ -147,9 +168,9 @@ def wall_data(mesh, ns, nd, e, a, b, nu, slm):
     return hx, hy
 
 
-def wall_load(mesh, ns, nd, nu, slm=False):
+def wall_load(mesh, ns, nd, nu, slm=False, inout=False):
     """G_a = int_wall N_a h ds [n_nodes] (on representative nodes)."""
-    rep = _rep(mesh)
+    rep = _rep(mesh, inout)
     G = np.zeros(len(mesh["xy"]))
     for a, b, e, nx, ny, L in wall_edges(mesh):
         hx, hy = wall_data(mesh, ns, nd, e, a, b, nu, slm)
@@ -173,32 +194,47 @@ def nodal_gradient(mesh, f):
     return s[rep] / np.maximum(c[rep], 1.0)[:, None]
 
 
-def solve_increment(mesh, ns, nd, pres, G_prev, nu, dt, Cp, slm=False):
-    """dP [n_nodes] (zero mean over the unknowns) and G^{n+1} [n_nodes]."""
+def solve_increment(mesh, ns, nd, pres, G_prev, nu, dt, Cp, slm=False, inout=False, Pi=0.0):
+    """dP [n_nodes] and G^{n+1} [n_nodes]: zero mean over the unknowns for
+    the periodic system; with inout=True the inflow/outflow Dirichlet
+    values at those nodes."""
     n = len(mesh["xy"])
-    rep = _rep(mesh)
+    rep = _rep(mesh, inout)
     idx = np.nonzero(rep == np.arange(n))[0]
-    K = stiffness(mesh)
-    d = divergence_load(mesh, ns)
-    G = wall_load(mesh, ns, nd, nu, slm)
+    K = stiffness(mesh, inout)
+    d = divergence_load(mesh, ns, inout)
+    G = wall_load(mesh, ns, nd, nu, slm, inout)
     Pn = np.asarray(pres, dtype=np.float64)[rep]
     b = -(d + Cp * (K @ Pn - G_prev)) / dt + G - G_prev
-    b_u = b[idx]
-    b_u = b_u - b_u.mean()
-    Ku = K[idx][:, idx].tocsc()
-    x = np.zeros(len(idx))
-    x[1:] = spla.spsolve(Ku[1:, 1:], b_u[1:])   # unknown 0 pinned to 0
-    x -= x.mean()
+    if not inout:
+        b_u = b[idx]
+        b_u = b_u - b_u.mean()
+        Ku = K[idx][:, idx].tocsc()
+        x = np.zeros(len(idx))
+        x[1:] = spla.spsolve(Ku[1:, 1:], b_u[1:])   # unknown 0 pinned to 0
+        x -= x.mean()
+        full = np.zeros(n)
+        full[idx] = x
+        return full[rep], G
+    io = inout_nodes(mesh)
+    Lx = float(mesh["period"])
+    g = np.where(io == 1, Pi * Lx, 0.0) - ns[:, 6] - np.asarray(pres, dtype=np.float64)
+    D = idx[io[idx] != 0]
+    F = idx[io[idx] == 0]
+    Kc = K.tocsr()
+    rhs = b[F] - Kc[F][:, D] @ g[D]
     full = np.zeros(n)
-    full[idx] = x
+    full[F] = spla.spsolve(Kc[F][:, F].tocsc(), rhs)
+    full[D] = g[D]
+    G[D] = 0.0
     return full[rep], G
 
 
-def project(mesh, ns, nd, st, pres, G_prev, nu, dt, Cp, slm=False):
+def project(mesh, ns, nd, st, pres, G_prev, nu, dt, Cp, slm=False, inout=False, Pi=0.0):
     """One projection after a predicted step: returns (dP, pres_new, G_new,
     gradP_nodal) and corrects the particle velocities st["u"], st["v"] in
     place (eq. velocity-correction)."""
-    dP, G = solve_increment(mesh, ns, nd, pres, G_prev, nu, dt, Cp, slm)
+    dP, G = solve_increment(mesh, ns, nd, pres, G_prev, nu, dt, Cp, slm, inout, Pi)
     ge = element_gradient(mesh, dP)
     el = st["elem"]
     st["u"] = st["u"] - dt * ge[el, 0]

@@ -39,7 +39,7 @@ def model_params(**kw):
     p = capi.ModelParams()
     lib().pdf_model_params_default(ctypes.byref(p))
     names = {"closure": {"glm": 0, "slm": 1, "frozen": 2}, "tm_mode": {"turb": 0, "cphi": 1, "source": 2},
-             "pressure": {"none": 0, "channel": 1, "projection": 2}, "arith": {"fx": 0, "fp64": 1}, "mix": {"iem": 0, "iecm": 1}}
+             "pressure": {"none": 0, "channel": 1, "projection": 2, "projection_inout": 3}, "arith": {"fx": 0, "fp64": 1}, "mix": {"iem": 0, "iecm": 1}}
     for k, v in kw.items():
         if k in names and isinstance(v, str):
             v = names[k][v]

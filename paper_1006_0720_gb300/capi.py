@@ -11,7 +11,7 @@ STATUS_NAMES = ["PDF_OK", "PDF_EINVAL", "PDF_ENOMEM", "PDF_ECUDA", "PDF_ELOST", 
 PDF_TAG_WALL, PDF_TAG_PERIODIC, PDF_TAG_INFLOW, PDF_TAG_OUTFLOW = 1, 2, 3, 4
 PDF_CLOSURE_GLM, PDF_CLOSURE_SLM, PDF_CLOSURE_FROZEN = 0, 1, 2
 PDF_TM_TURB, PDF_TM_CPHI, PDF_TM_SOURCE = 0, 1, 2
-PDF_PRESSURE_NONE, PDF_PRESSURE_CHANNEL = 0, 1
+PDF_PRESSURE_NONE, PDF_PRESSURE_CHANNEL, PDF_PRESSURE_PROJECTION, PDF_PRESSURE_PROJECTION_INOUT = 0, 1, 2, 3
 PDF_FP64, PDF_FP32_STATE = 0, 1
 PDF_ARITH_FX, PDF_ARITH_FP64 = 0, 1
 PDF_NCOEF, PDF_NES, PDF_NNS, PDF_NND = 26, 13, 12, 10

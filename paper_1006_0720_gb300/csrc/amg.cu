@@ -9,8 +9,9 @@
 // constant vector (the null space of the pure-Neumann matrix), smoothed
 // prolongation P = (I - w_p D^-1 A) P_tent with w_p = 4 / (3 rho(D^-1 A)),
 // Galerkin coarse matrices A_c = P^T A P, down to a dense coarsest matrix
-// whose regularised inverse (A_c + mean(diag) 1 1^T / n_c)^-1 solves every
-// compatible right-hand side exactly.
+// whose inverse (for a singular matrix with constant null space the
+// regularised (A_c + mean(diag) 1 1^T / n_c)^-1, which solves every
+// compatible right-hand side exactly) is applied directly.
 //
 // One V-cycle with one damped-Jacobi sweep (W = w_s D^-1) before and after
 // the coarse correction is, per level,
@@ -189,7 +190,7 @@ void amg_free(Amg& G) {
 }
 
 pdf_status amg_setup(int32_t n, const std::vector<int32_t>& rp, const std::vector<int32_t>& ci,
-                     const std::vector<double>& v, Amg& G) {
+                     const std::vector<double>& v, bool singular, Amg& G) {
   constexpr int32_t kCoarse = 256, kMaxLevels = 12;
   HCsr A;
   A.n = A.m = n;
@@ -272,7 +273,8 @@ pdf_status amg_setup(int32_t n, const std::vector<int32_t>& rp, const std::vecto
     }
   dmean = nc > 0 ? dmean / nc : 1.0;
   if (!(dmean > 0.0)) dmean = 1.0;
-  for (size_t k = 0; k < B.size(); ++k) B[k] += dmean / nc;
+  if (singular)
+    for (size_t k = 0; k < B.size(); ++k) B[k] += dmean / nc;
   for (int32_t i = 0; i < nc; ++i) Inv[(size_t)i * nc + i] = 1.0;
   for (int32_t c = 0; c < nc; ++c) {
     int32_t piv = c;

@@ -26,10 +26,11 @@ struct Amg {
   double *cb = nullptr, *cz = nullptr;
 };
 
-// Builds the hierarchy of the symmetric positive semi-definite CSR matrix
-// (n rows, columns sorted, constant null space) and uploads it.
+// Builds the hierarchy of the symmetric CSR matrix (n rows, columns
+// sorted; positive definite, or with singular = true positive semi-definite
+// with the constants as null space) and uploads it.
 pdf_status amg_setup(int32_t n, const std::vector<int32_t>& rp, const std::vector<int32_t>& ci,
-                     const std::vector<double>& v, Amg& G);
+                     const std::vector<double>& v, bool singular, Amg& G);
 void amg_free(Amg& G);
 // z = M^-1 r (one V-cycle); part receives the block partials of r . z
 // (blocks of 256 rows) when the hierarchy has a level, else nothing.  Every

@@ -121,23 +121,39 @@ struct RelaxWork {
   int32_t* active = nullptr;
 };
 void relax_free(RelaxWork& W);
-// The pressure projection's work space (allocated on first use).
+// One linear system of the pressure projection: its unknowns (periodic
+// twins merged; with inflow/outflow conditions the inflow and outflow twins
+// stay apart and are Dirichlet unknowns), the stiffness matrix K (kval) and
+// the matrix the iteration uses (kmask: Dirichlet rows and columns replaced
+// by the identity; kmask == kval without them), the wall edges at each
+// unknown, the multigrid hierarchy and the captured iteration chunk.
 struct Amg;
-struct PressWork {
-  int32_t nb = 0;
-  Amg* amg = nullptr;          // multigrid preconditioner of K
-  int32_t* ctl = nullptr;      // device: done, iterations, max_it, tol flag, block counters
-  int32_t* host_ctl = nullptr; // page-locked copy
-  double *kval = nullptr, *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr;
-  double *p = nullptr, *q = nullptr, *part = nullptr, *scal = nullptr, *dP = nullptr, *ge = nullptr;
+struct PressSys {
+  bool built = false, dirichlet = false, own = false;
+  int32_t n = 0;
+  int64_t nnz = 0;
+  int32_t *rp = nullptr, *ci = nullptr, *rep_node = nullptr, *node_rep = nullptr;
+  int32_t *pw_off = nullptr, *pw_e = nullptr;
+  double *kval = nullptr, *kmask = nullptr, *pw_n = nullptr;
+  int8_t* dir = nullptr;                     // [n] 0 free, 1 inflow, 2 outflow
   double *gw = nullptr, *gw_prev = nullptr;  // wall loads of the new and the current <P'>
-  float4* gc = nullptr;                      // per element -dt grad dP as double-float pairs
-  // a chunk of iterations captured as a CUDA graph on the library's own
-  // stream (replayed while kernel timing is off)
-  cudaStream_t cs = nullptr;
+  Amg* amg = nullptr;
   cudaGraphExec_t gx = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   long long graph_launches = 0;
+};
+// The pressure projection's work space (allocated on first use); vectors
+// are sized for n_nodes unknowns, enough for either system.
+struct PressWork {
+  PressSys sys[2];             // 0: periodic in x, 1: inflow/outflow conditions
+  int32_t last_sys = -1;
+  int32_t* ctl = nullptr;      // device: done, iterations, max_it, block counters
+  int32_t* host_ctl = nullptr; // page-locked copy
+  double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr;
+  double *p = nullptr, *q = nullptr, *part = nullptr, *scal = nullptr, *dP = nullptr, *ge = nullptr;
+  float4* gc = nullptr;        // per element -dt grad dP as double-float pairs
+  // iteration chunks run as CUDA graphs on the library's own stream
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double* host = nullptr;
 };
 void press_free(PressWork& W);
@@ -155,6 +171,11 @@ struct pdf_mesh {
   // relaxation pattern rp/ci, values sum_e A_e grad N_a . grad N_b)
   std::vector<int32_t> k_rp, k_ci;
   std::vector<double> k_v;
+  // x-period, shape-function derivatives [n_tri][6] and, per node, 1 on an
+  // INFLOW edge, 2 on an OUTFLOW edge, else 0
+  double period = 0.0;
+  std::vector<double> dN;
+  std::vector<int8_t> inout;
 };
 
 // Internal coefficient row: 32 doubles (256 B) per element.

@@ -424,6 +424,15 @@ extern "C" pdf_status pdf_mesh_create(const double* node_xy, int32_t n_nodes, co
     delete m;
     return s;
   }
+  // host data of the pressure system with inflow/outflow conditions
+  m->period = period_x;
+  m->dN = dN;
+  m->inout.assign(n_nodes, 0);
+  for (int32_t i = 0; i < n_bnd; ++i) {
+    const int32_t t = bnd_edge[3 * i + 2];
+    if (t != PDF_TAG_INFLOW && t != PDF_TAG_OUTFLOW) continue;
+    for (int q = 0; q < 2; ++q) m->inout[bnd_edge[3 * i + q]] = t == PDF_TAG_INFLOW ? 1 : 2;
+  }
   *out = m;
   return PDF_OK;
 }

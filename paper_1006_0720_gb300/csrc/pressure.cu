@@ -85,44 +85,67 @@ __device__ __forceinline__ double wall_load(const int32_t* __restrict__ ed, cons
   return (hx * nx + hy * ny) * en[2] * 0.5;
 }
 
-// b_u = -(d_u + C_p ((K <P'>)_u - G_u^n)) / dt + G_u^{n+1} - G_u^n:
-// d_u = sum over the elements around the unknown's node(s) of A_e / 3 times
-// the element divergence of the nodal <U>, <V>; G the wall load above (G^n
-// the one the current <P'> satisfies, G^{n+1} from the present statistics,
-// written to gw).  Block partials of sum b.
+// The device view of one pressure system.
+struct PSys {
+  int32_t n;
+  const int32_t *rp, *ci, *rep_node, *pw_off, *pw_e;
+  const double *kval, *pw_n;
+  const int8_t* dir;  // nullptr: no Dirichlet unknowns
+};
+
+// Dirichlet value of dP at a node of the inflow (1) or outflow (2) (the
+// street canyon's inflow/outflow condition): the target <P> there, Pi L_x
+// at the inflow, 0 at the outflow, minus <vv> of the node (the cross-stream
+// balance of an undisturbed channel), minus the current <P'>.
+__device__ __forceinline__ double dirichlet_dP(int kind, int32_t node, const double* __restrict__ ns,
+                                               const double* __restrict__ pres, double PiLx) {
+  return (kind == 1 ? PiLx : 0.0) - ns[(int64_t)node * PDF_NNS + 6] - pres[node];
+}
+
+// Free unknowns: b_u = -(d_u + C_p ((K <P'>)_u - G_u^n)) / dt + G_u^{n+1}
+// - G_u^n - sum over Dirichlet columns v of K_uv g_v, d_u = sum over the
+// elements around the unknown's node(s) of A_e / 3 times the element
+// divergence of the nodal <U>, <V>; G the wall load above (G^n the one the
+// current <P'> satisfies, G^{n+1} from the present statistics, written to
+// gw).  Dirichlet unknowns: b_u = 0 (the iteration solves for the free
+// part; the values are set afterwards).  Block partials of sum b.
 __global__ void __launch_bounds__(kPBlock) k_press_rhs(
-    int32_t n_rep, const int32_t* __restrict__ rep_node, const int32_t* __restrict__ rp,
-    const int32_t* __restrict__ ci, const double* __restrict__ kval, const int32_t* __restrict__ nse_off,
-    const int32_t* __restrict__ nse, const int32_t* __restrict__ tri, const double* __restrict__ dN,
-    const ElemGeo* __restrict__ geo, const double* __restrict__ ns, const double* __restrict__ nd,
-    const int32_t* __restrict__ pw_off, const int32_t* __restrict__ pw_e, const double* __restrict__ pw_n, double nu,
-    int slm, const double* __restrict__ pres, const double* __restrict__ gw_prev, double Cp, double inv_dt,
-    double* __restrict__ gw, double* __restrict__ b, double* __restrict__ part) {
+    PSys S, const int32_t* __restrict__ nse_off, const int32_t* __restrict__ nse, const int32_t* __restrict__ tri,
+    const double* __restrict__ dN, const ElemGeo* __restrict__ geo, const double* __restrict__ ns,
+    const double* __restrict__ nd, double nu, int slm, const double* __restrict__ pres,
+    const double* __restrict__ gw_prev, double Cp, double inv_dt, double PiLx, double* __restrict__ gw,
+    double* __restrict__ b, double* __restrict__ part) {
   const int32_t u = blockIdx.x * kPBlock + threadIdx.x;
   double bv = 0.0;
-  if (u < n_rep) {
-    const int32_t n = rep_node[u];
+  if (u < S.n && (S.dir == nullptr || S.dir[u] == 0)) {
+    const int32_t n = S.rep_node[u];
     double d = 0.0;
     for (int32_t i = nse_off[n]; i < nse_off[n + 1]; ++i) {
       const int32_t e = nse[i];
       const double* g = dN + (int64_t)e * 6;
       double div = 0.0;
       for (int j = 0; j < 3; ++j) {
-        const double* S = ns + (int64_t)tri[3 * e + j] * PDF_NNS;
-        div += g[j] * S[0] + g[3 + j] * S[1];
+        const double* Sn = ns + (int64_t)tri[3 * e + j] * PDF_NNS;
+        div += g[j] * Sn[0] + g[3 + j] * Sn[1];
       }
       d += 0.5 * geo[e].two_area / 3.0 * div;
     }
-    double kp = 0.0;
-    for (int32_t q = rp[u]; q < rp[u + 1]; ++q) kp += kval[q] * pres[rep_node[ci[q]]];
+    double kp = 0.0, lift = 0.0;
+    for (int32_t q = S.rp[u]; q < S.rp[u + 1]; ++q) {
+      const int32_t v = S.ci[q], node = S.rep_node[v];
+      kp += S.kval[q] * pres[node];
+      if (S.dir != nullptr && S.dir[v] != 0) lift += S.kval[q] * dirichlet_dP(S.dir[v], node, ns, pres, PiLx);
+    }
     double gn = 0.0;
-    for (int32_t i = pw_off[u]; i < pw_off[u + 1]; ++i)
-      gn += wall_load(pw_e + 3 * (int64_t)i, pw_n + 3 * (int64_t)i, tri, dN, ns, nd, nu, slm != 0);
+    for (int32_t i = S.pw_off[u]; i < S.pw_off[u + 1]; ++i)
+      gn += wall_load(S.pw_e + 3 * (int64_t)i, S.pw_n + 3 * (int64_t)i, tri, dN, ns, nd, nu, slm != 0);
     const double gp = gw_prev[u];
     gw[u] = gn;
-    bv = -(d + Cp * (kp - gp)) * inv_dt + (gn - gp);
-    b[u] = bv;
+    bv = -(d + Cp * (kp - gp)) * inv_dt + (gn - gp) - lift;
+  } else if (u < S.n) {
+    gw[u] = 0.0;
   }
+  if (u < S.n) b[u] = bv;
   const double s = pblock_sum(bv);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
@@ -161,9 +184,9 @@ __device__ __forceinline__ double sum_parts(const double* part, int32_t nb) {
   return pblock_sum(t);
 }
 
-// b -= mean(b); x = 0; r = b; p = 0; r.r (last block: the stopping
-// threshold rtol^2 r.r, done when r = 0).
-__global__ void __launch_bounds__(kPBlock) k_press_init(int32_t n_rep, double rtol2, int32_t max_it,
+// b -= mean(b) (the singular system only); x = 0; r = b; p = 0; r.r (last
+// block: the stopping threshold rtol^2 r.r, done when r = 0).
+__global__ void __launch_bounds__(kPBlock) k_press_init(int32_t n_rep, int singular, double rtol2, int32_t max_it,
                                                         double* __restrict__ scal,
                                                         int32_t* __restrict__ ctl, double* __restrict__ b,
                                                         double* __restrict__ x, double* __restrict__ r,
@@ -171,7 +194,7 @@ __global__ void __launch_bounds__(kPBlock) k_press_init(int32_t n_rep, double rt
   const int32_t u = blockIdx.x * kPBlock + threadIdx.x;
   double rr = 0.0;
   if (u < n_rep) {
-    const double bv = b[u] - scal[kSBsum] / (double)n_rep;
+    const double bv = singular ? b[u] - scal[kSBsum] / (double)n_rep : b[u];
     b[u] = bv;
     x[u] = 0.0;
     r[u] = bv;
@@ -288,12 +311,20 @@ __global__ void __launch_bounds__(kPBlock) k_press_xsum(int32_t n_rep, const dou
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-// dP at the nodes (zero mean over the unknowns) and <P'> += dP.
+// dP at the nodes and <P'> += dP: the Dirichlet value at inflow/outflow
+// nodes, else the solution (less its mean over the unknowns for the
+// singular system).
 __global__ void k_press_scatter(int32_t n_nodes, int32_t n_rep, const int32_t* __restrict__ node_rep,
-                                const double* __restrict__ x, const double* __restrict__ xsum,
+                                const int8_t* __restrict__ dir, const double* __restrict__ x,
+                                const double* __restrict__ xsum, const double* __restrict__ ns, double PiLx,
                                 double* __restrict__ dP, double* __restrict__ pres) {
   for (int32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < n_nodes; n += gridDim.x * blockDim.x) {
-    const double v = x[node_rep[n]] - *xsum / (double)n_rep;
+    const int32_t u = node_rep[n];
+    double v;
+    if (dir != nullptr && dir[u] != 0)
+      v = dirichlet_dP(dir[u], n, ns, pres, PiLx);
+    else
+      v = x[u] - (xsum ? *xsum / (double)n_rep : 0.0);
     dP[n] = v;
     pres[n] += v;
   }
@@ -381,97 +412,235 @@ __global__ void k_press_correct<float>(int64_t n, const int32_t* __restrict__ el
 
 static int pblocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096)); }
 
+static int32_t nblocks(int32_t n) { return (n + kPBlock - 1) / kPBlock; }
+
+// Work vectors for up to n_nodes unknowns, control words, the library's
+// stream and events.
 static pdf_status press_alloc(pdf_particles* P) {
   PressWork& W = P->pw;
   if (W.x) return PDF_OK;
   const pdf_mesh* m = P->mesh;
-  const RelaxMesh& R = m->rx;
   const int32_t nn = m->d.n_nodes, nt = m->d.n_tri;
-  W.nb = (R.n_rep + kPBlock - 1) / kPBlock;
   cudaError_t e = cudaSuccess;
   auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
-  A((void**)&W.kval, sizeof(double) * R.nnz);
-  A((void**)&W.b, sizeof(double) * R.n_rep);
-  A((void**)&W.x, sizeof(double) * R.n_rep);
-  A((void**)&W.r, sizeof(double) * R.n_rep);
-  A((void**)&W.z, sizeof(double) * R.n_rep);
-  A((void**)&W.p, sizeof(double) * R.n_rep);
-  A((void**)&W.q, sizeof(double) * R.n_rep);
-  A((void**)&W.part, sizeof(double) * 2 * W.nb);
+  A((void**)&W.b, sizeof(double) * nn);
+  A((void**)&W.x, sizeof(double) * nn);
+  A((void**)&W.r, sizeof(double) * nn);
+  A((void**)&W.z, sizeof(double) * nn);
+  A((void**)&W.p, sizeof(double) * nn);
+  A((void**)&W.q, sizeof(double) * nn);
+  A((void**)&W.part, sizeof(double) * 2 * nblocks(nn));
   A((void**)&W.scal, sizeof(double) * 16);
   A((void**)&W.dP, sizeof(double) * nn);
   A((void**)&W.ge, sizeof(double) * 2 * nt);
   A((void**)&W.gc, sizeof(float4) * nt);
-  A((void**)&W.gw, sizeof(double) * R.n_rep);
-  A((void**)&W.gw_prev, sizeof(double) * R.n_rep);
   A((void**)&W.ctl, sizeof(int32_t) * 8);
-  if (e == cudaSuccess) e = cudaMemset(W.gw_prev, 0, sizeof(double) * R.n_rep);
   if (e == cudaSuccess) e = cudaMemset(W.ctl, 0, sizeof(int32_t) * 8);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(W.kval, m->k_v.data(), sizeof(double) * R.nnz, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&W.host, sizeof(double) * 16);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&W.host_ctl, sizeof(int32_t) * 8);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&W.cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&W.ev0, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&W.ev1, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     press_free(W);
     return cuda_fail(e, "pdf_pressure_project: allocation");
   }
-  W.amg = new Amg();
-  pdf_status s = amg_setup(R.n_rep, m->k_rp, m->k_ci, m->k_v, *W.amg);
-  if (s != PDF_OK) press_free(W);
-  return s;
+  return PDF_OK;
+}
+
+static void sys_free(PressSys& S) {
+  if (S.own) {
+    cudaFree(S.rp); cudaFree(S.ci); cudaFree(S.rep_node); cudaFree(S.node_rep);
+    cudaFree(S.pw_off); cudaFree(S.pw_e); cudaFree(S.pw_n); cudaFree(S.dir); cudaFree(S.kmask);
+  }
+  cudaFree(S.kval); cudaFree(S.gw); cudaFree(S.gw_prev);
+  if (S.amg) {
+    amg_free(*S.amg);
+    delete S.amg;
+  }
+  if (S.gx) cudaGraphExecDestroy(S.gx);
+  S = PressSys();
 }
 
 void press_free(PressWork& W) {
-  cudaFree(W.kval); cudaFree(W.b); cudaFree(W.x); cudaFree(W.r); cudaFree(W.z);
+  for (PressSys& S : W.sys) sys_free(S);
+  cudaFree(W.b); cudaFree(W.x); cudaFree(W.r); cudaFree(W.z);
   cudaFree(W.p); cudaFree(W.q); cudaFree(W.part); cudaFree(W.scal); cudaFree(W.dP); cudaFree(W.ge);
-  cudaFree(W.gw); cudaFree(W.gw_prev); cudaFree(W.ctl); cudaFree(W.gc);
+  cudaFree(W.ctl); cudaFree(W.gc);
   if (W.host) cudaFreeHost(W.host);
   if (W.host_ctl) cudaFreeHost(W.host_ctl);
-  if (W.amg) {
-    amg_free(*W.amg);
-    delete W.amg;
-  }
-  if (W.gx) cudaGraphExecDestroy(W.gx);
   if (W.ev0) cudaEventDestroy(W.ev0);
   if (W.ev1) cudaEventDestroy(W.ev1);
   if (W.cs) cudaStreamDestroy(W.cs);
   W = PressWork();
 }
 
+template <typename T>
+static pdf_status up(T** dst, const std::vector<T>& src) {
+  cudaError_t e = cudaMalloc((void**)dst, std::max<size_t>(src.size(), 1) * sizeof(T));
+  if (e == cudaSuccess && !src.empty())
+    e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? PDF_OK : cuda_fail(e, "pdf_pressure_project: upload");
+}
+
+// System 0: the relaxation's unknowns (every twin pair merged), K with the
+// natural conditions, singular (constants).
+static pdf_status build_periodic(const pdf_mesh* m, PressSys& S) {
+  const RelaxMesh& R = m->rx;
+  S.own = false;
+  S.dirichlet = false;
+  S.n = R.n_rep;
+  S.nnz = R.nnz;
+  S.rp = R.rp; S.ci = R.ci; S.rep_node = R.rep_node; S.node_rep = R.node_rep;
+  S.pw_off = R.pw_off; S.pw_e = R.pw_e; S.pw_n = R.pw_n;
+  S.dir = nullptr;
+  pdf_status s = up(&S.kval, m->k_v);
+  if (s != PDF_OK) return s;
+  S.kmask = S.kval;
+  S.amg = new Amg();
+  return amg_setup(S.n, m->k_rp, m->k_ci, m->k_v, true, *S.amg);
+}
+
+// System 1: twins merged except the inflow/outflow pairs, whose nodes are
+// Dirichlet unknowns (the street canyon's inflow/outflow condition).
+static pdf_status build_inout(const pdf_mesh* m, PressSys& S) {
+  const int32_t nn = m->d.n_nodes, nt = m->d.n_tri;
+  const int32_t* T = m->tri.data();
+  const double* X = m->xy.data();
+  std::vector<int32_t> rep_of(nn), idx(nn, -1), rep_node, node_rep(nn);
+  for (int32_t n = 0; n < nn; ++n) {
+    const int32_t t = m->twin[n];
+    const bool split = t >= 0 && m->inout[n] != 0 && m->inout[t] != 0;
+    rep_of[n] = (t >= 0 && !split) ? std::min(n, t) : n;
+  }
+  for (int32_t n = 0; n < nn; ++n)
+    if (rep_of[n] == n) { idx[n] = (int32_t)rep_node.size(); rep_node.push_back(n); }
+  for (int32_t n = 0; n < nn; ++n) node_rep[n] = idx[rep_of[n]];
+  const int32_t nr = (int32_t)rep_node.size();
+  std::vector<int8_t> dir(nr);
+  int32_t n_dir = 0;
+  for (int32_t u = 0; u < nr; ++u) {
+    dir[u] = m->inout[rep_node[u]];
+    n_dir += dir[u] != 0;
+  }
+  if (n_dir == 0) return fail(PDF_EINVAL, "pdf_pressure_project: the mesh has no inflow/outflow edges");
+  // pattern and values, K_ab = sum_e A_e grad N_a . grad N_b
+  std::vector<std::vector<std::pair<int32_t, double>>> rows(nr);
+  for (int32_t e = 0; e < nt; ++e) {
+    const double* d = &m->dN[6 * (size_t)e];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        rows[node_rep[T[3 * e + a]]].push_back(
+            {node_rep[T[3 * e + b]], m->area[e] * (d[a] * d[b] + d[3 + a] * d[3 + b])});
+  }
+  std::vector<int32_t> rp(nr + 1, 0), ci;
+  std::vector<double> kv, km;
+  for (int32_t u = 0; u < nr; ++u) {
+    auto& r = rows[u];
+    std::stable_sort(r.begin(), r.end(), [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) {
+      return x.first < y.first;
+    });
+    for (size_t i = 0; i < r.size();) {
+      const int32_t c = r[i].first;
+      double v = 0.0;
+      for (; i < r.size() && r[i].first == c; ++i) v += r[i].second;
+      ci.push_back(c);
+      kv.push_back(v);
+      km.push_back(dir[u] != 0 ? (c == u ? 1.0 : 0.0) : (dir[c] != 0 ? 0.0 : v));
+    }
+    rp[u + 1] = (int32_t)ci.size();
+    if (rp[u + 1] - rp[u] > 64) return fail(PDF_EINVAL, "pdf_pressure_project: pressure row out of range");
+  }
+  // wall edges at each unknown
+  std::vector<std::vector<int32_t>> pwl(nr);
+  std::vector<int32_t> we;
+  std::vector<double> wn;
+  for (int32_t e = 0; e < nt; ++e)
+    for (int k = 0; k < 3; ++k) {
+      const int32_t c = m->nbr[3 * e + k];
+      if (c != kNbrWall && c != kNbrNoslip) continue;
+      const int32_t a = T[3 * e + (k + 1) % 3], b = T[3 * e + (k + 2) % 3];
+      const int32_t id = (int32_t)(we.size() / 3);
+      we.insert(we.end(), {e, a, b});
+      const double tx = X[2 * b] - X[2 * a], ty = X[2 * b + 1] - X[2 * a + 1];
+      const double len = std::sqrt(tx * tx + ty * ty);
+      wn.insert(wn.end(), {ty / len, -tx / len, len});
+      pwl[node_rep[a]].push_back(id);
+      pwl[node_rep[b]].push_back(id);
+    }
+  std::vector<int32_t> pw_off(nr + 1, 0), pw_e;
+  std::vector<double> pw_n;
+  for (int32_t u = 0; u < nr; ++u) {
+    pw_off[u + 1] = pw_off[u] + (int32_t)pwl[u].size();
+    for (int32_t id : pwl[u]) {
+      pw_e.insert(pw_e.end(), we.begin() + 3 * id, we.begin() + 3 * id + 3);
+      pw_n.insert(pw_n.end(), wn.begin() + 3 * id, wn.begin() + 3 * id + 3);
+    }
+  }
+  S.own = true;
+  S.dirichlet = true;
+  S.n = nr;
+  S.nnz = (int64_t)ci.size();
+  pdf_status s;
+  if ((s = up(&S.rp, rp)) != PDF_OK || (s = up(&S.ci, ci)) != PDF_OK || (s = up(&S.rep_node, rep_node)) != PDF_OK ||
+      (s = up(&S.node_rep, node_rep)) != PDF_OK || (s = up(&S.pw_off, pw_off)) != PDF_OK ||
+      (s = up(&S.pw_e, pw_e)) != PDF_OK || (s = up(&S.pw_n, pw_n)) != PDF_OK || (s = up(&S.dir, dir)) != PDF_OK ||
+      (s = up(&S.kval, kv)) != PDF_OK || (s = up(&S.kmask, km)) != PDF_OK)
+    return s;
+  S.amg = new Amg();
+  return amg_setup(nr, rp, ci, km, false, *S.amg);
+}
+
+static pdf_status sys_get(pdf_particles* P, int k, PressSys** out) {
+  PressSys& S = P->pw.sys[k];
+  if (!S.built) {
+    pdf_status s = k == 0 ? build_periodic(P->mesh, S) : build_inout(P->mesh, S);
+    if (s == PDF_OK) {
+      cudaError_t e = cudaMalloc((void**)&S.gw, sizeof(double) * std::max(S.n, 1));
+      if (e == cudaSuccess) e = cudaMalloc((void**)&S.gw_prev, sizeof(double) * std::max(S.n, 1));
+      if (e == cudaSuccess) e = cudaMemset(S.gw_prev, 0, sizeof(double) * std::max(S.n, 1));
+      if (e != cudaSuccess) s = cuda_fail(e, "pdf_pressure_project: allocation");
+    }
+    if (s != PDF_OK) {
+      sys_free(S);
+      return s;
+    }
+    S.built = true;
+  }
+  *out = &S;
+  return PDF_OK;
+}
+
+static PSys dev_view(const PressSys& S) {
+  return PSys{S.n, S.rp, S.ci, S.rep_node, S.pw_off, S.pw_e, S.kval, S.pw_n, S.dir};
+}
+
 // k preconditioned conjugate-gradient iterations (each kernel returns at
 // once after the stop).
-static pdf_status press_iterations(pdf_particles* P, int k, cudaStream_t st) {
-  PressWork& W = P->pw;
-  const RelaxMesh& R = P->mesh->rx;
-  const Amg& G = *W.amg;
-  const int nb = W.nb;
+static pdf_status press_iterations(PressWork& W, const PressSys& S, int k, cudaStream_t st) {
+  const Amg& G = *S.amg;
+  const int nb = nblocks(S.n);
   const int32_t* done = W.ctl + kCtlDone;
   for (int i = 0; i < k; ++i) {
     pdf_status s = amg_apply(G, W.r, W.z, W.part, done, st);
     if (s != PDF_OK) return s;
     if (G.lv.empty())
-      PDF_KERNEL("k_press_dot", st, k_press_dot<<<nb, kPBlock, 0, st>>>(R.n_rep, W.r, W.z, W.part, done));
+      PDF_KERNEL("k_press_dot", st, k_press_dot<<<nb, kPBlock, 0, st>>>(S.n, W.r, W.z, W.part, done));
     PDF_KERNEL("k_press_rz", st, k_press_rz<<<1, kPBlock, 0, st>>>(W.part, nb, W.scal, done));
-    PDF_KERNEL("k_press_dir", st, k_press_dir<<<pblocks(R.n_rep), 256, 0, st>>>(R.n_rep, W.scal, W.z, W.p, done));
-    PDF_KERNEL("k_press_spmv", st, k_press_spmv<<<nb, kPBlock, 0, st>>>(R.n_rep, R.rp, R.ci, W.kval, W.p, W.q, W.scal,
+    PDF_KERNEL("k_press_dir", st, k_press_dir<<<pblocks(S.n), 256, 0, st>>>(S.n, W.scal, W.z, W.p, done));
+    PDF_KERNEL("k_press_spmv", st, k_press_spmv<<<nb, kPBlock, 0, st>>>(S.n, S.rp, S.ci, S.kmask, W.p, W.q, W.scal,
                                                                          W.ctl, W.part));
-    PDF_KERNEL("k_press_update", st, k_press_update<<<nb, kPBlock, 0, st>>>(R.n_rep, W.scal, W.ctl, W.x, W.r, W.p, W.q,
+    PDF_KERNEL("k_press_update", st, k_press_update<<<nb, kPBlock, 0, st>>>(S.n, W.scal, W.ctl, W.x, W.r, W.p, W.q,
                                                                              W.part));
   }
   return PDF_OK;
 }
 
-// Captures k iterations into W.gx on the library's stream W.cs.
-static pdf_status press_capture(pdf_particles* P, int k) {
-  PressWork& W = P->pw;
-  if (!W.cs) {
-    PDF_CUDA(cudaStreamCreateWithFlags(&W.cs, cudaStreamNonBlocking));
-    PDF_CUDA(cudaEventCreateWithFlags(&W.ev0, cudaEventDisableTiming));
-    PDF_CUDA(cudaEventCreateWithFlags(&W.ev1, cudaEventDisableTiming));
-  }
+// Captures k iterations of system S into S.gx on the library's stream.
+static pdf_status press_capture(PressWork& W, PressSys& S, int k) {
   const long long n0 = prof_launches();
   PDF_CUDA(cudaStreamBeginCapture(W.cs, cudaStreamCaptureModeThreadLocal));
-  pdf_status s = press_iterations(P, k, W.cs);
+  pdf_status s = press_iterations(W, S, k, W.cs);
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(W.cs, &g);
   if (s != PDF_OK) {
@@ -479,18 +648,18 @@ static pdf_status press_capture(pdf_particles* P, int k) {
     return s;
   }
   if (e != cudaSuccess) return cuda_fail(e, "pdf_pressure_project: graph capture");
-  const cudaError_t e2 = cudaGraphInstantiate(&W.gx, g, 0);
+  const cudaError_t e2 = cudaGraphInstantiate(&S.gx, g, 0);
   cudaGraphDestroy(g);
   if (e2 != cudaSuccess) {
-    W.gx = nullptr;
+    S.gx = nullptr;
     return cuda_fail(e2, "pdf_pressure_project: graph instantiation");
   }
-  W.graph_launches = prof_launches() - n0;
-  prof_count(-W.graph_launches);  // captured, not launched
+  S.graph_launches = prof_launches() - n0;
+  prof_count(-S.graph_launches);  // captured, not launched
   return PDF_OK;
 }
 
-// Nodal gradient of <P'> for PDF_PRESSURE_PROJECTION steps.
+// Nodal gradient of <P'> for the projection modes of the step.
 static pdf_status press_gradient(pdf_particles* P, cudaStream_t st) {
   const MeshDev& M = P->mesh->d;
   PressWork& W = P->pw;
@@ -510,43 +679,54 @@ extern "C" pdf_status pdf_pressure_project(pdf_particles* p, const pdf_mesh* m, 
   if (!p || !m || p->mesh != m || !params) return fail(PDF_EINVAL, "pdf_pressure_project: bad arguments");
   if (!(rtol > 0.0) || max_it < 0 || !(Cp >= 0.0) || !(params->dt > 0.0))
     return fail(PDF_EINVAL, "pdf_pressure_project: rtol > 0, max_it >= 0, Cp >= 0 and dt > 0 required");
+  if (params->pressure != PDF_PRESSURE_PROJECTION && params->pressure != PDF_PRESSURE_PROJECTION_INOUT)
+    return fail(PDF_EINVAL, "pdf_pressure_project: params->pressure must be a projection mode");
   if (!p->have_stats) return fail(PDF_ESTATE, "pdf_pressure_project: call pdf_estimate_stats first");
   cudaStream_t st = (cudaStream_t)stream;
   pdf_status s = press_alloc(p);
   if (s != PDF_OK) return s;
-  const MeshDev& M = m->d;
-  const RelaxMesh& R = m->rx;
   PressWork& W = p->pw;
-  const int nb = W.nb;
-  PDF_KERNEL("k_press_rhs", st, k_press_rhs<<<nb, kPBlock, 0, st>>>(R.n_rep, R.rep_node, R.rp, R.ci, W.kval, M.nse_off,
-                                                                     M.nse, M.tri, M.dN, M.geo, p->ns, p->nd, R.pw_off,
-                                                                     R.pw_e, R.pw_n, params->nu,
+  const int k = params->pressure == PDF_PRESSURE_PROJECTION_INOUT ? 1 : 0;
+  PressSys* Sp = nullptr;
+  s = sys_get(p, k, &Sp);
+  if (s != PDF_OK) return s;
+  PressSys& S = *Sp;
+  if (W.last_sys != k) {
+    // the stored wall load belongs to the field the other system made
+    PDF_CUDA(cudaMemsetAsync(S.gw_prev, 0, sizeof(double) * std::max(S.n, 1), st));
+    W.last_sys = k;
+  }
+  const MeshDev& M = m->d;
+  const int nb = nblocks(S.n);
+  const double PiLx = params->Pi * m->period;
+  PDF_KERNEL("k_press_rhs", st, k_press_rhs<<<nb, kPBlock, 0, st>>>(dev_view(S), M.nse_off, M.nse, M.tri, M.dN, M.geo,
+                                                                     p->ns, p->nd, params->nu,
                                                                      params->closure == PDF_CLOSURE_SLM, p->pres,
-                                                                     W.gw_prev, Cp, 1.0 / params->dt, W.gw, W.b,
+                                                                     S.gw_prev, Cp, 1.0 / params->dt, PiLx, S.gw, W.b,
                                                                      W.part));
   PDF_KERNEL("k_press_sum", st, k_press_sum<<<1, kPBlock, 0, st>>>(W.part, nb, W.scal + kSBsum));
-  PDF_KERNEL("k_press_init", st, k_press_init<<<nb, kPBlock, 0, st>>>(R.n_rep, rtol * rtol, max_it, W.scal, W.ctl,
-                                                                       W.b, W.x, W.r, W.p, W.part));
+  PDF_KERNEL("k_press_init", st, k_press_init<<<nb, kPBlock, 0, st>>>(S.n, S.dirichlet ? 0 : 1, rtol * rtol, max_it,
+                                                                       W.scal, W.ctl, W.b, W.x, W.r, W.p, W.part));
   // iterations in chunks; the host reads the control words once per chunk
   constexpr int kChunk = 8;
   if (prof_timing()) {
     for (int launched = 0; launched < max_it; launched += kChunk) {
-      s = press_iterations(p, kChunk, st);
+      s = press_iterations(W, S, kChunk, st);
       if (s != PDF_OK) return s;
       PDF_CUDA(cudaMemcpyAsync(W.host_ctl, W.ctl, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, st));
       PDF_CUDA(cudaStreamSynchronize(st));
       if (W.host_ctl[kCtlDone]) break;
     }
   } else {
-    if (!W.gx) {
-      s = press_capture(p, kChunk);
+    if (!S.gx) {
+      s = press_capture(W, S, kChunk);
       if (s != PDF_OK) return s;
     }
     PDF_CUDA(cudaEventRecord(W.ev0, st));
     PDF_CUDA(cudaStreamWaitEvent(W.cs, W.ev0, 0));
     for (int launched = 0; launched < max_it; launched += kChunk) {
-      PDF_CUDA(cudaGraphLaunch(W.gx, W.cs));
-      prof_count(W.graph_launches);
+      PDF_CUDA(cudaGraphLaunch(S.gx, W.cs));
+      prof_count(S.graph_launches);
       PDF_CUDA(cudaMemcpyAsync(W.host_ctl, W.ctl, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, W.cs));
       PDF_CUDA(cudaStreamSynchronize(W.cs));
       if (W.host_ctl[kCtlDone]) break;
@@ -563,11 +743,14 @@ extern "C" pdf_status pdf_pressure_project(pdf_particles* p, const pdf_mesh* m, 
   const bool converged = W.host[kSRr] <= W.host[kSTol2];
   if (iters) *iters = it;
   if (rel_res) *rel_res = bn > 0.0 ? rn / bn : 0.0;
-  PDF_KERNEL("k_press_xsum", st, k_press_xsum<<<nb, kPBlock, 0, st>>>(R.n_rep, W.x, W.part));
-  PDF_KERNEL("k_press_sum", st, k_press_sum<<<1, kPBlock, 0, st>>>(W.part, nb, W.scal + kSXsum));
-  PDF_KERNEL("k_press_scatter", st, k_press_scatter<<<pblocks(M.n_nodes), 256, 0, st>>>(M.n_nodes, R.n_rep, R.node_rep,
-                                                                                          W.x, W.scal + kSXsum, W.dP, p->pres));
-  std::swap(W.gw, W.gw_prev);  // <P'>^{n+1} satisfies the new wall load
+  if (!S.dirichlet) {
+    PDF_KERNEL("k_press_xsum", st, k_press_xsum<<<nb, kPBlock, 0, st>>>(S.n, W.x, W.part));
+    PDF_KERNEL("k_press_sum", st, k_press_sum<<<1, kPBlock, 0, st>>>(W.part, nb, W.scal + kSXsum));
+  }
+  PDF_KERNEL("k_press_scatter", st, k_press_scatter<<<pblocks(M.n_nodes), 256, 0, st>>>(
+                                        M.n_nodes, S.n, S.node_rep, S.dir, W.x, S.dirichlet ? nullptr : W.scal + kSXsum,
+                                        p->ns, PiLx, W.dP, p->pres));
+  std::swap(S.gw, S.gw_prev);  // <P'>^{n+1} satisfies the new wall load
   // velocity correction with the element gradients of dP
   PDF_KERNEL("k_press_egrad", st, k_press_egrad<<<pblocks(M.n_tri), 256, 0, st>>>(M.n_tri, M.tri, M.dN, W.dP, W.ge));
   PDF_KERNEL("k_press_corr_coef", st, k_press_corr_coef<<<pblocks(M.n_tri), 256, 0, st>>>(M.n_tri, W.ge, params->dt,
@@ -577,17 +760,16 @@ extern "C" pdf_status pdf_pressure_project(pdf_particles* p, const pdf_mesh* m, 
     PDF_KERNEL("k_press_correct", st, k_press_correct<fx::df><<<pb, 256, 0, st>>>(p->n, p->elem, W.gc, p->u, p->v));
   else
     PDF_KERNEL("k_press_correct", st, k_press_correct<float><<<pb, 256, 0, st>>>(p->n, p->elem, W.gc, p->uf, p->vf));
-  s = press_gradient(p, st);
-  if (s != PDF_OK) return s;
+  // the statistics follow the correction (W.ge still holds grad dP)
   PDF_KERNEL("k_press_shift_stats", st, k_press_shift_stats<<<pblocks(M.n_tri), 256, 0, st>>>(M.n_tri, W.ge, params->dt,
                                                                                                 p->es));
+  s = press_gradient(p, st);
+  if (s != PDF_OK) return s;
   s = node_stats_from_elements(p, st);
   if (s != PDF_OK) return s;
   if (!converged) return fail(PDF_ENOTCONV, "pdf_pressure_project: not converged");
   return PDF_OK;
 }
-
-static int32_t m_rep(const pdf_particles* p) { return p->mesh->rx.n_rep; }
 
 extern "C" pdf_status pdf_pressure_field(pdf_particles* p, const double* set, double* get, void* stream) {
   if (!p) return fail(PDF_EINVAL, "pdf_pressure_field: NULL handle");
@@ -597,7 +779,8 @@ extern "C" pdf_status pdf_pressure_field(pdf_particles* p, const double* set, do
     pdf_status s = press_alloc(p);
     if (s != PDF_OK) return s;
     PDF_CUDA(cudaMemcpyAsync(p->pres, set, sizeof(double) * nn, cudaMemcpyDefault, st));
-    PDF_CUDA(cudaMemsetAsync(p->pw.gw_prev, 0, sizeof(double) * m_rep(p), st));
+    for (PressSys& S : p->pw.sys)
+      if (S.built) PDF_CUDA(cudaMemsetAsync(S.gw_prev, 0, sizeof(double) * std::max(S.n, 1), st));
     s = press_gradient(p, st);
     if (s != PDF_OK) return s;
   }

@@ -89,6 +89,7 @@ __global__ void k_node_coeff(int32_t n_nodes, const double* __restrict__ ns, con
     double dpx = 0.0, dpy = 0.0;
     if (P.pressure == PDF_PRESSURE_CHANNEL) { dpx = P.Pi; dpy = D[9]; }
     if (P.pressure == PDF_PRESSURE_PROJECTION) { dpx = P.Pi - gradP[2 * n]; dpy = -gradP[2 * n + 1]; }
+    if (P.pressure == PDF_PRESSURE_PROJECTION_INOUT) { dpx = -gradP[2 * n]; dpy = -gradP[2 * n + 1]; }
     if (P.closure == PDF_CLOSURE_SLM) {
       c[9] = dpx; c[10] = dpy; c[11] = 0.0;
       const double g = -(0.5 + 0.75 * P.C0_slm) * om;
@@ -1095,7 +1096,7 @@ static pdf_status check_params(const pdf_model_params* p) {
   if (!p) return fail(PDF_EINVAL, "NULL params");
   if (!(p->dt > 0.0) || !(p->nu >= 0.0)) return fail(PDF_EINVAL, "params: dt must be > 0 and nu >= 0");
   if (p->closure < 0 || p->closure > 2 || p->tm_mode < 0 || p->tm_mode > 2 || p->pressure < 0 ||
-      p->pressure > 2 || p->arith < 0 || p->arith > 1 || p->mix < 0 || p->mix > 1)
+      p->pressure > 3 || p->arith < 0 || p->arith > 1 || p->mix < 0 || p->mix > 1)
     return fail(PDF_EINVAL, "params: closure, tm_mode, pressure, arith or mix out of range");
   return PDF_OK;
 }

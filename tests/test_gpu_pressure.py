@@ -62,12 +62,13 @@ def test_projection_matches_the_oracle(closure, wall_tag):
         assert np.array_equal(st["elem"], ost["elem"])
         for key in ("u", "v"):
             assert_field_close(st[key], ost[key], "corrected %s %d" % (key, k), rtol=1e-10)
-        # the statistics the library estimated again after the correction
-        es_g = torch.empty((gm.n_tri, capi.PDF_NES), dtype=torch.float64, device="cuda")
-        ns_g = torch.empty((n, capi.PDF_NNS), dtype=torch.float64, device="cuda")
-        pg.pdf_estimate_stats(gp, gm, es_g, ns_g)
+        # the statistics the library carried through the correction (seen
+        # through the coefficient rows, without estimating them again)
         es, ns, nd, _ = oracle.statistics(M, ost, ns)
-        assert_field_close(ns_g.cpu().numpy(), ns, "node stats after projection %d" % k, rtol=1e-9)
+        po_k = oracle.make_params(dt=p.dt, nu=p.nu, Pi=p.Pi, closure=closure, pressure="projection")
+        assert_field_close(pg.pdf_elem_coeff(gp, gm, p).cpu().numpy(),
+                           oracle.elem_coeff(M, ns, nd, po_k, grad_p=gradP),
+                           "rows after projection %d" % k, rtol=1e-9)
     # a step whose drift sees Pi - grad <P'>
     po = oracle.make_params(dt=p.dt, nu=p.nu, Pi=p.Pi, closure=closure, pressure="projection")
     rows = oracle.elem_coeff(M, ns, nd, po, grad_p=gradP)
@@ -182,3 +183,56 @@ def test_projection_on_the_obstacle_mesh():
     assert np.all(same | ((status & oracle.TRK_NEAR_FACE) != 0))
     for key in KEYS:
         assert_field_close(st[key][same], ost[key][same], "obstacle projection step %s" % key)
+
+
+@pytest.mark.parametrize("where", ["channel", "obstacles"])
+def test_inflow_outflow_projection_matches_the_oracle(where):
+    """PDF_PRESSURE_PROJECTION_INOUT (the street canyon's inflow/outflow
+    condition): two projections and a step, GPU and oracle each from the
+    same seeded state."""
+    if where == "channel":
+        m = inputs.channel_mesh(16, 24, seed=2, inout=True, wall_tag=inputs.TAG_NOSLIP)
+        counts = np.full(len(m["tri"]), 30, dtype=np.int32)
+        closure, seed, prof, sig = "slm", 5, "parabola", 0.3
+        extra = {}
+    else:
+        cfg = inputs.OBSTACLES["obstacles_small_mean20"]
+        m = inputs.obstacle_mesh(h_min=cfg["h_min"], ratio=cfg["ratio"], growth=cfg["growth"])
+        counts = inputs.counts_by_area(m, cfg["mean_ppe"])
+        closure, seed, prof, sig = cfg["closure"], cfg["seed"], cfg["u_profile"], cfg["u_sigma"]
+        extra = dict(tm_mode=cfg["tm_mode"], src_x=cfg["src"][0], src_y=cfg["src"][1], src_r=cfg["src"][2])
+    gm = pg.Mesh(m)
+    gp = pg.Particles(gm, seed, count=counts, u_profile=prof, u_sigma=sig)
+    M = oracle.Mesh(m)
+    ost = oracle.init(M, counts, seed, u_profile=prof, u_sigma=sig)
+    p = pg.model_params(dt=2e-3, nu=5e-3, Pi=0.5, closure=closure, pressure="projection_inout", **extra)
+    po = oracle.make_params(dt=p.dt, nu=p.nu, Pi=p.Pi, closure=closure, pressure="projection_inout",
+                            tm_mode="source" if extra else "turb",
+                            src=(p.src_x, p.src_y, p.src_r))
+    n = gm.n_nodes
+    Cp = 0.5 * p.dt
+    pg.pdf_estimate_stats(gp, gm)
+    _, ns, nd, _ = oracle.statistics(M, ost)
+    pres, G = np.zeros(n), np.zeros(n)
+    for k in range(2):
+        it, res = pg.pdf_pressure_project(gp, gm, p, Cp=Cp, rtol=1e-13, max_it=5000)
+        assert res <= 1e-13
+        dP, pres, G, gradP = OP.project(m, ns, nd, ost, pres, G, p.nu, p.dt, Cp, closure == "slm", inout=True,
+                                        Pi=p.Pi)
+        assert_field_close(pg.pdf_pressure_field(gp, gm).cpu().numpy(), pres, "in/out pressure %d" % k, rtol=1e-9)
+        st = _host(gp.get_state())
+        for key in ("u", "v"):
+            assert_field_close(st[key], ost[key], "in/out corrected %s %d" % (key, k), rtol=1e-10)
+        _, ns, nd, _ = oracle.statistics(M, ost, ns)
+    io = OP.inout_nodes(m)
+    assert np.all(pres[io == 1] > pres[io == 2].mean())   # the imposed drop
+    rows = oracle.elem_coeff(M, ns, nd, po, grad_p=gradP)
+    assert_field_close(pg.pdf_elem_coeff(gp, gm, p).cpu().numpy(), rows, "in/out rows", rtol=1e-9)
+    kw = {"omega_wall": oracle.noslip_omega(M, ns)} if where == "channel" else {}
+    cnt, status = oracle.step(M, rows, po, seed, 0, ost, **kw)
+    pg.pdf_step(gp, gm, p, step=0)
+    st = _host(gp.get_state())
+    same = st["elem"] == ost["elem"]
+    assert np.all(same | ((status & oracle.TRK_NEAR_FACE) != 0))
+    for key in KEYS:
+        assert_field_close(st[key][same], ost[key][same], "in/out step %s" % key)

@@ -235,3 +235,39 @@ def test_coupled_projection_stability_depends_on_cp_over_dt():
     assert d[-5:].max() < d[0] and 0.9 < vr < 1.05
     d, vr = _coupled_run(1e-3)
     assert d[-1] > 100 * d[0]
+
+
+def test_inflow_outflow_condition_gives_the_imposed_drop():
+    """The street canyon's inflow/outflow condition on a straight channel
+    with constant <vv> = c and no flow: <P> = Pi L_x - c at the inflow, -c
+    at the outflow, linear in between (the walls carry no load), so the
+    drift's pressure gradient is exactly the imposed -Pi.  From <P'> = 0
+    with C_p = 0 the increment is that linear field; from any <P'>^n with
+    C_p = dt the stabilisation term replaces the interior by the harmonic
+    extension of the boundary values, the same linear field; the next
+    projection with the same statistics leaves it as it is."""
+    m = inputs.channel_mesh(12, 10, seed=3, inout=True)
+    x = m["xy"][:, 0]
+    n = len(x)
+    Pi, c, Lx, dt = 0.7, 0.05, 2.0 * np.pi, 1e-3
+    ns, nd = np.zeros((n, 12)), np.zeros((n, 10))
+    ns[:, 6] = c
+    target = Pi * (Lx - x) - c
+    dP, G = OP.solve_increment(m, ns, nd, np.zeros(n), np.zeros(n), 0.01, dt, 0.0, inout=True, Pi=Pi)
+    np.testing.assert_allclose(dP, target, atol=1e-9)
+    np.testing.assert_allclose(OP.nodal_gradient(m, dP), np.tile([-Pi, 0.0], (n, 1)), atol=1e-9)
+    pres0 = np.random.default_rng(2).standard_normal(n)[OP._rep(m, inout=True)]
+    dP, G = OP.solve_increment(m, ns, nd, pres0, np.zeros(n), 0.01, dt, dt, inout=True, Pi=Pi)
+    P1 = pres0 + dP
+    np.testing.assert_allclose(P1, target, atol=1e-9)
+    dP2, _ = OP.solve_increment(m, ns, nd, P1, G, 0.01, dt, dt, inout=True, Pi=Pi)
+    np.testing.assert_allclose(dP2, 0.0, atol=1e-9)
+    io = OP.inout_nodes(m)
+    assert (io == 1).sum() == 10 and (io == 2).sum() == 10
+    # the drift sees the whole gradient of the field in this mode
+    pj = oracle.make_params(dt=1e-3, nu=0.0, Pi=Pi, closure="slm", pressure="projection_inout")
+    S = np.zeros(12)
+    S[3] = 1.0
+    S[5:8] = 0.1
+    cf = oracle.node_coeff(S, np.zeros(10), None, pj, grad_p=np.array([-Pi, 0.0]))
+    assert np.isclose(cf[9], Pi) and cf[10] == 0.0
