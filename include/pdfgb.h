@@ -393,10 +393,17 @@ pdf_status pdf_mesh_wall_distance(const pdf_mesh* m, double* dist, double* norma
  *            C_p/dt -> 0 leaves the statistical noise undamped.
  *   rtol     stop when ||r|| <= rtol ||b||; PDF_ENOTCONV after max_it
  *   iters, rel_res  host or NULL
- * Synchronizes `stream` once per 8 iterations.  PDF_ESTATE without
- * statistics. */
+ * Synchronizes `stream` once per 8 iterations (once with the persistent
+ * solver, see pdf_pressure_set_solver).  PDF_ESTATE without statistics. */
 pdf_status pdf_pressure_project(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params, double Cp,
                                 double rtol, int32_t max_it, int32_t* iters, double* rel_res, void* stream);
+/* The iteration of pdf_pressure_project runs as separate kernels replayed
+ * in CUDA graphs of 8 iterations (persistent = 0, the default) or as one
+ * persistent cooperative kernel with grid-wide barriers between its phases
+ * (persistent = 1; the separate kernels are used when the device refuses
+ * the cooperative launch).  Both compute the same iterates up to the order
+ * of the reductions.  PDF_EINVAL for other values. */
+pdf_status pdf_pressure_set_solver(pdf_particles* p, int32_t persistent);
 /* Copies the pressure field <P'> [n_nodes] (FP64, device or host) in (set,
  * recomputing its nodal gradient and zeroing the stored wall load G^n)
  * and/or out (get); either may be NULL. */

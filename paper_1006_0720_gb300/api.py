@@ -247,6 +247,10 @@ def pdf_pressure_project(particles, mesh, params, Cp=None, rtol=1e-10, max_it=20
     return it.value, res.value
 
 
+def pdf_pressure_set_solver(particles, persistent=False):
+    check(lib().pdf_pressure_set_solver(particles.handle, 1 if persistent else 0), "pdf_pressure_set_solver")
+
+
 def pdf_pressure_field(particles, mesh, set=None, stream=None):
     """The projection's nodal pressure <P'> (device FP64 tensor); `set`
     replaces it first."""

@@ -22,7 +22,10 @@
 // the conjugate-gradient method needs.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
+
+#include <cooperative_groups.h>
 
 #include "amg.cuh"
 
@@ -374,39 +377,68 @@ __global__ void __launch_bounds__(256) k_amg_coarse(int32_t nc, const double* __
   if (lane == 0) z[row] = s;
 }
 
-// z = x + W (b - A x) + Q e_c, one thread per row.  With part != nullptr
-// (the finest level) the block partials of b . z go to part.
+// z = x + W (b - A x) + Q e_c on the finest level (kF lanes per row), the
+// block partials of b . z to part, and in the last block to finish their
+// sum: *rz_old = *rz, *rz = sum (counter returns to 0).  More lanes per row
+// shorten the gather chains but multiply the blocks, which costs more on
+// this level's 10^5 rows than it saves, so one.
+constexpr int kF = 1;
+
 __global__ void __launch_bounds__(256) k_amg_up(int32_t n, const int32_t* __restrict__ a_rp,
                                                 const int32_t* __restrict__ a_ci, const double* __restrict__ a_v,
                                                 const double* __restrict__ w, const int32_t* __restrict__ q_rp,
                                                 const int32_t* __restrict__ q_ci, const double* __restrict__ q_v,
                                                 const double* __restrict__ b, const double* __restrict__ x,
                                                 const double* __restrict__ ec, double* __restrict__ z,
-                                                double* __restrict__ part, const int32_t* __restrict__ done) {
+                                                double* __restrict__ part, int32_t* __restrict__ counter,
+                                                double* __restrict__ rz, double* __restrict__ rz_old,
+                                                const int32_t* __restrict__ done) {
   if (*done) return;
-  const int32_t i = blockIdx.x * 256 + threadIdx.x;
-  double bz = 0.0;
+  const int32_t i = (blockIdx.x * 256 + threadIdx.x) / kF, g = threadIdx.x % kF;
+  double ax = 0.0, qe = 0.0;
   if (i < n) {
-    double ax = 0.0;
-    for (int32_t q = a_rp[i]; q < a_rp[i + 1]; ++q) ax += a_v[q] * x[a_ci[q]];
-    double qe = 0.0;
-    for (int32_t q = q_rp[i]; q < q_rp[i + 1]; ++q) qe += q_v[q] * ec[q_ci[q]];
+    for (int32_t q = a_rp[i] + g; q < a_rp[i + 1]; q += kF) ax += a_v[q] * x[a_ci[q]];
+    for (int32_t q = q_rp[i] + g; q < q_rp[i + 1]; q += kF) qe += q_v[q] * ec[q_ci[q]];
+  }
+#pragma unroll
+  for (int o = kF / 2; o > 0; o >>= 1) {
+    ax += __shfl_xor_sync(0xffffffffu, ax, o, kF);
+    qe += __shfl_xor_sync(0xffffffffu, qe, o, kF);
+  }
+  double bz = 0.0;
+  if (i < n && g == 0) {
     const double bi = b[i];
     const double zi = x[i] + w[i] * (bi - ax) + qe;
     z[i] = zi;
     bz = bi * zi;
   }
-  if (part) {
-    __shared__ double sh[8];
+  __shared__ double sh[8];
+  __shared__ bool last;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) bz += __shfl_xor_sync(0xffffffffu, bz, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = bz;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int k = 0; k < 8; ++k) t += sh[k];
-      part[blockIdx.x] = t;
-    }
+  for (int o = 16; o > 0; o >>= 1) bz += __shfl_xor_sync(0xffffffffu, bz, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = bz;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += sh[k];
+    part[blockIdx.x] = t;
+    __threadfence();
+    last = atomicAdd(counter, 1) == (int32_t)gridDim.x - 1;
+    if (last) *counter = 0;
+  }
+  __syncthreads();
+  if (!last) return;
+  double t = 0.0;
+  for (int32_t k = threadIdx.x; k < (int32_t)gridDim.x; k += 256) t += __ldcg(part + k);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int k = 0; k < 8; ++k) v += sh[k];
+    *rz_old = *rz;
+    *rz = v;
   }
 }
 
@@ -430,7 +462,8 @@ __global__ void __launch_bounds__(256) k_amg_up_g(int32_t n, const int32_t* __re
   if (i < n && g == 0) z[i] = x[i] + w[i] * (b[i] - ax) + qe;
 }
 
-pdf_status amg_apply(const Amg& G, const double* r, double* z, double* part, const int32_t* done, cudaStream_t st) {
+pdf_status amg_apply(const Amg& G, const double* r, double* z, double* part, int32_t* counter, double* rz,
+                     double* rz_old, const int32_t* done, cudaStream_t st) {
   const int32_t L = (int32_t)G.lv.size();
   // down: level l's right-hand side is r (l = 0) or lv[l].b
   for (int32_t l = 0; l < L; ++l) {
@@ -452,12 +485,226 @@ pdf_status amg_apply(const Amg& G, const double* r, double* z, double* part, con
     const double* ec = l + 1 < L ? G.lv[l + 1].z : G.cz;
     double* out = l == 0 ? z : V.z;
     if (l == 0)
-      PDF_KERNEL("k_amg_up", st, k_amg_up<<<(V.n + 255) / 256, 256, 0, st>>>(
-                                     V.n, V.a_rp, V.a_ci, V.a_v, V.w, V.q_rp, V.q_ci, V.q_v, b, V.x, ec, out, part, done));
+      PDF_KERNEL("k_amg_up", st, k_amg_up<<<(int32_t)(((int64_t)V.n * kF + 255) / 256), 256, 0, st>>>(
+                                     V.n, V.a_rp, V.a_ci, V.a_v, V.w, V.q_rp, V.q_ci, V.q_v, b, V.x, ec, out, part,
+                                     counter, rz, rz_old, done));
     else
       PDF_KERNEL("k_amg_up", st, k_amg_up_g<<<(int32_t)(((int64_t)V.n * kG + 255) / 256), 256, 0, st>>>(
                                      V.n, V.a_rp, V.a_ci, V.a_v, V.w, V.q_rp, V.q_ci, V.q_v, b, V.x, ec, out, done));
   }
+  return PDF_OK;
+}
+
+// ------------------------------------------------------------- persistent PCG
+
+constexpr int kMaxLv = 12;
+
+struct PcgLevel {
+  int32_t n, nc;
+  const int32_t *a_rp, *a_ci, *q_rp, *q_ci, *s_rp, *s_ci;
+  const double *a_v, *w, *q_v, *s_v;
+  double *b, *x, *z;
+};
+
+struct PcgArgs {
+  int32_t n, L, nc;
+  const int32_t *rp, *ci;
+  const double* val;
+  double *x, *r, *z, *p, *q, *scal, *part;
+  int32_t* ctl;
+  const double* cinv;
+  double *cb, *cz;
+  PcgLevel lv[kMaxLv];
+};
+
+// Sum over the block of v; the result in every thread.
+__device__ __forceinline__ double block_sum_all(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) t += sh[i];
+  __syncthreads();
+  return t;
+}
+
+// Sum of the grid's block partials, in block order: identical in every block.
+__device__ __forceinline__ double grid_total(const double* part, double* sh) {
+  double t = 0.0;
+  for (int32_t i = threadIdx.x; i < (int32_t)gridDim.x; i += 256) t += __ldcg(part + i);
+  return block_sum_all(t, sh);
+}
+
+__global__ void __launch_bounds__(256) k_amg_pcg(PcgArgs A) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double sh[8];
+  const int32_t tid = blockIdx.x * 256 + threadIdx.x, nthr = gridDim.x * 256;
+  const int32_t gl = tid / kG, lane_g = threadIdx.x % kG, ngrp = nthr / kG;
+  double* part0 = A.part;
+  double* part1 = A.part + gridDim.x;
+  double* part2 = A.part + 2 * gridDim.x;
+  int32_t it = A.ctl[kPcgIters];
+  const int32_t max_it = A.ctl[kPcgMaxIt];
+  bool done = A.ctl[kPcgDone] != 0;
+  double rz = A.scal[kPcgRz], rz_old = A.scal[kPcgRzOld], rr = A.scal[kPcgRr], pq = 0.0;
+  const double tol2 = A.scal[kPcgTol2];
+  while (!done) {
+    // z = M^-1 r: down the levels
+    for (int l = 0; l < A.L; ++l) {
+      const PcgLevel& V = A.lv[l];
+      const double* b = l == 0 ? A.r : V.b;
+      double* bc = l + 1 < A.L ? A.lv[l + 1].b : A.cb;
+      for (int32_t i = tid; i < V.n; i += nthr) V.x[i] = V.w[i] * b[i];
+      for (int32_t J0 = 0; J0 < V.nc; J0 += ngrp) {
+        const int32_t J = J0 + gl;
+        double s = 0.0;
+        if (J < V.nc)
+          for (int32_t k = V.s_rp[J] + lane_g; k < V.s_rp[J + 1]; k += kG) s += V.s_v[k] * b[V.s_ci[k]];
+#pragma unroll
+        for (int o = kG / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, kG);
+        if (J < V.nc && lane_g == 0) bc[J] = s;
+      }
+      grid.sync();
+    }
+    // coarsest level, one warp per row
+    {
+      const double* b = A.L > 0 ? A.cb : A.r;
+      double* zc = A.L > 0 ? A.cz : A.z;
+      const int32_t w = tid >> 5, lane = threadIdx.x & 31, nw = nthr >> 5;
+      for (int32_t row0 = 0; row0 < A.nc; row0 += nw) {
+        const int32_t row = row0 + w;
+        double s = 0.0;
+        if (row < A.nc)
+          for (int32_t k = lane; k < A.nc; k += 32) s += A.cinv[(int64_t)row * A.nc + k] * b[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (row < A.nc && lane == 0) zc[row] = s;
+      }
+      grid.sync();
+    }
+    // up the levels; the finest one also gives r . z
+    double bz = 0.0;
+    for (int l = A.L - 1; l >= 0; --l) {
+      const PcgLevel& V = A.lv[l];
+      const double* b = l == 0 ? A.r : V.b;
+      const double* ec = l + 1 < A.L ? A.lv[l + 1].z : A.cz;
+      double* out = l == 0 ? A.z : V.z;
+      if (l == 0) {
+        for (int32_t i = tid; i < V.n; i += nthr) {
+          double ax = 0.0, qe = 0.0;
+          for (int32_t k = V.a_rp[i]; k < V.a_rp[i + 1]; ++k) ax += V.a_v[k] * V.x[V.a_ci[k]];
+          for (int32_t k = V.q_rp[i]; k < V.q_rp[i + 1]; ++k) qe += V.q_v[k] * ec[V.q_ci[k]];
+          const double zi = V.x[i] + V.w[i] * (b[i] - ax) + qe;
+          out[i] = zi;
+          bz += b[i] * zi;
+        }
+      } else {
+        for (int32_t i0 = 0; i0 < V.n; i0 += ngrp) {
+          const int32_t i = i0 + gl;
+          double ax = 0.0, qe = 0.0;
+          if (i < V.n) {
+            for (int32_t k = V.a_rp[i] + lane_g; k < V.a_rp[i + 1]; k += kG) ax += V.a_v[k] * V.x[V.a_ci[k]];
+            for (int32_t k = V.q_rp[i] + lane_g; k < V.q_rp[i + 1]; k += kG) qe += V.q_v[k] * ec[V.q_ci[k]];
+          }
+#pragma unroll
+          for (int o = kG / 2; o > 0; o >>= 1) {
+            ax += __shfl_xor_sync(0xffffffffu, ax, o, kG);
+            qe += __shfl_xor_sync(0xffffffffu, qe, o, kG);
+          }
+          if (i < V.n && lane_g == 0) out[i] = V.x[i] + V.w[i] * (b[i] - ax) + qe;
+        }
+      }
+      if (l > 0) grid.sync();
+    }
+    if (A.L == 0)
+      for (int32_t i = tid; i < A.n; i += nthr) bz += A.r[i] * A.z[i];
+    {
+      const double t = block_sum_all(bz, sh);
+      if (threadIdx.x == 0) part0[blockIdx.x] = t;
+    }
+    grid.sync();
+    // beta; p = z + beta p and q = K z + beta q (= K p by the recurrence,
+    // so no barrier between them); p . q
+    rz_old = rz;
+    rz = grid_total(part0, sh);
+    const double beta = rz_old != 0.0 ? rz / rz_old : 0.0;
+    double s_pq = 0.0;
+    for (int32_t i = tid; i < A.n; i += nthr) {
+      double kz = 0.0;
+      for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) kz += A.val[k] * A.z[A.ci[k]];
+      const double pv = A.z[i] + beta * A.p[i];
+      const double qv = kz + beta * A.q[i];
+      A.p[i] = pv;
+      A.q[i] = qv;
+      s_pq += pv * qv;
+    }
+    {
+      const double t = block_sum_all(s_pq, sh);
+      if (threadIdx.x == 0) part1[blockIdx.x] = t;
+    }
+    grid.sync();
+    pq = grid_total(part1, sh);
+    const double alpha = pq > 0.0 ? rz / pq : 0.0;
+    double s_rr = 0.0;
+    for (int32_t i = tid; i < A.n; i += nthr) {
+      A.x[i] += alpha * A.p[i];
+      const double rv = A.r[i] - alpha * A.q[i];
+      A.r[i] = rv;
+      s_rr += rv * rv;
+    }
+    {
+      const double t = block_sum_all(s_rr, sh);
+      if (threadIdx.x == 0) part2[blockIdx.x] = t;
+    }
+    grid.sync();
+    rr = grid_total(part2, sh);
+    ++it;
+    done = rr <= tol2 || it >= max_it || !(pq > 0.0);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    A.scal[kPcgRr] = rr;
+    A.scal[kPcgRz] = rz;
+    A.scal[kPcgRzOld] = rz_old;
+    A.scal[kPcgPq] = pq;
+    A.ctl[kPcgIters] = it;
+    A.ctl[kPcgDone] = 1;
+  }
+}
+
+pdf_status amg_pcg(const Amg& G, int32_t n, const int32_t* rp, const int32_t* ci, const double* val, double* x,
+                   double* r, double* z, double* p, double* q, double* scal, int32_t* ctl, double* part,
+                   int32_t part_cap, cudaStream_t st) {
+  if ((int)G.lv.size() > kMaxLv) return fail(PDF_EINVAL, "amg_pcg: too many levels");
+  int dev = 0, coop = 0, sms = 0, per_sm = 0;
+  PDF_CUDA(cudaGetDevice(&dev));
+  PDF_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  PDF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  PDF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_amg_pcg, 256, 0));
+  if (!coop || per_sm < 1) return fail(PDF_EINVAL, "amg_pcg: no cooperative launch");
+  // at most one row per thread on the finest level, at most the resident grid
+  int blocks = std::min<int64_t>((int64_t)sms * per_sm, ((int64_t)n + 255) / 256);
+  blocks = std::max(1, std::min(blocks, part_cap / 3));
+  PcgArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.n = n;
+  A.L = (int32_t)G.lv.size();
+  A.nc = G.nc;
+  A.rp = rp; A.ci = ci; A.val = val;
+  A.x = x; A.r = r; A.z = z; A.p = p; A.q = q; A.scal = scal; A.part = part; A.ctl = ctl;
+  A.cinv = G.cinv; A.cb = G.cb; A.cz = G.cz;
+  for (int l = 0; l < A.L; ++l) {
+    const AmgLevel& V = G.lv[l];
+    A.lv[l] = PcgLevel{V.n, V.nc, V.a_rp, V.a_ci, V.q_rp, V.q_ci, V.s_rp, V.s_ci,
+                       V.a_v, V.w, V.q_v, V.s_v, V.b, V.x, V.z};
+  }
+  void* args[] = {&A};
+  cudaError_t le = cudaSuccess;
+  PDF_KERNEL("k_amg_pcg", st,
+             le = cudaLaunchCooperativeKernel((const void*)k_amg_pcg, dim3(blocks), dim3(256), args, 0, st));
+  if (le != cudaSuccess) return cuda_fail(le, "amg_pcg: cooperative launch");
   return PDF_OK;
 }
 

@@ -32,9 +32,26 @@ struct Amg {
 pdf_status amg_setup(int32_t n, const std::vector<int32_t>& rp, const std::vector<int32_t>& ci,
                      const std::vector<double>& v, bool singular, Amg& G);
 void amg_free(Amg& G);
-// z = M^-1 r (one V-cycle); part receives the block partials of r . z
-// (blocks of 256 rows) when the hierarchy has a level, else nothing.  Every
-// kernel returns at once when *done is set.
-pdf_status amg_apply(const Amg& G, const double* r, double* z, double* part, const int32_t* done, cudaStream_t st);
+// z = M^-1 r (one V-cycle).  When the hierarchy has a level, the finest
+// up-sweep also forms r . z (block partials in part, finished by the last
+// block through *counter, which it resets): *rz_old = *rz, *rz = r . z;
+// else the caller forms it.  Every kernel returns at once when *done is set.
+pdf_status amg_apply(const Amg& G, const double* r, double* z, double* part, int32_t* counter, double* rz,
+                     double* rz_old, const int32_t* done, cudaStream_t st);
+
+// The whole preconditioned conjugate-gradient iteration for the CSR matrix
+// (n rows; rp, ci, val) in one persistent cooperative kernel, the phases
+// separated by grid-wide barriers.  Entry state (as left by the caller's
+// initialisation): x, r = b - A x, p = q = 0, scal[kPcgRz] = scal[kPcgRzOld] = 1,
+// scal[kPcgTol2] = the stopping threshold on r.r, ctl[kPcgDone/Iters/MaxIt].
+// On return x, r, scal[kPcgRr], ctl[kPcgIters] and ctl[kPcgDone] = 1 (the
+// caller tells convergence from r.r <= tol2).  part: 3 x grid doubles.
+// Returns PDF_EINVAL when the device cannot launch it cooperatively (the
+// caller then runs the separate kernels).
+enum { kPcgDone = 0, kPcgIters = 1, kPcgMaxIt = 2 };
+enum { kPcgPq = 0, kPcgRz = 1, kPcgRr = 2, kPcgRzOld = 6, kPcgTol2 = 7 };
+pdf_status amg_pcg(const Amg& G, int32_t n, const int32_t* rp, const int32_t* ci, const double* val, double* x,
+                   double* r, double* z, double* p, double* q, double* scal, int32_t* ctl, double* part,
+                   int32_t part_cap, cudaStream_t st);
 
 }  // namespace pdfgb

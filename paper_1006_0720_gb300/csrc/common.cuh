@@ -146,6 +146,7 @@ struct PressSys {
 struct PressWork {
   PressSys sys[2];             // 0: periodic in x, 1: inflow/outflow conditions
   int32_t last_sys = -1;
+  bool persistent = false;     // run the iteration as one persistent cooperative kernel
   int32_t* ctl = nullptr;      // device: done, iterations, max_it, block counters
   int32_t* host_ctl = nullptr; // page-locked copy
   double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr;

@@ -190,7 +190,8 @@ __global__ void __launch_bounds__(kPBlock) k_press_init(int32_t n_rep, int singu
                                                         double* __restrict__ scal,
                                                         int32_t* __restrict__ ctl, double* __restrict__ b,
                                                         double* __restrict__ x, double* __restrict__ r,
-                                                        double* __restrict__ p, double* __restrict__ part) {
+                                                        double* __restrict__ p, double* __restrict__ q,
+                                                        double* __restrict__ part) {
   const int32_t u = blockIdx.x * kPBlock + threadIdx.x;
   double rr = 0.0;
   if (u < n_rep) {
@@ -199,6 +200,7 @@ __global__ void __launch_bounds__(kPBlock) k_press_init(int32_t n_rep, int singu
     x[u] = 0.0;
     r[u] = bv;
     p[u] = 0.0;
+    q[u] = 0.0;
     rr = bv * bv;
   }
   const double s = pblock_sum(rr);
@@ -217,43 +219,29 @@ __global__ void __launch_bounds__(kPBlock) k_press_init(int32_t n_rep, int singu
   }
 }
 
-// r . z from the preconditioner's partials: rz_old = rz, rz = sum.
-__global__ void k_press_rz(const double* __restrict__ part, int32_t nb, double* __restrict__ scal,
-                           const int32_t* __restrict__ done) {
-  if (*done) return;
-  double s = 0.0;
-  for (int32_t i = threadIdx.x; i < nb; i += kPBlock) s += part[i];
-  s = pblock_sum(s);
-  if (threadIdx.x == 0) {
-    scal[kSRzOld] = scal[kSRz];
-    scal[kSRz] = s;
-  }
-}
-
-// p = z + beta p, beta = rz / rz_old (p = 0 before the first iteration).
-__global__ void k_press_dir(int32_t n_rep, const double* __restrict__ scal, const double* __restrict__ z,
-                            double* __restrict__ p, const int32_t* __restrict__ done) {
-  if (*done) return;
-  const double ro = scal[kSRzOld];
-  const double beta = ro != 0.0 ? scal[kSRz] / ro : 0.0;
-  for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n_rep; u += gridDim.x * blockDim.x)
-    p[u] = z[u] + beta * p[u];
-}
-
-// q = K p, p . q (last block: alpha = rz / p.q).
-__global__ void __launch_bounds__(kPBlock) k_press_spmv(int32_t n_rep, const int32_t* __restrict__ rp,
-                                                        const int32_t* __restrict__ ci, const double* __restrict__ kval,
-                                                        const double* __restrict__ p, double* __restrict__ q,
-                                                        double* __restrict__ scal, int32_t* __restrict__ ctl,
-                                                        double* __restrict__ part) {
+// The direction and its image in one pass (q = K p by the recurrence
+// K p_new = K z + beta K p_old, so no barrier between p and q): beta =
+// rz / rz_old, p = z + beta p, q = K z + beta q, p . q (last block: alpha =
+// rz / p.q).  p = q = 0 before the first iteration.
+__global__ void __launch_bounds__(kPBlock) k_press_dirspmv(int32_t n_rep, const int32_t* __restrict__ rp,
+                                                           const int32_t* __restrict__ ci,
+                                                           const double* __restrict__ kval,
+                                                           const double* __restrict__ z, double* __restrict__ p,
+                                                           double* __restrict__ q, double* __restrict__ scal,
+                                                           int32_t* __restrict__ ctl, double* __restrict__ part) {
   if (ctl[kCtlDone]) return;
+  const double rz = scal[kSRz], rz_old = scal[kSRzOld];
+  const double beta = rz_old != 0.0 ? rz / rz_old : 0.0;
   const int32_t u = blockIdx.x * kPBlock + threadIdx.x;
   double pq = 0.0;
   if (u < n_rep) {
-    double s = 0.0;
-    for (int32_t k = rp[u]; k < rp[u + 1]; ++k) s += kval[k] * p[ci[k]];
-    q[u] = s;
-    pq = s * p[u];
+    double kz = 0.0;
+    for (int32_t k = rp[u]; k < rp[u + 1]; ++k) kz += kval[k] * z[ci[k]];
+    const double pv = z[u] + beta * p[u];
+    const double qv = kz + beta * q[u];
+    p[u] = pv;
+    q[u] = qv;
+    pq = pv * qv;
   }
   const double t = pblock_sum(pq);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
@@ -261,7 +249,7 @@ __global__ void __launch_bounds__(kPBlock) k_press_spmv(int32_t n_rep, const int
   const double v = sum_parts(part, gridDim.x);
   if (threadIdx.x == 0) {
     scal[kSPq] = v;
-    scal[kSAlpha] = v > 0.0 ? scal[kSRz] / v : 0.0;
+    scal[kSAlpha] = v > 0.0 ? rz / v : 0.0;
   }
 }
 
@@ -290,6 +278,20 @@ __global__ void __launch_bounds__(kPBlock) k_press_update(int32_t n_rep, double*
     const int32_t it = ctl[kCtlIters] + 1;
     ctl[kCtlIters] = it;
     if (v <= scal[kSTol2] || it >= ctl[kCtlMaxIt] || !(scal[kSPq] > 0.0)) ctl[kCtlDone] = 1;
+  }
+}
+
+// r . z from its partials when the hierarchy has no level: rz_old = rz,
+// rz = sum.
+__global__ void k_press_rz(const double* __restrict__ part, int32_t nb, double* __restrict__ scal,
+                           const int32_t* __restrict__ done) {
+  if (*done) return;
+  double s = 0.0;
+  for (int32_t i = threadIdx.x; i < nb; i += kPBlock) s += part[i];
+  s = pblock_sum(s);
+  if (threadIdx.x == 0) {
+    scal[kSRzOld] = scal[kSRz];
+    scal[kSRz] = s;
   }
 }
 
@@ -429,7 +431,7 @@ static pdf_status press_alloc(pdf_particles* P) {
   A((void**)&W.z, sizeof(double) * nn);
   A((void**)&W.p, sizeof(double) * nn);
   A((void**)&W.q, sizeof(double) * nn);
-  A((void**)&W.part, sizeof(double) * 2 * nblocks(nn));
+  A((void**)&W.part, sizeof(double) * 4 * nblocks(nn));
   A((void**)&W.scal, sizeof(double) * 16);
   A((void**)&W.dP, sizeof(double) * nn);
   A((void**)&W.ge, sizeof(double) * 2 * nt);
@@ -622,16 +624,16 @@ static pdf_status press_iterations(PressWork& W, const PressSys& S, int k, cudaS
   const int nb = nblocks(S.n);
   const int32_t* done = W.ctl + kCtlDone;
   for (int i = 0; i < k; ++i) {
-    pdf_status s = amg_apply(G, W.r, W.z, W.part, done, st);
+    pdf_status s = amg_apply(G, W.r, W.z, W.part, W.ctl + kCtlCount1, W.scal + kSRz, W.scal + kSRzOld, done, st);
     if (s != PDF_OK) return s;
-    if (G.lv.empty())
+    if (G.lv.empty()) {
       PDF_KERNEL("k_press_dot", st, k_press_dot<<<nb, kPBlock, 0, st>>>(S.n, W.r, W.z, W.part, done));
-    PDF_KERNEL("k_press_rz", st, k_press_rz<<<1, kPBlock, 0, st>>>(W.part, nb, W.scal, done));
-    PDF_KERNEL("k_press_dir", st, k_press_dir<<<pblocks(S.n), 256, 0, st>>>(S.n, W.scal, W.z, W.p, done));
-    PDF_KERNEL("k_press_spmv", st, k_press_spmv<<<nb, kPBlock, 0, st>>>(S.n, S.rp, S.ci, S.kmask, W.p, W.q, W.scal,
-                                                                         W.ctl, W.part));
+      PDF_KERNEL("k_press_rz", st, k_press_rz<<<1, kPBlock, 0, st>>>(W.part, nb, W.scal, done));
+    }
+    PDF_KERNEL("k_press_dirspmv", st, k_press_dirspmv<<<nb, kPBlock, 0, st>>>(S.n, S.rp, S.ci, S.kmask, W.z, W.p, W.q,
+                                                                               W.scal, W.ctl, W.part + nb));
     PDF_KERNEL("k_press_update", st, k_press_update<<<nb, kPBlock, 0, st>>>(S.n, W.scal, W.ctl, W.x, W.r, W.p, W.q,
-                                                                             W.part));
+                                                                             W.part + 2 * nb));
   }
   return PDF_OK;
 }
@@ -706,10 +708,21 @@ extern "C" pdf_status pdf_pressure_project(pdf_particles* p, const pdf_mesh* m, 
                                                                      W.part));
   PDF_KERNEL("k_press_sum", st, k_press_sum<<<1, kPBlock, 0, st>>>(W.part, nb, W.scal + kSBsum));
   PDF_KERNEL("k_press_init", st, k_press_init<<<nb, kPBlock, 0, st>>>(S.n, S.dirichlet ? 0 : 1, rtol * rtol, max_it,
-                                                                       W.scal, W.ctl, W.b, W.x, W.r, W.p, W.part));
-  // iterations in chunks; the host reads the control words once per chunk
+                                                                       W.scal, W.ctl, W.b, W.x, W.r, W.p, W.q, W.part));
+  // the iteration: chunks of separate kernels (the host reads the control
+  // words once per chunk), or one persistent cooperative kernel when asked
+  // for and the device can launch it
   constexpr int kChunk = 8;
-  if (prof_timing()) {
+  bool coop = false;
+  if (W.persistent) {
+    s = amg_pcg(*S.amg, S.n, S.rp, S.ci, S.kmask, W.x, W.r, W.z, W.p, W.q, W.scal, W.ctl, W.part,
+                4 * nblocks(m->d.n_nodes), st);
+    coop = s == PDF_OK;
+    if (!coop) W.persistent = false;
+  }
+  if (coop) {
+    // nothing else to launch
+  } else if (prof_timing()) {
     for (int launched = 0; launched < max_it; launched += kChunk) {
       s = press_iterations(W, S, kChunk, st);
       if (s != PDF_OK) return s;
@@ -768,6 +781,12 @@ extern "C" pdf_status pdf_pressure_project(pdf_particles* p, const pdf_mesh* m, 
   s = node_stats_from_elements(p, st);
   if (s != PDF_OK) return s;
   if (!converged) return fail(PDF_ENOTCONV, "pdf_pressure_project: not converged");
+  return PDF_OK;
+}
+
+extern "C" pdf_status pdf_pressure_set_solver(pdf_particles* p, int32_t persistent) {
+  if (!p || (persistent != 0 && persistent != 1)) return fail(PDF_EINVAL, "pdf_pressure_set_solver: bad arguments");
+  p->pw.persistent = persistent != 0;
   return PDF_OK;
 }
 

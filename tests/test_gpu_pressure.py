@@ -42,9 +42,11 @@ def _setup(closure, wall_tag, seed=11, ppe=30, precision=capi.PDF_FP64):
     return m, gm, gp, M, ost, p
 
 
-@pytest.mark.parametrize("closure,wall_tag", [("slm", inputs.TAG_NOSLIP), ("glm", None)])
-def test_projection_matches_the_oracle(closure, wall_tag):
+@pytest.mark.parametrize("closure,wall_tag,persistent", [("slm", inputs.TAG_NOSLIP, True), ("glm", None, True),
+                                                          ("slm", inputs.TAG_NOSLIP, False)])
+def test_projection_matches_the_oracle(closure, wall_tag, persistent):
     m, gm, gp, M, ost, p = _setup(closure, wall_tag)
+    pg.pdf_pressure_set_solver(gp, persistent)
     slm = closure == "slm"
     Cp = 1e-3
     n = gm.n_nodes
@@ -116,6 +118,21 @@ def test_projection_fp32_state():
         assert_field_close(st[key], ost[key], "corrected %s (FP32 state)" % key, rtol=1e-5)
 
 
+def test_both_solvers_give_the_same_iterates():
+    """The persistent cooperative iteration and the separate kernels make the
+    same iterates up to the order of the reductions: the same iteration
+    count within one, the same pressure to the solve's tolerance."""
+    out = []
+    for persistent in (True, False):
+        m, gm, gp, M, ost, p = _setup("slm", inputs.TAG_NOSLIP)
+        pg.pdf_pressure_set_solver(gp, persistent)
+        pg.pdf_estimate_stats(gp, gm)
+        it, res = pg.pdf_pressure_project(gp, gm, p, Cp=1e-3, rtol=1e-10, max_it=500)
+        out.append((it, pg.pdf_pressure_field(gp, gm).cpu().numpy()))
+    assert abs(out[0][0] - out[1][0]) <= 1
+    assert_field_close(out[0][1], out[1][1], "persistent vs separate kernels", rtol=1e-9)
+
+
 def test_multigrid_keeps_the_iterations_few():
     """The multigrid-preconditioned iteration converges in tens of
     iterations on a 20 000-node channel (the Jacobi preconditioner needs
@@ -185,8 +202,8 @@ def test_projection_on_the_obstacle_mesh():
         assert_field_close(st[key][same], ost[key][same], "obstacle projection step %s" % key)
 
 
-@pytest.mark.parametrize("where", ["channel", "obstacles"])
-def test_inflow_outflow_projection_matches_the_oracle(where):
+@pytest.mark.parametrize("where,persistent", [("channel", True), ("obstacles", True), ("channel", False)])
+def test_inflow_outflow_projection_matches_the_oracle(where, persistent):
     """PDF_PRESSURE_PROJECTION_INOUT (the street canyon's inflow/outflow
     condition): two projections and a step, GPU and oracle each from the
     same seeded state."""
@@ -203,6 +220,7 @@ def test_inflow_outflow_projection_matches_the_oracle(where):
         extra = dict(tm_mode=cfg["tm_mode"], src_x=cfg["src"][0], src_y=cfg["src"][1], src_r=cfg["src"][2])
     gm = pg.Mesh(m)
     gp = pg.Particles(gm, seed, count=counts, u_profile=prof, u_sigma=sig)
+    pg.pdf_pressure_set_solver(gp, persistent)
     M = oracle.Mesh(m)
     ost = oracle.init(M, counts, seed, u_profile=prof, u_sigma=sig)
     p = pg.model_params(dt=2e-3, nu=5e-3, Pi=0.5, closure=closure, pressure="projection_inout", **extra)
