@@ -117,8 +117,13 @@ struct RelaxWork {
   int32_t nb = 0;
   double *f = nullptr, *L2 = nullptr, *aval = nullptr, *diag = nullptr, *g = nullptr;
   double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
-  double *part = nullptr, *scal = nullptr, *beta = nullptr, *host = nullptr;
-  int32_t* active = nullptr;
+  double *part = nullptr, *scal = nullptr, *host = nullptr;
+  int32_t *ctl = nullptr, *host_ctl = nullptr;  // device control words and their page-locked copy
+  // chunks of iterations captured as a CUDA graph on the library's stream
+  cudaStream_t cs = nullptr;
+  cudaGraphExec_t gx = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  long long graph_launches = 0;
 };
 void relax_free(RelaxWork& W);
 // One linear system of the pressure projection: its unknowns (periodic

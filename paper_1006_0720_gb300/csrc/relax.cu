@@ -199,38 +199,96 @@ __global__ void k_cg_reduce(const double* __restrict__ part, int32_t nb, int32_t
   if (threadIdx.x == 0) out[q] = s;
 }
 
-// q = A p and partials of p.q.
+// Device scalars (9 components each) and control words of the iteration.
+enum { kRPq = 0, kRRz = 9, kRRr = 18, kRBb = 27, kRTol2 = 36, kRAlpha = 45, kRBeta = 54 };
+enum { kRDone = 0, kRIt = 1, kRMaxIt = 2, kRCntSpmv = 8, kRCntUpd = 17, kRActive = 26, kRIters = 35 };
+
+// True in the block of component blockIdx.y that arrives last (its partial
+// written before); it resets the counter.
+__device__ __forceinline__ bool last_block_of(int32_t* counter) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    last = atomicAdd(counter, 1) == (int32_t)gridDim.x - 1;
+    if (last) *counter = 0;
+  }
+  __syncthreads();
+  return last;
+}
+
+__device__ __forceinline__ double sum_of(const double* part, int32_t nb) {
+  double t = 0.0;
+  for (int32_t i = threadIdx.x; i < nb; i += kRBlock) t += __ldcg(part + i);
+  return block_sum(t);  // valid in thread 0
+}
+
+// After the set-up sums (scal: [0,9) r.z, [9,18) r.r, [18,27) b.b): the
+// stopping thresholds, the active components and the control words.
+__global__ void k_cg_start(double rtol2, int32_t max_it, double* __restrict__ scal, int32_t* __restrict__ ctl) {
+  if (threadIdx.x != 0) return;
+  double rz[9], rr[9], bb[9];
+  for (int c = 0; c < 9; ++c) { rz[c] = scal[c]; rr[c] = scal[9 + c]; bb[c] = scal[18 + c]; }
+  int n_active = 0;
+  for (int c = 0; c < 9; ++c) {
+    scal[kRRz + c] = rz[c];
+    scal[kRRr + c] = rr[c];
+    scal[kRBb + c] = bb[c];
+    scal[kRTol2 + c] = rtol2 * bb[c];
+    const int a = (rr[c] > rtol2 * bb[c] && bb[c] > 0.0) ? 1 : 0;
+    ctl[kRActive + c] = a;
+    ctl[kRIters + c] = 0;
+    ctl[kRCntSpmv + c] = 0;
+    ctl[kRCntUpd + c] = 0;
+    n_active += a;
+  }
+  ctl[kRIt] = 0;
+  ctl[kRMaxIt] = max_it;
+  ctl[kRDone] = (n_active == 0 || max_it <= 0) ? 1 : 0;
+}
+
+// q = A p and p.q (last block of a component: alpha = r.z / p.q).
 __global__ void __launch_bounds__(kRBlock) k_cg_spmv(int32_t n_rep, int64_t nnz, const int32_t* __restrict__ rp,
                                                       const int32_t* __restrict__ ci, const double* __restrict__ aval,
                                                       const uint8_t* __restrict__ wall, const double* __restrict__ p,
                                                       double* __restrict__ q, double* __restrict__ part,
-                                                      const int32_t* __restrict__ active) {
+                                                      double* __restrict__ scal, int32_t* __restrict__ ctl) {
   const int ij = blockIdx.y;
+  if (ctl[kRDone] || !ctl[kRActive + ij]) return;
   const int32_t row = blockIdx.x * kRBlock + threadIdx.x;
   double pq = 0.0;
-  if (active[ij] && row < n_rep) {
+  if (row < n_rep) {
     const double v = spmv_row(row, ij, n_rep, nnz, rp, ci, aval, wall, p);
     q[(int64_t)ij * n_rep + row] = v;
     pq = v * p[(int64_t)ij * n_rep + row];
   }
+  double* pp = part + (int64_t)ij * gridDim.x;
   const double s = block_sum(pq);
-  if (threadIdx.x == 0) part[(int64_t)ij * gridDim.x + blockIdx.x] = s;
+  if (threadIdx.x == 0) pp[blockIdx.x] = s;
+  if (!last_block_of(ctl + kRCntSpmv + ij)) return;
+  const double t = sum_of(pp, gridDim.x);
+  if (threadIdx.x == 0) {
+    scal[kRPq + ij] = t;
+    scal[kRAlpha + ij] = t != 0.0 ? scal[kRRz + ij] / t : 0.0;
+  }
 }
 
-// alpha = rz / pq; x += alpha p; r -= alpha q; z = r / diag; partials of r.z, r.r.
+// x += alpha p; r -= alpha q; z = r / diag; r.z, r.r (last block of a
+// component: beta = r.z_new / r.z_old, count the iteration, retire the
+// component at r.r <= rtol^2 b.b; the last component to finish the
+// iteration stops the solve when none is left or at max_it).
 __global__ void __launch_bounds__(kRBlock) k_cg_update(int32_t n_rep, const double* __restrict__ diag,
-                                                        const uint8_t* __restrict__ wall,
-                                                        const double* __restrict__ scal, double* __restrict__ x,
-                                                        double* __restrict__ r, double* __restrict__ z,
-                                                        const double* __restrict__ p, const double* __restrict__ q,
-                                                        double* __restrict__ part, const int32_t* __restrict__ active) {
+                                                        const uint8_t* __restrict__ wall, double* __restrict__ scal,
+                                                        double* __restrict__ x, double* __restrict__ r,
+                                                        double* __restrict__ z, const double* __restrict__ p,
+                                                        const double* __restrict__ q, double* __restrict__ part,
+                                                        int32_t* __restrict__ ctl) {
   const int ij = blockIdx.y;
+  if (ctl[kRDone] || !ctl[kRActive + ij]) return;
   const int32_t row = blockIdx.x * kRBlock + threadIdx.x;
   double rz = 0.0, rr = 0.0;
-  if (active[ij] && row < n_rep) {
-    const double pq = scal[ij];        // p.q
-    const double rzo = scal[9 + ij];   // previous r.z
-    const double alpha = pq != 0.0 ? rzo / pq : 0.0;
+  if (row < n_rep) {
+    const double alpha = scal[kRAlpha + ij];
     const int64_t o = (int64_t)ij * n_rep + row;
     x[o] += alpha * p[o];
     const double res = r[o] - alpha * q[o];
@@ -241,21 +299,46 @@ __global__ void __launch_bounds__(kRBlock) k_cg_update(int32_t n_rep, const doub
     rz = res * zz;
     rr = res * res;
   }
+  double* p1 = part + (int64_t)(9 + ij) * gridDim.x;
+  double* p2 = part + (int64_t)(18 + ij) * gridDim.x;
   const double s1 = block_sum(rz), s2 = block_sum(rr);
   if (threadIdx.x == 0) {
-    part[(int64_t)(0 * 9 + ij) * gridDim.x + blockIdx.x] = s1;
-    part[(int64_t)(1 * 9 + ij) * gridDim.x + blockIdx.x] = s2;
+    p1[blockIdx.x] = s1;
+    p2[blockIdx.x] = s2;
+  }
+  if (!last_block_of(ctl + kRCntUpd + ij)) return;
+  const double rzn = sum_of(p1, gridDim.x), rrn = sum_of(p2, gridDim.x);
+  if (threadIdx.x == 0) {
+    const double rzo = scal[kRRz + ij];
+    scal[kRBeta + ij] = rzo != 0.0 ? rzn / rzo : 0.0;
+    scal[kRRz + ij] = rzn;
+    scal[kRRr + ij] = rrn;
+    ctl[kRIters + ij] += 1;
+    if (rrn <= scal[kRTol2 + ij]) ctl[kRActive + ij] = 0;
   }
 }
 
-// p = z + beta p, beta = rz_new / rz_old.
-__global__ void k_cg_dir(int32_t n_rep, const double* __restrict__ beta, const double* __restrict__ z,
-                         double* __restrict__ p, const int32_t* __restrict__ active) {
+// p = z + beta p for the active components; one thread closes the
+// iteration: it counts it and stops the solve when every component is done
+// or at max_it.
+__global__ void k_cg_dir(int32_t n_rep, const double* __restrict__ scal, const double* __restrict__ z,
+                         double* __restrict__ p, int32_t* __restrict__ ctl) {
   const int ij = blockIdx.y;
+  if (ctl[kRDone]) return;
   const int32_t row = blockIdx.x * kRBlock + threadIdx.x;
-  if (!active[ij] || row >= n_rep) return;
-  const int64_t o = (int64_t)ij * n_rep + row;
-  p[o] = z[o] + beta[ij] * p[o];
+  if (ctl[kRActive + ij] && row < n_rep) {
+    const int64_t o = (int64_t)ij * n_rep + row;
+    p[o] = z[o] + scal[kRBeta + ij] * p[o];
+  }
+}
+
+__global__ void k_cg_close(int32_t* __restrict__ ctl) {
+  if (threadIdx.x != 0 || ctl[kRDone]) return;
+  const int32_t it = ctl[kRIt] + 1;
+  ctl[kRIt] = it;
+  int n_active = 0;
+  for (int c = 0; c < 9; ++c) n_active += ctl[kRActive + c];
+  if (n_active == 0 || it >= ctl[kRMaxIt]) ctl[kRDone] = 1;
 }
 
 __global__ void k_cg_diag(int32_t n_rep, int64_t nnz, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
@@ -304,20 +387,71 @@ static pdf_status relax_alloc(pdf_particles* P) {
   A((void**)&W.p, sizeof(double) * 9 * R.n_rep);
   A((void**)&W.q, sizeof(double) * 9 * R.n_rep);
   A((void**)&W.part, sizeof(double) * 3 * 9 * nb);
-  A((void**)&W.scal, sizeof(double) * 64);  // [0,9) p.q  [9,18) r.z  [18,36) r.z, r.r  (and the 27 set-up sums)
-  A((void**)&W.beta, sizeof(double) * 9);
-  A((void**)&W.active, sizeof(int32_t) * 9);
+  A((void**)&W.scal, sizeof(double) * 64);
+  A((void**)&W.ctl, sizeof(int32_t) * 64);
+  if (e == cudaSuccess) e = cudaMemset(W.ctl, 0, sizeof(int32_t) * 64);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&W.host, sizeof(double) * 64);
-  if (e != cudaSuccess) return cuda_fail(e, "pdf_relax_solve: allocation");
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&W.host_ctl, sizeof(int32_t) * 64);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&W.cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&W.ev0, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&W.ev1, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    relax_free(W);
+    return cuda_fail(e, "pdf_relax_solve: allocation");
+  }
   return PDF_OK;
 }
 
 void relax_free(RelaxWork& W) {
   cudaFree(W.f); cudaFree(W.g); cudaFree(W.L2); cudaFree(W.aval); cudaFree(W.diag); cudaFree(W.x); cudaFree(W.r);
-  cudaFree(W.z); cudaFree(W.p); cudaFree(W.q); cudaFree(W.part); cudaFree(W.scal); cudaFree(W.beta);
-  cudaFree(W.active);
+  cudaFree(W.z); cudaFree(W.p); cudaFree(W.q); cudaFree(W.part); cudaFree(W.scal); cudaFree(W.ctl);
   if (W.host) cudaFreeHost(W.host);
+  if (W.host_ctl) cudaFreeHost(W.host_ctl);
+  if (W.gx) cudaGraphExecDestroy(W.gx);
+  if (W.ev0) cudaEventDestroy(W.ev0);
+  if (W.ev1) cudaEventDestroy(W.ev1);
+  if (W.cs) cudaStreamDestroy(W.cs);
   W = RelaxWork();
+}
+
+// k iterations of the nine components (every kernel returns at once after
+// the stop).
+static pdf_status relax_iterations(pdf_particles* P, int k, cudaStream_t st) {
+  const RelaxMesh& R = P->mesh->rx;
+  RelaxWork& W = P->rx;
+  const dim3 grid(W.nb, 9);
+  for (int i = 0; i < k; ++i) {
+    PDF_KERNEL("k_cg_spmv", st, k_cg_spmv<<<grid, kRBlock, 0, st>>>(R.n_rep, R.nnz, R.rp, R.ci, W.aval, R.wall, W.p,
+                                                                     W.q, W.part, W.scal, W.ctl));
+    PDF_KERNEL("k_cg_update", st, k_cg_update<<<grid, kRBlock, 0, st>>>(R.n_rep, W.diag, R.wall, W.scal, W.x, W.r,
+                                                                         W.z, W.p, W.q, W.part, W.ctl));
+    PDF_KERNEL("k_cg_dir", st, k_cg_dir<<<grid, kRBlock, 0, st>>>(R.n_rep, W.scal, W.z, W.p, W.ctl));
+    PDF_KERNEL("k_cg_close", st, k_cg_close<<<1, 32, 0, st>>>(W.ctl));
+  }
+  return PDF_OK;
+}
+
+static pdf_status relax_capture(pdf_particles* P, int k) {
+  RelaxWork& W = P->rx;
+  const long long n0 = prof_launches();
+  PDF_CUDA(cudaStreamBeginCapture(W.cs, cudaStreamCaptureModeThreadLocal));
+  pdf_status s = relax_iterations(P, k, W.cs);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(W.cs, &g);
+  if (s != PDF_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "pdf_relax_solve: graph capture");
+  const cudaError_t e2 = cudaGraphInstantiate(&W.gx, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) {
+    W.gx = nullptr;
+    return cuda_fail(e2, "pdf_relax_solve: graph instantiation");
+  }
+  W.graph_launches = prof_launches() - n0;
+  prof_count(-W.graph_launches);  // captured, not launched
+  return PDF_OK;
 }
 
 static RelaxParams relax_params(const pdf_model_params* p) {
@@ -379,53 +513,48 @@ extern "C" pdf_status pdf_relax_solve(pdf_particles* p, const pdf_mesh* m, const
                                                                    R.wall, R.rep_node, nn, W.f, W.g, wp, W.x, W.r, W.z,
                                                                    W.p, W.part));
   PDF_KERNEL("k_cg_reduce", st, k_cg_reduce<<<27, kRBlock, 0, st>>>(W.part, nb, 3, W.scal));
-  PDF_CUDA(cudaMemcpyAsync(W.host, W.scal, sizeof(double) * 27, cudaMemcpyDeviceToHost, st));
-  PDF_CUDA(cudaStreamSynchronize(st));
-  double rz[9], bn[9], rn[9];
-  int32_t act[9], it_done[9];
-  int n_active = 0;
-  for (int c = 0; c < 9; ++c) {
-    rz[c] = W.host[c];
-    rn[c] = std::sqrt(W.host[9 + c]);
-    bn[c] = std::sqrt(W.host[18 + c]);
-    act[c] = (rn[c] > rtol * bn[c] && bn[c] > 0.0) ? 1 : 0;
-    it_done[c] = 0;
-    n_active += act[c];
-  }
-  double scal_host[18];
-  int it = 0;
-  while (n_active > 0 && it < max_it) {
-    for (int c = 0; c < 9; ++c) scal_host[9 + c] = rz[c];
-    PDF_CUDA(cudaMemcpyAsync(W.active, act, sizeof(act), cudaMemcpyHostToDevice, st));
-    PDF_CUDA(cudaMemcpyAsync(W.scal + 9, scal_host + 9, sizeof(double) * 9, cudaMemcpyHostToDevice, st));
-    PDF_KERNEL("k_cg_spmv", st, k_cg_spmv<<<grid, kRBlock, 0, st>>>(R.n_rep, R.nnz, R.rp, R.ci, W.aval, R.wall, W.p, W.q,
-                                                                     W.part, W.active));
-    PDF_KERNEL("k_cg_reduce", st, k_cg_reduce<<<9, kRBlock, 0, st>>>(W.part, nb, 1, W.scal));
-    PDF_KERNEL("k_cg_update", st, k_cg_update<<<grid, kRBlock, 0, st>>>(R.n_rep, W.diag, R.wall, W.scal, W.x, W.r, W.z,
-                                                                         W.p, W.q, W.part, W.active));
-    PDF_KERNEL("k_cg_reduce", st, k_cg_reduce<<<18, kRBlock, 0, st>>>(W.part, nb, 2, W.scal + 18));
-    PDF_CUDA(cudaMemcpyAsync(W.host, W.scal + 18, sizeof(double) * 18, cudaMemcpyDeviceToHost, st));
-    PDF_CUDA(cudaStreamSynchronize(st));
-    ++it;
-    double beta[9];
-    for (int c = 0; c < 9; ++c) {
-      beta[c] = 0.0;
-      if (!act[c]) continue;
-      const double rzn = W.host[c];
-      rn[c] = std::sqrt(W.host[9 + c]);
-      beta[c] = rz[c] != 0.0 ? rzn / rz[c] : 0.0;
-      rz[c] = rzn;
-      it_done[c] = it;
-      if (rn[c] <= rtol * bn[c]) { act[c] = 0; --n_active; }
+  PDF_KERNEL("k_cg_start", st, k_cg_start<<<1, 32, 0, st>>>(rtol * rtol, max_it, W.scal, W.ctl));
+  // iterations in chunks of 8 (CUDA-graph replays while kernel timing is
+  // off); the host reads the control words once per chunk
+  constexpr int kChunk = 8;
+  if (prof_timing()) {
+    for (int launched = 0; launched < max_it; launched += kChunk) {
+      s = relax_iterations(p, kChunk, st);
+      if (s != PDF_OK) return s;
+      PDF_CUDA(cudaMemcpyAsync(W.host_ctl, W.ctl, sizeof(int32_t) * 64, cudaMemcpyDeviceToHost, st));
+      PDF_CUDA(cudaStreamSynchronize(st));
+      if (W.host_ctl[kRDone]) break;
     }
-    if (n_active == 0) break;
-    PDF_CUDA(cudaMemcpyAsync(W.beta, beta, sizeof(beta), cudaMemcpyHostToDevice, st));
-    PDF_CUDA(cudaMemcpyAsync(W.active, act, sizeof(act), cudaMemcpyHostToDevice, st));
-    PDF_KERNEL("k_cg_dir", st, k_cg_dir<<<grid, kRBlock, 0, st>>>(R.n_rep, W.beta, W.z, W.p, W.active));
+  } else if (max_it > 0) {
+    if (!W.gx) {
+      s = relax_capture(p, kChunk);
+      if (s != PDF_OK) return s;
+    }
+    PDF_CUDA(cudaEventRecord(W.ev0, st));
+    PDF_CUDA(cudaStreamWaitEvent(W.cs, W.ev0, 0));
+    for (int launched = 0; launched < max_it; launched += kChunk) {
+      PDF_CUDA(cudaGraphLaunch(W.gx, W.cs));
+      prof_count(W.graph_launches);
+      PDF_CUDA(cudaMemcpyAsync(W.host_ctl, W.ctl, sizeof(int32_t) * 64, cudaMemcpyDeviceToHost, W.cs));
+      PDF_CUDA(cudaStreamSynchronize(W.cs));
+      if (W.host_ctl[kRDone]) break;
+    }
+    PDF_CUDA(cudaEventRecord(W.ev1, W.cs));
+    PDF_CUDA(cudaStreamWaitEvent(st, W.ev1, 0));
+  }
+  PDF_CUDA(cudaMemcpyAsync(W.host, W.scal, sizeof(double) * 64, cudaMemcpyDeviceToHost, st));
+  PDF_CUDA(cudaMemcpyAsync(W.host_ctl, W.ctl, sizeof(int32_t) * 64, cudaMemcpyDeviceToHost, st));
+  PDF_CUDA(cudaStreamSynchronize(st));
+  int n_active = 0;
+  double rn[9], bn[9];
+  for (int c = 0; c < 9; ++c) {
+    rn[c] = std::sqrt(W.host[kRRr + c]);
+    bn[c] = std::sqrt(W.host[kRBb + c]);
+    n_active += W.host_ctl[kRActive + c];
   }
   PDF_KERNEL("k_cg_scatter", st, k_cg_scatter<<<dim3(rblocks(nn), 9), 256, 0, st>>>(nn, R.node_rep, R.n_rep, W.x, wp));
   for (int c = 0; c < 9; ++c) {
-    if (iters) iters[c] = it_done[c];
+    if (iters) iters[c] = W.host_ctl[kRIters + c];
     if (rel_res) rel_res[c] = bn[c] > 0.0 ? rn[c] / bn[c] : 0.0;
   }
   if (n_active > 0) return fail(PDF_ENOTCONV, "pdf_relax_solve: iteration cap reached");
