@@ -107,6 +107,9 @@ def lib():
             L.or_noslip_omega.argtypes = [ctypes.c_void_p, PD, PD]
             L.or_mesh_noslip.argtypes = [ctypes.c_void_p, PI, PD]
             L.or_iecm_cond.argtypes = [I, ctypes.c_long, PI, PD, PD, PD, PD, PI, I, I, I, I, PD]
+            L.or_redistribute.argtypes = [ctypes.c_void_p, ctypes.c_long] + [PD] * 7 + [PI, PI, I,
+                                                                                       ctypes.c_uint64, U32]
+            L.or_redistribute.restype = ctypes.c_long
             _lib = L
     return _lib
 
@@ -303,6 +306,18 @@ def iecm_cond(n_tri, st, bins=(5, 5, 5), m_min=2, pid=None):
                        None if pid is None else _p(pid, I), int(bins[0]), int(bins[1]), int(bins[2]),
                        int(m_min), _p(out, D))
     return out
+
+
+def redistribute(mesh, st, min_npel, seed, step, pid=None):
+    """The particle redistribution of App. D, in place; returns the number
+    of particles moved."""
+    for k in STATE_KEYS:
+        st[k] = np.ascontiguousarray(st[k], dtype=np.float64)
+    st["elem"] = np.ascontiguousarray(st["elem"], dtype=np.int32)
+    pid = None if pid is None else np.ascontiguousarray(pid, dtype=np.int32)
+    return int(lib().or_redistribute(mesh._h, len(st["x"]), *[_p(st[k], D) for k in STATE_KEYS],
+                                     _p(st["elem"], I), None if pid is None else _p(pid, I), int(min_npel),
+                                     int(seed), int(step)))
 
 
 def noslip_omega(mesh, ns):

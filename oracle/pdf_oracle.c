@@ -146,7 +146,7 @@ void or_gauss_fill(uint64_t seed, long n, uint32_t c1, uint32_t c2, uint32_t c3,
 }
 
 /* Counter purposes. */
-enum { OR_PURPOSE_STEP = 0, OR_PURPOSE_INIT = 1 };
+enum { OR_PURPOSE_STEP = 0, OR_PURPOSE_INIT = 1, OR_PURPOSE_REDIST = 2 };
 
 /* ------------------------------------------------------------------------ */
 /* Mesh connectivity (sec. 3.3 linked lists; sec. 3.5 element-surrounding-  */
@@ -1015,3 +1015,94 @@ void or_step(const or_mesh* m, long n_p, const double* rows, const or_params* P,
     if (!(ti.status & OR_TRK_LOST)) elem[p] = en;
   }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Particle redistribution, the more efficient algorithm of App. D (the     */
+/* basic idea in App. C, sec. 3.6): the elements sorted by their particle   */
+/* count (ascending); for the k-th element of the sorted order with fewer   */
+/* than min_npel particles (the critical ones, k = 0, 1, ...) the k-th      */
+/* element from the top gives min_npel - n_k of its particles, which take   */
+/* the properties (position, U, omega, psi) of the critical element's       */
+/* particles in turn (p mod n_k); a particle moved into an empty element    */
+/* keeps its properties and is placed uniformly in it.  The counts and the  */
+/* element lists are those before any move (the listing regenerates them    */
+/* once, at the end).                                                        */
+/* READINGS: ties in the sort by element index (a stable sort); "the p-th   */
+/* particle of an element" is the one with the p-th smallest particle id;   */
+/* the loop stops when the donor from the top would be a critical element   */
+/* itself or the same element (k >= n_tri - 1 - k), and a donor gives at    */
+/* most all its particles; the uniform point: Philox counter                */
+/* (pid, step, 0, purpose REDIST), words 0, 1 as the barycentric (r1, r2)   */
+/* of the initialisation.  pid may be NULL (the index).  Returns the number */
+/* of particles moved.                                                       */
+/* ------------------------------------------------------------------------ */
+static const int* g_sort_cnt;
+static int cmp_count_index(const void* a, const void* b) {
+  const int i = *(const int*)a, j = *(const int*)b;
+  if (g_sort_cnt[i] != g_sort_cnt[j]) return g_sort_cnt[i] < g_sort_cnt[j] ? -1 : 1;
+  return i < j ? -1 : (i > j ? 1 : 0);
+}
+static const int* g_sort_pid;
+static int cmp_pid(const void* a, const void* b) {
+  const long i = *(const long*)a, j = *(const long*)b;
+  const long pi = g_sort_pid ? g_sort_pid[i] : i, pj = g_sort_pid ? g_sort_pid[j] : j;
+  return pi < pj ? -1 : (pi > pj ? 1 : 0);
+}
+
+long or_redistribute(const or_mesh* m, long n, double* x, double* y, double* u, double* v, double* w,
+                     double* om, double* ps, int* elem, const int* pid, int min_npel, uint64_t seed,
+                     uint32_t step) {
+  const int nt = m->n_tri;
+  int* cnt = (int*)calloc(nt, sizeof(int));
+  for (long p = 0; p < n; ++p) cnt[elem[p]]++;
+  long* off = (long*)calloc(nt + 1, sizeof(long));
+  for (int e = 0; e < nt; ++e) off[e + 1] = off[e] + cnt[e];
+  long* lst = (long*)malloc(sizeof(long) * (n > 0 ? n : 1));
+  long* fill = (long*)malloc(sizeof(long) * (nt + 1));
+  for (int e = 0; e <= nt; ++e) fill[e] = off[e];
+  for (long p = 0; p < n; ++p) lst[fill[elem[p]]++] = p;
+  g_sort_pid = pid;
+  for (int e = 0; e < nt; ++e) qsort(lst + off[e], (size_t)cnt[e], sizeof(long), cmp_pid);
+  int* order = (int*)malloc(sizeof(int) * nt);
+  for (int e = 0; e < nt; ++e) order[e] = e;
+  g_sort_cnt = cnt;
+  qsort(order, (size_t)nt, sizeof(int), cmp_count_index);
+  int nce = 0;
+  while (nce < nt && cnt[order[nce]] < min_npel) ++nce;
+  long moved = 0;
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int k = 0; k < nce; ++k) {
+    if (nt - 1 - k <= k) break;
+    const int j = order[k], i = order[nt - 1 - k];
+    const int nj = cnt[j], ni = cnt[i];
+    int d = min_npel - nj;
+    if (d > ni) d = ni;
+    for (int q = 0; q < d; ++q) {
+      const long pi = lst[off[i] + q];
+      if (nj > 0) {
+        const long pj = lst[off[j] + q % nj];
+        x[pi] = x[pj]; y[pi] = y[pj];
+        u[pi] = u[pj]; v[pi] = v[pj]; w[pi] = w[pj];
+        om[pi] = om[pj]; ps[pi] = ps[pj];
+      } else {
+        const uint32_t id = pid ? (uint32_t)pid[pi] : (uint32_t)pi;
+        uint32_t ctr[4] = {id, step, 0u, OR_PURPOSE_REDIST}, wd[4];
+        or_philox(ctr, key, wd);
+        float r1 = or_u01(wd[0]), r2 = or_u01(wd[1]);
+        if (r1 + r2 > 1.0f) { r1 = 1.0f - r1; r2 = 1.0f - r2; }
+        const int* t = m->tri + 3 * j;
+        const double xa = m->xy[2 * t[0]], ya = m->xy[2 * t[0] + 1];
+        const double xb = m->xy[2 * t[1]], yb = m->xy[2 * t[1] + 1];
+        const double xc = m->xy[2 * t[2]], yc = m->xy[2 * t[2] + 1];
+        const double R1 = (double)r1, R2 = (double)r2;
+        x[pi] = xa + R1 * (xb - xa) + R2 * (xc - xa);
+        y[pi] = ya + R1 * (yb - ya) + R2 * (yc - ya);
+      }
+      elem[pi] = j;
+      ++moved;
+    }
+  }
+  free(cnt); free(off); free(lst); free(fill); free(order);
+  return moved;
+}
+
