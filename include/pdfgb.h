@@ -359,6 +359,29 @@ pdf_status pdf_relax_rhs(pdf_particles* p, const pdf_mesh* m, const pdf_model_pa
  * that edge's unit outward normal [n_nodes][2]; either may be NULL. */
 pdf_status pdf_mesh_wall_distance(const pdf_mesh* m, double* dist, double* normal);
 
+/* ---------------------------------------------------------------- particle redistribution */
+
+/* Particle redistribution (the more efficient algorithm of App. D; its idea
+ * in App. C and sec. 3.6), typically after pdf_step and before
+ * pdf_estimate_stats: the elements are sorted by their particle count
+ * (ties by element index); the k-th element with fewer than min_npel
+ * particles (k = 0, 1, ...) receives min_npel - n_k particles from the k-th
+ * element from the top (at most all of them; it stops where the donor
+ * would be a critical element itself).  The moved particles are the
+ * donor's lowest particle ids; they copy the position, U, omega and psi of
+ * the receiving element's particles in turn (donor particle p copies the
+ * receiving element's particle p mod n_k, ordered by particle id), or, into
+ * an empty element, keep their values and are placed uniformly in it
+ * (Philox4x32-10 keyed by seed, counter (particle id, step, 0, 2); words 0,
+ * 1 as the initialisation's barycentric (r1, r2)).  Particle ids (the
+ * random streams) stay with the moved particles.
+ *   min_npel in [1, 64], else PDF_EINVAL
+ *   moved    host or NULL: the number of particles moved
+ * Synchronizes `stream`.  The statistics must be estimated again before
+ * the next step (PDF_ESTATE otherwise). */
+pdf_status pdf_redistribute(pdf_particles* p, const pdf_mesh* m, int32_t min_npel, uint64_t seed, uint32_t step,
+                            int32_t* moved, void* stream);
+
 /* ---------------------------------------------------------------- pressure projection */
 
 /* The stabilised pressure projection (sec. 3.2: eqs. velocity-prediction,

@@ -247,6 +247,15 @@ def pdf_pressure_project(particles, mesh, params, Cp=None, rtol=1e-10, max_it=20
     return it.value, res.value
 
 
+def pdf_redistribute(particles, mesh, min_npel, seed, step, stream=None):
+    """Particle redistribution (App. D); returns the number of particles
+    moved.  Estimate the statistics again before the next step."""
+    moved = ctypes.c_int32()
+    check(lib().pdf_redistribute(particles.handle, mesh.handle, int(min_npel), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                 int(step) & 0xFFFFFFFF, ctypes.byref(moved), _stream(stream)), "pdf_redistribute")
+    return moved.value
+
+
 def pdf_pressure_set_solver(particles, persistent=False):
     check(lib().pdf_pressure_set_solver(particles.handle, 1 if persistent else 0), "pdf_pressure_set_solver")
 

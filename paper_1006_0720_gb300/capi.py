@@ -77,6 +77,7 @@ PROTOTYPES = {
     "pdf_particles_set_iecm": (I32, [V, I32, I32, I32, I32]),
     "pdf_iecm_cond": (I32, [V, V, V]),
     "pdf_pressure_project": (I32, [V, V, ctypes.POINTER(ModelParams), D, D, I32, ctypes.POINTER(I32), ctypes.POINTER(D), V]),
+    "pdf_redistribute": (I32, [V, V, I32, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(I32), V]),
     "pdf_pressure_set_solver": (I32, [V, I32]),
     "pdf_pressure_field": (I32, [V, V, V, V]),
     "pdf_particles_get_state": (I32, [V, V, V, V, V, V, V, V, V, V]),

@@ -163,6 +163,12 @@ struct PressWork {
   double* host = nullptr;
 };
 void press_free(PressWork& W);
+// The particle redistribution's work space (allocated on first use).
+struct RedistWork {
+  int32_t *cnt = nullptr, *k0 = nullptr, *v0 = nullptr, *k1 = nullptr, *v1 = nullptr;
+  int32_t *hist = nullptr, *hist_part = nullptr, *dev = nullptr, *host = nullptr;
+};
+void redist_free(RedistWork& W);
 }  // namespace pdfgb
 
 struct pdf_mesh {
@@ -267,6 +273,7 @@ struct pdf_particles {
   double* pres = nullptr;   // [n_nodes]
   double* gradP = nullptr;  // [n_nodes][2]
   pdfgb::PressWork pw;
+  pdfgb::RedistWork rd;
 };
 
 namespace pdfgb {

@@ -165,6 +165,7 @@ static void free_particles(pdf_particles* p) {
   cudaFree(p->pres); cudaFree(p->gradP);
   relax_free(p->rx);
   press_free(p->pw);
+  redist_free(p->rd);
   delete p;
 }
 

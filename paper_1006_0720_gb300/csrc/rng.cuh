@@ -104,6 +104,6 @@ __device__ __forceinline__ void gauss4(uint64_t seed, uint32_t c0, uint32_t c1, 
   box_muller(c[2], c[3], &g[2], &g[3]);
 }
 
-enum : uint32_t { kPurposeStep = 0, kPurposeInit = 1 };
+enum : uint32_t { kPurposeStep = 0, kPurposeInit = 1, kPurposeRedist = 2 };
 
 }  // namespace pdfgb

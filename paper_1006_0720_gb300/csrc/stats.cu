@@ -819,4 +819,38 @@ pdf_status estimate_stats_with_buffers(pdf_particles* P, int32_t* keys_a, int32_
   return iecm_cond(P, seg, vin, st);
 }
 
+// Stable LSD radix sort of n non-negative int32 keys below 2^bits, the
+// values the original indices; ping-pong buffers k0/v0, k1/v1 of n entries,
+// hist of radix_tiles(n) * radix_bins() and hist_part of
+// radix_scan_blocks(hist_len) + 1 entries.  *keys_out / *vals_out receive
+// the sorted buffers.
+pdf_status radix_sort_index(const int32_t* keys, int64_t n, int bits, int32_t* k0, int32_t* v0, int32_t* k1,
+                            int32_t* v1, int32_t* hist, int32_t* hist_part, const int32_t** keys_out,
+                            const int32_t** vals_out, cudaStream_t st) {
+  const int64_t n_tiles = radix_tiles(n);
+  const int64_t hist_len = n_tiles * kBins;
+  const int32_t n_scan = radix_scan_blocks(hist_len);
+  const int passes = std::max(1, (bits + kRadixBits - 1) / kRadixBits);
+  const int32_t* kin = keys;
+  const int32_t* vin = nullptr;
+  int32_t* kout[2] = {k0, k1};
+  int32_t* vout[2] = {v0, v1};
+  for (int pass = 0; pass < passes; ++pass) {
+    const int shift = pass * kRadixBits;
+    int32_t* ko = kout[pass & 1];
+    int32_t* vo = vout[pass & 1];
+    PDF_KERNEL("k_radix_hist", st, k_radix_hist<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(kin, n, shift, n_tiles, hist));
+    PDF_KERNEL("k_scan_reduce", st, k_scan_reduce<<<n_scan, 1024, 0, st>>>(hist, hist_len, hist_part));
+    PDF_KERNEL("k_scan_top", st, k_scan_top<<<1, 1024, 0, st>>>(hist_part, n_scan));
+    PDF_KERNEL("k_scan_apply", st, k_scan_apply<<<n_scan, 1024, 0, st>>>(hist, hist_len, hist_part));
+    PDF_KERNEL("k_radix_scatter", st, k_radix_scatter<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(
+                                          kin, vin, n, shift, n_tiles, hist, ko, vo));
+    kin = ko;
+    vin = vo;
+  }
+  *keys_out = kin;
+  *vals_out = vin;
+  return PDF_OK;
+}
+
 }  // namespace pdfgb
