@@ -167,6 +167,8 @@ void press_free(PressWork& W);
 struct RedistWork {
   int32_t *cnt = nullptr, *k0 = nullptr, *v0 = nullptr, *k1 = nullptr, *v1 = nullptr;
   int32_t *hist = nullptr, *hist_part = nullptr, *dev = nullptr, *host = nullptr;
+  int32_t *role = nullptr, *cur = nullptr;
+  int64_t* off = nullptr;
 };
 void redist_free(RedistWork& W);
 }  // namespace pdfgb

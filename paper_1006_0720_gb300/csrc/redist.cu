@@ -10,6 +10,11 @@
 // element lists are those before any move.  One warp per critical element:
 // the donors and the critical elements are disjoint, so the warps write
 // disjoint particles and read only unmoved ones.
+//
+// No grouping of all particles is needed: the counts come from a histogram
+// of the element ids (warp-aggregated atomics), and only the particles of
+// the critical elements and their donors are collected, unordered, into
+// per-element lists (the ordering by particle id happens in the warps).
 #include <algorithm>
 
 #include "common.cuh"
@@ -17,7 +22,6 @@
 
 namespace pdfgb {
 
-pdf_status group_by_element(pdf_particles* P, cudaStream_t st);
 pdf_status radix_sort_index(const int32_t* keys, int64_t n, int bits, int32_t* k0, int32_t* v0, int32_t* k1,
                             int32_t* v1, int32_t* hist, int32_t* hist_part, const int32_t** keys_out,
                             const int32_t** vals_out, cudaStream_t st);
@@ -27,9 +31,17 @@ int32_t radix_scan_blocks(int64_t hist_len);
 
 constexpr int kMaxMin = 64;  // largest min_npel (the critical element's particles fit a warp's scratch)
 
-__global__ void k_rd_counts(int32_t n_tri, const int32_t* __restrict__ seg, int32_t* __restrict__ cnt) {
-  for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n_tri; e += gridDim.x * blockDim.x)
-    cnt[e] = seg[e + 1] - seg[e];
+// cnt[e] += the particles with element e (cnt zeroed before): lanes with
+// the same element add once.
+__global__ void k_rd_hist(int64_t n, const int32_t* __restrict__ elem, int32_t* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 32; base < n; base += nw * 32) {
+    const int64_t p = base + lane;
+    const int32_t e = p < n ? elem[p] : -1;
+    const unsigned same = __match_any_sync(0xffffffffu, e);
+    if (e >= 0 && lane == __ffs(same) - 1) atomicAdd(cnt + e, __popc(same));
+  }
 }
 
 // dev[0] = the number of critical elements (first sorted count >= min_npel),
@@ -45,11 +57,75 @@ __global__ void k_rd_nce(int32_t n_tri, const int32_t* __restrict__ sk, int32_t 
   dev[1] = 0;
 }
 
+// role[j] = k + 1 for the k-th critical element j with a donor, role[i] =
+// -(k + 1) for its donor i (role zeroed before).
+__global__ void k_rd_roles(int32_t n_tri, const int32_t* __restrict__ sv, const int32_t* __restrict__ dev,
+                           int32_t* __restrict__ role) {
+  const int32_t nce = dev[0];
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nce; k += gridDim.x * blockDim.x) {
+    if (n_tri - 1 - k <= k) continue;
+    role[sv[k]] = k + 1;
+    role[sv[n_tri - 1 - k]] = -(k + 1);
+  }
+}
+
+// off[k] = sum over k' < k of (n_crit(k') + n_donor(k')): the start of the
+// k-th pair's lists (critical first, then the donor's); one block.
+__global__ void __launch_bounds__(1024) k_rd_offsets(int32_t n_tri, const int32_t* __restrict__ sk,
+                                                     const int32_t* __restrict__ dev, int64_t* __restrict__ off) {
+  __shared__ int64_t sh[1024];
+  const int32_t nce = dev[0];
+  int64_t carry = 0;
+  for (int32_t b0 = 0; b0 < nce; b0 += 1024) {
+    const int32_t k = b0 + threadIdx.x;
+    int64_t v = 0;
+    if (k < nce && n_tri - 1 - k > k) v = (int64_t)sk[k] + sk[n_tri - 1 - k];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan
+      const int64_t t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (k < nce) off[k] = carry + sh[threadIdx.x] - v;
+    carry += sh[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) off[nce] = carry;
+}
+
+// The particles of the critical elements and their donors into the pairs'
+// lists (unordered); cur: [n_tri] cursors of the critical lists, then
+// [n_tri] of the donor lists (zeroed before).  Lanes with the same role take
+// their places with one atomic (the particles are mostly grouped by element).
+__global__ void k_rd_collect(int64_t n, int32_t n_tri, const int32_t* __restrict__ elem,
+                             const int32_t* __restrict__ role, const int32_t* __restrict__ sk,
+                             const int64_t* __restrict__ off, int32_t* __restrict__ cur, int32_t* __restrict__ list) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 32; base < n; base += nw * 32) {
+    const int64_t s = base + lane;
+    const int32_t r = s < n ? role[elem[s]] : 0;
+    const unsigned same = __match_any_sync(0xffffffffu, r);
+    if (r == 0) continue;
+    const int leader = __ffs(same) - 1;
+    const int32_t k = r > 0 ? r - 1 : -r - 1;
+    int32_t* c = r > 0 ? cur + k : cur + n_tri + k;
+    int32_t at = 0;
+    if (lane == leader) at = atomicAdd(c, __popc(same));
+    at = __shfl_sync(same, at, leader) + __popc(same & ((1u << lane) - 1u));
+    const int64_t o = off[k] + (r > 0 ? 0 : sk[k]);
+    list[o + at] = (int32_t)s;
+  }
+}
+
 struct RdArgs {
   int32_t n_tri, min_npel;
   uint32_t step;
   uint64_t seed;
-  const int32_t *sk, *sv, *seg, *order, *pid, *tri;
+  const int32_t *sk, *sv, *list, *pid, *tri;
+  const int64_t* off;
   const double* xy;
   int32_t* elem;
   int64_t *x, *y;
@@ -59,30 +135,37 @@ struct RdArgs {
   int32_t* dev;
 };
 
-__global__ void __launch_bounds__(256) k_rd_move(RdArgs A) {
-  __shared__ int32_t s_cslot[8][kMaxMin], s_cpid[8][kMaxMin], s_dslot[8][kMaxMin];
+constexpr int kRdWarps = 4;      // warps per block of the move kernel
+constexpr int kRdStage = 1024;   // donor particles staged in shared memory per warp
+
+__global__ void __launch_bounds__(kRdWarps * 32) k_rd_move(RdArgs A) {
+  __shared__ int32_t s_cslot[kRdWarps][kMaxMin], s_cpid[kRdWarps][kMaxMin], s_dslot[kRdWarps][kMaxMin];
+  __shared__ int32_t s_dpid[kRdWarps][kRdStage], s_dsl[kRdWarps][kRdStage];
   const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int32_t nce = A.dev[0];
   int32_t* cslot = s_cslot[wi];
   int32_t* cpid = s_cpid[wi];
   int32_t* dslot = s_dslot[wi];
+  int32_t* dpid = s_dpid[wi];
+  int32_t* dsl = s_dsl[wi];
   const int32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nce; k += nwarps) {
     const int32_t di = A.n_tri - 1 - k;
     if (di <= k) break;  // the donor from the top would be critical itself
     const int32_t j = A.sv[k], nj = A.sk[k];
-    const int32_t i = A.sv[di], ni = A.sk[di];
+    const int32_t ni = A.sk[di];
     const int32_t d = min(A.min_npel - nj, ni);
     // the critical element's particles ordered by particle id
     __syncwarp();
     int32_t my_slot[2], my_pid[2];
+    const int32_t* clist = A.list + A.off[k];
+    const int32_t* dlist = clist + nj;
     for (int r = 0; r < 2; ++r) {
       const int32_t a = lane + 32 * r;
       my_slot[r] = -1;
       my_pid[r] = 0;
       if (a < nj) {
-        const int32_t at = A.seg[j] + a;
-        my_slot[r] = A.order ? A.order[at] : at;
+        my_slot[r] = clist[a];
         my_pid[r] = A.pid[my_slot[r]];
         cpid[a] = my_pid[r];
       }
@@ -95,13 +178,21 @@ __global__ void __launch_bounds__(256) k_rd_move(RdArgs A) {
       cslot[rank] = my_slot[r];
     }
     // the donor's d particles of smallest id, by repeated minimum search
+    // (over a copy in shared memory when the donor's list fits)
+    const bool staged = ni <= kRdStage;
+    if (staged)
+      for (int32_t a = lane; a < ni; a += 32) {
+        const int32_t sl = dlist[a];
+        dsl[a] = sl;
+        dpid[a] = A.pid[sl];
+      }
+    __syncwarp();
     int32_t last = -1;
     for (int32_t q = 0; q < d; ++q) {
       int32_t best = 0x7fffffff, bslot = -1;
       for (int32_t a = lane; a < ni; a += 32) {
-        const int32_t at = A.seg[i] + a;
-        const int32_t sl = A.order ? A.order[at] : at;
-        const int32_t pp = A.pid[sl];
+        const int32_t sl = staged ? dsl[a] : dlist[a];
+        const int32_t pp = staged ? dpid[a] : A.pid[sl];
         if (pp > last && pp < best) { best = pp; bslot = sl; }
       }
 #pragma unroll
@@ -152,7 +243,7 @@ __global__ void __launch_bounds__(256) k_rd_move(RdArgs A) {
 
 void redist_free(RedistWork& W) {
   cudaFree(W.cnt); cudaFree(W.k0); cudaFree(W.v0); cudaFree(W.k1); cudaFree(W.v1);
-  cudaFree(W.hist); cudaFree(W.hist_part); cudaFree(W.dev);
+  cudaFree(W.hist); cudaFree(W.hist_part); cudaFree(W.dev); cudaFree(W.role); cudaFree(W.cur); cudaFree(W.off);
   if (W.host) cudaFreeHost(W.host);
   W = RedistWork();
 }
@@ -172,6 +263,9 @@ static pdf_status redist_alloc(pdf_particles* P) {
   A(&W.hist, hist_len);
   A(&W.hist_part, radix_scan_blocks(hist_len) + 1);
   A(&W.dev, 4);
+  A(&W.role, nt);
+  A(&W.cur, 2 * nt);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&W.off, sizeof(int64_t) * (nt + 1));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&W.host, sizeof(int32_t) * 4);
   if (e != cudaSuccess) {
     redist_free(W);
@@ -191,18 +285,26 @@ extern "C" pdf_status pdf_redistribute(pdf_particles* p, const pdf_mesh* m, int3
   cudaStream_t st = (cudaStream_t)stream;
   pdf_status s = redist_alloc(p);
   if (s != PDF_OK) return s;
-  s = group_by_element(p, st);
-  if (s != PDF_OK) return s;
   const MeshDev& M = m->d;
   RedistWork& W = p->rd;
-  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((M.n_tri + 255) / 256, 4096));
-  PDF_KERNEL("k_rd_counts", st, k_rd_counts<<<nb, 256, 0, st>>>(M.n_tri, p->seg, W.cnt));
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((p->n + 255) / 256, 8192));
+  PDF_CUDA(cudaMemsetAsync(W.cnt, 0, sizeof(int32_t) * M.n_tri, st));
+  PDF_CUDA(cudaMemsetAsync(W.role, 0, sizeof(int32_t) * M.n_tri, st));
+  PDF_CUDA(cudaMemsetAsync(W.cur, 0, sizeof(int32_t) * 2 * M.n_tri, st));
+  PDF_KERNEL("k_rd_hist", st, k_rd_hist<<<nb, 256, 0, st>>>(p->n, p->elem, W.cnt));
   int bits = 1;
   while ((1LL << bits) <= p->n) ++bits;
   const int32_t *sk = nullptr, *sv = nullptr;
   s = radix_sort_index(W.cnt, M.n_tri, bits, W.k0, W.v0, W.k1, W.v1, W.hist, W.hist_part, &sk, &sv, st);
   if (s != PDF_OK) return s;
   PDF_KERNEL("k_rd_nce", st, k_rd_nce<<<1, 32, 0, st>>>(M.n_tri, sk, min_npel, W.dev));
+  const int eb = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)M.n_tri + 255) / 256, 4096));
+  PDF_KERNEL("k_rd_roles", st, k_rd_roles<<<eb, 256, 0, st>>>(M.n_tri, sv, W.dev, W.role));
+  PDF_KERNEL("k_rd_offsets", st, k_rd_offsets<<<1, 1024, 0, st>>>(M.n_tri, sk, W.dev, W.off));
+  // the lists go to a grouping buffer, free between a step and the statistics
+  int32_t* list = p->vals[0];
+  PDF_KERNEL("k_rd_collect", st, k_rd_collect<<<nb, 256, 0, st>>>(p->n, M.n_tri, p->elem, W.role, sk, W.off, W.cur,
+                                                                   list));
   RdArgs A;
   A.n_tri = M.n_tri;
   A.min_npel = min_npel;
@@ -210,8 +312,8 @@ extern "C" pdf_status pdf_redistribute(pdf_particles* p, const pdf_mesh* m, int3
   A.seed = seed;
   A.sk = sk;
   A.sv = sv;
-  A.seg = p->seg;
-  A.order = p->sorted_pid;
+  A.list = list;
+  A.off = W.off;
   A.pid = p->pid;
   A.tri = M.tri;
   A.xy = M.xy;
@@ -226,8 +328,8 @@ extern "C" pdf_status pdf_redistribute(pdf_particles* p, const pdf_mesh* m, int3
     A.st4[f] = s4[f];
   }
   A.dev = W.dev;
-  const int mb = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)M.n_tri / 2 + 7) / 8, 4096));
-  PDF_KERNEL("k_rd_move", st, k_rd_move<<<mb, 256, 0, st>>>(A));
+  const int mb = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)M.n_tri / 2 + kRdWarps - 1) / kRdWarps, 8192));
+  PDF_KERNEL("k_rd_move", st, k_rd_move<<<mb, kRdWarps * 32, 0, st>>>(A));
   PDF_CUDA(cudaMemcpyAsync(W.host, W.dev, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, st));
   PDF_CUDA(cudaStreamSynchronize(st));
   if (moved) *moved = W.host[1];

@@ -304,6 +304,8 @@ __device__ int32_t walk(const StepArgs& A, int32_t e, double& x, double& y, doub
       break;
     }
     if (steps >= 64) {
+      // a non-finite position is lost without the search over all elements
+      if (!isfinite(x) || !isfinite(y)) { c_walk += steps; return -1; }
       ++c_brute;
       int32_t hit = -1;
       for (int32_t f = 0; f < A.n_tri; ++f) {
