@@ -505,10 +505,24 @@ def run_obstacles(pg, torch, stream, steps=10, name="obstacles_20x5_mean128"):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
-    info = pg.pdf_step(gp, gm, p, step=3 + steps, info=True)
+    # the same with the particle redistribution of App. D after every step
+    # (at least min_npel particles per element, the cylinder case's 5)
+    min_npel = 5
+    moved = 0
+    e0.record(stream)
+    for s in range(steps):
+        pg.pdf_step(gp, gm, p, step=3 + steps + s, stream=stream)
+        moved += pg.pdf_redistribute(gp, gm, min_npel, cfg["seed"], 3 + steps + s, stream=stream)
+        pg.pdf_estimate_stats(gp, gm, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_rd = e0.elapsed_time(e1) / steps
+    info = pg.pdf_step(gp, gm, p, step=3 + 2 * steps, info=True)
     n = gp.n
     out = {"workload": name, "n_particles": n, "n_tri": gm.n_tri, "value": n / (ms * 1e-3), "unit": UNIT,
            "ms_per_step": ms, "steps": steps, "setup_seconds": setup_s, "precision": "fp32_state",
+           "with_redistribution": {"value": n / (ms_rd * 1e-3), "unit": UNIT, "ms_per_step": ms_rd,
+                                   "min_npel": min_npel, "moved_per_step": moved / steps},
            "last_step_counters": info}
     del gp, gm
     return out
