@@ -128,15 +128,39 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _setup_dist(n_gpus):
+def _setup_dist(n_gpus, backend="nccl"):
+    """Rank, world size, local rank and torch.distributed (None for one
+    process) from the launcher's environment."""
     rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     dist = None
     if world > 1:
         import torch.distributed as dist_mod
-        dist_mod.init_process_group("nccl")
+        dist_mod.init_process_group(backend)
         dist = dist_mod
     return rank, world, local, dist
+
+
+def max_over_ranks(dist, value, device):
+    """The largest of the ranks' values, on every rank (the timing rule:
+    the slowest replica sets the time)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(seed, rank):
+    """Independent replicas: rank r runs the workload with seed + r."""
+    return seed + rank
+
+
+def replica_value(world, n, steps, t_max_ms):
+    """Whole-job throughput of `world` replicas of n particles each, `steps`
+    steps in the slowest replica's t_max_ms."""
+    return world * n * steps / (t_max_ms * 1e-3)
 
 
 def cpu_baseline_measure(steps=1, warmup=0, ppe=None):
@@ -204,7 +228,7 @@ def run_gpu(args):
     m = inputs.channel_mesh(cfg["nx"], cfg["ny"], jitter=cfg["jitter"], seed=cfg["seed"])
     psi = inputs.scalar_slab(m, cfg["psi_slab_x"])
     gm = pg.Mesh(m)
-    seed = cfg["seed"] + rank  # independent replicas
+    seed = replica_seed(cfg["seed"], rank)
     gp = pg.Particles(gm, seed, ppe=cfg["ppe"], u_sigma=cfg["u_sigma"], elem_psi0=psi)
     n = gp.n
     p = pg.model_params(dt=cfg["dt"], nu=cfg["nu"], Pi=cfg["Pi"], closure=cfg["closure"])
@@ -268,12 +292,8 @@ def run_gpu(args):
         shares[kname] = {"launches": c, "ms_per_launch": t / c if c else None,
                          "share": t / ms_prof if ms_prof else None}
     pg.pdf_profile_reset()
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * n * args.steps / (t_max * 1e-3)
+    t_max = max_over_ranks(dist, ms, dev)
+    value = replica_value(world, n, args.steps, t_max)
 
     # ---- end-to-end through the public API with host-resident state
     keys = ("x", "y", "u", "v", "w", "om", "ps")
@@ -302,13 +322,9 @@ def run_gpu(args):
         step_no += 1
     barrier()
     e2e_s = time.perf_counter() - t0
-    e2e_max = e2e_s
-    if dist is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_max = float(t.item())
+    e2e_max = max_over_ranks(dist, e2e_s, dev)
     state_bytes = n * (7 * 8 + 4)
-    e2e = {"value": world * n * e2e_steps / e2e_max, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+    e2e = {"value": replica_value(world, n, e2e_steps, 1e3 * e2e_max), "unit": UNIT, "h2d_bytes_per_step": state_bytes,
            "d2h_bytes_per_step": state_bytes + gm.n_nodes * 12 * 8, "steps": e2e_steps,
            "what": "state in page-locked host memory: copied in, stepped, statistics and state copied out every step"}
 
