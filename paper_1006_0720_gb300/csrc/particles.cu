@@ -144,6 +144,73 @@ __global__ void k_f64_to_f32(const double* __restrict__ a, float* __restrict__ b
     b[i] = __double2float_rn(a[i]);
 }
 
+// Whole-state transfers in one pass, for caller buffers the kernels can
+// address (device memory, or page-locked host memory through its mapping:
+// the copy then runs as the kernel's own loads and stores over the
+// host link, with no staging).  Out: destination q (particle id) reads slot
+// inv[q], so that the stores to host memory are consecutive.
+struct StateOut {
+  int64_t n;
+  const int32_t* inv;
+  const int64_t *x, *y;
+  const fx::df* d[5];
+  const float* f[5];
+  const int32_t* elem;
+  double* o[7];  // x, y, u, v, w, om, ps (nullable)
+  int32_t* oe;   // elem (nullable)
+};
+
+__global__ void k_inv_pid(const int32_t* __restrict__ pid, int32_t* __restrict__ inv, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    inv[pid[i]] = (int32_t)i;
+}
+
+__global__ void k_state_out(StateOut S) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < S.n; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = S.inv[q];
+    if (S.o[0]) S.o[0][q] = __longlong_as_double((long long)fx::fix2d(S.x[i], kPosF));
+    if (S.o[1]) S.o[1][q] = __longlong_as_double((long long)fx::fix2d(S.y[i], kPosF));
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      if (S.o[2 + k]) S.o[2 + k][q] = S.d[k] ? fx::to_double(S.d[k][i]) : (double)S.f[k][i];
+    if (S.oe) S.oe[q] = S.elem[i];
+  }
+}
+
+// In: slot i takes particle i; positions outside |x| < 64 are counted in
+// *bad and stored as 0.
+struct StateIn {
+  int64_t n;
+  const double* in[7];  // x, y, u, v, w, om, ps
+  const int32_t* ie;
+  int64_t *x, *y;
+  fx::df* d[5];
+  float* f[5];
+  int32_t *elem, *pid;
+  unsigned long long* bad;
+};
+
+__global__ void k_state_in(StateIn S) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const uint64_t bits = (uint64_t)__double_as_longlong(S.in[k][i]);
+      int64_t v = 0;
+      if (fx::d_exp(bits) <= 1023 + 5) v = fx::d2fix(bits, kPosF);
+      else atomicAdd(S.bad, 1ull);
+      (k == 0 ? S.x : S.y)[i] = v;
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const double v = S.in[2 + k][i];
+      if (S.d[k]) S.d[k][i] = fx::from_double(v);
+      else S.f[k][i] = __double2float_rn(v);
+    }
+    S.elem[i] = S.ie[i];
+    S.pid[i] = (int32_t)i;
+  }
+}
+
 static void free_particles(pdf_particles* p) {
   if (!p) return;
   cudaFree(p->uf); cudaFree(p->vf); cudaFree(p->wf); cudaFree(p->omf); cudaFree(p->psf); cudaFree(p->rows_f32);
@@ -293,6 +360,20 @@ static bool is_device_ptr(const void* ptr) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// The address a kernel uses for a caller's buffer: device or managed memory
+// as it is, page-locked host memory through its mapping; nullptr for
+// pageable host memory (which goes through the staging buffer).
+static void* kernel_view(const void* ptr) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return const_cast<void*>(ptr);
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) return at.devicePointer;
+  return nullptr;
+}
+
 static pdf_status ensure_stage(const pdf_particles* p) {
   pdf_particles* q = const_cast<pdf_particles*>(p);
   if (!q->stage) PDF_CUDA(cudaMalloc((void**)&q->stage, sizeof(double) * (size_t)p->n));
@@ -306,6 +387,37 @@ extern "C" pdf_status pdf_particles_get_state(const pdf_particles* p, double* x,
   cudaStream_t st = (cudaStream_t)stream;
   const size_t b = sizeof(double) * p->n;
   double* dst[] = {x, y, u, v, w, om, ps};
+  {
+    // one pass when every destination is addressable by the kernels
+    StateOut S;
+    bool all = true;
+    for (int i = 0; i < 7; ++i) {
+      S.o[i] = dst[i] ? static_cast<double*>(kernel_view(dst[i])) : nullptr;
+      if (dst[i] && !S.o[i]) all = false;
+    }
+    S.oe = elem ? static_cast<int32_t*>(kernel_view(elem)) : nullptr;
+    if (elem && !S.oe) all = false;
+    if (all && p->n > 0) {
+      pdf_status s = ensure_stage(p);
+      if (s != PDF_OK) return s;
+      int32_t* inv = reinterpret_cast<int32_t*>(p->stage);
+      const int g = grid_for(p->n, 256);
+      PDF_KERNEL("k_inv_pid", st, k_inv_pid<<<g, 256, 0, st>>>(p->pid, inv, p->n));
+      S.n = p->n;
+      S.inv = inv;
+      S.x = p->x;
+      S.y = p->y;
+      const fx::df* dd[5] = {p->u, p->v, p->w, p->om, p->ps};
+      const float* ff[5] = {p->uf, p->vf, p->wf, p->omf, p->psf};
+      for (int k = 0; k < 5; ++k) {
+        S.d[k] = p->precision == PDF_FP64 ? dd[k] : nullptr;
+        S.f[k] = ff[k];
+      }
+      S.elem = p->elem;
+      PDF_KERNEL("k_state_out", st, k_state_out<<<g, 256, 0, st>>>(S));
+      return PDF_OK;
+    }
+  }
   const fx::df* srcd[] = {nullptr, nullptr, p->u, p->v, p->w, p->om, p->ps};
   const float* srcf[] = {nullptr, nullptr, p->uf, p->vf, p->wf, p->omf, p->psf};
   const int g = grid_for(p->n, 256);
@@ -356,7 +468,28 @@ extern "C" pdf_status pdf_particles_set_state(pdf_particles* p, const double* x,
   const int g = grid_for(p->n, 256);
   unsigned long long* bad = reinterpret_cast<unsigned long long*>(p->counters + 15);
   PDF_CUDA(cudaMemsetAsync(bad, 0, sizeof(long long), st));
+  StateIn S;
+  bool all = true;
   for (int i = 0; i < 7; ++i) {
+    S.in[i] = static_cast<const double*>(kernel_view(src[i]));
+    if (!S.in[i]) all = false;
+  }
+  S.ie = static_cast<const int32_t*>(kernel_view(elem));
+  if (!S.ie) all = false;
+  if (all) {  // one pass reading every source where it is
+    S.n = p->n;
+    S.x = p->x;
+    S.y = p->y;
+    for (int k = 0; k < 5; ++k) {
+      S.d[k] = dstd[2 + k];
+      S.f[k] = dstf[2 + k];
+    }
+    S.elem = p->elem;
+    S.pid = p->pid;
+    S.bad = bad;
+    if (p->n > 0) PDF_KERNEL("k_state_in", st, k_state_in<<<g, 256, 0, st>>>(S));
+  }
+  for (int i = 0; i < 7 && !all; ++i) {
     const bool dev = is_device_ptr(src[i]);
     if (!dev) {
       pdf_status s = ensure_stage(p);
@@ -373,8 +506,10 @@ extern "C" pdf_status pdf_particles_set_state(pdf_particles* p, const double* x,
       PDF_KERNEL("k_f64_to_f32", st, k_f64_to_f32<<<g, 256, 0, st>>>(from, dstf[i], p->n));
     }
   }
-  PDF_CUDA(cudaMemcpyAsync(p->elem, elem, sizeof(int32_t) * p->n, cudaMemcpyDefault, st));
-  PDF_KERNEL("k_iota", st, k_iota<<<g, 256, 0, st>>>(p->pid, p->n));
+  if (!all) {
+    PDF_CUDA(cudaMemcpyAsync(p->elem, elem, sizeof(int32_t) * p->n, cudaMemcpyDefault, st));
+    PDF_KERNEL("k_iota", st, k_iota<<<g, 256, 0, st>>>(p->pid, p->n));
+  }
   p->since_reorder = 0;
   p->have_cond = false;
   long long nbad = 0;

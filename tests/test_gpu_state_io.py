@@ -1,0 +1,81 @@
+"""State transfers through the C-ABI with every kind of caller buffer:
+device memory, page-locked host memory (read and written by the kernels
+through its mapping) and pageable host memory (through the staging
+buffer) give the same values, before and after a reordering of the state
+(slots then differ from particle ids), in both state forms."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1006_0720_gb300 as pg  # noqa: E402
+from paper_1006_0720_gb300 import capi  # noqa: E402
+
+KEYS = ("x", "y", "u", "v", "w", "om", "ps")
+
+
+def _bufs(kind, n):
+    if kind == "device":
+        b = {k: torch.empty(n, dtype=torch.float64, device="cuda") for k in KEYS}
+        b["elem"] = torch.empty(n, dtype=torch.int32, device="cuda")
+    elif kind == "pinned":
+        b = {k: torch.empty(n, dtype=torch.float64, pin_memory=True) for k in KEYS}
+        b["elem"] = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    else:
+        b = {k: torch.from_numpy(np.empty(n)) for k in KEYS}
+        b["elem"] = torch.from_numpy(np.empty(n, dtype=np.int32))
+    return b
+
+
+def _ptrs(b):
+    return [ctypes.c_void_p(b[k].data_ptr()) for k in KEYS + ("elem",)]
+
+
+def _get(gp, kind):
+    b = _bufs(kind, gp.n)
+    capi.check(pg.lib().pdf_particles_get_state(gp.handle, *_ptrs(b), None), "get_state")
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy().copy() for k, v in b.items()}
+
+
+@pytest.mark.parametrize("precision", [capi.PDF_FP64, capi.PDF_FP32_STATE])
+def test_state_round_trips_with_every_buffer_kind(precision):
+    m = inputs.channel_mesh(20, 40, seed=1)
+    gm = pg.Mesh(m)
+    gp = pg.Particles(gm, 3, ppe=30, u_sigma=0.2, elem_psi0=inputs.scalar_slab(m), precision=precision)
+    gp.set_reorder(1)
+    p = pg.model_params(closure="slm")
+    pg.pdf_estimate_stats(gp, gm)
+    for s in range(4):                      # moves particles; the reordering permutes the slots
+        pg.pdf_step(gp, gm, p, step=s)
+        pg.pdf_estimate_stats(gp, gm)
+    ref = _get(gp, "device")
+    for kind in ("pinned", "pageable"):
+        got = _get(gp, kind)
+        for k in KEYS + ("elem",):
+            assert np.array_equal(got[k], ref[k]), (kind, k)
+    # set from each kind, read back on the device: the same state
+    for kind in ("pinned", "pageable", "device"):
+        b = _bufs(kind, gp.n)
+        for k in KEYS + ("elem",):
+            b[k].copy_(torch.from_numpy(ref[k]))
+        capi.check(pg.lib().pdf_particles_set_state(gp.handle, *_ptrs(b), None), "set_state")
+        back = _get(gp, "device")
+        for k in KEYS + ("elem",):
+            assert np.array_equal(back[k], ref[k]), (kind, k)
+    # positions out of range are refused from every kind
+    for kind in ("pinned", "pageable"):
+        b = _bufs(kind, gp.n)
+        for k in KEYS + ("elem",):
+            b[k].copy_(torch.from_numpy(ref[k]))
+        b["x"][5] = 100.0
+        with pytest.raises(capi.PdfError):
+            capi.check(pg.lib().pdf_particles_set_state(gp.handle, *_ptrs(b), None), "set_state")
