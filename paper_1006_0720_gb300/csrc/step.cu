@@ -844,6 +844,13 @@ __device__ __forceinline__ bool small_move(const fx::acc& a) { return fabsf(a.h)
 // FP64 back to the stored forms after the FP64 walk (the wall fall-back).
 __device__ __forceinline__ bool pos_fits(double x) { return fabs(x) < 64.0; }
 
+__device__ __forceinline__ void prefetch_l1(const void* a) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+}
+__device__ __forceinline__ void prefetch_l2(const void* a) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
 __global__ void __launch_bounds__(256, 4) k_step_fx(StepArgs A, FxArgs F) {
   int c_walk = 0, c_per = 0, c_om = 0, c_near = 0;
   Counts cs;  // counts of the FP64 fall-backs
@@ -852,9 +859,27 @@ __global__ void __launch_bounds__(256, 4) k_step_fx(StepArgs A, FxArgs F) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   for (int64_t it = 0; it < iters; ++it, p += stride) {
     if (p >= A.n) continue;
-    const Draws D = draw_step(A, p);
     int32_t e = A.elem[p];
     const FxRow* R = F.rows + e;
+    // the element's row and geometry start on their way to L1 while the
+    // random numbers are drawn
+    prefetch_l1(R);
+    prefetch_l1(reinterpret_cast<const char*>(R) + 128);
+    prefetch_l1(F.geo + e);
+    // the next iteration's state starts on its way from DRAM to L2
+    if (p + stride < A.n) {
+      const int64_t q = p + stride;
+      prefetch_l2(A.x + q);
+      prefetch_l2(A.y + q);
+      prefetch_l2(A.u + q);
+      prefetch_l2(A.v + q);
+      prefetch_l2(A.w + q);
+      prefetch_l2(A.om + q);
+      prefetch_l2(A.ps + q);
+      prefetch_l2(A.elem + q);
+      prefetch_l2(A.pid + q);
+    }
+    const Draws D = draw_step(A, p);
     const fx::df U[3] = {ld_state(A.u, p), ld_state(A.v, p), ld_state(A.w, p)};
     // position (eq. Lagrangian-position-exact): X + U^n dt + sqrt(2 nu) dW
     fx::acc ax, ay;
@@ -986,9 +1011,23 @@ __global__ void __launch_bounds__(256, 4) k_step_f32(StepArgs A, FxArgs F, F32Ar
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   for (int64_t it = 0; it < iters; ++it, p += stride) {
     if (p >= A.n) continue;
-    const Draws D = draw_step(A, p);
     int32_t e = A.elem[p];
     const float* R = S.rows + (int64_t)e * PDFGB_ROW;
+    prefetch_l1(R);  // the 128-byte FP32 row and the geometry, as in k_step_fx
+    prefetch_l1(F.geo + e);
+    if (p + stride < A.n) {
+      const int64_t q = p + stride;
+      prefetch_l2(A.x + q);
+      prefetch_l2(A.y + q);
+      prefetch_l2(S.u + q);
+      prefetch_l2(S.v + q);
+      prefetch_l2(S.w + q);
+      prefetch_l2(S.om + q);
+      prefetch_l2(S.ps + q);
+      prefetch_l2(A.elem + q);
+      prefetch_l2(A.pid + q);
+    }
+    const Draws D = draw_step(A, p);
     const float U0 = S.u[p], U1 = S.v[p], U2 = S.w[p];
     const float d0 = U0 - __ldg(R + 0), d1 = U1 - __ldg(R + 1), d2 = U2 - __ldg(R + 2);
     const float b = __ldg(R + 21);
