@@ -100,6 +100,20 @@ __global__ void __launch_bounds__(kIecmThreads) k_iecm_cond(const int32_t* __res
       V.ge += beg;
     }
     __syncthreads();  // the previous element is done with the arrays
+    {  // the next element's particles on their way to L2 (after the periodic
+       // reordering they sit close to their grouped positions)
+      const int32_t en = e + gridDim.x;
+      if (en < n_tri) {
+        const int32_t nb = seg[en], ne = seg[en + 1];
+        for (int32_t i = nb + 16 * tid; i < ne; i += 16 * kIecmThreads) {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(u + i));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(v + i));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(w + i));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(ps + i));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(pid + i));
+        }
+      }
+    }
     for (int i = tid; i < N; i += kIecmThreads) {
       const int64_t s = order ? (int64_t)order[beg + i] : (int64_t)(beg + i);
       V.a.slot[i] = (int32_t)s;

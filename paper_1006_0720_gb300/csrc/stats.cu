@@ -336,6 +336,10 @@ struct StatScratch {
 };
 constexpr int kStatWarps = 4;  // warps per block (27 KB of shared memory)
 
+__device__ __forceinline__ void prefetch_l2(const void* a) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kStatWarps * 32, 8) k_elem_stats_fx(const int32_t* __restrict__ seg,
                                                        const int32_t* __restrict__ pid, int32_t n_tri,
@@ -356,6 +360,21 @@ __global__ void __launch_bounds__(kStatWarps * 32, 8) k_elem_stats_fx(const int3
       continue;
     }
     __syncwarp();  // the previous element's readers of the scratch are done
+    {  // the next element's state on its way to L2: after the periodic
+       // reordering its particles sit close to their grouped positions
+      const int64_t en = e + nwarps;
+      if (en < n_tri) {
+        const int32_t nb = seg[en], ne = seg[en + 1];
+        for (int32_t i = nb + 16 * lane; i < ne; i += 16 * 32) {
+          prefetch_l2(u + i);
+          prefetch_l2(v + i);
+          prefetch_l2(w + i);
+          prefetch_l2(om + i);
+          prefetch_l2(ps + i);
+          if (pid) prefetch_l2(pid + i);
+        }
+      }
+    }
     // pass 1: exact sums of the fixed-point values
     unsigned long long lo[5] = {0, 0, 0, 0, 0};
     long long hi[5] = {0, 0, 0, 0, 0};
