@@ -394,6 +394,8 @@ int or_track(const or_mesh* m, int e0, double* px, double* py, double* u, double
       break;
     }
     if (steps >= 64) {
+      /* a non-finite position is lost without the search over all elements */
+      if (!isfinite(x) || !isfinite(y)) { info->status |= OR_TRK_LOST; break; }
       info->status |= OR_TRK_BRUTE;
       int hit = -1;
       for (int f = 0; f < m->n_tri && hit < 0; ++f) {
