@@ -333,8 +333,9 @@ pdf_status pdf_elem_coeff(pdf_particles* p, const pdf_mesh* m, const pdf_model_p
 
 /* The elliptic-relaxation solve for the tensor wp_ij (eq. elliptic-relaxation-
  * Lagrangian, with eqs. H, A_v, bij, L and Cxi), discretised with linear
- * triangles and solved by Jacobi-preconditioned conjugate gradients in FP64
- * (sec. 3.2), all nine components at once:
+ * triangles and solved by preconditioned conjugate gradients in FP64 (sec.
+ * 3.2: there Jacobi-preconditioned; here a smoothed-aggregation multigrid
+ * V-cycle by default, see pdf_relax_set_solver), all nine components at once:
  *   (M + K_L) wp = M rhs,  M the consistent mass matrix, K_L the stiffness
  *   matrix weighted by the element mean of the nodal L^2.
  * Right-hand side and L from the statistics of the last pdf_estimate_stats.
@@ -347,9 +348,20 @@ pdf_status pdf_elem_coeff(pdf_particles* p, const pdf_mesh* m, const pdf_model_p
  *   rtol     stop a component when ||r|| <= rtol ||b|| (b = M rhs)
  *   max_it   iteration cap; PDF_ENOTCONV if a component is not converged
  *   iters, rel_res  host [9] or NULL: iterations and final ||r||/||b||
- * The call synchronizes `stream` once per iteration (convergence test). */
+ * The call synchronizes `stream` once per 8 iterations (convergence test). */
 pdf_status pdf_relax_solve(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params, double* wp,
                            double rtol, int32_t max_it, int32_t* iters, double* rel_res, void* stream);
+/* The preconditioner of pdf_relax_solve: multigrid = 1 (the default) a
+ * smoothed-aggregation V-cycle whose prolongations come from the mesh's
+ * stiffness matrix (built at the first solve) and whose level matrices are
+ * the Galerkin products of the current relaxation matrices (recomputed on
+ * the device at every solve; four operators: wp_11, wp_22, wp_33 and the
+ * off-diagonal components, each with its own fixed unknowns); multigrid = 0
+ * the diagonal (Jacobi) of the paper.  Both converge to the same tolerance;
+ * the solve falls back to Jacobi when the hierarchy cannot be built.
+ * Synchronizes the device when the choice changes.  PDF_EINVAL for other
+ * values. */
+pdf_status pdf_relax_set_solver(pdf_particles* p, int32_t multigrid);
 /* The nodal right-hand side rhs [9][n_nodes] and L^2 [3][n_nodes] (C_xi of
  * wp_11, of wp_22, and 1) that pdf_relax_solve uses (device or page-locked
  * host outputs; either may be NULL). */

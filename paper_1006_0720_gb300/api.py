@@ -299,6 +299,10 @@ def pdf_relax_solve(particles, mesh, params, wp, rtol=1e-10, max_it=1000, stream
     return list(it), list(rr)
 
 
+def pdf_relax_set_solver(particles, multigrid=True):
+    check(lib().pdf_relax_set_solver(particles.handle, 1 if multigrid else 0), "pdf_relax_set_solver")
+
+
 def pdf_relax_rhs(particles, mesh, params, stream=None):
     rhs = torch.empty((9, mesh.n_nodes), dtype=torch.float64, device="cuda")
     L2 = torch.empty((3, mesh.n_nodes), dtype=torch.float64, device="cuda")

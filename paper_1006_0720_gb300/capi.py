@@ -88,6 +88,7 @@ PROTOTYPES = {
     "pdf_elem_coeff": (I32, [V, V, ctypes.POINTER(ModelParams), V, V, V]),
     "pdf_relax_solve": (I32, [V, V, ctypes.POINTER(ModelParams), V, D, I32, ctypes.POINTER(I32), PD, V]),
     "pdf_relax_rhs": (I32, [V, V, ctypes.POINTER(ModelParams), V, V, V]),
+    "pdf_relax_set_solver": (I32, [V, I32]),
     "pdf_mesh_wall_distance": (I32, [V, PD, PD]),
     "pdf_mlp_create": (I32, [U64, PV]),
     "pdf_mlp_destroy": (I32, [V]),

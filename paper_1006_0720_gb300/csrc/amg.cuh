@@ -54,4 +54,80 @@ pdf_status amg_pcg(const Amg& G, int32_t n, const int32_t* rp, const int32_t* ci
                    double* r, double* z, double* p, double* q, double* scal, int32_t* ctl, double* part,
                    int32_t part_cap, cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// The relaxation's multigrid: the prolongations of the smoothed-aggregation
+// hierarchy of the stiffness matrix K (fixed per mesh), applied to the
+// relaxation matrices M + K_{L^2} of the current statistics, whose Galerkin
+// coarse matrices, smoothers and Q = (I - W A) P are recomputed on the
+// device at every solve through precomputed plans.  Four operators
+// ("variants"): the C_xi classes of wp_11, wp_22, wp_33 with their Dirichlet
+// rows (no-slip nodes) and the off-diagonal components (walls and no-slip
+// nodes).  Fixed unknowns carry identity rows and columns.
+constexpr int kRxVar = 4;
+constexpr int kRxMaxLv = 12;
+
+struct RxLevel {
+  int32_t n = 0, nc = 0;
+  int64_t nnz_a = 0, nnz_ap = 0;
+  int32_t *a_rp = nullptr, *a_ci = nullptr, *a_dpos = nullptr;  // A_l and its diagonal positions
+  int32_t *q_rp = nullptr, *q_ci = nullptr;                      // pattern of A_l P_l = pattern of Q_l
+  int32_t *s_rp = nullptr, *s_ci = nullptr, *s_perm = nullptr;   // Q_l^T: S[t] = Q[s_perm[t]]
+  int32_t *ap_off = nullptr, *ap_qa = nullptr;                   // (A P)[t] = sum a[ap_qa] * ap_pv
+  double* ap_pv = nullptr;
+  int32_t *c_off = nullptr, *c_tap = nullptr;                    // A_{l+1}[c] = sum c_pv * (A P)[c_tap]
+  double* c_pv = nullptr;
+  double* q_pin = nullptr;                                       // P at each (A P) position, else 0
+  int32_t* q_row = nullptr;
+  double *a_v[kRxVar] = {}, *ap_v[kRxVar] = {}, *q_v[kRxVar] = {}, *s_v[kRxVar] = {};
+  // FP32 copies for the cycle: A, Q, S and the smoother weights W = omega / a_ii
+  float *a_f[kRxVar] = {}, *q_f[kRxVar] = {}, *s_f[kRxVar] = {}, *w_f[kRxVar] = {};
+  float *b = nullptr, *x = nullptr, *z = nullptr;                // [9][n] (b, z for l > 0)
+};
+
+struct RelaxAmg {
+  std::vector<RxLevel> lv;
+  int32_t nc = 0;
+  int64_t nnz_c = 0;
+  int32_t *c_rp = nullptr, *c_ci = nullptr;  // the coarsest matrix
+  double* c_v[kRxVar] = {};
+  double* cmat = nullptr;                    // [kRxVar][nc][2 nc] Gauss-Jordan work
+  float* cinv = nullptr;                     // [kRxVar][nc][nc]
+  float *cb = nullptr, *cz = nullptr;        // [9][nc]
+  double *omega = nullptr, *gpart = nullptr; // [kRxVar][kRxMaxLv], Gershgorin partial maxima
+  int32_t gblocks = 0;
+  double* upart = nullptr;                   // [9][blocks of the finest up-sweep], r . z partials
+};
+
+// The end of a preconditioner application: z = 0 on the fixed unknowns
+// (wall[i] == 2 for every component; wall[i] == 1 also for the off-diagonal
+// components c != 0, 4, 8) and r . z per component, whose last block sets
+// beta[c] = (first ? 0 : r.z / rz[c]), rz[c] = r.z and returns counter[c]
+// to 0.
+struct RxDot {
+  const uint8_t* wall = nullptr;
+  double* rz = nullptr;       // [9]
+  double* beta = nullptr;     // [9]
+  int32_t* counter = nullptr; // [9]
+  int first = 0;
+};
+
+// Plans from the hierarchy of K (n unknowns, CSR rp / ci / kv), coarsest
+// level at most 64 unknowns.
+pdf_status relax_amg_setup(int32_t n, const std::vector<int32_t>& rp, const std::vector<int32_t>& ci,
+                           const std::vector<double>& kv, RelaxAmg& G);
+void relax_amg_free(RelaxAmg& G);
+// The finest matrix values of variant v, on the relaxation pattern: filled
+// by the caller before relax_amg_update.
+inline double* relax_amg_level0(RelaxAmg& G, int v) { return G.lv.empty() ? G.c_v[v] : G.lv[0].a_v[v]; }
+// The Galerkin matrices, smoother weights, Q and S of every level and the
+// inverses of the coarsest matrices of the four variants, from the finest
+// values (fixed unknowns with their diagonal only).
+pdf_status relax_amg_update(RelaxAmg& G, cudaStream_t st);
+// z = M^-1 r for the nine components ([9][n] each; component c uses
+// variant 0, 1, 2 for c = 0, 4, 8 and 3 otherwise); components with
+// active[c] = 0 and everything after *done are skipped.  The cycle runs in
+// FP32 (the level matrices and vectors), r and z are FP64.
+pdf_status relax_amg_apply(const RelaxAmg& G, const double* r, double* z, const int32_t* active,
+                           const int32_t* done, const RxDot& dot, cudaStream_t st);
+
 }  // namespace pdfgb

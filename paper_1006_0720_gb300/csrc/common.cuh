@@ -113,8 +113,13 @@ struct RelaxMesh {
   int32_t* pw_e = nullptr;      // [pw_off[n_rep]][3]
   double* pw_n = nullptr;       // [pw_off[n_rep]][3]
 };
+struct RelaxAmg;
 struct RelaxWork {
   int32_t nb = 0;
+  // multigrid preconditioner (default) or Jacobi; the hierarchy is built at
+  // the first multigrid solve
+  bool multigrid = true;
+  RelaxAmg* amg = nullptr;
   double *f = nullptr, *L2 = nullptr, *aval = nullptr, *diag = nullptr, *g = nullptr;
   double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
   double *part = nullptr, *scal = nullptr, *host = nullptr;

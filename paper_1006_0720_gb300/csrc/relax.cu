@@ -17,6 +17,7 @@
 #include <cstring>
 #include <vector>
 
+#include "amg.cuh"
 #include "common.cuh"
 
 namespace pdfgb {
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(kRBlock) k_cg_init(
     const uint8_t* __restrict__ wall, const int32_t* __restrict__ rep_node, int32_t n_nodes,
     const double* __restrict__ f, const double* __restrict__ gdir, const double* __restrict__ wp,
     double* __restrict__ x, double* __restrict__ r, double* __restrict__ z, double* __restrict__ p,
-    double* __restrict__ part) {
+    double* __restrict__ q, double* __restrict__ part) {
   const int ij = blockIdx.y;
   const int32_t row = blockIdx.x * kRBlock + threadIdx.x;
   double rz = 0.0, rr = 0.0, bb = 0.0;
@@ -177,6 +178,7 @@ __global__ void __launch_bounds__(kRBlock) k_cg_init(
     r[o] = res;
     z[o] = fixed_row ? 0.0 : zz;
     p[o] = z[o];
+    q[o] = 0.0;  // the multigrid path's q = A z + beta q starts from 0
     rz = res * z[o];
     rr = res * res;
     bb = b * b;
@@ -341,6 +343,92 @@ __global__ void k_cg_close(int32_t* __restrict__ ctl) {
   if (n_active == 0 || it >= ctl[kRMaxIt]) ctl[kRDone] = 1;
 }
 
+// Multigrid path.  The finest matrices of the four preconditioner variants
+// (components 0, 4, 8 and the off-diagonal ones): the class values with the
+// fixed unknowns' rows and columns reduced to their diagonal.
+__global__ void k_rx_fill(int32_t n_rep, int64_t nnz, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const double* __restrict__ aval, const uint8_t* __restrict__ wall, double* __restrict__ a0,
+                          double* __restrict__ a1, double* __restrict__ a2, double* __restrict__ a3) {
+  for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n_rep; r += gridDim.x * blockDim.x) {
+    const uint8_t wr = wall[r];
+    for (int32_t q = rp[r]; q < rp[r + 1]; ++q) {
+      const int32_t c = ci[q];
+      const uint8_t wc = wall[c];
+      const bool diag = c == r;
+      // variants 0-2: every component fixed on no-slip nodes; variant 3:
+      // also on free-slip wall nodes
+      const bool f012 = wr == 2 || wc == 2, f3 = wr != 0 || wc != 0;
+      a0[q] = f012 && !diag ? 0.0 : aval[q];
+      a1[q] = f012 && !diag ? 0.0 : aval[nnz + q];
+      a2[q] = f012 && !diag ? 0.0 : aval[2 * nnz + q];
+      a3[q] = f3 && !diag ? 0.0 : aval[2 * nnz + q];
+    }
+  }
+}
+
+// Multigrid path: p = z + beta p, q = A z + beta q (= A p) and p.q (last
+// block of a component: alpha = r.z / p.q).
+__global__ void __launch_bounds__(kRBlock) k_cg_spmv_rec(int32_t n_rep, int64_t nnz, const int32_t* __restrict__ rp,
+                                                          const int32_t* __restrict__ ci,
+                                                          const double* __restrict__ aval,
+                                                          const uint8_t* __restrict__ wall,
+                                                          const double* __restrict__ z, double* __restrict__ p,
+                                                          double* __restrict__ q, double* __restrict__ part,
+                                                          double* __restrict__ scal, int32_t* __restrict__ ctl) {
+  const int ij = blockIdx.y;
+  if (ctl[kRDone] || !ctl[kRActive + ij]) return;
+  const int32_t row = blockIdx.x * kRBlock + threadIdx.x;
+  double pq = 0.0;
+  if (row < n_rep) {
+    const double beta = scal[kRBeta + ij];
+    const int64_t o = (int64_t)ij * n_rep + row;
+    const double qn = spmv_row(row, ij, n_rep, nnz, rp, ci, aval, wall, z) + beta * q[o];
+    const double pn = z[o] + beta * p[o];
+    q[o] = qn;
+    p[o] = pn;
+    pq = qn * pn;
+  }
+  double* pp = part + (int64_t)ij * gridDim.x;
+  const double s = block_sum(pq);
+  if (threadIdx.x == 0) pp[blockIdx.x] = s;
+  if (!last_block_of(ctl + kRCntSpmv + ij)) return;
+  const double t = sum_of(pp, gridDim.x);
+  if (threadIdx.x == 0) {
+    scal[kRPq + ij] = t;
+    scal[kRAlpha + ij] = t != 0.0 ? scal[kRRz + ij] / t : 0.0;
+  }
+}
+
+// x += alpha p; r -= alpha q; r.r (last block of a component: count the
+// iteration, retire the component at r.r <= rtol^2 b.b).
+__global__ void __launch_bounds__(kRBlock) k_cg_update_mg(int32_t n_rep, double* __restrict__ scal,
+                                                           double* __restrict__ x, double* __restrict__ r,
+                                                           const double* __restrict__ p, const double* __restrict__ q,
+                                                           double* __restrict__ part, int32_t* __restrict__ ctl) {
+  const int ij = blockIdx.y;
+  if (ctl[kRDone] || !ctl[kRActive + ij]) return;
+  const int32_t row = blockIdx.x * kRBlock + threadIdx.x;
+  double rr = 0.0;
+  if (row < n_rep) {
+    const double alpha = scal[kRAlpha + ij];
+    const int64_t o = (int64_t)ij * n_rep + row;
+    x[o] += alpha * p[o];
+    const double res = r[o] - alpha * q[o];
+    r[o] = res;
+    rr = res * res;
+  }
+  double* p2 = part + (int64_t)(18 + ij) * gridDim.x;
+  const double s2 = block_sum(rr);
+  if (threadIdx.x == 0) p2[blockIdx.x] = s2;
+  if (!last_block_of(ctl + kRCntUpd + ij)) return;
+  const double rrn = sum_of(p2, gridDim.x);
+  if (threadIdx.x == 0) {
+    scal[kRRr + ij] = rrn;
+    ctl[kRIters + ij] += 1;
+    if (rrn <= scal[kRTol2 + ij]) ctl[kRActive + ij] = 0;
+  }
+}
+
 __global__ void k_cg_diag(int32_t n_rep, int64_t nnz, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                           const double* __restrict__ aval, double* __restrict__ diag) {
   const int cl = blockIdx.y;
@@ -367,8 +455,32 @@ __global__ void k_cg_scatter(int32_t n_nodes, const int32_t* __restrict__ node_r
 // ----------------------------------------------------------------------------
 namespace pdfgb {
 
+// The multigrid hierarchy of the relaxation pattern's stiffness matrix,
+// built once; on failure the solve falls back to Jacobi for good.
+static pdf_status relax_amg_build(pdf_particles* P) {
+  RelaxWork& W = P->rx;
+  if (W.amg || !W.multigrid) return PDF_OK;
+  const RelaxMesh& R = P->mesh->rx;
+  std::vector<int32_t> rp(R.n_rep + 1), ci(R.nnz), off(R.nnz + 1);
+  PDF_CUDA(cudaMemcpy(rp.data(), R.rp, sizeof(int32_t) * rp.size(), cudaMemcpyDeviceToHost));
+  PDF_CUDA(cudaMemcpy(ci.data(), R.ci, sizeof(int32_t) * ci.size(), cudaMemcpyDeviceToHost));
+  PDF_CUDA(cudaMemcpy(off.data(), R.ctb_off, sizeof(int32_t) * off.size(), cudaMemcpyDeviceToHost));
+  std::vector<double> kc(off[R.nnz]), kv(R.nnz, 0.0);
+  if (!kc.empty()) PDF_CUDA(cudaMemcpy(kc.data(), R.ctb_k, sizeof(double) * kc.size(), cudaMemcpyDeviceToHost));
+  for (int64_t q = 0; q < R.nnz; ++q)
+    for (int32_t t = off[q]; t < off[q + 1]; ++t) kv[q] += kc[t];
+  RelaxAmg* G = new RelaxAmg();
+  if (relax_amg_setup(R.n_rep, rp, ci, kv, *G) != PDF_OK) {
+    delete G;
+    W.multigrid = false;
+    return PDF_OK;
+  }
+  W.amg = G;
+  return PDF_OK;
+}
+
 static pdf_status relax_alloc(pdf_particles* P) {
-  if (P->rx.x) return PDF_OK;
+  if (P->rx.x) return relax_amg_build(P);
   const RelaxMesh& R = P->mesh->rx;
   const int32_t nn = P->mesh->d.n_nodes;
   const int32_t nb = (R.n_rep + kRBlock - 1) / kRBlock;
@@ -399,7 +511,7 @@ static pdf_status relax_alloc(pdf_particles* P) {
     relax_free(W);
     return cuda_fail(e, "pdf_relax_solve: allocation");
   }
-  return PDF_OK;
+  return relax_amg_build(P);
 }
 
 void relax_free(RelaxWork& W) {
@@ -411,15 +523,45 @@ void relax_free(RelaxWork& W) {
   if (W.ev0) cudaEventDestroy(W.ev0);
   if (W.ev1) cudaEventDestroy(W.ev1);
   if (W.cs) cudaStreamDestroy(W.cs);
+  if (W.amg) {
+    relax_amg_free(*W.amg);
+    delete W.amg;
+  }
   W = RelaxWork();
 }
 
 // k iterations of the nine components (every kernel returns at once after
 // the stop).
+// z = M^-1 r (multigrid), z = 0 on fixed unknowns, r.z and beta.
+static pdf_status relax_precondition(pdf_particles* P, int first, cudaStream_t st) {
+  const RelaxMesh& R = P->mesh->rx;
+  RelaxWork& W = P->rx;
+  RxDot d;
+  d.wall = R.wall;
+  d.rz = W.scal + kRRz;
+  d.beta = W.scal + kRBeta;
+  d.counter = W.ctl + kRCntUpd;
+  d.first = first;
+  return relax_amg_apply(*W.amg, W.r, W.z, W.ctl + kRActive, W.ctl + kRDone, d, st);
+}
+
 static pdf_status relax_iterations(pdf_particles* P, int k, cudaStream_t st) {
   const RelaxMesh& R = P->mesh->rx;
   RelaxWork& W = P->rx;
   const dim3 grid(W.nb, 9);
+  if (W.amg) {
+    for (int i = 0; i < k; ++i) {
+      PDF_KERNEL("k_cg_spmv_rec", st, k_cg_spmv_rec<<<grid, kRBlock, 0, st>>>(R.n_rep, R.nnz, R.rp, R.ci, W.aval,
+                                                                               R.wall, W.z, W.p, W.q, W.part, W.scal,
+                                                                               W.ctl));
+      PDF_KERNEL("k_cg_update_mg", st, k_cg_update_mg<<<grid, kRBlock, 0, st>>>(R.n_rep, W.scal, W.x, W.r, W.p, W.q,
+                                                                                 W.part, W.ctl));
+      PDF_KERNEL("k_cg_close", st, k_cg_close<<<1, 32, 0, st>>>(W.ctl));
+      const pdf_status s = relax_precondition(P, 0, st);
+      if (s != PDF_OK) return s;
+    }
+    return PDF_OK;
+  }
   for (int i = 0; i < k; ++i) {
     PDF_KERNEL("k_cg_spmv", st, k_cg_spmv<<<grid, kRBlock, 0, st>>>(R.n_rep, R.nnz, R.rp, R.ci, W.aval, R.wall, W.p,
                                                                      W.q, W.part, W.scal, W.ctl));
@@ -475,9 +617,38 @@ static pdf_status relax_prepare(pdf_particles* P, const pdf_model_params* params
   return PDF_OK;
 }
 
+// The preconditioner's matrices from the current relaxation matrices.
+static pdf_status relax_amg_values(pdf_particles* P, cudaStream_t st) {
+  const RelaxMesh& R = P->mesh->rx;
+  RelaxWork& W = P->rx;
+  RelaxAmg& G = *W.amg;
+  PDF_KERNEL("k_rx_fill", st, k_rx_fill<<<rblocks(R.n_rep), 256, 0, st>>>(
+                                  R.n_rep, R.nnz, R.rp, R.ci, W.aval, R.wall, relax_amg_level0(G, 0),
+                                  relax_amg_level0(G, 1), relax_amg_level0(G, 2), relax_amg_level0(G, 3)));
+  return relax_amg_update(G, st);
+}
+
 }  // namespace pdfgb
 
 using namespace pdfgb;
+
+extern "C" pdf_status pdf_relax_set_solver(pdf_particles* p, int32_t multigrid) {
+  if (!p || (multigrid != 0 && multigrid != 1)) return fail(PDF_EINVAL, "pdf_relax_set_solver: bad arguments");
+  RelaxWork& W = p->rx;
+  if (W.multigrid == (multigrid == 1)) return PDF_OK;
+  PDF_CUDA(cudaDeviceSynchronize());
+  if (W.gx) {
+    cudaGraphExecDestroy(W.gx);
+    W.gx = nullptr;
+  }
+  if (W.amg) {
+    relax_amg_free(*W.amg);
+    delete W.amg;
+    W.amg = nullptr;
+  }
+  W.multigrid = multigrid == 1;
+  return PDF_OK;
+}
 
 extern "C" pdf_status pdf_relax_rhs(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,
                                     double* rhs, double* L2, void* stream) {
@@ -511,9 +682,16 @@ extern "C" pdf_status pdf_relax_solve(pdf_particles* p, const pdf_mesh* m, const
   const dim3 grid(nb, 9);
   PDF_KERNEL("k_cg_init", st, k_cg_init<<<grid, kRBlock, 0, st>>>(R.n_rep, R.nnz, R.rp, R.ci, R.mval, W.aval, W.diag,
                                                                    R.wall, R.rep_node, nn, W.f, W.g, wp, W.x, W.r, W.z,
-                                                                   W.p, W.part));
+                                                                   W.p, W.q, W.part));
   PDF_KERNEL("k_cg_reduce", st, k_cg_reduce<<<27, kRBlock, 0, st>>>(W.part, nb, 3, W.scal));
   PDF_KERNEL("k_cg_start", st, k_cg_start<<<1, 32, 0, st>>>(rtol * rtol, max_it, W.scal, W.ctl));
+  if (W.amg) {
+    // the first direction from the multigrid (k_cg_init's Jacobi values
+    // replaced)
+    s = relax_amg_values(p, st);
+    if (s == PDF_OK) s = relax_precondition(p, 1, st);
+    if (s != PDF_OK) return s;
+  }
   // iterations in chunks of 8 (CUDA-graph replays while kernel timing is
   // off); the host reads the control words once per chunk
   constexpr int kChunk = 8;

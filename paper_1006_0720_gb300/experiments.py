@@ -73,9 +73,18 @@ def train(X, Y, steps=3000, batch=8192, lr=2e-3, seed=0, log_every=0):
     return net, losses
 
 
-def compare(gm, gp, p, wp_prev, net, rtol=1e-10, max_it=20000):
+def compare(gm, gp, p, wp_prev, net, rtol=1e-10, max_it=20000, multigrid=True):
     """Iterations and times to rtol from zero, from the previous solution and
-    from the network's guess (each from its own copy)."""
+    from the network's guess (each from its own copy), with the multigrid or
+    the Jacobi preconditioner (the choice is restored to multigrid after)."""
+    A.pdf_relax_set_solver(gp, multigrid)
+    try:
+        return _compare(gm, gp, p, wp_prev, net, rtol, max_it)
+    finally:
+        A.pdf_relax_set_solver(gp, True)
+
+
+def _compare(gm, gp, p, wp_prev, net, rtol, max_it):
     out = {}
     for name in ("zero", "previous", "mlp"):
         if name == "zero":

@@ -322,10 +322,12 @@ def test_fallbacks_for_values_outside_the_fixed_point_ranges():
     assert info["lost"] == 0
 
 
-def test_relaxation_solve_matches_the_oracle():
+@pytest.mark.parametrize("multigrid", [True, False])
+def test_relaxation_solve_matches_the_oracle(multigrid):
     """pdf_relax_solve on the small channel after a few steps: the nodal
     right-hand side, the L^2 fields and the converged solution agree with the
-    oracle's assembly and sparse direct solve."""
+    oracle's assembly and sparse direct solve (multigrid and Jacobi
+    preconditioners)."""
     import oracle.relax as OR
     m = inputs.channel_mesh(20, 40, seed=1)
     counts = np.full(2 * 19 * 39, 50, dtype=np.int32)
@@ -349,6 +351,7 @@ def test_relaxation_solve_matches_the_oracle():
     for c, cxi in enumerate((1 + 1.3 * nrm[:, 0] ** 2, 1 + 1.3 * nrm[:, 1] ** 2, np.ones(gm.n_nodes))):
         assert_field_close(L2[c].cpu().numpy(), OR.lengthscale2(S, p.nu, cxi), "L^2 class %d" % c)
     wp = torch.zeros((9, gm.n_nodes), dtype=torch.float64, device="cuda")
+    pg.pdf_relax_set_solver(gp, multigrid)
     iters, res = pg.pdf_relax_solve(gp, gm, p, wp, rtol=1e-13, max_it=2000)
     ref = OR.solve(m, S, ref_rhs, p.nu)
     assert_field_close(wp.cpu().numpy().T, ref.T, "relaxation solution", rtol=1e-9)
@@ -356,3 +359,30 @@ def test_relaxation_solve_matches_the_oracle():
     # warm start from the solution: converged at once
     iters2, _ = pg.pdf_relax_solve(gp, gm, p, wp, rtol=1e-10, max_it=2000)
     assert max(iters2) <= 1
+
+
+def test_relaxation_multigrid_and_jacobi_agree_on_a_larger_channel():
+    """The 100 x 200 channel (about 20,000 unknowns): both preconditioners
+    reach the same solution; the multigrid needs far fewer iterations, and
+    the choice can be switched between solves."""
+    m = inputs.channel_mesh(100, 200, seed=3)
+    gm = pg.Mesh(m)
+    gp = pg.Particles(gm, 4, ppe=30, u_sigma=0.1)
+    p = pg.model_params(closure="glm")
+    pg.pdf_estimate_stats(gp, gm)
+    pg.pdf_step(gp, gm, p, step=0)
+    pg.pdf_estimate_stats(gp, gm)
+    out = {}
+    for mg in (True, False, True):
+        wp = torch.zeros((9, gm.n_nodes), dtype=torch.float64, device="cuda")
+        pg.pdf_relax_set_solver(gp, mg)
+        iters, res = pg.pdf_relax_solve(gp, gm, p, wp, rtol=1e-12, max_it=20000)
+        assert max(res) <= 1e-12
+        if mg in out:
+            assert list(iters) == out[mg][0]
+            assert torch.equal(wp, out[mg][1])
+        out[mg] = (list(iters), wp)
+    it_mg, it_j = max(out[True][0]), max(out[False][0])
+    assert it_mg * 4 < it_j, (it_mg, it_j)
+    scale = out[False][1].abs().amax(dim=1, keepdim=True).clamp_min(1e-300)
+    assert float(((out[True][1] - out[False][1]).abs() / scale).max()) < 1e-9
