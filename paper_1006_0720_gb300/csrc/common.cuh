@@ -120,7 +120,7 @@ struct RelaxWork {
   // the first multigrid solve
   bool multigrid = true;
   RelaxAmg* amg = nullptr;
-  double *f = nullptr, *L2 = nullptr, *aval = nullptr, *diag = nullptr, *g = nullptr;
+  double *f = nullptr, *L2 = nullptr, *eL2 = nullptr, *aval = nullptr, *diag = nullptr, *g = nullptr;
   double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
   double *part = nullptr, *scal = nullptr, *host = nullptr;
   int32_t *ctl = nullptr, *host_ctl = nullptr;  // device control words and their page-locked copy

@@ -75,23 +75,31 @@ __global__ void k_relax_nodes(int32_t n_nodes, const double* __restrict__ ns, co
   }
 }
 
+// Element means of the nodal L^2 of the three classes, [n_tri][3].
+__global__ void k_relax_elem_l2(int32_t n_tri, const int32_t* __restrict__ tri, int32_t n_nodes,
+                                const double* __restrict__ L2, double* __restrict__ eL2) {
+  for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n_tri; e += gridDim.x * blockDim.x) {
+    const int32_t a = tri[3 * e], b = tri[3 * e + 1], c = tri[3 * e + 2];
+#pragma unroll
+    for (int cl = 0; cl < 3; ++cl) {
+      const double* L = L2 + (int64_t)cl * n_nodes;
+      eL2[3 * (int64_t)e + cl] = (L[a] + L[b] + L[c]) / 3.0;
+    }
+  }
+}
+
 // Matrix values of the three classes for every stored entry: the constant
 // mass part plus sum over contributing elements of L2_e * (stiffness entry).
 __global__ void k_relax_assemble(int64_t nnz, const double* __restrict__ mval, const int32_t* __restrict__ ctb_off,
                                  const int32_t* __restrict__ ctb_e, const double* __restrict__ ctb_k,
-                                 const int32_t* __restrict__ tri, int32_t n_nodes, const double* __restrict__ L2,
-                                 double* __restrict__ aval) {
+                                 const double* __restrict__ eL2, double* __restrict__ aval) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x) {
     double s[3] = {mval[q], mval[q], mval[q]};
     for (int32_t t = ctb_off[q]; t < ctb_off[q + 1]; ++t) {
-      const int32_t e = ctb_e[t];
+      const double* L = eL2 + 3 * (int64_t)ctb_e[t];
       const double kab = ctb_k[t];
-      const int32_t a = tri[3 * e], b = tri[3 * e + 1], c = tri[3 * e + 2];
 #pragma unroll
-      for (int cl = 0; cl < 3; ++cl) {
-        const double* L = L2 + (int64_t)cl * n_nodes;
-        s[cl] += (L[a] + L[b] + L[c]) / 3.0 * kab;
-      }
+      for (int cl = 0; cl < 3; ++cl) s[cl] += L[cl] * kab;
     }
 #pragma unroll
     for (int cl = 0; cl < 3; ++cl) aval[(int64_t)cl * nnz + q] = s[cl];
@@ -491,6 +499,7 @@ static pdf_status relax_alloc(pdf_particles* P) {
   A((void**)&W.f, sizeof(double) * 9 * nn);
   A((void**)&W.g, sizeof(double) * 9 * nn);
   A((void**)&W.L2, sizeof(double) * 3 * nn);
+  A((void**)&W.eL2, sizeof(double) * 3 * (size_t)P->mesh->d.n_tri);
   A((void**)&W.aval, sizeof(double) * 3 * R.nnz);
   A((void**)&W.diag, sizeof(double) * 3 * R.n_rep);
   A((void**)&W.x, sizeof(double) * 9 * R.n_rep);
@@ -515,7 +524,7 @@ static pdf_status relax_alloc(pdf_particles* P) {
 }
 
 void relax_free(RelaxWork& W) {
-  cudaFree(W.f); cudaFree(W.g); cudaFree(W.L2); cudaFree(W.aval); cudaFree(W.diag); cudaFree(W.x); cudaFree(W.r);
+  cudaFree(W.f); cudaFree(W.g); cudaFree(W.L2); cudaFree(W.eL2); cudaFree(W.aval); cudaFree(W.diag); cudaFree(W.x); cudaFree(W.r);
   cudaFree(W.z); cudaFree(W.p); cudaFree(W.q); cudaFree(W.part); cudaFree(W.scal); cudaFree(W.ctl);
   if (W.host) cudaFreeHost(W.host);
   if (W.host_ctl) cudaFreeHost(W.host_ctl);
@@ -611,8 +620,10 @@ static pdf_status relax_prepare(pdf_particles* P, const pdf_model_params* params
   RelaxWork& W = P->rx;
   const int32_t nn = m->d.n_nodes;
   PDF_KERNEL("k_relax_nodes", st, k_relax_nodes<<<rblocks(nn), 256, 0, st>>>(nn, P->ns, P->nd, R.wall_n, relax_params(params), W.f, W.L2, W.g));
+  PDF_KERNEL("k_relax_elem_l2", st, k_relax_elem_l2<<<rblocks(m->d.n_tri), 256, 0, st>>>(m->d.n_tri, m->d.tri, nn, W.L2,
+                                                                                         W.eL2));
   PDF_KERNEL("k_relax_assemble", st, k_relax_assemble<<<rblocks(R.nnz), 256, 0, st>>>(R.nnz, R.mval, R.ctb_off, R.ctb_e, R.ctb_k,
-                                                                                      m->d.tri, nn, W.L2, W.aval));
+                                                                                      W.eL2, W.aval));
   PDF_KERNEL("k_cg_diag", st, k_cg_diag<<<dim3(rblocks(R.n_rep), 3), 256, 0, st>>>(R.n_rep, R.nnz, R.rp, R.ci, W.aval, W.diag));
   return PDF_OK;
 }
