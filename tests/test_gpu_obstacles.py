@@ -90,3 +90,31 @@ def test_obstacles_fp32_state_invariants():
     assert st["ps"].min() >= 0.0 and st["ps"].max() <= 1.0
     assert np.all(st["om"] >= 0) and st["om"].max() < 100
     assert np.abs(st["u"]).max() < 20 and np.abs(st["v"]).max() < 20
+
+
+@pytest.mark.parametrize("multigrid", [True, False])
+def test_obstacles_relaxation_solve_matches_the_oracle(multigrid):
+    """The elliptic-relaxation solve on the obstacle mesh (walls in several
+    orientations, concave corners, graded elements, inflow/outflow twins):
+    the converged solution of both preconditioners agrees with the oracle's
+    sparse direct solve of the GPU's own statistics."""
+    import oracle.relax as OR
+    cfg = inputs.OBSTACLES["obstacles_small_mean20"]
+    m, counts, gm, gp, p = _setup(cfg, capi.PDF_FP64)
+    pg.pdf_estimate_stats(gp, gm)
+    for s in range(3):
+        pg.pdf_step(gp, gm, p, step=s)
+        pg.pdf_estimate_stats(gp, gm)
+    ns = torch.empty((gm.n_nodes, capi.PDF_NNS), dtype=torch.float64, device="cuda")
+    nd = torch.empty((gm.n_nodes, capi.PDF_NND), dtype=torch.float64, device="cuda")
+    pg.pdf_estimate_stats(gp, gm, node_stats=ns, node_derivs=nd)
+    S, Dv = ns.cpu().numpy(), nd.cpu().numpy()
+    wp = torch.zeros((9, gm.n_nodes), dtype=torch.float64, device="cuda")
+    pg.pdf_relax_set_solver(gp, multigrid)
+    iters, res = pg.pdf_relax_solve(gp, gm, p, wp, rtol=1e-13, max_it=6000)
+    assert max(res) <= 1e-13
+    rhs = np.stack([oracle.relax_rhs(S[n], Dv[n]) for n in range(gm.n_nodes)], axis=1)
+    ref = OR.solve(m, S, rhs, p.nu)
+    assert_field_close(wp.cpu().numpy().T, ref.T, "obstacle relaxation solution", rtol=1e-9)
+    if multigrid:
+        assert max(iters) < 200, iters
