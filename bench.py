@@ -311,13 +311,11 @@ def run_gpu(args):
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        pg.capi.check(L.pdf_particles_set_state(gp.handle, *[ctypes.c_void_p(ptr[k]) for k in keys + ("elem",)], sp),
-                      "set_state")
-        pg.pdf_step(gp, gm, p, step=step_no, stream=stream)
+        # the step reads the host state and writes the stepped state back
+        # (chunks of loads, steps and stores overlapped), then the statistics
+        pg.pdf_step_host(gp, gm, p, host, step=step_no, stream=stream)
         pg.capi.check(L.pdf_estimate_stats(gp.handle, gm.handle, None, ctypes.c_void_p(host_ns.data_ptr()), None, sp),
                       "estimate_stats")
-        pg.capi.check(L.pdf_particles_get_state(gp.handle, *[ctypes.c_void_p(ptr[k]) for k in keys + ("elem",)], sp),
-                      "get_state")
         stream.synchronize()
         step_no += 1
     barrier()
@@ -326,7 +324,8 @@ def run_gpu(args):
     state_bytes = n * (7 * 8 + 4)
     e2e = {"value": replica_value(world, n, e2e_steps, 1e3 * e2e_max), "unit": UNIT, "h2d_bytes_per_step": state_bytes,
            "d2h_bytes_per_step": state_bytes + gm.n_nodes * 12 * 8, "steps": e2e_steps,
-           "what": "state in page-locked host memory: copied in, stepped, statistics and state copied out every step"}
+           "what": "state in page-locked host memory: read, stepped and written back every step (pdf_step_host: "
+                   "chunked loads, steps and stores overlapped), node statistics copied out"}
 
     if rank != 0:
         if dist is not None:

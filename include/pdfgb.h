@@ -284,6 +284,27 @@ pdf_status pdf_particles_set_state(pdf_particles* p, const double* x, const doub
 pdf_status pdf_step(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,
                     const double* wp, const double* elem_coeff, uint32_t step, void* stream,
                     pdf_step_info* info);
+/* pdf_step for a state that lives in host memory: equivalent to
+ * pdf_particles_set_state(x ... elem), pdf_step(...) and
+ * pdf_particles_get_state(x ... elem) (same results, bit for bit), with the
+ * transfers overlapped: the particles are taken in chunks of particle ids,
+ * and the load of one chunk, the step of the previous one and the store of
+ * the one before run at once (the host link's two directions and the SMs
+ * busy together).
+ *   x ... ps    page-locked host (or device) [n] FP64, elem [n] int32; read,
+ *               then overwritten with the stepped state (in particle-id
+ *               order, as pdf_particles_get_state returns it)
+ *   other arguments as pdf_step; the counters are always gathered (one
+ *               synchronization of `stream` at the end) and filled into
+ *               info when given.
+ * The particle set keeps the stepped state (slot = particle id) for
+ * pdf_estimate_stats.  PDF_EINVAL for pageable host buffers, for positions
+ * outside |x|, |y| < 64 and for the IECM mixing model (its conditioned
+ * means belong to the device-resident order); PDF_ELOST if any particle was
+ * lost; PDF_ESTATE as pdf_step. */
+pdf_status pdf_step_host(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params, const double* wp,
+                         const double* elem_coeff, uint32_t step, double* x, double* y, double* u, double* v,
+                         double* w, double* om, double* ps, int32_t* elem, void* stream, pdf_step_info* info);
 
 /* Particle-in-cell statistics (sec. 3.3) and derivatives (sec. 3.4):
  * groups particles by element (stable radix sort by element id), element

@@ -186,6 +186,35 @@ def pdf_step(particles, mesh, params, wp=None, elem_coeff=None, step=0, stream=N
     return si.as_dict() if info else None
 
 
+def _host_ptr(t, dtype, numel):
+    if t.is_cuda or not t.is_pinned() or not t.is_contiguous():
+        raise ValueError("expected a contiguous page-locked host tensor")
+    if t.dtype != dtype or t.numel() != numel:
+        raise ValueError("expected %d elements of %s" % (numel, dtype))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def pdf_step_host(particles, mesh, params, state, wp=None, elem_coeff=None, step=0, stream=None, info=False):
+    """pdf_step for a state held in page-locked host tensors (dict x, y, u,
+    v, w, om, ps float64 and elem int32, particle-id order), which is read
+    and overwritten with the stepped state; the loads, the step and the
+    stores run overlapped in chunks.  Returns the counters dict when
+    info=True."""
+    si = capi.StepInfo()
+    args = [_host_ptr(state[k], torch.float64, particles.n) for k in ("x", "y", "u", "v", "w", "om", "ps")]
+    args.append(_host_ptr(state["elem"], torch.int32, particles.n))
+    st = lib().pdf_step_host(particles.handle, mesh.handle, ctypes.byref(params),
+                             _ptr(wp, torch.float64, None if wp is None else 9 * mesh.n_nodes),
+                             _ptr(elem_coeff, torch.float64, None if elem_coeff is None else capi.PDF_NCOEF * mesh.n_tri),
+                             int(step) & 0xFFFFFFFF, *args, _stream(stream), ctypes.byref(si))
+    if info and st == capi.PDF_ELOST:
+        d = si.as_dict()
+        d["status"] = "lost"
+        return d
+    check(st, "pdf_step_host")
+    return si.as_dict() if info else None
+
+
 def pdf_estimate_stats(particles, mesh, elem_stats=None, node_stats=None, node_derivs=None, stream=None):
     check(lib().pdf_estimate_stats(particles.handle, mesh.handle,
                                    _ptr(elem_stats, torch.float64, None if elem_stats is None else capi.PDF_NES * mesh.n_tri),

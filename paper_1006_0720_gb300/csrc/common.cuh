@@ -113,6 +113,13 @@ struct RelaxMesh {
   int32_t* pw_e = nullptr;      // [pw_off[n_rep]][3]
   double* pw_n = nullptr;       // [pw_off[n_rep]][3]
 };
+// Streams and events of pdf_step_host (created at its first call).
+constexpr int kHostChunks = 16;
+struct HostIo {
+  cudaStream_t in = nullptr, out = nullptr;
+  cudaEvent_t start = nullptr, done = nullptr;
+  cudaEvent_t loaded[kHostChunks] = {}, stepped[kHostChunks] = {};
+};
 struct RelaxAmg;
 struct RelaxWork {
   int32_t nb = 0;
@@ -281,9 +288,22 @@ struct pdf_particles {
   double* gradP = nullptr;  // [n_nodes][2]
   pdfgb::PressWork pw;
   pdfgb::RedistWork rd;
+  pdfgb::HostIo hio;
 };
 
 namespace pdfgb {
+// Host-resident state transfers of pdf_step_host (particles.cu): the
+// address kernels use for a caller's buffer (NULL for pageable memory);
+// the load of particles [beg, beg + cnt) into slots [beg, beg + cnt) (slot =
+// particle id; positions outside |x| < 64 counted in *bad) and the store of
+// those slots back to the same places.
+void* state_kernel_view(const void* ptr);
+pdf_status host_io_init(pdf_particles* p);
+int host_io_blocks();  // grid of each chunk's load and store kernels
+pdf_status state_in_range(pdf_particles* p, double* const in[7], const int32_t* ie, int64_t beg, int64_t cnt,
+                          unsigned long long* bad, int blocks, cudaStream_t st);
+pdf_status state_out_range(const pdf_particles* p, double* const out[7], int32_t* oe, int64_t beg, int64_t cnt,
+                           int blocks, cudaStream_t st);
 // Launches through prof_launch are counted and, when timing is enabled,
 // bracketed by CUDA events on the launch stream.
 void prof_launch(const char* name, cudaStream_t st, void (*launch)(void*), void* ctx);

@@ -167,7 +167,7 @@ __global__ void k_inv_pid(const int32_t* __restrict__ pid, int32_t* __restrict__
 
 __global__ void k_state_out(StateOut S) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < S.n; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = S.inv[q];
+    const int64_t i = S.inv ? S.inv[q] : q;  // no permutation: slot = particle id
     if (S.o[0]) S.o[0][q] = __longlong_as_double((long long)fx::fix2d(S.x[i], kPosF));
     if (S.o[1]) S.o[1][q] = __longlong_as_double((long long)fx::fix2d(S.y[i], kPosF));
 #pragma unroll
@@ -177,10 +177,10 @@ __global__ void k_state_out(StateOut S) {
   }
 }
 
-// In: slot i takes particle i; positions outside |x| < 64 are counted in
-// *bad and stored as 0.
+// In: slot i takes particle pid0 + i; positions outside |x| < 64 are
+// counted in *bad and stored as 0.
 struct StateIn {
-  int64_t n;
+  int64_t n, pid0;
   const double* in[7];  // x, y, u, v, w, om, ps
   const int32_t* ie;
   int64_t *x, *y;
@@ -207,7 +207,7 @@ __global__ void k_state_in(StateIn S) {
       else S.f[k][i] = __double2float_rn(v);
     }
     S.elem[i] = S.ie[i];
-    S.pid[i] = (int32_t)i;
+    S.pid[i] = (int32_t)(S.pid0 + i);
   }
 }
 
@@ -230,6 +230,17 @@ static void free_particles(pdf_particles* p) {
   cudaFree(p->hist); cudaFree(p->hist_part); cudaFree(p->seg);
   cudaFree(p->counters);
   cudaFree(p->pres); cudaFree(p->gradP);
+  {
+    HostIo& H = p->hio;
+    if (H.in) cudaStreamDestroy(H.in);
+    if (H.out) cudaStreamDestroy(H.out);
+    if (H.start) cudaEventDestroy(H.start);
+    if (H.done) cudaEventDestroy(H.done);
+    for (int k = 0; k < kHostChunks; ++k) {
+      if (H.loaded[k]) cudaEventDestroy(H.loaded[k]);
+      if (H.stepped[k]) cudaEventDestroy(H.stepped[k]);
+    }
+  }
   relax_free(p->rx);
   press_free(p->pw);
   redist_free(p->rd);
@@ -380,6 +391,75 @@ static pdf_status ensure_stage(const pdf_particles* p) {
   return PDF_OK;
 }
 
+namespace pdfgb {
+
+void* state_kernel_view(const void* ptr) { return kernel_view(ptr); }
+
+int host_io_blocks() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 148;
+}
+
+pdf_status host_io_init(pdf_particles* p) {
+  HostIo& H = p->hio;
+  if (H.in) return PDF_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&H.in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&H.out, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&H.start, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&H.done, cudaEventDisableTiming);
+  for (int k = 0; k < kHostChunks && e == cudaSuccess; ++k) {
+    e = cudaEventCreateWithFlags(&H.loaded[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&H.stepped[k], cudaEventDisableTiming);
+  }
+  return e == cudaSuccess ? PDF_OK : cuda_fail(e, "pdf_step_host: streams and events");
+}
+
+pdf_status state_in_range(pdf_particles* p, double* const in[7], const int32_t* ie, int64_t beg, int64_t cnt,
+                          unsigned long long* bad, int blocks, cudaStream_t st) {
+  StateIn S;
+  S.n = cnt;
+  S.pid0 = beg;
+  for (int i = 0; i < 7; ++i) S.in[i] = in[i] + beg;
+  S.ie = ie + beg;
+  S.x = p->x + beg;
+  S.y = p->y + beg;
+  fx::df* dd[5] = {p->u, p->v, p->w, p->om, p->ps};
+  float* ff[5] = {p->uf, p->vf, p->wf, p->omf, p->psf};
+  for (int k = 0; k < 5; ++k) {
+    S.d[k] = p->precision == PDF_FP64 ? dd[k] + beg : nullptr;
+    S.f[k] = p->precision == PDF_FP64 ? nullptr : ff[k] + beg;
+  }
+  S.elem = p->elem + beg;
+  S.pid = p->pid + beg;
+  S.bad = bad;
+  PDF_KERNEL("k_state_in", st, k_state_in<<<blocks, 256, 0, st>>>(S));
+  return PDF_OK;
+}
+
+pdf_status state_out_range(const pdf_particles* p, double* const out[7], int32_t* oe, int64_t beg, int64_t cnt,
+                           int blocks, cudaStream_t st) {
+  StateOut S;
+  S.n = cnt;
+  S.inv = nullptr;
+  S.x = p->x + beg;
+  S.y = p->y + beg;
+  const fx::df* dd[5] = {p->u, p->v, p->w, p->om, p->ps};
+  const float* ff[5] = {p->uf, p->vf, p->wf, p->omf, p->psf};
+  for (int k = 0; k < 5; ++k) {
+    S.d[k] = p->precision == PDF_FP64 ? dd[k] + beg : nullptr;
+    S.f[k] = p->precision == PDF_FP64 ? nullptr : ff[k] + beg;
+  }
+  S.elem = p->elem + beg;
+  for (int i = 0; i < 7; ++i) S.o[i] = out[i] + beg;
+  S.oe = oe + beg;
+  PDF_KERNEL("k_state_out", st, k_state_out<<<blocks, 256, 0, st>>>(S));
+  return PDF_OK;
+}
+
+}  // namespace pdfgb
+
 extern "C" pdf_status pdf_particles_get_state(const pdf_particles* p, double* x, double* y,
                                               double* u, double* v, double* w, double* om,
                                               double* ps, int32_t* elem, void* stream) {
@@ -478,6 +558,7 @@ extern "C" pdf_status pdf_particles_set_state(pdf_particles* p, const double* x,
   if (!S.ie) all = false;
   if (all) {  // one pass reading every source where it is
     S.n = p->n;
+    S.pid0 = 0;
     S.x = p->x;
     S.y = p->y;
     for (int k = 0; k < 5; ++k) {

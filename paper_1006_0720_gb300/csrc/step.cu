@@ -1172,13 +1172,15 @@ extern "C" pdf_status pdf_elem_coeff(pdf_particles* p, const pdf_mesh* m, const 
   return build_rows(p, params, wp, rows, false, (cudaStream_t)stream);
 }
 
-extern "C" pdf_status pdf_step(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,
-                               const double* wp, const double* elem_coeff, uint32_t step, void* stream,
-                               pdf_step_info* info) {
+namespace pdfgb {
+
+// Everything of a step before the particle kernel: checks, the coefficient
+// rows, the counters.
+static pdf_status step_prepare(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,
+                               const double* wp, const double* elem_coeff, bool count, cudaStream_t st) {
   if (!p || !m || p->mesh != m) return fail(PDF_EINVAL, "pdf_step: NULL or mismatched handles");
   pdf_status s = check_params(params);
   if (s != PDF_OK) return s;
-  cudaStream_t st = (cudaStream_t)stream;
   const MeshDev& M = m->d;
   if (params->closure == PDF_CLOSURE_FROZEN) {
     if (!elem_coeff) return fail(PDF_EINVAL, "pdf_step: FROZEN needs elem_coeff");
@@ -1192,8 +1194,45 @@ extern "C" pdf_status pdf_step(pdf_particles* p, const pdf_mesh* m, const pdf_mo
   }
   if (params->mix == PDF_MIX_IECM && !p->have_cond)
     return fail(PDF_ESTATE, "pdf_step: IECM needs pdf_particles_set_iecm and a pdf_estimate_stats after it");
-  if (info) PDF_CUDA(cudaMemsetAsync(p->counters, 0, sizeof(long long) * 8, st));
+  if (count) PDF_CUDA(cudaMemsetAsync(p->counters, 0, sizeof(long long) * 8, st));
+  return PDF_OK;
+}
+
+// The particle kernel's arguments; StepLaunch::run advances the slots
+// [beg, beg + cnt) (every per-slot pointer offset by beg) with at most
+// per_sm blocks per SM.
+struct StepLaunch {
   StepArgs A;
+  FxArgs F;
+  F32Args S;
+  int kind = 0;  // 0: FP64 kernel, 1: fixed point / double-float, 2: FP32 state
+
+  pdf_status run(int64_t beg, int64_t cnt, cudaStream_t st, int per_sm = 8) const {
+    if (cnt <= 0) return PDF_OK;
+    const int nb = blocks_for(cnt, 256, per_sm);
+    StepArgs a = A;
+    a.n = cnt;
+    a.x += beg; a.y += beg; a.elem += beg; a.pid += beg;
+    if (a.cond) a.cond += beg;
+    if (kind == 2) {
+      F32Args f = S;
+      f.u += beg; f.v += beg; f.w += beg; f.om += beg; f.ps += beg;
+      PDF_KERNEL("k_step", st, k_step_f32<<<nb, 256, 0, st>>>(a, F, f));
+    } else if (kind == 1) {
+      a.u += beg; a.v += beg; a.w += beg; a.om += beg; a.ps += beg;
+      PDF_KERNEL("k_step", st, k_step_fx<<<nb, 256, 0, st>>>(a, F));
+    } else {
+      a.u += beg; a.v += beg; a.w += beg; a.om += beg; a.ps += beg;
+      PDF_KERNEL("k_step", st, k_step<<<nb, 256, 0, st>>>(a));
+    }
+    return PDF_OK;
+  }
+};
+
+static StepLaunch step_args(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params, uint32_t step) {
+  const MeshDev& M = m->d;
+  StepLaunch L;
+  StepArgs& A = L.A;
   A.n = p->n;
   A.x = p->x; A.y = p->y; A.u = p->u; A.v = p->v; A.w = p->w; A.om = p->om; A.ps = p->ps;
   A.elem = p->elem;
@@ -1214,7 +1253,7 @@ extern "C" pdf_status pdf_step(pdf_particles* p, const pdf_mesh* m, const pdf_mo
   A.src_y = params->src_y;
   A.src_r = params->src_r;
   if (p->precision == PDF_FP32_STATE || params->arith == PDF_ARITH_FX) {
-    FxArgs F;
+    FxArgs& F = L.F;
     F.rows = p->rows_fx;
     F.geo = M.fgeo;
     uint64_t b;
@@ -1239,20 +1278,105 @@ extern "C" pdf_status pdf_step(pdf_particles* p, const pdf_mesh* m, const pdf_mo
       }
     }
     if (p->precision == PDF_FP32_STATE) {
-      F32Args S;
+      F32Args& S = L.S;
       S.u = p->uf; S.v = p->vf; S.w = p->wf; S.om = p->omf; S.ps = p->psf;
       S.rows = p->rows_f32;
-      PDF_KERNEL("k_step", st, k_step_f32<<<blocks_for(p->n, 256, 8), 256, 0, st>>>(A, F, S));
+      L.kind = 2;
     } else {
-      PDF_KERNEL("k_step", st, k_step_fx<<<blocks_for(p->n, 256, 8), 256, 0, st>>>(A, F));
+      L.kind = 1;
     }
-  } else {
-    PDF_KERNEL("k_step", st, k_step<<<blocks_for(p->n, 256, 8), 256, 0, st>>>(A));
   }
+  return L;
+}
+
+// The counters of the step into info (one synchronization).
+static pdf_status step_info(pdf_particles* p, pdf_step_info* info, cudaStream_t st) {
+  long long c[8];
+  PDF_CUDA(cudaMemcpyAsync(c, p->counters, sizeof(c), cudaMemcpyDeviceToHost, st));
+  PDF_CUDA(cudaStreamSynchronize(st));
+  info->walk_steps = c[kCntWalk];
+  info->reflections = c[kCntRefl];
+  info->crossings_periodic = c[kCntPeriodic];
+  info->fallbacks = c[kCntFallback];
+  info->brute = c[kCntBrute];
+  info->lost = c[kCntLost];
+  info->omega_reflections = c[kCntOmega];
+  info->near_face = c[kCntNear];
+  if (info->lost > 0) return fail(PDF_ELOST, "pdf_step: particles lost");
+  return PDF_OK;
+}
+
+}  // namespace pdfgb
+
+extern "C" pdf_status pdf_step(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,
+                               const double* wp, const double* elem_coeff, uint32_t step, void* stream,
+                               pdf_step_info* info) {
+  cudaStream_t st = (cudaStream_t)stream;
+  pdf_status s = step_prepare(p, m, params, wp, elem_coeff, info != nullptr, st);
+  if (s != PDF_OK) return s;
+  s = step_args(p, m, params, step).run(0, p->n, st);
+  if (s != PDF_OK) return s;
+  return info ? step_info(p, info, st) : PDF_OK;
+}
+
+extern "C" pdf_status pdf_step_host(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,
+                                    const double* wp, const double* elem_coeff, uint32_t step, double* x, double* y,
+                                    double* u, double* v, double* w, double* om, double* ps, int32_t* elem,
+                                    void* stream, pdf_step_info* info) {
+  if (!p || !x || !y || !u || !v || !w || !om || !ps || !elem)
+    return fail(PDF_EINVAL, "pdf_step_host: NULL argument");
+  if (params && params->mix == PDF_MIX_IECM)
+    return fail(PDF_EINVAL, "pdf_step_host: IECM needs the device-resident state (pdf_step)");
+  double* io[7] = {x, y, u, v, w, om, ps};
+  double* view[7];
+  for (int i = 0; i < 7; ++i)
+    if (!(view[i] = static_cast<double*>(state_kernel_view(io[i]))))
+      return fail(PDF_EINVAL, "pdf_step_host: the state arrays must be page-locked host or device memory");
+  int32_t* ve = static_cast<int32_t*>(state_kernel_view(elem));
+  if (!ve) return fail(PDF_EINVAL, "pdf_step_host: the state arrays must be page-locked host or device memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  pdf_status s = step_prepare(p, m, params, wp, elem_coeff, true, st);
+  if (s != PDF_OK) return s;
+  s = host_io_init(p);
+  if (s != PDF_OK) return s;
+  HostIo& H = p->hio;
+  unsigned long long* bad = reinterpret_cast<unsigned long long*>(p->counters + 15);
+  PDF_CUDA(cudaMemsetAsync(bad, 0, sizeof(long long), st));
+  // the state is loaded in particle-id order (slot = id), so that every
+  // chunk's loads and stores are contiguous ranges on both sides
+  const StepLaunch L = step_args(p, m, params, step);
+  const int64_t n = p->n;
+  const int K = (int)std::max<int64_t>(1, std::min<int64_t>(kHostChunks, n / 65536));
+  const int64_t chunk = (n + K - 1) / K;
+  const int io_blocks = host_io_blocks();
+  PDF_CUDA(cudaEventRecord(H.start, st));
+  PDF_CUDA(cudaStreamWaitEvent(H.in, H.start, 0));
+  PDF_CUDA(cudaStreamWaitEvent(H.out, H.start, 0));
+  for (int k = 0; k < K; ++k) {
+    const int64_t beg = k * chunk, cnt = std::min<int64_t>(chunk, n - beg);
+    if (cnt <= 0) break;
+    s = state_in_range(p, view, ve, beg, cnt, bad, io_blocks, H.in);
+    if (s != PDF_OK) return s;
+    PDF_CUDA(cudaEventRecord(H.loaded[k], H.in));
+    PDF_CUDA(cudaStreamWaitEvent(st, H.loaded[k], 0));
+    // two blocks per SM: the step kernel's blocks would otherwise fill the
+    // register files and hold off the load and store kernels, which keep
+    // the host link busy while it runs
+    s = L.run(beg, cnt, st, 2);
+    if (s != PDF_OK) return s;
+    PDF_CUDA(cudaEventRecord(H.stepped[k], st));
+    PDF_CUDA(cudaStreamWaitEvent(H.out, H.stepped[k], 0));
+    s = state_out_range(p, view, ve, beg, cnt, io_blocks, H.out);
+    if (s != PDF_OK) return s;
+  }
+  PDF_CUDA(cudaEventRecord(H.done, H.out));
+  PDF_CUDA(cudaStreamWaitEvent(st, H.done, 0));
+  p->since_reorder = 0;
+  long long c[16];
+  PDF_CUDA(cudaMemcpyAsync(c, p->counters, sizeof(c), cudaMemcpyDeviceToHost, st));
+  PDF_CUDA(cudaStreamSynchronize(st));
+  if (c[15]) return fail(PDF_EINVAL, "pdf_step_host: positions must lie within |x|, |y| < 64");
   if (info) {
-    long long c[8];
-    PDF_CUDA(cudaMemcpyAsync(c, p->counters, sizeof(c), cudaMemcpyDeviceToHost, st));
-    PDF_CUDA(cudaStreamSynchronize(st));
     info->walk_steps = c[kCntWalk];
     info->reflections = c[kCntRefl];
     info->crossings_periodic = c[kCntPeriodic];
@@ -1261,7 +1385,7 @@ extern "C" pdf_status pdf_step(pdf_particles* p, const pdf_mesh* m, const pdf_mo
     info->lost = c[kCntLost];
     info->omega_reflections = c[kCntOmega];
     info->near_face = c[kCntNear];
-    if (info->lost > 0) return fail(PDF_ELOST, "pdf_step: particles lost");
   }
+  if (c[kCntLost] > 0) return fail(PDF_ELOST, "pdf_step_host: particles lost");
   return PDF_OK;
 }

@@ -79,3 +79,68 @@ def test_state_round_trips_with_every_buffer_kind(precision):
         b["x"][5] = 100.0
         with pytest.raises(capi.PdfError):
             capi.check(pg.lib().pdf_particles_set_state(gp.handle, *_ptrs(b), None), "set_state")
+
+
+def _pinned_copy(st):
+    out = {}
+    for k, v in st.items():
+        h = torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
+        h.copy_(v)
+        out[k] = h
+    return out
+
+
+@pytest.mark.parametrize("precision", [capi.PDF_FP64, capi.PDF_FP32_STATE])
+def test_step_host_matches_set_step_get(precision):
+    """pdf_step_host (chunked loads, steps and stores of a page-locked host
+    state) gives, bit for bit, the state and the statistics of
+    set_state + pdf_step + get_state, over several steps with the state
+    reordered by every statistics call in between."""
+    m = inputs.channel_mesh(50, 100, seed=2)
+    gm = pg.Mesh(m)
+    psi = inputs.scalar_slab(m)
+    a = pg.Particles(gm, 6, ppe=30, u_sigma=0.2, elem_psi0=psi, precision=precision)
+    b = pg.Particles(gm, 6, ppe=30, u_sigma=0.2, elem_psi0=psi, precision=precision)
+    assert a.n > 4 * 65536   # several chunks
+    for q in (a, b):
+        q.set_reorder(1)
+        pg.pdf_estimate_stats(q, gm)
+    p = pg.model_params(closure="slm")
+    host_a = _pinned_copy(a.get_state())
+    dev_b = b.get_state()
+    ea = torch.empty((gm.n_tri, capi.PDF_NES), dtype=torch.float64, device="cuda")
+    eb = torch.empty_like(ea)
+    for s in range(3):
+        ia = pg.pdf_step_host(a, gm, p, host_a, step=s, info=True)
+        b.set_state(dev_b)
+        ib = pg.pdf_step(b, gm, p, step=s, info=True)
+        dev_b = b.get_state()
+        torch.cuda.synchronize()
+        for k in KEYS + ("elem",):
+            assert torch.equal(host_a[k], dev_b[k].cpu()), (s, k)
+        assert ia == ib
+        pg.pdf_estimate_stats(a, gm, ea)
+        pg.pdf_estimate_stats(b, gm, eb)
+        assert torch.equal(ea, eb), s
+    # the device copy holds the stepped state too
+    da = a.get_state()
+    for k in KEYS + ("elem",):
+        assert torch.equal(da[k].cpu(), host_a[k]), k
+
+
+def test_step_host_rejects_pageable_buffers_and_iecm():
+    m = inputs.channel_mesh(8, 6, seed=1)
+    gm = pg.Mesh(m)
+    gp = pg.Particles(gm, 1, ppe=4)
+    pg.pdf_estimate_stats(gp, gm)
+    p = pg.model_params(closure="slm")
+    st = _pinned_copy(gp.get_state())
+    pageable = {k: v.clone() for k, v in st.items()}
+    args = [ctypes.c_void_p(pageable[k].data_ptr()) for k in KEYS + ("elem",)]
+    rc = pg.lib().pdf_step_host(gp.handle, gm.handle, ctypes.byref(p), None, None, 0, *args, None, None)
+    assert rc == capi.PDF_EINVAL
+    gp.set_iecm((2, 2, 2), 2)
+    pi = pg.model_params(closure="slm", mix="iecm")
+    with pytest.raises(capi.PdfError):
+        pg.pdf_step_host(gp, gm, pi, st, step=0)
+    pg.pdf_step_host(gp, gm, p, st, step=0)   # the plain model still runs
