@@ -11,7 +11,12 @@
 // One block per element.  The element's particles are copied into shared
 // memory (or, above kIecmCap particles, into global scratch slices) and
 // sorted by rank counting inside each group: O(n^2) comparisons per level,
-// fine for the tens to hundreds of particles per element the method uses.
+// fine for the small groups of the second and third levels.  The first
+// level (the whole element) of an element with more than kIecmRunMin
+// particles in shared memory is sorted instead in runs of 32 (a bitonic
+// network across each warp's lanes) whose entries find their final rank by
+// binary searches in the other runs.  Both give the same order: (key, id)
+// is a strict total order.
 #include "common.cuh"
 #include "fx.cuh"
 
@@ -19,6 +24,7 @@ namespace pdfgb {
 
 constexpr int kIecmThreads = 128;
 constexpr int kIecmCap = 256;
+constexpr int kIecmRunMin = 64;
 
 // One copy of the per-particle data (shared or global): the three velocity
 // components and the scalar as (high, low) pairs, the particle id and the
@@ -52,6 +58,43 @@ __device__ __forceinline__ int key_less(float hj, float lj, int32_t ij, float hi
   return (int)((hj < hi) | ((hj == hi) & ((lj < li) | ((lj == li) & (ij < ii)))));
 }
 
+// Ascending bitonic sort of one (h, l, id, src) entry per lane across the warp.
+__device__ __forceinline__ void warp_bitonic(float& h, float& l, int32_t& id, int32_t& src) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const float ph = __shfl_xor_sync(0xffffffffu, h, j);
+      const float pl = __shfl_xor_sync(0xffffffffu, l, j);
+      const int32_t pid = __shfl_xor_sync(0xffffffffu, id, j);
+      const int32_t ps = __shfl_xor_sync(0xffffffffu, src, j);
+      const bool partner_less = key_less(ph, pl, pid, h, l, id);
+      const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+      // the lower lane of a pair keeps the smaller entry in an ascending
+      // subsequence, the larger one in a descending one
+      if (lower == up ? partner_less : !partner_less) {
+        h = ph;
+        l = pl;
+        id = pid;
+        src = ps;
+      }
+    }
+  }
+}
+
+// Entries of the sorted run [r0, r0 + len) below (h, l, id).
+__device__ __forceinline__ int32_t count_below(const float* rh, const float* rl, const int32_t* rid, int32_t r0,
+                                               int32_t len, float h, float l, int32_t id) {
+  int32_t lo = 0, hi = len;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi) >> 1;
+    if (key_less(rh[r0 + mid], rl[r0 + mid], rid[r0 + mid], h, l, id)) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
 // floor(k i / n) and ceil(j n / k) for 0 <= i < n, 0 <= j <= k <= 127: 32-bit
 // unsigned arithmetic while the products stay below 2^31 (n < 2^24), 64-bit
 // beyond
@@ -74,6 +117,8 @@ __global__ void __launch_bounds__(kIecmThreads) k_iecm_cond(const int32_t* __res
                                                             fx::df* __restrict__ cond) {
   __shared__ float s_f[2][8][kIecmCap];
   __shared__ int32_t s_i[6][kIecmCap];
+  __shared__ float s_rh[kIecmCap], s_rl[kIecmCap];      // sorted runs of the first level
+  __shared__ int32_t s_rid[kIecmCap], s_rsrc[kIecmCap];
   const int tid = threadIdx.x;
   for (int32_t e = blockIdx.x; e < n_tri; e += gridDim.x) {
     const int32_t beg = seg[e], N = seg[e + 1] - beg;
@@ -127,9 +172,45 @@ __global__ void __launch_bounds__(kIecmThreads) k_iecm_cond(const int32_t* __res
     }
     __syncthreads();
     const int ncs[3] = {nc0, nc1, nc2};
+#pragma unroll  // static indices into the copies' pointer arrays
     for (int level = 0; level < 3; ++level) {
       const float* kh = V.a.f[2 * level];
       const float* kl = V.a.f[2 * level + 1];
+      if (level == 0 && N > kIecmRunMin && N <= kIecmCap) {
+        // runs of 32 sorted across each warp's lanes
+        const int lane = tid & 31;
+        const int32_t R = (N + 31) >> 5;
+        for (int32_t r = tid >> 5; r < R; r += kIecmThreads / 32) {
+          const int32_t pos = 32 * r + lane;
+          const bool real = pos < N;
+          float h = real ? kh[pos] : __int_as_float(0x7f800000);
+          float l = real ? kl[pos] : 0.0f;
+          int32_t id = real ? V.a.id[pos] : 0x7fffffff;
+          int32_t src = pos;
+          warp_bitonic(h, l, id, src);
+          s_rh[pos] = h;
+          s_rl[pos] = l;
+          s_rid[pos] = id;
+          s_rsrc[pos] = src;
+        }
+        __syncthreads();
+        // the final rank of each entry: its place in its run plus the
+        // entries below it in the other runs; the entry moves there
+        for (int32_t t = tid; t < N; t += kIecmThreads) {
+          const int32_t r = t >> 5;
+          const float h = s_rh[t], l = s_rl[t];
+          const int32_t id = s_rid[t];
+          int32_t to = t - 32 * r;
+          for (int32_t q = 0; q < R; ++q)
+            if (q != r) to += count_below(s_rh, s_rl, s_rid, 32 * q, min(32, N - 32 * q), h, l, id);
+          const int32_t pos = s_rsrc[t];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) V.b.f[c][to] = V.a.f[c][pos];
+          V.b.id[to] = id;
+          V.b.slot[to] = V.a.slot[pos];
+        }
+        __syncthreads();
+      } else {
       // sort each group [gs, ge) by rank counting; every entry moves to its
       // sorted position in the other copy
       for (int pos = tid; pos < N; pos += kIecmThreads) {
@@ -146,6 +227,7 @@ __global__ void __launch_bounds__(kIecmThreads) k_iecm_cond(const int32_t* __res
         V.b.slot[to] = V.a.slot[pos];
       }
       __syncthreads();
+      }
       // divide each group into k parts of equal count
       for (int pos = tid; pos < N; pos += kIecmThreads) {
         const int32_t a = V.gs[pos], n = V.ge[pos] - a;
