@@ -350,15 +350,18 @@ def run_gpu(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "hbm_frac_step": step_frac, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
             "roofline": roofline, "kernels": shares, "kernels_pass_ms_per_step": ms_prof / args.steps}
+    def want(name):
+        return not args.skip_extras and (args.extras == "all" or name in args.extras.split(","))
+
     # the complex-geometry workload (obstacles, FP32 state, 68.6M particles)
-    if not args.skip_extras:
+    if want("complex"):
         del gp
         torch.cuda.empty_cache()
         line["complex_geometry"] = run_obstacles(pg, torch, stream, steps=max(5, min(args.steps, 10)))
         torch.cuda.empty_cache()
         gp = None
     # the precision form (FP32 velocity/frequency/scalar state) on the same workload
-    if not args.skip_extras:
+    if want("fp32") or want("relax"):
         gq = pg.Particles(gm, seed, ppe=cfg["ppe"], u_sigma=cfg["u_sigma"], elem_psi0=psi,
                           precision=pg.capi.PDF_FP32_STATE)
         pg.pdf_estimate_stats(gq, gm)
@@ -368,62 +371,66 @@ def run_gpu(args):
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ksteps = max(5, min(args.steps, 20))
-        for s in range(ksteps):
-            pg.pdf_step(gq, gm, p, step=3 + s, stream=stream)
-            pg.pdf_estimate_stats(gq, gm, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms32 = e0.elapsed_time(e1) / ksteps
-        line["precision_fp32_state"] = {"value": n / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32,
-                                        "steps": ksteps,
-                                        "what": "u, v, w, omega, psi stored and advanced in FP32; x, y 64-bit fixed point"}
-        # the elliptic-relaxation solve on this mesh: cold, and warm from the previous step
-        wp = torch.zeros((9, gm.n_nodes), dtype=torch.float64, device="cuda")
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        it_cold, _ = pg.pdf_relax_solve(gq, gm, p, wp, rtol=1e-10, max_it=20000)
-        t_cold = time.perf_counter() - t0
-        # the paper's Jacobi preconditioner on the same cold solve
-        wj = torch.zeros_like(wp)
-        pg.pdf_relax_set_solver(gq, False)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        it_jac, _ = pg.pdf_relax_solve(gq, gm, p, wj, rtol=1e-10, max_it=20000)
-        t_jac = time.perf_counter() - t0
-        pg.pdf_relax_set_solver(gq, True)
-        del wj
-        pg.pdf_step(gq, gm, p, wp=wp, step=100)
-        pg.pdf_estimate_stats(gq, gm)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        it_warm, _ = pg.pdf_relax_solve(gq, gm, p, wp, rtol=1e-10, max_it=20000)
-        t_warm = time.perf_counter() - t0
-        # whole steps with the elliptic relaxation: step (drift from the
-        # solved wp) + statistics + the solve warm-started from the previous
-        # step's wp
-        its = []
-        ksteps_rx = 5
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for s in range(ksteps_rx):
-            pg.pdf_step(gq, gm, p, wp=wp, step=200 + s, stream=stream)
-            pg.pdf_estimate_stats(gq, gm, stream=stream)
-            it_s, _ = pg.pdf_relax_solve(gq, gm, p, wp, rtol=1e-8, max_it=20000, stream=stream)
-            its.append(max(it_s))
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_rx = e0.elapsed_time(e1) / ksteps_rx
-        line["relax_solve"] = {"rtol": 1e-10, "n_nodes": gm.n_nodes, "preconditioner": "multigrid",
-                               "cold": {"iterations_max": max(it_cold), "seconds": t_cold},
-                               "cold_jacobi": {"iterations_max": max(it_jac), "seconds": t_jac},
-                               "warm_previous_step": {"iterations_max": max(it_warm), "seconds": t_warm},
-                               "whole_step": {"value": n / (ms_rx * 1e-3), "unit": UNIT, "ms_per_step": ms_rx,
-                                              "steps": ksteps_rx, "rtol": 1e-8, "iterations": [min(its), max(its)],
-                                              "what": "step + statistics + elliptic-relaxation solve (FP32 state)"}}
+        if want("fp32"):
+            e0.record(stream)
+            ksteps = max(5, min(args.steps, 20))
+            for s in range(ksteps):
+                pg.pdf_step(gq, gm, p, step=3 + s, stream=stream)
+                pg.pdf_estimate_stats(gq, gm, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms32 = e0.elapsed_time(e1) / ksteps
+            line["precision_fp32_state"] = {"value": n / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32,
+                                            "steps": ksteps,
+                                            "what": "u, v, w, omega, psi stored and advanced in FP32; x, y 64-bit fixed point"}
+        if want("relax"):
+            # the elliptic-relaxation solve on this mesh: cold, and warm from the previous step
+            wp = torch.zeros((9, gm.n_nodes), dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it_cold, _ = pg.pdf_relax_solve(gq, gm, p, wp, rtol=1e-10, max_it=20000)
+            t_cold = time.perf_counter() - t0
+            # the paper's Jacobi preconditioner on the same cold solve
+            wj = torch.zeros_like(wp)
+            pg.pdf_relax_set_solver(gq, False)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it_jac, _ = pg.pdf_relax_solve(gq, gm, p, wj, rtol=1e-10, max_it=20000)
+            t_jac = time.perf_counter() - t0
+            pg.pdf_relax_set_solver(gq, True)
+            del wj
+            pg.pdf_step(gq, gm, p, wp=wp, step=100)
+            pg.pdf_estimate_stats(gq, gm)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it_warm, _ = pg.pdf_relax_solve(gq, gm, p, wp, rtol=1e-10, max_it=20000)
+            t_warm = time.perf_counter() - t0
+            # whole steps with the elliptic relaxation: step (drift from the
+            # solved wp) + statistics + the solve warm-started from the previous
+            # step's wp
+            its = []
+            ksteps_rx = 5
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for s in range(ksteps_rx):
+                pg.pdf_step(gq, gm, p, wp=wp, step=200 + s, stream=stream)
+                pg.pdf_estimate_stats(gq, gm, stream=stream)
+                it_s, _ = pg.pdf_relax_solve(gq, gm, p, wp, rtol=1e-8, max_it=20000, stream=stream)
+                its.append(max(it_s))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_rx = e0.elapsed_time(e1) / ksteps_rx
+            line["relax_solve"] = {"rtol": 1e-10, "n_nodes": gm.n_nodes, "preconditioner": "multigrid",
+                                   "cold": {"iterations_max": max(it_cold), "seconds": t_cold},
+                                   "cold_jacobi": {"iterations_max": max(it_jac), "seconds": t_jac},
+                                   "warm_previous_step": {"iterations_max": max(it_warm), "seconds": t_warm},
+                                   "whole_step": {"value": n / (ms_rx * 1e-3), "unit": UNIT, "ms_per_step": ms_rx,
+                                                  "steps": ksteps_rx, "rtol": 1e-8, "iterations": [min(its), max(its)],
+                                                  "what": "step + statistics + elliptic-relaxation solve (FP32 state)"}}
         del gq
+    if want("iecm"):
         line["iecm"] = run_iecm(pg, torch, stream, gm, cfg, seed, psi, p, max(5, min(args.steps, 20)))
+    if want("projection"):
         line["pressure_projection"] = run_projection(pg, torch, stream, gm, cfg, seed, psi, p,
                                                      max(5, min(args.steps, 20)))
     if not args.no_cpu_baseline and world == 1:
@@ -610,6 +617,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, help="a smaller workload for profiling runs")
     ap.add_argument("--skip-extras", action="store_true", help="only the main line (no FP32-state and solve figures)")
+    ap.add_argument("--extras", default="all",
+                    help="comma-separated subset of complex, fp32, relax, iecm, projection (for profiling runs)")
     ap.add_argument("--mode", default="step", choices=["step", "warmstart"],
                     help="warmstart: the learned warm start experiment instead of the step benchmark")
     args = ap.parse_args()

@@ -26,6 +26,9 @@ CONFIGS = {
     "channel_200x400_ppe100": dict(CHANNEL_COMMON, nx=200, ny=400, ppe=100, steps=1000),
     # the same mesh with fewer particles (3.2M, state 200 MB > L2): profiler captures
     "channel_200x400_ppe20": dict(CHANNEL_COMMON, nx=200, ny=400, ppe=20, steps=1000),
+    # a quarter of the mesh at the measured density (3.9M particles, state 240 MB
+    # > L2): profiler captures of per-element work that depends on the density
+    "channel_100x200_ppe100": dict(CHANNEL_COMMON, nx=100, ny=200, ppe=100, steps=1000),
 }
 
 # Complex geometry: 20 x 5 domain, obstacles 1x1, 1x2, 0.5x1.5 on the bottom

@@ -558,7 +558,7 @@ static pdf_status relax_iterations(pdf_particles* P, int k, cudaStream_t st) {
   const RelaxMesh& R = P->mesh->rx;
   RelaxWork& W = P->rx;
   const dim3 grid(W.nb, 9);
-  if (W.amg) {
+  if (W.multigrid && W.amg) {
     for (int i = 0; i < k; ++i) {
       PDF_KERNEL("k_cg_spmv_rec", st, k_cg_spmv_rec<<<grid, kRBlock, 0, st>>>(R.n_rep, R.nnz, R.rp, R.ci, W.aval,
                                                                                R.wall, W.z, W.p, W.q, W.part, W.scal,
@@ -648,16 +648,11 @@ extern "C" pdf_status pdf_relax_set_solver(pdf_particles* p, int32_t multigrid) 
   RelaxWork& W = p->rx;
   if (W.multigrid == (multigrid == 1)) return PDF_OK;
   PDF_CUDA(cudaDeviceSynchronize());
-  if (W.gx) {
+  if (W.gx) {  // the captured iterations belong to the other preconditioner
     cudaGraphExecDestroy(W.gx);
     W.gx = nullptr;
   }
-  if (W.amg) {
-    relax_amg_free(*W.amg);
-    delete W.amg;
-    W.amg = nullptr;
-  }
-  W.multigrid = multigrid == 1;
+  W.multigrid = multigrid == 1;  // a built hierarchy is kept for a switch back
   return PDF_OK;
 }
 
@@ -696,7 +691,7 @@ extern "C" pdf_status pdf_relax_solve(pdf_particles* p, const pdf_mesh* m, const
                                                                    W.p, W.q, W.part));
   PDF_KERNEL("k_cg_reduce", st, k_cg_reduce<<<27, kRBlock, 0, st>>>(W.part, nb, 3, W.scal));
   PDF_KERNEL("k_cg_start", st, k_cg_start<<<1, 32, 0, st>>>(rtol * rtol, max_it, W.scal, W.ctl));
-  if (W.amg) {
+  if (W.multigrid && W.amg) {
     // the first direction from the multigrid (k_cg_init's Jacobi values
     // replaced)
     s = relax_amg_values(p, st);
