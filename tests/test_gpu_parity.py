@@ -386,3 +386,30 @@ def test_relaxation_multigrid_and_jacobi_agree_on_a_larger_channel():
     assert it_mg * 4 < it_j, (it_mg, it_j)
     scale = out[False][1].abs().amax(dim=1, keepdim=True).clamp_min(1e-300)
     assert float(((out[True][1] - out[False][1]).abs() / scale).max()) < 1e-9
+
+
+@pytest.mark.parametrize("multigrid", [True, False])
+def test_relaxation_solve_on_a_tiny_mesh(multigrid):
+    """An 8 x 6 channel (42 unknowns): the multigrid has no level and solves
+    with the dense inverse of the whole matrix; both preconditioners agree
+    with the oracle's direct solve."""
+    import oracle.relax as OR
+    m = inputs.channel_mesh(8, 6, seed=1)
+    counts = np.full(2 * 7 * 5, 40, dtype=np.int32)
+    gm, M, gp, ost = _pair(m, counts, psi=inputs.scalar_slab(m))
+    p = pg.model_params(closure="glm")
+    pg.pdf_estimate_stats(gp, gm)
+    pg.pdf_step(gp, gm, p, step=0)
+    ns = torch.empty((gm.n_nodes, pg.capi.PDF_NNS), dtype=torch.float64, device="cuda")
+    nd = torch.empty((gm.n_nodes, pg.capi.PDF_NND), dtype=torch.float64, device="cuda")
+    pg.pdf_estimate_stats(gp, gm, node_stats=ns, node_derivs=nd)
+    S, Dv = ns.cpu().numpy(), nd.cpu().numpy()
+    wp = torch.zeros((9, gm.n_nodes), dtype=torch.float64, device="cuda")
+    pg.pdf_relax_set_solver(gp, multigrid)
+    iters, res = pg.pdf_relax_solve(gp, gm, p, wp, rtol=1e-13, max_it=500)
+    assert max(res) <= 1e-13
+    rhs = np.stack([oracle.relax_rhs(S[n], Dv[n]) for n in range(gm.n_nodes)], axis=1)
+    ref = OR.solve(m, S, rhs, p.nu)
+    assert_field_close(wp.cpu().numpy().T, ref.T, "tiny-mesh relaxation solution", rtol=1e-9)
+    if multigrid:   # the exact inverse up to FP32 rounding: a few iterations
+        assert max(iters) <= 12, iters
