@@ -1,8 +1,12 @@
 // Smoothed-aggregation algebraic multigrid for the pressure projection's
-// Poisson matrix (sec. 3.2 solves it by Jacobi-preconditioned conjugate
-// gradients; the matrix depends on the mesh only, so a multigrid hierarchy
-// built once per mesh cuts the iterations from thousands to tens while the
-// solution stays that of the same linear system).
+// Poisson matrix and for the elliptic relaxation (sec. 3.2 solves both by
+// Jacobi-preconditioned conjugate gradients; a multigrid V-cycle as the
+// preconditioner cuts the iterations from hundreds or thousands to tens
+// while the solution stays that of the same linear system).  The Poisson
+// matrix depends on the mesh only: its hierarchy is built once.  The
+// relaxation matrices change with the statistics: the prolongations come
+// once from the stiffness matrix, the level matrices are recomputed on the
+// device at every solve (the second half of this file).
 //
 // Hierarchy (host, FP64, once): plain aggregation of the strongly connected
 // unknowns (|a_ij| >= theta sqrt(a_ii a_jj)), tentative prolongation by the

@@ -1,7 +1,9 @@
 // Elliptic relaxation for the tensor wp_ij (eq. elliptic-relaxation-
 // Lagrangian): (M + K_L) wp = M rhs with linear triangles (sec. 3.2: P1 FEM,
-// Jacobi-preconditioned conjugate gradients, warm start), solved in FP64 for
-// the nine components at once.
+// Jacobi-preconditioned conjugate gradients, warm start), solved by
+// conjugate gradients in FP64 for the nine components at once, with the
+// paper's Jacobi preconditioner or (the default) the multigrid V-cycle of
+// amg.cu.
 //   M_ab   = sum_e A_e (1 + delta_ab) / 12
 //   K_L,ab = sum_e L2_e A_e grad N_a . grad N_b,  L2_e = mean of nodal L^2
 //   L = C_L max(C_xi k^1.5 / eps, C_eta (nu^3 / eps)^1/4) (eq. L), with
