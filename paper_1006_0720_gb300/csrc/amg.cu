@@ -755,7 +755,7 @@ void relax_amg_free(RelaxAmg& G) {
     cudaFree(L.q_row); cudaFree(L.b); cudaFree(L.x); cudaFree(L.z);
     for (int v = 0; v < kRxVar; ++v) {
       cudaFree(L.a_v[v]); cudaFree(L.ap_v[v]); cudaFree(L.q_v[v]); cudaFree(L.s_v[v]);
-      cudaFree(L.a_f[v]); cudaFree(L.q_f[v]); cudaFree(L.s_f[v]); cudaFree(L.w_f[v]);
+      cudaFree(L.a_f[v]); cudaFree(L.q_f[v]); cudaFree(L.s_f[v]); cudaFree(L.w_f[v]); cudaFree(L.w_v[v]);
     }
   }
   cudaFree(G.c_rp); cudaFree(G.c_ci);
@@ -892,7 +892,8 @@ pdf_status relax_amg_setup(int32_t n, const std::vector<int32_t>& rp, const std:
       if ((s = zeros(&L.a_v[v], L.nnz_a)) != PDF_OK || (s = zeros(&L.ap_v[v], nap)) != PDF_OK ||
           (s = zeros(&L.q_v[v], nap)) != PDF_OK || (s = zeros(&L.s_v[v], nap)) != PDF_OK ||
           (s = zeros(&L.a_f[v], L.nnz_a)) != PDF_OK || (s = zeros(&L.q_f[v], nap)) != PDF_OK ||
-          (s = zeros(&L.s_f[v], nap)) != PDF_OK || (s = zeros(&L.w_f[v], (int64_t)na)) != PDF_OK)
+          (s = zeros(&L.s_f[v], nap)) != PDF_OK || (s = zeros(&L.w_f[v], (int64_t)na)) != PDF_OK ||
+          (s = zeros(&L.w_v[v], (int64_t)na)) != PDF_OK)
         break;
     if (s != PDF_OK) break;
     if ((s = zeros(&L.x, 9 * (int64_t)na)) != PDF_OK) break;
@@ -930,17 +931,23 @@ struct RxVals {
   double* s[kRxVar];
   double* an[kRxVar];  // the next level's matrix values
   float *af[kRxVar], *qf[kRxVar], *sf[kRxVar], *wf[kRxVar];
+  double* w[kRxVar];
 };
 
-// (A P)[t] for the four variants (blockIdx.y).
+// (A P)[t] for the four variants (each thread all four: the plan's indices
+// are loaded once).
 __global__ void k_rx_ap(int64_t nnz_ap, const int32_t* __restrict__ off, const int32_t* __restrict__ qa,
                         const double* __restrict__ pv, RxVals V) {
-  const int v = blockIdx.y;
-  const double* a = V.a[v];
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz_ap; t += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int32_t k = off[t]; k < off[t + 1]; ++k) s += a[qa[k]] * pv[k];
-    V.ap[v][t] = s;
+    double s[kRxVar] = {0.0, 0.0, 0.0, 0.0};
+    for (int32_t k = off[t]; k < off[t + 1]; ++k) {
+      const int32_t q = qa[k];
+      const double w = pv[k];
+#pragma unroll
+      for (int v = 0; v < kRxVar; ++v) s[v] += V.a[v][q] * w;
+    }
+#pragma unroll
+    for (int v = 0; v < kRxVar; ++v) V.ap[v][t] = s[v];
   }
 }
 
@@ -976,45 +983,62 @@ __global__ void k_rx_omega(const double* __restrict__ part, int32_t nb, int leve
   omega[v * kRxMaxLv + level] = m > 0.0 ? 4.0 / (3.0 * m) : 0.0;
 }
 
-// Q = P - W (A P), W = omega / a_ii; S = Q^T; the next level's matrix.
-__global__ void k_rx_q(int64_t nnz_ap, const double* __restrict__ pin, const int32_t* __restrict__ row,
-                       const int32_t* __restrict__ dpos, const double* __restrict__ omega, int level, RxVals V) {
-  const int v = blockIdx.y;
-  const double om = omega[v * kRxMaxLv + level];
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz_ap; t += (int64_t)gridDim.x * blockDim.x) {
-    const double q = pin[t] - om / V.a[v][dpos[row[t]]] * V.ap[v][t];
-    V.q[v][t] = q;
-    V.qf[v][t] = (float)q;
+// The smoother weights W = omega / a_ii (FP64 and FP32) and the FP32 copy
+// of the level matrix.
+__global__ void k_rx_cast(int32_t n, int64_t nnz_a, const int32_t* __restrict__ dpos,
+                          const double* __restrict__ omega, int level, RxVals V) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz_a; t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t d = t < n ? dpos[t] : 0;
+#pragma unroll
+    for (int v = 0; v < kRxVar; ++v) {
+      V.af[v][t] = (float)V.a[v][t];
+      if (t < n) {
+        const double w = omega[v * kRxMaxLv + level] / V.a[v][d];
+        V.w[v][t] = w;
+        V.wf[v][t] = (float)w;
+      }
+    }
   }
 }
 
-// FP32 copies of the level matrix and the smoother weights.
-__global__ void k_rx_cast(int32_t n, int64_t nnz_a, const int32_t* __restrict__ dpos,
-                          const double* __restrict__ omega, int level, RxVals V) {
-  const int v = blockIdx.y;
-  const double om = omega[v * kRxMaxLv + level];
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz_a; t += (int64_t)gridDim.x * blockDim.x) {
-    V.af[v][t] = (float)V.a[v][t];
-    if (t < n) V.wf[v][t] = (float)(om / V.a[v][dpos[t]]);
+// Q = P - W (A P); S = Q^T; the next level's matrix.
+__global__ void k_rx_q(int64_t nnz_ap, const double* __restrict__ pin, const int32_t* __restrict__ row, RxVals V) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz_ap; t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = row[t];
+    const double p = pin[t];
+#pragma unroll
+    for (int v = 0; v < kRxVar; ++v) {
+      const double q = p - V.w[v][i] * V.ap[v][t];
+      V.q[v][t] = q;
+      V.qf[v][t] = (float)q;
+    }
   }
 }
 
 __global__ void k_rx_s(int64_t nnz_ap, const int32_t* __restrict__ perm, RxVals V) {
-  const int v = blockIdx.y;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz_ap; t += (int64_t)gridDim.x * blockDim.x) {
-    const double q = V.q[v][perm[t]];
-    V.s[v][t] = q;
-    V.sf[v][t] = (float)q;
+    const int32_t k = perm[t];
+#pragma unroll
+    for (int v = 0; v < kRxVar; ++v) {
+      const double q = V.q[v][k];
+      V.s[v][t] = q;
+      V.sf[v][t] = (float)q;
+    }
   }
 }
 
 __global__ void k_rx_next(int64_t nnz_n, const int32_t* __restrict__ off, const int32_t* __restrict__ tap,
                           const double* __restrict__ pv, RxVals V) {
-  const int v = blockIdx.y;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nnz_n; c += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int32_t k = off[c]; k < off[c + 1]; ++k) s += V.ap[v][tap[k]] * pv[k];
-    V.an[v][c] = s;
+    double s[kRxVar] = {0.0, 0.0, 0.0, 0.0};
+    for (int32_t k = off[c]; k < off[c + 1]; ++k) {
+      const int32_t q = tap[k];
+      const double w = pv[k];
+#pragma unroll
+      for (int v = 0; v < kRxVar; ++v) s[v] += V.ap[v][q] * w;
+    }
+#pragma unroll
+    for (int v = 0; v < kRxVar; ++v) V.an[v][c] = s[v];
   }
 }
 
@@ -1070,25 +1094,23 @@ pdf_status relax_amg_update(RelaxAmg& G, cudaStream_t st) {
       R.qf[v] = V.q_f[v];
       R.sf[v] = V.s_f[v];
       R.wf[v] = V.w_f[v];
+      R.w[v] = V.w_v[v];
     }
     const int64_t nnz_n = l + 1 < L ? G.lv[l + 1].nnz_a : G.nnz_c;
-    PDF_KERNEL("k_rx_ap", st, k_rx_ap<<<dim3(rx_blocks(V.nnz_ap), kRxVar), 256, 0, st>>>(V.nnz_ap, V.ap_off, V.ap_qa,
-                                                                                          V.ap_pv, R));
+    PDF_KERNEL("k_rx_ap", st, k_rx_ap<<<rx_blocks(V.nnz_ap), 256, 0, st>>>(V.nnz_ap, V.ap_off, V.ap_qa, V.ap_pv, R));
     const int gb = std::min<int>(G.gblocks, rx_blocks(V.n));
     PDF_KERNEL("k_rx_gersh", st, k_rx_gersh<<<dim3(gb, kRxVar), 256, 0, st>>>(V.n, V.a_rp, V.a_dpos, R, G.gpart));
     PDF_KERNEL("k_rx_omega", st, k_rx_omega<<<1, 32, 0, st>>>(G.gpart, gb, l, G.omega));
-    PDF_KERNEL("k_rx_q", st, k_rx_q<<<dim3(rx_blocks(V.nnz_ap), kRxVar), 256, 0, st>>>(V.nnz_ap, V.q_pin, V.q_row,
-                                                                                        V.a_dpos, G.omega, l, R));
-    PDF_KERNEL("k_rx_s", st, k_rx_s<<<dim3(rx_blocks(V.nnz_ap), kRxVar), 256, 0, st>>>(V.nnz_ap, V.s_perm, R));
-    PDF_KERNEL("k_rx_cast", st, k_rx_cast<<<dim3(rx_blocks(V.nnz_a), kRxVar), 256, 0, st>>>(V.n, V.nnz_a, V.a_dpos,
-                                                                                             G.omega, l, R));
-    PDF_KERNEL("k_rx_next", st, k_rx_next<<<dim3(rx_blocks(nnz_n), kRxVar), 256, 0, st>>>(nnz_n, V.c_off, V.c_tap,
-                                                                                            V.c_pv, R));
+    PDF_KERNEL("k_rx_cast", st, k_rx_cast<<<rx_blocks(V.nnz_a), 256, 0, st>>>(V.n, V.nnz_a, V.a_dpos, G.omega, l, R));
+    PDF_KERNEL("k_rx_q", st, k_rx_q<<<rx_blocks(V.nnz_ap), 256, 0, st>>>(V.nnz_ap, V.q_pin, V.q_row, R));
+    PDF_KERNEL("k_rx_s", st, k_rx_s<<<rx_blocks(V.nnz_ap), 256, 0, st>>>(V.nnz_ap, V.s_perm, R));
+    PDF_KERNEL("k_rx_next", st, k_rx_next<<<rx_blocks(nnz_n), 256, 0, st>>>(nnz_n, V.c_off, V.c_tap, V.c_pv, R));
   }
   RxVals R;
   for (int v = 0; v < kRxVar; ++v) {
     R.a[v] = nullptr; R.ap[v] = nullptr; R.q[v] = nullptr; R.s[v] = nullptr;
     R.af[v] = R.qf[v] = R.sf[v] = R.wf[v] = nullptr;
+    R.w[v] = nullptr;
     R.an[v] = G.c_v[v];
   }
   PDF_KERNEL("k_rx_coarse_inv", st, k_rx_coarse_inv<<<kRxVar, 256, 0, st>>>(G.nc, G.c_rp, G.c_ci, R, G.cmat, G.cinv));

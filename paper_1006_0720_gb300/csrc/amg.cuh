@@ -79,7 +79,8 @@ struct RxLevel {
   double* q_pin = nullptr;                                       // P at each (A P) position, else 0
   int32_t* q_row = nullptr;
   double *a_v[kRxVar] = {}, *ap_v[kRxVar] = {}, *q_v[kRxVar] = {}, *s_v[kRxVar] = {};
-  // FP32 copies for the cycle: A, Q, S and the smoother weights W = omega / a_ii
+  double* w_v[kRxVar] = {};  // smoother weights W = omega / a_ii
+  // FP32 copies for the cycle: A, Q, S and W
   float *a_f[kRxVar] = {}, *q_f[kRxVar] = {}, *s_f[kRxVar] = {}, *w_f[kRxVar] = {};
   float *b = nullptr, *x = nullptr, *z = nullptr;                // [9][n] (b, z for l > 0)
 };
