@@ -422,6 +422,7 @@ pdf_status host_io_init(pdf_particles* p) {
 
 pdf_status state_in_range(pdf_particles* p, double* const in[7], const int32_t* ie, int64_t beg, int64_t cnt,
                           unsigned long long* bad, int blocks, cudaStream_t st) {
+  p->have_cond = false;  // the conditioned means follow the old slot order
   StateIn S;
   S.n = cnt;
   S.pid0 = beg;

@@ -140,7 +140,14 @@ def test_step_host_rejects_pageable_buffers_and_iecm():
     rc = pg.lib().pdf_step_host(gp.handle, gm.handle, ctypes.byref(p), None, None, 0, *args, None, None)
     assert rc == capi.PDF_EINVAL
     gp.set_iecm((2, 2, 2), 2)
+    pg.pdf_estimate_stats(gp, gm)
     pi = pg.model_params(closure="slm", mix="iecm")
     with pytest.raises(capi.PdfError):
         pg.pdf_step_host(gp, gm, pi, st, step=0)
     pg.pdf_step_host(gp, gm, p, st, step=0)   # the plain model still runs
+    # the conditioned means belonged to the old slot order: IECM waits for
+    # the next statistics
+    with pytest.raises(capi.PdfError):
+        pg.pdf_step(gp, gm, pi, step=1)
+    pg.pdf_estimate_stats(gp, gm)
+    pg.pdf_step(gp, gm, pi, step=1)
