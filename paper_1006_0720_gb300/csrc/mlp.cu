@@ -2,7 +2,7 @@
 // 11 -> 64 -> 64 -> 64 -> 9 with GELU, BF16 weights and activations, FP32
 // accumulation, trained with Adam by the kernels below.  (The paper warm-
 // starts the solve from the previous step, sec. 3.2; the network is an
-// addition and the FP64 solve it seeds stays the judge.)
+// addition; the FP64 solve it seeds still runs to the same residual.)
 //
 // Inputs per node: <U>, <V>, <W>, <uu>, <vv>, <ww>, <uv>, <uw>, <vw>,
 // <omega>, wall distance; outputs wp_ij.  Both standardized with stored
