@@ -231,20 +231,24 @@ pdf_status pdf_particles_set_iecm(pdf_particles* p, int32_t nu, int32_t nv, int3
  * particle-id order (device memory); PDF_ESTATE if there are none. */
 pdf_status pdf_iecm_cond(const pdf_particles* p, double* cond, void* stream);
 
-/* Copies the state, converted to FP64, into caller buffers [n] (any pointer
- * may be NULL).  The buffers may be device or host memory: device buffers
- * are written by conversion kernels on `stream`; host buffers through an
- * FP64 staging buffer of n doubles that the handle allocates on first use
- * and keeps (asynchronous on `stream` for page-locked memory).  elem: host
- * element id of each particle. */
+/* Copies the state, converted to FP64, into caller buffers [n] in
+ * particle-id order (any pointer may be NULL).  When every given buffer is
+ * device, managed or page-locked host memory, one kernel on `stream` writes
+ * them all (page-locked memory through its mapping, over the host link, no
+ * staging; asynchronous); a pageable host buffer goes through an FP64
+ * staging buffer of n doubles that the handle allocates on first use and
+ * keeps.  elem: host element id of each particle. */
 pdf_status pdf_particles_get_state(const pdf_particles* p, double* x, double* y, double* u,
                                    double* v, double* w, double* om, double* ps, int32_t* elem,
                                    void* stream);
-/* Overwrites the state from FP64 caller buffers [n] (all required; device
- * or host memory, host sources through the staging buffer above), rounding
- * to the stored forms.  Synchronizes `stream`.  A position outside
+/* Overwrites the state from FP64 caller buffers [n] in particle-id order
+ * (all required; device or host memory: one kernel reads them all where
+ * they are when none is pageable, else pageable sources go through the
+ * staging buffer above), rounding to the stored forms; the slots then
+ * follow the particle ids.  Synchronizes `stream`.  A position outside
  * |x|, |y| < 64 is PDF_EINVAL (the state is then undefined).  elem must
- * hold each particle's host element (not checked). */
+ * hold each particle's host element (not checked).  Invalidates the IECM
+ * conditioned means until the next pdf_estimate_stats. */
 pdf_status pdf_particles_set_state(pdf_particles* p, const double* x, const double* y,
                                    const double* u, const double* v, const double* w,
                                    const double* om, const double* ps, const int32_t* elem,
