@@ -83,3 +83,47 @@ def test_anisotropic_lengthscale_for_the_wall_normal_component():
     for cxi in (1.0, 2.3):
         L = 0.134 * max(cxi * k ** 1.5 / eps, 72.0 * (nu ** 3 / eps) ** 0.25)
         assert math.isclose(R.lengthscale2(S, nu, np.array([cxi]))[0], L * L, rel_tol=1e-14)
+
+
+def _obstacles():
+    cfg = inputs.OBSTACLES["obstacles_small_mean20"]
+    return inputs.obstacle_mesh(h_min=cfg["h_min"], ratio=cfg["ratio"], growth=cfg["growth"])
+
+
+def test_constant_right_hand_side_on_the_obstacle_mesh():
+    """Graded elements, walls in both orientations and concave corners: with
+    spatially varying statistics (so L^2 and C_xi vary) a constant right-hand
+    side of a diagonal component is still reproduced (the stiffness matrix
+    annihilates constants and the walls are natural boundaries for it), and
+    the off-diagonal components with zero right-hand side stay zero."""
+    m = _obstacles()
+    n = len(m["xy"])
+    rng = np.random.default_rng(7)
+    S = _uniform_stats(n)
+    S[:, 3] = rng.uniform(0.5, 2.0, n)
+    S[:, 5:8] *= rng.uniform(0.5, 2.0, (n, 3))
+    rhs = np.zeros((9, n))
+    rhs[0], rhs[4], rhs[8] = 0.3, -1.1, 2.5
+    wp = R.solve(m, S, rhs, 1e-3)
+    for ij, c in ((0, 0.3), (4, -1.1), (8, 2.5)):
+        assert np.allclose(wp[ij], c, rtol=1e-10), ij
+    assert np.allclose(wp[[1, 2, 3, 5, 6, 7]], 0.0, atol=1e-14)
+
+
+def test_wall_normals_of_the_obstacle_mesh():
+    """Every node's nearest-wall normal is a unit vector; on a wall node it
+    points out of the domain (away from the elements at that node) and the
+    distance is 0."""
+    m = _obstacles()
+    d, nrm = R.wall_normals(m)
+    assert np.allclose(np.hypot(nrm[:, 0], nrm[:, 1]), 1.0, atol=1e-12)
+    assert np.all(d >= 0.0)
+    xy, tri = m["xy"], m["tri"]
+    walls = R.wall_nodes(m, 1)
+    assert len(walls) > 0
+    assert np.allclose(d[walls], 0.0, atol=1e-12)
+    cent = xy[tri].mean(axis=1)
+    for a in walls[:: max(1, len(walls) // 200)]:
+        around = np.nonzero((tri == a).any(axis=1))[0]
+        inward = cent[around].mean(axis=0) - xy[a]
+        assert inward @ nrm[a] < 0.0, a
