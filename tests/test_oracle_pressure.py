@@ -271,3 +271,48 @@ def test_inflow_outflow_condition_gives_the_imposed_drop():
     S[5:8] = 0.1
     cf = oracle.node_coeff(S, np.zeros(10), None, pj, grad_p=np.array([-Pi, 0.0]))
     assert np.isclose(cf[9], Pi) and cf[10] == 0.0
+
+
+def _obstacles():
+    cfg = inputs.OBSTACLES["obstacles_small_mean20"]
+    return inputs.obstacle_mesh(h_min=cfg["h_min"], ratio=cfg["ratio"], growth=cfg["growth"])
+
+
+def test_obstacle_mesh_stiffness_null_space_and_energy():
+    """Graded elements and concave corners: K annihilates the constants and
+    the energy of y is the fluid area (the domain minus the obstacles)."""
+    m = _obstacles()
+    K = OP.stiffness(m)
+    mask = _rep_mask(m)
+    A, _ = OP.shape_gradients(m)
+    assert np.all(A > 0)
+    np.testing.assert_allclose(K @ mask.astype(float), 0.0, atol=1e-10)
+    yr = np.where(mask, m["xy"][:, 1], 0.0)
+    assert np.isclose(yr @ (K @ yr), A.sum(), rtol=1e-12)
+
+
+def test_obstacle_mesh_divergence_load_integrates_the_divergence():
+    m = _obstacles()
+    x, y = m["xy"][:, 0], m["xy"][:, 1]
+    rep = OP._rep(m)
+    ns = np.zeros((len(x), oracle.NNS))
+    ns[:, 0] = 0.0           # <U> = 0 keeps the field single-valued on the twins
+    ns[:, 1] = -0.75 * y     # div = -0.75
+    A, _ = OP.shape_gradients(m)
+    d = OP.divergence_load(m, ns)
+    assert np.isclose(d.sum(), -0.75 * A.sum(), rtol=1e-12)
+    assert np.all(d[rep != np.arange(len(rep))] == 0.0)
+
+
+def test_obstacle_mesh_wall_normals_close_the_boundary():
+    """Divergence theorem: the outward normals times the lengths of all
+    boundary edges sum to zero; the inflow and outflow edges are straight
+    and of equal total length, so the wall edges alone sum to zero."""
+    m = _obstacles()
+    E = OP.wall_edges(m)
+    assert len(E) > 50
+    s = np.zeros(2)
+    for a, b, e, nx, ny, L in E:
+        assert np.isclose(nx * nx + ny * ny, 1.0)
+        s += L * np.array([nx, ny])
+    np.testing.assert_allclose(s, 0.0, atol=1e-10)
