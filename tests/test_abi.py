@@ -34,6 +34,25 @@ def test_library_exports_every_declared_symbol():
         assert name in capi.PROTOTYPES, "binding lacks " + name
 
 
+def test_every_exported_entry_point_is_declared_and_documented():
+    """The reverse direction: each pdf_* symbol the library exports is
+    declared in the header and preceded there by a comment block."""
+    so = pg.lib()._name
+    out = subprocess.check_output(["nm", "-D", "--defined-only", so]).decode()
+    exported = sorted({ln.split()[-1] for ln in out.splitlines() if re.search(r" T pdf_[a-z0-9_]+$", ln)})
+    assert len(exported) > 20
+    declared = set(declared_functions())
+    text = open(HEADER).read()
+    for name in exported:
+        assert name in declared, "undeclared export " + name
+        # the declaration: a line that starts with its return type
+        m = re.search(r"^[A-Za-z_][\w \t\*]*\b" + name + r"\s*\(", text, flags=re.M)
+        assert m, name
+        before = text[:m.start()].rstrip()
+        # it follows a comment, directly or after other declarations of its group
+        assert "*/" in before[max(0, len(before) - 3000):], name
+
+
 def test_struct_layouts_match_the_header(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "%s"\n'
