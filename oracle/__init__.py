@@ -6,8 +6,10 @@ smoke check in ``__graft_entry__`` and the benchmark's CPU-baseline leg may
 import it.  It shares no code with the CUDA library.
 
 The arithmetic lives in ``pdf_oracle.c`` (compiled here with gcc); this module
-only marshals numpy arrays.  Parity of functions without an independent pin
-is stated in their docstrings ("parity unpinned").
+only marshals numpy arrays.  Every function here has pins of its own in
+``tests/test_oracle_*.py``; what no pin fixes is the composition of many
+steps (the paper prints no worked trajectory): parity unpinned there,
+covered by agreement with the GPU and by invariants.
 """
 import ctypes
 import os
