@@ -622,6 +622,10 @@ def main():
     ap.add_argument("--mode", default="step", choices=["step", "warmstart"],
                     help="warmstart: the learned warm start experiment instead of the step benchmark")
     args = ap.parse_args()
+    if args.extras != "all":
+        unknown = set(args.extras.split(",")) - {"complex", "fp32", "relax", "iecm", "projection"}
+        if unknown:
+            ap.error("--extras: unknown %s" % ", ".join(sorted(unknown)))
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "warmstart":
