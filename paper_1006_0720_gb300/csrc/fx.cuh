@@ -140,7 +140,9 @@ FX_HD df fix2df(int64_t X, int F) {
 }
 
 // FP64 bits -> double-float (leading 24 bits and the next 24, truncated);
-// values below 2^-100 in magnitude become 0.
+// values below 2^-100 in magnitude become 0, and a low part that would
+// fall below the FP32 normal range (|x| below about 2^-76) is dropped (an
+// absolute error below 2^-126).
 FX_HD df d2df(uint64_t b) {
   df r = {0.f, 0.f};
   const int e = d_exp(b);
@@ -152,8 +154,9 @@ FX_HD df d2df(uint64_t b) {
   const uint64_t rem = m & ((1ull << 29) - 1);  // weight 2^(e-1075)
   if (rem) {
     const int nr = 64 - FX_CLZ64(rem);          // <= 29
+    const int el = e - 1075 + nr - 1 + 127;     // FP32 exponent field of the low part
     const uint32_t mr = nr > 24 ? (uint32_t)(rem >> (nr - 24)) : (uint32_t)(rem << (24 - nr));
-    r.l = bits_f(sign | ((uint32_t)(e - 1075 + nr - 1 + 127) << 23) | (mr & 0x7FFFFFu));
+    if (el > 0) r.l = bits_f(sign | ((uint32_t)el << 23) | (mr & 0x7FFFFFu));
   }
   return r;
 }

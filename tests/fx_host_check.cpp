@@ -61,6 +61,21 @@ int main(){
     long double sx = (long double)dx.h + (long double)dx.l;
     if (fabsl((long double)back - sx) > fabsl(sx) * ldexpl(1.0L, -52)) { if (bad < 5) printf("df2d %.17g\n", x); bad++; }
   }
+  // FP64 -> double-float near the bottom of its range (2^-101 .. 2^-60),
+  // where the low part leaves the FP32 normal range: a valid pair within
+  // 2^-46 relative or 2^-125 absolute, and 0 below 2^-100
+  for (int i = 0; i < 200000; i++) {
+    const double x = (1.0 + U(g)) * std::pow(2.0, -60 - (int)(g() % 42)) * ((g() & 1) ? 1.0 : -1.0);
+    const fx::df d = fx::d2df(dbits(x));
+    const long double s = (long double)d.h + (long double)d.l;
+    const bool finite = std::isfinite(d.h) && std::isfinite(d.l) && fabsl((long double)d.l) <= fabsl((long double)d.h);
+    const long double tol = fabsl((long double)x) < ldexpl(1.0L, -100) ? fabsl((long double)x)
+                                                                       : fabsl((long double)x) * ldexpl(1.0L, -46) + ldexpl(1.0L, -125);
+    if (!finite || fabsl(s - (long double)x) > tol) {
+      if (bad < 5) printf("d2df small %.17g -> %.9g %.9g\n", x, d.h, d.l);
+      bad++;
+    }
+  }
   printf("bad %d\n", bad);
   return bad != 0;
 }
