@@ -388,14 +388,14 @@ def run_gpu(args):
             wp = torch.zeros((9, gm.n_nodes), dtype=torch.float64, device="cuda")
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            it_cold, _ = pg.pdf_relax_solve(gq, gm, p, wp, rtol=1e-10, max_it=20000)
+            it_cold, _ = pg.pdf_relax_solve_particles(gq, gm, p, wp, rtol=1e-10, max_it=20000)
             t_cold = time.perf_counter() - t0
             # the paper's Jacobi preconditioner on the same cold solve
             wj = torch.zeros_like(wp)
             pg.pdf_relax_set_solver(gq, False)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            it_jac, _ = pg.pdf_relax_solve(gq, gm, p, wj, rtol=1e-10, max_it=20000)
+            it_jac, _ = pg.pdf_relax_solve_particles(gq, gm, p, wj, rtol=1e-10, max_it=20000)
             t_jac = time.perf_counter() - t0
             pg.pdf_relax_set_solver(gq, True)
             del wj
@@ -403,7 +403,7 @@ def run_gpu(args):
             pg.pdf_estimate_stats(gq, gm)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            it_warm, _ = pg.pdf_relax_solve(gq, gm, p, wp, rtol=1e-10, max_it=20000)
+            it_warm, _ = pg.pdf_relax_solve_particles(gq, gm, p, wp, rtol=1e-10, max_it=20000)
             t_warm = time.perf_counter() - t0
             # whole steps with the elliptic relaxation: step (drift from the
             # solved wp) + statistics + the solve warm-started from the previous
@@ -415,7 +415,7 @@ def run_gpu(args):
             for s in range(ksteps_rx):
                 pg.pdf_step(gq, gm, p, wp=wp, step=200 + s, stream=stream)
                 pg.pdf_estimate_stats(gq, gm, stream=stream)
-                it_s, _ = pg.pdf_relax_solve(gq, gm, p, wp, rtol=1e-8, max_it=20000, stream=stream)
+                it_s, _ = pg.pdf_relax_solve_particles(gq, gm, p, wp, rtol=1e-8, max_it=20000, stream=stream)
                 its.append(max(it_s))
             e1.record(stream)
             torch.cuda.synchronize()

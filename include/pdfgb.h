@@ -254,6 +254,40 @@ pdf_status pdf_particles_set_state(pdf_particles* p, const double* x, const doub
                                    const double* om, const double* ps, const int32_t* elem,
                                    void* stream);
 
+/* A particle set in a saved byte form, and back: the stored state exactly
+ * as it sits in the slots (positions in 64-bit fixed point, velocity,
+ * frequency and scalar in the set's storage form, element and particle id
+ * of every slot), the statistics of the last pdf_estimate_stats, the IECM
+ * conditioned means and settings, the projected pressure field <P'> with
+ * its gradient, the reordering interval and counter, and the seed.  A
+ * loaded set continues bit for bit where the saved one stood: the same
+ * pdf_step / pdf_estimate_stats calls give the same results as on the saved
+ * set (the paper's runs restart from saved particle fields; sec. 3.6 and
+ * the setup phase of the solver, not a byte format).  Not saved: the
+ * relaxation and pressure solvers' work spaces (rebuilt at their next
+ * call) and the wall load the current <P'> was projected with (the next
+ * pdf_pressure_project starts it from zero, as after pdf_pressure_field).
+ * Format (version 1, little-endian, 8-byte aligned sections): an 80-byte
+ * header (magic "PDFGBPS\0", version, flags, n, seed, n_tri, n_nodes,
+ * precision, reorder interval and counter, IECM bins and minimum), the slot
+ * arrays x, y (i64), u, v, w, om, ps (8 B per value for PDF_FP64, 4 B for
+ * PDF_FP32_STATE), elem, pid (i32), then the optional sections the flags
+ * name (statistics; IECM means; pressure field), then an FNV-1a checksum
+ * over the preceding 64-bit words.
+ *   size        out: bytes of the saved form of p (pdf_particles_save_size)
+ *   buf, cap    host memory (pageable or page-locked) of at least that size;
+ *               pdf_particles_save synchronizes `stream`
+ * pdf_particles_load checks the magic, version, sizes against the mesh and
+ * the buffer, the checksum, that every element id is in range and that the
+ * slots' particle ids are a permutation (all on the host, before any device
+ * allocation) and returns PDF_EINVAL otherwise; PDF_ENOMEM if the device
+ * arrays cannot be allocated.  The new handle is freed with
+ * pdf_particles_destroy.  Synchronizes `stream`. */
+pdf_status pdf_particles_save_size(const pdf_particles* p, size_t* size);
+pdf_status pdf_particles_save(const pdf_particles* p, void* buf, size_t cap, void* stream);
+pdf_status pdf_particles_load(const pdf_mesh* m, const void* buf, size_t size, void* stream,
+                              pdf_particles** out);
+
 /* ---------------------------------------------------------------- the step */
 
 /* One explicit Euler-Maruyama step of every particle (sec. 2 summary):
@@ -363,20 +397,37 @@ pdf_status pdf_elem_coeff(pdf_particles* p, const pdf_mesh* m, const pdf_model_p
  * V-cycle by default, see pdf_relax_set_solver), all nine components at once:
  *   (M + K_L) wp = M rhs,  M the consistent mass matrix, K_L the stiffness
  *   matrix weighted by the element mean of the nodal L^2.
- * Right-hand side and L from the statistics of the last pdf_estimate_stats.
- * Reflecting walls act as symmetry planes: off-diagonal components are 0 on
+ * Right-hand side and L from the caller's node statistics (the node
+ * derivatives of sec. 3.4 are formed from them, as pdf_estimate_stats
+ * does).  Reflecting walls act as symmetry planes: off-diagonal components are 0 on
  * wall nodes, diagonal components have zero normal derivative.  C_xi =
  * 1 + 1.3 n_i n_i for wp_ii with n the outward normal of the nearest wall
  * edge.  Periodic twin nodes share one unknown.
+ *   node_stats  device (or page-locked host) [n_nodes][PDF_NNS], the node
+ *            layout of pdf_estimate_stats (<U>, <V>, <W>, <omega>, <phi>,
+ *            <uu>, <vv>, <ww>, <uv>, <uw>, <vw>, <phi'^2>); read on `stream`
  *   wp       device [9][n_nodes] (component-major, wp[(3i+j)*n_nodes + n]);
  *            in: the initial guess (warm start), out: the solution
  *   rtol     stop a component when ||r|| <= rtol ||b|| (b = M rhs)
  *   max_it   iteration cap; PDF_ENOTCONV if a component is not converged
  *   iters, rel_res  host [9] or NULL: iterations and final ||r||/||b||
+ * Multigrid-preconditioned (the default of pdf_relax_set_solver).  The work
+ * space (node statistics and derivatives, the CG vectors, the multigrid
+ * hierarchy) belongs to the mesh handle and is allocated at the first call
+ * (the hierarchy's host set-up then takes about 0.3 s for 80,000 nodes);
+ * calls on one mesh must not overlap.  PDF_EINVAL for NULL arguments, rtol
+ * <= 0 or max_it < 0; PDF_ENOMEM if the work space cannot be allocated.
  * The call synchronizes `stream` once per 8 iterations (convergence test). */
-pdf_status pdf_relax_solve(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params, double* wp,
-                           double rtol, int32_t max_it, int32_t* iters, double* rel_res, void* stream);
-/* The preconditioner of pdf_relax_solve: multigrid = 1 (the default) a
+pdf_status pdf_relax_solve(const pdf_mesh* m, const pdf_model_params* params, const double* node_stats,
+                           double* wp, double rtol, int32_t max_it, int32_t* iters, double* rel_res, void* stream);
+/* The same solve for the node statistics of a particle set's last
+ * pdf_estimate_stats (no copy), with the particle handle's own work space
+ * and preconditioner choice (pdf_relax_set_solver).  PDF_ESTATE before the
+ * first pdf_estimate_stats; otherwise as pdf_relax_solve. */
+pdf_status pdf_relax_solve_particles(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,
+                                     double* wp, double rtol, int32_t max_it, int32_t* iters, double* rel_res,
+                                     void* stream);
+/* The preconditioner of pdf_relax_solve_particles: multigrid = 1 (the default) a
  * smoothed-aggregation V-cycle whose prolongations come from the mesh's
  * stiffness matrix (built at the first solve) and whose level matrices are
  * the Galerkin products of the current relaxation matrices (recomputed on
@@ -390,7 +441,7 @@ pdf_status pdf_relax_solve(pdf_particles* p, const pdf_mesh* m, const pdf_model_
  * values. */
 pdf_status pdf_relax_set_solver(pdf_particles* p, int32_t multigrid);
 /* The nodal right-hand side rhs [9][n_nodes] and L^2 [3][n_nodes] (C_xi of
- * wp_11, of wp_22, and 1) that pdf_relax_solve uses (device or page-locked
+ * wp_11, of wp_22, and 1) that pdf_relax_solve_particles uses (device or page-locked
  * host outputs; either may be NULL). */
 pdf_status pdf_relax_rhs(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params, double* rhs,
                          double* L2, void* stream);

@@ -131,9 +131,11 @@ def noslip_values(S, nu, nrm):
     return np.stack([-4.5 * eps * n3[:, i] * n3[:, j] for i in range(3) for j in range(3)])
 
 
-def solve(mesh, S, rhs, nu):
-    """wp [9, n_nodes] from node statistics S [n, 12] and the right-hand side
-    rhs [9, n_nodes] (Eq. elliptic-relaxation-Lagrangian at the nodes)."""
+def _systems(mesh, S, rhs, nu):
+    """The nine linear systems of eq. elliptic-relaxation-Lagrangian over the
+    representative unknowns: for each component (ij, A, b, idx, rep) with
+    the Dirichlet values lifted into b and the fixed rows and columns
+    replaced by the identity."""
     n = len(mesh["xy"])
     rep = _rep(mesh)
     is_rep = rep == np.arange(n)
@@ -141,16 +143,15 @@ def solve(mesh, S, rhs, nu):
     noslip_rep = np.unique(rep[wall_nodes(mesh, 5)])
     free_rep = np.setdiff1d(np.unique(rep[wall_nodes(mesh, 1)]), noslip_rep)
     gval = noslip_values(S, nu, nrm)
-    out = np.zeros((9, n))
     idx = np.nonzero(is_rep)[0]
+    mats = {}  # the three L^2 classes: C_xi of wp_11, of wp_22, and 1
     for ij in range(9):
         i, j = divmod(ij, 3)
-        if i == j:
-            ni = nrm[:, i] if i < 2 else np.zeros(n)
-            cxi = 1.0 + 1.3 * ni * ni
-        else:
-            cxi = np.ones(n)
-        M, K = assemble(mesh, lengthscale2(S, nu, cxi))
+        cls = i if (i == j and i < 2) else 2
+        if cls not in mats:
+            cxi = 1.0 + 1.3 * nrm[:, cls] ** 2 if cls < 2 else np.ones(n)
+            mats[cls] = assemble(mesh, lengthscale2(S, nu, cxi))
+        M, K = mats[cls]
         A = (M + K).tocsr()
         fixed = noslip_rep if i == j else np.union1d(free_rep, noslip_rep)
         g = np.zeros(n)
@@ -161,8 +162,29 @@ def solve(mesh, S, rhs, nu):
         mask[fixed] = 0.0
         D = sp.diags(mask)
         A = (D @ A @ D + sp.diags(1.0 - mask)).tocsr()
-        x = spla.spsolve(A[idx][:, idx].tocsc(), b[idx])
+        yield ij, A[idx][:, idx], b[idx], idx, rep
+
+
+def solve(mesh, S, rhs, nu):
+    """wp [9, n_nodes] from node statistics S [n, 12] and the right-hand side
+    rhs [9, n_nodes] (Eq. elliptic-relaxation-Lagrangian at the nodes)."""
+    n = len(mesh["xy"])
+    out = np.zeros((9, n))
+    for ij, A, b, idx, rep in _systems(mesh, S, rhs, nu):
+        x = spla.spsolve(A.tocsc(), b)
         full = np.zeros(n)
         full[idx] = x
         out[ij] = full[rep]
+    return out
+
+
+def residual(mesh, S, rhs, nu, wp):
+    """Relative residual ||A x - b|| / ||b|| of a given solution wp [9, n]
+    in each of the nine systems that solve() solves (a sparse product, no
+    solve: usable at sizes where the direct solve is slow)."""
+    out = np.zeros(9)
+    for ij, A, b, idx, rep in _systems(mesh, S, rhs, nu):
+        x = np.asarray(wp[ij], dtype=np.float64)[idx]
+        nb = np.linalg.norm(b)
+        out[ij] = np.linalg.norm(A @ x - b) / (nb if nb > 0 else 1.0)
     return out

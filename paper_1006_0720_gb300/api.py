@@ -151,6 +151,31 @@ class Particles:
         args.append(_ptr(st["elem"], torch.int32, self.n))
         check(lib().pdf_particles_set_state(self.handle, *args, _stream(stream)), "pdf_particles_set_state")
 
+    def save(self, stream=None):
+        """The saved byte form of the set (pdf_particles_save) as a numpy uint8 array."""
+        size = ctypes.c_size_t()
+        check(lib().pdf_particles_save_size(self.handle, ctypes.byref(size)), "pdf_particles_save_size")
+        buf = np.empty(size.value, dtype=np.uint8)
+        check(lib().pdf_particles_save(self.handle, ctypes.c_void_p(buf.ctypes.data), size.value, _stream(stream)),
+              "pdf_particles_save")
+        return buf
+
+    @classmethod
+    def load(cls, mesh, buf, stream=None):
+        """A new set from a saved byte form (pdf_particles_load)."""
+        b = np.ascontiguousarray(np.frombuffer(buf, dtype=np.uint8) if not isinstance(buf, np.ndarray) else buf,
+                                 dtype=np.uint8)
+        h = ctypes.c_void_p()
+        check(lib().pdf_particles_load(mesh.handle, ctypes.c_void_p(b.ctypes.data), b.size, _stream(stream),
+                                       ctypes.byref(h)), "pdf_particles_load")
+        self = cls.__new__(cls)
+        self.handle = h
+        self.mesh = mesh
+        n = ctypes.c_int64()
+        check(lib().pdf_particles_count(h, ctypes.byref(n)), "pdf_particles_count")
+        self.n = n.value
+        return self
+
     def close(self):
         if getattr(self, "handle", None):
             lib().pdf_particles_destroy(self.handle)
@@ -165,6 +190,14 @@ class Particles:
 
 def pdf_mesh_create(mesh):
     return Mesh(mesh)
+
+
+def pdf_particles_save(particles, stream=None):
+    return particles.save(stream)
+
+
+def pdf_particles_load(mesh, buf, stream=None):
+    return Particles.load(mesh, buf, stream)
 
 
 def pdf_particles_init(mesh, seed, **kw):
@@ -317,14 +350,27 @@ def pdf_kernel_launches():
     return int(lib().pdf_kernel_launches())
 
 
-def pdf_relax_solve(particles, mesh, params, wp, rtol=1e-10, max_it=1000, stream=None):
-    """Solve for wp in place (device [9, n_nodes] float64, in: initial guess).
+def pdf_relax_solve(mesh, params, node_stats, wp, rtol=1e-10, max_it=1000, stream=None):
+    """Solve for wp in place (device [9, n_nodes] float64, in: initial guess)
+    from caller node statistics (device [n_nodes, 12] float64).
     Returns (iterations [9], relative residuals [9]); raises on PDF_ENOTCONV."""
     it = (ctypes.c_int32 * 9)()
     rr = (ctypes.c_double * 9)()
-    check(lib().pdf_relax_solve(particles.handle, mesh.handle, ctypes.byref(params),
+    check(lib().pdf_relax_solve(mesh.handle, ctypes.byref(params),
+                                _ptr(node_stats, torch.float64, capi.PDF_NNS * mesh.n_nodes),
                                 _ptr(wp, torch.float64, 9 * mesh.n_nodes), float(rtol), int(max_it), it, rr,
                                 _stream(stream)), "pdf_relax_solve")
+    return list(it), list(rr)
+
+
+def pdf_relax_solve_particles(particles, mesh, params, wp, rtol=1e-10, max_it=1000, stream=None):
+    """Solve for wp in place from the particle set's last statistics.
+    Returns (iterations [9], relative residuals [9]); raises on PDF_ENOTCONV."""
+    it = (ctypes.c_int32 * 9)()
+    rr = (ctypes.c_double * 9)()
+    check(lib().pdf_relax_solve_particles(particles.handle, mesh.handle, ctypes.byref(params),
+                                          _ptr(wp, torch.float64, 9 * mesh.n_nodes), float(rtol), int(max_it),
+                                          it, rr, _stream(stream)), "pdf_relax_solve_particles")
     return list(it), list(rr)
 
 

@@ -81,6 +81,9 @@ PROTOTYPES = {
     "pdf_pressure_set_solver": (I32, [V, I32]),
     "pdf_pressure_field": (I32, [V, V, V, V]),
     "pdf_particles_get_state": (I32, [V, V, V, V, V, V, V, V, V, V]),
+    "pdf_particles_save_size": (I32, [V, ctypes.POINTER(ctypes.c_size_t)]),
+    "pdf_particles_save": (I32, [V, V, ctypes.c_size_t, V]),
+    "pdf_particles_load": (I32, [V, V, ctypes.c_size_t, V, ctypes.POINTER(V)]),
     "pdf_particles_set_state": (I32, [V, V, V, V, V, V, V, V, V, V]),
     "pdf_step": (I32, [V, V, ctypes.POINTER(ModelParams), V, V, U32, V, ctypes.POINTER(StepInfo)]),
     "pdf_step_host": (I32, [V, V, ctypes.POINTER(ModelParams), V, V, U32, V, V, V, V, V, V, V, V, V,
@@ -88,7 +91,8 @@ PROTOTYPES = {
     "pdf_estimate_stats": (I32, [V, V, V, V, V, V]),
     "pdf_estimate_stats_noalloc": (I32, [V, V, V, V, V, V]),
     "pdf_elem_coeff": (I32, [V, V, ctypes.POINTER(ModelParams), V, V, V]),
-    "pdf_relax_solve": (I32, [V, V, ctypes.POINTER(ModelParams), V, D, I32, ctypes.POINTER(I32), PD, V]),
+    "pdf_relax_solve": (I32, [V, ctypes.POINTER(ModelParams), V, V, D, I32, ctypes.POINTER(I32), PD, V]),
+    "pdf_relax_solve_particles": (I32, [V, V, ctypes.POINTER(ModelParams), V, D, I32, ctypes.POINTER(I32), PD, V]),
     "pdf_relax_rhs": (I32, [V, V, ctypes.POINTER(ModelParams), V, V, V]),
     "pdf_relax_set_solver": (I32, [V, I32]),
     "pdf_mesh_wall_distance": (I32, [V, PD, PD]),

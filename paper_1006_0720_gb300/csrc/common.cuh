@@ -202,6 +202,9 @@ struct pdf_mesh {
   double period = 0.0;
   std::vector<double> dN;
   std::vector<int8_t> inout;
+  // statistics-only work space of the mesh-level relaxation solve
+  // (pdf_relax_solve), created at its first call
+  mutable pdf_particles* solver = nullptr;
 };
 
 // Internal coefficient row: 32 doubles (256 B) per element.
@@ -292,6 +295,13 @@ struct pdf_particles {
 };
 
 namespace pdfgb {
+// A handle without particles holding node statistics, derivatives and the
+// relaxation work space (the mesh-level solve); the release of any handle
+// and of everything it allocated.
+pdf_status stats_only_handle(const pdf_mesh* m, pdf_particles** out);
+void release_particles(pdf_particles* p);
+// Node derivatives (sec. 3.4) from the node statistics in P->ns.
+pdf_status node_derivs_from_node_stats(pdf_particles* P, cudaStream_t st);
 // Host-resident state transfers of pdf_step_host (particles.cu): the
 // address kernels use for a caller's buffer (NULL for pageable memory);
 // the load of particles [beg, beg + cnt) into slots [beg, beg + cnt) (slot =

@@ -439,6 +439,7 @@ extern "C" pdf_status pdf_mesh_create(const double* node_xy, int32_t n_nodes, co
 
 extern "C" pdf_status pdf_mesh_destroy(pdf_mesh* m) {
   if (!m) return PDF_OK;
+  if (m->solver) release_particles(m->solver);
   free_mesh_dev(m->d);
   free_relax(m->rx);
   delete m;

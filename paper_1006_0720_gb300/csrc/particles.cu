@@ -247,6 +247,24 @@ static void free_particles(pdf_particles* p) {
   delete p;
 }
 
+pdf_status stats_only_handle(const pdf_mesh* m, pdf_particles** out) {
+  *out = nullptr;
+  pdf_particles* P = new pdf_particles();
+  P->mesh = m;
+  const size_t nn = (size_t)m->d.n_nodes, nt = (size_t)m->d.n_tri;
+  cudaError_t e = cudaMalloc((void**)&P->ns, sizeof(double) * nn * PDF_NNS);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&P->nd, sizeof(double) * nn * PDF_NND);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&P->eg, sizeof(double) * nt * 8);
+  if (e != cudaSuccess) {
+    free_particles(P);
+    return fail(PDF_ENOMEM, "pdf_relax_solve: cudaMalloc failed");
+  }
+  *out = P;
+  return PDF_OK;
+}
+
+void release_particles(pdf_particles* p) { free_particles(p); }
+
 static int grid_for(int64_t n, int threads) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -268,6 +286,58 @@ using namespace pdfgb;
       return fail(PDF_ENOMEM, "pdf_particles_init: cudaMalloc failed");              \
     }                                                                                \
   } while (0)
+
+#define SA(ptr, count)                                                              \
+  do {                                                                              \
+    cudaError_t _e = cudaMalloc((void**)&(ptr), (size_t)(count) * sizeof(*(ptr))); \
+    if (_e != cudaSuccess) return fail(PDF_ENOMEM, "particle state: cudaMalloc failed"); \
+  } while (0)
+
+namespace pdfgb {
+// Device arrays of a particle set of P->n particles on P->mesh with
+// P->precision; statistics, counters and the pressure field zeroed.  On
+// failure the caller releases what was allocated (free_particles).
+pdf_status alloc_state(pdf_particles* P, cudaStream_t st) {
+  const int64_t n = P->n;
+  const int32_t precision = P->precision;
+  const int32_t n_tri = P->mesh->d.n_tri, n_nodes = P->mesh->d.n_nodes;
+  SA(P->x, n); SA(P->y, n); SA(P->elem, n); SA(P->pid, n);
+  SA(P->x2, n); SA(P->y2, n); SA(P->pid2, n);
+  if (precision == PDF_FP64) {
+    SA(P->u, n); SA(P->v, n); SA(P->w, n); SA(P->om, n); SA(P->ps, n);
+    SA(P->u2, n); SA(P->v2, n); SA(P->w2, n); SA(P->om2, n); SA(P->ps2, n);
+  } else {
+    SA(P->uf, n); SA(P->vf, n); SA(P->wf, n); SA(P->omf, n); SA(P->psf, n);
+    SA(P->uf2, n); SA(P->vf2, n); SA(P->wf2, n); SA(P->omf2, n); SA(P->psf2, n);
+    SA(P->rows_f32, (int64_t)n_tri * PDFGB_ROW);
+  }
+  SA(P->es, (int64_t)n_tri * PDF_NES);
+  SA(P->ns, (int64_t)n_nodes * PDF_NNS);
+  SA(P->nd, (int64_t)n_nodes * PDF_NND);
+  SA(P->eg, (int64_t)n_tri * 8);
+  SA(P->nc, (int64_t)n_nodes * PDF_NCOEF);
+  SA(P->rows, (int64_t)n_tri * PDFGB_ROW);
+  SA(P->rows_fx, (int64_t)n_tri);
+  SA(P->keys[0], n); SA(P->keys[1], n);
+  SA(P->vals[0], n); SA(P->vals[1], n);
+  P->n_tiles = radix_tiles(n);
+  P->hist_len = P->n_tiles * radix_bins();
+  P->n_scan_blocks = radix_scan_blocks(P->hist_len);
+  SA(P->hist, P->hist_len);
+  SA(P->hist_part, P->n_scan_blocks + 1);
+  SA(P->seg, (int64_t)n_tri + 1);
+  SA(P->counters, 16);
+  SA(P->pres, n_nodes);
+  SA(P->gradP, 2 * (int64_t)n_nodes);
+  cudaError_t e = cudaMemsetAsync(P->ns, 0, sizeof(double) * n_nodes * PDF_NNS, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->counters, 0, sizeof(long long) * 16, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->pres, 0, sizeof(double) * n_nodes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->gradP, 0, sizeof(double) * 2 * n_nodes, st);
+  if (e != cudaSuccess) return cuda_fail(e, "particle state: initial memsets");
+  return PDF_OK;
+}
+}  // namespace pdfgb
+#undef SA
 
 extern "C" pdf_status pdf_particles_init(const pdf_mesh* m, const pdf_init_params* ip,
                                          uint64_t seed, int32_t precision, void* stream,
@@ -292,38 +362,12 @@ extern "C" pdf_status pdf_particles_init(const pdf_mesh* m, const pdf_init_param
   P->n = n;
   P->precision = precision;
   P->seed = seed;
-  TRY_ALLOC(P->x, n); TRY_ALLOC(P->y, n); TRY_ALLOC(P->elem, n); TRY_ALLOC(P->pid, n);
-  TRY_ALLOC(P->x2, n); TRY_ALLOC(P->y2, n); TRY_ALLOC(P->pid2, n);
-  if (precision == PDF_FP64) {
-    TRY_ALLOC(P->u, n); TRY_ALLOC(P->v, n); TRY_ALLOC(P->w, n); TRY_ALLOC(P->om, n); TRY_ALLOC(P->ps, n);
-    TRY_ALLOC(P->u2, n); TRY_ALLOC(P->v2, n); TRY_ALLOC(P->w2, n); TRY_ALLOC(P->om2, n); TRY_ALLOC(P->ps2, n);
-  } else {
-    TRY_ALLOC(P->uf, n); TRY_ALLOC(P->vf, n); TRY_ALLOC(P->wf, n); TRY_ALLOC(P->omf, n); TRY_ALLOC(P->psf, n);
-    TRY_ALLOC(P->uf2, n); TRY_ALLOC(P->vf2, n); TRY_ALLOC(P->wf2, n); TRY_ALLOC(P->omf2, n); TRY_ALLOC(P->psf2, n);
-    TRY_ALLOC(P->rows_f32, (int64_t)n_tri * PDFGB_ROW);
+  pdf_status as = alloc_state(P, st);
+  if (as != PDF_OK) {
+    free_particles(P);
+    return as;
   }
-  TRY_ALLOC(P->es, (int64_t)n_tri * PDF_NES);
-  TRY_ALLOC(P->ns, (int64_t)n_nodes * PDF_NNS);
-  TRY_ALLOC(P->nd, (int64_t)n_nodes * PDF_NND);
-  TRY_ALLOC(P->eg, (int64_t)n_tri * 8);
-  TRY_ALLOC(P->nc, (int64_t)n_nodes * PDF_NCOEF);
-  TRY_ALLOC(P->rows, (int64_t)n_tri * PDFGB_ROW);
-  TRY_ALLOC(P->rows_fx, (int64_t)n_tri);
-  TRY_ALLOC(P->keys[0], n); TRY_ALLOC(P->keys[1], n);
-  TRY_ALLOC(P->vals[0], n); TRY_ALLOC(P->vals[1], n);
-  P->n_tiles = radix_tiles(n);
-  P->hist_len = P->n_tiles * radix_bins();
-  P->n_scan_blocks = radix_scan_blocks(P->hist_len);
-  TRY_ALLOC(P->hist, P->hist_len);
-  TRY_ALLOC(P->hist_part, P->n_scan_blocks + 1);
-  TRY_ALLOC(P->seg, (int64_t)n_tri + 1);
-  TRY_ALLOC(P->counters, 16);
-  TRY_ALLOC(P->pres, n_nodes);
-  TRY_ALLOC(P->gradP, 2 * (int64_t)n_nodes);
-  cudaError_t e = cudaMemsetAsync(P->ns, 0, sizeof(double) * n_nodes * PDF_NNS, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(P->counters, 0, sizeof(long long) * 16, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(P->pres, 0, sizeof(double) * n_nodes, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(P->gradP, 0, sizeof(double) * 2 * n_nodes, st);
+  cudaError_t e = cudaSuccess;
   int64_t* d_off = nullptr;
   double* d_psi = nullptr;
   if (e == cudaSuccess) e = cudaMalloc(&d_off, sizeof(int64_t) * (n_tri + 1));

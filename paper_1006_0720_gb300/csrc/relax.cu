@@ -673,13 +673,12 @@ extern "C" pdf_status pdf_relax_rhs(pdf_particles* p, const pdf_mesh* m, const p
   return PDF_OK;
 }
 
-extern "C" pdf_status pdf_relax_solve(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,
-                                      double* wp, double rtol, int32_t max_it, int32_t* iters, double* rel_res,
-                                      void* stream) {
-  if (!p || !m || p->mesh != m || !params || !wp) return fail(PDF_EINVAL, "pdf_relax_solve: bad arguments");
-  if (!(rtol > 0.0) || max_it < 0) return fail(PDF_EINVAL, "pdf_relax_solve: rtol must be > 0 and max_it >= 0");
-  if (!p->have_stats) return fail(PDF_ESTATE, "pdf_relax_solve: call pdf_estimate_stats first");
-  cudaStream_t st = (cudaStream_t)stream;
+namespace pdfgb {
+
+// The solve for the node statistics and derivatives held in p->ns, p->nd.
+static pdf_status relax_solve(pdf_particles* p, const pdf_model_params* params, double* wp, double rtol,
+                              int32_t max_it, int32_t* iters, double* rel_res, cudaStream_t st) {
+  const pdf_mesh* m = p->mesh;
   pdf_status s = relax_alloc(p);
   if (s != PDF_OK) return s;
   s = relax_prepare(p, params, st);
@@ -745,4 +744,37 @@ extern "C" pdf_status pdf_relax_solve(pdf_particles* p, const pdf_mesh* m, const
   }
   if (n_active > 0) return fail(PDF_ENOTCONV, "pdf_relax_solve: iteration cap reached");
   return PDF_OK;
+}
+
+}  // namespace pdfgb
+
+extern "C" pdf_status pdf_relax_solve_particles(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,
+                                                double* wp, double rtol, int32_t max_it, int32_t* iters,
+                                                double* rel_res, void* stream) {
+  if (!p || !m || p->mesh != m || !params || !wp)
+    return fail(PDF_EINVAL, "pdf_relax_solve_particles: bad arguments");
+  if (!(rtol > 0.0) || max_it < 0)
+    return fail(PDF_EINVAL, "pdf_relax_solve_particles: rtol must be > 0 and max_it >= 0");
+  if (!p->have_stats) return fail(PDF_ESTATE, "pdf_relax_solve_particles: call pdf_estimate_stats first");
+  return relax_solve(p, params, wp, rtol, max_it, iters, rel_res, (cudaStream_t)stream);
+}
+
+extern "C" pdf_status pdf_relax_solve(const pdf_mesh* m, const pdf_model_params* params, const double* node_stats,
+                                      double* wp, double rtol, int32_t max_it, int32_t* iters, double* rel_res,
+                                      void* stream) {
+  if (!m || !params || !node_stats || !wp) return fail(PDF_EINVAL, "pdf_relax_solve: bad arguments");
+  if (!(rtol > 0.0) || max_it < 0) return fail(PDF_EINVAL, "pdf_relax_solve: rtol must be > 0 and max_it >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!m->solver) {
+    pdf_particles* h = nullptr;
+    const pdf_status s = stats_only_handle(m, &h);
+    if (s != PDF_OK) return s;
+    m->solver = h;
+  }
+  pdf_particles* S = m->solver;
+  PDF_CUDA(cudaMemcpyAsync(S->ns, node_stats, sizeof(double) * (size_t)m->d.n_nodes * PDF_NNS, cudaMemcpyDefault, st));
+  const pdf_status s = node_derivs_from_node_stats(S, st);
+  if (s != PDF_OK) return s;
+  S->have_stats = true;
+  return relax_solve(S, params, wp, rtol, max_it, iters, rel_res, st);
 }

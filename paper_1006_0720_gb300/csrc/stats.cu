@@ -186,348 +186,200 @@ __global__ void k_seg_offsets(const int32_t* __restrict__ keys, int64_t n, int32
   }
 }
 
-// A state value as FP64, whatever its stored representation.
-__device__ __forceinline__ double ld64(const double* a, int64_t i) { return __ldg(a + i); }
-__device__ __forceinline__ double ld64(const float* a, int64_t i) { return (double)__ldg(a + i); }
-__device__ __forceinline__ double ld64(const fx::df* a, int64_t i) {
+// A stored state value as a double-float (exact for both storage forms).
+__device__ __forceinline__ fx::df ld_df(const fx::df* a, int64_t i) {
   const float2 v = __ldg(reinterpret_cast<const float2*>(a) + i);
-  return fx::to_double(fx::df{v.x, v.y});
+  return fx::df{v.x, v.y};
+}
+__device__ __forceinline__ fx::df ld_df(const float* a, int64_t i) { return fx::df{__ldg(a + i), 0.f}; }
+
+// Eight lanes per element (four elements per warp), one pass over the
+// element's particles in the grouping's order (sec. 3.3: N, means, central
+// moments with 1/N).  Lane j of a group takes sorted positions j, j + 8, ...
+// (eight consecutive positions per load across the group).
+//  * Means: every value is converted to fixed point q with 48 fraction
+//    bits and summed in 128-bit integers, exact and independent of the
+//    order (a reordering of the state does not change them).
+//  * Central moments: every value enters as its deviation d = x - x_0 from
+//    the element's first particle, a double-float with an absolute error
+//    of about 2^-48 |x| (the resolution of the stored forms); each lane sums
+//    the pairwise products of the deviations in double-float in its order,
+//    the eight lane sums are combined by a fixed butterfly, and
+//      moment_ab = (S_ab - S_a S_b / N) / N,  S_a = sum q_a - N q_a(x_0)
+//    (exact).  The shift keeps the cancellation to a factor of about two
+//    (the deviations are of the size of the fluctuations); the order of the
+//    additions is fixed by the stable grouping.
+//  * An element with a value outside |x| < 2^14 (beyond the exact sums)
+//    takes S_a as double-float sums of the deviations in a second pass and
+//    the mean as x_0 + S_a / N.
+constexpr int kStatLanes = 8;
+constexpr int kFQ = 48;       // fraction bits of the exact sums
+constexpr int kFixLim = 14;   // |value| < 2^14 for the exact sums
+
+__device__ __forceinline__ void acc_xor(fx::acc& a, int o) {
+  const float h = __shfl_xor_sync(0xffffffffu, a.h, o);
+  const float l = __shfl_xor_sync(0xffffffffu, a.l, o);
+  a.add(fx::df{h, l});
 }
 
-// One warp per element: first pass means, second pass central moments
-// (sec. 3.3, 1/N).  Lane j adds sorted positions j, j+32, ...; the lane
-// partials are combined by a fixed butterfly and lane 0's result is used.
-template <typename T>
-__device__ void elem_stats_fp64(int32_t beg, int32_t end, int lane, const int32_t* __restrict__ pid,
-                                const T* __restrict__ u, const T* __restrict__ v,
-                                const T* __restrict__ w, const T* __restrict__ om,
-                                const T* __restrict__ ps, double* __restrict__ out) {
-  const int32_t N = end - beg;
-  double s[5] = {0, 0, 0, 0, 0};
-  for (int32_t i = beg + lane; i < end; i += 32) {
-    const int32_t p = pid ? pid[i] : i;
-    s[0] += ld64(u, p); s[1] += ld64(v, p); s[2] += ld64(w, p); s[3] += ld64(om, p); s[4] += ld64(ps, p);
-  }
-#pragma unroll
-  for (int q = 0; q < 5; ++q) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
-    s[q] = __shfl_sync(0xffffffffu, s[q], 0) / (double)N;
-  }
-  double c[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (int32_t i = beg + lane; i < end; i += 32) {
-    const int32_t p = pid ? pid[i] : i;
-    const double du = ld64(u, p) - s[0], dv = ld64(v, p) - s[1], dw = ld64(w, p) - s[2],
-                 dp = ld64(ps, p) - s[4];
-    c[0] += du * du; c[1] += dv * dv; c[2] += dw * dw;
-    c[3] += du * dv; c[4] += du * dw; c[5] += dv * dw; c[6] += dp * dp;
-  }
-#pragma unroll
-  for (int q = 0; q < 7; ++q) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c[q] += __shfl_xor_sync(0xffffffffu, c[q], o);
-    c[q] = __shfl_sync(0xffffffffu, c[q], 0) / (double)N;
-  }
-  if (lane == 0) {
-    out[0] = (double)N;
-    for (int q = 0; q < 5; ++q) out[1 + q] = s[q];
-    for (int q = 0; q < 7; ++q) out[6 + q] = c[q];
-  }
-}
-
-// Element statistics without FP64 arithmetic per particle (the default):
-// the same two passes as above, but every particle value is decoded into
-// fixed point with 48 fraction bits and the sums are 128-bit integers, so
-// they are exact and independent of the order of the particles.
-//   pass 1: S_i = sum q_i (q = value 2^48)          -> means S_i / N
-//   pass 2: D_i = q_i - M_i with M_i ~ the mean,   -> central moments
-//           (sum D_i D_j - sum D_i sum D_j / N) / N
-// Only the per-element finishing (a few divisions) runs in FP64.  An element
-// with |value| >= 128 (omega >= 2^14) or more than 2^17 particles falls back
-// to the FP64 kernel's arithmetic (exact sums need those bounds).
-constexpr int kFQ = 48;
-
-// Signed 64 x 64 -> 128-bit product from 32 x 32 -> 64-bit pieces (the
-// native 64-bit multiply-high runs on GB300's slow FP64 unit).
-__device__ __forceinline__ void mul_s64(long long a, long long b, unsigned long long& lo, long long& hi) {
-  const bool neg = (a < 0) != (b < 0);
-  const unsigned long long ua = a < 0 ? 0ull - (unsigned long long)a : (unsigned long long)a;
-  const unsigned long long ub = b < 0 ? 0ull - (unsigned long long)b : (unsigned long long)b;
-  const unsigned int a0 = (unsigned int)ua, a1 = (unsigned int)(ua >> 32);
-  const unsigned int b0 = (unsigned int)ub, b1 = (unsigned int)(ub >> 32);
-  const unsigned long long p00 = (unsigned long long)a0 * b0;
-  const unsigned long long p01 = (unsigned long long)a0 * b1;
-  const unsigned long long p10 = (unsigned long long)a1 * b0;
-  const unsigned long long p11 = (unsigned long long)a1 * b1;
-  const unsigned long long mid = (p00 >> 32) + (unsigned int)p01 + (unsigned int)p10;
-  unsigned long long l = (mid << 32) | (unsigned int)p00;
-  unsigned long long h = p11 + (p01 >> 32) + (p10 >> 32) + (mid >> 32);
-  if (neg) {  // two's complement of the 128-bit magnitude
-    l = ~l + 1ull;
-    h = ~h + (l == 0ull ? 1ull : 0ull);
-  }
-  lo = l;
-  hi = (long long)h;
-}
-
-__device__ __forceinline__ void mac128(unsigned long long& lo, long long& hi, long long a, long long b) {
-  unsigned long long pl;
-  long long ph;
-  mul_s64(a, b, pl, ph);
-  const unsigned long long nl = lo + pl;
-  hi = hi + ph + (nl < lo ? 1 : 0);
-  lo = nl;
-}
-
+// 128-bit sums (hi:lo) of fixed-point values.
 __device__ __forceinline__ void add64(unsigned long long& lo, long long& hi, long long v) {
   const unsigned long long nl = lo + (unsigned long long)v;
   hi = hi + (v < 0 ? -1 : 0) + (nl < lo ? 1 : 0);
   lo = nl;
 }
-
-__device__ __forceinline__ void warp_sum128(unsigned long long& lo, long long& hi) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long ol = __shfl_xor_sync(0xffffffffu, lo, o);
-    const long long oh = __shfl_xor_sync(0xffffffffu, hi, o);
-    const unsigned long long nl = lo + ol;
-    hi = hi + oh + (nl < lo ? 1 : 0);
-    lo = nl;
-  }
+__device__ __forceinline__ void add128_xor(unsigned long long& lo, long long& hi, int o) {
+  const unsigned long long ol = __shfl_xor_sync(0xffffffffu, lo, o);
+  const long long oh = __shfl_xor_sync(0xffffffffu, hi, o);
+  const unsigned long long nl = lo + ol;
+  hi = hi + oh + (nl < lo ? 1 : 0);
+  lo = nl;
 }
 
-
-// Value -> fixed point with kFQ fraction bits; `ok` cleared outside |v| < 2^lim.
-__device__ __forceinline__ long long to_fix(const double* a, int64_t i, int lim, bool& ok) {
-  const uint64_t b = (uint64_t)__ldg(reinterpret_cast<const long long*>(a) + i);
-  ok = ok && fx::d_exp(b) <= 1023 + lim;
-  return fx::d2fix(b, kFQ);
-}
-__device__ __forceinline__ long long to_fix(const fx::df* a, int64_t i, int lim, bool& ok) {
-  const float2 v = __ldg(reinterpret_cast<const float2*>(a) + i);
-  ok = ok && (int)((fx::f_bits(v.x) >> 23) & 0xFF) <= 127 + lim;
-  return fx::f2fix(v.x, kFQ) + fx::f2fix(v.y, kFQ);
-}
-__device__ __forceinline__ long long to_fix(const float* a, int64_t i, int lim, bool& ok) {
-  const float f = __ldg(a + i);
-  ok = ok && (int)((fx::f_bits(f) >> 23) & 0xFF) <= 127 + lim;
-  return fx::f2fix(f, kFQ);
-}
-
-// Per-warp shared scratch of the statistics kernel.  Lane partials are
-// stored column-wise so that one lane can add up one quantity over the 32
-// lanes; rows are padded to 33 entries so that the lanes reading different
-// quantities at the same column hit different banks.  Pass 1 also keeps the
-// fixed-point u, v, w, psi of the element's first kStatCache particles for
-// pass 2 (which re-reads only the rest); the double-float partials of pass
-// 2 reuse that storage once it has been read.
-constexpr int kStatCache = 128;
-struct StatScratch {
-  unsigned long long lo[5][33];
-  long long hi[5][33];
-  unsigned long long lo2[5][6];  // second level of the pass-1 sums
-  long long hi2[5][6];
-  union {
-    long long q[4][kStatCache];
-    struct {
-      float h[11][33], l[11][33];
-    } f;
-  };
-};
-constexpr int kStatWarps = 4;  // warps per block (27 KB of shared memory)
-
-__device__ __forceinline__ void prefetch_l2(const void* a) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+// A double-float to fixed point with kFQ fraction bits; `ok` cleared
+// outside |x| < 2^kFixLim.
+__device__ __forceinline__ long long df_fix(fx::df x, bool& ok) {
+  ok = ok && (int)((fx::f_bits(x.h) >> 23) & 0xFF) < 127 + kFixLim;
+  return fx::f2fix(x.h, kFQ) + fx::f2fix(x.l, kFQ);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kStatWarps * 32, 8) k_elem_stats_fx(const int32_t* __restrict__ seg,
+__global__ void __launch_bounds__(256) k_elem_stats_grp(const int32_t* __restrict__ seg,
                                                        const int32_t* __restrict__ pid, int32_t n_tri,
                                                        const T* __restrict__ u, const T* __restrict__ v,
                                                        const T* __restrict__ w, const T* __restrict__ om,
                                                        const T* __restrict__ ps, double* __restrict__ es) {
-  __shared__ StatScratch scratch[kStatWarps];
-  StatScratch& SS = scratch[threadIdx.x >> 5];
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t e = warp; e < n_tri; e += nwarps) {
-    const int32_t beg = seg[e], end = seg[e + 1];
+  const int lane = threadIdx.x & 31, j = lane & (kStatLanes - 1);
+  const int64_t group = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kStatLanes;
+  const int64_t n_groups = ((int64_t)gridDim.x * blockDim.x) / kStatLanes;
+  // every lane of a warp runs the same number of rounds (the butterflies
+  // below need all 32 lanes)
+  const int64_t rounds = (n_tri + n_groups - 1) / n_groups;
+  int64_t e = group;
+  for (int64_t r = 0; r < rounds; ++r, e += n_groups) {
+    const bool live = e < n_tri;
+    const int32_t beg = live ? seg[e] : 0, end = live ? seg[e + 1] : 0;
     const int32_t N = end - beg;
-    double* out = es + e * PDF_NES;
-    if (N == 0) {
-      if (lane < PDF_NES) out[lane] = 0.0;
-      continue;
+    fx::df K[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) K[q] = fx::df{0.f, 0.f};
+    if (N > 0) {
+      const int32_t p0 = pid ? __ldg(pid + beg) : beg;
+      K[0] = ld_df(u, p0); K[1] = ld_df(v, p0); K[2] = ld_df(w, p0); K[3] = ld_df(om, p0); K[4] = ld_df(ps, p0);
     }
-    __syncwarp();  // the previous element's readers of the scratch are done
-    {  // the next element's state on its way to L2: after the periodic
-       // reordering its particles sit close to their grouped positions
-      const int64_t en = e + nwarps;
-      if (en < n_tri) {
-        const int32_t nb = seg[en], ne = seg[en + 1];
-        for (int32_t i = nb + 16 * lane; i < ne; i += 16 * 32) {
-          prefetch_l2(u + i);
-          prefetch_l2(v + i);
-          prefetch_l2(w + i);
-          prefetch_l2(om + i);
-          prefetch_l2(ps + i);
-          if (pid) prefetch_l2(pid + i);
-        }
-      }
-    }
-    // pass 1: exact sums of the fixed-point values
     unsigned long long lo[5] = {0, 0, 0, 0, 0};
     long long hi[5] = {0, 0, 0, 0, 0};
-    bool ok = N <= (1 << 17);
-    for (int32_t i = beg + lane; i < end; i += 32) {
-      const int32_t p = pid ? pid[i] : i;
-      const long long qu = to_fix(u, p, 6, ok), qv = to_fix(v, p, 6, ok), qw = to_fix(w, p, 6, ok);
-      const long long qs = to_fix(ps, p, 6, ok);
-      add64(lo[0], hi[0], qu);
-      add64(lo[1], hi[1], qv);
-      add64(lo[2], hi[2], qw);
-      add64(lo[3], hi[3], to_fix(om, p, 13, ok));
-      add64(lo[4], hi[4], qs);
-      const int32_t slot = i - beg;
-      if (slot < kStatCache) {
-        SS.q[0][slot] = qu;
-        SS.q[1][slot] = qv;
-        SS.q[2][slot] = qw;
-        SS.q[3][slot] = qs;
+    bool ok = true;
+    fx::acc s2[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) s2[q].init(fx::df{0.f, 0.f});
+    for (int32_t i = beg + j; i < end; i += kStatLanes) {
+      const int32_t p = pid ? __ldg(pid + i) : i;
+      const fx::df xu = ld_df(u, p), xv = ld_df(v, p), xw = ld_df(w, p), xm = ld_df(om, p), xp = ld_df(ps, p);
+      add64(lo[0], hi[0], df_fix(xu, ok));
+      add64(lo[1], hi[1], df_fix(xv, ok));
+      add64(lo[2], hi[2], df_fix(xw, ok));
+      add64(lo[3], hi[3], df_fix(xm, ok));
+      add64(lo[4], hi[4], df_fix(xp, ok));
+      // normalized, so that the dropped product of the low parts is below
+      // 2^-48 of the product even when the deviation is far below the value
+      const fx::df du = fx::sub(xu, K[0]);
+      const fx::df dv = fx::sub(xv, K[1]);
+      const fx::df dw = fx::sub(xw, K[2]);
+      const fx::df dp = fx::sub(xp, K[4]);
+      s2[0].add(fx::mul(du, du));
+      s2[1].add(fx::mul(dv, dv));
+      s2[2].add(fx::mul(dw, dw));
+      s2[3].add(fx::mul(du, dv));
+      s2[4].add(fx::mul(du, dw));
+      s2[5].add(fx::mul(dv, dw));
+      s2[6].add(fx::mul(dp, dp));
+    }
+    // butterflies within the group of eight: every lane ends with the totals
+#pragma unroll
+    for (int o = kStatLanes / 2; o > 0; o >>= 1) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) add128_xor(lo[q], hi[q], o);
+#pragma unroll
+      for (int q = 0; q < 7; ++q) acc_xor(s2[q], o);
+      ok = ok && __shfl_xor_sync(0xffffffffu, (int)ok, o);
+    }
+    // S_a: the sums of the deviations, exact from the integer sums, or (an
+    // element beyond the exact range) double-float sums of a second pass
+    fx::df S[5];
+    if (__any_sync(0xffffffffu, !ok)) {
+      fx::acc s1[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) s1[q].init(fx::df{0.f, 0.f});
+      if (!ok) {
+        for (int32_t i = beg + j; i < end; i += kStatLanes) {
+          const int32_t p = pid ? __ldg(pid + i) : i;
+          s1[0].add(fx::sub(ld_df(u, p), K[0]));
+          s1[1].add(fx::sub(ld_df(v, p), K[1]));
+          s1[2].add(fx::sub(ld_df(w, p), K[2]));
+          s1[3].add(fx::sub(ld_df(om, p), K[3]));
+          s1[4].add(fx::sub(ld_df(ps, p), K[4]));
+        }
+      }
+#pragma unroll
+      for (int o = kStatLanes / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) acc_xor(s1[q], o);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) S[q] = s1[q].value();
+    }
+    if (ok) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        bool dummy = true;
+        const long long qk = df_fix(K[q], dummy);
+        // sum q - N q_K in 128 bits: N q_K has |.| < 2^31 2^62
+        unsigned long long pl;
+        long long ph;
+        {
+          const bool neg = qk < 0;
+          const unsigned long long a = neg ? 0ull - (unsigned long long)qk : (unsigned long long)qk;
+          const unsigned long long a0 = a & 0xFFFFFFFFull, a1 = a >> 32;
+          const unsigned long long p0 = a0 * (unsigned long long)N, p1 = a1 * (unsigned long long)N;
+          pl = p0 + (p1 << 32);
+          ph = (long long)((p1 >> 32) + (pl < p0 ? 1ull : 0ull));
+          if (neg) {
+            pl = ~pl + 1ull;
+            ph = ~ph + (pl == 0ull ? 1 : 0);
+          }
+        }
+        const unsigned long long dl = lo[q] - pl;
+        const long long dh = hi[q] - ph - (lo[q] < pl ? 1 : 0);
+        S[q] = fx::i128_to_df(dl, dh, -kFQ);
       }
     }
-    ok = __all_sync(0xffffffffu, ok);
-    if (!ok) {
-      elem_stats_fp64(beg, end, lane, pid, u, v, w, om, ps, out);
+    if (!live) continue;
+    double* out = es + e * PDF_NES;
+    if (N == 0) {
+#pragma unroll
+      for (int q = 0; q < PDF_NES; ++q)
+        if ((q & (kStatLanes - 1)) == j) out[q] = 0.0;
       continue;
     }
+    const fx::df invN = fx::recip_df(N);
+    double val[PDF_NES];
+    val[0] = (double)N;
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-      SS.lo[q][lane] = lo[q];
-      SS.hi[q][lane] = hi[q];
+      const fx::df mean = ok ? fx::df_norm(fx::mul(fx::i128_to_df(lo[q], hi[q], -kFQ), invN))
+                             : fx::add(K[q], fx::df_norm(fx::mul(S[q], invN)));
+      val[1 + q] = __longlong_as_double((long long)fx::df2d(mean));
     }
-    __syncwarp();
-    // exact sums over the lanes in two levels: lane 6q + r (r < 6) adds
-    // columns r, r + 6, ... of quantity q, then lane q adds its six results
-    const fx::df invN = fx::recip_df(N);
-    fx::df mean = fx::df{0.f, 0.f};
-    if (lane < 30) {
-      const int q = lane / 6, r = lane - 6 * (lane / 6);
-      unsigned long long sl = 0;
-      long long sh = 0;
-      for (int j = r; j < 32; j += 6) {
-        const unsigned long long nl = sl + SS.lo[q][j];
-        sh = sh + SS.hi[q][j] + (nl < sl ? 1 : 0);
-        sl = nl;
-      }
-      SS.lo2[q][r] = sl;
-      SS.hi2[q][r] = sh;
-    }
-    __syncwarp();
-    if (lane < 5) {
-      unsigned long long sl = 0;
-      long long sh = 0;
-#pragma unroll
-      for (int r = 0; r < 6; ++r) {
-        const unsigned long long nl = sl + SS.lo2[lane][r];
-        sh = sh + SS.hi2[lane][r] + (nl < sl ? 1 : 0);
-        sl = nl;
-      }
-      mean = fx::df_norm(fx::mul(fx::i128_to_df(sl, sh, -kFQ), invN));
-    }
-    long long M[4];
-    const int idx[4] = {0, 1, 2, 4};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float mh = __shfl_sync(0xffffffffu, mean.h, idx[k]);
-      const float ml = __shfl_sync(0xffffffffu, mean.l, idx[k]);
-      M[k] = fx::f2fix(mh, kFQ) + fx::f2fix(ml, kFQ);
-    }
-    // pass 2: deviations from M (exact), their products and sums in
-    // double-float, each lane's particles in order
-    fx::acc c[7], d[4];
-#pragma unroll
-    for (int q = 0; q < 7; ++q) c[q].init(fx::df{0.f, 0.f});
-#pragma unroll
-    for (int k = 0; k < 4; ++k) d[k].init(fx::df{0.f, 0.f});
-    for (int32_t i = beg + lane; i < end; i += 32) {
-      const int32_t slot = i - beg;
-      long long qu, qv, qw, qs;
-      if (slot < kStatCache) {
-        qu = SS.q[0][slot];
-        qv = SS.q[1][slot];
-        qw = SS.q[2][slot];
-        qs = SS.q[3][slot];
-      } else {
-        const int32_t p = pid ? pid[i] : i;
-        bool dummy = true;
-        qu = to_fix(u, p, 6, dummy);
-        qv = to_fix(v, p, 6, dummy);
-        qw = to_fix(w, p, 6, dummy);
-        qs = to_fix(ps, p, 6, dummy);
-      }
-      const fx::df D0 = fx::fix2df(qu - M[0], kFQ);
-      const fx::df D1 = fx::fix2df(qv - M[1], kFQ);
-      const fx::df D2 = fx::fix2df(qw - M[2], kFQ);
-      const fx::df D3 = fx::fix2df(qs - M[3], kFQ);
-      d[0].add(D0); d[1].add(D1); d[2].add(D2); d[3].add(D3);
-      c[0].add(fx::mul(D0, D0));
-      c[1].add(fx::mul(D1, D1));
-      c[2].add(fx::mul(D2, D2));
-      c[3].add(fx::mul(D0, D1));
-      c[4].add(fx::mul(D0, D2));
-      c[5].add(fx::mul(D1, D2));
-      c[6].add(fx::mul(D3, D3));
-    }
-    __syncwarp();
+    const int pa[7] = {0, 1, 2, 0, 0, 1, 4}, pb[7] = {0, 1, 2, 1, 2, 2, 4};
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
-      SS.f.h[q][lane] = c[q].h;
-      SS.f.l[q][lane] = c[q].l;
+      const fx::df corr = fx::df_norm(fx::mul(fx::df_norm(fx::mul(S[pa[q]], S[pb[q]])), invN));
+      val[6 + q] = __longlong_as_double((long long)fx::df2d(fx::df_norm(fx::mul(fx::sub(s2[q].value(), corr), invN))));
     }
+    // lane j of the group writes outputs j and j + 8
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      SS.f.h[7 + k][lane] = d[k].h;
-      SS.f.l[7 + k][lane] = d[k].l;
-    }
-    __syncwarp();
-    // lanes 2q and 2q + 1 add the first and second 16 lanes' partials of
-    // quantity q in lane order; lane 2q adds the two halves; lane q gets it
-    fx::df half = fx::df{0.f, 0.f};
-    if (lane < 22) {
-      const int q = lane >> 1, j0 = (lane & 1) * 16;
-      fx::acc a;
-      a.init(fx::df{SS.f.h[q][j0], SS.f.l[q][j0]});
-#pragma unroll 5
-      for (int j = j0 + 1; j < j0 + 16; ++j) a.add(fx::df{SS.f.h[q][j], SS.f.l[q][j]});
-      half = fx::df{a.h, a.l};
-    }
-    const float oh = __shfl_down_sync(0xffffffffu, half.h, 1), ol = __shfl_down_sync(0xffffffffu, half.l, 1);
-    fx::acc a2;
-    a2.init(half);
-    a2.add(fx::df{oh, ol});
-    const fx::df pair = a2.value();
-    const float th = __shfl_sync(0xffffffffu, pair.h, (2 * lane) & 31);
-    const float tl = __shfl_sync(0xffffffffu, pair.l, (2 * lane) & 31);
-    const fx::df tot = lane < 11 ? fx::df{th, tl} : fx::df{0.f, 0.f};
-    // output lane: 0 -> N, 1..5 -> means, 6..12 -> central moments
-    // (sum D_a D_b - sum D_a sum D_b / N) / N
-    const int q = lane - 6;
-    const int pa = q == 1 ? 1 : (q == 2 ? 2 : (q == 5 ? 1 : (q == 6 ? 3 : 0)));
-    const int pb = q == 0 ? 0 : (q == 1 ? 1 : (q == 2 ? 2 : (q == 3 ? 1 : (q == 6 ? 3 : 2))));
-    const float s2h = __shfl_sync(0xffffffffu, tot.h, q < 0 ? 0 : q);
-    const float s2l = __shfl_sync(0xffffffffu, tot.l, q < 0 ? 0 : q);
-    const float dah = __shfl_sync(0xffffffffu, tot.h, 7 + pa), dal = __shfl_sync(0xffffffffu, tot.l, 7 + pa);
-    const float dbh = __shfl_sync(0xffffffffu, tot.h, 7 + pb), dbl = __shfl_sync(0xffffffffu, tot.l, 7 + pb);
-    const float mh = __shfl_sync(0xffffffffu, mean.h, (lane + 31) & 31);
-    const float ml = __shfl_sync(0xffffffffu, mean.l, (lane + 31) & 31);
-    fx::df val = fx::df{mh, ml};
-    if (lane >= 6) {
-      const fx::df corr = fx::df_norm(fx::mul(fx::df_norm(fx::mul(fx::df{dah, dal}, fx::df{dbh, dbl})), invN));
-      val = fx::df_norm(fx::mul(fx::sub(fx::df{s2h, s2l}, corr), invN));
-    }
-    if (lane == 0) out[0] = (double)N;
-    else if (lane < PDF_NES) out[lane] = __longlong_as_double((long long)fx::df2d(val));
+    for (int q = 0; q < PDF_NES; ++q)
+      if ((q & (kStatLanes - 1)) == j) out[q] = val[q];
   }
 }
 
@@ -738,12 +590,32 @@ static pdf_status reorder_state(pdf_particles* P, cudaStream_t st) {
 
 pdf_status iecm_cond(pdf_particles* P, const int32_t* seg, const int32_t* order, cudaStream_t st);
 
+// Element statistics of the grouped particles (seg, order) into P->es.
+static pdf_status elem_stats(pdf_particles* P, const int32_t* seg, const int32_t* order, cudaStream_t st) {
+  const MeshDev& M = P->mesh->d;
+  const int nb = blocks_for((int64_t)M.n_tri * kStatLanes, 256);
+  if (P->precision == PDF_FP64)
+    PDF_KERNEL("k_elem_stats", st, k_elem_stats_grp<fx::df><<<nb, 256, 0, st>>>(
+                                       seg, order, M.n_tri, P->u, P->v, P->w, P->om, P->ps, P->es));
+  else
+    PDF_KERNEL("k_elem_stats", st, k_elem_stats_grp<float><<<nb, 256, 0, st>>>(
+                                       seg, order, M.n_tri, P->uf, P->vf, P->wf, P->omf, P->psf, P->es));
+  return PDF_OK;
+}
+
+
+
 // Node statistics and node derivatives from the element statistics P->es
 // (sec. 3.3 second pass, sec. 3.4).
 pdf_status node_stats_from_elements(pdf_particles* P, cudaStream_t st) {
   const MeshDev& M = P->mesh->d;
   PDF_KERNEL("k_node_stats", st, k_node_stats<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(M.nse_off, M.nse, M.n_nodes, P->es, P->ns,
                                                           P->counters + 8););
+  return node_derivs_from_node_stats(P, st);
+}
+
+pdf_status node_derivs_from_node_stats(pdf_particles* P, cudaStream_t st) {
+  const MeshDev& M = P->mesh->d;
   PDF_KERNEL("k_elem_grad1", st, k_elem_grad1<<<blocks_for(M.n_tri, 128), 128, 0, st>>>(M.tri, M.dN, M.n_tri, P->ns, P->eg););
   PDF_KERNEL("k_node_grad1", st, k_node_grad1<<<blocks_for(M.n_nodes, 128), 128, 0, st>>>(M.nse_off, M.nse, M.n_nodes, P->eg, P->nd););
   PDF_KERNEL("k_elem_grad2", st, k_elem_grad2<<<blocks_for(M.n_tri, 128), 128, 0, st>>>(M.tri, M.dN, M.n_tri, P->nd, P->eg););
@@ -760,12 +632,8 @@ pdf_status estimate_stats(pdf_particles* P, cudaStream_t st) {
     if (s != PDF_OK) return s;
     P->since_reorder = 0;
   }
-  if (P->precision == PDF_FP64)
-    PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<fx::df><<<blocks_for((int64_t)M.n_tri * 32, kStatWarps * 32), kStatWarps * 32, 0, st>>>(
-        P->seg, P->sorted_pid, M.n_tri, P->u, P->v, P->w, P->om, P->ps, P->es));
-  else
-    PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<float><<<blocks_for((int64_t)M.n_tri * 32, kStatWarps * 32), kStatWarps * 32, 0, st>>>(
-        P->seg, P->sorted_pid, M.n_tri, P->uf, P->vf, P->wf, P->omf, P->psf, P->es));
+  s = elem_stats(P, P->seg, P->sorted_pid, st);
+  if (s != PDF_OK) return s;
   s = node_stats_from_elements(P, st);
   if (s != PDF_OK) return s;
   P->have_stats = true;
@@ -826,13 +694,9 @@ pdf_status estimate_stats_with_buffers(pdf_particles* P, int32_t* keys_a, int32_
     vin = vout[pass];
   }
   PDF_KERNEL("k_seg_offsets", st, k_seg_offsets<<<blocks_for(n + 1, 256), 256, 0, st>>>(kin, n, M.n_tri, seg));
-  if (P->precision == PDF_FP64)
-    PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<fx::df><<<blocks_for((int64_t)M.n_tri * 32, kStatWarps * 32), kStatWarps * 32, 0, st>>>(
-                                       seg, vin, M.n_tri, P->u, P->v, P->w, P->om, P->ps, P->es));
-  else
-    PDF_KERNEL("k_elem_stats", st, k_elem_stats_fx<float><<<blocks_for((int64_t)M.n_tri * 32, kStatWarps * 32), kStatWarps * 32, 0, st>>>(
-                                       seg, vin, M.n_tri, P->uf, P->vf, P->wf, P->omf, P->psf, P->es));
-  pdf_status s = node_stats_from_elements(P, st);
+  pdf_status s = elem_stats(P, seg, vin, st);
+  if (s != PDF_OK) return s;
+  s = node_stats_from_elements(P, st);
   if (s != PDF_OK) return s;
   P->have_stats = true;
   return iecm_cond(P, seg, vin, st);

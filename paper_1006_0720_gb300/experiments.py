@@ -36,7 +36,7 @@ def advance(gm, gp, p, wp, steps, step0=0, rtol=1e-10, max_it=5000):
     start from the previous solution).  Returns per-step iteration counts."""
     its = []
     for s in range(steps):
-        it, _ = A.pdf_relax_solve(gp, gm, p, wp, rtol=rtol, max_it=max_it)
+        it, _ = A.pdf_relax_solve_particles(gp, gm, p, wp, rtol=rtol, max_it=max_it)
         its.append(max(it))
         A.pdf_step(gp, gm, p, wp=wp, step=step0 + s)
         A.pdf_estimate_stats(gp, gm)
@@ -47,7 +47,7 @@ def collect_solves(n_solves, workload="channel_20x40_ppe50", seed=1, rtol=1e-10)
     cfg, gm, gp, p, wp = setup(workload, seed)
     Xs, Ys = [], []
     for s in range(n_solves):
-        A.pdf_relax_solve(gp, gm, p, wp, rtol=rtol, max_it=5000)
+        A.pdf_relax_solve_particles(gp, gm, p, wp, rtol=rtol, max_it=5000)
         X, Y = A.pdf_mlp_features(gp, gm, wp)
         Xs.append(X)
         Ys.append(Y)
@@ -97,7 +97,7 @@ def _compare(gm, gp, p, wp_prev, net, rtol, max_it):
         t0 = time.perf_counter()
         if name == "mlp":
             net.guess(gp, gm, w)
-        it, res = A.pdf_relax_solve(gp, gm, p, w, rtol=rtol, max_it=max_it)
+        it, res = A.pdf_relax_solve_particles(gp, gm, p, w, rtol=rtol, max_it=max_it)
         torch.cuda.synchronize()
         out[name] = {"iterations_max": max(it), "iterations_total": sum(it),
                      "seconds": time.perf_counter() - t0, "rel_res_max": max(res)}

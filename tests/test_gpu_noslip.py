@@ -99,7 +99,7 @@ def test_noslip_fp32_state_invariants():
 
 @pytest.mark.parametrize("multigrid", [True, False])
 def test_noslip_relaxation_solve_matches_the_oracle(multigrid):
-    """pdf_relax_solve on the no-slip channel after a few steps: every
+    """pdf_relax_solve_particles on the no-slip channel after a few steps: every
     component holds -4.5 eps n_i n_j on the no-slip nodes and the solution
     agrees with the oracle's sparse direct solve (each side with its own
     statistics)."""
@@ -123,7 +123,7 @@ def test_noslip_relaxation_solve_matches_the_oracle(multigrid):
         pg.pdf_estimate_stats(gp, gm)
     wp = torch.zeros((9, gm.n_nodes), dtype=torch.float64, device="cuda")
     pg.pdf_relax_set_solver(gp, multigrid)
-    iters, res = pg.pdf_relax_solve(gp, gm, p, wp, rtol=1e-13, max_it=4000)
+    iters, res = pg.pdf_relax_solve_particles(gp, gm, p, wp, rtol=1e-13, max_it=4000)
     got = wp.cpu().numpy()
     rhs = np.stack([oracle.relax_rhs(ns[n], nd[n]) for n in range(gm.n_nodes)], axis=1)
     ref = OR.solve(m, ns, rhs, p.nu)

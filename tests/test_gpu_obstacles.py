@@ -111,7 +111,7 @@ def test_obstacles_relaxation_solve_matches_the_oracle(multigrid):
     S, Dv = ns.cpu().numpy(), nd.cpu().numpy()
     wp = torch.zeros((9, gm.n_nodes), dtype=torch.float64, device="cuda")
     pg.pdf_relax_set_solver(gp, multigrid)
-    iters, res = pg.pdf_relax_solve(gp, gm, p, wp, rtol=1e-13, max_it=6000)
+    iters, res = pg.pdf_relax_solve_particles(gp, gm, p, wp, rtol=1e-13, max_it=6000)
     assert max(res) <= 1e-13
     rhs = np.stack([oracle.relax_rhs(S[n], Dv[n]) for n in range(gm.n_nodes)], axis=1)
     ref = OR.solve(m, S, rhs, p.nu)

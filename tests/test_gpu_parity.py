@@ -324,7 +324,7 @@ def test_fallbacks_for_values_outside_the_fixed_point_ranges():
 
 @pytest.mark.parametrize("multigrid", [True, False])
 def test_relaxation_solve_matches_the_oracle(multigrid):
-    """pdf_relax_solve on the small channel after a few steps: the nodal
+    """pdf_relax_solve_particles on the small channel after a few steps: the nodal
     right-hand side, the L^2 fields and the converged solution agree with the
     oracle's assembly and sparse direct solve (multigrid and Jacobi
     preconditioners)."""
@@ -352,12 +352,12 @@ def test_relaxation_solve_matches_the_oracle(multigrid):
         assert_field_close(L2[c].cpu().numpy(), OR.lengthscale2(S, p.nu, cxi), "L^2 class %d" % c)
     wp = torch.zeros((9, gm.n_nodes), dtype=torch.float64, device="cuda")
     pg.pdf_relax_set_solver(gp, multigrid)
-    iters, res = pg.pdf_relax_solve(gp, gm, p, wp, rtol=1e-13, max_it=2000)
+    iters, res = pg.pdf_relax_solve_particles(gp, gm, p, wp, rtol=1e-13, max_it=2000)
     ref = OR.solve(m, S, ref_rhs, p.nu)
     assert_field_close(wp.cpu().numpy().T, ref.T, "relaxation solution", rtol=1e-9)
     assert max(res) <= 1e-13
     # warm start from the solution: converged at once
-    iters2, _ = pg.pdf_relax_solve(gp, gm, p, wp, rtol=1e-10, max_it=2000)
+    iters2, _ = pg.pdf_relax_solve_particles(gp, gm, p, wp, rtol=1e-10, max_it=2000)
     assert max(iters2) <= 1
 
 
@@ -376,7 +376,7 @@ def test_relaxation_multigrid_and_jacobi_agree_on_a_larger_channel():
     for mg in (True, False, True):
         wp = torch.zeros((9, gm.n_nodes), dtype=torch.float64, device="cuda")
         pg.pdf_relax_set_solver(gp, mg)
-        iters, res = pg.pdf_relax_solve(gp, gm, p, wp, rtol=1e-12, max_it=20000)
+        iters, res = pg.pdf_relax_solve_particles(gp, gm, p, wp, rtol=1e-12, max_it=20000)
         assert max(res) <= 1e-12
         if mg in out:
             assert list(iters) == out[mg][0]
@@ -406,10 +406,43 @@ def test_relaxation_solve_on_a_tiny_mesh(multigrid):
     S, Dv = ns.cpu().numpy(), nd.cpu().numpy()
     wp = torch.zeros((9, gm.n_nodes), dtype=torch.float64, device="cuda")
     pg.pdf_relax_set_solver(gp, multigrid)
-    iters, res = pg.pdf_relax_solve(gp, gm, p, wp, rtol=1e-13, max_it=500)
+    iters, res = pg.pdf_relax_solve_particles(gp, gm, p, wp, rtol=1e-13, max_it=500)
     assert max(res) <= 1e-13
     rhs = np.stack([oracle.relax_rhs(S[n], Dv[n]) for n in range(gm.n_nodes)], axis=1)
     ref = OR.solve(m, S, rhs, p.nu)
     assert_field_close(wp.cpu().numpy().T, ref.T, "tiny-mesh relaxation solution", rtol=1e-9)
     if multigrid:   # the exact inverse up to FP32 rounding: a few iterations
         assert max(iters) <= 12, iters
+
+
+@pytest.mark.parametrize("nx,ny,ppe", [(20, 40, 50), (200, 400, 6)])
+def test_relaxation_solve_of_the_oracle_statistics(nx, ny, ppe):
+    """pdf_relax_solve, the mesh-level call: node statistics computed by the
+    oracle go in through the C-ABI; the library forms the node derivatives,
+    the right-hand side and L^2 itself and solves (multigrid PCG to 1e-13).
+    On the small channel the solution matches the oracle's sparse direct
+    solve; on the 80,000-node channel of the benchmark mesh (where that
+    solve is slow) the solution's residual in each of the oracle's nine
+    assembled systems is below 1e-12.  A second call warm-started from the
+    solution stops at once."""
+    import oracle.relax as OR
+    m = inputs.channel_mesh(nx, ny, seed=1)
+    M = oracle.Mesh(m)
+    counts = np.full(M.n_tri, ppe, dtype=np.int32)
+    ost = oracle.init(M, counts, 3, u_sigma=0.1, elem_psi0=inputs.scalar_slab(m))
+    es, ns, nd, _ = oracle.statistics(M, ost)
+    gm = pg.Mesh(m)
+    p = pg.model_params(closure="glm")
+    S = torch.from_numpy(np.ascontiguousarray(ns)).cuda()
+    wp = torch.zeros((9, gm.n_nodes), dtype=torch.float64, device="cuda")
+    iters, res = pg.pdf_relax_solve(gm, p, S, wp, rtol=1e-13, max_it=4000)
+    assert max(res) <= 1e-13
+    rhs = np.stack([oracle.relax_rhs(ns[n], nd[n]) for n in range(gm.n_nodes)], axis=1)
+    x = wp.cpu().numpy()
+    if gm.n_nodes <= 5000:
+        ref = OR.solve(m, ns, rhs, p.nu)
+        assert_field_close(x.T, ref.T, "mesh-level relaxation solution", rtol=1e-9)
+    r = OR.residual(m, ns, rhs, p.nu, x)
+    assert r.max() < 1e-12, r
+    iters2, _ = pg.pdf_relax_solve(gm, p, S, wp, rtol=1e-10, max_it=4000)
+    assert max(iters2) <= 1
