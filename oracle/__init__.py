@@ -45,8 +45,11 @@ def build(force=False):
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
     tmp = _LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC]
+    # OpenMP only spreads the particle loop of or_step_threads over threads;
+    # without it that loop runs on one thread
+    if subprocess.call(base + ["-fopenmp", "-lm"], stderr=subprocess.DEVNULL) != 0:
+        subprocess.check_call(base + ["-lm"])
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -106,6 +109,8 @@ def lib():
             L.or_elem_coeff.argtypes = [ctypes.c_void_p, PD, PD, PD, ctypes.POINTER(_Params), PD, PD]
             L.or_step.argtypes = [ctypes.c_void_p, ctypes.c_long, PD, ctypes.POINTER(_Params),
                                   ctypes.c_uint64, U32, PD, PD, PD, PD, PD, PD, PD, PI, PI, PL, PI, PD, PD]
+            L.or_step_threads.argtypes = L.or_step.argtypes + [I]
+            L.or_step_threads.restype = I
             L.or_noslip_omega.argtypes = [ctypes.c_void_p, PD, PD]
             L.or_mesh_noslip.argtypes = [ctypes.c_void_p, PI, PD]
             L.or_iecm_cond.argtypes = [I, ctypes.c_long, PI, PD, PD, PD, PD, PI, I, I, I, I, PD]
@@ -350,6 +355,27 @@ def step(mesh, rows, params, seed, step_no, st, pid=None, cond=None, omega_wall=
     names = ["walk_steps", "reflections", "crossings_periodic", "fallbacks", "brute", "lost",
              "omega_reflections", "near_face"]
     return dict(zip(names, counters.tolist())), status
+
+
+def step_threads(mesh, rows, params, seed, step_no, st, threads=0, pid=None, cond=None, omega_wall=None):
+    """step() with its particle loop over `threads` host threads (0: all;
+    OpenMP).  Bit for bit the results of step().  Returns (counters, status,
+    threads used)."""
+    n = len(st["x"])
+    pid = None if pid is None else np.ascontiguousarray(pid, dtype=np.int32)
+    cond = None if cond is None else np.ascontiguousarray(cond, dtype=np.float64)
+    omega_wall = None if omega_wall is None else np.ascontiguousarray(omega_wall, dtype=np.float64)
+    rows = np.ascontiguousarray(rows, dtype=np.float64)
+    status = np.zeros(n, dtype=np.int32)
+    counters = np.zeros(8, dtype=np.int64)
+    used = lib().or_step_threads(mesh._h, n, _p(rows, D), ctypes.byref(params), int(seed), int(step_no),
+                                 *[_p(st[k], D) for k in STATE_KEYS], _p(st["elem"], I), _p(status, I),
+                                 counters.ctypes.data_as(PL), None if pid is None else _p(pid, I),
+                                 None if cond is None else _p(cond, D),
+                                 None if omega_wall is None else _p(omega_wall, D), int(threads))
+    names = ["walk_steps", "reflections", "crossings_periodic", "fallbacks", "brute", "lost",
+             "omega_reflections", "near_face"]
+    return dict(zip(names, counters.tolist())), status, int(used)
 
 
 def statistics(mesh, st, prev_ns=None):

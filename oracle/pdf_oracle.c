@@ -16,6 +16,9 @@
  */
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -921,6 +924,100 @@ void or_elem_coeff(const or_mesh* m, const double* ns, const double* nd, const d
  * pid: the particle id of each entry (NULL: the index), for stepping a
  * subset of particles.  cond: the velocity-conditioned scalar mean of each
  * entry for eq. IECM (NULL: eq. IEM with the element mean). */
+/* One particle of or_step (the body of its particle loop); the tracking
+ * counts are added to counters[0..7]. */
+static void or_step_one(const or_mesh* m, long p, const double* rows, const or_params* P, uint64_t seed,
+                        uint32_t step, double sdt, double s2nu, double* x, double* y, double* u, double* v,
+                        double* w, double* om, double* ps, int* elem, int* status_out, long* counters,
+                        const int* pid, const double* cond, const double* omega_wall) {
+  int e = elem[p];
+  const double* c = rows + OR_NCOEF * e;
+  float g[8];
+  uint32_t id = pid ? (uint32_t)pid[p] : (uint32_t)p;
+  or_gauss4(seed, id, step, 0u, OR_PURPOSE_STEP, &g[0]);
+  or_gauss4(seed, id, step, 1u, OR_PURPOSE_STEP, &g[4]);
+  double dWx = sdt * (double)g[0], dWy = sdt * (double)g[1];
+  double dWp[3] = {sdt * (double)g[2], sdt * (double)g[3], sdt * (double)g[4]};
+  double dWo = sdt * (double)g[5];
+  double U[3] = {u[p], v[p], w[p]};
+  double Un[3];
+  for (int i = 0; i < 3; ++i) {
+    double gl = 0.0;
+    for (int j = 0; j < 3; ++j) gl += c[12 + 3 * i + j] * (U[j] - c[j]);
+    Un[i] = U[i] + c[9 + i] * P->dt
+          + s2nu * (c[3 + 2 * i] * dWx + c[4 + 2 * i] * dWy)
+          + gl * P->dt
+          + c[21] * dWp[i];
+  }
+  double xn = x[p] + U[0] * P->dt + s2nu * dWx;
+  double yn = y[p] + U[1] * P->dt + s2nu * dWy;
+  double o = om[p], mo = c[22];
+  double on = o - OR_C3 * mo * (o - mo) * P->dt - c[23] * mo * o * P->dt
+            + sqrt(2.0 * OR_C3 * OR_C4 * mo * mo * (o > 0.0 ? o : 0.0)) * dWo;
+  if (on < 0.0) { on = -on; counters[6]++; }
+  /* eq. IEM with the element mean, or eq. IECM with the velocity-conditioned
+   * mean of the particle's bin when cond is given */
+  double pn = ps[p] - (ps[p] - (cond ? cond[p] : c[24])) * P->dt * c[25];
+  /* distances from the no-slip wall before and after the move (sec.
+   * no-slip wall-boundary conditions), for particles in elements with a
+   * node on such a wall */
+  const int near = m->nsw_flag[e];
+  double dn = 0.0, d1 = 0.0;
+  if (near) {
+    const double* L = m->nsw + 4 * e;
+    dn = (x[p] - L[0]) * L[2] + (y[p] - L[1]) * L[3];
+    d1 = (xn - L[0]) * L[2] + (yn - L[1]) * L[3];
+  }
+  or_track_info ti;
+  int en = or_track(m, e, &xn, &yn, &Un[0], &Un[1], &ti);
+  /* wall condition: trajectory (a), behind the wall after the move (the
+   * walk reflected the position at a no-slip edge, or d^{n+1} < 0), or
+   * trajectory (b), eta < f_w = exp(-d^n d^{n+1} / (nu dt)) (eq. fw,
+   * eq. exp-wall-condition); eta is the third word of the step's second
+   * random block.  Then U = 0 and omega from a Gamma distribution with
+   * the mean of eq. frequency-wallstats and variance C4 <omega>^2 (shape
+   * 1/C4 = 4): -<omega>/4 times the sum of the logarithms of the four
+   * uniforms of the step's third block. */
+  int wall = (ti.status & OR_TRK_NOSLIP) != 0;
+  if (near && !wall) {
+    if (d1 < 0.0) {
+      wall = 1;
+    } else {
+      uint32_t ctr[4] = {id, step, 1u, OR_PURPOSE_STEP}, key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)}, out[4];
+      or_philox(ctr, key, out);
+      const double eta = (double)or_u01(out[2]);
+      if (eta < exp(-dn * d1 / (P->nu * P->dt))) wall = 1;
+    }
+  }
+  if (wall) {
+    Un[0] = Un[1] = Un[2] = 0.0;
+    uint32_t ctr[4] = {id, step, 2u, OR_PURPOSE_STEP}, key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)}, out[4];
+    or_philox(ctr, key, out);
+    float lsum = or_logf(or_u01(out[0])) + or_logf(or_u01(out[1]));
+    lsum = lsum + or_logf(or_u01(out[2]));
+    lsum = lsum + or_logf(or_u01(out[3]));
+    const double mw = omega_wall ? omega_wall[e] : mo;
+    on = -0.25 * (mw > 0.0 ? mw : mo) * (double)lsum;
+    ti.status |= OR_TRK_NOSLIP;
+  }
+  counters[0] += ti.walk_steps;
+  counters[1] += ti.reflections;
+  counters[2] += ti.crossings_periodic;
+  if (ti.status & OR_TRK_FALLBACK) counters[3]++;
+  if (ti.status & OR_TRK_BRUTE) counters[4]++;
+  if (ti.status & OR_TRK_LOST) counters[5]++;
+  if (!(ti.status & OR_TRK_LOST) && ti.min_rel < 1e-12) counters[7]++;
+  if (status_out) status_out[p] = ti.status | ((ti.min_rel < 1e-12) ? 256 : 0);
+  /* READING: fluid re-entering through the inflow carries no scalar */
+  if (ti.status & OR_TRK_REINJECT) pn = 0.0;
+  /* the concentrated source (ch. 4): particles inside it get psi = 1 */
+  if (P->src_r > 0.0 && (xn - P->src_x) * (xn - P->src_x) + (yn - P->src_y) * (yn - P->src_y) <= P->src_r * P->src_r)
+    pn = 1.0;
+  x[p] = xn; y[p] = yn; u[p] = Un[0]; v[p] = Un[1]; w[p] = Un[2];
+  om[p] = on; ps[p] = pn;
+  if (!(ti.status & OR_TRK_LOST)) elem[p] = en;
+}
+
 void or_step(const or_mesh* m, long n_p, const double* rows, const or_params* P, uint64_t seed,
              uint32_t step, double* x, double* y, double* u, double* v, double* w, double* om,
              double* ps, int* elem, int* status_out, long* counters, const int* pid, const double* cond,
@@ -928,94 +1025,47 @@ void or_step(const or_mesh* m, long n_p, const double* rows, const or_params* P,
   double sdt = sqrt(P->dt);
   double s2nu = (P->closure == OR_CLOSURE_SLM) ? 0.0 : sqrt(2.0 * P->nu);
   for (int i = 0; i < 8; ++i) counters[i] = 0;
-  for (long p = 0; p < n_p; ++p) {
-    int e = elem[p];
-    const double* c = rows + OR_NCOEF * e;
-    float g[8];
-    uint32_t id = pid ? (uint32_t)pid[p] : (uint32_t)p;
-    or_gauss4(seed, id, step, 0u, OR_PURPOSE_STEP, &g[0]);
-    or_gauss4(seed, id, step, 1u, OR_PURPOSE_STEP, &g[4]);
-    double dWx = sdt * (double)g[0], dWy = sdt * (double)g[1];
-    double dWp[3] = {sdt * (double)g[2], sdt * (double)g[3], sdt * (double)g[4]};
-    double dWo = sdt * (double)g[5];
-    double U[3] = {u[p], v[p], w[p]};
-    double Un[3];
-    for (int i = 0; i < 3; ++i) {
-      double gl = 0.0;
-      for (int j = 0; j < 3; ++j) gl += c[12 + 3 * i + j] * (U[j] - c[j]);
-      Un[i] = U[i] + c[9 + i] * P->dt
-            + s2nu * (c[3 + 2 * i] * dWx + c[4 + 2 * i] * dWy)
-            + gl * P->dt
-            + c[21] * dWp[i];
+  for (long p = 0; p < n_p; ++p)
+    or_step_one(m, p, rows, P, seed, step, sdt, s2nu, x, y, u, v, w, om, ps, elem, status_out, counters, pid,
+                cond, omega_wall);
+}
+
+/* The same particle loop spread over host threads: the particle-based loop
+ * of the paper's loop design (ii) (table of loop designs, sec. 3.9) under
+ * OpenMP.  Within a step every particle reads only its own state and its
+ * element's coefficients, so the results equal or_step's bit for bit; the
+ * threads' counts are summed at the end.  nthreads <= 0: all available.
+ * Returns the number of threads used (1 without OpenMP). */
+int or_step_threads(const or_mesh* m, long n_p, const double* rows, const or_params* P, uint64_t seed,
+                    uint32_t step, double* x, double* y, double* u, double* v, double* w, double* om,
+                    double* ps, int* elem, int* status_out, long* counters, const int* pid, const double* cond,
+                    const double* omega_wall, int nthreads) {
+  double sdt = sqrt(P->dt);
+  double s2nu = (P->closure == OR_CLOSURE_SLM) ? 0.0 : sqrt(2.0 * P->nu);
+  for (int i = 0; i < 8; ++i) counters[i] = 0;
+  int used = 1;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel num_threads(nthreads)
+  {
+    long c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma omp for schedule(static)
+    for (long p = 0; p < n_p; ++p)
+      or_step_one(m, p, rows, P, seed, step, sdt, s2nu, x, y, u, v, w, om, ps, elem, status_out, c, pid, cond,
+                  omega_wall);
+#pragma omp critical
+    {
+      for (int i = 0; i < 8; ++i) counters[i] += c[i];
+      used = omp_get_num_threads();
     }
-    double xn = x[p] + U[0] * P->dt + s2nu * dWx;
-    double yn = y[p] + U[1] * P->dt + s2nu * dWy;
-    double o = om[p], mo = c[22];
-    double on = o - OR_C3 * mo * (o - mo) * P->dt - c[23] * mo * o * P->dt
-              + sqrt(2.0 * OR_C3 * OR_C4 * mo * mo * (o > 0.0 ? o : 0.0)) * dWo;
-    if (on < 0.0) { on = -on; counters[6]++; }
-    /* eq. IEM with the element mean, or eq. IECM with the velocity-conditioned
-     * mean of the particle's bin when cond is given */
-    double pn = ps[p] - (ps[p] - (cond ? cond[p] : c[24])) * P->dt * c[25];
-    /* distances from the no-slip wall before and after the move (sec.
-     * no-slip wall-boundary conditions), for particles in elements with a
-     * node on such a wall */
-    const int near = m->nsw_flag[e];
-    double dn = 0.0, d1 = 0.0;
-    if (near) {
-      const double* L = m->nsw + 4 * e;
-      dn = (x[p] - L[0]) * L[2] + (y[p] - L[1]) * L[3];
-      d1 = (xn - L[0]) * L[2] + (yn - L[1]) * L[3];
-    }
-    or_track_info ti;
-    int en = or_track(m, e, &xn, &yn, &Un[0], &Un[1], &ti);
-    /* wall condition: trajectory (a), behind the wall after the move (the
-     * walk reflected the position at a no-slip edge, or d^{n+1} < 0), or
-     * trajectory (b), eta < f_w = exp(-d^n d^{n+1} / (nu dt)) (eq. fw,
-     * eq. exp-wall-condition); eta is the third word of the step's second
-     * random block.  Then U = 0 and omega from a Gamma distribution with
-     * the mean of eq. frequency-wallstats and variance C4 <omega>^2 (shape
-     * 1/C4 = 4): -<omega>/4 times the sum of the logarithms of the four
-     * uniforms of the step's third block. */
-    int wall = (ti.status & OR_TRK_NOSLIP) != 0;
-    if (near && !wall) {
-      if (d1 < 0.0) {
-        wall = 1;
-      } else {
-        uint32_t ctr[4] = {id, step, 1u, OR_PURPOSE_STEP}, key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)}, out[4];
-        or_philox(ctr, key, out);
-        const double eta = (double)or_u01(out[2]);
-        if (eta < exp(-dn * d1 / (P->nu * P->dt))) wall = 1;
-      }
-    }
-    if (wall) {
-      Un[0] = Un[1] = Un[2] = 0.0;
-      uint32_t ctr[4] = {id, step, 2u, OR_PURPOSE_STEP}, key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)}, out[4];
-      or_philox(ctr, key, out);
-      float lsum = or_logf(or_u01(out[0])) + or_logf(or_u01(out[1]));
-      lsum = lsum + or_logf(or_u01(out[2]));
-      lsum = lsum + or_logf(or_u01(out[3]));
-      const double mw = omega_wall ? omega_wall[e] : mo;
-      on = -0.25 * (mw > 0.0 ? mw : mo) * (double)lsum;
-      ti.status |= OR_TRK_NOSLIP;
-    }
-    counters[0] += ti.walk_steps;
-    counters[1] += ti.reflections;
-    counters[2] += ti.crossings_periodic;
-    if (ti.status & OR_TRK_FALLBACK) counters[3]++;
-    if (ti.status & OR_TRK_BRUTE) counters[4]++;
-    if (ti.status & OR_TRK_LOST) counters[5]++;
-    if (!(ti.status & OR_TRK_LOST) && ti.min_rel < 1e-12) counters[7]++;
-    if (status_out) status_out[p] = ti.status | ((ti.min_rel < 1e-12) ? 256 : 0);
-    /* READING: fluid re-entering through the inflow carries no scalar */
-    if (ti.status & OR_TRK_REINJECT) pn = 0.0;
-    /* the concentrated source (ch. 4): particles inside it get psi = 1 */
-    if (P->src_r > 0.0 && (xn - P->src_x) * (xn - P->src_x) + (yn - P->src_y) * (yn - P->src_y) <= P->src_r * P->src_r)
-      pn = 1.0;
-    x[p] = xn; y[p] = yn; u[p] = Un[0]; v[p] = Un[1]; w[p] = Un[2];
-    om[p] = on; ps[p] = pn;
-    if (!(ti.status & OR_TRK_LOST)) elem[p] = en;
   }
+#else
+  (void)nthreads;
+  for (long p = 0; p < n_p; ++p)
+    or_step_one(m, p, rows, P, seed, step, sdt, s2nu, x, y, u, v, w, om, ps, elem, status_out, counters, pid,
+                cond, omega_wall);
+#endif
+  return used;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -70,3 +70,25 @@ def test_full_method_invariants_small_channel(chan):
     assert st["ps"].min() >= 0.0 and st["ps"].max() <= 1.0
     assert np.all((st["y"] >= -1) & (st["y"] <= 1))
     assert np.all((st["x"] >= 0) & (st["x"] <= 2 * math.pi))
+
+
+def test_threaded_particle_loop_matches_the_serial_one():
+    """or_step_threads (the particle loop of loop design (ii) over host
+    threads) gives or_step's results bit for bit: every particle reads only
+    its own state and its element's coefficients within a step."""
+    m = inputs.channel_mesh(20, 40, seed=1)
+    M = oracle.Mesh(m)
+    counts = np.full(M.n_tri, 12, dtype=np.int32)
+    a = oracle.init(M, counts, 1, u_sigma=0.1, elem_psi0=inputs.scalar_slab(m))
+    b = {k: v.copy() for k, v in a.items()}
+    P = oracle.make_params(dt=1e-3, nu=1e-3, Pi=2e-3, closure="glm")
+    es, ns, nd, _ = oracle.statistics(M, a)
+    for s in range(4):
+        rows = oracle.elem_coeff(M, ns, nd, P)
+        ca, sa = oracle.step(M, rows, P, 1, s, a)
+        cb, sb, used = oracle.step_threads(M, rows, P, 1, s, b, threads=4)
+        assert used >= 1
+        assert ca == cb and np.array_equal(sa, sb)
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+        es, ns, nd, _ = oracle.statistics(M, a, ns)
