@@ -32,7 +32,9 @@ constexpr int64_t kScratchInts = 4 * kMaxParticles + kHistInts + kPartInts + (kM
 static __device__ __align__(256) int32_t g_noalloc_scratch[kScratchInts];
 
 std::mutex g_mu;
-int32_t* g_scratch_ptr[64] = {nullptr};  // device address of g_noalloc_scratch per device
+// device address of g_noalloc_scratch per device, kept for the life of the
+// process (a device reset between calls is not supported)
+int32_t* g_scratch_ptr[64] = {nullptr};
 
 }  // namespace
 

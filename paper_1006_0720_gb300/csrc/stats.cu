@@ -196,51 +196,28 @@ __device__ __forceinline__ fx::df ld_df(const float* a, int64_t i) { return fx::
 // Eight lanes per element (four elements per warp), one pass over the
 // element's particles in the grouping's order (sec. 3.3: N, means, central
 // moments with 1/N).  Lane j of a group takes sorted positions j, j + 8, ...
-// (eight consecutive positions per load across the group).
-//  * Means: every value is converted to fixed point q with 48 fraction
-//    bits and summed in 128-bit integers, exact and independent of the
-//    order (a reordering of the state does not change them).
-//  * Central moments: every value enters as its deviation d = x - x_0 from
-//    the element's first particle, a double-float with an absolute error
-//    of about 2^-48 |x| (the resolution of the stored forms); each lane sums
-//    the pairwise products of the deviations in double-float in its order,
-//    the eight lane sums are combined by a fixed butterfly, and
-//      moment_ab = (S_ab - S_a S_b / N) / N,  S_a = sum q_a - N q_a(x_0)
-//    (exact).  The shift keeps the cancellation to a factor of about two
-//    (the deviations are of the size of the fluctuations); the order of the
-//    additions is fixed by the stable grouping.
-//  * An element with a value outside |x| < 2^14 (beyond the exact sums)
-//    takes S_a as double-float sums of the deviations in a second pass and
-//    the mean as x_0 + S_a / N.
+// (eight consecutive positions per load across the group).  Every value
+// enters as its deviation d = x - x_0 from the element's first particle, a
+// double-float with an absolute error of about 2^-48 |x| (the resolution of
+// the stored forms); each lane sums the deviations and their pairwise
+// products in double-float in its order, the eight lane sums are combined
+// by a fixed butterfly, and
+//   mean = x_0 + S_a / N,   moment_ab = (S_ab - S_a S_b / N) / N.
+// The shift keeps the cancellation in the moments to a factor of about two
+// (the deviations are of the size of the fluctuations).  The order of every
+// addition is fixed by the stable grouping, so the results are
+// deterministic; a reordering of the storage changes them by rounding only.
+// Only FP32 additions and fused multiply-adds per particle (no conversions).
 constexpr int kStatLanes = 8;
-constexpr int kFQ = 48;       // fraction bits of the exact sums
-constexpr int kFixLim = 14;   // |value| < 2^14 for the exact sums
+
+__device__ __forceinline__ void prefetch_l2(const void* a) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
 
 __device__ __forceinline__ void acc_xor(fx::acc& a, int o) {
   const float h = __shfl_xor_sync(0xffffffffu, a.h, o);
   const float l = __shfl_xor_sync(0xffffffffu, a.l, o);
   a.add(fx::df{h, l});
-}
-
-// 128-bit sums (hi:lo) of fixed-point values.
-__device__ __forceinline__ void add64(unsigned long long& lo, long long& hi, long long v) {
-  const unsigned long long nl = lo + (unsigned long long)v;
-  hi = hi + (v < 0 ? -1 : 0) + (nl < lo ? 1 : 0);
-  lo = nl;
-}
-__device__ __forceinline__ void add128_xor(unsigned long long& lo, long long& hi, int o) {
-  const unsigned long long ol = __shfl_xor_sync(0xffffffffu, lo, o);
-  const long long oh = __shfl_xor_sync(0xffffffffu, hi, o);
-  const unsigned long long nl = lo + ol;
-  hi = hi + oh + (nl < lo ? 1 : 0);
-  lo = nl;
-}
-
-// A double-float to fixed point with kFQ fraction bits; `ok` cleared
-// outside |x| < 2^kFixLim.
-__device__ __forceinline__ long long df_fix(fx::df x, bool& ok) {
-  ok = ok && (int)((fx::f_bits(x.h) >> 23) & 0xFF) < 127 + kFixLim;
-  return fx::f2fix(x.h, kFQ) + fx::f2fix(x.l, kFQ);
 }
 
 template <typename T>
@@ -252,14 +229,26 @@ __global__ void __launch_bounds__(256) k_elem_stats_grp(const int32_t* __restric
   const int lane = threadIdx.x & 31, j = lane & (kStatLanes - 1);
   const int64_t group = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kStatLanes;
   const int64_t n_groups = ((int64_t)gridDim.x * blockDim.x) / kStatLanes;
-  // every lane of a warp runs the same number of rounds (the butterflies
-  // below need all 32 lanes)
+  // every lane of a warp runs the same number of rounds (the butterfly
+  // below needs all 32 lanes)
   const int64_t rounds = (n_tri + n_groups - 1) / n_groups;
   int64_t e = group;
   for (int64_t r = 0; r < rounds; ++r, e += n_groups) {
     const bool live = e < n_tri;
     const int32_t beg = live ? seg[e] : 0, end = live ? seg[e + 1] : 0;
     const int32_t N = end - beg;
+    {  // the next element of this group on its way to L2 (after a
+       // reordering of the state its particles sit near their positions in
+       // the grouped order)
+      const int64_t en = e + n_groups;
+      if (en < n_tri) {
+        const int32_t nb = seg[en], ne = seg[en + 1];
+        for (int32_t i = nb + 16 * j; i < ne; i += 16 * kStatLanes) {
+          prefetch_l2(u + i); prefetch_l2(v + i); prefetch_l2(w + i); prefetch_l2(om + i); prefetch_l2(ps + i);
+          if (pid) prefetch_l2(pid + i);
+        }
+      }
+    }
     fx::df K[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) K[q] = fx::df{0.f, 0.f};
@@ -267,26 +256,21 @@ __global__ void __launch_bounds__(256) k_elem_stats_grp(const int32_t* __restric
       const int32_t p0 = pid ? __ldg(pid + beg) : beg;
       K[0] = ld_df(u, p0); K[1] = ld_df(v, p0); K[2] = ld_df(w, p0); K[3] = ld_df(om, p0); K[4] = ld_df(ps, p0);
     }
-    unsigned long long lo[5] = {0, 0, 0, 0, 0};
-    long long hi[5] = {0, 0, 0, 0, 0};
-    bool ok = true;
-    fx::acc s2[7];
+    fx::acc s1[5], s2[7];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) s1[q].init(fx::df{0.f, 0.f});
 #pragma unroll
     for (int q = 0; q < 7; ++q) s2[q].init(fx::df{0.f, 0.f});
     for (int32_t i = beg + j; i < end; i += kStatLanes) {
       const int32_t p = pid ? __ldg(pid + i) : i;
-      const fx::df xu = ld_df(u, p), xv = ld_df(v, p), xw = ld_df(w, p), xm = ld_df(om, p), xp = ld_df(ps, p);
-      add64(lo[0], hi[0], df_fix(xu, ok));
-      add64(lo[1], hi[1], df_fix(xv, ok));
-      add64(lo[2], hi[2], df_fix(xw, ok));
-      add64(lo[3], hi[3], df_fix(xm, ok));
-      add64(lo[4], hi[4], df_fix(xp, ok));
       // normalized, so that the dropped product of the low parts is below
       // 2^-48 of the product even when the deviation is far below the value
-      const fx::df du = fx::sub(xu, K[0]);
-      const fx::df dv = fx::sub(xv, K[1]);
-      const fx::df dw = fx::sub(xw, K[2]);
-      const fx::df dp = fx::sub(xp, K[4]);
+      const fx::df du = fx::sub(ld_df(u, p), K[0]);
+      const fx::df dv = fx::sub(ld_df(v, p), K[1]);
+      const fx::df dw = fx::sub(ld_df(w, p), K[2]);
+      const fx::df dm = fx::sub(ld_df(om, p), K[3]);
+      const fx::df dp = fx::sub(ld_df(ps, p), K[4]);
+      s1[0].add(du); s1[1].add(dv); s1[2].add(dw); s1[3].add(dm); s1[4].add(dp);
       s2[0].add(fx::mul(du, du));
       s2[1].add(fx::mul(dv, dv));
       s2[2].add(fx::mul(dw, dw));
@@ -295,63 +279,13 @@ __global__ void __launch_bounds__(256) k_elem_stats_grp(const int32_t* __restric
       s2[5].add(fx::mul(dv, dw));
       s2[6].add(fx::mul(dp, dp));
     }
-    // butterflies within the group of eight: every lane ends with the totals
+    // butterfly within the group of eight: every lane ends with the totals
 #pragma unroll
     for (int o = kStatLanes / 2; o > 0; o >>= 1) {
 #pragma unroll
-      for (int q = 0; q < 5; ++q) add128_xor(lo[q], hi[q], o);
+      for (int q = 0; q < 5; ++q) acc_xor(s1[q], o);
 #pragma unroll
       for (int q = 0; q < 7; ++q) acc_xor(s2[q], o);
-      ok = ok && __shfl_xor_sync(0xffffffffu, (int)ok, o);
-    }
-    // S_a: the sums of the deviations, exact from the integer sums, or (an
-    // element beyond the exact range) double-float sums of a second pass
-    fx::df S[5];
-    if (__any_sync(0xffffffffu, !ok)) {
-      fx::acc s1[5];
-#pragma unroll
-      for (int q = 0; q < 5; ++q) s1[q].init(fx::df{0.f, 0.f});
-      if (!ok) {
-        for (int32_t i = beg + j; i < end; i += kStatLanes) {
-          const int32_t p = pid ? __ldg(pid + i) : i;
-          s1[0].add(fx::sub(ld_df(u, p), K[0]));
-          s1[1].add(fx::sub(ld_df(v, p), K[1]));
-          s1[2].add(fx::sub(ld_df(w, p), K[2]));
-          s1[3].add(fx::sub(ld_df(om, p), K[3]));
-          s1[4].add(fx::sub(ld_df(ps, p), K[4]));
-        }
-      }
-#pragma unroll
-      for (int o = kStatLanes / 2; o > 0; o >>= 1)
-#pragma unroll
-        for (int q = 0; q < 5; ++q) acc_xor(s1[q], o);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) S[q] = s1[q].value();
-    }
-    if (ok) {
-#pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        bool dummy = true;
-        const long long qk = df_fix(K[q], dummy);
-        // sum q - N q_K in 128 bits: N q_K has |.| < 2^31 2^62
-        unsigned long long pl;
-        long long ph;
-        {
-          const bool neg = qk < 0;
-          const unsigned long long a = neg ? 0ull - (unsigned long long)qk : (unsigned long long)qk;
-          const unsigned long long a0 = a & 0xFFFFFFFFull, a1 = a >> 32;
-          const unsigned long long p0 = a0 * (unsigned long long)N, p1 = a1 * (unsigned long long)N;
-          pl = p0 + (p1 << 32);
-          ph = (long long)((p1 >> 32) + (pl < p0 ? 1ull : 0ull));
-          if (neg) {
-            pl = ~pl + 1ull;
-            ph = ~ph + (pl == 0ull ? 1 : 0);
-          }
-        }
-        const unsigned long long dl = lo[q] - pl;
-        const long long dh = hi[q] - ph - (lo[q] < pl ? 1 : 0);
-        S[q] = fx::i128_to_df(dl, dh, -kFQ);
-      }
     }
     if (!live) continue;
     double* out = es + e * PDF_NES;
@@ -361,22 +295,23 @@ __global__ void __launch_bounds__(256) k_elem_stats_grp(const int32_t* __restric
         if ((q & (kStatLanes - 1)) == j) out[q] = 0.0;
       continue;
     }
+    // every lane of the group forms the 13 outputs (N, the five means, the
+    // seven central moments); lane j writes outputs j and j + 8
     const fx::df invN = fx::recip_df(N);
+    fx::df S[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) S[q] = s1[q].value();
     double val[PDF_NES];
     val[0] = (double)N;
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      const fx::df mean = ok ? fx::df_norm(fx::mul(fx::i128_to_df(lo[q], hi[q], -kFQ), invN))
-                             : fx::add(K[q], fx::df_norm(fx::mul(S[q], invN)));
-      val[1 + q] = __longlong_as_double((long long)fx::df2d(mean));
-    }
+    for (int q = 0; q < 5; ++q)
+      val[1 + q] = __longlong_as_double((long long)fx::df2d(fx::add(K[q], fx::df_norm(fx::mul(S[q], invN)))));
     const int pa[7] = {0, 1, 2, 0, 0, 1, 4}, pb[7] = {0, 1, 2, 1, 2, 2, 4};
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
       const fx::df corr = fx::df_norm(fx::mul(fx::df_norm(fx::mul(S[pa[q]], S[pb[q]])), invN));
       val[6 + q] = __longlong_as_double((long long)fx::df2d(fx::df_norm(fx::mul(fx::sub(s2[q].value(), corr), invN))));
     }
-    // lane j of the group writes outputs j and j + 8
 #pragma unroll
     for (int q = 0; q < PDF_NES; ++q)
       if ((q & (kStatLanes - 1)) == j) out[q] = val[q];
@@ -593,7 +528,10 @@ pdf_status iecm_cond(pdf_particles* P, const int32_t* seg, const int32_t* order,
 // Element statistics of the grouped particles (seg, order) into P->es.
 static pdf_status elem_stats(pdf_particles* P, const int32_t* seg, const int32_t* order, cudaStream_t st) {
   const MeshDev& M = P->mesh->d;
-  const int nb = blocks_for((int64_t)M.n_tri * kStatLanes, 256);
+  // three resident blocks of 256 per SM (80 registers): each group of
+  // eight lanes walks several elements and prefetches the next one
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)M.n_tri * kStatLanes + 255) / 256,
+                                                           (int64_t)sm_count() * 3));
   if (P->precision == PDF_FP64)
     PDF_KERNEL("k_elem_stats", st, k_elem_stats_grp<fx::df><<<nb, 256, 0, st>>>(
                                        seg, order, M.n_tri, P->u, P->v, P->w, P->om, P->ps, P->es));
