@@ -163,12 +163,15 @@ def replica_value(world, n, steps, t_max_ms):
     return world * n * steps / (t_max_ms * 1e-3)
 
 
-def cpu_baseline_measure(steps=1, warmup=0, ppe=None):
-    """The oracle as it stands, single-threaded on a host core, on a bounded
-    sample of the workload: the benchmark mesh with `ppe` particles per
-    element (default: the workload's 100), initialised once (untimed), then
-    `warmup` untimed and `steps` timed steps (coefficients + particle step +
-    statistics); value = the median per-step throughput."""
+def cpu_baseline_measure(steps=1, warmup=0, ppe=None, threads=1):
+    """The oracle as it stands on a bounded sample of the workload: the
+    benchmark mesh with `ppe` particles per element (default: the
+    workload's 100), initialised once (untimed), then `warmup` untimed and
+    `steps` timed steps (coefficients + particle step + statistics); value =
+    the median per-step throughput.  threads = 1: single-threaded on one host
+    core; otherwise the particle loop runs over that many host threads (0:
+    all; OpenMP, the paper's loop design (ii)) with the coefficients and
+    statistics single-threaded, and `cores` reports the threads used."""
     import oracle
     cfg = inputs.workload(WORKLOAD)
     ppe = ppe or cfg["ppe"]
@@ -180,17 +183,22 @@ def cpu_baseline_measure(steps=1, warmup=0, ppe=None):
     P = oracle.make_params(dt=cfg["dt"], nu=cfg["nu"], Pi=cfg["Pi"], closure=cfg["closure"])
     es, ns, nd, _ = oracle.statistics(M, st)
     n = int(counts.sum())
-    rates, total = [], 0.0
+    rates, total, used = [], 0.0, 1
     for s in range(warmup + steps):
         t0 = time.perf_counter()
         rows = oracle.elem_coeff(M, ns, nd, P)
-        oracle.step(M, rows, P, cfg["seed"], s, st)
+        if threads == 1:
+            oracle.step(M, rows, P, cfg["seed"], s, st)
+        else:
+            _, _, used = oracle.step_threads(M, rows, P, cfg["seed"], s, st, threads=threads)
         es, ns, nd, _ = oracle.statistics(M, st, ns)
         dt = time.perf_counter() - t0
         if s >= warmup:
             rates.append(n / dt)
             total += dt
-    return {"value": statistics.median(rates), "unit": UNIT, "cores": 1, "kind": "oracle",
+    kind = "oracle" if threads == 1 else ("oracle, particle loop over %d host threads (OpenMP, loop design (ii)); "
+                                          "coefficients and statistics single-threaded" % used)
+    return {"value": statistics.median(rates), "unit": UNIT, "cores": used, "kind": kind,
             "sample": "%d timed step(s) of the %d-triangle channel with %d particles per element (%d particles; "
                       "the workload has %d), %.1f s of stepping" % (steps, cfg["n_tri"], ppe, n, cfg["ppe"], total)}
 
@@ -200,10 +208,11 @@ def run_reference(args):
     if rank != 0:
         return 0
     cfg = inputs.workload(WORKLOAD)
-    # bound the whole run to ~2 minutes of oracle work at ~5.6e6 particle-steps/s
-    per_step = 6.5e8 / max(1, args.steps + args.warmup)
+    # bound the whole run to a few minutes of oracle work (all host cores on
+    # the particle loop: ~1.5e7 particle-steps/s or more)
+    per_step = 1.5e9 / max(1, args.steps + args.warmup)
     ppe = int(max(5, min(cfg["ppe"], per_step // cfg["n_tri"])))
-    base = cpu_baseline_measure(args.steps, args.warmup, ppe=ppe)
+    base = cpu_baseline_measure(args.steps, args.warmup, ppe=ppe, threads=0)
     value = base["value"]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
@@ -308,6 +317,14 @@ def run_gpu(args):
                   "get_state")
     torch.cuda.synchronize()
     e2e_steps = max(1, min(args.steps, 10))
+    # untimed warm-up of the host path (its first call allocates the staging
+    # buffers and creates the streams)
+    for _ in range(2):
+        pg.pdf_step_host(gp, gm, p, host, step=step_no, stream=stream)
+        pg.capi.check(L.pdf_estimate_stats(gp.handle, gm.handle, None, ctypes.c_void_p(host_ns.data_ptr()), None, sp),
+                      "estimate_stats")
+        step_no += 1
+    stream.synchronize()
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -325,7 +342,8 @@ def run_gpu(args):
     e2e = {"value": replica_value(world, n, e2e_steps, 1e3 * e2e_max), "unit": UNIT, "h2d_bytes_per_step": state_bytes,
            "d2h_bytes_per_step": state_bytes + gm.n_nodes * 12 * 8, "steps": e2e_steps,
            "what": "state in page-locked host memory: read, stepped and written back every step (pdf_step_host: "
-                   "chunked loads, steps and stores overlapped), node statistics copied out"}
+                   "chunks moved by the copy engines while the previous chunk is stepped), node statistics copied "
+                   "out; after 2 untimed warm-up steps"}
 
     if rank != 0:
         if dist is not None:
@@ -428,6 +446,10 @@ def run_gpu(args):
                                                   "steps": ksteps_rx, "rtol": 1e-8, "iterations": [min(its), max(its)],
                                                   "what": "step + statistics + elliptic-relaxation solve (FP32 state)"}}
         del gq
+    if want("fp64"):
+        line["native_fp64"] = run_native_fp64(pg, torch, stream, gm, cfg, seed, psi, p, max(3, min(args.steps, 10)))
+    if want("hostlink"):
+        line["host_link_copy_engines"] = measure_host_link(torch)
     if want("iecm"):
         line["iecm"] = run_iecm(pg, torch, stream, gm, cfg, seed, psi, p, max(5, min(args.steps, 20)))
     if want("projection"):
@@ -438,10 +460,87 @@ def run_gpu(args):
             line["cpu_baseline"] = cpu_baseline_measure(3)
         except Exception as exc:  # report, do not hide
             line["cpu_baseline"] = {"error": repr(exc)}
+        try:
+            line["cpu_baseline_all_cores"] = cpu_baseline_measure(3, threads=0)
+        except Exception as exc:
+            line["cpu_baseline_all_cores"] = {"error": repr(exc)}
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def run_native_fp64(pg, torch, stream, gm, cfg, seed, psi, p, steps):
+    """The benchmark workload with the particle kernel in native FP64
+    instructions (PDF_ARITH_FP64: FP64 state arithmetic, the FP64 walk),
+    the statistics as in the default path; time per step and of k_step."""
+    g64 = pg.Particles(gm, seed, ppe=cfg["ppe"], u_sigma=cfg["u_sigma"], elem_psi0=psi)
+    p64 = pg.model_params(dt=p.dt, nu=p.nu, Pi=p.Pi, closure=cfg["closure"], arith="fp64")
+    pg.pdf_estimate_stats(g64, gm)
+    for s in range(2):
+        pg.pdf_step(g64, gm, p64, step=s)
+        pg.pdf_estimate_stats(g64, gm)
+    torch.cuda.synchronize()
+    pg.pdf_profile_reset()
+    pg.pdf_profile_only("k_step")
+    pg.pdf_profile_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(steps):
+        pg.pdf_step(g64, gm, p64, step=2 + s, stream=stream)
+        pg.pdf_estimate_stats(g64, gm, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pg.pdf_profile_enable(False)
+    c, t = pg.pdf_profile_query("k_step")
+    pg.pdf_profile_reset()
+    pg.pdf_profile_only(None)
+    ms = e0.elapsed_time(e1) / steps
+    del g64
+    return {"value": gm_particles(cfg) / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "k_step_ms": t / c if c else None, "dtype": "f64",
+            "what": "native FP64 particle kernel (PDF_ARITH_FP64) + statistics, same workload"}
+
+
+def measure_host_link(torch, nbytes=1 << 30, repeats=3):
+    """The host link through the copy engines: cudaMemcpyAsync (torch
+    non_blocking copies) of 1 GiB between page-locked host memory and the
+    device, one call per direction on its own stream, each direction alone
+    and both at once; best of `repeats`."""
+    h_in = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    h_out = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    d_in = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    d_out = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(ops):
+        best = None
+        for _ in range(repeats):
+            torch.cuda.synchronize()
+            start = torch.cuda.Event(enable_timing=True)
+            start.record(torch.cuda.current_stream())
+            ends = []
+            for st, fn in ops:
+                st.wait_event(start)
+                with torch.cuda.stream(st):
+                    fn()
+                ev = torch.cuda.Event(enable_timing=True)
+                ev.record(st)
+                ends.append(ev)
+            torch.cuda.synchronize()
+            ms = max(start.elapsed_time(ev) for ev in ends)
+            best = ms if best is None else min(best, ms)
+        return best
+
+    h2d = (s_in, lambda: d_in.copy_(h_in, non_blocking=True))
+    d2h = (s_out, lambda: h_out.copy_(d_out, non_blocking=True))
+    t_in, t_out, t_both = timed([h2d]), timed([d2h]), timed([h2d, d2h])
+    out = {"bytes_per_direction": nbytes, "h2d_gbs": nbytes / (t_in * 1e-3) / 1e9,
+           "d2h_gbs": nbytes / (t_out * 1e-3) / 1e9, "both_gbs": 2 * nbytes / (t_both * 1e-3) / 1e9,
+           "what": "cudaMemcpyAsync, page-locked host <-> device, one call per direction on separate streams"}
+    del h_in, h_out, d_in, d_out
+    return out
 
 
 def run_iecm(pg, torch, stream, gm, cfg, seed, psi, p, steps, bins=(5, 5, 5)):
@@ -595,13 +694,25 @@ def run_warmstart(args):
     t_train = time.perf_counter() - t0
     del X, Y
     cfg, gm, gp, p, wp = E.setup(WORKLOAD, seed=3)
-    its = E.advance(gm, gp, p, wp, args.steps)
-    res = {"jacobi": E.compare(gm, gp, p, wp, net, multigrid=False),
-           "multigrid": E.compare(gm, gp, p, wp, net, multigrid=True)}
+    # the run on the benchmark mesh, its solves kept: a second network is
+    # trained on them (the method's own solves on this mesh), then both are
+    # judged on the state after the run (not in either training set)
+    its, Xo, Yo = E.advance(gm, gp, p, wp, args.steps, collect=True)
+    t0 = time.perf_counter()
+    net_o, losses_o = E.train(Xo, Yo, steps=args.train_steps, batch=8192, lr=2e-3, seed=1,
+                              log_every=max(1, args.train_steps // 10))
+    torch.cuda.synchronize()
+    t_train_o = time.perf_counter() - t0
+    del Xo, Yo
+    res = {"small_channel_net": {"jacobi": E.compare(gm, gp, p, wp, net, multigrid=False),
+                                 "multigrid": E.compare(gm, gp, p, wp, net, multigrid=True)},
+           "own_mesh_net": {"jacobi": E.compare(gm, gp, p, wp, net_o, multigrid=False),
+                            "multigrid": E.compare(gm, gp, p, wp, net_o, multigrid=True)}}
     line = {"mode": "warmstart", "train_solves": args.solves, "train_samples": args.solves * 800,
             "train_steps": args.train_steps, "collect_seconds": t_collect, "train_seconds": t_train,
             "loss_log": losses, "eval_workload": WORKLOAD, "eval_after_steps": args.steps,
-            "warm_iterations_during_run": its, "compare": res}
+            "own_mesh_train_samples": args.steps * gm.n_nodes, "own_mesh_train_seconds": t_train_o,
+            "own_mesh_loss_log": losses_o, "warm_iterations_during_run": its, "compare": res}
     print(json.dumps(line))
     return 0
 
@@ -618,12 +729,13 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, help="a smaller workload for profiling runs")
     ap.add_argument("--skip-extras", action="store_true", help="only the main line (no FP32-state and solve figures)")
     ap.add_argument("--extras", default="all",
-                    help="comma-separated subset of complex, fp32, relax, iecm, projection (for profiling runs)")
+                    help="comma-separated subset of complex, fp32, relax, iecm, projection, fp64, hostlink "
+                         "(for profiling runs)")
     ap.add_argument("--mode", default="step", choices=["step", "warmstart"],
                     help="warmstart: the learned warm start experiment instead of the step benchmark")
     args = ap.parse_args()
     if args.extras != "all":
-        unknown = set(args.extras.split(",")) - {"complex", "fp32", "relax", "iecm", "projection"}
+        unknown = set(args.extras.split(",")) - {"complex", "fp32", "relax", "iecm", "projection", "fp64", "hostlink"}
         if unknown:
             ap.error("--extras: unknown %s" % ", ".join(sorted(unknown)))
     if args.impl == "reference":

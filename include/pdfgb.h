@@ -325,10 +325,13 @@ pdf_status pdf_step(pdf_particles* p, const pdf_mesh* m, const pdf_model_params*
 /* pdf_step for a state that lives in host memory: equivalent to
  * pdf_particles_set_state(x ... elem), pdf_step(...) and
  * pdf_particles_get_state(x ... elem) (same results, bit for bit), with the
- * transfers overlapped: the particles are taken in chunks of particle ids,
- * and the load of one chunk, the step of the previous one and the store of
- * the one before run at once (the host link's two directions and the SMs
- * busy together).
+ * transfers overlapped: the particles are taken in chunks of particle ids;
+ * the copy engines move each chunk's arrays (cudaMemcpyAsync, one call per
+ * array and direction) into and out of device staging buffers while the
+ * SMs convert and step the previous chunk, so that the host link's two
+ * directions and the SMs are busy together.  The staging buffers (two per
+ * direction, 60 bytes per particle of a chunk each) are allocated at the
+ * first call and kept by the particle set.
  *   x ... ps    page-locked host (or device) [n] FP64, elem [n] int32; read,
  *               then overwritten with the stepped state (in particle-id
  *               order, as pdf_particles_get_state returns it)
@@ -338,8 +341,9 @@ pdf_status pdf_step(pdf_particles* p, const pdf_mesh* m, const pdf_model_params*
  * The particle set keeps the stepped state (slot = particle id) for
  * pdf_estimate_stats.  PDF_EINVAL for pageable host buffers, for positions
  * outside |x|, |y| < 64 and for the IECM mixing model (its conditioned
- * means belong to the device-resident order); PDF_ELOST if any particle was
- * lost; PDF_ESTATE as pdf_step. */
+ * means belong to the device-resident order); PDF_ENOMEM if the staging
+ * buffers cannot be allocated; PDF_ELOST if any particle was lost;
+ * PDF_ESTATE as pdf_step. */
 pdf_status pdf_step_host(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params, const double* wp,
                          const double* elem_coeff, uint32_t step, double* x, double* y, double* u, double* v,
                          double* w, double* om, double* ps, int32_t* elem, void* stream, pdf_step_info* info);
@@ -373,7 +377,9 @@ pdf_status pdf_estimate_stats(pdf_particles* p, const pdf_mesh* m, double* elem_
  *     elements, else PDF_EINVAL with a message naming the limit;
  *   - the first call on each device looks up that device's copy of the
  *     scratch array (with the device current), so make the first call on a
- *     device before any stream capture;
+ *     device before any stream capture; the address is kept for the life of
+ *     the process, so a device reset (cudaDeviceReset) between calls is not
+ *     supported;
  *   - every call shares the one scratch array: calls whose work overlaps on
  *     the GPU (different streams or threads without ordering) race and give
  *     wrong statistics.  The scratch keeps the last call's contents; nothing
@@ -527,8 +533,12 @@ pdf_status pdf_pressure_field(pdf_particles* p, const double* set, double* get, 
 /* A per-node MLP that proposes the initial guess of pdf_relax_solve.  The
  * paper warm-starts from the previous step (sec. 3.2); the network is an
  * addition, and the FP64 solve it seeds still runs to the same residual.
- * Architecture: 11 inputs (<U>, <V>, <W>, <uu>, <vv>, <ww>, <uv>, <uw>, <vw>,
- * <omega>, wall distance) -> 64 -> 64 -> 64 -> 9 outputs (wp_ij, row-major
+ * It corrects the local model: where the elliptic term of eq.
+ * elliptic-relaxation-Lagrangian vanishes, wp = rhs; the guess is rhs plus
+ * the network's estimate of wp - rhs.  Architecture: 11 inputs (the nine
+ * rhs_ij, the wall distance over L, log(L^2 / h^2) with L^2 the C_xi = 1
+ * length scale and h^2 the mean area of the node's elements) -> 64 -> 64 ->
+ * 64 -> 9 outputs (wp_ij - rhs_ij, row-major
  * ij), GELU, standardized inputs and outputs.  Matrix products on the
  * tensor cores from BF16 operands with FP32 accumulation; the standardized
  * input, the weights, each hidden activation and each back-propagated
@@ -559,14 +569,23 @@ pdf_status pdf_mlp_grad(pdf_mlp* net, const float* X, const float* Y, int64_t n,
 /* One Adam step with learning rate lr on the n pairs (one batch). */
 pdf_status pdf_mlp_train_step(pdf_mlp* net, const float* X, const float* Y, int64_t n, float lr, float* loss,
                               void* stream);
-/* Features X [n_nodes][11] of every node from the last statistics and, if wp
- * (device [9][n_nodes]) and Y are given, the targets Y [n_nodes][9]. */
-pdf_status pdf_mlp_features(pdf_particles* p, const pdf_mesh* m, const double* wp, float* X, float* Y,
-                            void* stream);
-/* The network's wp [9][n_nodes] (device FP64) for the current statistics;
- * scratch: device FP32 of at least 20 n_nodes entries. */
-pdf_status pdf_mlp_guess(const pdf_mlp* net, pdf_particles* p, const pdf_mesh* m, double* wp, float* scratch,
-                         void* stream);
+/* A training batch of `batch` rows drawn uniformly (with replacement) from
+ * the n pairs (X [n][11], Y [n][9], device FP32) into Xb, Yb (device):
+ * row i comes from row floor(w n / 2^32), w word 0 of Philox4x32-10 (key
+ * seed, counter (i, step, 0, 4)).  PDF_EINVAL for n outside [1, 2^32). */
+pdf_status pdf_mlp_batch(const float* X, const float* Y, int64_t n, uint64_t seed, uint32_t step, int64_t batch,
+                         float* Xb, float* Yb, void* stream);
+/* Features X [n_nodes][11] of every node from the last statistics (the
+ * relaxation's right-hand side and L^2 for params, as pdf_relax_rhs gives
+ * them) and, if wp (device [9][n_nodes], a solution) and Y are given, the
+ * targets Y [n_nodes][9] = wp - rhs. */
+pdf_status pdf_mlp_features(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params, const double* wp,
+                            float* X, float* Y, void* stream);
+/* The guess wp = rhs + the network's correction [9][n_nodes] (device FP64)
+ * for the current statistics; scratch: device FP32 of at least 20 n_nodes
+ * entries. */
+pdf_status pdf_mlp_guess(const pdf_mlp* net, pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,
+                         double* wp, float* scratch, void* stream);
 
 /* ---------------------------------------------------------------- random numbers */
 

@@ -6,7 +6,7 @@ The Python layer only marshals arguments; `capi.lib()` loads libpdfgb.so
 """
 from . import capi
 from .capi import PdfError, lib
-from .api import (Mesh, Mlp, Particles, pdf_mlp_features, model_params, pdf_elem_coeff, pdf_estimate_stats,
+from .api import (Mesh, Mlp, Particles, pdf_mlp_batch, pdf_mlp_features, model_params, pdf_elem_coeff, pdf_estimate_stats,
                   pdf_estimate_stats_noalloc, pdf_kernel_launches,
                   pdf_last_error, pdf_mesh_create, pdf_particles_init, pdf_particles_load, pdf_particles_save, pdf_profile_enable, pdf_profile_only,
                   pdf_profile_query, pdf_profile_reset, pdf_relax_rhs, pdf_relax_solve, pdf_relax_solve_particles,
@@ -14,7 +14,7 @@ from .api import (Mesh, Mlp, Particles, pdf_mlp_features, model_params, pdf_elem
                   pdf_pressure_project, pdf_pressure_field, pdf_pressure_set_solver, pdf_redistribute,
                   pdf_step, pdf_step_host)
 
-__all__ = ["capi", "PdfError", "lib", "Mesh", "Mlp", "pdf_mlp_features", "Particles", "model_params", "pdf_mesh_create",
+__all__ = ["capi", "PdfError", "lib", "Mesh", "Mlp", "pdf_mlp_batch", "pdf_mlp_features", "Particles", "model_params", "pdf_mesh_create",
            "pdf_particles_init", "pdf_particles_save", "pdf_particles_load", "pdf_step", "pdf_estimate_stats", "pdf_estimate_stats_noalloc", "pdf_elem_coeff", "pdf_rng_gauss",
            "pdf_last_error", "pdf_profile_enable", "pdf_profile_only", "pdf_profile_reset", "pdf_profile_query",
            "pdf_kernel_launches", "pdf_relax_solve", "pdf_relax_solve_particles", "pdf_relax_rhs", "pdf_relax_set_solver",

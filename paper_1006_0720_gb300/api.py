@@ -431,10 +431,11 @@ class Mlp:
               "pdf_mlp_train_step")
         return loss.value if want_loss else None
 
-    def guess(self, particles, mesh, wp, stream=None):
+    def guess(self, particles, mesh, params, wp, stream=None):
+        """wp = the relaxation's right-hand side + the network's correction."""
         scratch = torch.empty(20 * mesh.n_nodes, dtype=torch.float32, device="cuda")
-        check(lib().pdf_mlp_guess(self.handle, particles.handle, mesh.handle, _ptr(wp, torch.float64),
-                                  _ptr(scratch), _stream(stream)), "pdf_mlp_guess")
+        check(lib().pdf_mlp_guess(self.handle, particles.handle, mesh.handle, ctypes.byref(params),
+                                  _ptr(wp, torch.float64), _ptr(scratch), _stream(stream)), "pdf_mlp_guess")
         return wp
 
     def close(self):
@@ -449,9 +450,20 @@ class Mlp:
             pass
 
 
-def pdf_mlp_features(particles, mesh, wp=None, stream=None):
+def pdf_mlp_batch(X, Y, seed, step, batch, Xb=None, Yb=None, stream=None):
+    """A training batch drawn (Philox, with replacement) from the pairs (X, Y)."""
+    n = X.shape[0]
+    Xb = torch.empty((batch, X.shape[1]), dtype=torch.float32, device="cuda") if Xb is None else Xb
+    Yb = torch.empty((batch, Y.shape[1]), dtype=torch.float32, device="cuda") if Yb is None else Yb
+    check(lib().pdf_mlp_batch(_ptr(X, torch.float32), _ptr(Y, torch.float32), n, int(seed), int(step), int(batch),
+                              _ptr(Xb), _ptr(Yb), _stream(stream)), "pdf_mlp_batch")
+    return Xb, Yb
+
+
+def pdf_mlp_features(particles, mesh, params, wp=None, stream=None):
+    """Node features X [n, 11] and, with a solution wp, targets Y [n, 9] = wp - rhs."""
     X = torch.empty((mesh.n_nodes, 11), dtype=torch.float32, device="cuda")
     Y = None if wp is None else torch.empty((mesh.n_nodes, 9), dtype=torch.float32, device="cuda")
-    check(lib().pdf_mlp_features(particles.handle, mesh.handle, _ptr(wp, torch.float64), _ptr(X), _ptr(Y),
-                                 _stream(stream)), "pdf_mlp_features")
+    check(lib().pdf_mlp_features(particles.handle, mesh.handle, ctypes.byref(params), _ptr(wp, torch.float64),
+                                 _ptr(X), _ptr(Y), _stream(stream)), "pdf_mlp_features")
     return X, Y

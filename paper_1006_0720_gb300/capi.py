@@ -103,8 +103,9 @@ PROTOTYPES = {
     "pdf_mlp_forward": (I32, [V, V, I64, V, V]),
     "pdf_mlp_grad": (I32, [V, V, V, I64, V, ctypes.POINTER(ctypes.c_float), V]),
     "pdf_mlp_train_step": (I32, [V, V, V, I64, ctypes.c_float, ctypes.POINTER(ctypes.c_float), V]),
-    "pdf_mlp_features": (I32, [V, V, V, V, V, V]),
-    "pdf_mlp_guess": (I32, [V, V, V, V, V, V]),
+    "pdf_mlp_batch": (I32, [V, V, I64, U64, U32, I64, V, V, V]),
+    "pdf_mlp_features": (I32, [V, V, ctypes.POINTER(ModelParams), V, V, V, V]),
+    "pdf_mlp_guess": (I32, [V, V, V, ctypes.POINTER(ModelParams), V, V, V]),
     "pdf_rng_gauss": (I32, [U64, U32, U32, U32, I64, V, V]),
     "pdf_profile_enable": (I32, [I32]),
     "pdf_profile_only": (I32, [ctypes.c_char_p]),

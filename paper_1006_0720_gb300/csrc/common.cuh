@@ -113,12 +113,20 @@ struct RelaxMesh {
   int32_t* pw_e = nullptr;      // [pw_off[n_rep]][3]
   double* pw_n = nullptr;       // [pw_off[n_rep]][3]
 };
-// Streams and events of pdf_step_host (created at its first call).
+// Streams, events and staging buffers of pdf_step_host (created at its
+// first call): chunks of the caller's arrays are copied by the copy engines
+// into two device staging buffers per direction.
 constexpr int kHostChunks = 16;
 struct HostIo {
   cudaStream_t in = nullptr, out = nullptr;
   cudaEvent_t start = nullptr, done = nullptr;
   cudaEvent_t loaded[kHostChunks] = {}, stepped[kHostChunks] = {};
+  cudaEvent_t free_in[2] = {}, free_out[2] = {};
+  int64_t cap = 0;                              // particles per staging buffer
+  double* stage_in[2] = {nullptr, nullptr};     // [7][cap] FP64
+  double* stage_out[2] = {nullptr, nullptr};
+  int32_t* stage_ie[2] = {nullptr, nullptr};    // [cap] element ids
+  int32_t* stage_oe[2] = {nullptr, nullptr};
 };
 struct RelaxAmg;
 struct RelaxWork {
@@ -302,18 +310,25 @@ pdf_status stats_only_handle(const pdf_mesh* m, pdf_particles** out);
 void release_particles(pdf_particles* p);
 // Node derivatives (sec. 3.4) from the node statistics in P->ns.
 pdf_status node_derivs_from_node_stats(pdf_particles* P, cudaStream_t st);
+// The relaxation's nodal right-hand side [9][n_nodes] and L^2 [3][n_nodes]
+// for the particle set's current statistics (relax.cu's work space).
+pdf_status relax_fields(pdf_particles* P, const pdf_model_params* params, cudaStream_t st, const double** rhs,
+                        const double** L2);
 // Host-resident state transfers of pdf_step_host (particles.cu): the
 // address kernels use for a caller's buffer (NULL for pageable memory);
 // the load of particles [beg, beg + cnt) into slots [beg, beg + cnt) (slot =
 // particle id; positions outside |x| < 64 counted in *bad) and the store of
-// those slots back to the same places.
+// those slots back; the caller's arrays are indexed from io_off (beg for
+// the whole arrays, 0 for a staging buffer holding the chunk).
 void* state_kernel_view(const void* ptr);
 pdf_status host_io_init(pdf_particles* p);
 int host_io_blocks();  // grid of each chunk's load and store kernels
 pdf_status state_in_range(pdf_particles* p, double* const in[7], const int32_t* ie, int64_t beg, int64_t cnt,
-                          unsigned long long* bad, int blocks, cudaStream_t st);
+                          unsigned long long* bad, int blocks, cudaStream_t st, int64_t io_off);
 pdf_status state_out_range(const pdf_particles* p, double* const out[7], int32_t* oe, int64_t beg, int64_t cnt,
-                           int blocks, cudaStream_t st);
+                           int blocks, cudaStream_t st, int64_t io_off);
+// The staging buffers of pdf_step_host for chunks of up to cap particles.
+pdf_status host_io_stage(pdf_particles* p, int64_t cap);
 // Launches through prof_launch are counted and, when timing is enabled,
 // bracketed by CUDA events on the launch stream.
 void prof_launch(const char* name, cudaStream_t st, void (*launch)(void*), void* ctx);

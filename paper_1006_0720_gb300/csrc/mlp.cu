@@ -439,24 +439,53 @@ __global__ void k_mlp_init(uint64_t seed, float* __restrict__ w, float* __restri
   w[i] = g[0] * sqrtf(2.0f / (float)kRealK_(l));
 }
 
-// Features and targets of every node from the library's statistics.
-__global__ void k_mlp_features(int32_t n_nodes, const double* __restrict__ ns, const double* __restrict__ wall_d,
+// Features and targets of every node.  The network corrects the local
+// model of the elliptic relaxation: its inputs are the nodal right-hand
+// side rhs_ij of eq. elliptic-relaxation-Lagrangian (the solution where the
+// elliptic term vanishes), the wall distance over L and log(L^2 / h^2)
+// (L^2 of the C_xi = 1 class, h^2 the mean area of the node's elements),
+// and its target is the correction wp_ij - rhs_ij that the elliptic term
+// makes.
+__global__ void k_mlp_features(int32_t n_nodes, const double* __restrict__ rhs, const double* __restrict__ L2,
+                               const double* __restrict__ wall_d, const int32_t* __restrict__ nse_off,
+                               const int32_t* __restrict__ nse, const ElemGeo* __restrict__ geo,
                                const double* __restrict__ wp, float* __restrict__ X, float* __restrict__ Y) {
   for (int32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < n_nodes; n += gridDim.x * blockDim.x) {
-    const double* S = ns + (int64_t)n * PDF_NNS;
     float* x = X + (int64_t)n * kIn;
-    x[0] = (float)S[0]; x[1] = (float)S[1]; x[2] = (float)S[2];
-    for (int q = 0; q < 6; ++q) x[3 + q] = (float)S[5 + q];
-    x[9] = (float)S[3];
-    x[10] = (float)wall_d[n];
+    for (int q = 0; q < 9; ++q) x[q] = (float)rhs[(int64_t)q * n_nodes + n];
+    const double l2 = fmax(L2[(int64_t)2 * n_nodes + n], 1e-300);
+    double area = 0.0;
+    const int32_t b = nse_off[n], c = nse_off[n + 1] - b;
+    for (int32_t i = b; i < b + c; ++i) area += 0.5 * geo[nse[i]].two_area;
+    const double h2 = c > 0 ? area / (double)c : 1.0;
+    x[9] = (float)(wall_d[n] / sqrt(l2));
+    x[10] = (float)log(l2 / h2);
     if (wp && Y)
-      for (int q = 0; q < kOut; ++q) Y[(int64_t)n * kOut + q] = (float)wp[(int64_t)q * n_nodes + n];
+      for (int q = 0; q < kOut; ++q)
+        Y[(int64_t)n * kOut + q] = (float)(wp[(int64_t)q * n_nodes + n] - rhs[(int64_t)q * n_nodes + n]);
   }
 }
 
-__global__ void k_mlp_to_wp(int32_t n_nodes, const float* __restrict__ Y, double* __restrict__ wp) {
+// A training batch: row i of (Xb, Yb) is row r_i of (X, Y), r_i drawn
+// uniformly from [0, n) by Philox4x32-10 (key seed, counter (i, step, 0, 4)):
+// the top 32 bits of word 0 times n, shifted down.
+__global__ void k_mlp_batch(const float* __restrict__ X, const float* __restrict__ Y, int64_t n, uint64_t seed,
+                            uint32_t step, int64_t batch, float* __restrict__ Xb, float* __restrict__ Yb) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < batch; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t c[4] = {(uint32_t)i, step, 0u, 4u};
+    philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const int64_t r = (int64_t)(((uint64_t)c[0] * (uint64_t)n) >> 32);
+    for (int q = 0; q < kIn; ++q) Xb[i * kIn + q] = X[r * kIn + q];
+    for (int q = 0; q < kOut; ++q) Yb[i * kOut + q] = Y[r * kOut + q];
+  }
+}
+
+// wp = rhs + the network's correction.
+__global__ void k_mlp_to_wp(int32_t n_nodes, const float* __restrict__ Y, const double* __restrict__ rhs,
+                            double* __restrict__ wp) {
   for (int32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < n_nodes; n += gridDim.x * blockDim.x)
-    for (int q = 0; q < kOut; ++q) wp[(int64_t)q * n_nodes + n] = (double)Y[(int64_t)n * kOut + q];
+    for (int q = 0; q < kOut; ++q)
+      wp[(int64_t)q * n_nodes + n] = rhs[(int64_t)q * n_nodes + n] + (double)Y[(int64_t)n * kOut + q];
 }
 
 // Standardization from data: means and 1/std of inputs, means and std of targets.
@@ -604,27 +633,47 @@ extern "C" pdf_status pdf_mlp_train_step(pdf_mlp* M, const float* X, const float
   return mlp_pass(M, X, Y, n, lr, 1, loss, nullptr, (cudaStream_t)stream);
 }
 
-extern "C" pdf_status pdf_mlp_features(pdf_particles* p, const pdf_mesh* m, const double* wp, float* X, float* Y,
-                                       void* stream) {
-  if (!p || !m || p->mesh != m || !X) return fail(PDF_EINVAL, "pdf_mlp_features: bad arguments");
-  if (!p->have_stats) return fail(PDF_ESTATE, "pdf_mlp_features: call pdf_estimate_stats first");
+extern "C" pdf_status pdf_mlp_batch(const float* X, const float* Y, int64_t n, uint64_t seed, uint32_t step,
+                                    int64_t batch, float* Xb, float* Yb, void* stream) {
+  if (!X || !Y || !Xb || !Yb || n < 1 || n > (int64_t)UINT32_MAX || batch < 1)
+    return fail(PDF_EINVAL, "pdf_mlp_batch: bad arguments");
   cudaStream_t st = (cudaStream_t)stream;
-  const int32_t nn = m->d.n_nodes;
-  PDF_KERNEL("k_mlp_features", st, k_mlp_features<<<(nn + 255) / 256, 256, 0, st>>>(nn, p->ns, m->rx.wall_d, wp, X, Y));
+  const int blocks = (int)std::min<int64_t>((batch + 255) / 256, 4096);
+  PDF_KERNEL("k_mlp_batch", st, k_mlp_batch<<<blocks, 256, 0, st>>>(X, Y, n, seed, step, batch, Xb, Yb));
   return PDF_OK;
 }
 
-extern "C" pdf_status pdf_mlp_guess(const pdf_mlp* M, pdf_particles* p, const pdf_mesh* m, double* wp,
-                                    float* scratch, void* stream) {
-  if (!M || !p || !m || p->mesh != m || !wp || !scratch) return fail(PDF_EINVAL, "pdf_mlp_guess: bad arguments");
+extern "C" pdf_status pdf_mlp_features(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,
+                                       const double* wp, float* X, float* Y, void* stream) {
+  if (!p || !m || p->mesh != m || !params || !X) return fail(PDF_EINVAL, "pdf_mlp_features: bad arguments");
+  if (!p->have_stats) return fail(PDF_ESTATE, "pdf_mlp_features: call pdf_estimate_stats first");
+  cudaStream_t st = (cudaStream_t)stream;
+  const double *rhs = nullptr, *L2 = nullptr;
+  pdf_status s = relax_fields(p, params, st, &rhs, &L2);
+  if (s != PDF_OK) return s;
+  const int32_t nn = m->d.n_nodes;
+  PDF_KERNEL("k_mlp_features", st, k_mlp_features<<<(nn + 255) / 256, 256, 0, st>>>(
+                                       nn, rhs, L2, m->rx.wall_d, m->d.nse_off, m->d.nse, m->d.geo, wp, X, Y));
+  return PDF_OK;
+}
+
+extern "C" pdf_status pdf_mlp_guess(const pdf_mlp* M, pdf_particles* p, const pdf_mesh* m,
+                                    const pdf_model_params* params, double* wp, float* scratch, void* stream) {
+  if (!M || !p || !m || p->mesh != m || !params || !wp || !scratch)
+    return fail(PDF_EINVAL, "pdf_mlp_guess: bad arguments");
   if (!p->have_stats) return fail(PDF_ESTATE, "pdf_mlp_guess: call pdf_estimate_stats first");
   cudaStream_t st = (cudaStream_t)stream;
+  const double *rhs = nullptr, *L2 = nullptr;
+  pdf_status s = relax_fields(p, params, st, &rhs, &L2);
+  if (s != PDF_OK) return s;
   const int32_t nn = m->d.n_nodes;
   float* X = scratch;
   float* Y = scratch + (size_t)nn * kIn;
-  PDF_KERNEL("k_mlp_features", st, k_mlp_features<<<(nn + 255) / 256, 256, 0, st>>>(nn, p->ns, m->rx.wall_d, nullptr, X, nullptr));
-  pdf_status s = pdf_mlp_forward(M, X, nn, Y, stream);
+  PDF_KERNEL("k_mlp_features", st, k_mlp_features<<<(nn + 255) / 256, 256, 0, st>>>(
+                                       nn, rhs, L2, m->rx.wall_d, m->d.nse_off, m->d.nse, m->d.geo, nullptr, X,
+                                       nullptr));
+  s = pdf_mlp_forward(M, X, nn, Y, stream);
   if (s != PDF_OK) return s;
-  PDF_KERNEL("k_mlp_to_wp", st, k_mlp_to_wp<<<(nn + 255) / 256, 256, 0, st>>>(nn, Y, wp));
+  PDF_KERNEL("k_mlp_to_wp", st, k_mlp_to_wp<<<(nn + 255) / 256, 256, 0, st>>>(nn, Y, rhs, wp));
   return PDF_OK;
 }

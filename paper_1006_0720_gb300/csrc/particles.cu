@@ -236,6 +236,11 @@ static void free_particles(pdf_particles* p) {
     if (H.out) cudaStreamDestroy(H.out);
     if (H.start) cudaEventDestroy(H.start);
     if (H.done) cudaEventDestroy(H.done);
+    for (int b = 0; b < 2; ++b) {
+      if (H.free_in[b]) cudaEventDestroy(H.free_in[b]);
+      if (H.free_out[b]) cudaEventDestroy(H.free_out[b]);
+      cudaFree(H.stage_in[b]); cudaFree(H.stage_out[b]); cudaFree(H.stage_ie[b]); cudaFree(H.stage_oe[b]);
+    }
     for (int k = 0; k < kHostChunks; ++k) {
       if (H.loaded[k]) cudaEventDestroy(H.loaded[k]);
       if (H.stepped[k]) cudaEventDestroy(H.stepped[k]);
@@ -461,17 +466,42 @@ pdf_status host_io_init(pdf_particles* p) {
     e = cudaEventCreateWithFlags(&H.loaded[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&H.stepped[k], cudaEventDisableTiming);
   }
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    e = cudaEventCreateWithFlags(&H.free_in[b], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&H.free_out[b], cudaEventDisableTiming);
+  }
   return e == cudaSuccess ? PDF_OK : cuda_fail(e, "pdf_step_host: streams and events");
 }
 
+pdf_status host_io_stage(pdf_particles* p, int64_t cap) {
+  HostIo& H = p->hio;
+  if (H.cap >= cap) return PDF_OK;
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(H.stage_in[b]); cudaFree(H.stage_out[b]); cudaFree(H.stage_ie[b]); cudaFree(H.stage_oe[b]);
+    H.stage_in[b] = H.stage_out[b] = nullptr;
+    H.stage_ie[b] = H.stage_oe[b] = nullptr;
+  }
+  H.cap = 0;
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    e = cudaMalloc((void**)&H.stage_in[b], sizeof(double) * 7 * (size_t)cap);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&H.stage_out[b], sizeof(double) * 7 * (size_t)cap);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&H.stage_ie[b], sizeof(int32_t) * (size_t)cap);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&H.stage_oe[b], sizeof(int32_t) * (size_t)cap);
+  }
+  if (e != cudaSuccess) return fail(PDF_ENOMEM, "pdf_step_host: staging buffers");
+  H.cap = cap;
+  return PDF_OK;
+}
+
 pdf_status state_in_range(pdf_particles* p, double* const in[7], const int32_t* ie, int64_t beg, int64_t cnt,
-                          unsigned long long* bad, int blocks, cudaStream_t st) {
+                          unsigned long long* bad, int blocks, cudaStream_t st, int64_t io_off) {
   p->have_cond = false;  // the conditioned means follow the old slot order
   StateIn S;
   S.n = cnt;
   S.pid0 = beg;
-  for (int i = 0; i < 7; ++i) S.in[i] = in[i] + beg;
-  S.ie = ie + beg;
+  for (int i = 0; i < 7; ++i) S.in[i] = in[i] + io_off;
+  S.ie = ie + io_off;
   S.x = p->x + beg;
   S.y = p->y + beg;
   fx::df* dd[5] = {p->u, p->v, p->w, p->om, p->ps};
@@ -488,7 +518,7 @@ pdf_status state_in_range(pdf_particles* p, double* const in[7], const int32_t* 
 }
 
 pdf_status state_out_range(const pdf_particles* p, double* const out[7], int32_t* oe, int64_t beg, int64_t cnt,
-                           int blocks, cudaStream_t st) {
+                           int blocks, cudaStream_t st, int64_t io_off) {
   StateOut S;
   S.n = cnt;
   S.inv = nullptr;
@@ -501,8 +531,8 @@ pdf_status state_out_range(const pdf_particles* p, double* const out[7], int32_t
     S.f[k] = p->precision == PDF_FP64 ? nullptr : ff[k] + beg;
   }
   S.elem = p->elem + beg;
-  for (int i = 0; i < 7; ++i) S.o[i] = out[i] + beg;
-  S.oe = oe + beg;
+  for (int i = 0; i < 7; ++i) S.o[i] = out[i] + io_off;
+  S.oe = oe + io_off;
   PDF_KERNEL("k_state_out", st, k_state_out<<<blocks, 256, 0, st>>>(S));
   return PDF_OK;
 }

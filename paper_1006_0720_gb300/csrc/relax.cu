@@ -641,6 +641,20 @@ static pdf_status relax_amg_values(pdf_particles* P, cudaStream_t st) {
   return relax_amg_update(G, st);
 }
 
+// The nodal right-hand side [9][n_nodes] and L^2 [3][n_nodes] of the
+// relaxation for the particle set's statistics (the solve's own work space;
+// valid until its next call).
+pdf_status relax_fields(pdf_particles* P, const pdf_model_params* params, cudaStream_t st, const double** rhs,
+                        const double** L2) {
+  pdf_status s = relax_alloc(P);
+  if (s != PDF_OK) return s;
+  s = relax_prepare(P, params, st);
+  if (s != PDF_OK) return s;
+  *rhs = P->rx.f;
+  *L2 = P->rx.L2;
+  return PDF_OK;
+}
+
 }  // namespace pdfgb
 
 using namespace pdfgb;

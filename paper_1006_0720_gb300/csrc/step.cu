@@ -405,14 +405,23 @@ struct Draws {
   float g[8];
 };
 
+// The step's first Philox block: g0..g3 (dW_x, dW_y, dW'_1, dW'_2).
+__device__ __forceinline__ void draw_block0(const StepArgs& A, uint32_t id, Draws& d) {
+  gauss4(A.seed, id, A.step, 0u, kPurposeStep, &d.g[0]);
+}
+// The second block: g4, g5 (dW'_3, dW_omega); g6, g7 are not used.
+__device__ __forceinline__ void draw_block1(const StepArgs& A, uint32_t id, Draws& d) {
+  uint32_t c[4] = {id, A.step, 1u, kPurposeStep};
+  philox4x32_10(c, (uint32_t)A.seed, (uint32_t)(A.seed >> 32));
+  box_muller(c[0], c[1], &d.g[4], &d.g[5]);
+  d.g[6] = d.g[7] = 0.0f;
+}
+
 __device__ __forceinline__ Draws draw_step(const StepArgs& A, int64_t slot) {
   Draws d;
   const uint32_t id = (uint32_t)__ldg(A.pid + slot);
-  gauss4(A.seed, id, A.step, 0u, kPurposeStep, &d.g[0]);
-  uint32_t c[4] = {id, A.step, 1u, kPurposeStep};
-  philox4x32_10(c, (uint32_t)A.seed, (uint32_t)(A.seed >> 32));
-  box_muller(c[0], c[1], &d.g[4], &d.g[5]);  // g6, g7 are not used by the step
-  d.g[6] = d.g[7] = 0.0f;
+  draw_block0(A, id, d);
+  draw_block1(A, id, d);
   return d;
 }
 
@@ -685,6 +694,13 @@ __device__ __forceinline__ int certain_exit(const Screen& S) {
   return k;
 }
 
+__device__ __forceinline__ void prefetch_l1(const void* a) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+}
+__device__ __forceinline__ void prefetch_l2(const void* a) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
 // One element of the fixed-point neighbour walk:
 // kWalkInside (e holds the point), kWalkSlow (a wall or open-boundary edge,
 // or the 64-step cap: the FP64 walk finishes it) or kWalkMoved (e, Xn now
@@ -795,6 +811,43 @@ __device__ __forceinline__ bool walk_fx(const FxArgs& F, int32_t& e, int64_t& Xn
   }
 }
 
+// The first element of the walk screened ahead of the velocity update (its
+// geometry was prefetched with the row): kWalkInside when the FP32 screen
+// certainly places the new position in e, else the certain exit edge (0-2),
+// whose neighbour's geometry is then prefetched, or -1 (undecided).
+constexpr int kEarlyInside = 3;
+__device__ __forceinline__ int early_screen(const FxArgs& F, int32_t e, int64_t Xn, int64_t Yn) {
+  const int4* src = reinterpret_cast<const int4*>(F.geo + e);
+  const int4 a = __ldg(src), b = __ldg(src + 1), c = __ldg(src + 2);
+  const int4 d = __ldg(src + 3);
+  const int2 f = __ldg(reinterpret_cast<const int2*>(src + 4));
+  const Screen S = screen_xy(((int64_t)(uint32_t)a.y << 32) | (uint32_t)a.x,
+                             ((int64_t)(uint32_t)a.w << 32) | (uint32_t)a.z, __int_as_float(b.x),
+                             __int_as_float(b.z), __int_as_float(c.x), __int_as_float(c.z), __int_as_float(d.x), Xn, Yn);
+  if (certain_inside(S)) return kEarlyInside;
+  const int k = certain_exit(S);
+  if (k >= 0) {
+    const int32_t nbr = k == 0 ? d.z : (k == 1 ? d.w : f.x);
+    if (nbr >= 0) prefetch_l1(F.geo + nbr);
+  }
+  return k;
+}
+
+// The walk after early_screen: an "inside" answer ends it at once, a
+// certain exit crosses without screening e again.
+__device__ __forceinline__ bool walk_fx_from(const FxArgs& F, int first, int32_t& e, int64_t& Xn, int64_t Yn,
+                                             int& steps, int& c_per, int& c_near, bool& reinj) {
+  if (first == kEarlyInside) return false;
+  if (first >= 0) {
+    const int4* src = reinterpret_cast<const int4*>(F.geo + e);
+    const int4 d = __ldg(src + 3);
+    const int2 f = __ldg(reinterpret_cast<const int2*>(src + 4));
+    const int r = cross_edge(F, first, d, f, e, Xn, steps, c_per, reinj);
+    if (r != kWalkMoved) return r == kWalkSlow;
+  }
+  return walk_fx(F, e, Xn, Yn, steps, c_per, c_near, reinj);
+}
+
 // The FP64 walk (walls, open boundaries, the step cap), out of line and by
 // value for the fixed-point kernels.
 struct SlowWalk {
@@ -844,12 +897,6 @@ __device__ __forceinline__ bool small_move(const fx::acc& a) { return fabsf(a.h)
 // FP64 back to the stored forms after the FP64 walk (the wall fall-back).
 __device__ __forceinline__ bool pos_fits(double x) { return fabs(x) < 64.0; }
 
-__device__ __forceinline__ void prefetch_l1(const void* a) {
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
-}
-__device__ __forceinline__ void prefetch_l2(const void* a) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
-}
 
 __global__ void __launch_bounds__(256, 4) k_step_fx(StepArgs A, FxArgs F) {
   int c_walk = 0, c_per = 0, c_om = 0, c_near = 0;
@@ -879,7 +926,11 @@ __global__ void __launch_bounds__(256, 4) k_step_fx(StepArgs A, FxArgs F) {
       prefetch_l2(A.elem + q);
       prefetch_l2(A.pid + q);
     }
-    const Draws D = draw_step(A, p);
+    // the first random block (dW_x, dW_y, dW'_1, dW'_2) gives the position;
+    // the second is drawn after the early screen below
+    Draws D;
+    const uint32_t id = (uint32_t)__ldg(A.pid + p);
+    draw_block0(A, id, D);
     const fx::df U[3] = {ld_state(A.u, p), ld_state(A.v, p), ld_state(A.w, p)};
     // position (eq. Lagrangian-position-exact): X + U^n dt + sqrt(2 nu) dW
     fx::acc ax, ay;
@@ -892,11 +943,16 @@ __global__ void __launch_bounds__(256, 4) k_step_fx(StepArgs A, FxArgs F) {
     // that its latency is hidden)
     const int near_noslip = __ldg(reinterpret_cast<const int*>(F.geo + e) + 18);
     if (!(small_move(ax) && small_move(ay))) {
+      draw_block1(A, id, D);
       merge(cs, advance_native_ool(A, p, D));
       continue;
     }
     int64_t Xn = A.x[p] + ax.fix(kF);
     const int64_t Yn = A.y[p] + ay.fix(kF);
+    // the new position against the old element now, so that the geometry
+    // of the neighbour it leaves into arrives during the SDE updates
+    const int first = early_screen(F, e, Xn, Yn);
+    draw_block1(A, id, D);
     // velocity prediction (eq. velocity-prediction): U + a dt
     // + sqrt(2 nu) dU_i/dx_j dW_j + G_ij (U_j - <U_j>) dt + sqrt(C0 eps) dW'_i
     const fx::df d0 = dsub(U[0], ldmean(R, 0));
@@ -948,7 +1004,7 @@ __global__ void __launch_bounds__(256, 4) k_step_fx(StepArgs A, FxArgs F) {
     // the step cap go to the FP64 walk
     int steps = 0;
     bool reinj = false;
-    const bool slow = walk_fx(F, e, Xn, Yn, steps, c_per, c_near, reinj);
+    const bool slow = walk_fx_from(F, first, e, Xn, Yn, steps, c_per, c_near, reinj);
     c_walk += steps;
     int64_t Xs = Xn, Ys = Yn;
     bool slow_noslip = false;
@@ -1328,12 +1384,12 @@ extern "C" pdf_status pdf_step_host(pdf_particles* p, const pdf_mesh* m, const p
   if (params && params->mix == PDF_MIX_IECM)
     return fail(PDF_EINVAL, "pdf_step_host: IECM needs the device-resident state (pdf_step)");
   double* io[7] = {x, y, u, v, w, om, ps};
-  double* view[7];
+  // page-locked host or device memory: the copies then run asynchronously
   for (int i = 0; i < 7; ++i)
-    if (!(view[i] = static_cast<double*>(state_kernel_view(io[i]))))
+    if (!state_kernel_view(io[i]))
       return fail(PDF_EINVAL, "pdf_step_host: the state arrays must be page-locked host or device memory");
-  int32_t* ve = static_cast<int32_t*>(state_kernel_view(elem));
-  if (!ve) return fail(PDF_EINVAL, "pdf_step_host: the state arrays must be page-locked host or device memory");
+  if (!state_kernel_view(elem))
+    return fail(PDF_EINVAL, "pdf_step_host: the state arrays must be page-locked host or device memory");
   cudaStream_t st = (cudaStream_t)stream;
   pdf_status s = step_prepare(p, m, params, wp, elem_coeff, true, st);
   if (s != PDF_OK) return s;
@@ -1343,11 +1399,18 @@ extern "C" pdf_status pdf_step_host(pdf_particles* p, const pdf_mesh* m, const p
   unsigned long long* bad = reinterpret_cast<unsigned long long*>(p->counters + 15);
   PDF_CUDA(cudaMemsetAsync(bad, 0, sizeof(long long), st));
   // the state is loaded in particle-id order (slot = id), so that every
-  // chunk's loads and stores are contiguous ranges on both sides
+  // chunk is a contiguous range of the caller's arrays.  Per chunk: the
+  // copy engines bring its 8 arrays into a device staging buffer (stream
+  // in), the compute stream converts them into the slots, steps them and
+  // converts them back into an outgoing staging buffer, and the copy
+  // engines write that back (stream out); two staging buffers per
+  // direction, so that chunk k + 1 moves while chunk k is stepped.
   const StepLaunch L = step_args(p, m, params, step);
   const int64_t n = p->n;
   const int K = (int)std::max<int64_t>(1, std::min<int64_t>(kHostChunks, n / 65536));
   const int64_t chunk = (n + K - 1) / K;
+  s = host_io_stage(p, chunk);
+  if (s != PDF_OK) return s;
   const int io_blocks = host_io_blocks();
   PDF_CUDA(cudaEventRecord(H.start, st));
   PDF_CUDA(cudaStreamWaitEvent(H.in, H.start, 0));
@@ -1355,19 +1418,36 @@ extern "C" pdf_status pdf_step_host(pdf_particles* p, const pdf_mesh* m, const p
   for (int k = 0; k < K; ++k) {
     const int64_t beg = k * chunk, cnt = std::min<int64_t>(chunk, n - beg);
     if (cnt <= 0) break;
-    s = state_in_range(p, view, ve, beg, cnt, bad, io_blocks, H.in);
-    if (s != PDF_OK) return s;
+    const int b = k & 1;
+    double* sin[7];
+    double* sout[7];
+    for (int i = 0; i < 7; ++i) {
+      sin[i] = H.stage_in[b] + i * H.cap;
+      sout[i] = H.stage_out[b] + i * H.cap;
+    }
+    // in: the buffer is free once the compute stream has read chunk k - 2
+    if (k >= 2) PDF_CUDA(cudaStreamWaitEvent(H.in, H.free_in[b], 0));
+    for (int i = 0; i < 7; ++i)
+      PDF_CUDA(cudaMemcpyAsync(sin[i], io[i] + beg, sizeof(double) * cnt, cudaMemcpyDefault, H.in));
+    PDF_CUDA(cudaMemcpyAsync(H.stage_ie[b], elem + beg, sizeof(int32_t) * cnt, cudaMemcpyDefault, H.in));
     PDF_CUDA(cudaEventRecord(H.loaded[k], H.in));
+    // compute: staging -> slots, the step, slots -> staging
     PDF_CUDA(cudaStreamWaitEvent(st, H.loaded[k], 0));
-    // two blocks per SM: the step kernel's blocks would otherwise fill the
-    // register files and hold off the load and store kernels, which keep
-    // the host link busy while it runs
-    s = L.run(beg, cnt, st, 2);
+    s = state_in_range(p, sin, H.stage_ie[b], beg, cnt, bad, io_blocks, st, 0);
+    if (s != PDF_OK) return s;
+    PDF_CUDA(cudaEventRecord(H.free_in[b], st));
+    s = L.run(beg, cnt, st);
+    if (s != PDF_OK) return s;
+    if (k >= 2) PDF_CUDA(cudaStreamWaitEvent(st, H.free_out[b], 0));
+    s = state_out_range(p, sout, H.stage_oe[b], beg, cnt, io_blocks, st, 0);
     if (s != PDF_OK) return s;
     PDF_CUDA(cudaEventRecord(H.stepped[k], st));
+    // out: the copy engines write the chunk back
     PDF_CUDA(cudaStreamWaitEvent(H.out, H.stepped[k], 0));
-    s = state_out_range(p, view, ve, beg, cnt, io_blocks, H.out);
-    if (s != PDF_OK) return s;
+    for (int i = 0; i < 7; ++i)
+      PDF_CUDA(cudaMemcpyAsync(io[i] + beg, sout[i], sizeof(double) * cnt, cudaMemcpyDefault, H.out));
+    PDF_CUDA(cudaMemcpyAsync(elem + beg, H.stage_oe[b], sizeof(int32_t) * cnt, cudaMemcpyDefault, H.out));
+    PDF_CUDA(cudaEventRecord(H.free_out[b], H.out));
   }
   PDF_CUDA(cudaEventRecord(H.done, H.out));
   PDF_CUDA(cudaStreamWaitEvent(st, H.done, 0));
