@@ -63,19 +63,30 @@ def _kernel_sha():
     return h.hexdigest()[:16]
 
 
-def _traffic_from_profile():
-    """DRAM bytes per k_step launch from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
+def _profile_numbers():
+    """From the committed ncu summary of k_step, if it was taken on the
+    current kernel source: DRAM bytes per launch at the benchmark size and
+    warp instructions per particle; else an empty dict."""
     path = os.path.join(ROOT, "profiles", "k_step_fx_channel_200x400.md")
     try:
         text = open(path).read()
     except OSError:
-        return None
+        return {}
     m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
-    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m_sha or not m_b or m_sha.group(1) != _kernel_sha():
-        return None
-    return float(m_b.group(1))
+    if not m_sha or m_sha.group(1) != _kernel_sha():
+        return {}
+    out = {}
+    for key in ("dram_bytes_per_launch", "warp_inst_per_particle"):
+        m = re.search(key + r":\s*([0-9.eE+]+)", text)
+        if m:
+            out[key] = float(m.group(1))
+    return out
+
+
+def issue_peak(sm_mhz):
+    """Warp instructions per second the SMs can issue: 152 SMs x 4
+    schedulers x one instruction per clock."""
+    return 152 * 4 * sm_mhz * 1e6
 
 
 class ClockSampler:
@@ -353,9 +364,26 @@ def run_gpu(args):
     k_avg_ms = k_ms / k_launch if k_launch else float("nan")
     k_bytes = K_STEP_BYTES_PER_PARTICLE * n + K_STEP_BYTES_PER_ELEMENT * gm.n_tri
     achieved = k_bytes / (k_avg_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_step", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": _traffic_from_profile(), "peak_source": peak_kind,
-                "bytes_per_launch_alg": k_bytes, "ms_per_launch": k_avg_ms}
+    prof = _profile_numbers()
+    hbm = {"bound": "hbm", "kernel": "k_step", "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak, "traffic": prof.get("dram_bytes_per_launch"), "peak_source": peak_kind,
+           "bytes_per_launch_alg": k_bytes, "ms_per_launch": k_avg_ms,
+           "roof_ms": k_bytes / (peak * 1e9) * 1e3}
+    roofline = hbm
+    if "warp_inst_per_particle" in prof and clk.get("sm_mhz"):
+        # the instruction-issue roof: ncu's warp instructions per launch over
+        # what 152 SMs x 4 schedulers issue at the sampled clock
+        winst = prof["warp_inst_per_particle"] * n
+        ipk = issue_peak(clk["sm_mhz"])
+        issue = {"bound": "alu", "kernel": "k_step", "achieved": winst / (k_avg_ms * 1e-3), "peak": ipk,
+                 "unit": "warp-inst/s", "frac": winst / (k_avg_ms * 1e-3) / ipk,
+                 "traffic": prof.get("dram_bytes_per_launch"), "warp_inst_per_launch": winst,
+                 "peak_source": "152 SMs x 4 schedulers x sampled SM clock", "ms_per_launch": k_avg_ms,
+                 "roof_ms": winst / ipk * 1e3}
+        if issue["roof_ms"] > hbm["roof_ms"]:
+            roofline = dict(issue, hbm=hbm)
+        else:
+            roofline = dict(hbm, issue=issue)
     step_frac = STEP_BYTES_PER_PARTICLE * (n * args.steps / (ms * 1e-3)) / (peak * 1e9)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,

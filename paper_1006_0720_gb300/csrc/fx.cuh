@@ -111,6 +111,118 @@ FX_HD df from_double(double x) {
 }
 FX_HD double to_double(df a) { return (double)a.h + (double)a.l; }
 
+// The same two conversions without FP64 arithmetic (integer rounding of the
+// mantissas), bit-identical to from_double / to_double; outside the range
+// where every part is a normal FP32 number (|x| below 2^-73 or from 2^126
+// on, a low part far below the high part's last bit) they take the FP64
+// expressions.  Used by the state transfers, which would otherwise run five
+// FP64 additions and ten FP64 conversions per particle on the slow FP64
+// pipe.
+FX_HD df d2df_rn(uint64_t b) {
+  const int e = d_exp(b);
+  if (e < 1023 - 73 || e >= 1023 + 126) {
+    double x;
+    memcpy(&x, &b, 8);
+    return from_double(x);
+  }
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  const uint64_t M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);  // 53 bits
+  uint64_t hm = M >> 29;                                        // 24 bits
+  const uint64_t rem = M & ((1ull << 29) - 1);
+  if (rem > (1ull << 28) || (rem == (1ull << 28) && (hm & 1))) hm += 1;  // nearest, ties to even
+  const int64_t r = (int64_t)M - (int64_t)(hm << 29);  // x - h in units of 2^(e-1075), |r| <= 2^28
+  int eh = e - 1023 + 127;
+  if (hm == (1ull << 24)) {
+    hm >>= 1;
+    eh += 1;
+  }
+  df out;
+  out.h = bits_f(sign | ((uint32_t)eh << 23) | ((uint32_t)hm & 0x7FFFFFu));
+  if (r == 0) {
+    out.l = 0.0f;  // x - h == +0 under round to nearest
+    return out;
+  }
+  const uint32_t ls = sign ^ (r < 0 ? 0x80000000u : 0u);
+  uint64_t a = (uint64_t)(r < 0 ? -r : r);
+  const int nb = 64 - FX_CLZ64(a);  // <= 29
+  int el = e - 1075 + (nb - 1) + 127;
+  uint32_t lm;
+  if (nb <= 24) {
+    lm = (uint32_t)(a << (24 - nb));
+  } else {
+    const int sh = nb - 24;
+    uint64_t q = a >> sh;
+    const uint64_t rr = a & ((1ull << sh) - 1), hf = 1ull << (sh - 1);
+    if (rr > hf || (rr == hf && (q & 1))) q += 1;
+    if (q == (1ull << 24)) {
+      q >>= 1;
+      el += 1;
+    }
+    lm = (uint32_t)q;
+  }
+  out.l = bits_f(ls | ((uint32_t)el << 23) | (lm & 0x7FFFFFu));
+  return out;
+}
+
+// An FP32 value's FP64 bits (exact), without an FP64 conversion for normal
+// numbers and zeros.
+FX_HD uint64_t f2d_bits(float f) {
+  const uint32_t b = f_bits(f);
+  const int e = (int)((b >> 23) & 0xFF);
+  const uint64_t sign = (uint64_t)(b >> 31) << 63;
+  if ((b & 0x7FFFFFFFu) == 0) return sign;
+  if (e == 0 || e == 255) {
+    const double x = (double)f;
+    uint64_t r;
+    memcpy(&r, &x, 8);
+    return r;
+  }
+  return sign | ((uint64_t)(e - 127 + 1023) << 52) | ((uint64_t)(b & 0x7FFFFFu) << 29);
+}
+
+FX_HD uint64_t df2d_rn(df a) {
+  const uint32_t hb = f_bits(a.h), lb = f_bits(a.l);
+  const int eh = (int)((hb >> 23) & 0xFF), el = (int)((lb >> 23) & 0xFF);
+  const bool lzero = (lb & 0x7FFFFFFFu) == 0;
+  const int D = eh - el;
+  if (eh == 0 || eh == 255 || (!lzero && (el == 0 || el == 255 || D < 0 || D > 38))) {
+    const double x = to_double(a);
+    uint64_t r;
+    memcpy(&r, &x, 8);
+    return r;
+  }
+  const uint64_t hsign = (uint64_t)(hb >> 31) << 63;
+  const uint64_t H = (uint64_t)((hb & 0x7FFFFFu) | 0x800000u);
+  if (lzero) return hsign | ((uint64_t)(eh - 127 + 1023) << 52) | ((H & 0x7FFFFFu) << 29);
+  const uint64_t L = (uint64_t)((lb & 0x7FFFFFu) | 0x800000u);
+  // the exact sum S 2^(eh - 188): h at bits 61..38, l aligned below it
+  int64_t S = (int64_t)(H << 38);
+  const int64_t La = (int64_t)(L << (38 - D));
+  S = ((hb >> 31) == (lb >> 31)) ? S + La : S - La;
+  uint64_t sgn = hsign;
+  if (S < 0) {
+    S = -S;
+    sgn ^= 1ull << 63;
+  }
+  if (S == 0) return 0ull;
+  const uint64_t u = (uint64_t)S;
+  int nb = 64 - FX_CLZ64(u);
+  uint64_t q;
+  if (nb <= 53) {
+    q = u << (53 - nb);
+  } else {
+    const int sh = nb - 53;
+    q = u >> sh;
+    const uint64_t rr = u & ((1ull << sh) - 1), hf = 1ull << (sh - 1);
+    if (rr > hf || (rr == hf && (q & 1))) q += 1;
+    if (q == (1ull << 53)) {
+      q >>= 1;
+      nb += 1;
+    }
+  }
+  return sgn | ((uint64_t)(nb + eh + 834) << 52) | (q & 0xFFFFFFFFFFFFFull);
+}
+
 // Knuth's TwoSum: s + e == a + b exactly.
 FX_HD df two_sum(float a, float b) {
   const float s = FX_ADD(a, b);

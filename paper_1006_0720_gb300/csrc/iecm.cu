@@ -304,7 +304,7 @@ pdf_status iecm_cond(pdf_particles* P, const int32_t* seg, const int32_t* order,
 __global__ void k_cond_to_f64(const fx::df* __restrict__ a, const int32_t* __restrict__ pid,
                               double* __restrict__ b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[pid[i]] = fx::to_double(a[i]);
+    b[pid[i]] = __longlong_as_double((long long)fx::df2d_rn(a[i]));
 }
 
 }  // namespace pdfgb

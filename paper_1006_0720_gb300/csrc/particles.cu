@@ -100,13 +100,13 @@ __global__ void k_fix_to_f64(const int64_t* __restrict__ a, const int32_t* __res
 __global__ void k_df_to_f64(const fx::df* __restrict__ a, const int32_t* __restrict__ pid,
                             double* __restrict__ b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[pid[i]] = fx::to_double(a[i]);
+    b[pid[i]] = __longlong_as_double((long long)fx::df2d_rn(a[i]));
 }
 
 __global__ void k_f32_to_f64(const float* __restrict__ a, const int32_t* __restrict__ pid,
                              double* __restrict__ b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[pid[i]] = (double)a[i];
+    b[pid[i]] = __longlong_as_double((long long)fx::f2d_bits(a[i]));
 }
 
 __global__ void k_elem_by_id(const int32_t* __restrict__ a, const int32_t* __restrict__ pid,
@@ -136,12 +136,12 @@ __global__ void k_f64_to_fix(const double* __restrict__ a, int64_t* __restrict__
 
 __global__ void k_f64_to_df(const double* __restrict__ a, fx::df* __restrict__ b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = fx::from_double(a[i]);
+    b[i] = fx::d2df_rn((uint64_t)__double_as_longlong(a[i]));
 }
 
 __global__ void k_f64_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = __double2float_rn(a[i]);
+    b[i] = fx::d2df_rn((uint64_t)__double_as_longlong(a[i])).h;  // the FP64 -> FP32 rounding
 }
 
 // Whole-state transfers in one pass, for caller buffers the kernels can
@@ -172,7 +172,8 @@ __global__ void k_state_out(StateOut S) {
     if (S.o[1]) S.o[1][q] = __longlong_as_double((long long)fx::fix2d(S.y[i], kPosF));
 #pragma unroll
     for (int k = 0; k < 5; ++k)
-      if (S.o[2 + k]) S.o[2 + k][q] = S.d[k] ? fx::to_double(S.d[k][i]) : (double)S.f[k][i];
+      if (S.o[2 + k])
+        S.o[2 + k][q] = __longlong_as_double((long long)(S.d[k] ? fx::df2d_rn(S.d[k][i]) : fx::f2d_bits(S.f[k][i])));
     if (S.oe) S.oe[q] = S.elem[i];
   }
 }
@@ -202,9 +203,11 @@ __global__ void k_state_in(StateIn S) {
     }
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-      const double v = S.in[2 + k][i];
-      if (S.d[k]) S.d[k][i] = fx::from_double(v);
-      else S.f[k][i] = __double2float_rn(v);
+      // the stored forms without FP64 instructions (bit-identical to
+      // from_double and to the FP64 -> FP32 rounding)
+      const fx::df v = fx::d2df_rn((uint64_t)__double_as_longlong(S.in[2 + k][i]));
+      if (S.d[k]) S.d[k][i] = v;
+      else S.f[k][i] = v.h;
     }
     S.elem[i] = S.ie[i];
     S.pid[i] = (int32_t)(S.pid0 + i);

@@ -76,6 +76,56 @@ int main(){
       bad++;
     }
   }
+  // FP64-free conversions: bit-identical to from_double / to_double on
+  // doubles of every magnitude, exact floats, ties of the FP32 rounding and
+  // arbitrary (also unnormalized) pairs
+  std::uniform_real_distribution<double> U01(0.0, 1.0);
+  for (int i = 0; i < 2000000; i++) {
+    double x;
+    const int kind = (int)(g() % 6);
+    const double sgn = (g() & 1) ? 1.0 : -1.0;
+    if (kind == 0) x = sgn * (1.0 + U01(g)) * std::pow(2.0, (int)(g() % 260) - 130);
+    else if (kind == 1) x = sgn * (double)(float)(U01(g) * std::pow(2.0, (int)(g() % 60) - 30));
+    else if (kind == 2) {  // a float plus exactly half its ulp (a tie), or a quarter
+      const float f = (float)(1.0 + U01(g)) * (float)std::pow(2.0, (int)(g() % 40) - 20);
+      x = sgn * ((double)f + std::ldexp(1.0, (int)((fx::f_bits(f) >> 23) & 0xFF) - 127 - 24 - (int)(g() % 2)));
+    } else if (kind == 3) x = sgn * ldexp(1.0 + U01(g), -(int)(g() % 80));
+    else if (kind == 4) x = sgn * ((double)(float)U01(g) + ldexp(U01(g), -(int)(30 + g() % 40)));
+    else x = 0.0;
+    uint64_t xb;
+    memcpy(&xb, &x, 8);
+    const fx::df a = fx::from_double(x), b = fx::d2df_rn(xb);
+    if (fx::f_bits(a.h) != fx::f_bits(b.h) || fx::f_bits(a.l) != fx::f_bits(b.l)) {
+      if (bad < 5) printf("d2df_rn %.17g: %.9g %.9g vs %.9g %.9g\n", x, a.h, a.l, b.h, b.l);
+      bad++;
+    }
+    const double back = fx::to_double(a);
+    uint64_t bb;
+    memcpy(&bb, &back, 8);
+    if (fx::df2d_rn(a) != bb) {
+      if (bad < 5) printf("df2d_rn %.17g\n", x);
+      bad++;
+    }
+    // FP32 -> FP64 bits
+    const float fl = (float)(sgn * U01(g) * std::pow(2.0, (int)(g() % 300) - 150));
+    const double fd = (double)fl;
+    uint64_t fdb;
+    memcpy(&fdb, &fd, 8);
+    if (fx::f2d_bits(fl) != fdb) {
+      if (bad < 5) printf("f2d_bits %.9g\n", fl);
+      bad++;
+    }
+    // arbitrary pairs (the low part of any size and sign)
+    const fx::df c = {(float)(sgn * (1.0 + U01(g)) * std::pow(2.0, (int)(g() % 200) - 100)),
+                      (float)(((g() & 1) ? 1.0 : -1.0) * (1.0 + U01(g)) * std::pow(2.0, (int)(g() % 200) - 100))};
+    const double cs = fx::to_double(c);
+    uint64_t cb;
+    memcpy(&cb, &cs, 8);
+    if (fx::df2d_rn(c) != cb) {
+      if (bad < 5) printf("df2d_rn pair %.9g %.9g\n", c.h, c.l);
+      bad++;
+    }
+  }
   printf("bad %d\n", bad);
   return bad != 0;
 }

@@ -2,7 +2,8 @@
 compiled for the host and checked against long double on 2M random inputs:
 FP64 -> fixed point rounds to nearest, fixed point -> FP64 is IEEE
 round-to-nearest-even, the double-float splits, products, sums and square
-roots keep 44+ bits."""
+roots keep 44+ bits, and the FP64-free conversions between FP64, FP32 and
+the stored double-float pairs are bit-identical to the FP64 expressions."""
 import os
 import shutil
 import subprocess

@@ -263,8 +263,12 @@ def test_tiny_mesh_edge_cases():
 def test_full_size_steps_and_statistics():
     """The measured workload (200x400 nodes, 100 particles per element, ~16M
     particles) in the launch configuration the benchmark times: the oracle
-    runs the same two steps at full size on its own, then every particle and
-    every element statistic is compared."""
+    runs the same two steps at full size on its own, then every particle,
+    every element statistic, every node statistic and derivative (80,000
+    nodes) and every coefficient row is compared, except where a particle
+    the oracle flagged within 1e-12 of a face took the other element: those
+    elements, and the nodes and rows that depend on them (one ring of
+    elements per averaging pass), are left out."""
     cfg = inputs.workload("channel_200x400_ppe100")
     m = inputs.channel_mesh(cfg["nx"], cfg["ny"], jitter=cfg["jitter"], seed=cfg["seed"])
     psi = inputs.scalar_slab(m, cfg["psi_slab_x"])
@@ -286,14 +290,39 @@ def test_full_size_steps_and_statistics():
     st = _host(gp.get_state())
     _compare_states(st, ost, "full-size, 2 steps", flagged)
     es = torch.empty((gm.n_tri, 13), dtype=torch.float64, device="cuda")
-    pg.pdf_estimate_stats(gp, gm, es)
-    es = es.cpu().numpy()
+    ns = torch.empty((gm.n_nodes, 12), dtype=torch.float64, device="cuda")
+    nd = torch.empty((gm.n_nodes, 10), dtype=torch.float64, device="cuda")
+    pg.pdf_estimate_stats(gp, gm, es, ns, nd)
+    es, ns, nd = es.cpu().numpy(), ns.cpu().numpy(), nd.cpu().numpy()
     touched = np.zeros(gm.n_tri, dtype=bool)
     moved = st["elem"] != ost["elem"]
     touched[st["elem"][moved]] = True
     touched[ost["elem"][moved]] = True
     assert np.array_equal(es[~touched, 0], oes[~touched, 0])
     assert_field_close(es[~touched, 1:], oes[~touched, 1:], "full-size element stats")
+    tri = np.asarray(m["tri"])
+    twin = np.asarray(m["twin"])
+
+    def ring(bad_e):
+        """Nodes of the given elements (periodic twins merged), and every
+        element holding such a node."""
+        bad_n = np.zeros(gm.n_nodes, dtype=bool)
+        bad_n[tri[bad_e].ravel()] = True
+        bad_n[twin[(twin >= 0) & bad_n]] = True
+        return bad_n, bad_n[tri].any(axis=1)
+
+    n1, e1 = ring(touched)   # node statistics
+    n2, e2 = ring(e1)        # first derivatives
+    n3, e3 = ring(e2)        # second derivatives
+    assert (~n3).mean() > 0.99
+    assert_field_close(ns[~n1], ons[~n1], "full-size node stats")
+    assert_field_close(nd[~n3, :6], ond[~n3, :6], "full-size node gradients")
+    assert_field_close(nd[~n3, 6:], ond[~n3, 6:], "full-size node second derivatives and d<vv>/dy")
+    # coefficient rows: element means of the three nodal coefficient sets
+    rows = pg.pdf_elem_coeff(gp, gm, p).cpu().numpy()
+    ref = oracle.elem_coeff(M, ons, ond, po)
+    _, e4 = ring(e3)
+    assert_field_close(rows[~e4], ref[~e4], "full-size coefficient rows")
 
 
 def test_fallbacks_for_values_outside_the_fixed_point_ranges():
