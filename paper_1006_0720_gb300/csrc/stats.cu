@@ -1,9 +1,9 @@
 // Particle-in-cell statistics (sec. 3.3) and derivatives (sec. 3.4).
 //
 // Grouping: a stable least-significant-digit radix sort of (element id,
-// particle id) pairs, 9-bit digits, in place of the paper's per-element
+// storage slot) pairs, 9-bit digits, in place of the paper's per-element
 // linked lists.  Stability makes the particle order inside every element
-// ascending in particle id, so the segmented reductions below always add
+// ascending in storage slot, so the segmented reductions below always add
 // the same numbers in the same order: the statistics are deterministic
 // without floating-point atomics.
 #include <algorithm>
@@ -32,10 +32,16 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const int32_t* __re
   for (int b = threadIdx.x; b < kBins; b += kSortThreads) h[b] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kTile;
+  // all sixteen keys in flight before the first count
+  int d[kItemsPerThread];
+#pragma unroll
   for (int r = 0; r < kItemsPerThread; ++r) {
     const int64_t i = base + r * kSortThreads + threadIdx.x;
-    if (i < n) atomicAdd(&h[(keys[i] >> shift) & (kBins - 1)], 1);
+    d[r] = (i < n) ? ((__ldg(keys + i) >> shift) & (kBins - 1)) : -1;
   }
+#pragma unroll
+  for (int r = 0; r < kItemsPerThread; ++r)
+    if (d[r] >= 0) atomicAdd(&h[d[r]], 1);
   __syncthreads();
   for (int b = threadIdx.x; b < kBins; b += kSortThreads) hist[(int64_t)b * n_tiles + blockIdx.x] = h[b];
 }
@@ -175,14 +181,33 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
   }
 }
 
-// seg[e] = first sorted position whose key >= e; seg[n_tri] = n.
+// seg[e] = first sorted position whose key >= e; seg[n_tri] = n.  Thread t
+// takes positions 4t .. 4t + 3 (one 16-byte load when the keys are 16-byte
+// aligned); the last quad also takes position n.
 __global__ void k_seg_offsets(const int32_t* __restrict__ keys, int64_t n, int32_t n_tri,
                               int32_t* __restrict__ seg) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t prev = (i == 0) ? -1 : keys[i - 1];
-    const int32_t cur = (i == n) ? n_tri : keys[i];
-    for (int32_t e = prev + 1; e <= cur; ++e) seg[e] = (int32_t)i;
+  const int64_t n4 = n / 4;
+  const bool vec = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= n4;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = 4 * t;
+    int32_t prev = (i0 == 0) ? -1 : keys[i0 - 1];
+    int32_t k[4];
+    if (t < n4 && vec) {
+      const int4 v = __ldg(reinterpret_cast<const int4*>(keys) + t);
+      k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) k[j] = (i0 + j < n) ? keys[i0 + j] : n_tri;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t i = i0 + j;
+      if (i > n) break;
+      const int32_t cur = k[j];  // n_tri at i == n
+      for (int32_t e = prev + 1; e <= cur; ++e) seg[e] = (int32_t)i;
+      prev = cur;
+    }
   }
 }
 
@@ -218,6 +243,34 @@ __device__ __forceinline__ void acc_xor(fx::acc& a, int o) {
   const float h = __shfl_xor_sync(0xffffffffu, a.h, o);
   const float l = __shfl_xor_sync(0xffffffffu, a.l, o);
   a.add(fx::df{h, l});
+}
+
+// a[i] for a lane-dependent i, by selects (no local-memory array)
+template <int N>
+__device__ __forceinline__ fx::df pick(const fx::df (&a)[N], int i) {
+  fx::df r = a[0];
+#pragma unroll
+  for (int q = 1; q < N; ++q)
+    if (i == q) r = a[q];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ fx::df pick_acc(const fx::acc (&a)[N], int i) {
+  fx::df r = fx::df{a[0].h, a[0].l};
+#pragma unroll
+  for (int q = 1; q < N; ++q)
+    if (i == q) r = fx::df{a[q].h, a[q].l};
+  return fx::df_norm(r);
+}
+
+// Central moment m (pairs uu, vv, ww, uv, uw, vw, psi psi) from the sums of
+// the deviations (s1) and of their products (s2): (S_ab - S_a S_b / N) / N.
+__device__ __forceinline__ double moment(const fx::acc (&s1)[5], const fx::acc (&s2)[7], int m, fx::df invN) {
+  const int a = m == 6 ? 4 : (m < 3 ? m : (m == 5 ? 1 : 0));
+  const int b = m == 6 ? 4 : (m < 3 ? m : (m == 3 ? 1 : 2));
+  const fx::df Sa = pick_acc(s1, a), Sb = pick_acc(s1, b);
+  const fx::df corr = fx::df_norm(fx::mul(fx::df_norm(fx::mul(Sa, Sb)), invN));
+  return __longlong_as_double((long long)fx::df2d(fx::df_norm(fx::mul(fx::sub(pick_acc(s2, m), corr), invN))));
 }
 
 template <typename T>
@@ -295,26 +348,19 @@ __global__ void __launch_bounds__(256) k_elem_stats_grp(const int32_t* __restric
         if ((q & (kStatLanes - 1)) == j) out[q] = 0.0;
       continue;
     }
-    // every lane of the group forms the 13 outputs (N, the five means, the
-    // seven central moments); lane j writes outputs j and j + 8
+    // the 13 outputs (N, the five means, the seven central moments) are
+    // shared out: lane j forms and writes outputs j and j + 8
+    // (lanes 1-5 a mean, lanes 0-4 and 6-7 one moment each: one pass of
+    // each formula per warp)
     const fx::df invN = fx::recip_df(N);
-    fx::df S[5];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) S[q] = s1[q].value();
-    double val[PDF_NES];
-    val[0] = (double)N;
-#pragma unroll
-    for (int q = 0; q < 5; ++q)
-      val[1 + q] = __longlong_as_double((long long)fx::df2d(fx::add(K[q], fx::df_norm(fx::mul(S[q], invN)))));
-    const int pa[7] = {0, 1, 2, 0, 0, 1, 4}, pb[7] = {0, 1, 2, 1, 2, 2, 4};
-#pragma unroll
-    for (int q = 0; q < 7; ++q) {
-      const fx::df corr = fx::df_norm(fx::mul(fx::df_norm(fx::mul(S[pa[q]], S[pb[q]])), invN));
-      val[6 + q] = __longlong_as_double((long long)fx::df2d(fx::df_norm(fx::mul(fx::sub(s2[q].value(), corr), invN))));
+    if (j == 0) out[0] = (double)N;
+    if (j >= 1 && j <= 5) {
+      const fx::df Kq = pick(K, j - 1);
+      const fx::df Sq = pick_acc(s1, j - 1);
+      out[j] = __longlong_as_double((long long)fx::df2d(fx::add(Kq, fx::df_norm(fx::mul(Sq, invN)))));
     }
-#pragma unroll
-    for (int q = 0; q < PDF_NES; ++q)
-      if ((q & (kStatLanes - 1)) == j) out[q] = val[q];
+    const int m = j < 5 ? j + 2 : j - 6;  // output 6 + m; lane 5 has none
+    if (j != 5) out[6 + m] = moment(s1, s2, m, invN);
   }
 }
 
@@ -457,7 +503,7 @@ pdf_status group_by_element(pdf_particles* P, cudaStream_t st) {
     vin = P->vals[cur];
     cur ^= 1;
   }
-  PDF_KERNEL("k_seg_offsets", st, k_seg_offsets<<<blocks_for(n + 1, 256), 256, 0, st>>>(kin, n, n_tri, P->seg););
+  PDF_KERNEL("k_seg_offsets", st, k_seg_offsets<<<blocks_for(n / 4 + 1, 256), 256, 0, st>>>(kin, n, n_tri, P->seg););
   P->sorted_pid = vin;
   P->sorted_key_slot = cur ^ 1;
   return PDF_OK;
@@ -631,7 +677,7 @@ pdf_status estimate_stats_with_buffers(pdf_particles* P, int32_t* keys_a, int32_
     kin = kout[pass];
     vin = vout[pass];
   }
-  PDF_KERNEL("k_seg_offsets", st, k_seg_offsets<<<blocks_for(n + 1, 256), 256, 0, st>>>(kin, n, M.n_tri, seg));
+  PDF_KERNEL("k_seg_offsets", st, k_seg_offsets<<<blocks_for(n / 4 + 1, 256), 256, 0, st>>>(kin, n, M.n_tri, seg));
   pdf_status s = elem_stats(P, seg, vin, st);
   if (s != PDF_OK) return s;
   s = node_stats_from_elements(P, st);
