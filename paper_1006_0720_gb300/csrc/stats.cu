@@ -314,8 +314,12 @@ __global__ void __launch_bounds__(256) k_elem_stats_grp(const int32_t* __restric
     for (int q = 0; q < 5; ++q) s1[q].init(fx::df{0.f, 0.f});
 #pragma unroll
     for (int q = 0; q < 7; ++q) s2[q].init(fx::df{0.f, 0.f});
+    // the slot of the lane's next particle is loaded one iteration ahead,
+    // so that its state loads do not wait for it
+    int32_t p_next = (pid && beg + j < end) ? __ldg(pid + beg + j) : beg + j;
     for (int32_t i = beg + j; i < end; i += kStatLanes) {
-      const int32_t p = pid ? __ldg(pid + i) : i;
+      const int32_t p = p_next;
+      p_next = (pid && i + kStatLanes < end) ? __ldg(pid + i + kStatLanes) : i + kStatLanes;
       // normalized, so that the dropped product of the low parts is below
       // 2^-48 of the product even when the deviation is far below the value
       const fx::df du = fx::sub(ld_df(u, p), K[0]);
