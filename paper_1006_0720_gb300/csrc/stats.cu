@@ -274,7 +274,7 @@ __device__ __forceinline__ double moment(const fx::acc (&s1)[5], const fx::acc (
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_elem_stats_grp(const int32_t* __restrict__ seg,
+__global__ void __launch_bounds__(256, 3) k_elem_stats_grp(const int32_t* __restrict__ seg,
                                                        const int32_t* __restrict__ pid, int32_t n_tri,
                                                        const T* __restrict__ u, const T* __restrict__ v,
                                                        const T* __restrict__ w, const T* __restrict__ om,
@@ -314,19 +314,21 @@ __global__ void __launch_bounds__(256) k_elem_stats_grp(const int32_t* __restric
     for (int q = 0; q < 5; ++q) s1[q].init(fx::df{0.f, 0.f});
 #pragma unroll
     for (int q = 0; q < 7; ++q) s2[q].init(fx::df{0.f, 0.f});
-    // the slot of the lane's next particle is loaded one iteration ahead,
-    // so that its state loads do not wait for it
-    int32_t p_next = (pid && beg + j < end) ? __ldg(pid + beg + j) : beg + j;
-    for (int32_t i = beg + j; i < end; i += kStatLanes) {
-      const int32_t p = p_next;
-      p_next = (pid && i + kStatLanes < end) ? __ldg(pid + i + kStatLanes) : i + kStatLanes;
+    // two particles per lane and iteration (positions i and i + 8), their
+    // slots loaded one iteration ahead, so that ten state loads are in
+    // flight before the first is needed; the sums still take the particles
+    // in the lane's order i, i + 8, i + 16, ...
+    auto slot = [&](int32_t i) { return pid ? __ldg(pid + i) : i; };
+    int32_t qa = beg + j < end ? slot(beg + j) : 0;
+    int32_t qb = beg + j + kStatLanes < end ? slot(beg + j + kStatLanes) : 0;
+    auto acc1 = [&](fx::df xu, fx::df xv, fx::df xw, fx::df xm, fx::df xp) {
       // normalized, so that the dropped product of the low parts is below
       // 2^-48 of the product even when the deviation is far below the value
-      const fx::df du = fx::sub(ld_df(u, p), K[0]);
-      const fx::df dv = fx::sub(ld_df(v, p), K[1]);
-      const fx::df dw = fx::sub(ld_df(w, p), K[2]);
-      const fx::df dm = fx::sub(ld_df(om, p), K[3]);
-      const fx::df dp = fx::sub(ld_df(ps, p), K[4]);
+      const fx::df du = fx::sub(xu, K[0]);
+      const fx::df dv = fx::sub(xv, K[1]);
+      const fx::df dw = fx::sub(xw, K[2]);
+      const fx::df dm = fx::sub(xm, K[3]);
+      const fx::df dp = fx::sub(xp, K[4]);
       s1[0].add(du); s1[1].add(dv); s1[2].add(dw); s1[3].add(dm); s1[4].add(dp);
       s2[0].add(fx::mul(du, du));
       s2[1].add(fx::mul(dv, dv));
@@ -335,6 +337,17 @@ __global__ void __launch_bounds__(256) k_elem_stats_grp(const int32_t* __restric
       s2[4].add(fx::mul(du, dw));
       s2[5].add(fx::mul(dv, dw));
       s2[6].add(fx::mul(dp, dp));
+    };
+    for (int32_t i = beg + j; i < end; i += 2 * kStatLanes) {
+      const int32_t pa = qa, pb = qb;
+      const bool hb = i + kStatLanes < end;
+      qa = i + 2 * kStatLanes < end ? slot(i + 2 * kStatLanes) : 0;
+      qb = i + 3 * kStatLanes < end ? slot(i + 3 * kStatLanes) : 0;
+      const fx::df au = ld_df(u, pa), av = ld_df(v, pa), aw = ld_df(w, pa), am = ld_df(om, pa), ap = ld_df(ps, pa);
+      fx::df bu = au, bv = av, bw = aw, bm = am, bp = ap;
+      if (hb) { bu = ld_df(u, pb); bv = ld_df(v, pb); bw = ld_df(w, pb); bm = ld_df(om, pb); bp = ld_df(ps, pb); }
+      acc1(au, av, aw, am, ap);
+      if (hb) acc1(bu, bv, bw, bm, bp);
     }
     // butterfly within the group of eight: every lane ends with the totals
 #pragma unroll
