@@ -306,8 +306,8 @@ def run_gpu(args):
     ms_prof = ev0.elapsed_time(ev1)
     shares = {}
     for kname in ("k_step", "k_radix_scatter", "k_radix_hist", "k_elem_stats", "k_node_coeff",
-                  "k_elem_rows", "k_seg_offsets", "k_node_stats", "k_scan_reduce", "k_scan_apply",
-                  "k_scan_top", "k_elem_grad1", "k_node_grad1", "k_elem_grad2", "k_node_grad2", "k_reorder"):
+                  "k_elem_rows", "k_seg_offsets", "k_node_stats", "k_scan_bins",
+                  "k_elem_grad1", "k_node_grad1", "k_elem_grad2", "k_node_grad2", "k_reorder"):
         c, t = pg.pdf_profile_query(kname)
         shares[kname] = {"launches": c, "ms_per_launch": t / c if c else None,
                          "share": t / ms_prof if ms_prof else None}

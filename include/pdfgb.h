@@ -202,7 +202,7 @@ pdf_status pdf_particles_init(const pdf_mesh* m, const pdf_init_params* ip, uint
                               int32_t precision, void* stream, pdf_particles** out);
 pdf_status pdf_particles_destroy(pdf_particles* p);
 pdf_status pdf_particles_count(const pdf_particles* p, int64_t* n);
-/* Storage order.  Every `every`-th pdf_estimate_stats call (default 8; 0
+/* Storage order.  Every `every`-th pdf_estimate_stats call (default 4; 0
  * never) copies the state into the element order its grouping computed, so
  * that the particles of one element sit in consecutive slots and the
  * step's coefficient-row and geometry loads, and the statistics' reads,

@@ -259,7 +259,7 @@ struct pdf_particles {
   fx::df *u2 = nullptr, *v2 = nullptr, *w2 = nullptr, *om2 = nullptr, *ps2 = nullptr;
   float *uf2 = nullptr, *vf2 = nullptr, *wf2 = nullptr, *omf2 = nullptr, *psf2 = nullptr;
   int32_t* pid2 = nullptr;
-  int32_t reorder_every = 8, since_reorder = 0;
+  int32_t reorder_every = 4, since_reorder = 0;
   // IECM (eq. IECM): velocity-conditioned scalar mean per slot, computed by
   // every pdf_estimate_stats while iecm_bins[0] > 0
   fx::df* cond = nullptr;

@@ -23,12 +23,12 @@ constexpr int64_t kMaxParticles = PDF_NOALLOC_MAX_PARTICLES;  // 2^19
 constexpr int64_t kMaxElements = PDF_NOALLOC_MAX_ELEMENTS;    // 2^18
 constexpr int64_t kMaxTiles = (kMaxParticles + 4095) / 4096;  // radix tiles of 4096 keys
 constexpr int64_t kHistInts = kMaxTiles * 512;
-constexpr int64_t kPartInts = 64;
+constexpr int64_t kPartInts = 520;  // the digit totals of the scan (512), rounded up
 // int32 layout: keys_a | vals_a | keys_b | vals_b | hist | part | seg
 constexpr int64_t kScratchInts = 4 * kMaxParticles + kHistInts + kPartInts + (kMaxElements + 1);
 
-// 4 x 2 MiB + 128 KiB + 1 MiB: every GPU that loads the library holds these
-// ~9.2 MiB until the process exits.
+// 4 x 2 MiB + 256 KiB + 2 KiB + 1 MiB: every GPU that loads the library
+// holds these ~9.2 MiB until the process exits.
 static __device__ __align__(256) int32_t g_noalloc_scratch[kScratchInts];
 
 std::mutex g_mu;

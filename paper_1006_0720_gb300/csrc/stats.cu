@@ -18,11 +18,12 @@ constexpr int kBins = 1 << kRadixBits;      // 512
 constexpr int kSortThreads = 256;
 constexpr int kItemsPerThread = 16;
 constexpr int kTile = kSortThreads * kItemsPerThread;  // 4096 keys per tile
-constexpr int kScanChunk = 4096;                       // hist entries per scan block
 
 int64_t radix_tiles(int64_t n) { return (n + kTile - 1) / kTile; }
 int32_t radix_bins() { return kBins; }
-int32_t radix_scan_blocks(int64_t hist_len) { return (int32_t)((hist_len + kScanChunk - 1) / kScanChunk); }
+// the digit scan runs one block per digit; callers size the partials
+// buffer as radix_scan_blocks(hist_len) + 1
+int32_t radix_scan_blocks(int64_t) { return kBins; }
 
 // Per-tile digit histogram, stored bin-major: hist[bin * n_tiles + tile].
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const int32_t* __restrict__ keys, int64_t n,
@@ -46,8 +47,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const int32_t* __re
   for (int b = threadIdx.x; b < kBins; b += kSortThreads) hist[(int64_t)b * n_tiles + blockIdx.x] = h[b];
 }
 
-// Exclusive scan of hist in three launches: chunk sums, scan of the sums,
-// then each chunk scanned with its base.
+// Exclusive block-wide prefix sum (blockDim a multiple of 32, at most
+// 1024); *total receives the block's sum.
 __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t* total) {
   __shared__ int32_t warp_sums[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -77,46 +78,34 @@ __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t* tota
   return r;
 }
 
-__global__ void __launch_bounds__(1024) k_scan_reduce(const int32_t* __restrict__ a, int64_t len,
-                                                      int32_t* __restrict__ part) {
-  const int64_t base = (int64_t)blockIdx.x * kScanChunk;
-  int32_t s = 0;
-  for (int i = threadIdx.x; i < kScanChunk; i += blockDim.x)
-    if (base + i < len) s += a[base + i];
-  int32_t total;
-  block_exclusive_scan(s, &total);
-  if (threadIdx.x == 0) part[blockIdx.x] = total;
-}
-
-__global__ void __launch_bounds__(1024) k_scan_top(int32_t* __restrict__ part, int32_t nparts) {
+// Per digit, one block each: the exclusive prefix of the digit's tile
+// counts over the tiles (in place; the digit's row of hist is contiguous)
+// and the digit's total in part[digit].  The scatter adds the totals of the
+// smaller digits.
+__global__ void __launch_bounds__(1024) k_scan_bins(int32_t* __restrict__ hist, int64_t n_tiles,
+                                                    int32_t* __restrict__ part) {
+  int32_t* row = hist + (int64_t)blockIdx.x * n_tiles;
   int32_t carry = 0;
-  for (int32_t start = 0; start < nparts; start += blockDim.x) {
-    const int32_t i = start + threadIdx.x;
-    const int32_t v = i < nparts ? part[i] : 0;
+  for (int64_t start = 0; start < n_tiles; start += 4 * (int64_t)blockDim.x) {
+    // each thread owns 4 consecutive entries
+    const int64_t base = start + 4 * (int64_t)threadIdx.x;
+    int32_t v[4];
+    int32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      v[j] = (base + j < n_tiles) ? row[base + j] : 0;
+      sum += v[j];
+    }
     int32_t total;
-    const int32_t ex = block_exclusive_scan(v, &total);
-    if (i < nparts) part[i] = carry + ex;
+    int32_t ex = block_exclusive_scan(sum, &total) + carry;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (base + j < n_tiles) row[base + j] = ex;
+      ex += v[j];
+    }
     carry += total;
   }
-}
-
-__global__ void __launch_bounds__(1024) k_scan_apply(int32_t* __restrict__ a, int64_t len,
-                                                     const int32_t* __restrict__ part) {
-  // each thread owns 4 consecutive entries of the chunk
-  const int64_t base = (int64_t)blockIdx.x * kScanChunk + 4 * threadIdx.x;
-  int32_t v[4];
-  int32_t s = 0;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    v[j] = (base + j < len) ? a[base + j] : 0;
-    s += v[j];
-  }
-  int32_t ex = block_exclusive_scan(s, nullptr) + part[blockIdx.x];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    if (base + j < len) a[base + j] = ex;
-    ex += v[j];
-  }
+  if (threadIdx.x == 0) part[blockIdx.x] = carry;
 }
 
 // Stable scatter of one tile.  Warp w owns the tile's items
@@ -127,12 +116,22 @@ __global__ void __launch_bounds__(1024) k_scan_apply(int32_t* __restrict__ a, in
 // index order.
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in, int64_t n, int shift,
-    int64_t n_tiles, const int32_t* __restrict__ hist, int32_t* __restrict__ keys_out,
-    int32_t* __restrict__ vals_out) {
+    int64_t n_tiles, const int32_t* __restrict__ hist, const int32_t* __restrict__ part,
+    int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out) {
   constexpr int kWarps = kSortThreads / 32;
   constexpr int kPerWarp = kTile / kWarps;  // 512 items, 16 rounds
+  static_assert(kBins == 2 * kSortThreads, "two digits per thread in the digit-base scan");
   __shared__ int32_t wcnt[kWarps][kBins + 1];  // the extra bin takes the tile's padding
+  __shared__ int32_t dbase[kBins];             // first output position of each digit
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  {
+    const int b0 = 2 * threadIdx.x;
+    const int32_t c0 = __ldg(part + b0), c1 = __ldg(part + b0 + 1);
+    int32_t total;
+    const int32_t ex = block_exclusive_scan(c0 + c1, &total);
+    dbase[b0] = ex;
+    dbase[b0 + 1] = ex + c0;
+  }
   for (int i = threadIdx.x; i < kWarps * (kBins + 1); i += kSortThreads) (&wcnt[0][0])[i] = 0;
   __syncthreads();
   const uint32_t lt_mask = (1u << lane) - 1u;
@@ -158,9 +157,10 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     off[r] = before + rank;
   }
   __syncthreads();
-  // (warp, digit) offsets: the tile's base of the digit plus the earlier warps' counts
+  // (warp, digit) offsets: the digit's base, the earlier tiles' counts of
+  // the digit and the earlier warps' counts
   for (int b = threadIdx.x; b < kBins; b += kSortThreads) {
-    int32_t acc = hist[(int64_t)b * n_tiles + blockIdx.x];
+    int32_t acc = dbase[b] + hist[(int64_t)b * n_tiles + blockIdx.x];
 #pragma unroll
     for (int k = 0; k < kWarps; ++k) {
       const int32_t c = wcnt[k][b];
@@ -497,6 +497,18 @@ static int blocks_for(int64_t n, int threads) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)sm_count() * 32));
 }
 
+// One stable pass of the radix sort on the digit at `shift`: tile
+// histograms, the per-digit scan over the tiles, the scatter.  hist holds
+// n_tiles * kBins entries, part kBins.
+static pdf_status radix_pass(const int32_t* kin, const int32_t* vin, int64_t n, int shift, int64_t n_tiles,
+                             int32_t* hist, int32_t* part, int32_t* kout, int32_t* vout, cudaStream_t st) {
+  PDF_KERNEL("k_radix_hist", st, k_radix_hist<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(kin, n, shift, n_tiles, hist););
+  PDF_KERNEL("k_scan_bins", st, k_scan_bins<<<kBins, 1024, 0, st>>>(hist, n_tiles, part););
+  PDF_KERNEL("k_radix_scatter", st, k_radix_scatter<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(
+                                        kin, vin, n, shift, n_tiles, hist, part, kout, vout););
+  return PDF_OK;
+}
+
 // Stable grouping of particles by element.  Leaves sorted element ids in
 // keys[out], particle ids in vals[out] and segment offsets in seg.
 pdf_status group_by_element(pdf_particles* P, cudaStream_t st) {
@@ -510,12 +522,9 @@ pdf_status group_by_element(pdf_particles* P, cudaStream_t st) {
   int cur = 0;
   for (int pass = 0; pass < passes; ++pass) {
     const int shift = pass * kRadixBits;
-    PDF_KERNEL("k_radix_hist", st, k_radix_hist<<<(unsigned)P->n_tiles, kSortThreads, 0, st>>>(kin, n, shift, P->n_tiles, P->hist););
-    PDF_KERNEL("k_scan_reduce", st, k_scan_reduce<<<P->n_scan_blocks, 1024, 0, st>>>(P->hist, P->hist_len, P->hist_part););
-    PDF_KERNEL("k_scan_top", st, k_scan_top<<<1, 1024, 0, st>>>(P->hist_part, P->n_scan_blocks););
-    PDF_KERNEL("k_scan_apply", st, k_scan_apply<<<P->n_scan_blocks, 1024, 0, st>>>(P->hist, P->hist_len, P->hist_part););
-    PDF_KERNEL("k_radix_scatter", st, k_radix_scatter<<<(unsigned)P->n_tiles, kSortThreads, 0, st>>>(kin, vin, n, shift, P->n_tiles, P->hist,
-                                                                   P->keys[cur], P->vals[cur]););
+    const pdf_status s = radix_pass(kin, vin, n, shift, P->n_tiles, P->hist, P->hist_part, P->keys[cur],
+                                    P->vals[cur], st);
+    if (s != PDF_OK) return s;
     kin = P->keys[cur];
     vin = P->vals[cur];
     cur ^= 1;
@@ -549,10 +558,9 @@ __global__ void k_reorder(ReorderArgs R) {
   }
 }
 
-// Permutes the state into element order after a grouping: afterwards the
-// sorted order is the storage order (sorted_pid = NULL) and the element ids
-// are the sorted keys.
-static pdf_status reorder_state(pdf_particles* P, cudaStream_t st) {
+// Copies the state into the grouping's order, into the second set of state
+// arrays (adopt_reorder then makes them the state).
+static pdf_status launch_reorder(pdf_particles* P, cudaStream_t st) {
   ReorderArgs R;
   R.idx = P->sorted_pid;
   R.n = P->n;
@@ -574,6 +582,13 @@ static pdf_status reorder_state(pdf_particles* P, cudaStream_t st) {
   }
   add4(P->pid, P->pid2);
   PDF_KERNEL("k_reorder", st, k_reorder<<<blocks_for(P->n, 256), 256, 0, st>>>(R););
+  return PDF_OK;
+}
+
+// Adopts the copy (host pointers only; work issued afterwards sees it): the
+// sorted order becomes the storage order (sorted_pid = NULL) and the element
+// ids are the sorted keys.
+static void adopt_reorder(pdf_particles* P) {
   std::swap(P->x, P->x2);
   std::swap(P->y, P->y2);
   std::swap(P->u, P->u2); std::swap(P->v, P->v2); std::swap(P->w, P->w2);
@@ -583,7 +598,6 @@ static pdf_status reorder_state(pdf_particles* P, cudaStream_t st) {
   std::swap(P->pid, P->pid2);
   std::swap(P->elem, P->keys[P->sorted_key_slot]);
   P->sorted_pid = nullptr;
-  return PDF_OK;
 }
 
 pdf_status iecm_cond(pdf_particles* P, const int32_t* seg, const int32_t* order, cudaStream_t st);
@@ -625,12 +639,14 @@ pdf_status node_derivs_from_node_stats(pdf_particles* P, cudaStream_t st) {
 }
 
 pdf_status estimate_stats(pdf_particles* P, cudaStream_t st) {
-  const MeshDev& M = P->mesh->d;
   pdf_status s = group_by_element(P, st);
   if (s != PDF_OK) return s;
   if (P->reorder_every > 0 && ++P->since_reorder >= P->reorder_every) {
-    s = reorder_state(P, st);
+    // (the copy beside the statistics on a second stream gained nothing:
+    // both are limited by the same gathers)
+    s = launch_reorder(P, st);
     if (s != PDF_OK) return s;
+    adopt_reorder(P);
     P->since_reorder = 0;
   }
   s = elem_stats(P, P->seg, P->sorted_pid, st);
@@ -677,20 +693,14 @@ pdf_status estimate_stats_with_buffers(pdf_particles* P, int32_t* keys_a, int32_
   const int passes = (bits + kRadixBits - 1) / kRadixBits;
   if (passes > 2) return fail(PDF_EINVAL, "estimate_stats_with_buffers: more than 2^18 elements");
   const int64_t n_tiles = radix_tiles(n);
-  const int64_t hist_len = n_tiles * kBins;
-  const int32_t n_scan = radix_scan_blocks(hist_len);
   const int32_t* kin = P->elem;
   const int32_t* vin = nullptr;
   int32_t* kout[2] = {passes == 2 ? keys_a : keys_b, keys_b};
   int32_t* vout[2] = {passes == 2 ? vals_a : vals_b, vals_b};
   for (int pass = 0; pass < passes; ++pass) {
     const int shift = pass * kRadixBits;
-    PDF_KERNEL("k_radix_hist", st, k_radix_hist<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(kin, n, shift, n_tiles, hist));
-    PDF_KERNEL("k_scan_reduce", st, k_scan_reduce<<<n_scan, 1024, 0, st>>>(hist, hist_len, hist_part));
-    PDF_KERNEL("k_scan_top", st, k_scan_top<<<1, 1024, 0, st>>>(hist_part, n_scan));
-    PDF_KERNEL("k_scan_apply", st, k_scan_apply<<<n_scan, 1024, 0, st>>>(hist, hist_len, hist_part));
-    PDF_KERNEL("k_radix_scatter", st, k_radix_scatter<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(
-                                          kin, vin, n, shift, n_tiles, hist, kout[pass], vout[pass]));
+    const pdf_status s = radix_pass(kin, vin, n, shift, n_tiles, hist, hist_part, kout[pass], vout[pass], st);
+    if (s != PDF_OK) return s;
     kin = kout[pass];
     vin = vout[pass];
   }
@@ -712,8 +722,6 @@ pdf_status radix_sort_index(const int32_t* keys, int64_t n, int bits, int32_t* k
                             int32_t* v1, int32_t* hist, int32_t* hist_part, const int32_t** keys_out,
                             const int32_t** vals_out, cudaStream_t st) {
   const int64_t n_tiles = radix_tiles(n);
-  const int64_t hist_len = n_tiles * kBins;
-  const int32_t n_scan = radix_scan_blocks(hist_len);
   const int passes = std::max(1, (bits + kRadixBits - 1) / kRadixBits);
   const int32_t* kin = keys;
   const int32_t* vin = nullptr;
@@ -723,12 +731,8 @@ pdf_status radix_sort_index(const int32_t* keys, int64_t n, int bits, int32_t* k
     const int shift = pass * kRadixBits;
     int32_t* ko = kout[pass & 1];
     int32_t* vo = vout[pass & 1];
-    PDF_KERNEL("k_radix_hist", st, k_radix_hist<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(kin, n, shift, n_tiles, hist));
-    PDF_KERNEL("k_scan_reduce", st, k_scan_reduce<<<n_scan, 1024, 0, st>>>(hist, hist_len, hist_part));
-    PDF_KERNEL("k_scan_top", st, k_scan_top<<<1, 1024, 0, st>>>(hist_part, n_scan));
-    PDF_KERNEL("k_scan_apply", st, k_scan_apply<<<n_scan, 1024, 0, st>>>(hist, hist_len, hist_part));
-    PDF_KERNEL("k_radix_scatter", st, k_radix_scatter<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(
-                                          kin, vin, n, shift, n_tiles, hist, ko, vo));
+    const pdf_status s = radix_pass(kin, vin, n, shift, n_tiles, hist, hist_part, ko, vo, st);
+    if (s != PDF_OK) return s;
     kin = ko;
     vin = vo;
   }
