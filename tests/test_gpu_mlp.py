@@ -108,18 +108,22 @@ def test_training_reduces_the_loss():
     assert last < 0.1 * first, (first, last)
 
 
-def test_learned_warm_start_beats_a_cold_start():
+def test_learned_warm_start_beats_a_cold_start(capsys):
     """Train briefly on solves of the small channel, then on a later state of
     the same run compare CG iterations: the network's guess needs fewer
-    iterations than a zero guess with the paper's Jacobi preconditioner (the
-    previous-step warm start, and the multigrid preconditioner, with which
-    the guess matters little, are reported by the benchmark, not asserted
-    here)."""
+    iterations than a zero guess with the paper's Jacobi preconditioner.
+    The previous-step start (the paper's warm start, the judge of the
+    learned one) is printed beside them, not asserted: no learned start has
+    beaten it (the quantified negative result is in the design notes)."""
     from paper_1006_0720_gb300 import experiments as E
     X, Y = E.collect_solves(120)
     net, _ = E.train(X, Y, steps=600, batch=4096, lr=3e-3)
     cfg, gm, gp, p, wp = E.setup("channel_20x40_ppe50", seed=5)
     E.advance(gm, gp, p, wp, 40)
     res = E.compare(gm, gp, p, wp, net, multigrid=False)
+    with capsys.disabled():
+        print("\nJacobi-PCG iterations to 1e-10 (max over 9 components / total):",
+              ", ".join("%s %d / %d" % (k, res[k]["iterations_max"], res[k]["iterations_total"])
+                        for k in ("zero", "previous", "local", "mlp")))
     assert res["mlp"]["iterations_total"] < res["zero"]["iterations_total"], res
     assert res["mlp"]["rel_res_max"] <= 1e-10 and res["zero"]["rel_res_max"] <= 1e-10
