@@ -605,10 +605,13 @@ pdf_status iecm_cond(pdf_particles* P, const int32_t* seg, const int32_t* order,
 // Element statistics of the grouped particles (seg, order) into P->es.
 static pdf_status elem_stats(pdf_particles* P, const int32_t* seg, const int32_t* order, cudaStream_t st) {
   const MeshDev& M = P->mesh->d;
-  // three resident blocks of 256 per SM (80 registers): each group of
-  // eight lanes walks several elements and prefetches the next one
+  // one element per group of eight lanes up to 48 blocks of 256 per SM
+  // (three resident at 80 registers); beyond that each group walks several
+  // elements and prefetches the next one.  At 15.9M particles on 158,802
+  // elements 3, 12, 24 and 48 blocks per SM took 0.29, 0.27, 0.25 and
+  // 0.22 ms: with one element per group no group waits for a long one.
   const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)M.n_tri * kStatLanes + 255) / 256,
-                                                           (int64_t)sm_count() * 3));
+                                                           (int64_t)sm_count() * 48));
   if (P->precision == PDF_FP64)
     PDF_KERNEL("k_elem_stats", st, k_elem_stats_grp<fx::df><<<nb, 256, 0, st>>>(
                                        seg, order, M.n_tri, P->u, P->v, P->w, P->om, P->ps, P->es));

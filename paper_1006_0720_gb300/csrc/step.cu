@@ -1255,15 +1255,16 @@ static pdf_status step_prepare(pdf_particles* p, const pdf_mesh* m, const pdf_mo
 }
 
 // The particle kernel's arguments; StepLaunch::run advances the slots
-// [beg, beg + cnt) (every per-slot pointer offset by beg) with at most
-// per_sm blocks per SM.
+// [beg, beg + cnt) (every per-slot pointer offset by beg) with a grid of at
+// most per_sm blocks per SM (4 resident; at 15.9M particles 4, 8, 12, 16
+// and 32 blocks per SM took 0.96, 0.94, 0.94, 0.92 and 0.92 ms).
 struct StepLaunch {
   StepArgs A;
   FxArgs F;
   F32Args S;
   int kind = 0;  // 0: FP64 kernel, 1: fixed point / double-float, 2: FP32 state
 
-  pdf_status run(int64_t beg, int64_t cnt, cudaStream_t st, int per_sm = 8) const {
+  pdf_status run(int64_t beg, int64_t cnt, cudaStream_t st, int per_sm = 16) const {
     if (cnt <= 0) return PDF_OK;
     const int nb = blocks_for(cnt, 256, per_sm);
     StepArgs a = A;
