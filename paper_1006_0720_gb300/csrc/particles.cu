@@ -447,10 +447,11 @@ namespace pdfgb {
 
 void* state_kernel_view(const void* ptr) { return kernel_view(ptr); }
 
-// Four blocks per SM: enough loads and stores in flight to keep the host
-// link busy next to the step kernel's two blocks per SM (for 15.9M
-// particles pdf_step_host took 10.9, 10.1, 9.8 and 10.9 ms with 1, 2, 4 and
-// 8 blocks per SM).
+// Grid of the state conversion kernels: four blocks per SM.  For
+// get_state / set_state they read and write the caller's page-locked arrays
+// through the mapping, and four blocks per SM keep enough loads and stores
+// in flight for the host link; pdf_step_host's conversions run between
+// device staging buffers and the slots.
 int host_io_blocks() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
