@@ -331,19 +331,17 @@ def run_gpu(args):
     # untimed warm-up of the host path (its first call allocates the staging
     # buffers and creates the streams)
     for _ in range(2):
-        pg.pdf_step_host(gp, gm, p, host, step=step_no, stream=stream)
-        pg.capi.check(L.pdf_estimate_stats(gp.handle, gm.handle, None, ctypes.c_void_p(host_ns.data_ptr()), None, sp),
-                      "estimate_stats")
+        pg.pdf_step_host_stats(gp, gm, p, host, node_stats=host_ns, step=step_no, stream=stream)
         step_no += 1
     stream.synchronize()
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         # the step reads the host state and writes the stepped state back
-        # (chunks of loads, steps and stores overlapped), then the statistics
-        pg.pdf_step_host(gp, gm, p, host, step=step_no, stream=stream)
-        pg.capi.check(L.pdf_estimate_stats(gp.handle, gm.handle, None, ctypes.c_void_p(host_ns.data_ptr()), None, sp),
-                      "estimate_stats")
+        # (chunks of loads, steps and stores overlapped), the statistics
+        # running beside the last chunks' write-back, node statistics copied
+        # to the host
+        pg.pdf_step_host_stats(gp, gm, p, host, node_stats=host_ns, step=step_no, stream=stream)
         stream.synchronize()
         step_no += 1
     barrier()
@@ -352,9 +350,10 @@ def run_gpu(args):
     state_bytes = n * (7 * 8 + 4)
     e2e = {"value": replica_value(world, n, e2e_steps, 1e3 * e2e_max), "unit": UNIT, "h2d_bytes_per_step": state_bytes,
            "d2h_bytes_per_step": state_bytes + gm.n_nodes * 12 * 8, "steps": e2e_steps,
-           "what": "state in page-locked host memory: read, stepped and written back every step (pdf_step_host: "
-                   "chunks moved by the copy engines while the previous chunk is stepped), node statistics copied "
-                   "out; after 2 untimed warm-up steps"}
+           "what": "state in page-locked host memory: read, stepped and written back every step "
+                   "(pdf_step_host_stats: chunks moved by the copy engines while the previous chunk is stepped, the "
+                   "statistics beside the last chunks' write-back), node statistics copied out; after 2 untimed "
+                   "warm-up steps"}
 
     if rank != 0:
         if dist is not None:

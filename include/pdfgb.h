@@ -348,6 +348,23 @@ pdf_status pdf_step_host(pdf_particles* p, const pdf_mesh* m, const pdf_model_pa
                          const double* elem_coeff, uint32_t step, double* x, double* y, double* u, double* v,
                          double* w, double* om, double* ps, int32_t* elem, void* stream, pdf_step_info* info);
 
+/* pdf_step_host followed by pdf_estimate_stats, in one call: the same
+ * results, bit for bit, as the two calls in sequence, but the statistics of
+ * the stepped state start as soon as the last chunk is stepped, while the
+ * copy engines still write the last chunks back to the host arrays.
+ *   x ... elem  as pdf_step_host (read, then overwritten with the stepped
+ *               state)
+ *   elem_stats, node_stats, node_derivs  optional copies of the statistics
+ *               (NULL for none; device or page-locked host memory, layouts
+ *               as pdf_estimate_stats)
+ *   other arguments and errors as pdf_step_host; the statistics are kept
+ *   for the next step as after pdf_estimate_stats. */
+pdf_status pdf_step_host_stats(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,
+                               const double* wp, const double* elem_coeff, uint32_t step, double* x, double* y,
+                               double* u, double* v, double* w, double* om, double* ps, int32_t* elem,
+                               double* elem_stats, double* node_stats, double* node_derivs, void* stream,
+                               pdf_step_info* info);
+
 /* Particle-in-cell statistics (sec. 3.3) and derivatives (sec. 3.4):
  * groups particles by element (stable radix sort by element id), element
  * means and central moments (two passes, 1/N), node averages over the

@@ -227,6 +227,13 @@ def _host_ptr(t, dtype, numel):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _out_ptr(t, numel):
+    """An optional output: a CUDA tensor or a page-locked host tensor."""
+    if t is None:
+        return None
+    return _ptr(t, torch.float64, numel) if t.is_cuda else _host_ptr(t, torch.float64, numel)
+
+
 def pdf_step_host(particles, mesh, params, state, wp=None, elem_coeff=None, step=0, stream=None, info=False):
     """pdf_step for a state held in page-locked host tensors (dict x, y, u,
     v, w, om, ps float64 and elem int32, particle-id order), which is read
@@ -245,6 +252,31 @@ def pdf_step_host(particles, mesh, params, state, wp=None, elem_coeff=None, step
         d["status"] = "lost"
         return d
     check(st, "pdf_step_host")
+    return si.as_dict() if info else None
+
+
+def pdf_step_host_stats(particles, mesh, params, state, elem_stats=None, node_stats=None, node_derivs=None,
+                        wp=None, elem_coeff=None, step=0, stream=None, info=False):
+    """pdf_step_host followed by pdf_estimate_stats in one call (the same
+    results); the statistics run while the last chunks are written back.
+    The optional statistics outputs are device or page-locked host tensors
+    laid out as for pdf_estimate_stats."""
+    si = capi.StepInfo()
+    args = [_host_ptr(state[k], torch.float64, particles.n) for k in ("x", "y", "u", "v", "w", "om", "ps")]
+    args.append(_host_ptr(state["elem"], torch.int32, particles.n))
+    st = lib().pdf_step_host_stats(particles.handle, mesh.handle, ctypes.byref(params),
+                                   _ptr(wp, torch.float64, None if wp is None else 9 * mesh.n_nodes),
+                                   _ptr(elem_coeff, torch.float64, None if elem_coeff is None else capi.PDF_NCOEF * mesh.n_tri),
+                                   int(step) & 0xFFFFFFFF, *args,
+                                   _out_ptr(elem_stats, capi.PDF_NES * mesh.n_tri),
+                                   _out_ptr(node_stats, capi.PDF_NNS * mesh.n_nodes),
+                                   _out_ptr(node_derivs, capi.PDF_NND * mesh.n_nodes),
+                                   _stream(stream), ctypes.byref(si))
+    if info and st == capi.PDF_ELOST:
+        d = si.as_dict()
+        d["status"] = "lost"
+        return d
+    check(st, "pdf_step_host_stats")
     return si.as_dict() if info else None
 
 

@@ -88,6 +88,8 @@ PROTOTYPES = {
     "pdf_step": (I32, [V, V, ctypes.POINTER(ModelParams), V, V, U32, V, ctypes.POINTER(StepInfo)]),
     "pdf_step_host": (I32, [V, V, ctypes.POINTER(ModelParams), V, V, U32, V, V, V, V, V, V, V, V, V,
                             ctypes.POINTER(StepInfo)]),
+    "pdf_step_host_stats": (I32, [V, V, ctypes.POINTER(ModelParams), V, V, U32, V, V, V, V, V, V, V, V, V, V, V,
+                                  V, ctypes.POINTER(StepInfo)]),
     "pdf_estimate_stats": (I32, [V, V, V, V, V, V]),
     "pdf_estimate_stats_noalloc": (I32, [V, V, V, V, V, V]),
     "pdf_elem_coeff": (I32, [V, V, ctypes.POINTER(ModelParams), V, V, V]),

@@ -1376,22 +1376,30 @@ extern "C" pdf_status pdf_step(pdf_particles* p, const pdf_mesh* m, const pdf_mo
   return info ? step_info(p, info, st) : PDF_OK;
 }
 
-extern "C" pdf_status pdf_step_host(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,
-                                    const double* wp, const double* elem_coeff, uint32_t step, double* x, double* y,
-                                    double* u, double* v, double* w, double* om, double* ps, int32_t* elem,
-                                    void* stream, pdf_step_info* info) {
-  if (!p || !x || !y || !u || !v || !w || !om || !ps || !elem)
-    return fail(PDF_EINVAL, "pdf_step_host: NULL argument");
+namespace pdfgb {
+pdf_status estimate_stats(pdf_particles* P, cudaStream_t st);
+}
+
+// pdf_step_host, and with `stats` pdf_step_host_stats: the statistics of the
+// stepped state are issued on the compute stream after the last chunk's
+// step, so that they run while the copy engines still write the last chunks
+// back (es, ns, nd: optional copies of the results, as pdf_estimate_stats).
+static pdf_status step_host(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params, const double* wp,
+                            const double* elem_coeff, uint32_t step, double* const io_arg[7], int32_t* elem,
+                            cudaStream_t st, pdf_step_info* info, bool stats, double* es, double* ns, double* nd) {
+  for (int i = 0; i < 7; ++i)
+    if (!io_arg[i]) return fail(PDF_EINVAL, "pdf_step_host: NULL argument");
+  if (!p || !elem) return fail(PDF_EINVAL, "pdf_step_host: NULL argument");
   if (params && params->mix == PDF_MIX_IECM)
     return fail(PDF_EINVAL, "pdf_step_host: IECM needs the device-resident state (pdf_step)");
-  double* io[7] = {x, y, u, v, w, om, ps};
+  double* io[7];
+  for (int i = 0; i < 7; ++i) io[i] = io_arg[i];
   // page-locked host or device memory: the copies then run asynchronously
   for (int i = 0; i < 7; ++i)
     if (!state_kernel_view(io[i]))
       return fail(PDF_EINVAL, "pdf_step_host: the state arrays must be page-locked host or device memory");
   if (!state_kernel_view(elem))
     return fail(PDF_EINVAL, "pdf_step_host: the state arrays must be page-locked host or device memory");
-  cudaStream_t st = (cudaStream_t)stream;
   pdf_status s = step_prepare(p, m, params, wp, elem_coeff, true, st);
   if (s != PDF_OK) return s;
   s = host_io_init(p);
@@ -1450,9 +1458,17 @@ extern "C" pdf_status pdf_step_host(pdf_particles* p, const pdf_mesh* m, const p
     PDF_CUDA(cudaMemcpyAsync(elem + beg, H.stage_oe[b], sizeof(int32_t) * cnt, cudaMemcpyDefault, H.out));
     PDF_CUDA(cudaEventRecord(H.free_out[b], H.out));
   }
+  p->since_reorder = 0;
+  if (stats) {
+    s = estimate_stats(p, st);
+    if (s != PDF_OK) return s;
+    const MeshDev& M = m->d;
+    if (es) PDF_CUDA(cudaMemcpyAsync(es, p->es, sizeof(double) * M.n_tri * PDF_NES, cudaMemcpyDefault, st));
+    if (ns) PDF_CUDA(cudaMemcpyAsync(ns, p->ns, sizeof(double) * M.n_nodes * PDF_NNS, cudaMemcpyDefault, st));
+    if (nd) PDF_CUDA(cudaMemcpyAsync(nd, p->nd, sizeof(double) * M.n_nodes * PDF_NND, cudaMemcpyDefault, st));
+  }
   PDF_CUDA(cudaEventRecord(H.done, H.out));
   PDF_CUDA(cudaStreamWaitEvent(st, H.done, 0));
-  p->since_reorder = 0;
   long long c[16];
   PDF_CUDA(cudaMemcpyAsync(c, p->counters, sizeof(c), cudaMemcpyDeviceToHost, st));
   PDF_CUDA(cudaStreamSynchronize(st));
@@ -1469,4 +1485,23 @@ extern "C" pdf_status pdf_step_host(pdf_particles* p, const pdf_mesh* m, const p
   }
   if (c[kCntLost] > 0) return fail(PDF_ELOST, "pdf_step_host: particles lost");
   return PDF_OK;
+}
+
+extern "C" pdf_status pdf_step_host(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,
+                                    const double* wp, const double* elem_coeff, uint32_t step, double* x, double* y,
+                                    double* u, double* v, double* w, double* om, double* ps, int32_t* elem,
+                                    void* stream, pdf_step_info* info) {
+  double* const io[7] = {x, y, u, v, w, om, ps};
+  return step_host(p, m, params, wp, elem_coeff, step, io, elem, (cudaStream_t)stream, info, false, nullptr,
+                   nullptr, nullptr);
+}
+
+extern "C" pdf_status pdf_step_host_stats(pdf_particles* p, const pdf_mesh* m, const pdf_model_params* params,
+                                          const double* wp, const double* elem_coeff, uint32_t step, double* x,
+                                          double* y, double* u, double* v, double* w, double* om, double* ps,
+                                          int32_t* elem, double* elem_stats, double* node_stats,
+                                          double* node_derivs, void* stream, pdf_step_info* info) {
+  double* const io[7] = {x, y, u, v, w, om, ps};
+  return step_host(p, m, params, wp, elem_coeff, step, io, elem, (cudaStream_t)stream, info, true, elem_stats,
+                   node_stats, node_derivs);
 }

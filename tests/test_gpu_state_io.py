@@ -128,6 +128,37 @@ def test_step_host_matches_set_step_get(precision):
         assert torch.equal(da[k].cpu(), host_a[k]), k
 
 
+def test_step_host_stats_matches_step_host_then_statistics():
+    """pdf_step_host_stats gives, bit for bit, the state of pdf_step_host and
+    the statistics (element, node, derivatives) of a following
+    pdf_estimate_stats, into device and page-locked host outputs, over
+    several steps that include reorderings of the device state."""
+    m = inputs.channel_mesh(50, 100, seed=3)
+    gm = pg.Mesh(m)
+    psi = inputs.scalar_slab(m)
+    a = pg.Particles(gm, 8, ppe=30, u_sigma=0.2, elem_psi0=psi)
+    b = pg.Particles(gm, 8, ppe=30, u_sigma=0.2, elem_psi0=psi)
+    for q in (a, b):
+        q.set_reorder(2)
+        pg.pdf_estimate_stats(q, gm)
+    p = pg.model_params(closure="glm")
+    host_a = _pinned_copy(a.get_state())
+    host_b = _pinned_copy(b.get_state())
+    shapes = {"e": (gm.n_tri, capi.PDF_NES), "n": (gm.n_nodes, capi.PDF_NNS), "d": (gm.n_nodes, capi.PDF_NND)}
+    out_a = {k: torch.empty(v, dtype=torch.float64, pin_memory=True) for k, v in shapes.items()}
+    out_b = {k: torch.empty(v, dtype=torch.float64, device="cuda") for k, v in shapes.items()}
+    for s in range(4):
+        ia = pg.pdf_step_host_stats(a, gm, p, host_a, out_a["e"], out_a["n"], out_a["d"], step=s, info=True)
+        ib = pg.pdf_step_host(b, gm, p, host_b, step=s, info=True)
+        pg.pdf_estimate_stats(b, gm, out_b["e"], out_b["n"], out_b["d"])
+        torch.cuda.synchronize()
+        assert ia == ib
+        for k in KEYS + ("elem",):
+            assert torch.equal(host_a[k], host_b[k]), (s, k)
+        for k in shapes:
+            assert torch.equal(out_a[k], out_b[k].cpu()), (s, k)
+
+
 def test_step_host_rejects_pageable_buffers_and_iecm():
     m = inputs.channel_mesh(8, 6, seed=1)
     gm = pg.Mesh(m)
