@@ -41,29 +41,36 @@ constexpr double kEFloor = 1e-12;  // floor of eps
 // A_v = min(1, C_v det<uu> / (2k/3)^3) and b_ij of eq. bij.  Contracting H
 // with the gradient gives
 //   (C2 A_v + g5/3) dU_i/dx_j - (g5/3) dU_j/dx_i + g5 b_ik dU_k/dx_j - g5 b_il dU_j/dx_l.
-__device__ void relax_rhs(const double* S, const double* D, const CoeffParams& P, double rhs[9]) {
+// k is the floored turbulent energy and inv_k its reciprocal (the caller's);
+// the gradient's third column (d/dz) is zero and its terms are left out.
+// The FP64 pipe bounds this kernel, so the divisions are reciprocals taken
+// once and multiplied.
+__device__ void relax_rhs(const double* S, const double* D, const CoeffParams& P, double k, double inv_k,
+                          double rhs[9]) {
   const double R[3][3] = {{S[5], S[8], S[9]}, {S[8], S[6], S[10]}, {S[9], S[10], S[7]}};
-  const double k = fmax(0.5 * (S[5] + S[6] + S[7]), kKFloor);
-  const double grad[3][3] = {{D[0], D[1], 0.0}, {D[2], D[3], 0.0}, {D[4], D[5], 0.0}};  // dU_i/dx_j
+  const double grad[3][2] = {{D[0], D[1]}, {D[2], D[3]}, {D[4], D[5]}};  // dU_i/dx_j, j < 2
   const double det = R[0][0] * (R[1][1] * R[2][2] - R[1][2] * R[2][1]) -
                      R[0][1] * (R[1][0] * R[2][2] - R[1][2] * R[2][0]) +
                      R[0][2] * (R[1][0] * R[2][1] - R[1][1] * R[2][0]);
-  const double tk = 2.0 * k / 3.0;
-  const double Av = fmin(1.0, P.Cv * det / (tk * tk * tk));
+  // (2k/3)^-3 = (27/8) k^-3
+  const double Av = fmin(1.0, P.Cv * det * (3.375 * inv_k * inv_k * inv_k));
   double b[3][3];
-  const double inv_2k = 0.5 / k;
+  const double inv_2k = 0.5 * inv_k;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) b[i][j] = R[i][j] * inv_2k - (i == j ? 1.0 / 3.0 : 0.0);
   const double g3 = P.gamma5 / 3.0;
+  const double cg = P.C2 * Av + g3;
+  const double diag = 0.5 * (1.0 - P.C1) * k * S[3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      double bk = 0.0, bl = 0.0;
-      for (int q = 0; q < 3; ++q) {
-        bk += b[i][q] * grad[q][j];
-        bl += b[i][q] * grad[j][q];
-      }
-      const double h = (P.C2 * Av + g3) * grad[i][j] - g3 * grad[j][i] + P.gamma5 * (bk - bl);
-      rhs[3 * i + j] = (i == j ? 0.5 * (1.0 - P.C1) * k * S[3] : 0.0) + k * h;
+      // b_ik dU_k/dx_j (zero for j = 2) and b_il dU_j/dx_l (l < 2)
+      double bk = 0.0;
+      if (j < 2) bk = b[i][0] * grad[0][j] + b[i][1] * grad[1][j] + b[i][2] * grad[2][j];
+      const double bl = b[i][0] * grad[j][0] + b[i][1] * grad[j][1];
+      double h = P.gamma5 * (bk - bl);
+      if (j < 2) h += cg * grad[i][j];
+      if (i < 2) h -= g3 * grad[j][i];
+      rhs[3 * i + j] = (i == j ? diag : 0.0) + k * h;
     }
 }
 
@@ -84,6 +91,7 @@ __global__ void k_node_coeff(int32_t n_nodes, const double* __restrict__ ns, con
     const double om = S[3];
     const double eps = (P.closure == PDF_CLOSURE_SLM) ? k * om : om * (k + P.nu * P.CT * P.CT * om);
     const double eg = fmax(eps, kEFloor);
+    const double inv_kg = 1.0 / kg, inv_eg = 1.0 / eg;
     c[0] = S[0]; c[1] = S[1]; c[2] = S[2];
     for (int q = 0; q < 6; ++q) c[3 + q] = D[q];
     double dpx = 0.0, dpy = 0.0;
@@ -103,24 +111,23 @@ __global__ void k_node_coeff(int32_t n_nodes, const double* __restrict__ ns, con
       if (wp) {
         for (int q = 0; q < 9; ++q) w9[q] = wp[(int64_t)q * n_nodes + n];
       } else {
-        relax_rhs(S, D, P, w9);
+        relax_rhs(S, D, P, kg, inv_kg, w9);
       }
       const double R9[9] = {S[5], S[8], S[9], S[8], S[6], S[10], S[9], S[10], S[7]};
       double wr = 0.0;
       for (int q = 0; q < 9; ++q) wr += w9[q] * R9[q];
-      const double inv_kg = 1.0 / kg;
       for (int q = 0; q < 9; ++q) c[12 + q] = (w9[q] - ((q % 4 == 0) ? 0.5 * eg : 0.0)) * inv_kg;
-      const double C0 = fmax(-2.0 * wr / (3.0 * kg * eg), 0.0);
+      const double C0 = fmax((-2.0 / 3.0) * wr * inv_kg * inv_eg, 0.0);
       c[21] = sqrt(C0 * eg);
     }
     c[22] = om;
     const double prod = -(S[5] * D[0] + S[8] * D[1] + S[8] * D[2] + S[6] * D[3] + S[9] * D[4] + S[10] * D[5]);
-    c[23] = P.Comega2 - P.Comega1 * prod / eg;
+    c[23] = P.Comega2 - P.Comega1 * prod * inv_eg;
     c[24] = S[4];
     if (P.tm_mode == PDF_TM_CPHI) {
       c[25] = 0.5 * P.c_phi * om;
     } else {
-      double tm = fmax(kg / eg, P.CT * sqrt(P.nu / eg));
+      double tm = fmax(kg * inv_eg, P.CT * sqrt(P.nu * inv_eg));
       if (P.tm_mode == PDF_TM_SOURCE) {
         // eq. micromixing-timescale-canyon: the source term, U_c = |<U>| at the node
         const double dx = xy[2 * n] - P.src_x, dy = xy[2 * n + 1] - P.src_y;
