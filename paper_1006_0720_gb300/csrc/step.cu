@@ -198,11 +198,19 @@ __global__ void k_elem_rows(const int32_t* __restrict__ tri, int32_t n_tri, cons
                             const ElemGeo* __restrict__ geo, const double* __restrict__ nsw_line,
                             const double* __restrict__ ns, const double* __restrict__ dN) {
   for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n_tri; e += gridDim.x * blockDim.x) {
-    const double* c0 = nc + (int64_t)tri[3 * e] * PDF_NCOEF;
-    const double* c1 = nc + (int64_t)tri[3 * e + 1] * PDF_NCOEF;
-    const double* c2 = nc + (int64_t)tri[3 * e + 2] * PDF_NCOEF;
+    // node rows of 26 doubles (208 B, 16-byte aligned): 16-byte loads, and
+    // 16-byte stores of the 256-byte element row (the kernel's loads and
+    // stores, not its arithmetic, filled the load-store queue)
+    const double2* c0 = reinterpret_cast<const double2*>(nc + (int64_t)tri[3 * e] * PDF_NCOEF);
+    const double2* c1 = reinterpret_cast<const double2*>(nc + (int64_t)tri[3 * e + 1] * PDF_NCOEF);
+    const double2* c2 = reinterpret_cast<const double2*>(nc + (int64_t)tri[3 * e + 2] * PDF_NCOEF);
     double a[PDF_NCOEF];
-    for (int q = 0; q < PDF_NCOEF; ++q) a[q] = (c0[q] + c1[q] + c2[q]) * (1.0 / 3.0);
+#pragma unroll
+    for (int q = 0; q < PDF_NCOEF / 2; ++q) {
+      const double2 x0 = __ldg(c0 + q), x1 = __ldg(c1 + q), x2 = __ldg(c2 + q);
+      a[2 * q] = (x0.x + x1.x + x2.x) * (1.0 / 3.0);
+      a[2 * q + 1] = (x0.y + x1.y + x2.y) * (1.0 / 3.0);
+    }
     if (avg_out)
       for (int q = 0; q < PDF_NCOEF; ++q) avg_out[(int64_t)e * PDF_NCOEF + q] = a[q];
     if (rows || rows_fx || rows_f32) {
@@ -210,8 +218,11 @@ __global__ void k_elem_rows(const int32_t* __restrict__ tri, int32_t n_tri, cons
       scale_row(a, P, r);
       // r[28]: the no-slip wall frequency of elements next to a no-slip wall
       if (geo[e].nsw) r[28] = noslip_omega(e, tri, ns, dN, nsw_line + 4 * (int64_t)e, P.CT);
-      if (rows)
-        for (int q = 0; q < PDFGB_ROW; ++q) rows[(int64_t)e * PDFGB_ROW + q] = r[q];
+      if (rows) {
+        double2* o = reinterpret_cast<double2*>(rows + (int64_t)e * PDFGB_ROW);
+#pragma unroll
+        for (int q = 0; q < PDFGB_ROW / 2; ++q) o[q] = make_double2(r[2 * q], r[2 * q + 1]);
+      }
       if (rows_fx) make_fx_row(r, rows_fx + e);
       if (rows_f32)
         for (int q = 0; q < PDFGB_ROW; ++q) rows_f32[(int64_t)e * PDFGB_ROW + q] = __double2float_rn(r[q]);
