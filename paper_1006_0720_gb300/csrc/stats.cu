@@ -26,23 +26,44 @@ int32_t radix_bins() { return kBins; }
 int32_t radix_scan_blocks(int64_t) { return kBins; }
 
 // Per-tile digit histogram, stored bin-major: hist[bin * n_tiles + tile].
+// Thread t counts the tile's keys 16t .. 16t + 15 (four 16-byte loads when
+// the keys are 16-byte aligned) as runs of equal digits, one shared atomic
+// per run: the element ids arrive nearly sorted (the state is reordered
+// by element every few steps, and the second pass reads the first pass's
+// output), so a thread's sixteen keys are mostly one or two runs.
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const int32_t* __restrict__ keys, int64_t n,
                                                              int shift, int64_t n_tiles,
                                                              int32_t* __restrict__ hist) {
   __shared__ int32_t h[kBins];
   for (int b = threadIdx.x; b < kBins; b += kSortThreads) h[b] = 0;
   __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * kTile;
-  // all sixteen keys in flight before the first count
-  int d[kItemsPerThread];
+  const int64_t i0 = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kItemsPerThread;
+  int32_t k[kItemsPerThread];
+  if (i0 + kItemsPerThread <= n && (reinterpret_cast<uintptr_t>(keys + i0) & 15) == 0) {
+    const int4* q = reinterpret_cast<const int4*>(keys + i0);
+#pragma unroll
+    for (int j = 0; j < kItemsPerThread / 4; ++j) {
+      const int4 v = __ldg(q + j);
+      k[4 * j] = v.x; k[4 * j + 1] = v.y; k[4 * j + 2] = v.z; k[4 * j + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < kItemsPerThread; ++r) k[r] = (i0 + r < n) ? __ldg(keys + i0 + r) : 0;
+  }
+  const int m = (int)max((int64_t)0, min((int64_t)kItemsPerThread, n - i0));  // keys of this thread
+  int run_d = -1, run_c = 0;
 #pragma unroll
   for (int r = 0; r < kItemsPerThread; ++r) {
-    const int64_t i = base + r * kSortThreads + threadIdx.x;
-    d[r] = (i < n) ? ((__ldg(keys + i) >> shift) & (kBins - 1)) : -1;
+    if (r >= m) break;
+    const int d = (k[r] >> shift) & (kBins - 1);
+    if (d != run_d) {
+      if (run_c) atomicAdd(&h[run_d], run_c);
+      run_d = d;
+      run_c = 0;
+    }
+    ++run_c;
   }
-#pragma unroll
-  for (int r = 0; r < kItemsPerThread; ++r)
-    if (d[r] >= 0) atomicAdd(&h[d[r]], 1);
+  if (run_c) atomicAdd(&h[run_d], run_c);
   __syncthreads();
   for (int b = threadIdx.x; b < kBins; b += kSortThreads) hist[(int64_t)b * n_tiles + blockIdx.x] = h[b];
 }
@@ -132,6 +153,9 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     dbase[b0] = ex;
     dbase[b0 + 1] = ex + c0;
   }
+  // this tile's counts of the thread's two digits, loaded before the ranking
+  const int32_t th0 = hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x];
+  const int32_t th1 = hist[(int64_t)(threadIdx.x + kSortThreads) * n_tiles + blockIdx.x];
   for (int i = threadIdx.x; i < kWarps * (kBins + 1); i += kSortThreads) (&wcnt[0][0])[i] = 0;
   __syncthreads();
   const uint32_t lt_mask = (1u << lane) - 1u;
@@ -159,8 +183,10 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
   __syncthreads();
   // (warp, digit) offsets: the digit's base, the earlier tiles' counts of
   // the digit and the earlier warps' counts
-  for (int b = threadIdx.x; b < kBins; b += kSortThreads) {
-    int32_t acc = dbase[b] + hist[(int64_t)b * n_tiles + blockIdx.x];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int b = threadIdx.x + h * kSortThreads;
+    int32_t acc = dbase[b] + (h ? th1 : th0);
 #pragma unroll
     for (int k = 0; k < kWarps; ++k) {
       const int32_t c = wcnt[k][b];
