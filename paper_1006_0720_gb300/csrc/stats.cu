@@ -208,32 +208,37 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
 }
 
 // seg[e] = first sorted position whose key >= e; seg[n_tri] = n.  Thread t
-// takes positions 4t .. 4t + 3 (one 16-byte load when the keys are 16-byte
-// aligned); the last quad also takes position n.
-__global__ void k_seg_offsets(const int32_t* __restrict__ keys, int64_t n, int32_t n_tri,
-                              int32_t* __restrict__ seg) {
-  const int64_t n4 = n / 4;
-  const bool vec = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= n4;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i0 = 4 * t;
-    int32_t prev = (i0 == 0) ? -1 : keys[i0 - 1];
-    int32_t k[4];
-    if (t < n4 && vec) {
-      const int4 v = __ldg(reinterpret_cast<const int4*>(keys) + t);
-      k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
-    } else {
+// takes positions 16t .. 16t + 15 (four 16-byte loads when the keys are
+// 16-byte aligned) and position n counts as key n_tri; the key before the
+// thread's first comes from the lane below (lane 0 loads it).  One thread
+// per 16 positions, n / 16 + 1 threads in all.
+constexpr int kSegPer = 16;
+int64_t seg_offsets_threads(int64_t n) { return n / kSegPer + 1; }
+__global__ void __launch_bounds__(256) k_seg_offsets(const int32_t* __restrict__ keys, int64_t n, int32_t n_tri,
+                                                     int32_t* __restrict__ seg) {
+  const int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * kSegPer;
+  int32_t k[kSegPer];
+  if (i0 + kSegPer <= n && (reinterpret_cast<uintptr_t>(keys + i0) & 15) == 0) {
+    const int4* q = reinterpret_cast<const int4*>(keys + i0);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) k[j] = (i0 + j < n) ? keys[i0 + j] : n_tri;
+    for (int j = 0; j < kSegPer / 4; ++j) {
+      const int4 v = __ldg(q + j);
+      k[4 * j] = v.x; k[4 * j + 1] = v.y; k[4 * j + 2] = v.z; k[4 * j + 3] = v.w;
     }
+  } else {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int64_t i = i0 + j;
-      if (i > n) break;
-      const int32_t cur = k[j];  // n_tri at i == n
-      for (int32_t e = prev + 1; e <= cur; ++e) seg[e] = (int32_t)i;
-      prev = cur;
-    }
+    for (int j = 0; j < kSegPer; ++j) k[j] = (i0 + j < n) ? __ldg(keys + i0 + j) : n_tri;
+  }
+  int32_t prev = __shfl_up_sync(0xffffffffu, k[kSegPer - 1], 1);
+  if ((threadIdx.x & 31) == 0) prev = (i0 == 0) ? -1 : ((i0 - 1 < n) ? __ldg(keys + i0 - 1) : n_tri);
+  if (i0 > n) return;
+#pragma unroll
+  for (int j = 0; j < kSegPer; ++j) {
+    const int64_t i = i0 + j;
+    if (i > n) break;
+    const int32_t cur = k[j];  // n_tri at i == n
+    for (int32_t e = prev + 1; e <= cur; ++e) seg[e] = (int32_t)i;
+    prev = cur;
   }
 }
 
@@ -555,7 +560,7 @@ pdf_status group_by_element(pdf_particles* P, cudaStream_t st) {
     vin = P->vals[cur];
     cur ^= 1;
   }
-  PDF_KERNEL("k_seg_offsets", st, k_seg_offsets<<<blocks_for(n / 4 + 1, 256), 256, 0, st>>>(kin, n, n_tri, P->seg););
+  PDF_KERNEL("k_seg_offsets", st, k_seg_offsets<<<(unsigned)((seg_offsets_threads(n) + 255) / 256), 256, 0, st>>>(kin, n, n_tri, P->seg););
   P->sorted_pid = vin;
   P->sorted_key_slot = cur ^ 1;
   return PDF_OK;
@@ -735,7 +740,7 @@ pdf_status estimate_stats_with_buffers(pdf_particles* P, int32_t* keys_a, int32_
     kin = kout[pass];
     vin = vout[pass];
   }
-  PDF_KERNEL("k_seg_offsets", st, k_seg_offsets<<<blocks_for(n / 4 + 1, 256), 256, 0, st>>>(kin, n, M.n_tri, seg));
+  PDF_KERNEL("k_seg_offsets", st, k_seg_offsets<<<(unsigned)((seg_offsets_threads(n) + 255) / 256), 256, 0, st>>>(kin, n, M.n_tri, seg));
   pdf_status s = elem_stats(P, seg, vin, st);
   if (s != PDF_OK) return s;
   s = node_stats_from_elements(P, st);
