@@ -325,11 +325,12 @@ pdf_status pdf_step(pdf_particles* p, const pdf_mesh* m, const pdf_model_params*
 /* pdf_step for a state that lives in host memory: equivalent to
  * pdf_particles_set_state(x ... elem), pdf_step(...) and
  * pdf_particles_get_state(x ... elem) (same results, bit for bit), with the
- * transfers overlapped: the particles are taken in chunks of particle ids;
- * the copy engines move each chunk's arrays (cudaMemcpyAsync, one call per
- * array and direction) into and out of device staging buffers while the
- * SMs convert and step the previous chunk, so that the host link's two
- * directions and the SMs are busy together.  The staging buffers (two per
+ * transfers overlapped: the particles are taken in chunks of particle ids
+ * (starting on 4 KiB boundaries of the arrays); the copy engines move each
+ * chunk's arrays (cudaMemcpyAsync, one call per array and direction) into
+ * and out of device staging buffers while the SMs convert and step the
+ * previous chunk, so that the host link's two directions and the SMs are
+ * busy together.  The staging buffers (two per
  * direction, 60 bytes per particle of a chunk each) are allocated at the
  * first call and kept by the particle set.
  *   x ... ps    page-locked host (or device) [n] FP64, elem [n] int32; read,

@@ -1418,30 +1418,37 @@ static pdf_status step_host(pdf_particles* p, const pdf_mesh* m, const pdf_model
       return fail(PDF_EINVAL, "pdf_step_host: the state arrays must be page-locked host or device memory");
   if (!state_kernel_view(elem))
     return fail(PDF_EINVAL, "pdf_step_host: the state arrays must be page-locked host or device memory");
-  pdf_status s = step_prepare(p, m, params, wp, elem_coeff, true, st);
-  if (s != PDF_OK) return s;
-  s = host_io_init(p);
+  pdf_status s = host_io_init(p);
   if (s != PDF_OK) return s;
   HostIo& H = p->hio;
-  unsigned long long* bad = reinterpret_cast<unsigned long long*>(p->counters + 15);
-  PDF_CUDA(cudaMemsetAsync(bad, 0, sizeof(long long), st));
   // the state is loaded in particle-id order (slot = id), so that every
   // chunk is a contiguous range of the caller's arrays.  Per chunk: the
   // copy engines bring its 8 arrays into a device staging buffer (stream
   // in), the compute stream converts them into the slots, steps them and
   // converts them back into an outgoing staging buffer, and the copy
   // engines write that back (stream out); two staging buffers per
-  // direction, so that chunk k + 1 moves while chunk k is stepped.
-  const StepLaunch L = step_args(p, m, params, step);
+  // direction, so that chunk k + 1 moves while chunk k is stepped.  Chunks
+  // start on 4 KiB boundaries of the arrays: with both directions moving,
+  // pieces that start only 8-byte aligned went 12-15 % slower (8 and 16
+  // pieces per array of 15.9M doubles: 237 and 233 GB/s together against
+  // 271 and 265 aligned).  With the first copies started before the
+  // coefficient rows, a call with statistics at 15.9M particles went from
+  // 7.54 to 6.89 ms.
   const int64_t n = p->n;
   const int K = (int)std::max<int64_t>(1, std::min<int64_t>(kHostChunks, n / 65536));
-  const int64_t chunk = (n + K - 1) / K;
+  const int64_t chunk = ((n + K - 1) / K + 511) / 512 * 512;
   s = host_io_stage(p, chunk);
   if (s != PDF_OK) return s;
-  const int io_blocks = host_io_blocks();
+  // the first chunks' copies may start while the coefficient rows are formed
   PDF_CUDA(cudaEventRecord(H.start, st));
   PDF_CUDA(cudaStreamWaitEvent(H.in, H.start, 0));
   PDF_CUDA(cudaStreamWaitEvent(H.out, H.start, 0));
+  s = step_prepare(p, m, params, wp, elem_coeff, true, st);
+  if (s != PDF_OK) return s;
+  unsigned long long* bad = reinterpret_cast<unsigned long long*>(p->counters + 15);
+  PDF_CUDA(cudaMemsetAsync(bad, 0, sizeof(long long), st));
+  const StepLaunch L = step_args(p, m, params, step);
+  const int io_blocks = host_io_blocks();
   for (int k = 0; k < K; ++k) {
     const int64_t beg = k * chunk, cnt = std::min<int64_t>(chunk, n - beg);
     if (cnt <= 0) break;
