@@ -56,10 +56,16 @@ def _peaks():
 
 
 def _kernel_sha():
+    """Hash of the particle kernel's sources (step.cu, rng.cuh, common.cuh,
+    fx.cuh) with comments and whitespace removed: a change of code, not of
+    comments, makes the committed profile stale."""
     h = hashlib.sha256()
     for f in ("step.cu", "rng.cuh", "common.cuh", "fx.cuh"):
-        with open(os.path.join(ROOT, "paper_1006_0720_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1006_0720_gb300", "csrc", f), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

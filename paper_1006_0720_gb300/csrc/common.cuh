@@ -116,9 +116,8 @@ struct RelaxMesh {
 // Streams, events and staging buffers of pdf_step_host (created at its
 // first call): chunks of the caller's arrays are copied by the copy engines
 // into two device staging buffers per direction.  At most 7 chunks (at
-// least 65,536 particles each): for 15.9M particles 2, 3, 4, 5, 6, 7, 9,
-// 11 and 16 chunks took 9.55, 8.25, 9.04, 7.86, 8.43, 7.79, 8.56, 8.74 and
-// 9.18 ms per call.
+// least 65,536 particles each): for 15.9M particles with statistics, 5, 7,
+// 10 and 14 chunks took 7.2, 7.0, 7.0 and 7.2 ms per call.
 constexpr int kHostChunks = 7;
 struct HostIo {
   cudaStream_t in = nullptr, out = nullptr;
