@@ -129,47 +129,40 @@ __global__ void __launch_bounds__(1024) k_scan_bins(int32_t* __restrict__ hist, 
   if (threadIdx.x == 0) part[blockIdx.x] = carry;
 }
 
-// Stable scatter of one tile.  Warp w owns the tile's items
-// [512 w, 512 (w + 1)) and ranks them in 16 rounds of 32 in index order,
-// counting digits in its own row of shared counters (no block barrier
-// between rounds); one block-wide prefix over the warps then gives every
-// (warp, digit) its output offset, so items with equal digits keep their
-// index order.
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+// Stable scatter of one tile (512 threads of 8 items).
+constexpr int kScatterThreads = 512;
+constexpr int kScatterItems = kTile / kScatterThreads;  // 8
+__global__ void __launch_bounds__(kScatterThreads, 2) k_radix_scatter(
     const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in, int64_t n, int shift,
     int64_t n_tiles, const int32_t* __restrict__ hist, const int32_t* __restrict__ part,
     int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out) {
-  constexpr int kWarps = kSortThreads / 32;
-  constexpr int kPerWarp = kTile / kWarps;  // 512 items, 16 rounds
-  static_assert(kBins == 2 * kSortThreads, "two digits per thread in the digit-base scan");
+  constexpr int kWarps = kScatterThreads / 32;  // 16
+  constexpr int kPerWarp = kTile / kWarps;      // 256 items, 8 rounds
+  static_assert(kBins == kScatterThreads, "one digit per thread in the digit-base scan");
   __shared__ int32_t wcnt[kWarps][kBins + 1];  // the extra bin takes the tile's padding
   __shared__ int32_t dbase[kBins];             // first output position of each digit
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   {
-    const int b0 = 2 * threadIdx.x;
-    const int32_t c0 = __ldg(part + b0), c1 = __ldg(part + b0 + 1);
+    const int32_t c0 = __ldg(part + threadIdx.x);
     int32_t total;
-    const int32_t ex = block_exclusive_scan(c0 + c1, &total);
-    dbase[b0] = ex;
-    dbase[b0 + 1] = ex + c0;
+    dbase[threadIdx.x] = block_exclusive_scan(c0, &total);
   }
-  // this tile's counts of the thread's two digits, loaded before the ranking
+  // this tile's count of the thread's digit, loaded before the ranking
   const int32_t th0 = hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x];
-  const int32_t th1 = hist[(int64_t)(threadIdx.x + kSortThreads) * n_tiles + blockIdx.x];
-  for (int i = threadIdx.x; i < kWarps * (kBins + 1); i += kSortThreads) (&wcnt[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < kWarps * (kBins + 1); i += kScatterThreads) (&wcnt[0][0])[i] = 0;
   __syncthreads();
   const uint32_t lt_mask = (1u << lane) - 1u;
   const int64_t w0 = (int64_t)blockIdx.x * kTile + (int64_t)wid * kPerWarp;
-  int32_t key[kItemsPerThread], val[kItemsPerThread], off[kItemsPerThread];
+  int32_t key[kScatterItems], val[kScatterItems], off[kScatterItems];
 #pragma unroll
-  for (int r = 0; r < kItemsPerThread; ++r) {
+  for (int r = 0; r < kScatterItems; ++r) {
     const int64_t i = w0 + r * 32 + lane;
     const bool valid = i < n;
     key[r] = valid ? keys_in[i] : 0;
     val[r] = valid ? (vals_in ? vals_in[i] : (int32_t)i) : 0;
   }
 #pragma unroll
-  for (int r = 0; r < kItemsPerThread; ++r) {
+  for (int r = 0; r < kScatterItems; ++r) {
     const int64_t i = w0 + r * 32 + lane;
     const int d = (i < n) ? ((key[r] >> shift) & (kBins - 1)) : kBins;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
@@ -181,12 +174,10 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     off[r] = before + rank;
   }
   __syncthreads();
-  // (warp, digit) offsets: the digit's base, the earlier tiles' counts of
-  // the digit and the earlier warps' counts
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int b = threadIdx.x + h * kSortThreads;
-    int32_t acc = dbase[b] + (h ? th1 : th0);
+  {  // (warp, digit) offsets: the digit's base, the earlier tiles' counts of
+     // the digit and the earlier warps' counts
+    const int b = threadIdx.x;
+    int32_t acc = dbase[b] + th0;
 #pragma unroll
     for (int k = 0; k < kWarps; ++k) {
       const int32_t c = wcnt[k][b];
@@ -196,7 +187,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
   }
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < kItemsPerThread; ++r) {
+  for (int r = 0; r < kScatterItems; ++r) {
     const int64_t i = w0 + r * 32 + lane;
     if (i < n) {
       const int d = (key[r] >> shift) & (kBins - 1);
@@ -535,7 +526,7 @@ static pdf_status radix_pass(const int32_t* kin, const int32_t* vin, int64_t n, 
                              int32_t* hist, int32_t* part, int32_t* kout, int32_t* vout, cudaStream_t st) {
   PDF_KERNEL("k_radix_hist", st, k_radix_hist<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(kin, n, shift, n_tiles, hist););
   PDF_KERNEL("k_scan_bins", st, k_scan_bins<<<kBins, 1024, 0, st>>>(hist, n_tiles, part););
-  PDF_KERNEL("k_radix_scatter", st, k_radix_scatter<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(
+  PDF_KERNEL("k_radix_scatter", st, k_radix_scatter<<<(unsigned)n_tiles, kScatterThreads, 0, st>>>(
                                         kin, vin, n, shift, n_tiles, hist, part, kout, vout););
   return PDF_OK;
 }
