@@ -102,29 +102,48 @@ __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t* tota
 // Per digit, one block each: the exclusive prefix of the digit's tile
 // counts over the tiles (in place; the digit's row of hist is contiguous)
 // and the digit's total in part[digit].  The scatter adds the totals of the
-// smaller digits.
-__global__ void __launch_bounds__(1024) k_scan_bins(int32_t* __restrict__ hist, int64_t n_tiles,
-                                                    int32_t* __restrict__ part) {
+// smaller digits.  512 threads (the 512 digit blocks fit on the GPU at once,
+// four per SM); each round stages 4,096 entries through shared memory with
+// coalesced loads and stores, thread t scanning entries 8t .. 8t + 7 (one
+// padding word per 32 keeps those reads free of bank conflicts).
+constexpr int kScanThreads = 512;
+constexpr int kScanPer = 8;
+constexpr int kScanRound = kScanThreads * kScanPer;  // 4096
+__device__ __forceinline__ int scan_pad(int i) { return i + (i >> 5); }
+__global__ void __launch_bounds__(kScanThreads, 4) k_scan_bins(int32_t* __restrict__ hist, int64_t n_tiles,
+                                                            int32_t* __restrict__ part) {
+  __shared__ int32_t s[kScanRound + kScanRound / 32];
   int32_t* row = hist + (int64_t)blockIdx.x * n_tiles;
   int32_t carry = 0;
-  for (int64_t start = 0; start < n_tiles; start += 4 * (int64_t)blockDim.x) {
-    // each thread owns 4 consecutive entries
-    const int64_t base = start + 4 * (int64_t)threadIdx.x;
-    int32_t v[4];
+  for (int64_t start = 0; start < n_tiles; start += kScanRound) {
+#pragma unroll
+    for (int j = 0; j < kScanPer; ++j) {
+      const int i = threadIdx.x + j * kScanThreads;
+      s[scan_pad(i)] = (start + i < n_tiles) ? row[start + i] : 0;
+    }
+    __syncthreads();
+    int32_t v[kScanPer];
     int32_t sum = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      v[j] = (base + j < n_tiles) ? row[base + j] : 0;
+    for (int j = 0; j < kScanPer; ++j) {
+      v[j] = s[scan_pad(kScanPer * threadIdx.x + j)];
       sum += v[j];
     }
     int32_t total;
-    int32_t ex = block_exclusive_scan(sum, &total) + carry;
+    int32_t ex = block_exclusive_scan(sum, &total) + carry;  // (its barriers order the reads above)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (base + j < n_tiles) row[base + j] = ex;
+    for (int j = 0; j < kScanPer; ++j) {
+      s[scan_pad(kScanPer * threadIdx.x + j)] = ex;
       ex += v[j];
     }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kScanPer; ++j) {
+      const int i = threadIdx.x + j * kScanThreads;
+      if (start + i < n_tiles) row[start + i] = s[scan_pad(i)];
+    }
     carry += total;
+    __syncthreads();  // the next round overwrites s
   }
   if (threadIdx.x == 0) part[blockIdx.x] = carry;
 }
@@ -525,7 +544,7 @@ static int blocks_for(int64_t n, int threads) {
 static pdf_status radix_pass(const int32_t* kin, const int32_t* vin, int64_t n, int shift, int64_t n_tiles,
                              int32_t* hist, int32_t* part, int32_t* kout, int32_t* vout, cudaStream_t st) {
   PDF_KERNEL("k_radix_hist", st, k_radix_hist<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(kin, n, shift, n_tiles, hist););
-  PDF_KERNEL("k_scan_bins", st, k_scan_bins<<<kBins, 1024, 0, st>>>(hist, n_tiles, part););
+  PDF_KERNEL("k_scan_bins", st, k_scan_bins<<<kBins, kScanThreads, 0, st>>>(hist, n_tiles, part););
   PDF_KERNEL("k_radix_scatter", st, k_radix_scatter<<<(unsigned)n_tiles, kScatterThreads, 0, st>>>(
                                         kin, vin, n, shift, n_tiles, hist, part, kout, vout););
   return PDF_OK;
