@@ -422,6 +422,22 @@ __global__ void __launch_bounds__(256, 3) k_elem_stats_grp(const int32_t* __rest
   }
 }
 
+// 1 / c for the element counts of a node (the correctly rounded quotients,
+// as the division gives them): GB300's FP64 pipe bounds the node passes,
+// and a division costs it more than a dozen instructions.
+constexpr int kRecipMax = 64;
+struct RecipTable {
+  double v[kRecipMax + 1];
+  constexpr RecipTable() : v() {
+    v[0] = 0.0;
+    for (int c = 1; c <= kRecipMax; ++c) v[c] = 1.0 / (double)c;
+  }
+};
+__device__ const RecipTable kRecip;
+__device__ __forceinline__ double recip_count(int32_t c) {
+  return c <= kRecipMax ? __ldg(&kRecip.v[c]) : 1.0 / (double)c;
+}
+
 // Node pass: mean over the non-empty surrounding elements (twins merged);
 // a node with none keeps its previous value.
 __global__ void k_node_stats(const int32_t* __restrict__ nse_off, const int32_t* __restrict__ nse,
@@ -434,7 +450,9 @@ __global__ void k_node_stats(const int32_t* __restrict__ nse_off, const int32_t*
     int c = 0;
     for (int32_t i = nse_off[n]; i < nse_off[n + 1]; ++i) {
       const double* s = es + (int64_t)nse[i] * PDF_NES;
-      if (s[0] <= 0.0) continue;
+      // s[0] = N >= 0: the bits of +0.0 (and -0.0) are not positive, those of
+      // any N > 0 are (an integer test instead of an FP64 compare)
+      if (__double_as_longlong(s[0]) <= 0) continue;
 #pragma unroll
       for (int q = 0; q < PDF_NNS; ++q) acc[q] += s[1 + q];
       ++c;
@@ -443,7 +461,7 @@ __global__ void k_node_stats(const int32_t* __restrict__ nse_off, const int32_t*
       atomicAdd(reinterpret_cast<unsigned long long*>(kept), 1ULL);
       continue;
     }
-    const double inv = 1.0 / (double)c;
+    const double inv = recip_count(c);
 #pragma unroll
     for (int q = 0; q < PDF_NNS; ++q) ns[(int64_t)n * PDF_NNS + q] = acc[q] * inv;
   }
@@ -483,7 +501,7 @@ __global__ void k_node_grad1(const int32_t* __restrict__ nse_off, const int32_t*
       acc[6] += g[7];
     }
     double* D = nd + (int64_t)n * PDF_NND;
-    const double inv = 1.0 / (c > 0 ? (double)c : 1.0);
+    const double inv = recip_count(c > 0 ? c : 1);
 #pragma unroll
     for (int q = 0; q < 6; ++q) D[q] = acc[q] * inv;
     D[9] = acc[6] * inv;
@@ -516,7 +534,7 @@ __global__ void k_node_grad2(const int32_t* __restrict__ nse_off, const int32_t*
       const double* g = eg + (int64_t)nse[i] * 8;
       acc[0] += g[0]; acc[1] += g[1]; acc[2] += g[2];
     }
-    const double inv = 1.0 / (c > 0 ? (double)c : 1.0);
+    const double inv = recip_count(c > 0 ? c : 1);
     double* D = nd + (int64_t)n * PDF_NND;
     D[6] = acc[0] * inv; D[7] = acc[1] * inv; D[8] = acc[2] * inv;
   }
