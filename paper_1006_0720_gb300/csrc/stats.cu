@@ -148,7 +148,15 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan_bins(int32_t* __restri
   if (threadIdx.x == 0) part[blockIdx.x] = carry;
 }
 
-// Stable scatter of one tile (512 threads of 8 items).
+// Stable scatter of one tile, 512 threads of 8 items.  Warp w owns the
+// tile's items [256 w, 256 (w + 1)) and ranks them in 8 rounds of 32 in
+// index order (match.any groups equal digits, one lane of each group
+// advances the warp's own row of shared digit counters, so no block barrier
+// between rounds); one pass over the (warp, digit) counts then gives every
+// warp and digit its output offset, so items with equal digits keep their
+// index order.  Twice the warps per SM of 256 threads with 16 items each
+// (64 registers, two blocks per SM): the ranking waits on the MIO queue, and
+// more warps cover it.
 constexpr int kScatterThreads = 512;
 constexpr int kScatterItems = kTile / kScatterThreads;  // 8
 __global__ void __launch_bounds__(kScatterThreads, 2) k_radix_scatter(
