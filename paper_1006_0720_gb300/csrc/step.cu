@@ -18,6 +18,12 @@ struct CoeffParams {
   double src_x, src_y, src_r, Cs, Ct;
   double C1, C2, C3, C4, CT, Cv, gamma5, Comega1, Comega2, C0_slm;
   double sdt, s2nu, s2c3c4dt;  // sqrt(dt), sqrt(2 nu), sqrt(2 C3 C4 dt): once per call, not per element
+  // products and quotients of the constants, formed once per call on the host
+  // with the same operations as before (GB300's FP64 pipe bounds the node pass)
+  double g5_3;     // gamma5 / 3
+  double half_1mC1;  // 0.5 (1 - C1)
+  double nuCT2;    // nu CT CT
+  double two_nu;   // 2 nu
 };
 
 static CoeffParams coeff_params(const pdf_model_params* p) {
@@ -30,6 +36,10 @@ static CoeffParams coeff_params(const pdf_model_params* p) {
   c.sdt = std::sqrt(p->dt);
   c.s2nu = std::sqrt(2.0 * p->nu);
   c.s2c3c4dt = std::sqrt(2.0 * p->C3 * p->C4 * p->dt);
+  c.g5_3 = p->gamma5 / 3.0;
+  c.half_1mC1 = 0.5 * (1.0 - p->C1);
+  c.nuCT2 = p->nu * p->CT * p->CT;
+  c.two_nu = 2.0 * p->nu;
   return c;
 }
 
@@ -58,9 +68,9 @@ __device__ void relax_rhs(const double* S, const double* D, const CoeffParams& P
   const double inv_2k = 0.5 * inv_k;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) b[i][j] = R[i][j] * inv_2k - (i == j ? 1.0 / 3.0 : 0.0);
-  const double g3 = P.gamma5 / 3.0;
+  const double g3 = P.g5_3;
   const double cg = P.C2 * Av + g3;
-  const double diag = 0.5 * (1.0 - P.C1) * k * S[3];
+  const double diag = P.half_1mC1 * k * S[3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
       // b_ik dU_k/dx_j (zero for j = 2) and b_il dU_j/dx_l (l < 2)
@@ -89,7 +99,7 @@ __global__ void k_node_coeff(int32_t n_nodes, const double* __restrict__ ns, con
     const double k = 0.5 * (S[5] + S[6] + S[7]);
     const double kg = fmax(k, kKFloor);
     const double om = S[3];
-    const double eps = (P.closure == PDF_CLOSURE_SLM) ? k * om : om * (k + P.nu * P.CT * P.CT * om);
+    const double eps = (P.closure == PDF_CLOSURE_SLM) ? k * om : om * (k + P.nuCT2 * om);
     const double eg = fmax(eps, kEFloor);
     const double inv_kg = 1.0 / kg, inv_eg = 1.0 / eg;
     c[0] = S[0]; c[1] = S[1]; c[2] = S[2];
@@ -104,9 +114,9 @@ __global__ void k_node_coeff(int32_t n_nodes, const double* __restrict__ ns, con
       for (int q = 0; q < 9; ++q) c[12 + q] = (q % 4 == 0) ? g : 0.0;
       c[21] = sqrt(P.C0_slm * fmax(eps, 0.0));
     } else {
-      c[9] = dpx + 2.0 * P.nu * D[6];
-      c[10] = dpy + 2.0 * P.nu * D[7];
-      c[11] = 2.0 * P.nu * D[8];
+      c[9] = dpx + P.two_nu * D[6];
+      c[10] = dpy + P.two_nu * D[7];
+      c[11] = P.two_nu * D[8];
       double w9[9];
       if (wp) {
         for (int q = 0; q < 9; ++q) w9[q] = wp[(int64_t)q * n_nodes + n];
